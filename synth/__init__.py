@@ -1,0 +1,254 @@
+"""Seeded synthetic scene generators.
+
+This module builds the inputs that both the CUDA path and the FP64 oracle consume:
+tetrahedral meshes of hex lattices (5-tet split with alternating parity), material
+draws, initial velocities, targets, and vertex-plane contact sets with their frames.
+It holds geometry and random draws only -- none of the adjoint method's arithmetic --
+so that the oracle and the GPU library can share inputs without sharing any code.
+
+All randomness goes through ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GRAVITY = 9.81  # m/s^2, along -z of the world frame
+
+
+# --------------------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------------------
+
+# Corners of a unit cell, index = x + 2y + 4z.  Even cells put the tet made of the four
+# odd corners in the middle; odd cells the four even corners.  Neighbouring cells then
+# agree on every face diagonal (conforming mesh).
+_EVEN_SPLIT = ((1, 2, 4, 7), (0, 1, 2, 4), (3, 1, 2, 7), (5, 1, 4, 7), (6, 2, 4, 7))
+_ODD_SPLIT = ((0, 3, 5, 6), (1, 0, 3, 5), (2, 0, 3, 6), (4, 0, 5, 6), (7, 3, 5, 6))
+
+
+def hex_tet_mesh(nx: int, ny: int, nz: int, cell: float, origin=(0.0, 0.0, 0.0)):
+    """Lattice of nx*ny*nz cubic cells of edge ``cell``, each split into 5 tets.
+
+    Returns (X, tets): X float64 [n_v, 3] (vertex index = i + (nx+1)(j + (ny+1)k)),
+    tets int32 [n_t, 4], every tet positively oriented.
+    """
+    ii, jj, kk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    vid = lambda i, j, k: i + (nx + 1) * (j + (ny + 1) * k)  # noqa: E731
+    X = np.zeros(((nx + 1) * (ny + 1) * (nz + 1), 3))
+    X[vid(ii, jj, kk).ravel(), 0] = ii.ravel() * cell + origin[0]
+    X[vid(ii, jj, kk).ravel(), 1] = jj.ravel() * cell + origin[1]
+    X[vid(ii, jj, kk).ravel(), 2] = kk.ravel() * cell + origin[2]
+    tets = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                corner = [vid(i + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1)) for c in range(8)]
+                split = _EVEN_SPLIT if (i + j + k) % 2 == 0 else _ODD_SPLIT
+                for t in split:
+                    tets.append([corner[c] for c in t])
+    tets = np.asarray(tets, dtype=np.int64)
+    # orientation: swap two vertices where the signed volume is negative (mesh hygiene)
+    e = X[tets[:, 1:]] - X[tets[:, [0]]]
+    neg = np.linalg.det(e) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    return X, tets.astype(np.int32)
+
+
+# --------------------------------------------------------------------------------------
+# contacts
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class Plane:
+    """Rigid plane {x : n.x = offset} with friction coefficient mu; frame rows n, t1, t2."""
+    normal: np.ndarray
+    offset: float
+    mu: float
+    t1: np.ndarray = None
+    t2: np.ndarray = None
+
+    def __post_init__(self):
+        self.normal = np.asarray(self.normal, float)
+        if self.t1 is None:
+            a = np.array([1.0, 0.0, 0.0]) if abs(self.normal[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+            t1 = a - self.normal * (a @ self.normal)
+            self.t1 = t1 / np.linalg.norm(t1)
+        self.t1 = np.asarray(self.t1, float)
+        if self.t2 is None:
+            self.t2 = np.cross(self.normal, self.t1)
+        self.t2 = np.asarray(self.t2, float)
+
+    @property
+    def frame(self):
+        return np.stack([self.normal, self.t1, self.t2])
+
+
+@dataclass
+class Contacts:
+    """Vertex-plane contact set, frozen for one step.
+
+    vertex int32 [n_c]; frame float64 [n_c, 3, 3] (rows n, t1, t2); d_n float64 [n_c]
+    (normal gap delta_n = n.x - d_n); d_f float64 [n_c, 2] (tangential offset, zero here);
+    mu float64 [n_c]; region int32 [n_c] (friction region id), n_regions.
+    """
+    vertex: np.ndarray
+    frame: np.ndarray
+    d_n: np.ndarray
+    d_f: np.ndarray
+    mu: np.ndarray
+    region: np.ndarray
+    n_regions: int
+
+    @property
+    def n(self):
+        return int(self.vertex.shape[0])
+
+    @staticmethod
+    def empty():
+        return Contacts(np.zeros(0, np.int32), np.zeros((0, 3, 3)), np.zeros(0), np.zeros((0, 2)),
+                        np.zeros(0), np.zeros(0, np.int32), 1)
+
+
+def detect_contacts(x_prev: np.ndarray, planes, margin: float, candidates=None) -> Contacts:
+    """Vertices whose gap to a plane at the previous positions is below ``margin``.
+
+    ``candidates`` restricts the search to a vertex subset (e.g. a bottom face).
+    Friction regions: one region per plane.
+    """
+    verts = np.arange(x_prev.shape[0]) if candidates is None else np.asarray(candidates)
+    vs, frames, dn, mus, reg = [], [], [], [], []
+    for pi, pl in enumerate(planes):
+        gap = x_prev[verts] @ pl.normal - pl.offset
+        sel = verts[gap < margin]
+        vs.append(sel)
+        frames.append(np.repeat(pl.frame[None], len(sel), 0))
+        dn.append(np.full(len(sel), pl.offset))
+        mus.append(np.full(len(sel), pl.mu))
+        reg.append(np.full(len(sel), pi))
+    v = np.concatenate(vs).astype(np.int32)
+    return Contacts(v, np.concatenate(frames).reshape(-1, 3, 3), np.concatenate(dn),
+                    np.zeros((len(v), 2)), np.concatenate(mus), np.concatenate(reg).astype(np.int32),
+                    max(1, len(planes)))
+
+
+# --------------------------------------------------------------------------------------
+# scenes
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class Scene:
+    """Mesh + material + step size.  E, nu are per tet (float64 [n_t])."""
+    X: np.ndarray
+    tets: np.ndarray
+    E: np.ndarray
+    nu: np.ndarray
+    density: float
+    h: float
+    gravity: np.ndarray
+    planes: list = field(default_factory=list)
+    contact_candidates: np.ndarray = None
+    margin: float = 2e-3
+    eps: float = 1e-4
+    name: str = ""
+
+    @property
+    def n_verts(self):
+        return int(self.X.shape[0])
+
+    @property
+    def n_tets(self):
+        return int(self.tets.shape[0])
+
+    def contacts(self, x_prev):
+        if not self.planes:
+            return Contacts.empty()
+        return detect_contacts(x_prev, self.planes, self.margin, self.contact_candidates)
+
+
+@dataclass
+class Problem:
+    """A scene plus the start state (q0, v0), per-vertex external forces besides gravity
+    (zeros unless stated), and a target for the loss."""
+    scene: Scene
+    q0: np.ndarray
+    v0: np.ndarray
+    f_ctrl: np.ndarray
+    q_target: np.ndarray
+
+
+def cube_drop(seed: int = 0, cells: int = 4, edge: float = 0.1, drop: float = 0.01,
+              E: float = 1e5, nu: float = 0.4, density: float = 1000.0, h: float = 1.0 / 60.0,
+              mu: float = 0.5, eps: float = 1e-4, v_sigma: float = 0.01, tgt_sigma: float = 1e-3,
+              margin: float = 2e-3) -> Problem:
+    """Neo-Hookean cube of cells^3 hex cells x 5 tets, bottom ``drop`` above the ground z=0.
+
+    Default: 4x4x4 cells (125 vertices, 320 tets), edge 0.1 m, dropped 1 cm, E=1e5, nu=0.4,
+    rho=1000, h=1/60, ground mu=0.5, eps=1e-4, v0 ~ N(0, 0.01^2), target = rest + N(0, 1e-3^2).
+    """
+    rng = np.random.default_rng(seed)
+    X, tets = hex_tet_mesh(cells, cells, cells, edge / cells, origin=(-edge / 2, -edge / 2, drop))
+    bottom = np.nonzero(np.isclose(X[:, 2], drop))[0]
+    scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), density, h,
+                  np.array([0.0, 0.0, -GRAVITY]), [Plane([0.0, 0.0, 1.0], 0.0, mu, [1.0, 0, 0], [0, 1.0, 0])],
+                  bottom, margin, eps, f"cube{cells}")
+    v0 = rng.normal(0.0, v_sigma, X.shape)
+    q_tgt = X + rng.normal(0.0, tgt_sigma, X.shape)
+    return Problem(scene, X.copy(), v0, np.zeros_like(X), q_tgt)
+
+
+def beam_incline(seed: int = 0, nx: int = 40, ny: int = 10, nz: int = 10, cell: float = 0.01,
+                 angle_deg: float = 20.0, E: float = 5e5, nu: float = 0.45, density: float = 1000.0,
+                 h: float = 1.0 / 100.0, mu: float = 0.3, eps: float = 1e-4, gap0: float = 1e-7,
+                 margin: float = 2e-3) -> Problem:
+    """Beam of nx*ny*nz cells x 5 tets lying on a plane inclined by ``angle_deg`` about y.
+
+    Default: 40x10x10 cells of 1 cm (4,961 vertices, 20,000 tets), 20 deg incline, mu=0.3
+    (below tan 20 deg, so it slides), E=5e5, nu=0.45, h=1/100, starting at rest with its
+    bottom face ``gap0`` above the plane.  Target: the start positions (the loss used with it
+    is a centre-of-mass error, which the caller defines).
+    """
+    del seed  # deterministic geometry; kept for a uniform signature
+    th = np.deg2rad(angle_deg)
+    Xl, tets = hex_tet_mesh(nx, ny, nz, cell, origin=(0.0, -ny * cell / 2, gap0))
+    rot = np.array([[np.cos(th), 0.0, -np.sin(th)], [0.0, 1.0, 0.0], [np.sin(th), 0.0, np.cos(th)]])
+    X = Xl @ rot.T
+    n = rot @ np.array([0.0, 0.0, 1.0])
+    t1 = rot @ np.array([1.0, 0.0, 0.0])
+    bottom = np.nonzero(np.isclose(Xl[:, 2], gap0))[0]
+    scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), density, h,
+                  np.array([0.0, 0.0, -GRAVITY]), [Plane(n, 0.0, mu, t1, [0.0, 1.0, 0.0])], bottom,
+                  margin, eps, f"beam{nx}x{ny}x{nz}")
+    return Problem(scene, X.copy(), np.zeros_like(X), np.zeros_like(X), X.copy())
+
+
+def two_tet(seed: int = 0, E: float = 1e5, nu: float = 0.4, h: float = 1.0 / 60.0, mu: float = 0.5,
+            eps: float = 1e-4, jitter: float = 0.1) -> Problem:
+    """Tiny jittered mesh (one cell, 5 tets, 8 vertices) resting on the ground, 4 contacts."""
+    rng = np.random.default_rng(seed)
+    X, tets = hex_tet_mesh(1, 1, 1, 0.05, origin=(0.0, 0.0, 1e-6))
+    X[4:] += rng.normal(0, jitter * 0.05, (4, 3))
+    bottom = np.arange(4)
+    scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), 1000.0, h,
+                  np.array([0.0, 0.0, -GRAVITY]), [Plane([0.0, 0.0, 1.0], 0.0, mu, [1.0, 0, 0], [0, 1.0, 0])],
+                  bottom, 2e-3, eps, "twotet")
+    v0 = rng.normal(0.0, 0.01, X.shape)
+    return Problem(scene, X.copy(), v0, np.zeros_like(X), X + rng.normal(0, 1e-3, X.shape))
+
+
+def random_deformation_gradients(n: int, seed: int = 0, strain: float = 0.05) -> np.ndarray:
+    """n random F = R (I + S): R a random rotation, S ~ strain * N(0,1) (float64 [n, 3, 3])."""
+    rng = np.random.default_rng(seed)
+    A = rng.normal(size=(n, 3, 3))
+    Q, Rr = np.linalg.qr(A)
+    Q = Q * np.sign(np.diagonal(Rr, axis1=1, axis2=2))[:, None, :]
+    Q[np.linalg.det(Q) < 0, :, 0] *= -1
+    S = strain * rng.normal(size=(n, 3, 3))
+    return Q @ (np.eye(3) + S)
+
+
+def random_seed_vectors(n_verts: int, seed: int = 0, scale: float = 1.0):
+    """Seeded dL/dq, dL/dv seeds (float64 [n_v, 3] each)."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.normal(size=(n_verts, 3)), scale * rng.normal(size=(n_verts, 3))
