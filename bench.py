@@ -1,0 +1,314 @@
+"""Benchmark: adjoint gradients/s of one implicit step on the beam-on-incline scene.
+
+Workload (the mid-size single scene): Neo-Hookean beam of 40x10x10 hex cells x 5 tets (20,000 tets,
+4,961 vertices), E=5e5, nu=0.45, rho=1000, resting on a 20 deg plane with mu=0.3 (451 frictional
+contacts, eps=1e-4), h=1/100.  The state is produced on the GPU by the forward step (3 steps from
+rest, so the beam slides); one bench step = one complete adjoint step through the C-ABI: assembly
+of script_A^T (per-tet SVD Jacobians, contact blocks), Woodbury set-up (Delassus, capacitance,
+its inversion), GMRES to rtol 1e-8 and all gradient contractions (dL/dqbar, dL/dvbar, dL/dfext,
+dL/dE, dL/dnu per tet, dL/dmu).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
+events on the library's stream; L2 (129 MB) is flushed by writing a 512 MB buffer before every
+timed step (the working set, ~90 MB, would otherwise stay resident).  Multi-GPU: the path does
+not shard within a scene, so N ranks run N independent replicas (one process per GPU); value is
+the adjoints of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "adjoint gradients/sec per step (batched FP32/64 vs plain FP64) at rel err <=1e-3"
+WORKLOAD = ("beam 40x10x10 cells x 5 tets (20000 tets, 4961 verts), 451 frictional contacts on a 20deg incline, "
+            "mu=0.3, eps=1e-4, h=1/100, one adjoint step (state: GPU forward, 3 steps from rest)")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6777.0), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle, single-threaded, in a child process
+# --------------------------------------------------------------------------------------------
+def oracle_times(steps, warmup):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-m", "oracle.timing", "--steps", str(steps), "--warmup", str(warmup)],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    d = oracle_times(args.steps, args.warmup)
+    secs = d["seconds"]
+    total = sum(secs)
+    val = len(secs) / total
+    sample = (f"{len(secs)} oracle adjoints (explicit assembly + direct sparse LU + contractions) of the beam "
+              f"at the oracle's start point of step 1, {d['threads']} thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "gradients/s", "n_gpus": args.gpus,
+        "steps": len(secs), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(secs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": val, "unit": "gradients/s", "cores": d["threads"], "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "gradients/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_2603_16478_gb300 as pkg
+    import synth
+
+    pb = synth.beam_incline()
+    sc = pb.scene
+    ct = sc.contacts(pb.q0)
+    ctx = pkg.Context(local)
+    scene = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    contacts = pkg.Contacts(T(ct.vertex, torch.int32), T(ct.frame), T(ct.d_n), T(ct.mu), None,
+                            T(ct.region, torch.int32), ct.n_regions)
+    # converged state from the GPU forward step: 3 steps from rest
+    q_prev, v_prev = T(pb.q0), T(pb.v0)
+    fwd_stats = []
+    for _ in range(3):
+        q, lam, fs = pkg.forward_step(scene, contacts, q_prev, v_prev, None, tuple(sc.gravity), eps=sc.eps)
+        fwd_stats.append(fs)
+        v_prev = (q - q_prev) / sc.h
+        q_prev, q = q, None
+    q_prev_adj = q_prev - v_prev * sc.h   # the differentiated step maps q_prev_adj -> q_adj
+    q_adj = q_prev
+    lam_adj = lam.contiguous()
+    # centroid loss L = ||mean(q) - c_tgt||^2, target 1 mm further down the slope
+    c_tgt = q_adj.mean(0) + 1e-3 * T(sc.planes[0].t1)
+    dL_dq = (2.0 * (q_adj.mean(0) - c_tgt) / sc.n_verts).expand(sc.n_verts, 3).contiguous()
+    dL_dv = torch.zeros_like(dL_dq)
+    outputs = {k: torch.empty(v, dtype=torch.float64, device=dev) for k, v in (
+        ("dL_dq_prev", (sc.n_verts, 3)), ("dL_dv_prev", (sc.n_verts, 3)), ("dL_dfext", (sc.n_verts, 3)),
+        ("z", (sc.n_verts, 3)), ("dL_dE", (sc.n_tets,)), ("dL_dnu", (sc.n_tets,)), ("dL_dmu", (1,)),
+        ("dL_dmu_contact", (ct.n,)))}
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one(mem="device", ins=None, outs=None):
+        a = ins or (q_adj, q_prev_adj, lam_adj, dL_dq, dL_dv, contacts)
+        return pkg.adjoint_step(scene, a[5], a[0], a[1], a[2], a[3], a[4], eps=sc.eps, rtol=1e-8, memory=mem,
+                                outputs=outs or outputs, stream=stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()  # evict the previous step's working set from L2
+            ev[i][0].record(stream)
+            _, st = one()
+            ev[i][1].record(stream)
+            stats.append(st)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the C-ABI with host buffers (copies inside the timed region) ----
+    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+    h_contacts = pkg.Contacts(pin(contacts.vertex), pin(contacts.frame), pin(contacts.d_n), pin(contacts.mu), None,
+                              pin(contacts.region), contacts.n_regions)
+    h_in = (pin(q_adj), pin(q_prev_adj), pin(lam_adj), pin(dL_dq), pin(dL_dv), h_contacts)
+    h_out = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in outputs.items()}
+    h2d = sum(t.numel() * t.element_size() for t in h_in[:5]) + sum(
+        t.numel() * t.element_size() for t in (h_contacts.vertex, h_contacts.frame, h_contacts.d_n, h_contacts.mu,
+                                                h_contacts.region))
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+    with torch.cuda.stream(stream):
+        e2e_t = []
+        if not args.no_e2e:
+            one("host", h_in, h_out)
+        for _ in range(0 if args.no_e2e else max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            one("host", h_in, h_out)  # synchronous: returns after the outputs reached host memory
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world / (sum(e2e_t) / len(e2e_t)) if e2e_t else None
+
+    # ---- roofline of the dominant kernel ----
+    it = statistics.median(s["iterations"] for s in stats)
+    cap_ms = statistics.mean(s["ms_cap_inverse"] for s in stats)
+    kry_ms = statistics.mean(s["ms_krylov"] for s in stats)
+    ncap = stats[0]["capacitance_dim"]
+    info = scene.info()
+    hbm_peak, hbm_src = peaks()
+    launches = int(statistics.median(s["kernel_launches"] for s in stats))
+    if cap_ms >= kry_ms:
+        # capacitance inversion (Gauss-Jordan, FP64): n^3 fused multiply-adds, ALU bound
+        flops = 2.0 * ncap ** 3
+        achieved = flops / (cap_ms / 1e3) / 1e12
+        peak = 1.25  # nominal FP64 of the part, TFLOP/s
+        roof = {"kernel": "k_gj (capacitance inversion, FP64 Gauss-Jordan)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (no FP64 entry in the measured peaks)",
+                "ms_per_launch": cap_ms}
+    else:
+        n3 = 3 * sc.n_verts
+        per_it = (info["n_blocks"] * (72 + 4) + 2 * n3 * 8) + 4 * (info["nnz_Linv"] * 12 + 2 * n3 * 8) + ncap * ncap * 8
+        per_it += (it / 2 + 3) * 2 * n3 * 8
+        achieved = per_it * it / (kry_ms / 1e3) / 1e9
+        roof = {"kernel": "Krylov stage (SpMV + Woodbury apply + CGS2)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": hbm_src}
+
+    # ---- CPU baseline: the oracle, one thread, bounded sample ----
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            d = oracle_times(3, 1)
+            cpu = {"value": len(d["seconds"]) / sum(d["seconds"]), "unit": "gradients/s", "cores": d["threads"],
+                   "kind": "oracle", "sample": f"{len(d['seconds'])} oracle adjoints of the beam (assembly + direct "
+                   "sparse LU + contractions) at the oracle's start point of step 1, after 1 warm-up"}
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "plain FP64", "preconditioner": "Woodbury",
+                       "solver": "GMRES(64)", "rtol": 1e-8, "krylov_iterations": it, "capacitance_dim": ncap,
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                       "wall_s": t_wall, "stage_ms": {k: statistics.mean(s[k] for s in stats) for k in
+                                                      ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract",
+                                                       "ms_cap_inverse")},
+                       "forward_newton_iters": [f["newton_iters"] for f in fwd_stats],
+                       "forward_residual": [f["residual"] for f in fwd_stats],
+                       "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"]},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "gradients/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches * args.steps, "clocks": clk,
+        }))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

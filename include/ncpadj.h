@@ -1,0 +1,239 @@
+/*
+ * ncpadj -- analytical adjoint of one implicit time step of a Neo-Hookean tet mesh with
+ * smoothed Signorini-Coulomb (Fischer-Burmeister) contact, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: "Fast and Reliable Gradients for Deformables Across Frictional Contact Regimes".
+ * One call of ncpadj_adjoint_step computes, for a converged forward state,
+ *   script_A^T z = dL/dq + dL/dv / h                                  (Eq. adjoint, Sec. 4.1)
+ *   script_A = A - Delta A + h^2 J_c^T K_c J_c                         (Eq. differential_2)
+ * with the per-tet SVD projection Jacobians of Sec. 4.3 / App. B, the per-contact smoothed
+ * FB blocks of Sec. 4.2 / Eq. final_diff_contact, a Woodbury-preconditioned Krylov solve
+ * (Sec. 4.4, Eq. woodbury_formula) and the gradient contractions dL/dx = z^T K_x
+ * (Eq. compute_gradient, App. B.3).
+ *
+ * Conventions
+ *  - Positions are [n_verts][3] row-major float64 (DOF 3v+r is coordinate r of vertex v).
+ *  - Tets are [n_tets][4] int32, positively oriented (det[X1-X0, X2-X0, X3-X0] > 0).
+ *  - Contacts are vertex-plane pairs.  frame is [n_c][3][3] row-major with rows n, t1, t2.
+ *    delta_n = n . q_v - d_n,  delta_f = [t1; t2](q_v - q_prev_v) - d_f     (Eq. contact).
+ *    The contact force lambda_c = (lambda_n, lambda_f1, lambda_f2) is in frame coordinates
+ *    and enters the momentum equation as -h^2 J_c^T lambda_c.
+ *  - Ownership: the library never frees or keeps caller pointers past a call.  Handles own
+ *    only device workspace, the scene's operators and its elastic factor.
+ *  - Memory: with options.memory == NCPADJ_MEM_DEVICE every array argument of
+ *    ncpadj_adjoint_step is a device pointer; with NCPADJ_MEM_HOST every one is a host
+ *    pointer (pinned memory recommended) and the call copies inputs in and outputs out
+ *    on the given stream.  Scene descriptions are always host arrays.
+ *  - Output pointers may be NULL (that output is skipped).  Non-NULL outputs are
+ *    overwritten, not accumulated.
+ *  - Errors: every call returns a status; nothing aborts or throws across the ABI.
+ *    Invalid sizes or NULL required pointers give NCPADJ_ERR_INVALID_ARG before any
+ *    launch.  ncpadj_last_error() returns a thread-local message for the last failure.
+ *  - Streams: the stream is borrowed (cudaStream_t passed as void*; NULL = legacy default
+ *    stream).  ncpadj_adjoint_step synchronises that stream before it returns (it reads the
+ *    solver status), so it is not capturable in a CUDA graph.
+ *  - Threads: a scene's workspace is used by every call on that scene; calls on the same
+ *    scene must not overlap.
+ */
+#ifndef NCPADJ_H
+#define NCPADJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NCPADJ_OK = 0,
+  NCPADJ_ERR_INVALID_ARG = 1,      /* bad size, NULL required pointer, bad option value */
+  NCPADJ_ERR_CUDA = 2,             /* a CUDA runtime call failed (message in last_error) */
+  NCPADJ_ERR_OOM = 3,              /* device allocation failed */
+  NCPADJ_ERR_INVERTED_ELEMENT = 4, /* some tet has det F <= 0 (Neo-Hookean needs J > 0) */
+  NCPADJ_ERR_NOT_CONVERGED = 5,    /* Krylov hit max_iters; outputs hold the last iterate */
+  NCPADJ_ERR_NONFINITE = 6,        /* NaN/Inf met in the solve */
+  NCPADJ_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up */
+  NCPADJ_ERR_NOT_FACTORED = 8,     /* the scene's elastic factor is missing */
+  NCPADJ_ERR_UNSUPPORTED = 9,      /* option combination not implemented */
+  NCPADJ_ERR_CONTACT_DOMAIN = 10   /* a frictional contact has zero slip (no direction) */
+} ncpadj_status;
+
+enum { NCPADJ_FP64 = 0, NCPADJ_MIXED = 1 };
+enum {
+  NCPADJ_PRECOND_NONE = 0,
+  NCPADJ_PRECOND_JACOBI = 1,   /* diag(script_A)^{-1} (Sec. 4.4, Jacobi preconditioner) */
+  NCPADJ_PRECOND_ELASTIC = 2,  /* A^{-1} by the elastic factor (sparse-inverse preconditioner) */
+  NCPADJ_PRECOND_WOODBURY = 3  /* (A + K_c)^{-1} by Eq. woodbury_formula (default) */
+};
+enum { NCPADJ_SOLVER_AUTO = 0, NCPADJ_SOLVER_CG = 1, NCPADJ_SOLVER_GMRES = 2 };
+enum { NCPADJ_MEM_DEVICE = 0, NCPADJ_MEM_HOST = 1 };
+
+typedef struct ncpadj_ctx_s* ncpadj_ctx;     /* one per device; owns the CUDA device binding */
+typedef struct ncpadj_scene_s* ncpadj_scene; /* mesh + material + h + elastic factor + workspace */
+
+/* Library version string (static storage). */
+const char* ncpadj_version(void);
+/* Human-readable name of a status (static storage). */
+const char* ncpadj_status_string(ncpadj_status s);
+/* Message of the last failure on the calling thread ("" if none); valid until the next call. */
+const char* ncpadj_last_error(void);
+
+/* Bind a context to CUDA device `device`.  *out receives the handle.  Errors: INVALID_ARG
+ * (out NULL or no such device), CUDA. */
+ncpadj_status ncpadj_ctx_create(int device, ncpadj_ctx* out);
+/* Destroy a context (NULL is a no-op).  Scenes created from it must be destroyed first. */
+void ncpadj_ctx_destroy(ncpadj_ctx ctx);
+
+/* Scene description: all host arrays, copied during ncpadj_scene_create.
+ *   rest_pos [n_verts*3] float64, tets [n_tets*4] int32, E and nu [n_tets] float64
+ *   (Young's modulus > 0, Poisson ratio in (-1, 0.5)), density > 0 (kg/m^3), h > 0 (s).
+ * Lumped mass m_v = density * sum_{i containing v} V_i / 4; w_i = 2 mu_i V_i (App. B.2). */
+typedef struct {
+  int32_t n_verts, n_tets;
+  const double* rest_pos;
+  const int32_t* tets;
+  const double* E;
+  const double* nu;
+  double density, h;
+} ncpadj_scene_desc;
+
+/* Build a scene: per-tet operators, lumped mass, the scalar elastic matrix
+ * A_s = M_s + h^2 sum_i w_i B_i^T B_i (A = A_s (x) I_3, Eq. dynamics), its nested-dissection
+ * Cholesky factor A_s = L L^T and the sparse inverse S = L^{-1} (Sec. 3, sparse-inverse
+ * factorisation), and the fixed block pattern of script_A (Sec. 4.4, matrix assembly).
+ * Errors: INVALID_ARG (sizes, indices out of range, inverted rest tet, bad material),
+ * OOM, CUDA. */
+ncpadj_status ncpadj_scene_create(ncpadj_ctx ctx, const ncpadj_scene_desc* desc, ncpadj_scene* out);
+/* Destroy a scene (NULL is a no-op). */
+void ncpadj_scene_destroy(ncpadj_scene scene);
+
+typedef struct {
+  int32_t n_verts, n_tets;
+  int32_t n_blocks;        /* 3x3 blocks in the pattern of script_A */
+  int64_t nnz_L;           /* nonzeros of the scalar Cholesky factor */
+  int64_t nnz_Linv;        /* nonzeros of its explicit inverse S */
+  double ms_factor;        /* host time of ordering + factorisation + inversion */
+} ncpadj_scene_info;
+ncpadj_status ncpadj_scene_get_info(ncpadj_scene scene, ncpadj_scene_info* out);
+
+/* Contact set for one call (frozen: Sec. 4.2 treats J_c and the frame as fixed).
+ *   vertex [n_c] int32, frame [n_c*9] float64 (rows n, t1, t2; orthonormal),
+ *   d_n [n_c], d_f [n_c*2] or NULL (= 0), mu [n_c] >= 0 (mu = 0: frictionless),
+ *   region [n_c] int32 in [0, n_regions) or NULL (= 0); n_regions >= 1. */
+typedef struct {
+  int32_t n_contacts;
+  const int32_t* vertex;
+  const double* frame;
+  const double* d_n;
+  const double* d_f;
+  const double* mu;
+  const int32_t* region;
+  int32_t n_regions;
+} ncpadj_contacts;
+
+/* Converged forward state: q, q_prev [n_verts*3]; lambda [n_c*3] contact forces in frame
+ * coordinates (lambda_n, lambda_f1, lambda_f2).  The tangential multiplier used in the
+ * friction blocks is gamma = -lambda_f . delta_f / ||delta_f|| (signed). */
+typedef struct {
+  const double* q;
+  const double* q_prev;
+  const double* lambda;
+} ncpadj_state;
+
+/* Loss seeds dL/dq and dL/dv [n_verts*3] at the end of the step (dL_dv may be NULL = 0). */
+typedef struct {
+  const double* dL_dq;
+  const double* dL_dv;
+} ncpadj_seed;
+
+/* Gradient outputs (each nullable):
+ *   dL_dq_prev, dL_dv_prev, dL_dfext, z  [n_verts*3]
+ *   dL_dE, dL_dnu                        [n_tets]   (per-tet material parameters)
+ *   dL_dmu                               [n_regions] (friction coefficient per region)
+ *   dL_dmu_contact                       [n_c]       (per contact) */
+typedef struct {
+  double* dL_dq_prev;
+  double* dL_dv_prev;
+  double* dL_dfext;
+  double* dL_dE;
+  double* dL_dnu;
+  double* dL_dmu;
+  double* dL_dmu_contact;
+  double* z;
+} ncpadj_grads;
+
+/* Solver options; fill with ncpadj_options_default first.
+ *   eps        smoothing of FB_eps(x, y) = x + y - sqrt(x^2 + y^2 + 2 eps^2); must equal the
+ *              forward pass's (App. A.2).  Default 1e-4.
+ *   rtol       stop at ||b - script_A^T z|| <= rtol ||b||.  Default 1e-8 (Sec. 5).
+ *   max_iters  Krylov iteration cap (default 2000); gmres_restart m (default 64).
+ *   precision  NCPADJ_FP64 (default) or NCPADJ_MIXED.
+ *   precond    NCPADJ_PRECOND_* (default WOODBURY); solver NCPADJ_SOLVER_* (default AUTO:
+ *              CG when every mu is 0, else GMRES, Sec. 4.4); memory NCPADJ_MEM_*. */
+typedef struct {
+  double eps, rtol;
+  int32_t max_iters, gmres_restart;
+  int32_t precision, precond, solver, memory;
+} ncpadj_options;
+void ncpadj_options_default(ncpadj_options* opt);
+
+/* Per-call statistics (nullable).  Times are CUDA-event times of the stages on the stream. */
+typedef struct {
+  int32_t iterations;       /* Krylov iterations */
+  int32_t solver_used;      /* NCPADJ_SOLVER_CG or NCPADJ_SOLVER_GMRES */
+  int32_t n_contacts;
+  int32_t capacitance_dim;  /* dimension of the dense contact-space system (0 if none) */
+  double rel_residual;      /* final ||b - script_A^T z|| / ||b|| (recomputed explicitly) */
+  float ms_total, ms_assemble, ms_setup, ms_krylov, ms_contract;
+  float ms_cap_inverse;     /* the capacitance inversion kernel alone (0 if not run) */
+  int64_t kernel_launches;  /* kernels this call enqueued */
+} ncpadj_stats;
+
+/* One adjoint step: assemble script_A^T at the given converged state, solve for z and
+ * contract the gradients.  Errors: INVALID_ARG, INVERTED_ELEMENT, CONTACT_DOMAIN,
+ * NOT_CONVERGED (outputs hold the last iterate's gradients, stats the residual),
+ * NONFINITE, TIMEOUT, OOM, CUDA. */
+ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpadj_contacts* contacts,
+                                  const ncpadj_state* state, const ncpadj_seed* seed,
+                                  const ncpadj_options* opt, ncpadj_grads* grads,
+                                  ncpadj_stats* stats, void* stream);
+
+/* ---- forward step -------------------------------------------------------------------------
+ * The converged state that ncpadj_adjoint_step differentiates.  One implicit Euler step of
+ * Eq. (dynamics): q minimises the incremental potential of Eq. (implicit) with the projective
+ * Neo-Hookean force of Eq. (internal) and the smoothed-FB contact conditions of Eq. (contact).
+ * Solved by Newton's method in q alone: the multipliers are eliminated by the exact local
+ * solution of the contact equations (lambda_n = eps^2 / delta_n, and along -t = -delta_f/||delta_f||
+ * the friction magnitude gamma = mu lambda_n - eps^2/||delta_f||), so the Newton matrix is script_A
+ * itself, solved by the same Woodbury-preconditioned Krylov method.  A backtracking line search
+ * keeps every contact inside that local-solve domain and does not let the slip of a contact
+ * carrying friction turn by more than 60 degrees in one step.
+ *   q_prev, v_prev [n_verts*3] (v_prev may be NULL = 0); f_ext [n_verts*3] forces besides
+ *   gravity or NULL; gravity: acceleration vector (m/s^2).
+ * All arrays are device pointers (options.memory must be NCPADJ_MEM_DEVICE). */
+typedef struct {
+  const double* q_prev;
+  const double* v_prev;
+  const double* f_ext;
+  double gravity[3];
+} ncpadj_forward_input;
+
+typedef struct {
+  int32_t newton_iters, krylov_iters;
+  double residual;  /* ||R_q|| / (h^2 ||M g||) at the returned state */
+  float ms_total;
+} ncpadj_forward_stats;
+
+/* Outputs: q_out [n_verts*3], lambda_out [n_c*3] (frame coordinates, required if n_c > 0).
+ * Stops when ||R_q|| <= newton_tol h^2 ||M g|| or when no step decreases ||R_q|| any more.
+ * Errors: INVALID_ARG, UNSUPPORTED, CONTACT_DOMAIN (no start point inside the local-solve
+ * domain), INVERTED_ELEMENT, NOT_CONVERGED (residual above 1e3 newton_tol), NONFINITE, OOM, CUDA. */
+ncpadj_status ncpadj_forward_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpadj_contacts* contacts,
+                                  const ncpadj_forward_input* input, const ncpadj_options* opt, double newton_tol,
+                                  int32_t max_newton, double* q_out, double* lambda_out, ncpadj_forward_stats* stats,
+                                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NCPADJ_H */

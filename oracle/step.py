@@ -123,6 +123,21 @@ class Step:
             lam_n[c], gam[c] = C.local_solve(d, mu_c[c], self.eps)
         return lam_n, gam
 
+    def start_point(self, q_prev, qt, seed=0):
+        """The inertial prediction (its slips point along the free motion), with every contact
+        vertex lifted along its normal to a small positive gap."""
+        rng = np.random.default_rng(seed)
+        q = qt.copy()
+        gap0 = 10.0 * self.eps * self.eps / (np.max(self.mass) * np.linalg.norm(self.gravity) + 1e-300)
+        for c in range(self.nc):
+            v = self.ct.vertex[c]
+            dn = self.delta(q, q_prev, c)[0]
+            if dn < gap0:
+                q[v] += (gap0 - dn) * self.ct.frame[c][0]
+            if np.linalg.norm(self.delta(q, q_prev, c)[1:]) == 0.0:
+                q[v] += 1e-12 * (self.ct.frame[c][1:].T @ rng.normal(size=2))
+        return q
+
     def forward(self, q_prev, v_prev, f_ctrl=None, mu_c=None, q_init=None, tol=1e-9,
                        max_iter=200, seed=0):
         """Converged step by Newton in q alone (Returns State).
@@ -141,21 +156,7 @@ class Step:
         f_ctrl = np.zeros_like(q_prev) if f_ctrl is None else f_ctrl
         qt = self.qtilde(q_prev, v_prev, f_ctrl)
         N = self.N
-        if q_init is None:
-            # start: the inertial prediction (its slips point along the free motion), with
-            # every contact vertex lifted along its normal to a small positive gap
-            rng = np.random.default_rng(seed)
-            q = qt.copy()
-            gap0 = 10.0 * self.eps * self.eps / (np.max(self.mass) * np.linalg.norm(self.gravity) + 1e-300)
-            for c in range(self.nc):
-                v = self.ct.vertex[c]
-                dn = self.delta(q, q_prev, c)[0]
-                if dn < gap0:
-                    q[v] += (gap0 - dn) * self.ct.frame[c][0]
-                if np.linalg.norm(self.delta(q, q_prev, c)[1:]) == 0.0:
-                    q[v] += 1e-12 * (self.ct.frame[c][1:].T @ rng.normal(size=2))
-        else:
-            q = q_init.copy()
+        q = self.start_point(q_prev, qt, seed) if q_init is None else q_init.copy()
         scale_f = np.max(self.mass) * np.linalg.norm(self.gravity) + 1e-300
 
         def resid(qq):

@@ -1,0 +1,299 @@
+"""ctypes binding of ``include/ncpadj.h`` (argument marshalling only).
+
+Tensors are passed by pointer: CUDA tensors with ``memory="device"``, CPU tensors (pinned
+memory recommended) with ``memory="host"``.  float64 everywhere except int32 indices.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+STATUS = ["OK", "INVALID_ARG", "CUDA", "OOM", "INVERTED_ELEMENT", "NOT_CONVERGED", "NONFINITE", "TIMEOUT",
+          "NOT_FACTORED", "UNSUPPORTED", "CONTACT_DOMAIN"]
+PRECOND = {"none": 0, "jacobi": 1, "elastic": 2, "woodbury": 3}
+SOLVER = {"auto": 0, "cg": 1, "gmres": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+MEMORY = {"device": 0, "host": 1}
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libncpadj.so")
+
+
+class NcpadjError(RuntimeError):
+    def __init__(self, status: int, message: str, stats=None, grads=None):
+        super().__init__(f"ncpadj {status_name(status)}: {message}")
+        self.status = status
+        self.stats = stats
+        self.grads = grads
+
+
+def status_name(s: int) -> str:
+    return STATUS[s] if 0 <= s < len(STATUS) else f"status {s}"
+
+
+class _SceneDesc(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("rest_pos", C.c_void_p), ("tets", C.c_void_p),
+                ("E", C.c_void_p), ("nu", C.c_void_p), ("density", C.c_double), ("h", C.c_double)]
+
+
+class _SceneInfo(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("n_blocks", C.c_int32), ("nnz_L", C.c_int64),
+                ("nnz_Linv", C.c_int64), ("ms_factor", C.c_double)]
+
+
+class _Contacts(C.Structure):
+    _fields_ = [("n_contacts", C.c_int32), ("vertex", C.c_void_p), ("frame", C.c_void_p), ("d_n", C.c_void_p),
+                ("d_f", C.c_void_p), ("mu", C.c_void_p), ("region", C.c_void_p), ("n_regions", C.c_int32)]
+
+
+class _State(C.Structure):
+    _fields_ = [("q", C.c_void_p), ("q_prev", C.c_void_p), ("lam", C.c_void_p)]
+
+
+class _Seed(C.Structure):
+    _fields_ = [("dL_dq", C.c_void_p), ("dL_dv", C.c_void_p)]
+
+
+class _Grads(C.Structure):
+    _fields_ = [("dL_dq_prev", C.c_void_p), ("dL_dv_prev", C.c_void_p), ("dL_dfext", C.c_void_p),
+                ("dL_dE", C.c_void_p), ("dL_dnu", C.c_void_p), ("dL_dmu", C.c_void_p),
+                ("dL_dmu_contact", C.c_void_p), ("z", C.c_void_p)]
+
+
+class _Options(C.Structure):
+    _fields_ = [("eps", C.c_double), ("rtol", C.c_double), ("max_iters", C.c_int32), ("gmres_restart", C.c_int32),
+                ("precision", C.c_int32), ("precond", C.c_int32), ("solver", C.c_int32), ("memory", C.c_int32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("solver_used", C.c_int32), ("n_contacts", C.c_int32),
+                ("capacitance_dim", C.c_int32), ("rel_residual", C.c_double), ("ms_total", C.c_float),
+                ("ms_assemble", C.c_float), ("ms_setup", C.c_float), ("ms_krylov", C.c_float),
+                ("ms_contract", C.c_float), ("ms_cap_inverse", C.c_float), ("kernel_launches", C.c_int64)]
+
+    def to_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class _ForwardInput(C.Structure):
+    _fields_ = [("q_prev", C.c_void_p), ("v_prev", C.c_void_p), ("f_ext", C.c_void_p), ("gravity", C.c_double * 3)]
+
+
+class _ForwardStats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("krylov_iters", C.c_int32), ("residual", C.c_double),
+                ("ms_total", C.c_float)]
+
+    def to_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
+           "ncpadj_scene_create", "ncpadj_scene_destroy", "ncpadj_scene_get_info", "ncpadj_options_default",
+           "ncpadj_adjoint_step", "ncpadj_forward_step"]
+
+
+def load_library(path: Optional[str] = None):
+    """Load libncpadj.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build the CUDA library first (python -c 'import __graft_entry__ as g; "
+                           "g.build()')")
+    lib = C.CDLL(p)
+    lib.ncpadj_version.restype = C.c_char_p
+    lib.ncpadj_status_string.restype = C.c_char_p
+    lib.ncpadj_status_string.argtypes = [C.c_int]
+    lib.ncpadj_last_error.restype = C.c_char_p
+    lib.ncpadj_ctx_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+    lib.ncpadj_ctx_destroy.argtypes = [C.c_void_p]
+    lib.ncpadj_scene_create.argtypes = [C.c_void_p, C.POINTER(_SceneDesc), C.POINTER(C.c_void_p)]
+    lib.ncpadj_scene_destroy.argtypes = [C.c_void_p]
+    lib.ncpadj_scene_get_info.argtypes = [C.c_void_p, C.POINTER(_SceneInfo)]
+    lib.ncpadj_options_default.argtypes = [C.POINTER(_Options)]
+    lib.ncpadj_adjoint_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_State),
+                                        C.POINTER(_Seed), C.POINTER(_Options), C.POINTER(_Grads), C.POINTER(_Stats),
+                                        C.c_void_p]
+    lib.ncpadj_forward_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_ForwardInput),
+                                        C.POINTER(_Options), C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                        C.POINTER(_ForwardStats), C.c_void_p]
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _check(lib, st):
+    if st != 0:
+        raise NcpadjError(st, lib.ncpadj_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        _check(self.lib, self.lib.ncpadj_ctx_create(device, C.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self.lib.ncpadj_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """Mesh + material + step size; builds the elastic factor on construction (host arrays)."""
+
+    def __init__(self, ctx: Context, X, tets, E, nu, density: float, h: float):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self._X = torch.as_tensor(X, dtype=torch.float64).contiguous().cpu()
+        self._T = torch.as_tensor(tets, dtype=torch.int32).contiguous().cpu()
+        nt = self._T.shape[0]
+        self._E = torch.as_tensor(E, dtype=torch.float64).expand(nt).contiguous().cpu()
+        self._nu = torch.as_tensor(nu, dtype=torch.float64).expand(nt).contiguous().cpu()
+        d = _SceneDesc(self._X.shape[0], nt, self._X.data_ptr(), self._T.data_ptr(), self._E.data_ptr(),
+                       self._nu.data_ptr(), float(density), float(h))
+        hnd = C.c_void_p()
+        _check(self.lib, self.lib.ncpadj_scene_create(ctx.handle, C.byref(d), C.byref(hnd)))
+        self.handle = hnd
+        self.n_verts = int(self._X.shape[0])
+        self.n_tets = nt
+        self.h = float(h)
+
+    def info(self) -> dict:
+        inf = _SceneInfo()
+        _check(self.lib, self.lib.ncpadj_scene_get_info(self.handle, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def close(self):
+        if self.handle:
+            self.lib.ncpadj_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Contacts:
+    """Vertex-plane contacts (tensors on the device the call uses)."""
+    vertex: torch.Tensor               # int32 [n_c]
+    frame: torch.Tensor                # float64 [n_c, 3, 3] rows n, t1, t2
+    d_n: torch.Tensor                  # float64 [n_c]
+    mu: torch.Tensor                   # float64 [n_c]
+    d_f: Optional[torch.Tensor] = None       # float64 [n_c, 2]
+    region: Optional[torch.Tensor] = None    # int32 [n_c]
+    n_regions: int = 1
+
+    @property
+    def n(self):
+        return int(self.vertex.shape[0])
+
+    def to(self, device):
+        f = lambda t: None if t is None else t.to(device)  # noqa: E731
+        return Contacts(f(self.vertex), f(self.frame), f(self.d_n), f(self.mu), f(self.d_f), f(self.region),
+                        self.n_regions)
+
+
+def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4,
+                 rtol=1e-8, max_iters=2000, restart=64, precision="fp64", precond="woodbury", solver="auto",
+                 memory="device", outputs: Optional[dict] = None, stream=None, want=("dL_dq_prev", "dL_dv_prev",
+                 "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z")):
+    """One adjoint step through the C-ABI.  Returns (grads dict of tensors, stats dict).
+
+    ``outputs`` may hold preallocated output tensors by name; otherwise they are allocated on
+    q's device (pinned CPU memory with memory="host").
+    """
+    lib = scene.lib
+    nc = contacts.n if contacts is not None else 0
+    nv, nt = scene.n_verts, scene.n_tets
+    nreg = contacts.n_regions if contacts is not None else 1
+    dev = q.device
+    outputs = dict(outputs or {})
+    shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
+              "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (max(nc, 0),)}
+    for k in want:
+        if k not in outputs:
+            if memory == "host":
+                outputs[k] = torch.empty(shapes[k], dtype=torch.float64, pin_memory=torch.cuda.is_available())
+            else:
+                outputs[k] = torch.empty(shapes[k], dtype=torch.float64, device=dev)
+    cts = _Contacts(0, None, None, None, None, None, None, 1)
+    if nc:
+        cts = _Contacts(nc, _ptr(contacts.vertex), _ptr(contacts.frame), _ptr(contacts.d_n), _ptr(contacts.d_f),
+                        _ptr(contacts.mu), _ptr(contacts.region), int(contacts.n_regions))
+    stt = _State(_ptr(q), _ptr(q_prev), _ptr(lam) if nc else None)
+    sd = _Seed(_ptr(dL_dq), _ptr(dL_dv))
+    gr = _Grads(*[_ptr(outputs.get(k)) for k in ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu",
+                                                 "dL_dmu", "dL_dmu_contact", "z")])
+    opt = _Options()
+    lib.ncpadj_options_default(C.byref(opt))
+    opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
+    opt.precision = PRECISION[precision]
+    opt.precond = PRECOND[precond]
+    opt.solver = SOLVER[solver]
+    opt.memory = MEMORY[memory]
+    stats = _Stats()
+    if stream is None and dev.type == "cuda":
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    st = lib.ncpadj_adjoint_step(scene.ctx.handle, scene.handle, C.byref(cts), C.byref(stt), C.byref(sd),
+                                 C.byref(opt), C.byref(gr), C.byref(stats), C.c_void_p(stream or 0))
+    if st != 0:
+        raise NcpadjError(st, lib.ncpadj_last_error().decode(), stats.to_dict(), outputs)
+    return outputs, stats.to_dict()
+
+
+def _contacts_struct(contacts):
+    if contacts is None or contacts.n == 0:
+        return _Contacts(0, None, None, None, None, None, None, 1)
+    return _Contacts(contacts.n, _ptr(contacts.vertex), _ptr(contacts.frame), _ptr(contacts.d_n), _ptr(contacts.d_f),
+                     _ptr(contacts.mu), _ptr(contacts.region), int(contacts.n_regions))
+
+
+def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None, f_ext=None,
+                 gravity=(0.0, 0.0, -9.81), *, eps=1e-4, newton_tol=1e-10, max_newton=60, precond="woodbury",
+                 rtol=1e-10, max_iters=2000, restart=64, stream=None):
+    """One forward step on the GPU (device tensors).  Returns (q, lambda [n_c, 3], stats)."""
+    lib = scene.lib
+    nc = contacts.n if contacts is not None else 0
+    dev = q_prev.device
+    q = torch.empty_like(q_prev)
+    lam = torch.empty((max(nc, 1), 3), dtype=torch.float64, device=dev)
+    fin = _ForwardInput(_ptr(q_prev), _ptr(v_prev), _ptr(f_ext), (C.c_double * 3)(*[float(g) for g in gravity]))
+    opt = _Options()
+    lib.ncpadj_options_default(C.byref(opt))
+    opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
+    opt.precond = PRECOND[precond]
+    stats = _ForwardStats()
+    if stream is None and dev.type == "cuda":
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    cts = _contacts_struct(contacts)
+    st = lib.ncpadj_forward_step(scene.ctx.handle, scene.handle, C.byref(cts), C.byref(fin), C.byref(opt),
+                                 float(newton_tol), int(max_newton), _ptr(q), _ptr(lam), C.byref(stats),
+                                 C.c_void_p(stream or 0))
+    if st != 0:
+        raise NcpadjError(st, lib.ncpadj_last_error().decode(), stats.to_dict())
+    return q, lam[:nc], stats.to_dict()

@@ -1,0 +1,917 @@
+// C-ABI entry points, scene set-up and the host-driven adjoint solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace ncpadj {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void DevBuf::ensure(size_t n) {
+  if (n <= bytes) return;
+  release();
+  if (n == 0) return;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    bytes = 0;
+    cudaGetLastError();
+    throw Error{NCPADJ_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+  }
+  bytes = n;
+}
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+template <class T>
+static void upload(DevBuf& b, const std::vector<T>& v) {
+  b.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+  if (!v.empty()) NCPADJ_CUDA_TRY(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+static ncpadj_status fail(const Error& e) {
+  set_error(e.msg);
+  return e.status;
+}
+
+// ------------------------------------------------------------------------------------------
+// scene set-up
+// ------------------------------------------------------------------------------------------
+static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
+  const int nv = d.n_verts, nt = d.n_tets;
+  NCPADJ_REQUIRE(nv > 0 && nt > 0, "n_verts and n_tets must be positive");
+  NCPADJ_REQUIRE(d.rest_pos && d.tets && d.E && d.nu, "scene arrays must not be NULL");
+  NCPADJ_REQUIRE(d.density > 0 && d.h > 0 && std::isfinite(d.density) && std::isfinite(d.h),
+                 "density and h must be positive");
+  S.nv = nv;
+  S.nt = nt;
+  S.h = d.h;
+  S.density = d.density;
+  std::vector<double> gvec(12 * (size_t)nt), vol(nt), mu(nt), lam(nt), lame_d(4 * (size_t)nt);
+  S.mass.assign(nv, 0.0);
+  for (int t = 0; t < nt; ++t) {
+    int v[4];
+    for (int a = 0; a < 4; ++a) {
+      v[a] = d.tets[4 * t + a];
+      NCPADJ_REQUIRE(v[a] >= 0 && v[a] < nv, "tet " + std::to_string(t) + " has a vertex index out of range");
+    }
+    double Dm[3][3];  // columns X_a - X_0
+    for (int a = 1; a < 4; ++a)
+      for (int r = 0; r < 3; ++r) Dm[r][a - 1] = d.rest_pos[3 * v[a] + r] - d.rest_pos[3 * v[0] + r];
+    double det = Dm[0][0] * (Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1]) -
+                 Dm[0][1] * (Dm[1][0] * Dm[2][2] - Dm[1][2] * Dm[2][0]) +
+                 Dm[0][2] * (Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0]);
+    NCPADJ_REQUIRE(det > 0 && std::isfinite(det), "tet " + std::to_string(t) + " is inverted or degenerate at rest");
+    double B[3][3];  // inverse by cofactors
+    B[0][0] = (Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1]) / det;
+    B[0][1] = (Dm[0][2] * Dm[2][1] - Dm[0][1] * Dm[2][2]) / det;
+    B[0][2] = (Dm[0][1] * Dm[1][2] - Dm[0][2] * Dm[1][1]) / det;
+    B[1][0] = (Dm[1][2] * Dm[2][0] - Dm[1][0] * Dm[2][2]) / det;
+    B[1][1] = (Dm[0][0] * Dm[2][2] - Dm[0][2] * Dm[2][0]) / det;
+    B[1][2] = (Dm[0][2] * Dm[1][0] - Dm[0][0] * Dm[1][2]) / det;
+    B[2][0] = (Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0]) / det;
+    B[2][1] = (Dm[0][1] * Dm[2][0] - Dm[0][0] * Dm[2][1]) / det;
+    B[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) / det;
+    // g_a = row (a-1) of B for a = 1..3, g_0 = -(g_1 + g_2 + g_3): F = sum_a x_a g_a^T
+    for (int k = 0; k < 3; ++k) {
+      gvec[12 * t + k] = -(B[0][k] + B[1][k] + B[2][k]);
+      for (int a = 1; a < 4; ++a) gvec[12 * t + 3 * a + k] = B[a - 1][k];
+    }
+    vol[t] = det / 6.0;
+    const double E = d.E[t], nu = d.nu[t];
+    NCPADJ_REQUIRE(E > 0 && nu > -1.0 && nu < 0.5 && std::isfinite(E),
+                   "tet " + std::to_string(t) + ": need E > 0 and -1 < nu < 0.5");
+    mu[t] = E / (2.0 * (1.0 + nu));
+    lam[t] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    lame_d[4 * t + 0] = 1.0 / (2.0 * (1.0 + nu));
+    lame_d[4 * t + 1] = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    lame_d[4 * t + 2] = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+    const double q = (1.0 + nu) * (1.0 - 2.0 * nu);
+    lame_d[4 * t + 3] = E * (1.0 + 2.0 * nu * nu) / (q * q);
+    for (int a = 0; a < 4; ++a) S.mass[v[a]] += d.density * vol[t] / 4.0;
+  }
+  // block pattern: vertices sharing a tet (sorted neighbour lists, self included)
+  std::vector<std::vector<int32_t>> nbr(nv);
+  for (int v = 0; v < nv; ++v) nbr[v].push_back(v);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) nbr[d.tets[4 * t + a]].push_back(d.tets[4 * t + b]);
+  std::vector<int32_t> row_ptr(nv + 1, 0), col;
+  for (int v = 0; v < nv; ++v) {
+    auto& L = nbr[v];
+    std::sort(L.begin(), L.end());
+    L.erase(std::unique(L.begin(), L.end()), L.end());
+    row_ptr[v + 1] = row_ptr[v] + (int)L.size();
+    col.insert(col.end(), L.begin(), L.end());
+  }
+  S.nb = row_ptr[nv];
+  auto find_slot = [&](int u, int w) {
+    auto b = col.begin() + row_ptr[u], e = col.begin() + row_ptr[u + 1];
+    return (int32_t)(std::lower_bound(b, e, w) - col.begin());
+  };
+  std::vector<int32_t> slot(16 * (size_t)nt), diag_slot(nv);
+  for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) slot[16 * t + 4 * a + b] = find_slot(d.tets[4 * t + a], d.tets[4 * t + b]);
+  for (int v = 0; v < nv; ++v) diag_slot[v] = find_slot(v, v);
+  // scalar elastic matrix A_s = M_s + h^2 sum_i w_i (g_a . g_b), w_i = 2 mu_i V_i
+  CsrD As;
+  As.n = nv;
+  As.ptr.assign(row_ptr.begin(), row_ptr.end());
+  As.col = col;
+  As.val.assign(col.size(), 0.0);
+  for (int v = 0; v < nv; ++v) As.val[diag_slot[v]] += S.mass[v];
+  const double h2 = d.h * d.h;
+  for (int t = 0; t < nt; ++t) {
+    const double w = 2.0 * mu[t] * vol[t];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        double gg = 0;
+        for (int k = 0; k < 3; ++k) gg += gvec[12 * t + 3 * a + k] * gvec[12 * t + 3 * b + k];
+        As.val[slot[16 * t + 4 * a + b]] += h2 * w * gg;
+      }
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  ElasticFactor F;
+  factor_elastic(As, d.rest_pos, F);
+  S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  S.nnz_L = F.nnz_L;
+  S.nnz_S = (int64_t)F.S.col.size();
+  // S rows gather from the caller's (original) vertex numbering: remap column ids
+  std::vector<int32_t> Scol_orig(F.S.col.size());
+  for (size_t p = 0; p < F.S.col.size(); ++p) Scol_orig[p] = F.perm[F.S.col[p]];
+  std::vector<int32_t> tets(d.tets, d.tets + 4 * (size_t)nt);
+  upload(S.tets, tets);
+  upload(S.gvec, gvec);
+  upload(S.vol, vol);
+  upload(S.mu, mu);
+  upload(S.lam, lam);
+  upload(S.lame_d, lame_d);
+  upload(S.massd, S.mass);
+  upload(S.row_ptr, row_ptr);
+  upload(S.col, col);
+  upload(S.slot, slot);
+  upload(S.diag_slot, diag_slot);
+  upload(S.perm, F.perm);
+  upload(S.iperm, F.iperm);
+  upload(S.S_ptr, F.S.ptr);
+  upload(S.S_col, Scol_orig);
+  upload(S.S_val, F.S.val);
+  upload(S.St_ptr, F.St.ptr);
+  upload(S.St_col, F.St.col);
+  upload(S.St_val, F.St.val);
+  S.St_ptr_h = F.St.ptr;
+  S.flags.ensure(FLAG_COUNT * sizeof(int));
+  NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
+  NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
+  for (auto& e : S.ev) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
+}
+
+// ------------------------------------------------------------------------------------------
+// the solve engine shared by the adjoint step and the forward Newton step
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct Inputs {  // device pointers for one call
+  const int32_t* cvertex = nullptr;
+  const double* frame = nullptr;
+  const double* d_n = nullptr;
+  const double* d_f = nullptr;
+  const double* mu = nullptr;
+  const int32_t* region = nullptr;
+  const double* q = nullptr;
+  const double* q_prev = nullptr;
+  const double* lambda = nullptr;
+  const double* dL_dq = nullptr;
+  const double* dL_dv = nullptr;
+};
+
+struct Engine {
+  Scene& S;
+  const Ctx& C;
+  cudaStream_t st;
+  int nv = 0, nt = 0, nc = 0, N = 0, ncap = 0, m = 64, precond = NCPADJ_PRECOND_WOODBURY, transpose = 1;
+  double h = 0;
+  Inputs in;
+  int* flags = nullptr;
+  // vectors [N]
+  double *b, *x, *r, *w, *t0, *t1, *t2, *t3, *dinv;
+  // contact-space vectors [ncap]
+  double *sc, *tc, *ytmp;
+  double *partial, *scal;
+  double *Ds = nullptr, *Cm = nullptr;
+  int32_t* piv = nullptr;
+  bool cap_timed = false;
+  SinvArgs sinv{};
+
+  Engine(Scene& s, const Ctx& c, cudaStream_t stream) : S(s), C(c), st(stream) {
+    nv = S.nv;
+    nt = S.nt;
+    N = 3 * nv;
+    h = S.h;
+    flags = S.flags.as<int>();
+  }
+
+  void workspace(int nc_, int m_, int precond_) {
+    nc = nc_;
+    m = m_;
+    precond = precond_;
+    ncap = 3 * nc;
+    S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
+    S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
+    S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
+    const size_t nvec = 9, ncv = 3 * (size_t)std::max(ncap, 1);
+    S.vecs.ensure(sizeof(double) * (nvec * N + ncv + 64));
+    S.gmres.ensure(sizeof(double) * ((size_t)(m + 1) * N + (size_t)(m + 1) * (m + 4) + 16));
+    S.red.ensure(sizeof(double) * (64 * (size_t)(m + 2) + 64));
+    S.scal.ensure(sizeof(double) * (64 + (size_t)m + 8));
+    if (nc && precond == NCPADJ_PRECOND_WOODBURY) {
+      S.cap.ensure(sizeof(double) * ((size_t)ncap * ncap + (size_t)nc * nc + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
+      S.capw.ensure(gj_scratch_bytes(ncap, C.sm_count));
+      Cm = S.cap.as<double>();
+      Ds = Cm + (size_t)ncap * ncap;
+      piv = reinterpret_cast<int32_t*>(Ds + (size_t)nc * nc + 16);
+    }
+    double* base = S.vecs.as<double>();
+    for (double** v : {&b, &x, &r, &w, &t0, &t1, &t2, &t3, &dinv}) {
+      *v = base;
+      base += N;
+    }
+    const size_t nv3 = std::max(ncap, 1);
+    sc = base; base += nv3;
+    tc = base; base += nv3;
+    ytmp = base; base += nv3;
+    partial = S.red.as<double>();
+    scal = S.scal.as<double>();
+    sinv = SinvArgs{nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+                    S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>()};
+  }
+
+  ContactArgs contact_args(const double* q, const double* q_prev, const double* lambda, double eps) const {
+    return ContactArgs{nc, in.cvertex, in.frame, in.d_n, in.d_f, in.mu, lambda, q, q_prev, S.diag_slot.as<int32_t>(),
+                       eps, h, transpose, S.bsr64.as<double>(), nullptr, S.cdata.as<double>(), flags};
+  }
+
+  // script_A (transpose = 0) or script_A^T (transpose = 1) at (q, lambda) into the block pattern
+  void assemble(const double* q, const double* q_prev, const double* lambda, double eps) {
+    launch_bsr_init(nv, S.nb, S.diag_slot.as<int32_t>(), S.massd.as<double>(), S.bsr64.as<double>(), nullptr, st);
+    TetArgs ta{nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(), S.lam.as<double>(),
+               S.slot.as<int32_t>(), q, h, S.bsr64.as<double>(), nullptr, S.tetdata.as<double>(), flags};
+    launch_tet_assemble64(ta, st);
+    if (nc) launch_contact_blocks(contact_args(q, q_prev, lambda, eps), st);
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+  }
+
+  void setup_precond() {
+    if (precond == NCPADJ_PRECOND_JACOBI)
+      launch_diag_inv(nv, S.diag_slot.as<int32_t>(), S.bsr64.as<double>(), nullptr, dinv, st);
+    if (precond == NCPADJ_PRECOND_WOODBURY && nc) {
+      launch_delassus(nc, in.cvertex, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
+                      S.St_val.as<double>(), Ds, st);
+      launch_cap_form(nc, Ds, in.frame, S.cdata.as<double>(), h, transpose, Cm, st);
+      NCPADJ_CUDA_TRY(cudaGetLastError());
+      NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
+      if (!launch_gj_invert(ncap, Cm, piv, S.capw.as<double>(), flags, C.sm_count, st)) {
+        cudaGetLastError();
+        throw Error{NCPADJ_ERR_UNSUPPORTED,
+                    "capacitance of dimension " + std::to_string(ncap) + " does not fit the direct inverse"};
+      }
+      NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[7], st));
+      cap_timed = true;
+      NCPADJ_CUDA_TRY(cudaGetLastError());
+    }
+  }
+
+  void matvec(const double* xin, double* yout) {
+    launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), xin, yout, st);
+  }
+  void ainv(const double* xin, double* yout) { launch_ainv(sinv, xin, t3, yout, st); }
+
+  // yout = P^{-1} xin; uses t0..t3 as scratch (yout must be none of them)
+  void apply_precond(const double* xin, double* yout) {
+    switch (precond) {
+      case NCPADJ_PRECOND_NONE:
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(yout, xin, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        break;
+      case NCPADJ_PRECOND_JACOBI:
+        launch_mul(N, dinv, xin, yout, st);
+        break;
+      case NCPADJ_PRECOND_ELASTIC:
+        ainv(xin, yout);
+        break;
+      default: {  // Woodbury (Eq. woodbury_formula without K^{-1}): y = u - h^2 A^{-1} J^T C^{-1} K' J u, u = A^{-1} x
+        if (nc == 0) {
+          ainv(xin, yout);
+          break;
+        }
+        ainv(xin, t1);
+        launch_contact_gather_kt(nc, in.cvertex, in.frame, S.cdata.as<double>(), transpose, t1, sc, st);
+        launch_gj_apply(ncap, Cm, piv, sc, ytmp, tc, st);
+        launch_contact_scatter(nv, nc, in.cvertex, in.frame, tc, t2, st);
+        ainv(t2, t0);
+        launch_axpby(N, 1.0, t1, -h * h, t0, yout, st);
+      }
+    }
+  }
+
+  double dot_host(const double* a, const double* bb) {
+    launch_multi_dot(N, 1, a, N, bb, partial, scal, st);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    return S.scal_host[0];
+  }
+
+  // Solve B x = b (B the assembled matrix) to ||b - B x|| <= rtol ||b||, x0 = 0.
+  // CG for symmetric systems, else right-preconditioned restarted GMRES with classical
+  // Gram-Schmidt applied twice.  Returns the number of iterations; *rel = final true residual.
+  int solve(int solver, double rtol, int max_iters, double* rel, double* bnorm_out) {
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+    const double bnorm = std::sqrt(dot_host(b, b));
+    *bnorm_out = bnorm;
+    int iters = 0;
+    if (bnorm > 0.0 && std::isfinite(bnorm)) {
+      const double tol = rtol * bnorm;
+      if (solver == NCPADJ_SOLVER_CG) {
+        double* p = w;
+        double* rr = S.gmres.as<double>();
+        double* zz = rr + N;
+        double* Ap = rr + 2 * (size_t)N;
+        double* s2 = scal + 8;  // rz_old, rz_new, pAp, alpha
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(rr, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        apply_precond(rr, zz);
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(p, zz, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        launch_multi_dot(N, 1, rr, N, zz, partial, s2 + 0, st);
+        for (iters = 1; iters <= max_iters; ++iters) {
+          matvec(p, Ap);
+          launch_multi_dot(N, 1, p, N, Ap, partial, s2 + 2, st);
+          launch_cg_alpha(s2 + 0, s2 + 2, s2 + 3, st);
+          launch_cg_update_xr(N, s2 + 3, p, Ap, x, rr, st);
+          const double rn = std::sqrt(dot_host(rr, rr));
+          if (!std::isfinite(rn) || rn <= tol) break;
+          apply_precond(rr, zz);
+          launch_multi_dot(N, 1, rr, N, zz, partial, s2 + 1, st);
+          launch_cg_update_p(N, s2 + 1, s2 + 0, zz, p, st);
+          launch_copy_scalar(s2 + 1, s2 + 0, st);
+        }
+        iters = std::min(iters, max_iters);
+      } else {
+        double* V = S.gmres.as<double>();    // (m+1) x N
+        double* H = V + (size_t)(m + 1) * N;  // (m+1) x m, column-major
+        double* cs = H + (size_t)(m + 1) * m;
+        double* sn = cs + m;
+        double* g = sn + m;  // m+1
+        double* y = g + m + 1;
+        double* hc2 = scal + 32;
+        double* res_d = scal + 4;
+        double* nrm2 = scal + 5;
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        double beta = bnorm;
+        std::vector<double> g0(m + 1, 0.0);
+        for (;;) {
+          launch_axpby(N, 1.0 / beta, r, 0.0, nullptr, V, st);
+          g0[0] = beta;
+          NCPADJ_CUDA_TRY(cudaMemcpyAsync(g, g0.data(), sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
+          int k = 0;
+          for (int j = 0; j < m; ++j) {
+            double* vj = V + (size_t)j * N;
+            double* vn = V + (size_t)(j + 1) * N;
+            double* hcol = H + (size_t)(m + 1) * j;
+            apply_precond(vj, w);
+            matvec(w, vn);
+            launch_multi_dot(N, j + 1, V, N, vn, partial, hcol, st);
+            launch_multi_axpy(N, j + 1, V, N, hcol, vn, st);
+            launch_multi_dot(N, j + 1, V, N, vn, partial, hc2, st);
+            launch_multi_axpy(N, j + 1, V, N, hc2, vn, st);
+            launch_axpby(j + 1, 1.0, hcol, 1.0, hc2, hcol, st);
+            launch_multi_dot(N, 1, vn, N, vn, partial, nrm2, st);
+            launch_normalize(N, vn, nrm2, vn, hcol + j + 1, st);
+            launch_givens(j, m, H, cs, sn, g, res_d, st);
+            NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host, res_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+            NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+            ++iters;
+            k = j + 1;
+            const double res_est = S.scal_host[0];
+            if (!std::isfinite(res_est) || res_est <= tol || iters >= max_iters) break;
+          }
+          launch_hess_solve(k, m, H, g, y, st);
+          launch_combine(N, k, V, N, y, r, st);
+          apply_precond(r, w);
+          launch_axpby(N, 1.0, x, 1.0, w, x, st);
+          matvec(x, w);
+          launch_axpby(N, 1.0, b, -1.0, w, r, st);
+          beta = std::sqrt(dot_host(r, r));
+          if (!std::isfinite(beta) || beta <= tol || iters >= max_iters) break;
+        }
+      }
+    }
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+    matvec(x, w);
+    launch_axpby(N, 1.0, b, -1.0, w, r, st);
+    const double rfinal = std::sqrt(dot_host(r, r));
+    *rel = (bnorm > 0) ? rfinal / bnorm : 0.0;
+    return iters;
+  }
+};
+
+void read_flags(Scene& S, cudaStream_t st) {
+  NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.flags_host, S.flags.as<int>(), FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, st));
+  NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void check_contacts(Scene& S, int nc, const int32_t* cvertex, const int32_t* region, int nreg, cudaStream_t st) {
+  if (!nc) return;
+  launch_check_contacts(nc, cvertex, region, S.nv, nreg, S.flags.as<int>(), st);
+  read_flags(S, st);
+  NCPADJ_REQUIRE(S.flags_host[FLAG_BADINDEX] == 0, "a contact vertex or region id is out of range");
+}
+
+int pick_solver(int requested, int nc, const double* mu, bool host_mem, cudaStream_t st) {
+  if (requested != NCPADJ_SOLVER_AUTO) return requested;
+  bool frictionless = true;
+  if (nc) {
+    std::vector<double> muh(nc);
+    if (host_mem) std::memcpy(muh.data(), mu, nc * sizeof(double));
+    else {
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(muh.data(), mu, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+      NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    for (double v : muh) frictionless = frictionless && (v == 0.0);
+  }
+  return frictionless ? NCPADJ_SOLVER_CG : NCPADJ_SOLVER_GMRES;
+}
+
+void validate_options(const ncpadj_options& opt) {
+  NCPADJ_REQUIRE(opt.eps > 0 && opt.rtol > 0 && opt.max_iters > 0 && opt.gmres_restart > 0 && opt.gmres_restart <= 512,
+                 "bad options (eps, rtol, max_iters, gmres_restart)");
+  NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 2, "bad precond/solver");
+  NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
+  if (opt.precision != NCPADJ_FP64) throw Error{NCPADJ_ERR_UNSUPPORTED, "only NCPADJ_FP64 is implemented in this build"};
+}
+
+void raise_flags(const int* fh) {
+  if (fh[FLAG_INVERTED]) throw Error{NCPADJ_ERR_INVERTED_ELEMENT, "a tet has det F <= 0 at the given state"};
+  if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a grid barrier of the capacitance inversion timed out"};
+  if (fh[FLAG_DOMAIN]) throw Error{NCPADJ_ERR_CONTACT_DOMAIN, "a frictional contact has zero slip and zero tangential force"};
+  if (fh[FLAG_SINGULAR]) throw Error{NCPADJ_ERR_NONFINITE, "the contact capacitance is singular"};
+  if (fh[FLAG_NONFINITE]) throw Error{NCPADJ_ERR_NONFINITE, "non-finite values in the solve"};
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// the adjoint step
+// ------------------------------------------------------------------------------------------
+static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const ncpadj_contacts* ct,
+                                  const ncpadj_state* state, const ncpadj_seed* seed, const ncpadj_options* opt_in,
+                                  ncpadj_grads* grads, ncpadj_stats* stats, cudaStream_t st) {
+  NCPADJ_REQUIRE(ctx && sc, "NULL context or scene");
+  NCPADJ_REQUIRE(state && seed && state->q && state->q_prev && seed->dL_dq, "state.q, state.q_prev and seed.dL_dq are required");
+  ncpadj_options opt;
+  if (opt_in) opt = *opt_in;
+  else ncpadj_options_default(&opt);
+  validate_options(opt);
+  Scene& S = sc->s;
+  const int nc = ct ? ct->n_contacts : 0;
+  NCPADJ_REQUIRE(nc >= 0, "n_contacts < 0");
+  if (nc > 0) {
+    NCPADJ_REQUIRE(ct->vertex && ct->frame && ct->d_n && ct->mu, "contact arrays vertex, frame, d_n, mu are required");
+    NCPADJ_REQUIRE(state->lambda, "state.lambda is required when there are contacts");
+    NCPADJ_REQUIRE(ct->n_regions >= 1, "n_regions must be >= 1");
+  }
+  const int nv = S.nv, nt = S.nt, N = 3 * nv;
+  const int nreg = (nc > 0) ? ct->n_regions : 1;
+  const bool host_mem = opt.memory == NCPADJ_MEM_HOST;
+  if (nc && host_mem)
+    for (int c = 0; c < nc; ++c) NCPADJ_REQUIRE(ct->vertex[c] >= 0 && ct->vertex[c] < nv, "contact vertex out of range");
+
+  const long long launches0 = g_launches;
+  Engine E(S, ctx->c, st);
+  Inputs& in = E.in;
+  // ---- stage inputs ----
+  if (host_mem) {
+    size_t nd = (size_t)4 * N + (size_t)nc * (3 + 9 + 1 + 2 + 1);
+    S.io.ensure(nd * sizeof(double) + (size_t)2 * nc * sizeof(int32_t) + 64);
+    double* p = S.io.as<double>();
+    auto put = [&](const double* src, size_t n) -> const double* {
+      if (!src || n == 0) return nullptr;
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(p, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      const double* r = p;
+      p += n;
+      return r;
+    };
+    in.q = put(state->q, N);
+    in.q_prev = put(state->q_prev, N);
+    in.dL_dq = put(seed->dL_dq, N);
+    in.dL_dv = put(seed->dL_dv, N);
+    if (nc) {
+      in.lambda = put(state->lambda, 3 * (size_t)nc);
+      in.frame = put(ct->frame, 9 * (size_t)nc);
+      in.d_n = put(ct->d_n, nc);
+      in.d_f = put(ct->d_f, 2 * (size_t)nc);
+      in.mu = put(ct->mu, nc);
+      int32_t* ip = reinterpret_cast<int32_t*>(S.io.as<double>() + nd);
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(ip, ct->vertex, nc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      in.cvertex = ip;
+      if (ct->region) {
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(ip + nc, ct->region, nc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        in.region = ip + nc;
+      }
+    }
+  } else {
+    in.q = state->q;
+    in.q_prev = state->q_prev;
+    in.dL_dq = seed->dL_dq;
+    in.dL_dv = seed->dL_dv;
+    if (nc) {
+      in.lambda = state->lambda;
+      in.frame = ct->frame;
+      in.d_n = ct->d_n;
+      in.d_f = ct->d_f;
+      in.mu = ct->mu;
+      in.cvertex = ct->vertex;
+      in.region = ct->region;
+    }
+  }
+  const int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
+  E.workspace(nc, opt.gmres_restart, opt.precond);
+  E.transpose = 1;
+  int* flags = E.flags;
+  NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
+  check_contacts(S, nc, in.cvertex, in.region, nreg, st);
+  NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[0], st));
+  E.assemble(in.q, in.q_prev, in.lambda, opt.eps);
+  NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[1], st));
+  E.setup_precond();
+  NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[2], st));
+  launch_rhs(N, in.dL_dq, in.dL_dv, 1.0 / S.h, E.b, st);
+  double rel = 0, bnorm = 0;
+  const int iters = E.solve(solver, opt.rtol, opt.max_iters, &rel, &bnorm);
+  NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[3], st));
+
+  // ---- contractions ----
+  ncpadj_grads go{};
+  if (grads) go = *grads;
+  if (host_mem) {  // device staging for outputs
+    size_t need = (size_t)4 * N + 2 * (size_t)nt + nreg + nc + 16;
+    S.c_in.ensure(need * sizeof(double));
+    double* p = S.c_in.as<double>();
+    auto slot = [&](double* user, size_t n) -> double* {
+      if (!user) return nullptr;
+      double* r = p;
+      p += n;
+      return r;
+    };
+    go.dL_dq_prev = slot(grads ? grads->dL_dq_prev : nullptr, N);
+    go.dL_dv_prev = slot(grads ? grads->dL_dv_prev : nullptr, N);
+    go.dL_dfext = slot(grads ? grads->dL_dfext : nullptr, N);
+    go.z = slot(grads ? grads->z : nullptr, N);
+    go.dL_dE = slot(grads ? grads->dL_dE : nullptr, nt);
+    go.dL_dnu = slot(grads ? grads->dL_dnu : nullptr, nt);
+    go.dL_dmu = slot(grads ? grads->dL_dmu : nullptr, nreg);
+    go.dL_dmu_contact = slot(grads ? grads->dL_dmu_contact : nullptr, nc);
+  }
+  if (go.dL_dmu) NCPADJ_CUDA_TRY(cudaMemsetAsync(go.dL_dmu, 0, sizeof(double) * nreg, st));
+  ContractArgs ka{nv, nt, nc, S.h, E.x, S.massd.as<double>(), in.dL_dv, S.tets.as<int32_t>(), S.gvec.as<double>(),
+                  S.tetdata.as<double>(), S.lame_d.as<double>(), in.cvertex, in.frame, S.cdata.as<double>(), in.region,
+                  go.dL_dq_prev, go.dL_dv_prev, go.dL_dfext, go.dL_dE, go.dL_dnu, go.dL_dmu, go.dL_dmu_contact};
+  launch_contractions(ka, st);
+  if (go.z) NCPADJ_CUDA_TRY(cudaMemcpyAsync(go.z, E.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  launch_nonfinite_check(N, E.x, flags, st);
+  NCPADJ_CUDA_TRY(cudaGetLastError());
+  NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[4], st));
+  if (host_mem && grads) {
+    auto back = [&](double* user, double* dev, size_t n) {
+      if (user && dev) NCPADJ_CUDA_TRY(cudaMemcpyAsync(user, dev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    };
+    back(grads->dL_dq_prev, go.dL_dq_prev, N);
+    back(grads->dL_dv_prev, go.dL_dv_prev, N);
+    back(grads->dL_dfext, go.dL_dfext, N);
+    back(grads->z, go.z, N);
+    back(grads->dL_dE, go.dL_dE, nt);
+    back(grads->dL_dnu, go.dL_dnu, nt);
+    back(grads->dL_dmu, go.dL_dmu, nreg);
+    back(grads->dL_dmu_contact, go.dL_dmu_contact, nc);
+  }
+  read_flags(S, st);
+  if (stats) {
+    stats->iterations = iters;
+    stats->solver_used = solver;
+    stats->n_contacts = nc;
+    stats->capacitance_dim = (opt.precond == NCPADJ_PRECOND_WOODBURY) ? 3 * nc : 0;
+    stats->rel_residual = rel;
+    float ms[5] = {0, 0, 0, 0, 0};
+    cudaEventElapsedTime(&ms[0], S.ev[0], S.ev[4]);
+    cudaEventElapsedTime(&ms[1], S.ev[0], S.ev[1]);
+    cudaEventElapsedTime(&ms[2], S.ev[1], S.ev[2]);
+    cudaEventElapsedTime(&ms[3], S.ev[2], S.ev[3]);
+    cudaEventElapsedTime(&ms[4], S.ev[3], S.ev[4]);
+    stats->ms_total = ms[0];
+    stats->ms_assemble = ms[1];
+    stats->ms_setup = ms[2];
+    stats->ms_krylov = ms[3];
+    stats->ms_contract = ms[4];
+    float mc = 0;
+    if (E.cap_timed) cudaEventElapsedTime(&mc, S.ev[6], S.ev[7]);
+    stats->ms_cap_inverse = mc;
+    stats->kernel_launches = g_launches - launches0;
+  }
+  raise_flags(S.flags_host);
+  if (!std::isfinite(rel)) throw Error{NCPADJ_ERR_NONFINITE, "non-finite residual"};
+  if (!(rel <= opt.rtol * 1.0000001) && bnorm > 0)
+    throw Error{NCPADJ_ERR_NOT_CONVERGED, "Krylov stopped at relative residual " + std::to_string(rel) + " after " +
+                                              std::to_string(iters) + " iterations"};
+  return NCPADJ_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// the forward step (produces the converged state the adjoint differentiates)
+// ------------------------------------------------------------------------------------------
+static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const ncpadj_contacts* ct,
+                                  const ncpadj_forward_input* fin, const ncpadj_options* opt_in, double newton_tol,
+                                  int max_newton, double* q_out, double* lambda_out, ncpadj_forward_stats* stats,
+                                  cudaStream_t st) {
+  NCPADJ_REQUIRE(ctx && sc && fin && fin->q_prev && q_out, "NULL required argument");
+  NCPADJ_REQUIRE(newton_tol > 0 && max_newton > 0, "newton_tol and max_newton must be positive");
+  ncpadj_options opt;
+  if (opt_in) opt = *opt_in;
+  else ncpadj_options_default(&opt);
+  validate_options(opt);
+  if (opt.memory != NCPADJ_MEM_DEVICE) throw Error{NCPADJ_ERR_UNSUPPORTED, "the forward step takes device memory"};
+  Scene& S = sc->s;
+  const int nc = ct ? ct->n_contacts : 0;
+  if (nc) {
+    NCPADJ_REQUIRE(ct->vertex && ct->frame && ct->d_n && ct->mu && ct->n_regions >= 1, "incomplete contact arrays");
+    NCPADJ_REQUIRE(lambda_out, "lambda_out is required when there are contacts");
+  }
+  const int nv = S.nv, N = 3 * nv;
+  Engine E(S, ctx->c, st);
+  E.in.cvertex = nc ? ct->vertex : nullptr;
+  E.in.frame = nc ? ct->frame : nullptr;
+  E.in.d_n = nc ? ct->d_n : nullptr;
+  E.in.d_f = nc ? ct->d_f : nullptr;
+  E.in.mu = nc ? ct->mu : nullptr;
+  E.in.region = nc ? ct->region : nullptr;
+  E.in.q_prev = fin->q_prev;
+  const int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
+  E.workspace(nc, opt.gmres_restart, opt.precond);
+  E.transpose = 0;
+  int* flags = E.flags;
+  NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
+  check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);
+  S.fwd.ensure(sizeof(double) * (4 * (size_t)N + 3 * (size_t)std::max(nc, 1) + 4 * (size_t)std::max(nc, 1)) +
+               sizeof(int) * std::max(nc, 1) + 64);
+  double* qt = S.fwd.as<double>();  // inertial prediction
+  double* q = qt + N;               // current iterate (q_out holds trials)
+  double* R = q + N;
+  double* Rt = R + N;
+  double* lam = Rt + N;                         // [3 nc]
+  double* slip_old = lam + 3 * std::max(nc, 1);  // [2 nc]
+  double* slip_new = slip_old + 2 * std::max(nc, 1);
+  int* loaded = reinterpret_cast<int*>(slip_new + 2 * std::max(nc, 1));
+  cudaEvent_t e0 = S.ev[0], e1 = S.ev[5];
+  NCPADJ_CUDA_TRY(cudaEventRecord(e0, st));
+  launch_predict(nv, fin->q_prev, fin->v_prev, fin->f_ext, S.massd.as<double>(), fin->gravity[0], fin->gravity[1],
+                 fin->gravity[2], S.h, qt, st);
+  NCPADJ_CUDA_TRY(cudaMemcpyAsync(q, qt, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  double fscale = 0;
+  {
+    const double g2 = fin->gravity[0] * fin->gravity[0] + fin->gravity[1] * fin->gravity[1] + fin->gravity[2] * fin->gravity[2];
+    double mmax = 0, m2 = 0;
+    for (double mv : S.mass) {
+      mmax = std::max(mmax, mv);
+      m2 += mv * mv;
+    }
+    fscale = S.h * S.h * std::sqrt(m2 * std::max(g2, 1e-30));
+    const double gap0 = 10.0 * opt.eps * opt.eps / std::max(mmax * std::sqrt(std::max(g2, 1e-30)), 1e-300);
+    launch_lift(nc, E.in.cvertex, E.in.frame, E.in.d_n, gap0, q, st);
+  }
+  // residual at a point: R = M (q - qt) + h^2 sum w G^T (G q - p) - h^2 J^T lambda(q); returns ||R||^2 or
+  // +inf if the point leaves the local-solve domain (or turns a loaded slip, when asked)
+  auto evaluate = [&](const double* qq, double* RR, double* slip, bool check_turn) -> double {
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(flags + FLAG_INFEASIBLE, 0, 2 * sizeof(int), st));
+    launch_inertia(nv, S.massd.as<double>(), qq, qt, RR, st);
+    launch_tet_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
+                     S.lam.as<double>(), qq, S.h, RR, flags, st);
+    if (nc) {
+      ContactArgs ca = E.contact_args(qq, fin->q_prev, nullptr, opt.eps);
+      // the loaded mask belongs to the accepted iterate: trial points (check_turn) leave it alone
+      launch_local_contact(ca, lam, slip, check_turn ? nullptr : loaded, RR, st);
+      if (check_turn) launch_turn_check(nc, slip_old, slip, loaded, flags, st);
+    }
+    launch_multi_dot(N, 1, RR, N, RR, E.partial, E.scal + 6, st);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host + 6, E.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    read_flags(S, st);
+    if (S.flags_host[FLAG_INVERTED] || S.flags_host[FLAG_INFEASIBLE] || S.flags_host[FLAG_TURN]) {
+      S.flags_host[FLAG_INVERTED] = 0;
+      NCPADJ_CUDA_TRY(cudaMemsetAsync(flags + FLAG_INVERTED, 0, sizeof(int), st));
+      return INFINITY;
+    }
+    return S.scal_host[6];
+  };
+  double phi = evaluate(q, R, slip_old, false);
+  if (!std::isfinite(phi)) throw Error{NCPADJ_ERR_CONTACT_DOMAIN, "no feasible start point for the Newton solve"};
+  int it = 0, kry = 0;
+  for (it = 0; it < max_newton; ++it) {
+    if (std::sqrt(phi) <= newton_tol * fscale) break;
+    // Newton matrix script_A at q with the local multipliers (loaded mask recomputed here)
+    if (nc) {
+      ContactArgs ca = E.contact_args(q, fin->q_prev, nullptr, opt.eps);
+      launch_local_contact(ca, lam, slip_old, loaded, Rt, st);  // refresh lam/slips/loaded at q (Rt scratch)
+    }
+    E.assemble(q, fin->q_prev, lam, opt.eps);
+    E.setup_precond();
+    launch_axpby(N, -1.0, R, 0.0, nullptr, E.b, st);
+    double rel = 0, bn = 0;
+    kry += E.solve(solver, std::min(1e-10, 1e-3), opt.max_iters, &rel, &bn);
+    read_flags(S, st);
+    raise_flags(S.flags_host);
+    // backtracking line search on ||R||
+    double t = 1.0, phit = INFINITY;
+    bool ok = false;
+    for (int ls = 0; ls < 40; ++ls) {
+      launch_axpby(N, 1.0, q, t, E.x, q_out, st);
+      phit = evaluate(q_out, Rt, slip_new, true);
+      if (phit <= (1.0 - 1e-4 * t) * phi) {
+        ok = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!ok) break;  // no decrease possible: rounding floor
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(q, q_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(R, Rt, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(slip_old, slip_new, sizeof(double) * 2 * nc, cudaMemcpyDeviceToDevice, st));
+    phi = phit;
+  }
+  // outputs at the final iterate
+  NCPADJ_CUDA_TRY(cudaMemcpyAsync(q_out, q, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  phi = evaluate(q, R, slip_new, false);
+  if (nc) NCPADJ_CUDA_TRY(cudaMemcpyAsync(lambda_out, lam, sizeof(double) * 3 * nc, cudaMemcpyDeviceToDevice, st));
+  NCPADJ_CUDA_TRY(cudaEventRecord(e1, st));
+  NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+  const double res = std::sqrt(phi) / fscale;
+  if (stats) {
+    stats->newton_iters = it;
+    stats->krylov_iters = kry;
+    stats->residual = res;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    stats->ms_total = ms;
+  }
+  if (!std::isfinite(res)) throw Error{NCPADJ_ERR_NONFINITE, "non-finite forward residual"};
+  if (res > 1e3 * newton_tol)
+    throw Error{NCPADJ_ERR_NOT_CONVERGED, "forward Newton stopped at relative residual " + std::to_string(res)};
+  return NCPADJ_OK;
+}
+
+}  // namespace ncpadj
+
+// ------------------------------------------------------------------------------------------
+// C-ABI
+// ------------------------------------------------------------------------------------------
+using namespace ncpadj;
+
+extern "C" {
+
+const char* ncpadj_version(void) { return "ncpadj 0.1 (sm_103a)"; }
+
+const char* ncpadj_status_string(ncpadj_status s) {
+  switch (s) {
+    case NCPADJ_OK: return "OK";
+    case NCPADJ_ERR_INVALID_ARG: return "INVALID_ARG";
+    case NCPADJ_ERR_CUDA: return "CUDA";
+    case NCPADJ_ERR_OOM: return "OOM";
+    case NCPADJ_ERR_INVERTED_ELEMENT: return "INVERTED_ELEMENT";
+    case NCPADJ_ERR_NOT_CONVERGED: return "NOT_CONVERGED";
+    case NCPADJ_ERR_NONFINITE: return "NONFINITE";
+    case NCPADJ_ERR_TIMEOUT: return "TIMEOUT";
+    case NCPADJ_ERR_NOT_FACTORED: return "NOT_FACTORED";
+    case NCPADJ_ERR_UNSUPPORTED: return "UNSUPPORTED";
+    case NCPADJ_ERR_CONTACT_DOMAIN: return "CONTACT_DOMAIN";
+  }
+  return "UNKNOWN";
+}
+
+const char* ncpadj_last_error(void) { return g_last_error.c_str(); }
+
+void ncpadj_options_default(ncpadj_options* o) {
+  if (!o) return;
+  o->eps = 1e-4;
+  o->rtol = 1e-8;
+  o->max_iters = 2000;
+  o->gmres_restart = 64;
+  o->precision = NCPADJ_FP64;
+  o->precond = NCPADJ_PRECOND_WOODBURY;
+  o->solver = NCPADJ_SOLVER_AUTO;
+  o->memory = NCPADJ_MEM_DEVICE;
+}
+
+ncpadj_status ncpadj_ctx_create(int device, ncpadj_ctx* out) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(out, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    NCPADJ_CUDA_TRY(cudaGetDeviceCount(&n));
+    NCPADJ_REQUIRE(device >= 0 && device < n, "no CUDA device " + std::to_string(device));
+    NCPADJ_CUDA_TRY(cudaSetDevice(device));
+    auto* c = new ncpadj_ctx_s();
+    c->c.device = device;
+    cudaDeviceGetAttribute(&c->c.sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&c->c.coop_ok, cudaDevAttrCooperativeLaunch, device);
+    *out = c;
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_INVALID_ARG, e.what()});
+  }
+}
+
+void ncpadj_ctx_destroy(ncpadj_ctx ctx) { delete ctx; }
+
+ncpadj_status ncpadj_scene_create(ncpadj_ctx ctx, const ncpadj_scene_desc* desc, ncpadj_scene* out) {
+  g_last_error.clear();
+  ncpadj_scene_s* s = nullptr;
+  try {
+    NCPADJ_REQUIRE(ctx && desc && out, "NULL argument");
+    *out = nullptr;
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    s = new ncpadj_scene_s();
+    s->ctx = ctx;
+    build_scene(s->s, *desc);
+    *out = s;
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    ncpadj_scene_destroy(s);
+    return fail(e);
+  } catch (const std::exception& e) {
+    ncpadj_scene_destroy(s);
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+void ncpadj_scene_destroy(ncpadj_scene s) {
+  if (!s) return;
+  if (s->s.flags_host) cudaFreeHost(s->s.flags_host);
+  if (s->s.scal_host) cudaFreeHost(s->s.scal_host);
+  for (auto& e : s->s.ev)
+    if (e) cudaEventDestroy(e);
+  delete s;
+}
+
+ncpadj_status ncpadj_scene_get_info(ncpadj_scene s, ncpadj_scene_info* out) {
+  if (!s || !out) {
+    set_error("NULL argument");
+    return NCPADJ_ERR_INVALID_ARG;
+  }
+  out->n_verts = s->s.nv;
+  out->n_tets = s->s.nt;
+  out->n_blocks = s->s.nb;
+  out->nnz_L = s->s.nnz_L;
+  out->nnz_Linv = s->s.nnz_S;
+  out->ms_factor = s->s.ms_factor;
+  return NCPADJ_OK;
+}
+
+ncpadj_status ncpadj_forward_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpadj_contacts* contacts,
+                                  const ncpadj_forward_input* input, const ncpadj_options* opt, double newton_tol,
+                                  int32_t max_newton, double* q_out, double* lambda_out, ncpadj_forward_stats* stats,
+                                  void* stream) {
+  g_last_error.clear();
+  try {
+    if (ctx) NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    return forward_step(ctx, scene, contacts, input, opt, newton_tol, max_newton, q_out, lambda_out, stats,
+                        (cudaStream_t)stream);
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpadj_contacts* contacts,
+                                  const ncpadj_state* state, const ncpadj_seed* seed, const ncpadj_options* opt,
+                                  ncpadj_grads* grads, ncpadj_stats* stats, void* stream) {
+  g_last_error.clear();
+  try {
+    if (ctx) NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    return adjoint_step(ctx, scene, contacts, state, seed, opt, grads, stats, (cudaStream_t)stream);
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal declarations of the ncpadj library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ncpadj.h"
+
+namespace ncpadj {
+
+// ------------------------------------------------------------------------------------------
+// error plumbing
+// ------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+struct Error {
+  ncpadj_status status;
+  std::string msg;
+};
+#define NCPADJ_CUDA_TRY(expr)                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::ncpadj::Error{NCPADJ_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define NCPADJ_REQUIRE(cond, msg) \
+  do {                            \
+    if (!(cond)) throw ::ncpadj::Error{NCPADJ_ERR_INVALID_ARG, msg}; \
+  } while (0)
+
+// device buffer (grow-only)
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t n);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+  ~DevBuf() { release(); }
+};
+
+// ------------------------------------------------------------------------------------------
+// host-side factorisation of the scalar elastic matrix (factor.cpp)
+// ------------------------------------------------------------------------------------------
+struct CsrD {
+  int n = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+};
+
+struct ElasticFactor {
+  int n = 0;
+  std::vector<int32_t> perm;   // perm[i] = original vertex at elimination position i
+  std::vector<int32_t> iperm;  // iperm[v] = elimination position of vertex v
+  std::vector<int32_t> parent; // elimination tree (position space), -1 at roots
+  int64_t nnz_L = 0;
+  CsrD S;   // S = L^{-1} by rows, position space (row i: columns j <= i, descendants of i)
+  CsrD St;  // S^T by rows = columns of S (row j: entries i >= j on the etree path from j)
+};
+
+// A_s given as a symmetric CSR (both triangles) in original vertex numbering.
+// xyz [n][3] vertex coordinates drive the nested-dissection ordering.
+void factor_elastic(const CsrD& As, const double* xyz, ElasticFactor& out);
+
+// ------------------------------------------------------------------------------------------
+// device data of a scene
+// ------------------------------------------------------------------------------------------
+struct Scene {
+  int nv = 0, nt = 0, nb = 0;
+  double h = 0, density = 0;
+  // host copies
+  std::vector<double> mass;  // [nv]
+  // device
+  DevBuf tets;      // int32 [nt][4]
+  DevBuf gvec;      // double [nt][12]  g_0..g_3 (rows of the 4x3 gradient operator)
+  DevBuf vol;       // double [nt]
+  DevBuf mu, lam;   // double [nt]  Lame parameters
+  DevBuf lame_d;    // double [nt][4] dmu/dE, dlam/dE, dmu/dnu, dlam/dnu
+  DevBuf massd;     // double [nv]
+  DevBuf row_ptr;   // int32 [nv+1]  block pattern of script_A
+  DevBuf col;       // int32 [nb]
+  DevBuf slot;      // int32 [nt][16] block slot of (a, b)
+  DevBuf diag_slot; // int32 [nv]
+  // elastic factor (position space), device copies
+  DevBuf perm, iperm;          // int32 [nv]
+  DevBuf S_ptr, S_col, S_val;  // rows of S; S_col holds ORIGINAL vertex ids (gather from x)
+  DevBuf St_ptr, St_col, St_val;  // rows of S^T; St_col in position space
+  int64_t nnz_S = 0;
+  int64_t nnz_L = 0;
+  double ms_factor = 0;
+  std::vector<int64_t> St_ptr_h;  // host copy (Delassus pair scheduling)
+
+  // per-call workspace
+  DevBuf bsr64, bsr32;            // block values
+  DevBuf tetdata;                 // double [nt][18]  P_mu, P_lam contraction tensors
+  DevBuf cdata;                   // double [nc][16]  per-contact K (9), kmu (3), M_a pieces
+  DevBuf c_in;                    // staging of contact inputs for host-memory calls
+  DevBuf vecs;                    // Krylov vectors
+  DevBuf cap, capw;               // capacitance matrix / inverse and scratch
+  DevBuf red;                     // reduction scratch
+  DevBuf flags;                   // int32 status flags
+  DevBuf scal;                    // double scalars
+  DevBuf io;                      // staging for host-memory calls
+  DevBuf gmres;                   // GMRES basis + Hessenberg
+  DevBuf fwd;                     // forward Newton vectors
+  int* flags_host = nullptr;      // pinned
+  double* scal_host = nullptr;    // pinned
+  cudaEvent_t ev[8] = {};
+};
+
+struct Ctx {
+  int device = 0;
+  int sm_count = 0;
+  int coop_ok = 0;
+};
+
+// kernels launch helpers (kernels.cu)
+struct AdjointArgs;  // defined in kernels.cuh
+}  // namespace ncpadj
+
+struct ncpadj_ctx_s {
+  ncpadj::Ctx c;
+};
+struct ncpadj_scene_s {
+  ncpadj::Scene s;
+  ncpadj_ctx_s* ctx = nullptr;
+};

@@ -1,0 +1,189 @@
+// Device kernels of the adjoint step and their launch wrappers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ncpadj {
+
+// kernels enqueued by this thread (read and reset by the entry points for their statistics)
+extern thread_local long long g_launches;
+
+// status flags written by kernels (int32 slots in Scene::flags)
+enum Flag {
+  FLAG_INVERTED = 0,   // det F <= 0 in some tet
+  FLAG_DOMAIN = 1,     // frictional contact with zero slip and zero tangential force
+  FLAG_NONFINITE = 2,  // NaN/Inf seen
+  FLAG_SINGULAR = 3,   // zero pivot in the capacitance inversion
+  FLAG_TIMEOUT = 4,    // a bounded grid barrier gave up
+  FLAG_BARRIER = 5,    // barrier arrival counter
+  FLAG_GEN = 6,        // barrier generation
+  FLAG_BADINDEX = 7,   // a contact vertex or region id out of range
+  FLAG_INFEASIBLE = 8, // forward: a contact outside the local-solve domain (gap <= 0 or zero slip)
+  FLAG_TURN = 9,       // forward: a loaded contact's slip turned by more than 60 degrees
+  FLAG_COUNT = 12
+};
+
+// ---- element / contact / contraction kernels (elem.cu) ---------------------------------
+struct TetArgs {
+  int nt;
+  const int32_t* tets;
+  const double* gvec;  // [nt][12]
+  const double* vol;
+  const double* mu;
+  const double* lam;
+  const int32_t* slot;  // [nt][16]
+  const double* q;      // [nv][3]
+  double h;
+  double* bsr;          // [nb][9] (FP64 path) or null
+  float* bsr32;         // [nb][9] (mixed path) or null
+  double* tetdata;      // [nt][18] contraction tensors
+  int* flags;
+};
+void launch_tet_assemble64(const TetArgs& a, cudaStream_t s);
+void launch_tet_assemble32(const TetArgs& a, cudaStream_t s);
+
+struct ContactArgs {
+  int nc;
+  const int32_t* vertex;
+  const double* frame;   // [nc][9]
+  const double* d_n;
+  const double* d_f;     // [nc][2] or null
+  const double* mu;
+  const double* lambda;  // [nc][3]
+  const double* q;
+  const double* q_prev;
+  const int32_t* diag_slot;
+  double eps, h;
+  int transpose;         // 1: add K^T (adjoint matrix script_A^T), 0: add K (Newton matrix script_A)
+  double* bsr;           // add h^2 F^T K^T F into diagonal blocks (FP64) or null
+  float* bsr32;          // or FP32
+  double* cdata;         // [nc][12] K (frame coords, row-major), k_mu
+  int* flags;
+};
+void launch_contact_blocks(const ContactArgs& a, cudaStream_t s);
+// flags FLAG_BADINDEX if any contact vertex is outside [0, nv) or region outside [0, nreg)
+void launch_check_contacts(int nc, const int32_t* vertex, const int32_t* region, int nv, int nreg, int* flags,
+                           cudaStream_t s);
+
+void launch_bsr_init(int nv, int nb, const int32_t* diag_slot, const double* mass, double* bsr,
+                     float* bsr32, cudaStream_t s);
+
+struct ContractArgs {
+  int nv, nt, nc;
+  double h;
+  const double* z;
+  const double* mass;
+  const double* dL_dv;   // may be null
+  const int32_t* tets;
+  const double* gvec;
+  const double* tetdata;
+  const double* lame_d;  // [nt][4]
+  const int32_t* cvertex;
+  const double* frame;
+  const double* cdata;
+  const int32_t* region;  // may be null
+  double* dL_dq_prev;
+  double* dL_dv_prev;
+  double* dL_dfext;
+  double* dL_dE;
+  double* dL_dnu;
+  double* dL_dmu;         // [n_regions] (zeroed by the caller)
+  double* dL_dmu_contact; // [nc]
+};
+void launch_contractions(const ContractArgs& a, cudaStream_t s);
+
+// ---- forward step (elem.cu) ----------------------------------------------------------------
+// qt = q_prev + h v_prev + h^2 (g + f_ext / m)
+void launch_predict(int nv, const double* q_prev, const double* v_prev, const double* f_ext, const double* mass,
+                    double g0, double g1, double g2, double h, double* qt, cudaStream_t s);
+// q[v_c] += max(0, gap0 - delta_n) n_c  (start point inside the local-solve domain)
+void launch_lift(int nc, const int32_t* vertex, const double* frame, const double* d_n, double gap0, double* q,
+                 cudaStream_t s);
+// R = M (q - qt)
+void launch_inertia(int nv, const double* mass, const double* q, const double* qt, double* R, cudaStream_t s);
+// R[v_a] += h^2 w_i (F - p(F)) g_a  (elastic force of Eq. internal)
+void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
+                      const double* lam, const double* q, double h, double* R, int* flags, cudaStream_t s);
+// exact local solution of the contact equations at q: lambda_n = eps^2/delta_n,
+// gamma = mu lambda_n - eps^2/||delta_f||; writes lambda (frame coords), slips, loaded mask, and
+// R[v] -= h^2 F^T lambda
+void launch_local_contact(const ContactArgs& a, double* lambda, double* slip, int* loaded, double* R,
+                          cudaStream_t s);
+// FLAG_TURN if a loaded contact's slip turned by more than 60 degrees from slip_old
+void launch_turn_check(int nc, const double* slip_old, const double* slip_new, const int* loaded, int* flags,
+                       cudaStream_t s);
+
+// ---- linear algebra (linalg.cu) ---------------------------------------------------------
+// y = B x for the 3x3-block matrix (FP64)
+void launch_bsr_spmv(int nv, const int32_t* row_ptr, const int32_t* col, const double* val,
+                     const double* x, double* y, cudaStream_t s);
+void launch_bsr_spmv32(int nv, const int32_t* row_ptr, const int32_t* col, const float* val,
+                       const double* x, double* y, cudaStream_t s);
+// inverse of the scalar diagonal of the block matrix
+void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
+                     cudaStream_t s);
+
+// A^{-1} x = P^T S^T S P x for 3 right-hand sides ([nv][3]); w is [nv][3] scratch
+struct SinvArgs {
+  int nv;
+  const int64_t* S_ptr;
+  const int32_t* S_col;   // original vertex ids
+  const double* S_val;
+  const int64_t* St_ptr;
+  const int32_t* St_col;  // positions
+  const double* St_val;
+  const int32_t* perm;
+};
+void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
+
+// Delassus of the contact vertices: Ds[a][b] = (A_s^{-1})_{v_a v_b}
+void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
+                     const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s);
+// capacitance C = I + h^2 K^T D (3nc x 3nc, row-major)
+void launch_cap_form(int nc, const double* Ds, const double* frame, const double* cdata, double h, int transpose,
+                     double* C, cudaStream_t s);
+// in-place Gauss-Jordan inverse with partial pivoting (cooperative); returns false if the
+// launch configuration is impossible (n too large for the shared-memory row blocks)
+bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count,
+                      cudaStream_t s);
+size_t gj_scratch_bytes(int n, int sm_count);
+// x = C^{-1} y with the swept matrix B and pivot rows: x_k = B[piv_k] . y[piv]
+void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
+                     cudaStream_t s);
+
+// contact gather/scatter: s_c = K_c^T F_c u_{v_c};  e_{v_c} += F_c^T t_c  (e zeroed first)
+void launch_contact_gather_kt(int nc, const int32_t* cvertex, const double* frame, const double* cdata,
+                              int transpose, const double* u, double* sc, cudaStream_t s);
+void launch_contact_scatter(int nv, int nc, const int32_t* cvertex, const double* frame, const double* t,
+                            double* e, cudaStream_t s);
+
+// vector kernels
+void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
+void launch_rhs(int n, const double* dL_dq, const double* dL_dv, double inv_h, double* b, cudaStream_t s);
+void launch_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y,
+                      cudaStream_t s);
+void launch_mul(int n, const double* a, const double* b, double* y, cudaStream_t s);
+// out[k] = sum_i V_k[i] w[i], k < nvec (vectors of length n, stride ld); partials scratch
+void launch_multi_dot(int n, int nvec, const double* V, long ld, const double* w, double* partial, double* out,
+                      cudaStream_t s);
+// w -= sum_k coef[k] V_k (coef on device); if add_to != null also add_to[k] += coef[k]
+void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w,
+                       cudaStream_t s);
+// y = sum_k coef[k] V_k
+void launch_combine(int n, int nvec, const double* V, long ld, const double* coef, double* y, cudaStream_t s);
+// v_out = w / nrm (nrm on device); writes nrm into H slot too
+void launch_normalize(int n, const double* w, const double* nrm2, double* v_out, double* h_slot, cudaStream_t s);
+// GMRES Givens step for column j (single thread): H [(m+1) x m] column-major, cs, sn, g
+void launch_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res_out, cudaStream_t s);
+void launch_hess_solve(int k, int m, const double* H, const double* g, double* y, cudaStream_t s);
+// CG scalar updates
+void launch_cg_alpha(const double* rz, const double* pAp, double* alpha, cudaStream_t s);
+void launch_cg_update_xr(int n, const double* alpha, const double* p, const double* Ap, double* x, double* r,
+                         cudaStream_t s);
+void launch_cg_update_p(int n, const double* rz_new, const double* rz_old, const double* z, double* p,
+                        cudaStream_t s);
+void launch_copy_scalar(const double* src, double* dst, cudaStream_t s);
+void launch_nonfinite_check(int n, const double* x, int* flags, cudaStream_t s);
+
+}  // namespace ncpadj

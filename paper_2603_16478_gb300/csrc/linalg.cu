@@ -1,0 +1,607 @@
+// Sparse and dense linear algebra of the adjoint solve.
+//
+//  * block sparse matrix-vector product with the assembled script_A^T (3x3 blocks),
+//  * A^{-1} x = P^T S^T S P x through the explicit sparse inverse S = L^{-1} of the scalar
+//    elastic factor, applied to the 3 coordinates at once (Sec. 3, sparse-inverse factorisation),
+//  * the contact-space pieces of the Woodbury preconditioner (Eq. woodbury_formula, used in the
+//    form without K^{-1}): Delassus entries (A_s^{-1})_{v_a v_b}, the capacitance
+//    C = I + h^2 K^T D, its inverse by in-place Gauss-Jordan elimination with partial pivoting in
+//    one cooperative launch, and the gather/scatter with the contact frames,
+//  * the vector kernels of CG and restarted GMRES (Sec. 4.4).
+#include <math.h>
+
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace ncpadj {
+
+thread_local long long g_launches = 0;
+
+namespace {
+
+inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_bsr_spmv(int nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nv) return;
+  const int v = i / 3, r = i - 3 * v;
+  double acc = 0.0;
+  for (int p = rp[v]; p < rp[v + 1]; ++p) {
+    const double* B = val + 9 * (size_t)p + 3 * r;
+    const int c = col[p];
+    acc += B[0] * x[3 * c] + B[1] * x[3 * c + 1] + B[2] * x[3 * c + 2];
+  }
+  y[i] = acc;
+}
+
+__global__ void k_bsr_spmv32(int nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const float* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nv) return;
+  const int v = i / 3, r = i - 3 * v;
+  double acc = 0.0;
+  for (int p = rp[v]; p < rp[v + 1]; ++p) {
+    const float* B = val + 9 * (size_t)p + 3 * r;
+    const int c = col[p];
+    acc += (double)B[0] * x[3 * c] + (double)B[1] * x[3 * c + 1] + (double)B[2] * x[3 * c + 2];
+  }
+  y[i] = acc;
+}
+
+__global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nv) return;
+  const int v = i / 3, r = i - 3 * v;
+  const size_t k = 9 * (size_t)diag_slot[v] + 4 * r;
+  dinv[i] = 1.0 / (val ? val[k] : (double)val32[k]);
+}
+
+// w[i] = sum_p S_val[p] x[S_col[p]]  (row i of S, position space; S_col holds original ids)
+__global__ void k_spmv_S(int nv, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                         const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ w) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nv) return;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t p = ptr[row] + lane; p < ptr[row + 1]; p += 32) {
+    const double s = val[p];
+    const int c = col[p];
+    a0 += s * x[3 * c];
+    a1 += s * x[3 * c + 1];
+    a2 += s * x[3 * c + 2];
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane == 0) {
+    w[3 * row] = a0;
+    w[3 * row + 1] = a1;
+    w[3 * row + 2] = a2;
+  }
+}
+
+// y[perm[j]] = sum_p St_val[p] w[St_col[p]]  (row j of S^T = column j of S)
+__global__ void k_spmv_St(int nv, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const int32_t* __restrict__ perm,
+                          const double* __restrict__ w, double* __restrict__ y) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nv) return;
+  double a0 = 0, a1 = 0, a2 = 0;
+  for (int64_t p = ptr[row] + lane; p < ptr[row + 1]; p += 32) {
+    const double s = val[p];
+    const int c = col[p];
+    a0 += s * w[3 * c];
+    a1 += s * w[3 * c + 1];
+    a2 += s * w[3 * c + 2];
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane == 0) {
+    const int v = perm[row];
+    y[3 * v] = a0;
+    y[3 * v + 1] = a1;
+    y[3 * v + 2] = a2;
+  }
+}
+
+// Ds[a][b] = sum_k S[k][ia] S[k][ib]: rows ia, ib of S^T are the elimination-tree paths of
+// ia and ib; they share exactly the path from their lowest common ancestor to the root, which
+// is a common suffix of both rows.
+__global__ void k_delassus(int nc, const int32_t* __restrict__ cvertex, const int32_t* __restrict__ iperm,
+                           const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, double* Ds) {
+  long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)nc * nc) return;
+  const int a = (int)(idx / nc), b = (int)(idx - (long)a * nc);
+  const int ia = iperm[cvertex[a]], ib = iperm[cvertex[b]];
+  int64_t pa = ptr[ia + 1] - 1, pb = ptr[ib + 1] - 1;
+  const int64_t ea = ptr[ia], eb = ptr[ib];
+  double acc = 0.0;
+  while (pa >= ea && pb >= eb && col[pa] == col[pb]) {
+    acc += val[pa] * val[pb];
+    --pa;
+    --pb;
+  }
+  Ds[idx] = acc;
+}
+
+// C[3a+r][3b+s] = delta + h^2 Ds[a][b] sum_l K'_a[r][l] (F_a F_b^T)[l][s],  K' = K^T (adjoint) or K
+__global__ void k_cap_form(int nc, const double* __restrict__ Ds, const double* __restrict__ frame,
+                           const double* __restrict__ cdata, double h2, int transpose, double* C) {
+  const long n = 3L * nc;
+  long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int R = (int)(idx / n), Cc = (int)(idx - (long)R * n);
+  const int a = R / 3, r = R - 3 * a, b = Cc / 3, s = Cc - 3 * b;
+  const double* Fa = frame + 9 * (size_t)a;
+  const double* Fb = frame + 9 * (size_t)b;
+  const double* Ka = cdata + 12 * (size_t)a;
+  double acc = 0.0;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const double ff = Fa[3 * l] * Fb[3 * s] + Fa[3 * l + 1] * Fb[3 * s + 1] + Fa[3 * l + 2] * Fb[3 * s + 2];
+    acc += (transpose ? Ka[3 * l + r] : Ka[3 * r + l]) * ff;
+  }
+  C[idx] = (R == Cc ? 1.0 : 0.0) + h2 * Ds[(size_t)a * nc + b] * acc;
+}
+
+// ---- cooperative Gauss-Jordan inversion -------------------------------------------------
+
+// Grid-wide barrier for a cooperative launch, with a bounded wait: after ~1 s of spinning it
+// sets FLAG_TIMEOUT and lets the block go on; every block then stops at its next barrier.
+__device__ bool grid_barrier(int* flags) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* vgen = (volatile int*)&flags[FLAG_GEN];
+    const int gen = *vgen;
+    __threadfence();
+    const int arrived = atomicAdd(&flags[FLAG_BARRIER], 1);
+    if (arrived == (int)gridDim.x - 1) {
+      atomicExch(&flags[FLAG_BARRIER], 0);
+      __threadfence();
+      atomicAdd(&flags[FLAG_GEN], 1);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > (1LL << 24)) {
+          atomicExch(&flags[FLAG_TIMEOUT], 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)&flags[FLAG_TIMEOUT] == 0;
+}
+
+struct GJScratch {
+  double* cand_val;   // [2][G]  |pivot candidate| (or -1: no unused row)
+  int* cand_row;      // [2][G]
+  double* cand_data;  // [2][G][n]
+};
+
+// Sweep elimination on pivot pairs (r_k, k): rows are owned round-robin by the blocks and kept
+// in shared memory.  At step k every block agrees on the pivot row r_k (largest |a[i][k]| among
+// rows not used yet; each block published its best candidate row at the end of step k-1), and
+//   a[r][j] <- a[r][j]/p (j != k), a[r][k] <- 1/p,
+//   a[i][j] <- a[i][j] - a[i][k] a[r][j]/p (j != k), a[i][k] <- -a[i][k]/p  (i != r).
+// After n steps the matrix B satisfies  (C^{-1})[k][r_k'] = B[r_k][k'].  One barrier per step.
+__global__ void k_gj(int n, int nloc_max, double* C, int32_t* piv, GJScratch sc, int* flags) {
+  extern __shared__ double sm[];
+  const int G = gridDim.x, me = blockIdx.x;
+  double* rows = sm;                              // [nloc_max][n]
+  double* prow = sm + (size_t)nloc_max * n;       // [n]
+  double* fl = prow + n;                          // [nloc_max]
+  int* used = (int*)(fl + nloc_max);              // [nloc_max]
+  __shared__ double red_v[32];
+  __shared__ int red_l[32];
+  __shared__ int s_win, s_row;
+  __shared__ double s_piv;
+  const int nloc = (me < n) ? (n - me + G - 1) / G : 0;
+  for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
+    const int l = (int)(e / n), j = (int)(e - (long)l * n);
+    rows[e] = C[(size_t)(me + G * l) * n + j];
+  }
+  for (int l = threadIdx.x; l < nloc_max; l += blockDim.x) used[l] = 0;
+  __syncthreads();
+
+  // publish this block's candidate for column col into buffer buf
+  auto publish = [&](int col, int buf) {
+    double best = -1.0;
+    int bl = -1;
+    for (int l = threadIdx.x; l < nloc; l += blockDim.x)
+      if (!used[l]) {
+        const double v = fabs(rows[(size_t)l * n + col]);
+        if (v > best) { best = v; bl = l; }
+      }
+    // block argmax (ties -> lower local index)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (ov > best || (ov == best && ol >= 0 && (bl < 0 || ol < bl))) { best = ov; bl = ol; }
+    }
+    if ((threadIdx.x & 31) == 0) { red_v[threadIdx.x >> 5] = best; red_l[threadIdx.x >> 5] = bl; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int L = -1;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (red_v[w] > b || (red_v[w] == b && red_l[w] >= 0 && (L < 0 || red_l[w] < L))) { b = red_v[w]; L = red_l[w]; }
+      sc.cand_val[buf * G + me] = (L >= 0) ? b : -1.0;
+      sc.cand_row[buf * G + me] = (L >= 0) ? me + G * L : -1;
+      red_l[0] = L;
+    }
+    __syncthreads();
+    const int L = red_l[0];
+    if (L >= 0)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) sc.cand_data[((size_t)buf * G + me) * n + j] = rows[(size_t)L * n + j];
+    __syncthreads();
+  };
+
+  publish(0, 0);
+  if (!grid_barrier(flags)) return;
+
+  for (int k = 0; k < n; ++k) {
+    const int buf = k & 1;
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int w = -1, wr = -1;
+      for (int g = 0; g < G; ++g) {
+        const double v = __ldcg(&sc.cand_val[buf * G + g]);
+        const int rr = __ldcg(&sc.cand_row[buf * G + g]);
+        if (rr >= 0 && (v > b || (v == b && rr < wr))) { b = v; w = g; wr = rr; }
+      }
+      s_win = w;
+      s_row = wr;
+      if (w < 0 || !(b > 0.0)) atomicExch(&flags[FLAG_SINGULAR], 1);
+    }
+    __syncthreads();
+    if (*(volatile int*)&flags[FLAG_SINGULAR]) break;
+    const int w = s_win, r = s_row;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(&sc.cand_data[((size_t)buf * G + w) * n + j]);
+    __syncthreads();
+    if (threadIdx.x == 0) s_piv = prow[k];
+    for (int l = threadIdx.x; l < nloc; l += blockDim.x) fl[l] = rows[(size_t)l * n + k];
+    __syncthreads();
+    const double inv_p = 1.0 / s_piv;
+    const int lr = (w == me) ? (r - me) / G : -1;
+    for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
+      const int l = (int)(e / n), j = (int)(e - (long)l * n);
+      double v;
+      if (l == lr) v = (j == k) ? inv_p : prow[j] * inv_p;
+      else v = (j == k) ? -fl[l] * inv_p : rows[e] - fl[l] * prow[j] * inv_p;
+      rows[e] = v;
+    }
+    if (lr >= 0 && threadIdx.x == 0) {
+      used[lr] = 1;
+      piv[k] = r;
+    }
+    __syncthreads();
+    if (k + 1 < n) publish(k + 1, buf ^ 1);
+    if (!grid_barrier(flags)) return;
+  }
+  for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
+    const int l = (int)(e / n), j = (int)(e - (long)l * n);
+    C[(size_t)(me + G * l) * n + j] = rows[e];
+  }
+}
+
+__global__ void k_gather_perm(int n, const int32_t* piv, const double* y, double* ytmp) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) ytmp[k] = y[piv[k]];
+}
+
+__global__ void k_gemv_rows_perm(int n, const double* __restrict__ B, const int32_t* __restrict__ piv,
+                                 const double* __restrict__ ytmp, double* __restrict__ x) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const double* row = B + (size_t)piv[k] * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += row[j] * ytmp[j];
+  acc = warp_sum(acc);
+  if (lane == 0) x[k] = acc;
+}
+
+// s_c = K_c^T F_c u_{v_c} (adjoint) or K_c F_c u_{v_c}
+__global__ void k_contact_gather_kt(int nc, const int32_t* cv, const double* frame, const double* cdata,
+                                    int transpose, const double* u, double* sc) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int v = cv[c];
+  const double* F = frame + 9 * (size_t)c;
+  const double* K = cdata + 12 * (size_t)c;
+  double y[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = F[3 * i] * u[3 * v] + F[3 * i + 1] * u[3 * v + 1] + F[3 * i + 2] * u[3 * v + 2];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    sc[3 * c + j] = transpose ? K[j] * y[0] + K[3 + j] * y[1] + K[6 + j] * y[2]
+                              : K[3 * j] * y[0] + K[3 * j + 1] * y[1] + K[3 * j + 2] * y[2];
+}
+
+__global__ void k_contact_scatter(int nc, const int32_t* cv, const double* frame, const double* t, double* e) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int v = cv[c];
+  const double* F = frame + 9 * (size_t)c;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    atomicAdd(&e[3 * v + r], F[r] * t[3 * c] + F[3 + r] * t[3 * c + 1] + F[6 + r] * t[3 * c + 2]);
+}
+
+__global__ void k_axpby(int n, double a, const double* x, double b, const double* y, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * (y ? y[i] : 0.0);
+}
+__global__ void k_rhs(int n, const double* dq, const double* dv, double inv_h, double* b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = dq[i] + (dv ? dv[i] * inv_h : 0.0);
+}
+__global__ void k_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sign * x[i] * (*num) / (*den);
+}
+__global__ void k_mul(int n, const double* a, const double* b, double* y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a[i] * b[i];
+}
+
+// partial[k][blk] = sum over this block's slice of V_k . w
+__global__ void k_multi_dot_partial(int n, const double* __restrict__ V, long ld, const double* __restrict__ w,
+                                    double* partial) {
+  const int k = blockIdx.y;
+  const double* vk = V + (size_t)k * ld;
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    acc += vk[i] * w[i];
+  acc = warp_sum(acc);
+  __shared__ double s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? s[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = v;
+  }
+}
+__global__ void k_multi_dot_final(int nparts, const double* partial, double* out) {
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[(size_t)k * nparts + i];
+  acc = warp_sum(acc);
+  __shared__ double s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? s[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[k] = v;
+  }
+}
+__global__ void k_multi_axpy(int n, int nvec, const double* __restrict__ V, long ld, const double* __restrict__ coef,
+                             double* __restrict__ w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = w[i];
+  for (int k = 0; k < nvec; ++k) acc -= coef[k] * V[(size_t)k * ld + i];
+  w[i] = acc;
+}
+__global__ void k_combine(int n, int nvec, const double* __restrict__ V, long ld, const double* __restrict__ coef,
+                          double* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int k = 0; k < nvec; ++k) acc += coef[k] * V[(size_t)k * ld + i];
+  y[i] = acc;
+}
+__global__ void k_normalize(int n, const double* w, const double* nrm2, double* v, double* h_slot) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double nr = sqrt(*nrm2);
+  if (i < n) v[i] = (nr > 0.0) ? w[i] / nr : 0.0;
+  if (i == 0 && h_slot) *h_slot = nr;
+}
+__global__ void k_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res) {
+  const int ld = m + 1;
+  double* h = H + (size_t)ld * j;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = h[j + 1];
+  const double r = hypot(a, b);
+  const double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  h[j] = r;
+  h[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  *res = fabs(g[j + 1]);
+}
+__global__ void k_hess_solve(int k, int m, const double* H, const double* g, double* y) {
+  const int ld = m + 1;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int jj = i + 1; jj < k; ++jj) s -= H[(size_t)ld * jj + i] * y[jj];
+    y[i] = s / H[(size_t)ld * i + i];
+  }
+}
+__global__ void k_cg_alpha(const double* rz, const double* pAp, double* alpha) { *alpha = *rz / *pAp; }
+__global__ void k_cg_update_xr(int n, const double* alpha, const double* p, const double* Ap, double* x, double* r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = *alpha;
+  x[i] += a * p[i];
+  r[i] -= a * Ap[i];
+}
+__global__ void k_cg_update_p(int n, const double* rz_new, const double* rz_old, const double* z, double* p) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double beta = *rz_new / *rz_old;
+  p[i] = z[i] + beta * p[i];
+}
+__global__ void k_copy_scalar(const double* a, double* b) { *b = *a; }
+__global__ void k_nonfinite(int n, const double* x, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(x[i])) atomicExch(&flags[FLAG_NONFINITE], 1);
+}
+
+}  // namespace
+
+void launch_bsr_spmv(int nv, const int32_t* rp, const int32_t* col, const double* val, const double* x, double* y,
+                     cudaStream_t s) {
+  g_launches += 1;
+  k_bsr_spmv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+}
+void launch_bsr_spmv32(int nv, const int32_t* rp, const int32_t* col, const float* val, const double* x, double* y,
+                       cudaStream_t s) {
+  g_launches += 1;
+  k_bsr_spmv32<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+}
+void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
+                     cudaStream_t s) {
+  g_launches += 1;
+  k_diag_inv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, diag_slot, val, val32, dinv);
+}
+void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s) {
+  g_launches += 2;
+  k_spmv_S<<<nblk(32L * a.nv, 256), 256, 0, s>>>(a.nv, a.S_ptr, a.S_col, a.S_val, x, w);
+  k_spmv_St<<<nblk(32L * a.nv, 256), 256, 0, s>>>(a.nv, a.St_ptr, a.St_col, a.St_val, a.perm, w, y);
+}
+void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
+                     const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s) {
+  g_launches += 1;
+  k_delassus<<<nblk((long)nc * nc, 128), 128, 0, s>>>(nc, cvertex, iperm, St_ptr, St_col, St_val, Ds);
+}
+void launch_cap_form(int nc, const double* Ds, const double* frame, const double* cdata, double h, int transpose,
+                     double* C, cudaStream_t s) {
+  g_launches += 1;
+  const long n = 3L * nc;
+  k_cap_form<<<nblk(n * n, 256), 256, 0, s>>>(nc, Ds, frame, cdata, h * h, transpose, C);
+}
+
+static int gj_blocks(int n, int sm_count) { return n < sm_count ? n : sm_count; }
+static size_t gj_smem(int n, int G) {
+  const int nloc_max = (n + G - 1) / G;
+  return ((size_t)nloc_max * n + n + nloc_max) * sizeof(double) + (size_t)nloc_max * sizeof(int);
+}
+size_t gj_scratch_bytes(int n, int sm_count) {
+  const int G = gj_blocks(n, sm_count);
+  return (size_t)2 * G * sizeof(double) + (size_t)2 * G * sizeof(int) + (size_t)2 * G * n * sizeof(double) + 256;
+}
+bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count, cudaStream_t s) {
+  g_launches += 1;
+  const int G = gj_blocks(n, sm_count);
+  const int nloc_max = (n + G - 1) / G;
+  const size_t smem = gj_smem(n, G);
+  if (smem > 220 * 1024) return false;
+  if (cudaFuncSetAttribute(k_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj, 256, smem) != cudaSuccess || per_sm < 1) return false;
+  GJScratch sc;
+  sc.cand_val = scratch;
+  sc.cand_data = scratch + 2 * G;
+  sc.cand_row = (int*)(scratch + 2 * G + (size_t)2 * G * n);
+  int nn = n, nl = nloc_max;
+  void* args[] = {&nn, &nl, &C, &piv, &sc, &flags};
+  return cudaLaunchCooperativeKernel((void*)k_gj, dim3(G), dim3(256), args, smem, s) == cudaSuccess;
+}
+void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
+                     cudaStream_t s) {
+  g_launches += 2;
+  k_gather_perm<<<nblk(n, 256), 256, 0, s>>>(n, piv, y, ytmp);
+  k_gemv_rows_perm<<<nblk(32L * n, 256), 256, 0, s>>>(n, B, piv, ytmp, x);
+}
+void launch_contact_gather_kt(int nc, const int32_t* cv, const double* frame, const double* cdata, int transpose,
+                              const double* u, double* sc, cudaStream_t s) {
+  g_launches += 1;
+  k_contact_gather_kt<<<nblk(nc, 128), 128, 0, s>>>(nc, cv, frame, cdata, transpose, u, sc);
+}
+void launch_contact_scatter(int nv, int nc, const int32_t* cv, const double* frame, const double* t, double* e,
+                            cudaStream_t s) {
+  g_launches += 1;
+  cudaMemsetAsync(e, 0, sizeof(double) * 3 * (size_t)nv, s);
+  k_contact_scatter<<<nblk(nc, 128), 128, 0, s>>>(nc, cv, frame, t, e);
+}
+void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
+  g_launches += 1;
+  k_axpby<<<nblk(n, 256), 256, 0, s>>>(n, a, x, b, y, out);
+}
+void launch_rhs(int n, const double* dq, const double* dv, double inv_h, double* b, cudaStream_t s) {
+  g_launches += 1;
+  k_rhs<<<nblk(n, 256), 256, 0, s>>>(n, dq, dv, inv_h, b);
+}
+void launch_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y,
+                      cudaStream_t s) {
+  g_launches += 1;
+  k_scale_dev<<<nblk(n, 256), 256, 0, s>>>(n, x, num, den, sign, y);
+}
+void launch_mul(int n, const double* a, const double* b, double* y, cudaStream_t s) {
+  g_launches += 1;
+  k_mul<<<nblk(n, 256), 256, 0, s>>>(n, a, b, y);
+}
+void launch_multi_dot(int n, int nvec, const double* V, long ld, const double* w, double* partial, double* out,
+                      cudaStream_t s) {
+  g_launches += 2;
+  int nb = nblk(n, 256);
+  if (nb > 64) nb = 64;
+  k_multi_dot_partial<<<dim3(nb, nvec), 256, 0, s>>>(n, V, ld, w, partial);
+  k_multi_dot_final<<<nvec, 64, 0, s>>>(nb, partial, out);
+}
+void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {
+  g_launches += 1;
+  k_multi_axpy<<<nblk(n, 256), 256, 0, s>>>(n, nvec, V, ld, coef, w);
+}
+void launch_combine(int n, int nvec, const double* V, long ld, const double* coef, double* y, cudaStream_t s) {
+  g_launches += 1;
+  k_combine<<<nblk(n, 256), 256, 0, s>>>(n, nvec, V, ld, coef, y);
+}
+void launch_normalize(int n, const double* w, const double* nrm2, double* v, double* h_slot, cudaStream_t s) {
+  g_launches += 1;
+  k_normalize<<<nblk(n, 256), 256, 0, s>>>(n, w, nrm2, v, h_slot);
+}
+void launch_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res, cudaStream_t s) {
+  g_launches += 1;
+  k_givens<<<1, 1, 0, s>>>(j, m, H, cs, sn, g, res);
+}
+void launch_hess_solve(int k, int m, const double* H, const double* g, double* y, cudaStream_t s) {
+  g_launches += 1;
+  k_hess_solve<<<1, 1, 0, s>>>(k, m, H, g, y);
+}
+void launch_cg_alpha(const double* rz, const double* pAp, double* alpha, cudaStream_t s) {
+  g_launches += 1;
+  k_cg_alpha<<<1, 1, 0, s>>>(rz, pAp, alpha);
+}
+void launch_cg_update_xr(int n, const double* alpha, const double* p, const double* Ap, double* x, double* r,
+                         cudaStream_t s) {
+  g_launches += 1;
+  k_cg_update_xr<<<nblk(n, 256), 256, 0, s>>>(n, alpha, p, Ap, x, r);
+}
+void launch_cg_update_p(int n, const double* rz_new, const double* rz_old, const double* z, double* p,
+                        cudaStream_t s) {
+  g_launches += 1;
+  k_cg_update_p<<<nblk(n, 256), 256, 0, s>>>(n, rz_new, rz_old, z, p);
+}
+void launch_copy_scalar(const double* src, double* dst, cudaStream_t s) {
+  g_launches += 1; k_copy_scalar<<<1, 1, 0, s>>>(src, dst); }
+void launch_nonfinite_check(int n, const double* x, int* flags, cudaStream_t s) {
+  g_launches += 1;
+  k_nonfinite<<<nblk(n, 256), 256, 0, s>>>(n, x, flags);
+}
+
+}  // namespace ncpadj

@@ -1,0 +1,184 @@
+"""Parity of the CUDA adjoint (through the C-ABI) with the FP64 oracle, element by element.
+
+The GPU is fed the oracle's converged states, so only the adjoint is compared.  Tolerances:
+relative 2-norm error per output block (Sec. 5.1's MRE form); <= 1e-8 with the Krylov solve
+driven to rtol 1e-12, and <= 1e-5 (the FP64 target) at the paper's rtol 1e-8.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from tests._cases import make_step, rel, step_case  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+KEYS = [("dL_dq_prev", "dL_dq_prev"), ("dL_dv_prev", "dL_dv_prev"), ("dL_dfext", "dL_dfext"), ("z", "z"),
+        ("dL_dE", "dL_dE"), ("dL_dnu", "dL_dnu"), ("dL_dmu", "dL_dmu_region"), ("dL_dmu_contact", "dL_dmu_contact")]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2603_16478_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    return pkg.Context(0)
+
+
+_scenes = {}
+
+
+def gpu_scene(pkg, ctx, sc):
+    key = (id(sc), sc.name)
+    if key not in _scenes:
+        _scenes[key] = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+    return _scenes[key]
+
+
+def T(a, dt=None, dev="cuda"):
+    dt = dt or torch.float64
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+
+
+def gpu_contacts(pkg, ct, dev="cuda"):
+    if ct.n == 0:
+        return None
+    return pkg.Contacts(T(ct.vertex, torch.int32, dev), T(ct.frame, dev=dev), T(ct.d_n, dev=dev), T(ct.mu, dev=dev),
+                        T(ct.d_f, dev=dev), T(ct.region, torch.int32, dev), ct.n_regions)
+
+
+def run_both(pkg, ctx, case, seed=0, rtol=1e-12, memory="device", **kw):
+    pb, st, s, q_prev, v_prev = case
+    sc = pb.scene
+    rng = np.random.default_rng(seed)
+    dq = 2 * (s.q - pb.q_target) + rng.normal(size=s.q.shape) * 1e-4
+    dv = rng.normal(size=s.q.shape) * 1e-3
+    ref = st.adjoint(s, q_prev, dq, dv)
+    scene = gpu_scene(pkg, ctx, sc)
+    dev = "cuda" if memory == "device" else "cpu"
+    lam = s.lam_frame(st, q_prev) if st.nc else np.zeros((0, 3))
+    g, stats = pkg.adjoint_step(scene, gpu_contacts(pkg, st.ct, dev), T(s.q, dev=dev), T(q_prev, dev=dev),
+                                T(lam, dev=dev), T(dq, dev=dev), T(dv, dev=dev), eps=sc.eps, rtol=rtol,
+                                memory=memory, **kw)
+    torch.cuda.synchronize()
+    return g, ref, stats
+
+
+def assert_parity(g, ref, tol, nc):
+    for k, rk in KEYS:
+        if nc == 0 and k in ("dL_dmu", "dL_dmu_contact"):
+            continue
+        a = g[k].cpu().numpy().reshape(-1)
+        b = np.asarray(ref[rk]).reshape(-1)
+        assert rel(a, b) <= tol, (k, rel(a, b))
+
+
+@pytest.mark.parametrize("name,k", [("cube_drop", 0), ("cube_drop", 2), ("cube_drop", 5), ("two_tet", 1)])
+def test_fp64_parity_tight(pkg, ctx, name, k):
+    case = step_case(name, k)
+    g, ref, stats = run_both(pkg, ctx, case, rtol=1e-12)
+    assert stats["rel_residual"] <= 1e-12
+    assert_parity(g, ref, 1e-8, case[1].nc)
+
+
+@pytest.mark.parametrize("name,k", [("cube_drop", 2), ("cube_drop", 5)])
+def test_fp64_parity_at_paper_tolerance(pkg, ctx, name, k):
+    case = step_case(name, k)
+    g, ref, stats = run_both(pkg, ctx, case, rtol=1e-8)
+    assert_parity(g, ref, 1e-5, case[1].nc)
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "elastic", "woodbury"])
+def test_preconditioners_reach_the_same_gradient(pkg, ctx, precond):
+    case = step_case("cube_drop", 2)
+    g, ref, stats = run_both(pkg, ctx, case, rtol=1e-11, precond=precond, solver="gmres", max_iters=5000)
+    assert_parity(g, ref, 1e-6, case[1].nc)
+
+
+def _iterations(pkg, ctx, case, precond, rtol=1e-8, cap=5000):
+    try:
+        _, _, s = run_both(pkg, ctx, case, rtol=rtol, precond=precond, max_iters=cap)
+        return s["iterations"]
+    except pkg.NcpadjError as e:
+        assert "NOT_CONVERGED" in str(e)
+        return cap + 1
+
+
+def test_woodbury_needs_fewer_iterations_than_jacobi_and_none(pkg, ctx):
+    """Sec. 5.2: Woodbury-GMRES converges in far fewer iterations than Jacobi-GMRES and the
+    unpreconditioned solve (frictional contact)."""
+    case = step_case("cube_drop", 2)
+    n_w = _iterations(pkg, ctx, case, "woodbury")
+    n_j = _iterations(pkg, ctx, case, "jacobi")
+    n_n = _iterations(pkg, ctx, case, "none")
+    assert n_w * 3 < n_j and n_w * 3 < n_n, (n_w, n_j, n_n)
+
+
+def test_frictionless_uses_cg(pkg, ctx):
+    """mu = 0 everywhere: script_A is symmetric and the solver is CG (Sec. 4.4)."""
+    pb, st, s, q_prev, v_prev = step_case("cube_drop", 5)
+    ct = st.ct
+    ct0 = type(ct)(ct.vertex, ct.frame, ct.d_n, ct.d_f, np.zeros_like(ct.mu), ct.region, ct.n_regions)
+    st0 = make_step(pb.scene, ct0)
+    s0 = st0.forward(q_prev, v_prev)
+    g, ref, stats = run_both(pkg, ctx, (pb, st0, s0, q_prev, v_prev), rtol=1e-12)
+    assert stats["solver_used"] == 1
+    assert_parity(g, ref, 1e-8, st0.nc)
+
+
+def test_host_memory_calls_match_device_calls(pkg, ctx):
+    case = step_case("cube_drop", 2)
+    gd, ref, _ = run_both(pkg, ctx, case, rtol=1e-12)
+    gh, _, _ = run_both(pkg, ctx, case, rtol=1e-12, memory="host")
+    for k, _ in KEYS:
+        assert np.array_equal(gd[k].cpu().numpy(), gh[k].numpy()), k
+
+
+def test_repeated_calls_are_deterministic(pkg, ctx):
+    case = step_case("cube_drop", 2)
+    g1, _, _ = run_both(pkg, ctx, case, rtol=1e-10)
+    g2, _, _ = run_both(pkg, ctx, case, rtol=1e-10)
+    # atomics in the assembly may reorder sums: equal to rounding, not bit for bit
+    for k, _ in KEYS:
+        assert rel(g1[k].cpu().numpy(), g2[k].cpu().numpy()) < 1e-12, k
+
+
+def test_inverted_state_is_reported(pkg, ctx):
+    case = step_case("two_tet", 1)
+    pb, st, s, q_prev, v_prev = case
+    q_bad = s.q.copy()
+    q_bad[4:] = q_bad[4:] * np.array([1, 1, -1])  # flip the top layer through the bottom
+    scene = gpu_scene(pkg, ctx, pb.scene)
+    with pytest.raises(pkg.NcpadjError, match="INVERTED_ELEMENT"):
+        pkg.adjoint_step(scene, gpu_contacts(pkg, st.ct), T(q_bad), T(q_prev), T(s.lam_frame(st, q_prev)),
+                         T(np.ones_like(s.q)), None)
+
+
+def test_invalid_arguments_are_rejected(pkg, ctx):
+    case = step_case("two_tet", 1)
+    pb, st, s, q_prev, _ = case
+    scene = gpu_scene(pkg, ctx, pb.scene)
+    with pytest.raises(pkg.NcpadjError, match="INVALID_ARG"):
+        pkg.adjoint_step(scene, gpu_contacts(pkg, st.ct), T(s.q), T(q_prev), T(s.lam_frame(st, q_prev)),
+                         T(np.ones_like(s.q)), None, rtol=-1.0)
+    with pytest.raises(pkg.NcpadjError, match="NOT_CONVERGED"):
+        pkg.adjoint_step(scene, gpu_contacts(pkg, st.ct), T(s.q), T(q_prev), T(s.lam_frame(st, q_prev)),
+                         T(np.ones_like(s.q)), None, rtol=1e-14, max_iters=1, precond="none")
+
+
+def test_out_of_range_contact_vertex_is_rejected(pkg, ctx):
+    case = step_case("two_tet", 1)
+    pb, st, s, q_prev, _ = case
+    scene = gpu_scene(pkg, ctx, pb.scene)
+    c = gpu_contacts(pkg, st.ct)
+    c.vertex = c.vertex.clone()
+    c.vertex[0] = 10 ** 6
+    with pytest.raises(pkg.NcpadjError, match="INVALID_ARG"):
+        pkg.adjoint_step(scene, c, T(s.q), T(q_prev), T(s.lam_frame(st, q_prev)), T(np.ones_like(s.q)), None)
