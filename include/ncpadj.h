@@ -198,6 +198,12 @@ ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpa
                                   const ncpadj_options* opt, ncpadj_grads* grads,
                                   ncpadj_stats* stats, void* stream);
 
+/* y = A^{-1} x for the elastic matrix A = M + h^2 sum_i w_i G_i^T G_i of the scene (Eq. dynamics),
+ * applied through the scene's sparse-inverse factorisation A^{-1} = P^T S^T S P (Sec. 3).
+ * x, y: device arrays [n_verts*3] (not aliased).  Uses the scene's workspace (allocated on first
+ * use).  Errors: INVALID_ARG, OOM, CUDA. */
+ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y, void* stream);
+
 /* ---- forward step -------------------------------------------------------------------------
  * The converged state that ncpadj_adjoint_step differentiates.  One implicit Euler step of
  * Eq. (dynamics): q minimises the incremental potential of Eq. (implicit) with the projective

@@ -97,7 +97,7 @@ class _ForwardStats(C.Structure):
 
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_destroy", "ncpadj_scene_get_info", "ncpadj_options_default",
-           "ncpadj_adjoint_step", "ncpadj_forward_step"]
+           "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve"]
 
 
 def load_library(path: Optional[str] = None):
@@ -126,6 +126,7 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_forward_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_ForwardInput),
                                         C.POINTER(_Options), C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                         C.POINTER(_ForwardStats), C.c_void_p]
+    lib.ncpadj_elastic_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     if path is None:
         _LIB = lib
     return lib
@@ -297,3 +298,13 @@ def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None
     if st != 0:
         raise NcpadjError(st, lib.ncpadj_last_error().decode(), stats.to_dict())
     return q, lam[:nc], stats.to_dict()
+
+
+def elastic_solve(scene: Scene, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None):
+    """y = A^{-1} x with the scene's elastic factor (device tensors [n_verts, 3])."""
+    lib = scene.lib
+    y = torch.empty_like(x) if y is None else y
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib, lib.ncpadj_elastic_solve(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y), C.c_void_p(stream)))
+    return y

@@ -171,6 +171,22 @@ static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
   upload(S.St_col, F.St.col);
   upload(S.St_val, F.St.val);
   S.St_ptr_h = F.St.ptr;
+  auto chunk = [](const CsrD& M, DevBuf& crow, DevBuf& cb, DevBuf& ce) {
+    std::vector<int32_t> r;
+    std::vector<int64_t> b, e;
+    for (int i = 0; i < M.n; ++i)
+      for (int64_t p = M.ptr[i]; p < M.ptr[i + 1]; p += 256) {
+        r.push_back(i);
+        b.push_back(p);
+        e.push_back(std::min<int64_t>(p + 256, M.ptr[i + 1]));
+      }
+    upload(crow, r);
+    upload(cb, b);
+    upload(ce, e);
+    return (int)r.size();
+  };
+  S.nS_chunks = chunk(F.S, S.S_crow, S.S_cbeg, S.S_cend);
+  S.nSt_chunks = chunk(F.St, S.St_crow, S.St_cbeg, S.St_cend);
   S.flags.ensure(FLAG_COUNT * sizeof(int));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
@@ -254,7 +270,9 @@ struct Engine {
     partial = S.red.as<double>();
     scal = S.scal.as<double>();
     sinv = SinvArgs{nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
-                    S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>()};
+                    S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
+                    S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
+                    S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
   }
 
   ContactArgs contact_args(const double* q, const double* q_prev, const double* lambda, double eps) const {
@@ -882,6 +900,28 @@ ncpadj_status ncpadj_scene_get_info(ncpadj_scene s, ncpadj_scene_info* out) {
   out->nnz_Linv = s->s.nnz_S;
   out->ms_factor = s->s.ms_factor;
   return NCPADJ_OK;
+}
+
+ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y, void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(ctx && scene && x && y && x != y, "NULL or aliased argument");
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    Scene& S = scene->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    S.io.ensure(sizeof(double) * 3 * (size_t)S.nv);
+    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+               S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
+               S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
+               S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
+    launch_ainv(a, x, S.io.as<double>(), y, st);
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
 }
 
 ncpadj_status ncpadj_forward_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpadj_contacts* contacts,

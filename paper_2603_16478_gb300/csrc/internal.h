@@ -87,6 +87,8 @@ struct Scene {
   DevBuf perm, iperm;          // int32 [nv]
   DevBuf S_ptr, S_col, S_val;  // rows of S; S_col holds ORIGINAL vertex ids (gather from x)
   DevBuf St_ptr, St_col, St_val;  // rows of S^T; St_col in position space
+  DevBuf S_crow, S_cbeg, S_cend, St_crow, St_cbeg, St_cend;  // row chunks (<= 256 entries)
+  int nS_chunks = 0, nSt_chunks = 0;
   int64_t nnz_S = 0;
   int64_t nnz_L = 0;
   double ms_factor = 0;

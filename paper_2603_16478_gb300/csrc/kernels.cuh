@@ -134,6 +134,10 @@ struct SinvArgs {
   const int32_t* St_col;  // positions
   const double* St_val;
   const int32_t* perm;
+  // chunks of at most 256 entries of the rows of S and S^T
+  int nS, nSt;
+  const int32_t *S_crow, *St_crow;
+  const int64_t *S_cbeg, *S_cend, *St_cbeg, *St_cend;
 };
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
 

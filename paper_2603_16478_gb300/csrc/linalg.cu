@@ -64,53 +64,45 @@ __global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, 
   dinv[i] = 1.0 / (val ? val[k] : (double)val32[k]);
 }
 
-// w[i] = sum_p S_val[p] x[S_col[p]]  (row i of S, position space; S_col holds original ids)
-__global__ void k_spmv_S(int nv, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                         const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ w) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Chunked product of a CSR matrix with 3 right-hand sides: chunk k covers entries
+// [cbeg[k], cend[k]) of row crow[k] (at most 256), one warp per chunk with 8 loads in flight per
+// lane; partial sums are added atomically into y[3 out(row) + r] (y zeroed by the caller),
+// out(row) = omap ? omap[row] : row.  Splitting the long rows near the elimination-tree root over
+// many warps keeps the product bandwidth- rather than latency-bound.
+__global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t* __restrict__ crow,
+                                                     const int64_t* __restrict__ cbeg, const int64_t* __restrict__ cend,
+                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                     const int32_t* __restrict__ omap, const double* __restrict__ x,
+                                                     double* __restrict__ y) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (row >= nv) return;
+  if (k >= nchunks) return;
+  const int64_t b = cbeg[k], e = cend[k];
   double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t p = ptr[row] + lane; p < ptr[row + 1]; p += 32) {
-    const double s = val[p];
-    const int c = col[p];
-    a0 += s * x[3 * c];
-    a1 += s * x[3 * c + 1];
-    a2 += s * x[3 * c + 2];
+  int c[8];
+  double s[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int64_t p = b + lane + 32 * u;
+    c[u] = (p < e) ? col[p] : -1;
+    s[u] = (p < e) ? val[p] : 0.0;
   }
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (c[u] >= 0) {
+      a0 += s[u] * x[3 * c[u]];
+      a1 += s[u] * x[3 * c[u] + 1];
+      a2 += s[u] * x[3 * c[u] + 2];
+    }
   a0 = warp_sum(a0);
   a1 = warp_sum(a1);
   a2 = warp_sum(a2);
   if (lane == 0) {
-    w[3 * row] = a0;
-    w[3 * row + 1] = a1;
-    w[3 * row + 2] = a2;
-  }
-}
-
-// y[perm[j]] = sum_p St_val[p] w[St_col[p]]  (row j of S^T = column j of S)
-__global__ void k_spmv_St(int nv, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                          const double* __restrict__ val, const int32_t* __restrict__ perm,
-                          const double* __restrict__ w, double* __restrict__ y) {
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= nv) return;
-  double a0 = 0, a1 = 0, a2 = 0;
-  for (int64_t p = ptr[row] + lane; p < ptr[row + 1]; p += 32) {
-    const double s = val[p];
-    const int c = col[p];
-    a0 += s * w[3 * c];
-    a1 += s * w[3 * c + 1];
-    a2 += s * w[3 * c + 2];
-  }
-  a0 = warp_sum(a0);
-  a1 = warp_sum(a1);
-  a2 = warp_sum(a2);
-  if (lane == 0) {
-    const int v = perm[row];
-    y[3 * v] = a0;
-    y[3 * v + 1] = a1;
-    y[3 * v + 2] = a2;
+    const int row = crow[k];
+    const int o = omap ? omap[row] : row;
+    atomicAdd(&y[3 * o], a0);
+    atomicAdd(&y[3 * o + 1], a1);
+    atomicAdd(&y[3 * o + 2], a2);
   }
 }
 
@@ -198,7 +190,7 @@ struct GJScratch {
 //   a[r][j] <- a[r][j]/p (j != k), a[r][k] <- 1/p,
 //   a[i][j] <- a[i][j] - a[i][k] a[r][j]/p (j != k), a[i][k] <- -a[i][k]/p  (i != r).
 // After n steps the matrix B satisfies  (C^{-1})[k][r_k'] = B[r_k][k'].  One barrier per step.
-__global__ void k_gj(int n, int nloc_max, double* C, int32_t* piv, GJScratch sc, int* flags) {
+__global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, double* C, int32_t* piv, GJScratch sc, int* flags) {
   extern __shared__ double sm[];
   const int G = gridDim.x, me = blockIdx.x;
   double* rows = sm;                              // [nloc_max][n]
@@ -256,34 +248,53 @@ __global__ void k_gj(int n, int nloc_max, double* C, int32_t* piv, GJScratch sc,
 
   for (int k = 0; k < n; ++k) {
     const int buf = k & 1;
-    if (threadIdx.x == 0) {
-      double b = -1.0;
-      int w = -1, wr = -1;
-      for (int g = 0; g < G; ++g) {
+    {  // winner among the G published candidates: block-wide argmax (ties -> lower row index)
+      double bv = -1.0;
+      int br = -1, bw = -1;
+      for (int g = threadIdx.x; g < G; g += blockDim.x) {
         const double v = __ldcg(&sc.cand_val[buf * G + g]);
         const int rr = __ldcg(&sc.cand_row[buf * G + g]);
-        if (rr >= 0 && (v > b || (v == b && rr < wr))) { b = v; w = g; wr = rr; }
+        if (rr >= 0 && (v > bv || (v == bv && rr < br))) { bv = v; br = rr; bw = g; }
       }
-      s_win = w;
-      s_row = wr;
-      if (w < 0 || !(b > 0.0)) atomicExch(&flags[FLAG_SINGULAR], 1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (orr >= 0 && (ov > bv || (ov == bv && (br < 0 || orr < br)))) { bv = ov; br = orr; bw = ow; }
+      }
+      __shared__ double wv[32];
+      __shared__ int wr[32], ww[32];
+      if ((threadIdx.x & 31) == 0) { wv[threadIdx.x >> 5] = bv; wr[threadIdx.x >> 5] = br; ww[threadIdx.x >> 5] = bw; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double b = -1.0;
+        int w = -1, rr = -1;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+          if (wr[i] >= 0 && (wv[i] > b || (wv[i] == b && (rr < 0 || wr[i] < rr)))) { b = wv[i]; rr = wr[i]; w = ww[i]; }
+        s_win = w;
+        s_row = rr;
+        if (w < 0 || !(b > 0.0)) atomicExch(&flags[FLAG_SINGULAR], 1);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (*(volatile int*)&flags[FLAG_SINGULAR]) break;
     const int w = s_win, r = s_row;
     for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(&sc.cand_data[((size_t)buf * G + w) * n + j]);
     __syncthreads();
-    if (threadIdx.x == 0) s_piv = prow[k];
-    for (int l = threadIdx.x; l < nloc; l += blockDim.x) fl[l] = rows[(size_t)l * n + k];
-    __syncthreads();
-    const double inv_p = 1.0 / s_piv;
+    const double inv_p = 1.0 / prow[k];
     const int lr = (w == me) ? (r - me) / G : -1;
-    for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
-      const int l = (int)(e / n), j = (int)(e - (long)l * n);
-      double v;
-      if (l == lr) v = (j == k) ? inv_p : prow[j] * inv_p;
-      else v = (j == k) ? -fl[l] * inv_p : rows[e] - fl[l] * prow[j] * inv_p;
-      rows[e] = v;
+    // per-row multipliers a[i][k] / p (one FMA per element below)
+    for (int l = threadIdx.x; l < nloc; l += blockDim.x) fl[l] = rows[(size_t)l * n + k] * inv_p;
+    __syncthreads();
+    for (int l = 0; l < nloc; ++l) {
+      double* row = rows + (size_t)l * n;
+      if (l == lr) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = (j == k) ? inv_p : prow[j] * inv_p;
+      } else {
+        const double m = fl[l];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = (j == k) ? -m : fma(-m, prow[j], row[j]);
+      }
     }
     if (lr >= 0 && threadIdx.x == 0) {
       used[lr] = 1;
@@ -480,8 +491,12 @@ void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const 
 }
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s) {
   g_launches += 2;
-  k_spmv_S<<<nblk(32L * a.nv, 256), 256, 0, s>>>(a.nv, a.S_ptr, a.S_col, a.S_val, x, w);
-  k_spmv_St<<<nblk(32L * a.nv, 256), 256, 0, s>>>(a.nv, a.St_ptr, a.St_col, a.St_val, a.perm, w, y);
+  cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
+  k_spmv_chunks<<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr,
+                                                      x, w);
+  cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
+  k_spmv_chunks<<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val,
+                                                       a.perm, w, y);
 }
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
                      const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s) {
@@ -495,6 +510,7 @@ void launch_cap_form(int nc, const double* Ds, const double* frame, const double
   k_cap_form<<<nblk(n * n, 256), 256, 0, s>>>(nc, Ds, frame, cdata, h * h, transpose, C);
 }
 
+static constexpr int kGJThreads = 1024;
 static int gj_blocks(int n, int sm_count) { return n < sm_count ? n : sm_count; }
 static size_t gj_smem(int n, int G) {
   const int nloc_max = (n + G - 1) / G;
@@ -512,14 +528,15 @@ bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flag
   if (smem > 220 * 1024) return false;
   if (cudaFuncSetAttribute(k_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj, 256, smem) != cudaSuccess || per_sm < 1) return false;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj, kGJThreads, smem) != cudaSuccess || per_sm < 1)
+    return false;
   GJScratch sc;
   sc.cand_val = scratch;
   sc.cand_data = scratch + 2 * G;
   sc.cand_row = (int*)(scratch + 2 * G + (size_t)2 * G * n);
   int nn = n, nl = nloc_max;
   void* args[] = {&nn, &nl, &C, &piv, &sc, &flags};
-  return cudaLaunchCooperativeKernel((void*)k_gj, dim3(G), dim3(256), args, smem, s) == cudaSuccess;
+  return cudaLaunchCooperativeKernel((void*)k_gj, dim3(G), dim3(kGJThreads), args, smem, s) == cudaSuccess;
 }
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                      cudaStream_t s) {
