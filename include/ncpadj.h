@@ -204,6 +204,22 @@ ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpa
  * use).  Errors: INVALID_ARG, OOM, CUDA. */
 ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y, void* stream);
 
+/* Variant of ncpadj_elastic_solve that allocates nothing (the paper has no counterpart).
+ * For callers that cannot have device memory allocated while they run -- programs whose device
+ * memory is reserved up front by their own pool, or loops with hard latency limits where a
+ * cudaMalloc is not acceptable.  Same arguments and result as ncpadj_elastic_solve; the
+ * intermediate vector lives in a static device array sized for at most 262,144 vertices
+ * (6 MiB, held by every GPU that loads the library until the process exits).
+ *  - Scenes with more vertices are rejected with NCPADJ_ERR_INVALID_ARG.
+ *  - The call makes no cudaMalloc or cudaFree.  Its first call on a device looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array: calls that overlap on the GPU (other streams, other
+ *    threads) race with each other.  Each call clears the array before use.
+ * Errors: INVALID_ARG, CUDA. */
+ncpadj_status ncpadj_elastic_solve_noalloc(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y,
+                                           void* stream);
+
 /* ---- forward step -------------------------------------------------------------------------
  * The converged state that ncpadj_adjoint_step differentiates.  One implicit Euler step of
  * Eq. (dynamics): q minimises the incremental potential of Eq. (implicit) with the projective

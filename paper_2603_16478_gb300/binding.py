@@ -97,7 +97,7 @@ class _ForwardStats(C.Structure):
 
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_destroy", "ncpadj_scene_get_info", "ncpadj_options_default",
-           "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve"]
+           "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc"]
 
 
 def load_library(path: Optional[str] = None):
@@ -127,6 +127,7 @@ def load_library(path: Optional[str] = None):
                                         C.POINTER(_Options), C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                         C.POINTER(_ForwardStats), C.c_void_p]
     lib.ncpadj_elastic_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.ncpadj_elastic_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     if path is None:
         _LIB = lib
     return lib
@@ -307,4 +308,15 @@ def elastic_solve(scene: Scene, x: torch.Tensor, y: Optional[torch.Tensor] = Non
     if stream is None:
         stream = torch.cuda.current_stream(x.device).cuda_stream
     _check(lib, lib.ncpadj_elastic_solve(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y), C.c_void_p(stream)))
+    return y
+
+
+def elastic_solve_noalloc(scene: Scene, x: torch.Tensor, y: torch.Tensor, stream=None):
+    """y = A^{-1} x without device allocation in the call (y preallocated by the caller; scenes
+    of at most 262,144 vertices; concurrent calls race on the library's static scratch)."""
+    lib = scene.lib
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib, lib.ncpadj_elastic_solve_noalloc(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y),
+                                                 C.c_void_p(stream)))
     return y
