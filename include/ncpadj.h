@@ -107,12 +107,28 @@ ncpadj_status ncpadj_scene_create(ncpadj_ctx ctx, const ncpadj_scene_desc* desc,
 /* Destroy a scene (NULL is a no-op). */
 void ncpadj_scene_destroy(ncpadj_scene scene);
 
+/* A batch of independent scenes solved together (the batched adjoint).  The scene built is the
+ * disjoint union of the n_scenes meshes: the vertices of mesh s are numbered after those of meshes
+ * 0..s-1 (tets likewise), and every array argument of the other calls is the concatenation of
+ * the per-mesh arrays in that order.  All meshes must share h.  Each mesh's elastic factor is
+ * built independently (host threads); the union's matrices are block-diagonal.  In
+ * ncpadj_adjoint_step / ncpadj_forward_step on a batch:
+ *  - contacts must be grouped by mesh (non-decreasing mesh of their vertex); the contact
+ *    capacitance is inverted block by block, one dense block per mesh with contacts;
+ *  - the adjoint scales each mesh's right-hand side to unit norm and tightens the tolerance to
+ *    rtol / sqrt(number of meshes with a nonzero seed), so every mesh's own relative residual is
+ *    at most rtol (the scaling is undone before the contractions).
+ * Errors: as ncpadj_scene_create (the message names the failing mesh). */
+ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_scene_desc* descs,
+                                        ncpadj_scene* out);
+
 typedef struct {
   int32_t n_verts, n_tets;
   int32_t n_blocks;        /* 3x3 blocks in the pattern of script_A */
   int64_t nnz_L;           /* nonzeros of the scalar Cholesky factor */
   int64_t nnz_Linv;        /* nonzeros of its explicit inverse S */
-  double ms_factor;        /* host time of ordering + factorisation + inversion */
+  double ms_factor;        /* host time of ordering + factorisation + inversion (summed over meshes) */
+  int32_t n_scenes;        /* meshes in the scene (1 unless built by ncpadj_scene_create_batch) */
 } ncpadj_scene_info;
 ncpadj_status ncpadj_scene_get_info(ncpadj_scene scene, ncpadj_scene_info* out);
 
@@ -167,13 +183,18 @@ typedef struct {
  *              forward pass's (App. A.2).  Default 1e-4.
  *   rtol       stop at ||b - script_A^T z|| <= rtol ||b||.  Default 1e-8 (Sec. 5).
  *   max_iters  Krylov iteration cap (default 2000); gmres_restart m (default 64).
- *   precision  NCPADJ_FP64 (default) or NCPADJ_MIXED.
+ *   precision  NCPADJ_FP64 (default) or NCPADJ_MIXED: FP32 matrix values (per-tet SVD Jacobians in
+ *              FP32), FP32 matvec and preconditioner apply, FP64 vectors, dot products,
+ *              Gram-Schmidt and Hessenberg; contact blocks always from FP64 state.
  *   precond    NCPADJ_PRECOND_* (default WOODBURY); solver NCPADJ_SOLVER_* (default AUTO:
- *              CG when every mu is 0, else GMRES, Sec. 4.4); memory NCPADJ_MEM_*. */
+ *              CG when every mu is 0, else GMRES, Sec. 4.4); memory NCPADJ_MEM_*.
+ *   cap_precision  factorisation of the contact capacitance: NCPADJ_FP64 (default) or, with
+ *              precision MIXED only, NCPADJ_MIXED (factorised in FP32). */
 typedef struct {
   double eps, rtol;
   int32_t max_iters, gmres_restart;
   int32_t precision, precond, solver, memory;
+  int32_t cap_precision;
 } ncpadj_options;
 void ncpadj_options_default(ncpadj_options* opt);
 

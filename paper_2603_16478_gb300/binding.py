@@ -46,7 +46,7 @@ class _SceneDesc(C.Structure):
 
 class _SceneInfo(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("n_blocks", C.c_int32), ("nnz_L", C.c_int64),
-                ("nnz_Linv", C.c_int64), ("ms_factor", C.c_double)]
+                ("nnz_Linv", C.c_int64), ("ms_factor", C.c_double), ("n_scenes", C.c_int32)]
 
 
 class _Contacts(C.Structure):
@@ -70,7 +70,8 @@ class _Grads(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("eps", C.c_double), ("rtol", C.c_double), ("max_iters", C.c_int32), ("gmres_restart", C.c_int32),
-                ("precision", C.c_int32), ("precond", C.c_int32), ("solver", C.c_int32), ("memory", C.c_int32)]
+                ("precision", C.c_int32), ("precond", C.c_int32), ("solver", C.c_int32), ("memory", C.c_int32),
+                ("cap_precision", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -96,7 +97,8 @@ class _ForwardStats(C.Structure):
 
 
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
-           "ncpadj_scene_create", "ncpadj_scene_destroy", "ncpadj_scene_get_info", "ncpadj_options_default",
+           "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
+           "ncpadj_options_default",
            "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc"]
 
 
@@ -118,6 +120,7 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_ctx_destroy.argtypes = [C.c_void_p]
     lib.ncpadj_scene_create.argtypes = [C.c_void_p, C.POINTER(_SceneDesc), C.POINTER(C.c_void_p)]
     lib.ncpadj_scene_destroy.argtypes = [C.c_void_p]
+    lib.ncpadj_scene_create_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_SceneDesc), C.POINTER(C.c_void_p)]
     lib.ncpadj_scene_get_info.argtypes = [C.c_void_p, C.POINTER(_SceneInfo)]
     lib.ncpadj_options_default.argtypes = [C.POINTER(_Options)]
     lib.ncpadj_adjoint_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_State),
@@ -163,24 +166,45 @@ class Context:
 
 
 class Scene:
-    """Mesh + material + step size; builds the elastic factor on construction (host arrays)."""
+    """Mesh + material + step size; builds the elastic factor on construction (host arrays).
 
-    def __init__(self, ctx: Context, X, tets, E, nu, density: float, h: float):
+    ``Scene.batch(ctx, meshes, h)`` builds a batch: the disjoint union of several meshes, each
+    ``(X, tets, E, nu, density)``, numbered one after the other (``vertex_offsets``)."""
+
+    def __init__(self, ctx: Context, X, tets, E, nu, density: float, h: float, _batch=None):
         self.ctx = ctx
         self.lib = ctx.lib
-        self._X = torch.as_tensor(X, dtype=torch.float64).contiguous().cpu()
-        self._T = torch.as_tensor(tets, dtype=torch.int32).contiguous().cpu()
-        nt = self._T.shape[0]
-        self._E = torch.as_tensor(E, dtype=torch.float64).expand(nt).contiguous().cpu()
-        self._nu = torch.as_tensor(nu, dtype=torch.float64).expand(nt).contiguous().cpu()
-        d = _SceneDesc(self._X.shape[0], nt, self._X.data_ptr(), self._T.data_ptr(), self._E.data_ptr(),
-                       self._nu.data_ptr(), float(density), float(h))
+        meshes = _batch if _batch is not None else [(X, tets, E, nu, density)]
+        self._keep = []
+        descs = (_SceneDesc * len(meshes))()
+        offs = [0]
+        toffs = [0]
+        for i, (Xi, Ti, Ei, nui, rho) in enumerate(meshes):
+            Xt = torch.as_tensor(Xi, dtype=torch.float64).contiguous().cpu()
+            Tt = torch.as_tensor(Ti, dtype=torch.int32).contiguous().cpu()
+            nt = Tt.shape[0]
+            Et = torch.as_tensor(Ei, dtype=torch.float64).expand(nt).contiguous().cpu()
+            nut = torch.as_tensor(nui, dtype=torch.float64).expand(nt).contiguous().cpu()
+            self._keep += [Xt, Tt, Et, nut]
+            descs[i] = _SceneDesc(Xt.shape[0], nt, Xt.data_ptr(), Tt.data_ptr(), Et.data_ptr(), nut.data_ptr(),
+                                  float(rho), float(h))
+            offs.append(offs[-1] + Xt.shape[0])
+            toffs.append(toffs[-1] + nt)
         hnd = C.c_void_p()
-        _check(self.lib, self.lib.ncpadj_scene_create(ctx.handle, C.byref(d), C.byref(hnd)))
+        if _batch is None:
+            _check(self.lib, self.lib.ncpadj_scene_create(ctx.handle, C.byref(descs[0]), C.byref(hnd)))
+        else:
+            _check(self.lib, self.lib.ncpadj_scene_create_batch(ctx.handle, len(meshes), descs, C.byref(hnd)))
         self.handle = hnd
-        self.n_verts = int(self._X.shape[0])
-        self.n_tets = nt
+        self.vertex_offsets = offs
+        self.tet_offsets = toffs
+        self.n_verts = offs[-1]
+        self.n_tets = toffs[-1]
         self.h = float(h)
+
+    @classmethod
+    def batch(cls, ctx: Context, meshes, h: float) -> "Scene":
+        return cls(ctx, None, None, None, None, None, h, _batch=list(meshes))
 
     def info(self) -> dict:
         inf = _SceneInfo()
@@ -221,7 +245,8 @@ class Contacts:
 
 
 def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4,
-                 rtol=1e-8, max_iters=2000, restart=64, precision="fp64", precond="woodbury", solver="auto",
+                 rtol=1e-8, max_iters=2000, restart=64, precision="fp64", cap_precision="fp64", precond="woodbury",
+                 solver="auto",
                  memory="device", outputs: Optional[dict] = None, stream=None, want=("dL_dq_prev", "dL_dv_prev",
                  "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z")):
     """One adjoint step through the C-ABI.  Returns (grads dict of tensors, stats dict).
@@ -255,6 +280,7 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
     opt.precision = PRECISION[precision]
+    opt.cap_precision = PRECISION[cap_precision]
     opt.precond = PRECOND[precond]
     opt.solver = SOLVER[solver]
     opt.memory = MEMORY[memory]

@@ -1,6 +1,8 @@
 // C-ABI entry points, scene set-up and the host-driven adjoint solve.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -47,18 +49,27 @@ static ncpadj_status fail(const Error& e) {
 // ------------------------------------------------------------------------------------------
 // scene set-up
 // ------------------------------------------------------------------------------------------
-static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
+// One mesh's share of a (batch) scene, computed independently of the others.
+struct MeshPart {
+  std::vector<double> gvec, vol, mu, lam, lame_d, mass;
+  std::vector<int32_t> row_ptr, col, slot, diag_slot;  // local vertex numbering
+  ElasticFactor F;
+  double ms_factor = 0;
+};
+
+static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
   const int nv = d.n_verts, nt = d.n_tets;
   NCPADJ_REQUIRE(nv > 0 && nt > 0, "n_verts and n_tets must be positive");
   NCPADJ_REQUIRE(d.rest_pos && d.tets && d.E && d.nu, "scene arrays must not be NULL");
   NCPADJ_REQUIRE(d.density > 0 && d.h > 0 && std::isfinite(d.density) && std::isfinite(d.h),
                  "density and h must be positive");
-  S.nv = nv;
-  S.nt = nt;
-  S.h = d.h;
-  S.density = d.density;
-  std::vector<double> gvec(12 * (size_t)nt), vol(nt), mu(nt), lam(nt), lame_d(4 * (size_t)nt);
-  S.mass.assign(nv, 0.0);
+  NCPADJ_REQUIRE(d.h == h, "every scene of a batch must use the same step size h");
+  P.gvec.assign(12 * (size_t)nt, 0.0);
+  P.vol.assign(nt, 0.0);
+  P.mu.assign(nt, 0.0);
+  P.lam.assign(nt, 0.0);
+  P.lame_d.assign(4 * (size_t)nt, 0.0);
+  P.mass.assign(nv, 0.0);
   for (int t = 0; t < nt; ++t) {
     int v[4];
     for (int a = 0; a < 4; ++a) {
@@ -84,21 +95,21 @@ static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
     B[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) / det;
     // g_a = row (a-1) of B for a = 1..3, g_0 = -(g_1 + g_2 + g_3): F = sum_a x_a g_a^T
     for (int k = 0; k < 3; ++k) {
-      gvec[12 * t + k] = -(B[0][k] + B[1][k] + B[2][k]);
-      for (int a = 1; a < 4; ++a) gvec[12 * t + 3 * a + k] = B[a - 1][k];
+      P.gvec[12 * t + k] = -(B[0][k] + B[1][k] + B[2][k]);
+      for (int a = 1; a < 4; ++a) P.gvec[12 * t + 3 * a + k] = B[a - 1][k];
     }
-    vol[t] = det / 6.0;
+    P.vol[t] = det / 6.0;
     const double E = d.E[t], nu = d.nu[t];
     NCPADJ_REQUIRE(E > 0 && nu > -1.0 && nu < 0.5 && std::isfinite(E),
                    "tet " + std::to_string(t) + ": need E > 0 and -1 < nu < 0.5");
-    mu[t] = E / (2.0 * (1.0 + nu));
-    lam[t] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    lame_d[4 * t + 0] = 1.0 / (2.0 * (1.0 + nu));
-    lame_d[4 * t + 1] = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    lame_d[4 * t + 2] = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+    P.mu[t] = E / (2.0 * (1.0 + nu));
+    P.lam[t] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    P.lame_d[4 * t + 0] = 1.0 / (2.0 * (1.0 + nu));
+    P.lame_d[4 * t + 1] = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    P.lame_d[4 * t + 2] = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
     const double q = (1.0 + nu) * (1.0 - 2.0 * nu);
-    lame_d[4 * t + 3] = E * (1.0 + 2.0 * nu * nu) / (q * q);
-    for (int a = 0; a < 4; ++a) S.mass[v[a]] += d.density * vol[t] / 4.0;
+    P.lame_d[4 * t + 3] = E * (1.0 + 2.0 * nu * nu) / (q * q);
+    for (int a = 0; a < 4; ++a) P.mass[v[a]] += d.density * P.vol[t] / 4.0;
   }
   // block pattern: vertices sharing a tet (sorted neighbour lists, self included)
   std::vector<std::vector<int32_t>> nbr(nv);
@@ -106,51 +117,132 @@ static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
   for (int t = 0; t < nt; ++t)
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) nbr[d.tets[4 * t + a]].push_back(d.tets[4 * t + b]);
-  std::vector<int32_t> row_ptr(nv + 1, 0), col;
+  P.row_ptr.assign(nv + 1, 0);
+  P.col.clear();
   for (int v = 0; v < nv; ++v) {
     auto& L = nbr[v];
     std::sort(L.begin(), L.end());
     L.erase(std::unique(L.begin(), L.end()), L.end());
-    row_ptr[v + 1] = row_ptr[v] + (int)L.size();
-    col.insert(col.end(), L.begin(), L.end());
+    P.row_ptr[v + 1] = P.row_ptr[v] + (int)L.size();
+    P.col.insert(P.col.end(), L.begin(), L.end());
   }
-  S.nb = row_ptr[nv];
   auto find_slot = [&](int u, int w) {
-    auto b = col.begin() + row_ptr[u], e = col.begin() + row_ptr[u + 1];
-    return (int32_t)(std::lower_bound(b, e, w) - col.begin());
+    auto b = P.col.begin() + P.row_ptr[u], e = P.col.begin() + P.row_ptr[u + 1];
+    return (int32_t)(std::lower_bound(b, e, w) - P.col.begin());
   };
-  std::vector<int32_t> slot(16 * (size_t)nt), diag_slot(nv);
+  P.slot.assign(16 * (size_t)nt, 0);
+  P.diag_slot.assign(nv, 0);
   for (int t = 0; t < nt; ++t)
     for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) slot[16 * t + 4 * a + b] = find_slot(d.tets[4 * t + a], d.tets[4 * t + b]);
-  for (int v = 0; v < nv; ++v) diag_slot[v] = find_slot(v, v);
+      for (int b = 0; b < 4; ++b) P.slot[16 * t + 4 * a + b] = find_slot(d.tets[4 * t + a], d.tets[4 * t + b]);
+  for (int v = 0; v < nv; ++v) P.diag_slot[v] = find_slot(v, v);
   // scalar elastic matrix A_s = M_s + h^2 sum_i w_i (g_a . g_b), w_i = 2 mu_i V_i
   CsrD As;
   As.n = nv;
-  As.ptr.assign(row_ptr.begin(), row_ptr.end());
-  As.col = col;
-  As.val.assign(col.size(), 0.0);
-  for (int v = 0; v < nv; ++v) As.val[diag_slot[v]] += S.mass[v];
+  As.ptr.assign(P.row_ptr.begin(), P.row_ptr.end());
+  As.col = P.col;
+  As.val.assign(P.col.size(), 0.0);
+  for (int v = 0; v < nv; ++v) As.val[P.diag_slot[v]] += P.mass[v];
   const double h2 = d.h * d.h;
   for (int t = 0; t < nt; ++t) {
-    const double w = 2.0 * mu[t] * vol[t];
+    const double w = 2.0 * P.mu[t] * P.vol[t];
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) {
         double gg = 0;
-        for (int k = 0; k < 3; ++k) gg += gvec[12 * t + 3 * a + k] * gvec[12 * t + 3 * b + k];
-        As.val[slot[16 * t + 4 * a + b]] += h2 * w * gg;
+        for (int k = 0; k < 3; ++k) gg += P.gvec[12 * t + 3 * a + k] * P.gvec[12 * t + 3 * b + k];
+        As.val[P.slot[16 * t + 4 * a + b]] += h2 * w * gg;
       }
   }
   auto t0 = std::chrono::steady_clock::now();
-  ElasticFactor F;
-  factor_elastic(As, d.rest_pos, F);
-  S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  S.nnz_L = F.nnz_L;
-  S.nnz_S = (int64_t)F.S.col.size();
-  // S rows gather from the caller's (original) vertex numbering: remap column ids
-  std::vector<int32_t> Scol_orig(F.S.col.size());
-  for (size_t p = 0; p < F.S.col.size(); ++p) Scol_orig[p] = F.perm[F.S.col[p]];
-  std::vector<int32_t> tets(d.tets, d.tets + 4 * (size_t)nt);
+  factor_elastic(As, d.rest_pos, P.F);
+  P.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// A scene is the disjoint union of one or more meshes (a batch): vertex and tet ids of mesh s are
+// offset by the counts of meshes 0..s-1.  Each mesh's factor is computed independently (in
+// parallel) and the union's matrices are block-diagonal.
+static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) {
+  NCPADJ_REQUIRE(n_scenes >= 1 && descs, "need at least one scene description");
+  const double h = descs[0].h;
+  std::vector<MeshPart> parts(n_scenes);
+  std::vector<Error> errs(n_scenes, Error{NCPADJ_OK, ""});
+  {
+    const int nth = std::max(1, std::min<int>(n_scenes, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nth; ++w)
+      pool.emplace_back([&]() {
+        for (int i = next++; i < n_scenes; i = next++) {
+          try {
+            build_part(descs[i], h, parts[i]);
+          } catch (const Error& e) {
+            errs[i] = e;
+          } catch (const std::exception& e) {
+            errs[i] = Error{NCPADJ_ERR_OOM, e.what()};
+          }
+        }
+      });
+    for (auto& t : pool) t.join();
+  }
+  for (int i = 0; i < n_scenes; ++i)
+    if (errs[i].status != NCPADJ_OK)
+      throw Error{errs[i].status, (n_scenes > 1 ? "scene " + std::to_string(i) + ": " : std::string()) + errs[i].msg};
+  // union with offsets
+  S.n_scenes = n_scenes;
+  S.voff.assign(n_scenes + 1, 0);
+  S.toff.assign(n_scenes + 1, 0);
+  for (int i = 0; i < n_scenes; ++i) {
+    S.voff[i + 1] = S.voff[i] + descs[i].n_verts;
+    S.toff[i + 1] = S.toff[i] + descs[i].n_tets;
+  }
+  const int nv = S.voff[n_scenes], nt = S.toff[n_scenes];
+  S.nv = nv;
+  S.nt = nt;
+  S.h = h;
+  S.density = descs[0].density;
+  std::vector<double> gvec, vol, mu, lam, lame_d;
+  std::vector<int32_t> tets, row_ptr(1, 0), col, slot, diag_slot, perm, iperm, scene_of_vertex;
+  S.mass.clear();
+  CsrD Su, Stu;  // union sparse inverse (position space of the union = concatenated positions)
+  Su.n = Stu.n = nv;
+  Su.ptr.assign(1, 0);
+  Stu.ptr.assign(1, 0);
+  int64_t nnz_L = 0;
+  double ms = 0;
+  for (int i = 0; i < n_scenes; ++i) {
+    const MeshPart& P = parts[i];
+    const int vo = S.voff[i];
+    const int bo = (int)col.size();
+    gvec.insert(gvec.end(), P.gvec.begin(), P.gvec.end());
+    vol.insert(vol.end(), P.vol.begin(), P.vol.end());
+    mu.insert(mu.end(), P.mu.begin(), P.mu.end());
+    lam.insert(lam.end(), P.lam.begin(), P.lam.end());
+    lame_d.insert(lame_d.end(), P.lame_d.begin(), P.lame_d.end());
+    S.mass.insert(S.mass.end(), P.mass.begin(), P.mass.end());
+    for (int t = 0; t < descs[i].n_tets * 4; ++t) tets.push_back(descs[i].tets[t] + vo);
+    for (int v = 0; v < descs[i].n_verts; ++v) row_ptr.push_back(bo + P.row_ptr[v + 1]);
+    for (int32_t c : P.col) col.push_back(c + vo);
+    for (int32_t x : P.slot) slot.push_back(x + bo);
+    for (int32_t x : P.diag_slot) diag_slot.push_back(x + bo);
+    for (int32_t x : P.F.perm) perm.push_back(x + vo);
+    for (int32_t x : P.F.iperm) iperm.push_back(x + vo);
+    scene_of_vertex.insert(scene_of_vertex.end(), descs[i].n_verts, i);
+    const int64_t so = (int64_t)Su.col.size(), sto = (int64_t)Stu.col.size();
+    for (int r = 0; r < P.F.n; ++r) {
+      Su.ptr.push_back(so + P.F.S.ptr[r + 1]);
+      Stu.ptr.push_back(sto + P.F.St.ptr[r + 1]);
+    }
+    for (int32_t c : P.F.S.col) Su.col.push_back(P.F.perm[c] + vo);  // rows of S gather by original id
+    Su.val.insert(Su.val.end(), P.F.S.val.begin(), P.F.S.val.end());
+    for (int32_t c : P.F.St.col) Stu.col.push_back(c + vo);  // position space
+    Stu.val.insert(Stu.val.end(), P.F.St.val.begin(), P.F.St.val.end());
+    nnz_L += P.F.nnz_L;
+    ms += P.ms_factor;
+  }
+  S.nb = (int)col.size();
+  S.ms_factor = ms;
+  S.nnz_L = nnz_L;
+  S.nnz_S = (int64_t)Su.col.size();
   upload(S.tets, tets);
   upload(S.gvec, gvec);
   upload(S.vol, vol);
@@ -162,15 +254,21 @@ static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
   upload(S.col, col);
   upload(S.slot, slot);
   upload(S.diag_slot, diag_slot);
-  upload(S.perm, F.perm);
-  upload(S.iperm, F.iperm);
-  upload(S.S_ptr, F.S.ptr);
-  upload(S.S_col, Scol_orig);
-  upload(S.S_val, F.S.val);
-  upload(S.St_ptr, F.St.ptr);
-  upload(S.St_col, F.St.col);
-  upload(S.St_val, F.St.val);
-  S.St_ptr_h = F.St.ptr;
+  upload(S.perm, perm);
+  upload(S.iperm, iperm);
+  upload(S.scene_of_vertex, scene_of_vertex);
+  upload(S.S_ptr, Su.ptr);
+  upload(S.S_col, Su.col);
+  upload(S.S_val, Su.val);
+  upload(S.St_ptr, Stu.ptr);
+  upload(S.St_col, Stu.col);
+  upload(S.St_val, Stu.val);
+  {
+    std::vector<float> f1(Su.val.begin(), Su.val.end()), f2(Stu.val.begin(), Stu.val.end());
+    upload(S.S_val32, f1);
+    upload(S.St_val32, f2);
+  }
+  S.St_ptr_h = Stu.ptr;
   auto chunk = [](const CsrD& M, DevBuf& crow, DevBuf& cb, DevBuf& ce) {
     std::vector<int32_t> r;
     std::vector<int64_t> b, e;
@@ -185,11 +283,12 @@ static void build_scene(Scene& S, const ncpadj_scene_desc& d) {
     upload(ce, e);
     return (int)r.size();
   };
-  S.nS_chunks = chunk(F.S, S.S_crow, S.S_cbeg, S.S_cend);
-  S.nSt_chunks = chunk(F.St, S.St_crow, S.St_cbeg, S.St_cend);
+  S.nS_chunks = chunk(Su, S.S_crow, S.S_cbeg, S.S_cend);
+  S.nSt_chunks = chunk(Stu, S.St_crow, S.St_cbeg, S.St_cend);
   S.flags.ensure(FLAG_COUNT * sizeof(int));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
+  NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_host, (2 * 513 + 1) * sizeof(double)));
   for (auto& e : S.ev) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
 }
 
@@ -228,6 +327,48 @@ struct Engine {
   double *Ds = nullptr, *Cm = nullptr;
   int32_t* piv = nullptr;
   bool cap_timed = false;
+  // mixed precision: FP32 matrix values, FP32 A^{-1} products and capacitance apply
+  bool mixed = false;
+  bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
+  float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr, *Ctmp32 = nullptr;
+  // the capacitance is block-diagonal by scene (contacts of different meshes share no ancestor
+  // in the elimination forest): one dense block per scene that has contacts
+  std::vector<int> blk_c0, blk_nc;
+  std::vector<size_t> blk_moff, blk_doff;
+  size_t cap_elems = 0, ds_elems = 0;
+
+  void plan_blocks() {
+    blk_c0.clear();
+    blk_nc.clear();
+    if (nc == 0) return;
+    if (S.n_scenes == 1) {
+      blk_c0.push_back(0);
+      blk_nc.push_back(nc);
+    } else {
+      S.io.ensure(sizeof(int32_t) * (size_t)nc + 64);
+      launch_contact_scene(nc, in.cvertex, S.scene_of_vertex.as<int32_t>(), S.io.as<int32_t>(), st);
+      std::vector<int32_t> cs(nc);
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(cs.data(), S.io.as<int32_t>(), sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, st));
+      NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int c = 0; c < nc; ++c) {
+        NCPADJ_REQUIRE(c == 0 || cs[c] >= cs[c - 1], "contacts of a batch scene must be grouped by scene");
+        if (c == 0 || cs[c] != cs[c - 1]) {
+          blk_c0.push_back(c);
+          blk_nc.push_back(0);
+        }
+        blk_nc.back()++;
+      }
+    }
+    blk_moff.assign(blk_c0.size(), 0);
+    blk_doff.assign(blk_c0.size(), 0);
+    cap_elems = ds_elems = 0;
+    for (size_t b = 0; b < blk_c0.size(); ++b) {
+      blk_moff[b] = cap_elems;
+      blk_doff[b] = ds_elems;
+      cap_elems += (size_t)9 * blk_nc[b] * blk_nc[b];
+      ds_elems += (size_t)blk_nc[b] * blk_nc[b];
+    }
+  }
   SinvArgs sinv{};
 
   Engine(Scene& s, const Ctx& c, cudaStream_t stream) : S(s), C(c), st(stream) {
@@ -243,20 +384,32 @@ struct Engine {
     m = m_;
     precond = precond_;
     ncap = 3 * nc;
-    S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
+    plan_blocks();
+    if (mixed) {
+      S.bsr32.ensure(sizeof(float) * 9 * (size_t)S.nb);
+      S.vec32.ensure(sizeof(float) * (2 * (size_t)N + 2 * cap_elems + 64));
+      x32 = S.vec32.as<float>();
+      w32 = x32 + N;
+      Cm32 = w32 + N;
+      Ctmp32 = Cm32 + cap_elems;
+    } else {
+      S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
+    }
     S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
     S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
     const size_t nvec = 9, ncv = 3 * (size_t)std::max(ncap, 1);
     S.vecs.ensure(sizeof(double) * (nvec * N + ncv + 64));
-    S.gmres.ensure(sizeof(double) * ((size_t)(m + 1) * N + (size_t)(m + 1) * (m + 4) + 16));
+    S.gmres.ensure(sizeof(double) * ((size_t)(m + 1) * N + 3 * (size_t)(m + 1) + 16));
     S.red.ensure(sizeof(double) * (64 * (size_t)(m + 2) + 64));
     S.scal.ensure(sizeof(double) * (64 + (size_t)m + 8));
     if (nc && precond == NCPADJ_PRECOND_WOODBURY) {
-      S.cap.ensure(sizeof(double) * ((size_t)ncap * ncap + (size_t)nc * nc + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
-      S.capw.ensure(gj_scratch_bytes(ncap, C.sm_count));
+      S.cap.ensure(sizeof(double) * (cap_elems + ds_elems + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
+      int nmax = 0;
+      for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
+      S.capw.ensure(gj_scratch_bytes(nmax, C.sm_count));
       Cm = S.cap.as<double>();
-      Ds = Cm + (size_t)ncap * ncap;
-      piv = reinterpret_cast<int32_t*>(Ds + (size_t)nc * nc + 16);
+      Ds = Cm + cap_elems;
+      piv = reinterpret_cast<int32_t*>(Ds + ds_elems + 16);
     }
     double* base = S.vecs.as<double>();
     for (double** v : {&b, &x, &r, &w, &t0, &t1, &t2, &t3, &dinv}) {
@@ -272,48 +425,74 @@ struct Engine {
     sinv = SinvArgs{nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
                     S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                     S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
-                    S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
+                    S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};
   }
 
   ContactArgs contact_args(const double* q, const double* q_prev, const double* lambda, double eps) const {
     return ContactArgs{nc, in.cvertex, in.frame, in.d_n, in.d_f, in.mu, lambda, q, q_prev, S.diag_slot.as<int32_t>(),
-                       eps, h, transpose, S.bsr64.as<double>(), nullptr, S.cdata.as<double>(), flags};
+                       eps, h, transpose, mixed ? nullptr : S.bsr64.as<double>(), mixed ? S.bsr32.as<float>() : nullptr,
+                       S.cdata.as<double>(), flags};
   }
 
   // script_A (transpose = 0) or script_A^T (transpose = 1) at (q, lambda) into the block pattern
   void assemble(const double* q, const double* q_prev, const double* lambda, double eps) {
-    launch_bsr_init(nv, S.nb, S.diag_slot.as<int32_t>(), S.massd.as<double>(), S.bsr64.as<double>(), nullptr, st);
+    double* b64 = mixed ? nullptr : S.bsr64.as<double>();
+    float* b32 = mixed ? S.bsr32.as<float>() : nullptr;
+    launch_bsr_init(nv, S.nb, S.diag_slot.as<int32_t>(), S.massd.as<double>(), b64, b32, st);
     TetArgs ta{nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(), S.lam.as<double>(),
-               S.slot.as<int32_t>(), q, h, S.bsr64.as<double>(), nullptr, S.tetdata.as<double>(), flags};
-    launch_tet_assemble64(ta, st);
+               S.slot.as<int32_t>(), q, h, b64, b32, S.tetdata.as<double>(), flags};
+    if (mixed) launch_tet_assemble32(ta, st);
+    else launch_tet_assemble64(ta, st);
     if (nc) launch_contact_blocks(contact_args(q, q_prev, lambda, eps), st);
     NCPADJ_CUDA_TRY(cudaGetLastError());
   }
 
   void setup_precond() {
     if (precond == NCPADJ_PRECOND_JACOBI)
-      launch_diag_inv(nv, S.diag_slot.as<int32_t>(), S.bsr64.as<double>(), nullptr, dinv, st);
+      launch_diag_inv(nv, S.diag_slot.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
+                      mixed ? S.bsr32.as<float>() : nullptr, dinv, st);
     if (precond == NCPADJ_PRECOND_WOODBURY && nc) {
-      launch_delassus(nc, in.cvertex, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
-                      S.St_val.as<double>(), Ds, st);
-      launch_cap_form(nc, Ds, in.frame, S.cdata.as<double>(), h, transpose, Cm, st);
-      NCPADJ_CUDA_TRY(cudaGetLastError());
-      NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
-      if (!launch_gj_invert(ncap, Cm, piv, S.capw.as<double>(), flags, C.sm_count, st)) {
-        cudaGetLastError();
-        throw Error{NCPADJ_ERR_UNSUPPORTED,
-                    "capacitance of dimension " + std::to_string(ncap) + " does not fit the direct inverse"};
+      for (size_t k = 0; k < blk_c0.size(); ++k) {
+        const int c0 = blk_c0[k], m_ = blk_nc[k], n_ = 3 * m_;
+        double* Cb = Cm + blk_moff[k];
+        double* Db = Ds + blk_doff[k];
+        int32_t* pb = piv + 3 * c0;
+        launch_delassus(m_, in.cvertex + c0, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
+                        S.St_val.as<double>(), Db, st);
+        launch_cap_form(m_, Db, in.frame + 9 * (size_t)c0, S.cdata.as<double>() + 12 * (size_t)c0, h, transpose, Cb,
+                        st);
+        NCPADJ_CUDA_TRY(cudaGetLastError());
+        if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
+        bool ok;
+        if (mixed && cap_fp32) {
+          launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
+          ok = launch_gj_invert32(n_, Cm32 + blk_moff[k], Ctmp32 + blk_moff[k], pb, flags, C.sm_count, st);
+        } else {
+          ok = launch_gj_invert(n_, Cb, pb, S.capw.as<double>(), flags, C.sm_count, st);
+          if (ok && mixed) launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);  // FP32 apply
+        }
+        if (!ok) {
+          cudaGetLastError();
+          throw Error{NCPADJ_ERR_UNSUPPORTED,
+                      "capacitance block of dimension " + std::to_string(n_) + " does not fit the direct inverse"};
+        }
+        if (k + 1 == blk_c0.size()) {
+          NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[7], st));
+          cap_timed = true;
+        }
+        NCPADJ_CUDA_TRY(cudaGetLastError());
       }
-      NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[7], st));
-      cap_timed = true;
-      NCPADJ_CUDA_TRY(cudaGetLastError());
     }
   }
 
   void matvec(const double* xin, double* yout) {
-    launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), xin, yout, st);
+    if (mixed) launch_bsr_spmv32(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), xin, yout, st);
+    else launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), xin, yout, st);
   }
-  void ainv(const double* xin, double* yout) { launch_ainv(sinv, xin, t3, yout, st); }
+  void ainv(const double* xin, double* yout) {
+    if (mixed) launch_ainv32(sinv, xin, x32, w32, yout, st);
+    else launch_ainv(sinv, xin, t3, yout, st);
+  }
 
   // yout = P^{-1} xin; uses t0..t3 as scratch (yout must be none of them)
   void apply_precond(const double* xin, double* yout) {
@@ -334,7 +513,12 @@ struct Engine {
         }
         ainv(xin, t1);
         launch_contact_gather_kt(nc, in.cvertex, in.frame, S.cdata.as<double>(), transpose, t1, sc, st);
-        launch_gj_apply(ncap, Cm, piv, sc, ytmp, tc, st);
+        for (size_t k = 0; k < blk_c0.size(); ++k) {
+          const size_t o = 3 * (size_t)blk_c0[k];
+          const int n_ = 3 * blk_nc[k];
+          if (mixed) launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+          else launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+        }
         launch_contact_scatter(nv, nc, in.cvertex, in.frame, tc, t2, st);
         ainv(t2, t0);
         launch_axpby(N, 1.0, t1, -h * h, t0, yout, st);
@@ -383,46 +567,60 @@ struct Engine {
         }
         iters = std::min(iters, max_iters);
       } else {
-        double* V = S.gmres.as<double>();    // (m+1) x N
-        double* H = V + (size_t)(m + 1) * N;  // (m+1) x m, column-major
-        double* cs = H + (size_t)(m + 1) * m;
-        double* sn = cs + m;
-        double* g = sn + m;  // m+1
-        double* y = g + m + 1;
-        double* hc2 = scal + 32;
-        double* res_d = scal + 4;
+        // Arnoldi vectors on the device; the small Hessenberg least-squares problem (Givens
+        // rotations, triangular solve) on the host, which reads the Gram-Schmidt coefficients of
+        // each iteration in one copy together with the convergence check.
+        double* V = S.gmres.as<double>();  // (m+1) x N
+        double* gs = V + (size_t)(m + 1) * N;  // [0..m]: first-pass, [m+1..2m+1]: second-pass, [2m+2]: norm
+        double* ydev = gs + 2 * (m + 1) + 1;
         double* nrm2 = scal + 5;
+        std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m), hbuf(2 * (m + 1) + 1);
         NCPADJ_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         double beta = bnorm;
-        std::vector<double> g0(m + 1, 0.0);
         for (;;) {
           launch_axpby(N, 1.0 / beta, r, 0.0, nullptr, V, st);
-          g0[0] = beta;
-          NCPADJ_CUDA_TRY(cudaMemcpyAsync(g, g0.data(), sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
+          std::fill(g.begin(), g.end(), 0.0);
+          g[0] = beta;
           int k = 0;
           for (int j = 0; j < m; ++j) {
-            double* vj = V + (size_t)j * N;
             double* vn = V + (size_t)(j + 1) * N;
-            double* hcol = H + (size_t)(m + 1) * j;
-            apply_precond(vj, w);
+            apply_precond(V + (size_t)j * N, w);
             matvec(w, vn);
-            launch_multi_dot(N, j + 1, V, N, vn, partial, hcol, st);
-            launch_multi_axpy(N, j + 1, V, N, hcol, vn, st);
-            launch_multi_dot(N, j + 1, V, N, vn, partial, hc2, st);
-            launch_multi_axpy(N, j + 1, V, N, hc2, vn, st);
-            launch_axpby(j + 1, 1.0, hcol, 1.0, hc2, hcol, st);
+            launch_multi_dot(N, j + 1, V, N, vn, partial, gs, st);
+            launch_multi_axpy(N, j + 1, V, N, gs, vn, st);
+            launch_multi_dot(N, j + 1, V, N, vn, partial, gs + (m + 1), st);
+            launch_multi_axpy(N, j + 1, V, N, gs + (m + 1), vn, st);
             launch_multi_dot(N, 1, vn, N, vn, partial, nrm2, st);
-            launch_normalize(N, vn, nrm2, vn, hcol + j + 1, st);
-            launch_givens(j, m, H, cs, sn, g, res_d, st);
-            NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host, res_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+            launch_normalize(N, vn, nrm2, vn, gs + 2 * (m + 1), st);
+            NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_host, gs, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, st));
             NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+            double* h = &H[(size_t)(m + 1) * j];
+            for (int i = 0; i <= j; ++i) h[i] = S.gs_host[i] + S.gs_host[m + 1 + i];
+            h[j + 1] = S.gs_host[2 * (m + 1)];
+            for (int i = 0; i < j; ++i) {  // previous rotations
+              const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+              h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+              h[i] = t;
+            }
+            const double rr = std::hypot(h[j], h[j + 1]);
+            cs[j] = rr > 0 ? h[j] / rr : 1.0;
+            sn[j] = rr > 0 ? h[j + 1] / rr : 0.0;
+            h[j] = rr;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
             ++iters;
             k = j + 1;
-            const double res_est = S.scal_host[0];
+            const double res_est = std::fabs(g[j + 1]);
             if (!std::isfinite(res_est) || res_est <= tol || iters >= max_iters) break;
           }
-          launch_hess_solve(k, m, H, g, y, st);
-          launch_combine(N, k, V, N, y, r, st);
+          for (int i = k - 1; i >= 0; --i) {  // H(0:k,0:k) y = g(0:k)
+            double t = g[i];
+            for (int jj = i + 1; jj < k; ++jj) t -= H[(size_t)(m + 1) * jj + i] * y[jj];
+            y[i] = t / H[(size_t)(m + 1) * i + i];
+          }
+          NCPADJ_CUDA_TRY(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+          launch_combine(N, k, V, N, ydev, r, st);
           apply_precond(r, w);
           launch_axpby(N, 1.0, x, 1.0, w, x, st);
           matvec(x, w);
@@ -473,7 +671,8 @@ void validate_options(const ncpadj_options& opt) {
                  "bad options (eps, rtol, max_iters, gmres_restart)");
   NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 2, "bad precond/solver");
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
-  if (opt.precision != NCPADJ_FP64) throw Error{NCPADJ_ERR_UNSUPPORTED, "only NCPADJ_FP64 is implemented in this build"};
+  NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
+  NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED, "bad cap_precision");
 }
 
 void raise_flags(const int* fh) {
@@ -561,6 +760,8 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     }
   }
   const int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
+  E.mixed = opt.precision == NCPADJ_MIXED;
+  E.cap_fp32 = E.mixed && opt.cap_precision == NCPADJ_MIXED;
   E.workspace(nc, opt.gmres_restart, opt.precond);
   E.transpose = 1;
   int* flags = E.flags;
@@ -573,7 +774,34 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[2], st));
   launch_rhs(N, in.dL_dq, in.dL_dv, 1.0 / S.h, E.b, st);
   double rel = 0, bnorm = 0;
-  const int iters = E.solve(solver, opt.rtol, opt.max_iters, &rel, &bnorm);
+  // a batch holds independent systems: scale each scene's right-hand side to unit norm so that the
+  // union's relative residual bounds every scene's (the scaling is undone on z afterwards)
+  std::vector<double> scale;
+  double rtol = opt.rtol;
+  if (S.n_scenes > 1) {
+    const int ns = S.n_scenes;
+    S.sceneval.ensure(sizeof(double) * 2 * (size_t)ns);
+    double* sq = S.sceneval.as<double>();
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(sq, 0, sizeof(double) * ns, st));
+    launch_scene_sq(nv, E.b, S.scene_of_vertex.as<int32_t>(), sq, st);
+    std::vector<double> h_sq(ns);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(h_sq.data(), sq, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    scale.assign(2 * (size_t)ns, 1.0);
+    int nz = 0;
+    for (int i = 0; i < ns; ++i)
+      if (h_sq[i] > 0) {
+        scale[i] = 1.0 / std::sqrt(h_sq[i]);
+        scale[ns + i] = std::sqrt(h_sq[i]);
+        ++nz;
+      }
+    rtol = opt.rtol / std::sqrt((double)std::max(nz, 1));
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(sq, scale.data(), sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, st));
+    launch_scale_by_scene(nv, E.b, S.scene_of_vertex.as<int32_t>(), sq, st);
+  }
+  const int iters = E.solve(solver, rtol, opt.max_iters, &rel, &bnorm);
+  if (S.n_scenes > 1)
+    launch_scale_by_scene(nv, E.x, S.scene_of_vertex.as<int32_t>(), S.sceneval.as<double>() + S.n_scenes, st);
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[3], st));
 
   // ---- contractions ----
@@ -645,7 +873,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   }
   raise_flags(S.flags_host);
   if (!std::isfinite(rel)) throw Error{NCPADJ_ERR_NONFINITE, "non-finite residual"};
-  if (!(rel <= opt.rtol * 1.0000001) && bnorm > 0)
+  if (!(rel <= rtol * 1.0000001) && bnorm > 0)
     throw Error{NCPADJ_ERR_NOT_CONVERGED, "Krylov stopped at relative residual " + std::to_string(rel) + " after " +
                                               std::to_string(iters) + " iterations"};
   return NCPADJ_OK;
@@ -832,6 +1060,7 @@ void ncpadj_options_default(ncpadj_options* o) {
   o->precond = NCPADJ_PRECOND_WOODBURY;
   o->solver = NCPADJ_SOLVER_AUTO;
   o->memory = NCPADJ_MEM_DEVICE;
+  o->cap_precision = NCPADJ_FP64;
 }
 
 ncpadj_status ncpadj_ctx_create(int device, ncpadj_ctx* out) {
@@ -867,7 +1096,29 @@ ncpadj_status ncpadj_scene_create(ncpadj_ctx ctx, const ncpadj_scene_desc* desc,
     NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
     s = new ncpadj_scene_s();
     s->ctx = ctx;
-    build_scene(s->s, *desc);
+    build_scene(s->s, desc, 1);
+    *out = s;
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    ncpadj_scene_destroy(s);
+    return fail(e);
+  } catch (const std::exception& e) {
+    ncpadj_scene_destroy(s);
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_scene_desc* descs,
+                                        ncpadj_scene* out) {
+  g_last_error.clear();
+  ncpadj_scene_s* s = nullptr;
+  try {
+    NCPADJ_REQUIRE(ctx && descs && out && n_scenes >= 1, "NULL argument or n_scenes < 1");
+    *out = nullptr;
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    s = new ncpadj_scene_s();
+    s->ctx = ctx;
+    build_scene(s->s, descs, n_scenes);
     *out = s;
     return NCPADJ_OK;
   } catch (const Error& e) {
@@ -883,6 +1134,7 @@ void ncpadj_scene_destroy(ncpadj_scene s) {
   if (!s) return;
   if (s->s.flags_host) cudaFreeHost(s->s.flags_host);
   if (s->s.scal_host) cudaFreeHost(s->s.scal_host);
+  if (s->s.gs_host) cudaFreeHost(s->s.gs_host);
   for (auto& e : s->s.ev)
     if (e) cudaEventDestroy(e);
   delete s;
@@ -899,6 +1151,7 @@ ncpadj_status ncpadj_scene_get_info(ncpadj_scene s, ncpadj_scene_info* out) {
   out->nnz_L = s->s.nnz_L;
   out->nnz_Linv = s->s.nnz_S;
   out->ms_factor = s->s.ms_factor;
+  out->n_scenes = s->s.n_scenes;
   return NCPADJ_OK;
 }
 

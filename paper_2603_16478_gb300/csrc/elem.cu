@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(128) k_tet_assemble(TetArgs A, OutT* bsr) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) c[i][a] = g[a][0] * V[0][i] + g[a][1] * V[1][i] + g[a][2] * V[2][i];
   const T hw = (T)(A.h * A.h) * T(2) * mu * (T)A.vol[t];
+  if (bsr != nullptr) {
   // blocks (a, b), a <= b:  U Q U^T with, in the U basis,
   //   Q_pp = g_a.g_b - W_pp c_p[a] c_p[b] - sum_{j != p} M_pj c_j[a] c_j[b]
   //   Q_pq = -W_pq c_p[a] c_q[b] - N_pq c_q[a] c_p[b]          (p != q)
@@ -306,6 +307,8 @@ __global__ void __launch_bounds__(128) k_tet_assemble(TetArgs A, OutT* bsr) {
       }
     }
   }
+  }
+  if (A.tetdata == nullptr) return;
   // contraction tensors P_mu = U diag(e_mu) V^T, P_lam = U diag(e_lam) V^T with
   // e_mu = 2 h^2 V (mu dtheta/dmu + theta - sigma), e_lam = 2 h^2 V mu dtheta/dlambda
   const double h2v2 = 2.0 * A.h * A.h * A.vol[t];
@@ -624,6 +627,21 @@ __global__ void k_local_contact(ContactArgs A, double* lambda, double* slip, int
   for (int r = 0; r < 3; ++r) atomicAdd(&R[3 * v + r], -h2 * (F[r] * lam_n + F[3 + r] * l1 + F[6 + r] * l2));
 }
 
+__global__ void k_contact_scene(int nc, const int32_t* cv, const int32_t* sov, int32_t* out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) out[c] = sov[cv[c]];
+}
+__global__ void k_scene_sq(int nv, const double* x, const int32_t* sov, double* sq) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double a = x[3 * v], b = x[3 * v + 1], c = x[3 * v + 2];
+  atomicAdd(&sq[sov[v]], a * a + b * b + c * c);
+}
+__global__ void k_scale_by_scene(int nv, double* x, const int32_t* sov, const double* scale) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * nv) x[i] *= scale[sov[i / 3]];
+}
+
 __global__ void k_turn_check(int nc, const double* so, const double* sn, const int* loaded, int* flags) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc || !loaded[c]) return;
@@ -648,8 +666,14 @@ void launch_tet_assemble64(const TetArgs& a, cudaStream_t s) {
   if (a.nt) k_tet_assemble<double, double><<<nblk(a.nt, 128), 128, 0, s>>>(a, a.bsr);
 }
 void launch_tet_assemble32(const TetArgs& a, cudaStream_t s) {
-  g_launches += 1;
-  if (a.nt) k_tet_assemble<float, float><<<nblk(a.nt, 128), 128, 0, s>>>(a, a.bsr32);
+  g_launches += 2;
+  if (!a.nt) return;
+  // FP32 Jacobian blocks; the contraction tensors (theta - sigma, dtheta/dmu, dtheta/dlambda, which lose
+  // about three digits in FP32 at small strain) from an FP64 pass that skips the blocks
+  TetArgs a32 = a;
+  a32.tetdata = nullptr;
+  k_tet_assemble<float, float><<<nblk(a.nt, 128), 128, 0, s>>>(a32, a.bsr32);
+  k_tet_assemble<double, double><<<nblk(a.nt, 128), 128, 0, s>>>(a, (double*)nullptr);
 }
 void launch_contact_blocks(const ContactArgs& a, cudaStream_t s) {
   g_launches += 1;
@@ -692,6 +716,18 @@ void launch_local_contact(const ContactArgs& a, double* lambda, double* slip, in
                           cudaStream_t s) {
   g_launches += 1;
   if (a.nc) k_local_contact<<<nblk(a.nc, 128), 128, 0, s>>>(a, lambda, slip, loaded, R);
+}
+void launch_contact_scene(int nc, const int32_t* cvertex, const int32_t* sov, int32_t* out, cudaStream_t s) {
+  g_launches += 1;
+  if (nc) k_contact_scene<<<nblk(nc, 128), 128, 0, s>>>(nc, cvertex, sov, out);
+}
+void launch_scene_sq(int nv, const double* x, const int32_t* sov, double* sq, cudaStream_t s) {
+  g_launches += 1;
+  k_scene_sq<<<nblk(nv, 256), 256, 0, s>>>(nv, x, sov, sq);
+}
+void launch_scale_by_scene(int nv, double* x, const int32_t* sov, const double* scale, cudaStream_t s) {
+  g_launches += 1;
+  k_scale_by_scene<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, x, sov, scale);
 }
 void launch_turn_check(int nc, const double* slip_old, const double* slip_new, const int* loaded, int* flags,
                        cudaStream_t s) {

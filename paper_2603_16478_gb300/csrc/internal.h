@@ -69,6 +69,10 @@ void factor_elastic(const CsrD& As, const double* xyz, ElasticFactor& out);
 // ------------------------------------------------------------------------------------------
 struct Scene {
   int nv = 0, nt = 0, nb = 0;
+  int n_scenes = 1;                 // meshes in the (batch) scene
+  std::vector<int> voff, toff;      // vertex / tet offsets of each mesh [n_scenes + 1]
+  DevBuf scene_of_vertex;           // int32 [nv]
+  DevBuf sceneval;                  // per-scene scale factors (batch adjoints)
   double h = 0, density = 0;
   // host copies
   std::vector<double> mass;  // [nv]
@@ -87,6 +91,7 @@ struct Scene {
   DevBuf perm, iperm;          // int32 [nv]
   DevBuf S_ptr, S_col, S_val;  // rows of S; S_col holds ORIGINAL vertex ids (gather from x)
   DevBuf St_ptr, St_col, St_val;  // rows of S^T; St_col in position space
+  DevBuf S_val32, St_val32;       // FP32 copies of the values (mixed precision)
   DevBuf S_crow, S_cbeg, S_cend, St_crow, St_cbeg, St_cend;  // row chunks (<= 256 entries)
   int nS_chunks = 0, nSt_chunks = 0;
   int64_t nnz_S = 0;
@@ -107,8 +112,10 @@ struct Scene {
   DevBuf io;                      // staging for host-memory calls
   DevBuf gmres;                   // GMRES basis + Hessenberg
   DevBuf fwd;                     // forward Newton vectors
+  DevBuf vec32;                   // FP32 scratch of the mixed path
   int* flags_host = nullptr;      // pinned
   double* scal_host = nullptr;    // pinned
+  double* gs_host = nullptr;      // pinned: Gram-Schmidt coefficients of one GMRES iteration
   cudaEvent_t ev[8] = {};
 };
 

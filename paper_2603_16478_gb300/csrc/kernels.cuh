@@ -92,6 +92,11 @@ struct ContractArgs {
   double* dL_dmu_contact; // [nc]
 };
 void launch_contractions(const ContractArgs& a, cudaStream_t s);
+// batch scenes: scene id of every contact; per-scene sums of squares of a DOF vector (sq zeroed by
+// the caller); x[i] *= scale[scene_of_vertex[i / 3]]
+void launch_contact_scene(int nc, const int32_t* cvertex, const int32_t* scene_of_vertex, int32_t* out, cudaStream_t s);
+void launch_scene_sq(int nv, const double* x, const int32_t* scene_of_vertex, double* sq, cudaStream_t s);
+void launch_scale_by_scene(int nv, double* x, const int32_t* scene_of_vertex, const double* scale, cudaStream_t s);
 
 // ---- forward step (elem.cu) ----------------------------------------------------------------
 // qt = q_prev + h v_prev + h^2 (g + f_ext / m)
@@ -138,8 +143,11 @@ struct SinvArgs {
   int nS, nSt;
   const int32_t *S_crow, *St_crow;
   const int64_t *S_cbeg, *S_cend, *St_cbeg, *St_cend;
+  const float *S_val32 = nullptr, *St_val32 = nullptr;  // FP32 copies (mixed precision)
 };
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
+// the same with FP32 values and intermediate (x32, w32 [nv][3] float scratch); y accumulated in FP64
+void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s);
 
 // Delassus of the contact vertices: Ds[a][b] = (A_s^{-1})_{v_a v_b}
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
@@ -152,6 +160,11 @@ void launch_cap_form(int nc, const double* Ds, const double* frame, const double
 bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count,
                       cudaStream_t s);
 size_t gj_scratch_bytes(int n, int sm_count);
+// FP32 blocked variant (one grid barrier per panel); tmp is an n x n scratch
+bool launch_gj_invert32(int n, float* C, float* tmp, int32_t* piv, int* flags, int sm_count, cudaStream_t s);
+void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* y, double* ytmp, double* x,
+                       cudaStream_t s);
+void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s);
 // x = C^{-1} y with the swept matrix B and pivot rows: x_k = B[piv_k] . y[piv]
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                      cudaStream_t s);

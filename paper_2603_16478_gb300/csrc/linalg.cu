@@ -22,7 +22,8 @@ namespace {
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -69,30 +70,31 @@ __global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, 
 // lane; partial sums are added atomically into y[3 out(row) + r] (y zeroed by the caller),
 // out(row) = omap ? omap[row] : row.  Splitting the long rows near the elimination-tree root over
 // many warps keeps the product bandwidth- rather than latency-bound.
+template <typename V, typename X, typename Y, typename Acc = Y>
 __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t* __restrict__ crow,
                                                      const int64_t* __restrict__ cbeg, const int64_t* __restrict__ cend,
-                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
-                                                     const int32_t* __restrict__ omap, const double* __restrict__ x,
-                                                     double* __restrict__ y) {
+                                                     const int32_t* __restrict__ col, const V* __restrict__ val,
+                                                     const int32_t* __restrict__ omap, const X* __restrict__ x,
+                                                     Y* __restrict__ y) {
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= nchunks) return;
   const int64_t b = cbeg[k], e = cend[k];
-  double a0 = 0, a1 = 0, a2 = 0;
+  Acc a0 = 0, a1 = 0, a2 = 0;
   int c[8];
-  double s[8];
+  V s[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int64_t p = b + lane + 32 * u;
     c[u] = (p < e) ? col[p] : -1;
-    s[u] = (p < e) ? val[p] : 0.0;
+    s[u] = (p < e) ? val[p] : V(0);
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u)
     if (c[u] >= 0) {
-      a0 += s[u] * x[3 * c[u]];
-      a1 += s[u] * x[3 * c[u] + 1];
-      a2 += s[u] * x[3 * c[u] + 2];
+      a0 += (Acc)s[u] * (Acc)x[3 * c[u]];
+      a1 += (Acc)s[u] * (Acc)x[3 * c[u] + 1];
+      a2 += (Acc)s[u] * (Acc)x[3 * c[u] + 2];
     }
   a0 = warp_sum(a0);
   a1 = warp_sum(a1);
@@ -100,9 +102,9 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
   if (lane == 0) {
     const int row = crow[k];
     const int o = omap ? omap[row] : row;
-    atomicAdd(&y[3 * o], a0);
-    atomicAdd(&y[3 * o + 1], a1);
-    atomicAdd(&y[3 * o + 2], a2);
+    atomicAdd(&y[3 * o], (Y)a0);
+    atomicAdd(&y[3 * o + 1], (Y)a1);
+    atomicAdd(&y[3 * o + 2], (Y)a2);
   }
 }
 
@@ -178,10 +180,11 @@ __device__ bool grid_barrier(int* flags) {
   return *(volatile int*)&flags[FLAG_TIMEOUT] == 0;
 }
 
+template <typename T>
 struct GJScratch {
-  double* cand_val;   // [2][G]  |pivot candidate| (or -1: no unused row)
-  int* cand_row;      // [2][G]
-  double* cand_data;  // [2][G][n]
+  double* cand_val;  // [2][G]  |pivot candidate| (or -1: no unused row)
+  int* cand_row;     // [2][G]
+  T* cand_data;      // [2][G][n]
 };
 
 // Sweep elimination on pivot pairs (r_k, k): rows are owned round-robin by the blocks and kept
@@ -190,17 +193,17 @@ struct GJScratch {
 //   a[r][j] <- a[r][j]/p (j != k), a[r][k] <- 1/p,
 //   a[i][j] <- a[i][j] - a[i][k] a[r][j]/p (j != k), a[i][k] <- -a[i][k]/p  (i != r).
 // After n steps the matrix B satisfies  (C^{-1})[k][r_k'] = B[r_k][k'].  One barrier per step.
-__global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, double* C, int32_t* piv, GJScratch sc, int* flags) {
-  extern __shared__ double sm[];
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, T* C, int32_t* piv, GJScratch<T> sc, int* flags) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int G = gridDim.x, me = blockIdx.x;
-  double* rows = sm;                              // [nloc_max][n]
-  double* prow = sm + (size_t)nloc_max * n;       // [n]
-  double* fl = prow + n;                          // [nloc_max]
+  T* rows = reinterpret_cast<T*>(smraw);          // [nloc_max][n]
+  T* prow = rows + (size_t)nloc_max * n;          // [n]
+  T* fl = prow + n;                               // [nloc_max]
   int* used = (int*)(fl + nloc_max);              // [nloc_max]
   __shared__ double red_v[32];
   __shared__ int red_l[32];
   __shared__ int s_win, s_row;
-  __shared__ double s_piv;
   const int nloc = (me < n) ? (n - me + G - 1) / G : 0;
   for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
     const int l = (int)(e / n), j = (int)(e - (long)l * n);
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, double* C, int
     int bl = -1;
     for (int l = threadIdx.x; l < nloc; l += blockDim.x)
       if (!used[l]) {
-        const double v = fabs(rows[(size_t)l * n + col]);
+        const double v = fabs((double)rows[(size_t)l * n + col]);
         if (v > best) { best = v; bl = l; }
       }
     // block argmax (ties -> lower local index)
@@ -282,17 +285,17 @@ __global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, double* C, int
     const int w = s_win, r = s_row;
     for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(&sc.cand_data[((size_t)buf * G + w) * n + j]);
     __syncthreads();
-    const double inv_p = 1.0 / prow[k];
+    const T inv_p = T(1) / prow[k];
     const int lr = (w == me) ? (r - me) / G : -1;
     // per-row multipliers a[i][k] / p (one FMA per element below)
     for (int l = threadIdx.x; l < nloc; l += blockDim.x) fl[l] = rows[(size_t)l * n + k] * inv_p;
     __syncthreads();
     for (int l = 0; l < nloc; ++l) {
-      double* row = rows + (size_t)l * n;
+      T* row = rows + (size_t)l * n;
       if (l == lr) {
         for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = (j == k) ? inv_p : prow[j] * inv_p;
       } else {
-        const double m = fl[l];
+        const T m = fl[l];
         for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = (j == k) ? -m : fma(-m, prow[j], row[j]);
       }
     }
@@ -310,19 +313,173 @@ __global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, double* C, int
   }
 }
 
+// Blocked Gauss-Jordan (FP32): the same pivot pairs and result as k_gj, one grid barrier per panel of
+// BP columns instead of one per column.  For panel K (pivot rows R, chosen by partial pivoting on the
+// panel columns alone):
+//   P       = the panel columns after the BP scalar sweeps (computed redundantly by every block, with
+//             each thread holding up to ROWS rows of the panel in registers),
+//   M'[:,K] = P,   M'[R,j] = P[R,:] M[R,j],   M'[i,j] = M[i,j] + P[i,:] M[R,j]  (i not in R, j not in K),
+// with the matrix double-buffered in global memory (A <-> B) so that the old pivot rows stay readable.
+template <int BP, int ROWS>
+__global__ void __launch_bounds__(1024) k_gj_blocked(int n, float* A, float* B, int32_t* piv, int* flags) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* P = reinterpret_cast<float*>(smraw);               // [n][BP] panel (for the update phase)
+  float* MR = P + (size_t)n * BP;                            // [BP][n] old pivot rows
+  int* panel_of = reinterpret_cast<int*>(MR + (size_t)BP * n);  // [n]: panel a row was pivoted in, -1 unused
+  __shared__ float wrow[32][BP];
+  __shared__ float wv[32];
+  __shared__ int wi[32];
+  __shared__ float prow[BP];
+  __shared__ int s_r;
+  __shared__ int R[BP];
+  const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n; i += nt) panel_of[i] = -1;
+  __syncthreads();
+  float* Mc = A;
+  float* Mn = B;
+  const int npanels = (n + BP - 1) / BP;
+  bool singular = false;
+  float Pr[ROWS][BP];
+  for (int pi = 0; pi < npanels && !singular; ++pi) {
+    const int k0 = pi * BP, bb = min(BP, n - k0);
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      const int i = tid + k * nt;
+#pragma unroll
+      for (int c = 0; c < BP; ++c) Pr[k][c] = (i < n && c < bb) ? __ldcg(&Mc[(size_t)i * n + k0 + c]) : 0.0f;
+    }
+    for (int jj = 0; jj < bb; ++jj) {
+      // pivot: largest |P[i][jj]| among rows not used yet (ties -> lower row)
+      float bv = -1.0f;
+      int bi = -1;
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        const int i = tid + k * nt;
+        if (i < n && panel_of[i] < 0) {
+          float v = 0.0f;
+#pragma unroll
+          for (int c = 0; c < BP; ++c)
+            if (c == jj) v = fabsf(Pr[k][c]);
+          if (v > bv) { bv = v; bi = i; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (ov > bv || (ov == bv && (bi < 0 || oi < bi)))) { bv = ov; bi = oi; }
+      }
+      // the lane holding the warp's winning row publishes it
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k)
+        if (bi >= 0 && tid + k * nt == bi) {
+#pragma unroll
+          for (int c = 0; c < BP; ++c) wrow[warp][c] = Pr[k][c];
+        }
+      if (lane == 0) { wv[warp] = bv; wi[warp] = bi; }
+      __syncthreads();
+      if (warp == 0) {
+        float v = (lane < (nt >> 5)) ? wv[lane] : -1.0f;
+        int i = (lane < (nt >> 5)) ? wi[lane] : -1;
+        int w = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+          const int ow = __shfl_xor_sync(0xffffffffu, w, o);
+          if (oi >= 0 && (ov > v || (ov == v && (i < 0 || oi < i)))) { v = ov; i = oi; w = ow; }
+        }
+        const bool ok = i >= 0 && v > 0.0f;
+        if (lane < BP) prow[lane] = ok ? wrow[w][lane] : 0.0f;
+        if (lane == 0) {
+          s_r = ok ? i : -1;
+          if (ok) {
+            panel_of[i] = pi;
+            R[jj] = i;
+            if (me == 0) piv[k0 + jj] = i;
+          }
+        }
+      }
+      __syncthreads();
+      const int r = s_r;
+      if (r < 0) {
+        if (tid == 0 && me == 0) atomicExch(&flags[FLAG_SINGULAR], 1);
+        singular = true;
+        break;
+      }
+      const float inv_p = 1.0f / prow[jj];
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        const int i = tid + k * nt;
+        if (i >= n) continue;
+        if (i == r) {
+#pragma unroll
+          for (int c = 0; c < BP; ++c) Pr[k][c] = (c == jj) ? inv_p : prow[c] * inv_p;
+        } else {
+          float m = 0.0f;
+#pragma unroll
+          for (int c = 0; c < BP; ++c)
+            if (c == jj) m = Pr[k][c] * inv_p;
+#pragma unroll
+          for (int c = 0; c < BP; ++c) Pr[k][c] = (c == jj) ? -m : fmaf(-m, prow[c], Pr[k][c]);
+        }
+      }
+    }
+    if (singular) break;
+    // panel to shared memory, old pivot rows of the panel
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      const int i = tid + k * nt;
+      if (i < n)
+#pragma unroll
+        for (int c = 0; c < BP; ++c) P[(size_t)i * BP + c] = Pr[k][c];
+    }
+    for (long e = tid; e < (long)bb * n; e += nt) {
+      const int t = (int)(e / n), j = (int)(e - (long)t * n);
+      MR[(size_t)t * n + j] = __ldcg(&Mc[(size_t)R[t] * n + j]);
+    }
+    __syncthreads();
+    // update this block's rows
+    for (int i = me; i < n; i += G) {
+      const float* Pi = P + (size_t)i * BP;
+      const bool is_piv = panel_of[i] == pi;
+      for (int j = tid; j < n; j += nt) {
+        float v;
+        if (j >= k0 && j < k0 + bb) {
+          v = Pi[j - k0];
+        } else {
+          float acc = is_piv ? 0.0f : __ldcg(&Mc[(size_t)i * n + j]);
+          for (int t = 0; t < bb; ++t) acc = fmaf(Pi[t], MR[(size_t)t * n + j], acc);
+          v = acc;
+        }
+        Mn[(size_t)i * n + j] = v;
+      }
+    }
+    if (!grid_barrier(flags)) return;
+    float* tmp = Mc;
+    Mc = Mn;
+    Mn = tmp;
+  }
+  if (Mc != A)  // result must end in A
+    for (int i = me; i < n; i += G)
+      for (int j = tid; j < n; j += nt) A[(size_t)i * n + j] = Mc[(size_t)i * n + j];
+}
+
 __global__ void k_gather_perm(int n, const int32_t* piv, const double* y, double* ytmp) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) ytmp[k] = y[piv[k]];
 }
 
-__global__ void k_gemv_rows_perm(int n, const double* __restrict__ B, const int32_t* __restrict__ piv,
+template <typename T>
+__global__ void k_gemv_rows_perm(int n, const T* __restrict__ B, const int32_t* __restrict__ piv,
                                  const double* __restrict__ ytmp, double* __restrict__ x) {
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= n) return;
-  const double* row = B + (size_t)piv[k] * n;
-  double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc += row[j] * ytmp[j];
+  const T* row = B + (size_t)piv[k] * n;
+  T acc = 0;  // FP32 rows accumulate in FP32 (the preconditioner apply of the mixed path)
+  for (int j = lane; j < n; j += 32) acc += row[j] * (T)ytmp[j];
   acc = warp_sum(acc);
   if (lane == 0) x[k] = acc;
 }
@@ -489,13 +646,30 @@ void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const 
   g_launches += 1;
   k_diag_inv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, diag_slot, val, val32, dinv);
 }
+__global__ void k_to_float(int n, const double* __restrict__ x, float* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s) {
+  g_launches += 3;
+  const int n = 3 * a.nv;
+  k_to_float<<<nblk(n, 256), 256, 0, s>>>(n, x, x32);
+  cudaMemsetAsync(w32, 0, sizeof(float) * n, s);
+  k_spmv_chunks<float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend,
+                                                                           a.S_col, a.S_val32, nullptr, x32, w32);
+  cudaMemsetAsync(y, 0, sizeof(double) * n, s);
+  k_spmv_chunks<float, float, double, float><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend,
+                                                                             a.St_col, a.St_val32, a.perm, w32, y);
+}
+
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s) {
   g_launches += 2;
   cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr,
+  k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr,
                                                       x, w);
   cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val,
+  k_spmv_chunks<double, double, double><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val,
                                                        a.perm, w, y);
 }
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
@@ -512,37 +686,79 @@ void launch_cap_form(int nc, const double* Ds, const double* frame, const double
 
 static constexpr int kGJThreads = 1024;
 static int gj_blocks(int n, int sm_count) { return n < sm_count ? n : sm_count; }
-static size_t gj_smem(int n, int G) {
+static size_t gj_smem(int n, int G, size_t es) {
   const int nloc_max = (n + G - 1) / G;
-  return ((size_t)nloc_max * n + n + nloc_max) * sizeof(double) + (size_t)nloc_max * sizeof(int);
+  return ((size_t)nloc_max * n + n + nloc_max) * es + (size_t)nloc_max * sizeof(int) + 16;
 }
 size_t gj_scratch_bytes(int n, int sm_count) {
   const int G = gj_blocks(n, sm_count);
   return (size_t)2 * G * sizeof(double) + (size_t)2 * G * sizeof(int) + (size_t)2 * G * n * sizeof(double) + 256;
 }
-bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count, cudaStream_t s) {
+template <typename T>
+static bool gj_invert(int n, T* C, int32_t* piv, double* scratch, int* flags, int sm_count, cudaStream_t s) {
   g_launches += 1;
   const int G = gj_blocks(n, sm_count);
   const int nloc_max = (n + G - 1) / G;
-  const size_t smem = gj_smem(n, G);
+  const size_t smem = gj_smem(n, G, sizeof(T));
   if (smem > 220 * 1024) return false;
-  if (cudaFuncSetAttribute(k_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+  if (cudaFuncSetAttribute(k_gj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj, kGJThreads, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj<T>, kGJThreads, smem) != cudaSuccess || per_sm < 1)
     return false;
-  GJScratch sc;
+  GJScratch<T> sc;
   sc.cand_val = scratch;
-  sc.cand_data = scratch + 2 * G;
-  sc.cand_row = (int*)(scratch + 2 * G + (size_t)2 * G * n);
+  sc.cand_row = reinterpret_cast<int*>(scratch + 2 * G);
+  sc.cand_data = reinterpret_cast<T*>(scratch + 2 * G + G + 1);  // after 2G doubles and 2G ints
   int nn = n, nl = nloc_max;
   void* args[] = {&nn, &nl, &C, &piv, &sc, &flags};
-  return cudaLaunchCooperativeKernel((void*)k_gj, dim3(G), dim3(kGJThreads), args, smem, s) == cudaSuccess;
+  return cudaLaunchCooperativeKernel((void*)k_gj<T>, dim3(G), dim3(kGJThreads), args, smem, s) == cudaSuccess;
+}
+bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count, cudaStream_t s) {
+  return gj_invert<double>(n, C, piv, scratch, flags, sm_count, s);
+}
+template <int BP, int ROWS>
+static bool gj_blocked(int n, float* C, float* tmp, int32_t* piv, int* flags, int G, cudaStream_t s) {
+  const size_t smem = (size_t)2 * n * BP * sizeof(float) + (size_t)n * sizeof(int) + 64;
+  if (smem > 220 * 1024) return false;
+  if (cudaFuncSetAttribute(k_gj_blocked<BP, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_blocked<BP, ROWS>, kGJThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    return false;
+  int nn = n;
+  void* args[] = {&nn, &C, &tmp, &piv, &flags};
+  return cudaLaunchCooperativeKernel((void*)k_gj_blocked<BP, ROWS>, dim3(G), dim3(kGJThreads), args, smem, s) ==
+         cudaSuccess;
+}
+bool launch_gj_invert32(int n, float* C, float* tmp, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {
+  g_launches += 1;
+  const int G = gj_blocks(n, sm_count);
+  if (n <= kGJThreads && n <= 1600) return gj_blocked<16, 1>(n, C, tmp, piv, flags, G, s);
+  if (n <= 1600) return gj_blocked<16, 2>(n, C, tmp, piv, flags, G, s);
+  if (n <= 2 * kGJThreads) return gj_blocked<8, 2>(n, C, tmp, piv, flags, G, s);
+  // larger systems: the one-column-per-barrier form
+  return gj_invert<float>(n, C, piv, reinterpret_cast<double*>(tmp), flags, sm_count, s);
+}
+__global__ void k_to_float_n(long n, const double* __restrict__ x, float* __restrict__ y) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s) {
+  g_launches += 1;
+  k_to_float_n<<<nblk(n, 256), 256, 0, s>>>(n, x, y);
 }
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                      cudaStream_t s) {
   g_launches += 2;
   k_gather_perm<<<nblk(n, 256), 256, 0, s>>>(n, piv, y, ytmp);
-  k_gemv_rows_perm<<<nblk(32L * n, 256), 256, 0, s>>>(n, B, piv, ytmp, x);
+  k_gemv_rows_perm<double><<<nblk(32L * n, 256), 256, 0, s>>>(n, B, piv, ytmp, x);
+}
+void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* y, double* ytmp, double* x,
+                       cudaStream_t s) {
+  g_launches += 2;
+  k_gather_perm<<<nblk(n, 256), 256, 0, s>>>(n, piv, y, ytmp);
+  k_gemv_rows_perm<float><<<nblk(32L * n, 256), 256, 0, s>>>(n, B, piv, ytmp, x);
 }
 void launch_contact_gather_kt(int nc, const int32_t* cv, const double* frame, const double* cdata, int transpose,
                               const double* u, double* sc, cudaStream_t s) {

@@ -1,0 +1,133 @@
+"""Differentiable rollouts: one implicit step as a ``torch.autograd.Function`` whose backward is the
+analytical adjoint (Sec. 4.1), chained over time with checkpointed forward recomputation.
+
+The gradient flow across steps follows Sec. 4.1: the adjoint of step t turns the seeds dL/dq_t,
+dL/dv_t into dL/dq_{t-1}, dL/dv_{t-1} (propagated to the previous step) and into contributions to
+the parameter gradients (summed over steps).  Every call goes to the C-ABI library; this module
+only detects vertex-plane contacts (a gap test) and moves tensors.
+
+Memory: a step saves only its inputs (q_prev, v_prev) and recomputes its converged state with
+the forward step when the backward pass reaches it.  ``rollout(..., checkpoint_every=k)`` also
+wraps segments of k steps in ``torch.utils.checkpoint`` so that only segment boundaries stay
+resident during the forward pass.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import torch
+from torch.utils.checkpoint import checkpoint
+
+from .binding import Contacts, Scene, adjoint_step, forward_step
+
+
+@dataclass
+class PlaneCollider:
+    """Rigid plane {x : normal . x = offset} with frame rows (normal, t1, t2) and a friction region."""
+    normal: Sequence[float]
+    offset: float
+    t1: Sequence[float]
+    t2: Sequence[float]
+    region: int = 0
+
+
+@dataclass
+class Simulator:
+    """A scene plus the settings of its contact detection and solver."""
+    scene: Scene
+    planes: List[PlaneCollider]
+    candidates: Optional[torch.Tensor] = None  # int64 vertex ids that may touch a plane (None: all)
+    margin: float = 2e-3
+    eps: float = 1e-4
+    gravity: Sequence[float] = (0.0, 0.0, -9.81)
+    n_regions: int = 1
+    precision: str = "fp64"
+    cap_precision: str = "fp64"
+    rtol: float = 1e-8
+    newton_tol: float = 1e-10
+    _frames: dict = field(default_factory=dict)
+
+    def contacts(self, q_prev: torch.Tensor, mu_region: torch.Tensor) -> Optional[Contacts]:
+        """Vertices whose gap at q_prev is below the margin, one contact per (vertex, plane)."""
+        dev = q_prev.device
+        verts = torch.arange(q_prev.shape[0], device=dev) if self.candidates is None else self.candidates.to(dev)
+        vs, frames, dn, regs = [], [], [], []
+        for pl in self.planes:
+            n = torch.tensor(pl.normal, dtype=torch.float64, device=dev)
+            gap = q_prev[verts] @ n - pl.offset
+            sel = verts[gap < self.margin]
+            if sel.numel() == 0:
+                continue
+            fr = torch.stack([n, torch.tensor(pl.t1, dtype=torch.float64, device=dev),
+                              torch.tensor(pl.t2, dtype=torch.float64, device=dev)])
+            vs.append(sel)
+            frames.append(fr.expand(sel.numel(), 3, 3))
+            dn.append(torch.full((sel.numel(),), float(pl.offset), dtype=torch.float64, device=dev))
+            regs.append(torch.full((sel.numel(),), pl.region, dtype=torch.int32, device=dev))
+        if not vs:
+            return None
+        region = torch.cat(regs)
+        return Contacts(torch.cat(vs).to(torch.int32).contiguous(), torch.cat(frames).contiguous(),
+                        torch.cat(dn).contiguous(), mu_region.detach()[region.long()].contiguous(), None,
+                        region.contiguous(), self.n_regions)
+
+    def step(self, q_prev, v_prev, contacts, f_ext=None):
+        return forward_step(self.scene, contacts, q_prev.contiguous(), v_prev.contiguous(), f_ext, self.gravity,
+                            eps=self.eps, newton_tol=self.newton_tol)
+
+
+class StepFn(torch.autograd.Function):
+    """(q_prev, v_prev, E, nu, mu_region, f_ext) -> (q, v) for one implicit step.
+
+    E and nu are scalar tensors equal to the scene's (uniform) material: the scene holds the
+    elastic factor built for them, so the forward pass checks the values and the backward pass
+    returns dL/dE and dL/dnu summed over tets.  mu_region [n_regions] sets every contact's
+    friction coefficient through its region.
+    """
+
+    @staticmethod
+    def forward(ctx, q_prev, v_prev, E, nu, mu_region, f_ext, sim: Simulator):
+        contacts = sim.contacts(q_prev, mu_region)
+        q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext)
+        v = (q - q_prev) / sim.scene.h
+        ctx.sim = sim
+        ctx.has_fext = f_ext is not None
+        # save the inputs only: the converged state is recomputed in backward
+        ctx.save_for_backward(q_prev, v_prev, mu_region, f_ext if f_ext is not None else torch.empty(0))
+        return q, v
+
+    @staticmethod
+    def backward(ctx, gq, gv):
+        sim: Simulator = ctx.sim
+        q_prev, v_prev, mu_region, f_ext = ctx.saved_tensors
+        contacts = sim.contacts(q_prev, mu_region)
+        q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext if ctx.has_fext else None)
+        gq = torch.zeros_like(q) if gq is None else gq.contiguous()
+        gv = torch.zeros_like(q) if gv is None else gv.contiguous()
+        g, _ = adjoint_step(sim.scene, contacts, q, q_prev, lam.contiguous(), gq, gv, eps=sim.eps, rtol=sim.rtol,
+                            precision=sim.precision, cap_precision=sim.cap_precision)
+        d_mu = g["dL_dmu"] if contacts is not None else torch.zeros_like(mu_region)
+        d_f = g["dL_dfext"] if ctx.has_fext else None
+        return (g["dL_dq_prev"], g["dL_dv_prev"], g["dL_dE"].sum(), g["dL_dnu"].sum(), d_mu, d_f, None)
+
+
+def rollout(sim: Simulator, q0, v0, E, nu, mu_region, n_steps: int, checkpoint_every: int = 0, f_ext=None):
+    """Run n_steps differentiable steps; returns (q_T, v_T).  With checkpoint_every = k > 0 the steps
+    are grouped in segments of k under torch.utils.checkpoint (forward recomputed in backward)."""
+    q, v = q0, v0
+
+    def segment(q_, v_, E_, nu_, mu_, k):
+        for _ in range(k):
+            q_, v_ = StepFn.apply(q_, v_, E_, nu_, mu_, f_ext, sim)
+        return q_, v_
+
+    t = 0
+    while t < n_steps:
+        k = min(checkpoint_every, n_steps - t) if checkpoint_every > 0 else 1
+        if checkpoint_every > 0:
+            q, v = checkpoint(segment, q, v, E, nu, mu_region, k, use_reentrant=False)
+        else:
+            q, v = segment(q, v, E, nu, mu_region, 1)
+        t += k
+    return q, v

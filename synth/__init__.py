@@ -252,3 +252,38 @@ def random_seed_vectors(n_verts: int, seed: int = 0, scale: float = 1.0):
     """Seeded dL/dq, dL/dv seeds (float64 [n_v, 3] each)."""
     rng = np.random.default_rng(seed)
     return scale * rng.normal(size=(n_verts, 3)), scale * rng.normal(size=(n_verts, 3))
+
+
+def block_batch(n_blocks: int = 64, seed: int = 0, tets_range=(2000, 50000), cell: float = 0.01,
+                h: float = 1.0 / 60.0, eps: float = 1e-4, margin: float = 2e-3, height_range=(0.0, 0.02),
+                v_sigma: float = 0.05):
+    """Independent Neo-Hookean blocks for the batched adjoint.
+
+    Tet counts log-uniform in ``tets_range``; each block has a x b x c cells of edge ``cell`` with
+    n_cells = round(n_t / 5) and aspect (r_x, r_y, r_z) ~ U(0.5, 2)^3; E log-uniform in [1e4, 1e6],
+    nu ~ U(0.3, 0.48), ground friction mu ~ U(0.1, 1.0), bottom at a height ~ U(0, 2 cm) above its
+    own ground plane z = 0, initial velocity N(0, 0.05^2) per vertex component, h = 1/60.
+    Returns a list of Problems (one per block; loss target = rest positions + N(0, 1e-3^2)).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_blocks):
+        nt = np.exp(rng.uniform(np.log(tets_range[0]), np.log(tets_range[1])))
+        ncell = max(1, int(round(nt / 5)))
+        r = rng.uniform(0.5, 2.0, 3)
+        s = (ncell / np.prod(r)) ** (1.0 / 3.0)
+        a = max(1, int(round(r[0] * s)))
+        b = max(1, int(round(r[1] * s)))
+        c = max(1, int(round(ncell / (a * b))))
+        height = rng.uniform(*height_range)
+        X, tets = hex_tet_mesh(a, b, c, cell, origin=(0.0, 0.0, max(height, 1e-7)))
+        E = np.exp(rng.uniform(np.log(1e4), np.log(1e6)))
+        nu = rng.uniform(0.3, 0.48)
+        mu = rng.uniform(0.1, 1.0)
+        bottom = np.nonzero(np.isclose(X[:, 2], max(height, 1e-7)))[0]
+        scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), 1000.0, h,
+                      np.array([0.0, 0.0, -GRAVITY]), [Plane([0.0, 0.0, 1.0], 0.0, mu, [1.0, 0, 0], [0, 1.0, 0])],
+                      bottom, margin, eps, f"block{a}x{b}x{c}")
+        v0 = rng.normal(0.0, v_sigma, X.shape)
+        out.append(Problem(scene, X.copy(), v0, np.zeros_like(X), X + rng.normal(0.0, 1e-3, X.shape)))
+    return out

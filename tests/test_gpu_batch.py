@@ -1,0 +1,100 @@
+"""The batched adjoint (one call over the disjoint union of several scenes) gives each scene the
+same gradients as its own single-scene adjoint, and the oracle's."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from tests._cases import rel, step_case  # noqa: E402
+from tests.test_gpu_parity import KEYS, T  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2603_16478_gb300 as p
+    return p
+
+
+def _cases():
+    # three scenes with contacts of different kinds + one without contacts
+    return [step_case("cube_drop", 2), step_case("two_tet", 1), step_case("cube_drop", 5), step_case("cube_drop", 0)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_equals_single_scene_adjoints(pkg, precision):
+    ctx = pkg.Context(0)
+    cases = _cases()
+    rng = np.random.default_rng(0)
+    meshes, seeds, refs = [], [], []
+    for pb, st, s, q_prev, v_prev in cases:
+        sc = pb.scene
+        meshes.append((sc.X, sc.tets, sc.E, sc.nu, sc.density))
+        dq = rng.normal(size=s.q.shape) * 10.0 ** rng.uniform(-3, 3)  # scenes with very different seed scales
+        dv = rng.normal(size=s.q.shape) * 1e-3
+        seeds.append((dq, dv))
+        refs.append(st.adjoint(s, q_prev, dq, dv))
+    batch = pkg.Scene.batch(ctx, meshes, cases[0][0].scene.h)
+    off = batch.vertex_offsets
+    vert, frame, dn, mu, region, lam, q, qp, dqs, dvs = [], [], [], [], [], [], [], [], [], []
+    nreg = 0
+    for i, ((pb, st, s, q_prev, v_prev), (dq, dv)) in enumerate(zip(cases, seeds)):
+        ct = st.ct
+        vert.append(ct.vertex + off[i])
+        frame.append(ct.frame)
+        dn.append(ct.d_n)
+        mu.append(ct.mu)
+        region.append(ct.region + nreg)
+        nreg += ct.n_regions
+        lam.append(s.lam_frame(st, q_prev) if ct.n else np.zeros((0, 3)))
+        q.append(s.q)
+        qp.append(q_prev)
+        dqs.append(dq)
+        dvs.append(dv)
+    contacts = pkg.Contacts(T(np.concatenate(vert), torch.int32), T(np.concatenate(frame)), T(np.concatenate(dn)),
+                            T(np.concatenate(mu)), None, T(np.concatenate(region), torch.int32), nreg)
+    g, stats = pkg.adjoint_step(batch, contacts, T(np.concatenate(q)), T(np.concatenate(qp)), T(np.concatenate(lam)),
+                                T(np.concatenate(dqs)), T(np.concatenate(dvs)), eps=cases[0][0].scene.eps,
+                                rtol=1e-12 if precision == "fp64" else 1e-8, precision=precision,
+                                cap_precision=precision)
+    torch.cuda.synchronize()
+    tol = 1e-8 if precision == "fp64" else 1e-3
+    toff = batch.tet_offsets
+    c0 = 0
+    r0 = 0
+    for i, ((pb, st, s, q_prev, v_prev), ref) in enumerate(zip(cases, refs)):
+        sl_v = slice(off[i], off[i + 1])
+        for k in ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "z"):
+            assert rel(g[k][sl_v].cpu().numpy(), ref[k]) <= tol, (i, k)
+        for k in ("dL_dE", "dL_dnu"):
+            assert rel(g[k][toff[i]:toff[i + 1]].cpu().numpy(), ref[k]) <= tol, (i, k)
+        nci = st.ct.n
+        if nci:
+            assert rel(g["dL_dmu_contact"][c0:c0 + nci].cpu().numpy(), ref["dL_dmu_contact"]) <= tol, (i, "mu_c")
+            assert rel(g["dL_dmu"][r0:r0 + st.ct.n_regions].cpu().numpy(), ref["dL_dmu_region"]) <= tol, (i, "mu")
+        c0 += nci
+        r0 += st.ct.n_regions
+
+
+def test_batch_rejects_ungrouped_contacts(pkg):
+    ctx = pkg.Context(0)
+    cases = _cases()[:2]
+    batch = pkg.Scene.batch(ctx, [(c[0].scene.X, c[0].scene.tets, c[0].scene.E, c[0].scene.nu, c[0].scene.density)
+                                  for c in cases], cases[0][0].scene.h)
+    off = batch.vertex_offsets
+    (pa, sa, xa, qa, _), (pb_, sb, xb, qb, _) = cases
+    vert = np.concatenate([sb.ct.vertex + off[1], sa.ct.vertex + off[0]])  # scene 1 before scene 0
+    frame = np.concatenate([sb.ct.frame, sa.ct.frame])
+    n = len(vert)
+    contacts = pkg.Contacts(T(vert, torch.int32), T(frame), T(np.zeros(n)), T(np.full(n, 0.5)), None,
+                            T(np.zeros(n), torch.int32), 1)
+    q = T(np.concatenate([xa.q, xb.q]))
+    lam = T(np.concatenate([xb.lam_frame(sb, qb), xa.lam_frame(sa, qa)]))
+    with pytest.raises(pkg.NcpadjError, match="grouped by scene"):
+        pkg.adjoint_step(batch, contacts, q, T(np.concatenate([qa, qb])), lam, torch.ones_like(q), None)
