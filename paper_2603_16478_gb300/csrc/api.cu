@@ -345,10 +345,11 @@ struct Engine {
       blk_c0.push_back(0);
       blk_nc.push_back(nc);
     } else {
-      S.io.ensure(sizeof(int32_t) * (size_t)nc + 64);
-      launch_contact_scene(nc, in.cvertex, S.scene_of_vertex.as<int32_t>(), S.io.as<int32_t>(), st);
+      S.cscene.ensure(sizeof(int32_t) * (size_t)nc + 64);
+      launch_contact_scene(nc, in.cvertex, S.scene_of_vertex.as<int32_t>(), S.cscene.as<int32_t>(), st);
       std::vector<int32_t> cs(nc);
-      NCPADJ_CUDA_TRY(cudaMemcpyAsync(cs.data(), S.io.as<int32_t>(), sizeof(int32_t) * nc, cudaMemcpyDeviceToHost, st));
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(cs.data(), S.cscene.as<int32_t>(), sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
+                                      st));
       NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
       for (int c = 0; c < nc; ++c) {
         NCPADJ_REQUIRE(c == 0 || cs[c] >= cs[c - 1], "contacts of a batch scene must be grouped by scene");
@@ -400,7 +401,10 @@ struct Engine {
     const size_t nvec = 9, ncv = 3 * (size_t)std::max(ncap, 1);
     S.vecs.ensure(sizeof(double) * (nvec * N + ncv + 64));
     S.gmres.ensure(sizeof(double) * ((size_t)(m + 1) * N + 3 * (size_t)(m + 1) + 16));
-    S.red.ensure(sizeof(double) * (64 * (size_t)(m + 2) + 64));
+    if (S.red.bytes < dot_scratch_bytes()) {  // counters of the fused dot product start at zero
+      S.red.ensure(dot_scratch_bytes());
+      NCPADJ_CUDA_TRY(cudaMemset(S.red.p, 0, dot_scratch_bytes()));
+    }
     S.scal.ensure(sizeof(double) * (64 + (size_t)m + 8));
     if (nc && precond == NCPADJ_PRECOND_WOODBURY) {
       S.cap.ensure(sizeof(double) * (cap_elems + ds_elems + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
@@ -762,11 +766,11 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   const int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
   E.mixed = opt.precision == NCPADJ_MIXED;
   E.cap_fp32 = E.mixed && opt.cap_precision == NCPADJ_MIXED;
-  E.workspace(nc, opt.gmres_restart, opt.precond);
-  E.transpose = 1;
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
-  check_contacts(S, nc, in.cvertex, in.region, nreg, st);
+  check_contacts(S, nc, in.cvertex, in.region, nreg, st);  // before anything indexes with the ids
+  E.workspace(nc, opt.gmres_restart, opt.precond);
+  E.transpose = 1;
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[0], st));
   E.assemble(in.q, in.q_prev, in.lambda, opt.eps);
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[1], st));
@@ -909,11 +913,11 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   E.in.region = nc ? ct->region : nullptr;
   E.in.q_prev = fin->q_prev;
   const int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
-  E.workspace(nc, opt.gmres_restart, opt.precond);
-  E.transpose = 0;
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
-  check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);
+  check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);  // before any indexing
+  E.workspace(nc, opt.gmres_restart, opt.precond);
+  E.transpose = 0;
   S.fwd.ensure(sizeof(double) * (4 * (size_t)N + 3 * (size_t)std::max(nc, 1) + 4 * (size_t)std::max(nc, 1)) +
                sizeof(int) * std::max(nc, 1) + 64);
   double* qt = S.fwd.as<double>();  // inertial prediction

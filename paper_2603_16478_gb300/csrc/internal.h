@@ -73,6 +73,7 @@ struct Scene {
   std::vector<int> voff, toff;      // vertex / tet offsets of each mesh [n_scenes + 1]
   DevBuf scene_of_vertex;           // int32 [nv]
   DevBuf sceneval;                  // per-scene scale factors (batch adjoints)
+  DevBuf cscene;                    // int32 [nc]: mesh of each contact (batch scenes)
   double h = 0, density = 0;
   // host copies
   std::vector<double> mass;  // [nv]
