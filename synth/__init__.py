@@ -248,6 +248,15 @@ def random_deformation_gradients(n: int, seed: int = 0, strain: float = 0.05) ->
     return Q @ (np.eye(3) + S)
 
 
+def random_actuation(n_tets: int, seed: int = 0, scale: float = 1e3):
+    """Per-tet activations a ~ N(0, scale^2) Pa (float32, [n_t]) and unit fibre directions d_i
+    uniform on the sphere (float64, [n_t, 3]), both seeded."""
+    rng = np.random.default_rng(seed)
+    act = (scale * rng.standard_normal(n_tets)).astype(np.float32)
+    d = rng.standard_normal((n_tets, 3))
+    return act, d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
 def random_seed_vectors(n_verts: int, seed: int = 0, scale: float = 1.0):
     """Seeded dL/dq, dL/dv seeds (float64 [n_v, 3] each)."""
     rng = np.random.default_rng(seed)

@@ -383,3 +383,73 @@ def test_whole_step_gradient_matches_central_differences(k):
         d /= np.linalg.norm(d)
         fd = cd(lambda e: L(**{arg: e * d}), 1e-6 * scale)
         assert rel(np.sum(g[key] * d), fd) < 1e-4, key
+
+
+# ---- per-tet actuation (constant active stress a_i d_i d_i^T) ---------------------------------
+
+def _face_normal_forces(X, tet, P):
+    """Nodal forces of a constant first Piola stress on one tet from its faces: vertex a gets
+    P (A_a n_a) / 3, with A_a n_a the outward area vector of the face opposite a."""
+    out = np.zeros((4, 3))
+    for a in range(4):
+        b, c, d = [tet[k] for k in range(4) if k != a]
+        av = 0.5 * np.cross(X[c] - X[b], X[d] - X[b])
+        if av @ (X[tet[a]] - X[b]) > 0:
+            av = -av
+        out[a] = P @ av / 3.0
+    return out
+
+
+def test_stress_force_matches_face_area_vectors():
+    from oracle.actuation import stress_force
+    from oracle.model import Mesh
+    rng = np.random.default_rng(21)
+    X = rng.normal(size=(4, 3))
+    tet = np.array([0, 1, 2, 3])
+    if np.linalg.det(np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]], axis=1)) < 0:
+        tet = np.array([0, 2, 1, 3])
+    P = rng.normal(size=(3, 3))  # not symmetric: a transposed operand shows
+    f = stress_force(Mesh(X, tet[None]), P[None])
+    ref = _face_normal_forces(X, tet, P)
+    assert np.abs(f[tet] - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_actuation_force_has_no_net_force_or_torque_at_rest():
+    from oracle.actuation import actuation_force
+    from oracle.model import Mesh
+    X, tets = synth.hex_tet_mesh(3, 2, 2, 0.01)
+    act, fibre = synth.random_actuation(len(tets), seed=3)
+    f = actuation_force(Mesh(X, tets), act, fibre)
+    scale = np.abs(f).max()
+    assert scale > 0
+    assert np.abs(f.sum(axis=0)).max() < 1e-12 * scale * len(X)
+    assert np.abs(np.cross(X, f).sum(axis=0)).max() < 1e-12 * scale * len(X) * np.abs(X).max()
+
+
+def test_actuation_gradient_matches_central_differences():
+    """dL/da through the whole oracle step (contacts and frames frozen), directional check."""
+    from oracle.actuation import actuation_force, actuation_gradient
+    pb, st, base, q_prev, v_prev = step_case("cube_drop", 2)
+    sc = pb.scene
+    qt = pb.q_target
+    act, fibre = synth.random_actuation(st.mesh.n_tets, seed=5)
+    act = act.astype(float)
+
+    def solve(a):
+        r = st.forward(q_prev, v_prev, f_ctrl=actuation_force(st.mesh, a, fibre), q_init=base.q)
+        assert r.residual < 1e-8
+        return r
+
+    s0 = solve(act)
+    g = st.adjoint(s0, q_prev, 2 * (s0.q - qt), np.zeros_like(qt))
+    ga = actuation_gradient(st.mesh, g["z"], fibre, sc.h)
+    # the chain through f_ext: dL/da = (dL/df_ext) . df_act/da
+    e = np.zeros(st.mesh.n_tets)
+    e[7] = 1.0
+    assert abs(ga[7] - np.sum(g["dL_dfext"] * actuation_force(st.mesh, e, fibre))) < 1e-12 * np.abs(ga).max()
+    rng = np.random.default_rng(22)
+    d = rng.normal(size=act.shape)
+    d /= np.linalg.norm(d)
+    eta = 1e-6 * np.abs(act).max()
+    fd = (np.sum((solve(act + eta * d).q - qt) ** 2) - np.sum((solve(act - eta * d).q - qt) ** 2)) / (2 * eta)
+    assert rel(ga @ d, fd) < 1e-5
