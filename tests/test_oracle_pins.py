@@ -453,3 +453,57 @@ def test_actuation_gradient_matches_central_differences():
     eta = 1e-6 * np.abs(act).max()
     fd = (np.sum((solve(act + eta * d).q - qt) ** 2) - np.sum((solve(act - eta * d).q - qt) ** 2)) / (2 * eta)
     assert rel(ga @ d, fd) < 1e-5
+
+
+# ---- eps -> 0 limit: the smoothed step tends to the equality-constrained (bilateral) step ----------
+
+def test_resting_frictionless_contacts_converge_to_the_bilateral_kkt_gradient():
+    """As eps -> 0 a resting frictionless contact enforces delta_n = 0: state, multipliers and
+    adjoint solution z tend to those of the KKT system of the constrained step (dense LU), at
+    the O(eps^2) rate of lambda_n = eps^2 / delta_n."""
+    from oracle.bilateral import constrained_adjoint, constrained_step
+    pb = synth.cube_drop(cells=2, drop=1e-4, v_sigma=0.0, mu=0.0)
+    sc = pb.scene
+    q_prev, v_prev = pb.q0.copy(), pb.v0.copy()
+    ct = sc.contacts(q_prev)
+    assert ct.n == 9
+    seed = np.random.default_rng(3).normal(size=q_prev.shape)
+    runs = []
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5):
+        st = make_step(sc, ct, eps=eps)
+        s = st.forward(q_prev, v_prev)
+        assert s.residual < 1e-10 and np.all(s.lam_n > 0)
+        runs.append((s, st.adjoint(s, q_prev, seed, np.zeros_like(seed))["z"]))
+    q_star, lam_star = constrained_step(st, q_prev, v_prev, runs[-1][0].q)
+    assert np.all(lam_star > 0)
+    z_star = constrained_adjoint(st, q_star, q_prev, seed)
+    ez = [rel(z, z_star) for _, z in runs]
+    eq = [rel(s.q - q_prev, q_star - q_prev) for s, _ in runs]
+    el = [rel(s.lam_n, lam_star) for s, _ in runs]
+    for e in (ez, eq, el):
+        assert all(e[i + 1] < e[i] / 30 for i in range(len(e) - 1)), e
+    assert ez[-1] < 1e-6 and eq[-1] < 1e-6 and el[-1] < 1e-6
+
+
+def test_separating_contacts_converge_to_the_contact_free_gradient():
+    """Contacts that open during the step carry lambda_n = eps^2/delta_n -> 0 and a tangential
+    stiffness ~ eps^2/||delta_f||^2 (both FB arguments are small): the adjoint solution tends to
+    that of the same step without contacts, at the O(eps^2) rate."""
+    from oracle.bilateral import _free
+    pb = synth.cube_drop(cells=2, drop=1e-3, v_sigma=0.0, mu=0.3)
+    sc = pb.scene
+    q_prev = pb.q0.copy()
+    v_prev = np.tile([0.3, 0.0, 0.5], (len(q_prev), 1))  # moving up and sideways: every gap opens
+    ct = sc.contacts(q_prev)
+    assert ct.n == 9
+    seed = np.random.default_rng(4).normal(size=q_prev.shape)
+    free = _free(make_step(sc, ct))
+    s0 = free.forward(q_prev, v_prev)
+    z0 = free.adjoint(s0, q_prev, seed, np.zeros_like(seed))["z"]
+    errs = []
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5):
+        st = make_step(sc, ct, eps=eps)
+        s = st.forward(q_prev, v_prev)
+        assert s.residual < 1e-10
+        errs.append(rel(st.adjoint(s, q_prev, seed, np.zeros_like(seed))["z"], z0))
+    assert all(errs[i + 1] < errs[i] / 30 for i in range(len(errs) - 1)) and errs[-1] < 1e-7, errs
