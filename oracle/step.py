@@ -125,9 +125,15 @@ class Step:
 
     def start_point(self, q_prev, qt, seed=0):
         """The inertial prediction (its slips point along the free motion), with every contact
-        vertex lifted along its normal to a small positive gap."""
+        vertex lifted along its normal to a small positive gap.  If the prediction inverts a tet
+        (large forces on light vertices), it is pulled back towards q_prev by halving
+        q_prev + t (qt - q_prev) until no tet is inverted."""
         rng = np.random.default_rng(seed)
         q = qt.copy()
+        t = 1.0
+        while np.linalg.det(self.mesh.F(q)).min() <= 0 and t > 1e-12:
+            t *= 0.5
+            q = q_prev + t * (qt - q_prev)
         gap0 = 10.0 * self.eps * self.eps / (np.max(self.mass) * np.linalg.norm(self.gravity) + 1e-300)
         for c in range(self.nc):
             v = self.ct.vertex[c]

@@ -507,3 +507,49 @@ def test_separating_contacts_converge_to_the_contact_free_gradient():
         assert s.residual < 1e-10
         errs.append(rel(st.adjoint(s, q_prev, seed, np.zeros_like(seed))["z"], z0))
     assert all(errs[i + 1] < errs[i] / 30 for i in range(len(errs) - 1)) and errs[-1] < 1e-7, errs
+
+
+# ---- continuity of dL/dmu through the slip threshold ----------------------------------------
+
+def test_friction_gradient_is_continuous_through_the_stick_slip_threshold():
+    """A block sliding down the 20 degree incline (5 cm/s) is stopped within the step once
+    mu exceeds ~0.91.  Sweeping mu across that threshold, the adjoint dL/dmu must equal the
+    central difference of L(mu) at every sample (sliding, transition and sticking alike), and
+    its integral must reproduce the change of L: a jump or a wrong value in the transition fails
+    one of the two."""
+    pb = synth.beam_incline(nx=4, ny=2, nz=2)
+    sc = pb.scene
+    q_prev = pb.q0.copy()
+    t1 = sc.planes[0].frame[1]                      # up the slope
+    v_prev = np.tile(-0.05 * t1, (len(q_prev), 1))  # sliding down
+    ct = sc.contacts(q_prev)
+    st = make_step(sc, ct)
+    com_t = q_prev.mean(axis=0) + np.array([0.001, 0.0, 0.0])
+
+    def run(mu, grad=True):
+        mu_c = np.full(ct.n, mu)
+        s = st.forward(q_prev, v_prev, mu_c=mu_c)
+        assert s.residual < 1e-10
+        com = s.q.mean(axis=0)
+        L = np.sum((com - com_t) ** 2)
+        if not grad:
+            return L
+        seed = np.tile(2 * (com - com_t) / len(s.q), (len(s.q), 1))
+        g = st.adjoint(s, q_prev, seed, np.zeros_like(seed), mu_c=mu_c)["dL_dmu_region"][0]
+        slip = min(np.linalg.norm(st.delta(s.q, q_prev, c)[1:]) for c in range(ct.n))
+        return L, g, slip
+
+    mus = np.linspace(0.84, 0.98, 15)
+    res = [run(m) for m in mus]
+    Ls = np.array([r[0] for r in res])
+    gs = np.array([r[1] for r in res])
+    slips = np.array([r[2] for r in res])
+    assert slips[0] > 10 * slips[-1]          # sliding at the start of the sweep, sticking at its end
+    assert abs(gs[0]) > 5 * abs(gs[-1])       # and the friction gradient changes regime with it
+    for m, g in zip(mus[::3], gs[::3]):
+        eta = 1e-6
+        fd = (run(m + eta, False) - run(m - eta, False)) / (2 * eta)
+        assert abs(g - fd) <= 1e-5 * abs(g), (m, g, fd)
+    # trapezoid integral of dL/dmu against L(mu_end) - L(mu_start)
+    integral = np.sum(0.5 * (gs[1:] + gs[:-1]) * np.diff(mus))
+    assert abs(integral - (Ls[-1] - Ls[0])) <= 5e-3 * abs(Ls[-1] - Ls[0])
