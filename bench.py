@@ -199,6 +199,73 @@ def batched(pkg, torch, dev, steps, warmup):
             "scene_build_s": t_build, "nnz_Linv": info["nnz_Linv"], "forward_newton_iters": fs["newton_iters"]}
 
 
+def sphere(pkg, torch, dev, steps, warmup):
+    """The large contact-heavy scene at full size: ball (r = 0.1 m, ~32k vertices, ~211k tets) pressed
+    between the ground and a kinematic plate, ~2,300 frictional contacts in 32 friction regions.
+    One GPU forward step gives the state; the adjoint is timed in FP64 and mixed precision, and
+    the Krylov iterations of Woodbury, Jacobi and no preconditioner are compared (capped at 5000)."""
+    import synth
+    pb = synth.sphere_press()
+    sc = pb.scene
+    ctx = pkg.Context(dev.index or 0)
+    t0 = time.perf_counter()
+    scene = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+    t_build = time.perf_counter() - t0
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    ct = sc.contacts(pb.q0)
+    contacts = pkg.Contacts(T(ct.vertex, torch.int32), T(ct.frame), T(ct.d_n), T(ct.mu), None,
+                            T(ct.region, torch.int32), ct.n_regions)
+    q0, v0 = T(pb.q0), T(pb.v0)
+    t0 = time.perf_counter()
+    q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(sc.gravity), eps=sc.eps, max_newton=100)
+    t_fwd = time.perf_counter() - t0
+    dq = 2 * (q - T(pb.q_target))
+    lam = lam.contiguous()
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out, grads = {}, {}
+    for prec in ("fp64", "mixed"):
+        kw = dict(eps=sc.eps, precision=prec, cap_precision="mixed", stream=stream.cuda_stream,
+                  want=("dL_dfext", "dL_dmu", "z"))
+        for _ in range(warmup):
+            pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, **kw)
+        ms, sts = [], []
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g, st = pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+                sts.append(st)
+        out[prec] = {"gradients_per_s": steps / (sum(ms) / 1e3), "ms_per_call": sum(ms) / steps,
+                     "krylov_iterations": statistics.median(x["iterations"] for x in sts),
+                     "capacitance_blocks": sts[-1]["capacitance_blocks"],
+                     "stage_ms": {k: statistics.mean(x[k] for x in sts) for k in
+                                  ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract", "ms_cap_inverse")}}
+        grads[prec] = {k: v.clone() for k, v in g.items()}
+    err = max(float((torch.linalg.norm(grads["mixed"][k] - grads["fp64"][k]) /
+                     torch.linalg.norm(grads["fp64"][k]).clamp_min(1e-300)).item()) for k in grads["fp64"])
+    iters = {}
+    for pc in ("woodbury", "jacobi", "none"):
+        try:
+            _, st = pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, eps=sc.eps, precision="mixed",
+                                     cap_precision="mixed", precond=pc, max_iters=5000, want=("z",))
+            iters[pc] = st["iterations"]
+        except pkg.NcpadjError as e:
+            iters[pc] = "not converged in 5000" if "NOT_CONVERGED" in str(e) else str(e)[:120]
+    info = scene.info()
+    return {"workload": f"ball r=0.1 m flattened at |z|<=5 cm, {sc.n_verts} verts / {sc.n_tets} tets, "
+                        f"{ct.n} frictional contacts (ground + plate pressing 0.5 mm), {ct.n_regions} friction "
+                        "regions, h=1/60, E=1e5, nu=0.4",
+            "fp64": out["fp64"], "mixed": out["mixed"], "max_rel_err_mixed_vs_fp64": err,
+            "krylov_iterations_by_preconditioner": iters, "scene_build_s": t_build, "forward_s": t_fwd,
+            "forward_newton_iters": fs["newton_iters"], "forward_residual": fs["residual"],
+            "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "factor_ms": info["ms_factor"]}
+
+
 # --------------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------------
@@ -212,6 +279,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-block measurement")
+    ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -383,6 +451,13 @@ def main():
         except Exception as e:  # noqa: BLE001
             batch_res = {"error": str(e)[:300]}
 
+    sphere_res = None
+    if args.sphere:
+        try:
+            sphere_res = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)
+        except Exception as e:  # noqa: BLE001
+            sphere_res = {"error": str(e)[:300]}
+
     # ---- CPU baseline: the oracle, one thread, bounded sample ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -411,7 +486,8 @@ def main():
                                                        "ms_cap_inverse")},
                        "forward_newton_iters": [f["newton_iters"] for f in fwd_stats],
                        "forward_residual": [f["residual"] for f in fwd_stats],
-                       "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "batched": batch_res},
+                       "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "batched": batch_res,
+                       **({"sphere": sphere_res} if sphere_res is not None else {})},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "gradients/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches * args.steps, "clocks": clk,

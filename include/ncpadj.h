@@ -166,7 +166,9 @@ typedef struct {
  *   dL_dq_prev, dL_dv_prev, dL_dfext, z  [n_verts*3]
  *   dL_dE, dL_dnu                        [n_tets]   (per-tet material parameters)
  *   dL_dmu                               [n_regions] (friction coefficient per region)
- *   dL_dmu_contact                       [n_c]       (per contact) */
+ *   dL_dmu_contact                       [n_c]       (per contact)
+ *   dL_dact                              [n_tets]    (FP32; per-tet activation, see
+ *                                                     ncpadj_scene_set_fibres) */
 typedef struct {
   double* dL_dq_prev;
   double* dL_dv_prev;
@@ -176,6 +178,7 @@ typedef struct {
   double* dL_dmu;
   double* dL_dmu_contact;
   double* z;
+  float* dL_dact;  /* [n_tets] activation gradient; requires the scene's fibres (see below) */
 } ncpadj_grads;
 
 /* Solver options; fill with ncpadj_options_default first.
@@ -188,13 +191,23 @@ typedef struct {
  *              Gram-Schmidt and Hessenberg; contact blocks always from FP64 state.
  *   precond    NCPADJ_PRECOND_* (default WOODBURY); solver NCPADJ_SOLVER_* (default AUTO:
  *              CG when every mu is 0, else GMRES, Sec. 4.4); memory NCPADJ_MEM_*.
- *   cap_precision  factorisation of the contact capacitance: NCPADJ_FP64 (default) or, with
- *              precision MIXED only, NCPADJ_MIXED (factorised in FP32). */
+ *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default) or
+ *              NCPADJ_MIXED (inverted and applied in FP32; it only preconditions, so the result
+ *              keeps the solve's precision and tolerance).
+ *   cap_block  most contacts per directly inverted capacitance block (0 = default = 1365, the
+ *              most the direct inverse takes; larger values are clamped to it).  A scene with
+ *              more contacts has its capacitance solved iteratively (Sec. 4.4): its full dense
+ *              capacitance (FP32) is applied by an inner right-preconditioned GMRES to relative
+ *              residual 1e-6, preconditioned by the exact inverses of contiguous, nearly equal
+ *              groups of its contacts in the given order, and the outer solve becomes flexible
+ *              GMRES (the preconditioner varies).  Order the contacts spatially (e.g. by plane,
+ *              then by position) so that groups are compact. */
 typedef struct {
   double eps, rtol;
   int32_t max_iters, gmres_restart;
   int32_t precision, precond, solver, memory;
   int32_t cap_precision;
+  int32_t cap_block;
 } ncpadj_options;
 void ncpadj_options_default(ncpadj_options* opt);
 
@@ -208,6 +221,8 @@ typedef struct {
   float ms_total, ms_assemble, ms_setup, ms_krylov, ms_contract;
   float ms_cap_inverse;     /* the capacitance inversion kernel alone (0 if not run) */
   int64_t kernel_launches;  /* kernels this call enqueued */
+  int32_t capacitance_blocks;  /* capacitance blocks inverted directly (0 if none) */
+  int32_t inner_iterations;    /* iterations of the inner capacitance solves (0 if none) */
 } ncpadj_stats;
 
 /* One adjoint step: assemble script_A^T at the given converged state, solve for z and
@@ -224,6 +239,29 @@ ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpa
  * x, y: device arrays [n_verts*3] (not aliased).  Uses the scene's workspace (allocated on first
  * use).  Errors: INVALID_ARG, OOM, CUDA. */
 ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y, void* stream);
+
+/* Per-tet actuation (the paper's muscle-driven soft robots describe their actuators only in words;
+ * this is the reading used here): tet i carries an activation a_i (Pa, FP32) and a fixed unit fibre
+ * direction d_i in the rest frame, adding the constant first Piola stress a_i d_i d_i^T.  Its nodal
+ * force f_act = - sum_i V_i G_i^T vec(a_i d_i d_i^T) does not depend on q, so it joins f_ext in the
+ * forward step (ncpadj_forward_input.act) and leaves the adjoint matrix unchanged; the adjoint
+ * returns dL/da_i = h^2 z^T df_act/da_i = -h^2 V_i d_i^T Z_i d_i with Z_i = unvec(G_i z)
+ * (ncpadj_grads.dL_dact).
+ * fibre: HOST array [n_tets*3] of unit vectors (copied; replaces earlier fibres of the scene).
+ * Errors: INVALID_ARG (NULL, or a fibre whose length is not 1 within 1e-6), OOM, CUDA. */
+ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre);
+
+/* Cinv = C^{-1} for a dense row-major n x n matrix, by the blocked Gauss-Jordan elimination with
+ * partial pivoting that inverts the contact capacitance I + h^2 K D of the Woodbury
+ * preconditioner (Sec. 4.4); exposed so that the inversion can be used and checked on its own.
+ * C, Cinv: device arrays [n*n] (not aliased; C is not modified).  precision NCPADJ_FP64 computes
+ * in FP64; NCPADJ_MIXED rounds C to FP32 and computes in FP32 (the result is returned as double).
+ * 1 <= n <= 4096.  Synchronises the stream (it reads the pivot status).  Uses workspace owned by
+ * the context (allocated on first use, grown as needed).
+ * Errors: INVALID_ARG, NONFINITE (a zero pivot: C is singular in the working precision),
+ * TIMEOUT, UNSUPPORTED (the cooperative launch was refused), OOM, CUDA. */
+ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, double* Cinv, int32_t precision,
+                                   void* stream);
 
 /* Variant of ncpadj_elastic_solve that allocates nothing (the paper has no counterpart).
  * For callers that cannot have device memory allocated while they run -- programs whose device
@@ -259,6 +297,7 @@ typedef struct {
   const double* v_prev;
   const double* f_ext;
   double gravity[3];
+  const float* act;  /* [n_tets] activations (Pa) or NULL; requires the scene's fibres */
 } ncpadj_forward_input;
 
 typedef struct {

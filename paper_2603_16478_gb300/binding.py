@@ -65,27 +65,29 @@ class _Seed(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("dL_dq_prev", C.c_void_p), ("dL_dv_prev", C.c_void_p), ("dL_dfext", C.c_void_p),
                 ("dL_dE", C.c_void_p), ("dL_dnu", C.c_void_p), ("dL_dmu", C.c_void_p),
-                ("dL_dmu_contact", C.c_void_p), ("z", C.c_void_p)]
+                ("dL_dmu_contact", C.c_void_p), ("z", C.c_void_p), ("dL_dact", C.c_void_p)]
 
 
 class _Options(C.Structure):
     _fields_ = [("eps", C.c_double), ("rtol", C.c_double), ("max_iters", C.c_int32), ("gmres_restart", C.c_int32),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("solver", C.c_int32), ("memory", C.c_int32),
-                ("cap_precision", C.c_int32)]
+                ("cap_precision", C.c_int32), ("cap_block", C.c_int32)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("solver_used", C.c_int32), ("n_contacts", C.c_int32),
                 ("capacitance_dim", C.c_int32), ("rel_residual", C.c_double), ("ms_total", C.c_float),
                 ("ms_assemble", C.c_float), ("ms_setup", C.c_float), ("ms_krylov", C.c_float),
-                ("ms_contract", C.c_float), ("ms_cap_inverse", C.c_float), ("kernel_launches", C.c_int64)]
+                ("ms_contract", C.c_float), ("ms_cap_inverse", C.c_float), ("kernel_launches", C.c_int64),
+                ("capacitance_blocks", C.c_int32), ("inner_iterations", C.c_int32)]
 
     def to_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class _ForwardInput(C.Structure):
-    _fields_ = [("q_prev", C.c_void_p), ("v_prev", C.c_void_p), ("f_ext", C.c_void_p), ("gravity", C.c_double * 3)]
+    _fields_ = [("q_prev", C.c_void_p), ("v_prev", C.c_void_p), ("f_ext", C.c_void_p), ("gravity", C.c_double * 3),
+                ("act", C.c_void_p)]
 
 
 class _ForwardStats(C.Structure):
@@ -99,7 +101,8 @@ class _ForwardStats(C.Structure):
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
            "ncpadj_options_default",
-           "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc"]
+           "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc",
+           "ncpadj_dense_inverse", "ncpadj_scene_set_fibres"]
 
 
 def load_library(path: Optional[str] = None):
@@ -131,6 +134,8 @@ def load_library(path: Optional[str] = None):
                                         C.POINTER(_ForwardStats), C.c_void_p]
     lib.ncpadj_elastic_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_elastic_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.ncpadj_scene_set_fibres.argtypes = [C.c_void_p, C.c_void_p]
+    lib.ncpadj_dense_inverse.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
     if path is None:
         _LIB = lib
     return lib
@@ -206,6 +211,14 @@ class Scene:
     def batch(cls, ctx: Context, meshes, h: float) -> "Scene":
         return cls(ctx, None, None, None, None, None, h, _batch=list(meshes))
 
+    def set_fibres(self, fibre) -> None:
+        """Unit fibre directions [n_tets, 3] of the per-tet actuation (host array)."""
+        f = torch.as_tensor(fibre, dtype=torch.float64).reshape(-1, 3).contiguous().cpu()
+        if f.shape[0] != self.n_tets:
+            raise ValueError(f"expected {self.n_tets} fibres, got {f.shape[0]}")
+        self._fibre = f
+        _check(self.lib, self.lib.ncpadj_scene_set_fibres(self.handle, C.c_void_p(f.data_ptr())))
+
     def info(self) -> dict:
         inf = _SceneInfo()
         _check(self.lib, self.lib.ncpadj_scene_get_info(self.handle, C.byref(inf)))
@@ -246,7 +259,7 @@ class Contacts:
 
 def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4,
                  rtol=1e-8, max_iters=2000, restart=64, precision="fp64", cap_precision="fp64", precond="woodbury",
-                 solver="auto",
+                 solver="auto", cap_block=0,
                  memory="device", outputs: Optional[dict] = None, stream=None, want=("dL_dq_prev", "dL_dv_prev",
                  "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z")):
     """One adjoint step through the C-ABI.  Returns (grads dict of tensors, stats dict).
@@ -261,13 +274,14 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     dev = q.device
     outputs = dict(outputs or {})
     shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
-              "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (max(nc, 0),)}
+              "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (max(nc, 0),), "dL_dact": (nt,)}
     for k in want:
         if k not in outputs:
+            dt = torch.float32 if k == "dL_dact" else torch.float64
             if memory == "host":
-                outputs[k] = torch.empty(shapes[k], dtype=torch.float64, pin_memory=torch.cuda.is_available())
+                outputs[k] = torch.empty(shapes[k], dtype=dt, pin_memory=torch.cuda.is_available())
             else:
-                outputs[k] = torch.empty(shapes[k], dtype=torch.float64, device=dev)
+                outputs[k] = torch.empty(shapes[k], dtype=dt, device=dev)
     cts = _Contacts(0, None, None, None, None, None, None, 1)
     if nc:
         cts = _Contacts(nc, _ptr(contacts.vertex), _ptr(contacts.frame), _ptr(contacts.d_n), _ptr(contacts.d_f),
@@ -275,12 +289,13 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     stt = _State(_ptr(q), _ptr(q_prev), _ptr(lam) if nc else None)
     sd = _Seed(_ptr(dL_dq), _ptr(dL_dv))
     gr = _Grads(*[_ptr(outputs.get(k)) for k in ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu",
-                                                 "dL_dmu", "dL_dmu_contact", "z")])
+                                                 "dL_dmu", "dL_dmu_contact", "z", "dL_dact")])
     opt = _Options()
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
     opt.precision = PRECISION[precision]
     opt.cap_precision = PRECISION[cap_precision]
+    opt.cap_block = int(cap_block)
     opt.precond = PRECOND[precond]
     opt.solver = SOLVER[solver]
     opt.memory = MEMORY[memory]
@@ -303,14 +318,16 @@ def _contacts_struct(contacts):
 
 def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None, f_ext=None,
                  gravity=(0.0, 0.0, -9.81), *, eps=1e-4, newton_tol=1e-10, max_newton=60, precond="woodbury",
-                 rtol=1e-10, max_iters=2000, restart=64, stream=None):
-    """One forward step on the GPU (device tensors).  Returns (q, lambda [n_c, 3], stats)."""
+                 rtol=1e-10, max_iters=2000, restart=64, stream=None, act=None):
+    """One forward step on the GPU (device tensors).  ``act``: float32 [n_tets] activations (the
+    scene needs fibres, ``Scene.set_fibres``).  Returns (q, lambda [n_c, 3], stats)."""
     lib = scene.lib
     nc = contacts.n if contacts is not None else 0
     dev = q_prev.device
     q = torch.empty_like(q_prev)
     lam = torch.empty((max(nc, 1), 3), dtype=torch.float64, device=dev)
-    fin = _ForwardInput(_ptr(q_prev), _ptr(v_prev), _ptr(f_ext), (C.c_double * 3)(*[float(g) for g in gravity]))
+    fin = _ForwardInput(_ptr(q_prev), _ptr(v_prev), _ptr(f_ext), (C.c_double * 3)(*[float(g) for g in gravity]),
+                        _ptr(act))
     opt = _Options()
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
@@ -346,3 +363,18 @@ def elastic_solve_noalloc(scene: Scene, x: torch.Tensor, y: torch.Tensor, stream
     _check(lib, lib.ncpadj_elastic_solve_noalloc(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y),
                                                  C.c_void_p(stream)))
     return y
+
+
+def dense_inverse(ctx: Context, Cm: torch.Tensor, precision: str = "fp64", stream=None) -> torch.Tensor:
+    """C^{-1} of a dense square FP64 device matrix by the library's Gauss-Jordan inversion (the
+    capacitance inverse of the Woodbury preconditioner); precision "mixed" computes in FP32."""
+    lib = ctx.lib
+    if Cm.dim() != 2 or Cm.shape[0] != Cm.shape[1] or Cm.dtype != torch.float64 or not Cm.is_cuda:
+        raise ValueError("expected a square float64 CUDA matrix")
+    Cm = Cm.contiguous()
+    out = torch.empty_like(Cm)
+    if stream is None:
+        stream = torch.cuda.current_stream(Cm.device).cuda_stream
+    _check(lib, lib.ncpadj_dense_inverse(ctx.handle, Cm.shape[0], _ptr(Cm), _ptr(out), PRECISION[precision],
+                                         C.c_void_p(stream)))
+    return out

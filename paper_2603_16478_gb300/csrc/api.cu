@@ -330,12 +330,23 @@ struct Engine {
   // mixed precision: FP32 matrix values, FP32 A^{-1} products and capacitance apply
   bool mixed = false;
   bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
+  int cap_block = 0;      // most contacts per capacitance block (0: the largest the direct inverse takes)
   float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr, *Ctmp32 = nullptr;
   // the capacitance is block-diagonal by scene (contacts of different meshes share no ancestor
   // in the elimination forest): one dense block per scene that has contacts
   std::vector<int> blk_c0, blk_nc;
   std::vector<size_t> blk_moff, blk_doff;
   size_t cap_elems = 0, ds_elems = 0;
+  // scene blocks above the direct inverse's size are solved iteratively (Sec. 4.4: inner Krylov
+  // solve on the capacitance): the full dense capacitance of such a block (FP32) is applied by an
+  // inner right-preconditioned GMRES whose preconditioner is the exact inverse of each of its
+  // contiguous groups (blk_*).  sup_g0/sup_g1: the groups of super-block k.
+  std::vector<int> sup_c0, sup_nc, sup_g0, sup_g1;
+  std::vector<size_t> sup_off, sup_doff;
+  size_t sup_elems = 0, sup_delems = 0;
+  static constexpr int kInnerRestart = 40;
+  double inner_rtol = 1e-6;
+  int inner_iters = 0;
 
   void plan_blocks() {
     blk_c0.clear();
@@ -359,6 +370,42 @@ struct Engine {
         }
         blk_nc.back()++;
       }
+    }
+    // blocks above the direct inverse's size (or the caller's limit) are split into contiguous,
+    // nearly equal groups; the Delassus coupling between groups is left out of the preconditioner
+    {
+      const int lim = cap_block > 0 ? std::min(cap_block, gj_cols_max_dim() / 3) : gj_cols_max_dim() / 3;
+      std::vector<int> c0s, ncs;
+      sup_c0.clear();
+      sup_nc.clear();
+      sup_g0.clear();
+      sup_g1.clear();
+      for (size_t b = 0; b < blk_c0.size(); ++b) {
+        const int parts = (blk_nc[b] + lim - 1) / lim;
+        if (parts > 1) {
+          sup_c0.push_back(blk_c0[b]);
+          sup_nc.push_back(blk_nc[b]);
+          sup_g0.push_back((int)c0s.size());
+          sup_g1.push_back((int)c0s.size() + parts);
+        }
+        for (int k = 0; k < parts; ++k) {
+          const int lo = blk_c0[b] + (int)((long)blk_nc[b] * k / parts);
+          const int hi = blk_c0[b] + (int)((long)blk_nc[b] * (k + 1) / parts);
+          c0s.push_back(lo);
+          ncs.push_back(hi - lo);
+        }
+      }
+      blk_c0.swap(c0s);
+      blk_nc.swap(ncs);
+    }
+    sup_off.assign(sup_c0.size(), 0);
+    sup_doff.assign(sup_c0.size(), 0);
+    sup_elems = sup_delems = 0;
+    for (size_t k = 0; k < sup_c0.size(); ++k) {
+      sup_off[k] = sup_elems;
+      sup_doff[k] = sup_delems;
+      sup_elems += (size_t)9 * sup_nc[k] * sup_nc[k];
+      sup_delems += (size_t)sup_nc[k] * sup_nc[k];
     }
     blk_moff.assign(blk_c0.size(), 0);
     blk_doff.assign(blk_c0.size(), 0);
@@ -386,15 +433,14 @@ struct Engine {
     precond = precond_;
     ncap = 3 * nc;
     plan_blocks();
-    if (mixed) {
-      S.bsr32.ensure(sizeof(float) * 9 * (size_t)S.nb);
+    if (mixed) S.bsr32.ensure(sizeof(float) * 9 * (size_t)S.nb);
+    else S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
+    if (mixed || cap_fp32) {
       S.vec32.ensure(sizeof(float) * (2 * (size_t)N + 2 * cap_elems + 64));
       x32 = S.vec32.as<float>();
       w32 = x32 + N;
       Cm32 = w32 + N;
       Ctmp32 = Cm32 + cap_elems;
-    } else {
-      S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
     }
     S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
     S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
@@ -410,10 +456,24 @@ struct Engine {
       S.cap.ensure(sizeof(double) * (cap_elems + ds_elems + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
       int nmax = 0;
       for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
-      S.capw.ensure(gj_scratch_bytes(nmax, C.sm_count));
+      const size_t wbytes =
+          std::max(gj_cols_reserved_bytes() + gj_scratch_bytes(nmax, C.sm_count), gj_cols_scratch_bytes(nmax, false));
+      if (S.capw.bytes < wbytes) {  // the column-owned inverse expects its flags zero
+        S.capw.ensure(wbytes);
+        NCPADJ_CUDA_TRY(cudaMemset(S.capw.p, 0, wbytes));
+      }
       Cm = S.cap.as<double>();
       Ds = Cm + cap_elems;
       piv = reinterpret_cast<int32_t*>(Ds + ds_elems + 16);
+      if (!sup_c0.empty()) {
+        int smax = 0;
+        for (int v : sup_nc) smax = std::max(smax, 3 * v);
+        // FP64 Delassus + FP64 capacitance (formed), FP32 capacitance (applied)
+        S.capfull.ensure(sizeof(double) * (sup_delems + sup_elems) + sizeof(float) * sup_elems + 256);
+        S.inner.ensure(sizeof(double) * ((size_t)(kInnerRestart + 1) * smax + 3 * (size_t)smax +
+                                         2 * (size_t)(kInnerRestart + 2) + 64));
+        S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
+      }
     }
     double* base = S.vecs.as<double>();
     for (double** v : {&b, &x, &r, &w, &t0, &t1, &t2, &t3, &dinv}) {
@@ -468,11 +528,16 @@ struct Engine {
         NCPADJ_CUDA_TRY(cudaGetLastError());
         if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
         bool ok;
-        if (mixed && cap_fp32) {
+        const bool cols = n_ <= gj_cols_max_dim();
+        if (cap_fp32) {
           launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
-          ok = launch_gj_invert32(n_, Cm32 + blk_moff[k], Ctmp32 + blk_moff[k], pb, flags, C.sm_count, st);
+          ok = cols ? launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st)
+                    : launch_gj_invert32(n_, Cm32 + blk_moff[k], Ctmp32 + blk_moff[k], pb, flags, C.sm_count, st);
         } else {
-          ok = launch_gj_invert(n_, Cb, pb, S.capw.as<double>(), flags, C.sm_count, st);
+          ok = cols ? launch_gj_cols64(n_, Cb, S.capw.p, pb, flags, C.sm_count, st)
+                    : launch_gj_invert(n_, Cb, pb,
+                                       reinterpret_cast<double*>(S.capw.as<char>() + gj_cols_reserved_bytes()), flags,
+                                       C.sm_count, st);
           if (ok && mixed) launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);  // FP32 apply
         }
         if (!ok) {
@@ -486,6 +551,116 @@ struct Engine {
         }
         NCPADJ_CUDA_TRY(cudaGetLastError());
       }
+      for (size_t k = 0; k < sup_c0.size(); ++k) {  // full capacitance of the iteratively solved blocks
+        const int c0 = sup_c0[k], m_ = sup_nc[k];
+        double* Dfull = S.capfull.as<double>() + sup_doff[k];
+        double* Cfull = S.capfull.as<double>() + sup_delems + sup_off[k];
+        float* Cfull32 = reinterpret_cast<float*>(S.capfull.as<double>() + sup_delems + sup_elems) + sup_off[k];
+        launch_delassus(m_, in.cvertex + c0, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
+                        S.St_val.as<double>(), Dfull, st);
+        launch_cap_form(m_, Dfull, in.frame + 9 * (size_t)c0, S.cdata.as<double>() + 12 * (size_t)c0, h, transpose,
+                        Cfull, st);
+        launch_convert_f32((long)9 * m_ * m_, Cfull, Cfull32, st);
+        NCPADJ_CUDA_TRY(cudaGetLastError());
+      }
+    }
+  }
+
+  float* sup_matrix32(size_t k) {
+    return reinterpret_cast<float*>(S.capfull.as<double>() + sup_delems + sup_elems) + sup_off[k];
+  }
+
+  // out = B^{-1} in over the groups g0..g1-1 of a super-block whose first contact is c0 (segment
+  // vectors of length 3 * contacts)
+  void group_precond(int g0, int g1, int c0, const double* in_seg, double* out_seg) {
+    for (int g = g0; g < g1; ++g) {
+      const size_t o = 3 * (size_t)(blk_c0[g] - c0);
+      const int n_ = 3 * blk_nc[g];
+      int32_t* pb = piv + 3 * (size_t)blk_c0[g];
+      if (mixed || cap_fp32) launch_gj_apply32(n_, Cm32 + blk_moff[g], pb, in_seg + o, nullptr, out_seg + o, st);
+      else launch_gj_apply(n_, Cm + blk_moff[g], pb, in_seg + o, nullptr, out_seg + o, st);
+    }
+  }
+
+  // Inner solve C y = s on super-block k by right-preconditioned restarted GMRES (classical
+  // Gram-Schmidt twice; Hessenberg on the host), to ||s - C y|| <= inner_rtol ||s||.
+  void inner_solve(size_t k, const double* sseg, double* yseg) {
+    const int n = 3 * sup_nc[k], c0 = sup_c0[k], mi = kInnerRestart;
+    const float* Cf = sup_matrix32(k);
+    double* V = S.inner.as<double>();               // (mi+1) x n
+    double* u = V + (size_t)(mi + 1) * n;            // preconditioned vector
+    double* rr = u + n;                              // residual
+    double* ww = rr + n;                             // C y scratch
+    double* gs = ww + n;                             // [0..mi]: pass 1, [mi+1..2mi+1]: pass 2, [2mi+2]: norm
+    double* nrm2 = scal + 5;
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(yseg, 0, sizeof(double) * n, st));
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(rr, sseg, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    auto norm_host = [&](const double* a) {
+      launch_multi_dot(n, 1, a, n, a, partial, scal + 4, st);
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host + 4, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+      return std::sqrt(S.scal_host[4]);
+    };
+    const double s0 = norm_host(rr);
+    if (!(s0 > 0.0) || !std::isfinite(s0)) return;
+    const double tol = inner_rtol * s0;
+    double beta = s0;
+    std::vector<double> H((size_t)(mi + 1) * mi, 0.0), cs(mi), sn(mi), g(mi + 1), yv(mi);
+    for (int cycle = 0; cycle < 50; ++cycle) {
+      launch_axpby(n, 1.0 / beta, rr, 0.0, nullptr, V, st);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int kk = 0;
+      bool done = false;
+      for (int j = 0; j < mi; ++j) {
+        double* vn = V + (size_t)(j + 1) * n;
+        group_precond(sup_g0[k], sup_g1[k], c0, V + (size_t)j * n, u);
+        launch_dense_gemv32(n, Cf, u, vn, st);
+        launch_multi_dot(n, j + 1, V, n, vn, partial, gs, st);
+        launch_multi_axpy(n, j + 1, V, n, gs, vn, st);
+        launch_multi_dot(n, j + 1, V, n, vn, partial, gs + (mi + 1), st);
+        launch_multi_axpy(n, j + 1, V, n, gs + (mi + 1), vn, st);
+        launch_multi_dot(n, 1, vn, n, vn, partial, nrm2, st);
+        launch_normalize(n, vn, nrm2, vn, gs + 2 * (mi + 1), st);
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_host, gs, sizeof(double) * (2 * (mi + 1) + 1), cudaMemcpyDeviceToHost, st));
+        NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+        double* hcol = &H[(size_t)(mi + 1) * j];
+        for (int i = 0; i <= j; ++i) hcol[i] = S.gs_host[i] + S.gs_host[mi + 1 + i];
+        hcol[j + 1] = S.gs_host[2 * (mi + 1)];
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+          hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+          hcol[i] = t;
+        }
+        const double rn = std::hypot(hcol[j], hcol[j + 1]);
+        cs[j] = rn > 0 ? hcol[j] / rn : 1.0;
+        sn[j] = rn > 0 ? hcol[j + 1] / rn : 0.0;
+        hcol[j] = rn;
+        hcol[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++inner_iters;
+        kk = j + 1;
+        const double est = std::fabs(g[j + 1]);
+        if (!std::isfinite(est) || est <= tol) {
+          done = true;
+          break;
+        }
+      }
+      for (int i = kk - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int jj = i + 1; jj < kk; ++jj) t -= H[(size_t)(mi + 1) * jj + i] * yv[jj];
+        yv[i] = t / H[(size_t)(mi + 1) * i + i];
+      }
+      double* ydev = gs + 2 * (mi + 1) + 1;
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(ydev, yv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, st));
+      launch_combine(n, kk, V, n, ydev, ww, st);        // ww = V y
+      group_precond(sup_g0[k], sup_g1[k], c0, ww, u);  // u = B^{-1} V y
+      launch_axpby(n, 1.0, yseg, 1.0, u, yseg, st);
+      launch_dense_gemv32(n, Cf, yseg, ww, st);
+      launch_axpby(n, 1.0, sseg, -1.0, ww, rr, st);
+      beta = norm_host(rr);
+      if (done || !std::isfinite(beta) || beta <= tol) break;
     }
   }
 
@@ -510,22 +685,41 @@ struct Engine {
       case NCPADJ_PRECOND_ELASTIC:
         ainv(xin, yout);
         break;
-      default: {  // Woodbury (Eq. woodbury_formula without K^{-1}): y = u - h^2 A^{-1} J^T C^{-1} K' J u, u = A^{-1} x
+      default: {
+        // Woodbury (Eq. woodbury_formula without K^{-1}), written as
+        //   y = A^{-1} (x - h^2 J^T C^{-1} K' J A^{-1} x),   A^{-1} = P^T S^T S P:
+        // w = S P x once; J A^{-1} x needs A^{-1} x at the contact vertices only, i.e. rows of S^T
+        // (elimination-tree paths) against w; the correction enters w along the same paths; then
+        // y = P^T S^T w.  One full product with S and one with S^T per apply instead of two each.
         if (nc == 0) {
           ainv(xin, yout);
           break;
         }
-        ainv(xin, t1);
-        launch_contact_gather_kt(nc, in.cvertex, in.frame, S.cdata.as<double>(), transpose, t1, sc, st);
-        for (size_t k = 0; k < blk_c0.size(); ++k) {
-          const size_t o = 3 * (size_t)blk_c0[k];
-          const int n_ = 3 * blk_nc[k];
-          if (mixed) launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
-          else launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+        const int32_t* ip = S.iperm.as<int32_t>();
+        if (mixed) launch_sinv_half1_32(sinv, xin, w32, st);
+        else launch_sinv_half1(sinv, xin, t3, st);
+        launch_path_gather(nc, in.cvertex, ip, sinv, t3, mixed ? w32 : nullptr, in.frame, S.cdata.as<double>(),
+                           transpose, sc, st);
+        {
+          size_t ks = 0;  // super-blocks in contact order
+          for (size_t k = 0; k < blk_c0.size();) {
+            if (ks < sup_c0.size() && (int)k == sup_g0[ks]) {
+              const size_t o = 3 * (size_t)sup_c0[ks];
+              inner_solve(ks, sc + o, tc + o);
+              k = sup_g1[ks];
+              ++ks;
+              continue;
+            }
+            const size_t o = 3 * (size_t)blk_c0[k];
+            const int n_ = 3 * blk_nc[k];
+            if (mixed || cap_fp32) launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+            else launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+            ++k;
+          }
         }
-        launch_contact_scatter(nv, nc, in.cvertex, in.frame, tc, t2, st);
-        ainv(t2, t0);
-        launch_axpby(N, 1.0, t1, -h * h, t0, yout, st);
+        launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st);
+        if (mixed) launch_sinv_half2_32(sinv, w32, yout, st);
+        else launch_sinv_half2(sinv, t3, yout, st);
       }
     }
   }
@@ -575,6 +769,10 @@ struct Engine {
         // rotations, triangular solve) on the host, which reads the Gram-Schmidt coefficients of
         // each iteration in one copy together with the convergence check.
         double* V = S.gmres.as<double>();  // (m+1) x N
+        // flexible GMRES when the preconditioner contains an inner iterative solve: keep
+        // z_j = P^{-1} v_j and update x with Z y (Saad's FGMRES)
+        const bool flexible = !sup_c0.empty() && precond == NCPADJ_PRECOND_WOODBURY && nc > 0;
+        double* Z = flexible ? S.fgmres.as<double>() : nullptr;
         double* gs = V + (size_t)(m + 1) * N;  // [0..m]: first-pass, [m+1..2m+1]: second-pass, [2m+2]: norm
         double* ydev = gs + 2 * (m + 1) + 1;
         double* nrm2 = scal + 5;
@@ -588,8 +786,9 @@ struct Engine {
           int k = 0;
           for (int j = 0; j < m; ++j) {
             double* vn = V + (size_t)(j + 1) * N;
-            apply_precond(V + (size_t)j * N, w);
-            matvec(w, vn);
+            double* zj = flexible ? Z + (size_t)j * N : w;
+            apply_precond(V + (size_t)j * N, zj);
+            matvec(zj, vn);
             launch_multi_dot(N, j + 1, V, N, vn, partial, gs, st);
             launch_multi_axpy(N, j + 1, V, N, gs, vn, st);
             launch_multi_dot(N, j + 1, V, N, vn, partial, gs + (m + 1), st);
@@ -624,8 +823,12 @@ struct Engine {
             y[i] = t / H[(size_t)(m + 1) * i + i];
           }
           NCPADJ_CUDA_TRY(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-          launch_combine(N, k, V, N, ydev, r, st);
-          apply_precond(r, w);
+          if (flexible) {
+            launch_combine(N, k, Z, N, ydev, w, st);
+          } else {
+            launch_combine(N, k, V, N, ydev, r, st);
+            apply_precond(r, w);
+          }
           launch_axpby(N, 1.0, x, 1.0, w, x, st);
           matvec(x, w);
           launch_axpby(N, 1.0, b, -1.0, w, r, st);
@@ -677,6 +880,7 @@ void validate_options(const ncpadj_options& opt) {
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
   NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
   NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED, "bad cap_precision");
+  NCPADJ_REQUIRE(opt.cap_block >= 0, "bad cap_block");
 }
 
 void raise_flags(const int* fh) {
@@ -697,6 +901,8 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
                                   ncpadj_grads* grads, ncpadj_stats* stats, cudaStream_t st) {
   NCPADJ_REQUIRE(ctx && sc, "NULL context or scene");
   NCPADJ_REQUIRE(state && seed && state->q && state->q_prev && seed->dL_dq, "state.q, state.q_prev and seed.dL_dq are required");
+  NCPADJ_REQUIRE(!grads || !grads->dL_dact || sc->s.fibre.p,
+                 "dL_dact requested but the scene has no fibres (ncpadj_scene_set_fibres)");
   ncpadj_options opt;
   if (opt_in) opt = *opt_in;
   else ncpadj_options_default(&opt);
@@ -763,13 +969,16 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
       in.region = ct->region;
     }
   }
-  const int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
+  int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
   E.mixed = opt.precision == NCPADJ_MIXED;
-  E.cap_fp32 = E.mixed && opt.cap_precision == NCPADJ_MIXED;
+  E.cap_fp32 = opt.cap_precision == NCPADJ_MIXED;
+  E.cap_block = opt.cap_block;
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, in.cvertex, in.region, nreg, st);  // before anything indexes with the ids
   E.workspace(nc, opt.gmres_restart, opt.precond);
+  // an inner iterative capacitance solve makes the preconditioner vary: flexible GMRES only
+  if (!E.sup_c0.empty() && opt.precond == NCPADJ_PRECOND_WOODBURY) solver = NCPADJ_SOLVER_GMRES;
   E.transpose = 1;
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[0], st));
   E.assemble(in.q, in.q_prev, in.lambda, opt.eps);
@@ -835,6 +1044,17 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
                   S.tetdata.as<double>(), S.lame_d.as<double>(), in.cvertex, in.frame, S.cdata.as<double>(), in.region,
                   go.dL_dq_prev, go.dL_dv_prev, go.dL_dfext, go.dL_dE, go.dL_dnu, go.dL_dmu, go.dL_dmu_contact};
   launch_contractions(ka, st);
+  float* dact = nullptr;
+  if (grads && grads->dL_dact) {
+    if (host_mem) {
+      S.actf.ensure(std::max(sizeof(float) * (size_t)nt, sizeof(double) * N));
+      dact = S.actf.as<float>();
+    } else {
+      dact = grads->dL_dact;
+    }
+    launch_act_grad(nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.fibre.as<double>(), E.x, S.h,
+                    dact, st);
+  }
   if (go.z) NCPADJ_CUDA_TRY(cudaMemcpyAsync(go.z, E.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   launch_nonfinite_check(N, E.x, flags, st);
   NCPADJ_CUDA_TRY(cudaGetLastError());
@@ -851,6 +1071,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     back(grads->dL_dnu, go.dL_dnu, nt);
     back(grads->dL_dmu, go.dL_dmu, nreg);
     back(grads->dL_dmu_contact, go.dL_dmu_contact, nc);
+    if (dact) NCPADJ_CUDA_TRY(cudaMemcpyAsync(grads->dL_dact, dact, sizeof(float) * nt, cudaMemcpyDeviceToHost, st));
   }
   read_flags(S, st);
   if (stats) {
@@ -858,6 +1079,8 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     stats->solver_used = solver;
     stats->n_contacts = nc;
     stats->capacitance_dim = (opt.precond == NCPADJ_PRECOND_WOODBURY) ? 3 * nc : 0;
+    stats->capacitance_blocks = (opt.precond == NCPADJ_PRECOND_WOODBURY && nc) ? (int32_t)E.blk_c0.size() : 0;
+    stats->inner_iterations = E.inner_iters;
     stats->rel_residual = rel;
     float ms[5] = {0, 0, 0, 0, 0};
     cudaEventElapsedTime(&ms[0], S.ev[0], S.ev[4]);
@@ -891,6 +1114,7 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
                                   int max_newton, double* q_out, double* lambda_out, ncpadj_forward_stats* stats,
                                   cudaStream_t st) {
   NCPADJ_REQUIRE(ctx && sc && fin && fin->q_prev && q_out, "NULL required argument");
+  NCPADJ_REQUIRE(!fin->act || sc->s.fibre.p, "actuation given but the scene has no fibres (ncpadj_scene_set_fibres)");
   NCPADJ_REQUIRE(newton_tol > 0 && max_newton > 0, "newton_tol and max_newton must be positive");
   ncpadj_options opt;
   if (opt_in) opt = *opt_in;
@@ -912,11 +1136,12 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   E.in.mu = nc ? ct->mu : nullptr;
   E.in.region = nc ? ct->region : nullptr;
   E.in.q_prev = fin->q_prev;
-  const int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
+  int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);  // before any indexing
   E.workspace(nc, opt.gmres_restart, opt.precond);
+  if (!E.sup_c0.empty() && opt.precond == NCPADJ_PRECOND_WOODBURY) solver = NCPADJ_SOLVER_GMRES;
   E.transpose = 0;
   S.fwd.ensure(sizeof(double) * (4 * (size_t)N + 3 * (size_t)std::max(nc, 1) + 4 * (size_t)std::max(nc, 1)) +
                sizeof(int) * std::max(nc, 1) + 64);
@@ -930,10 +1155,20 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   int* loaded = reinterpret_cast<int*>(slip_new + 2 * std::max(nc, 1));
   cudaEvent_t e0 = S.ev[0], e1 = S.ev[5];
   NCPADJ_CUDA_TRY(cudaEventRecord(e0, st));
-  launch_predict(nv, fin->q_prev, fin->v_prev, fin->f_ext, S.massd.as<double>(), fin->gravity[0], fin->gravity[1],
+  const double* f_total = fin->f_ext;
+  if (fin->act) {  // f_ext + f_act
+    S.actf.ensure(sizeof(double) * N);
+    double* fa = S.actf.as<double>();
+    if (fin->f_ext) NCPADJ_CUDA_TRY(cudaMemcpyAsync(fa, fin->f_ext, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    else NCPADJ_CUDA_TRY(cudaMemsetAsync(fa, 0, sizeof(double) * N, st));
+    launch_act_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), fin->act,
+                     S.fibre.as<double>(), fa, st);
+    f_total = fa;
+  }
+  launch_predict(nv, fin->q_prev, fin->v_prev, f_total, S.massd.as<double>(), fin->gravity[0], fin->gravity[1],
                  fin->gravity[2], S.h, qt, st);
   NCPADJ_CUDA_TRY(cudaMemcpyAsync(q, qt, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-  double fscale = 0;
+  double fscale = 0, start_gap = 0;
   {
     const double g2 = fin->gravity[0] * fin->gravity[0] + fin->gravity[1] * fin->gravity[1] + fin->gravity[2] * fin->gravity[2];
     double mmax = 0, m2 = 0;
@@ -942,8 +1177,8 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
       m2 += mv * mv;
     }
     fscale = S.h * S.h * std::sqrt(m2 * std::max(g2, 1e-30));
-    const double gap0 = 10.0 * opt.eps * opt.eps / std::max(mmax * std::sqrt(std::max(g2, 1e-30)), 1e-300);
-    launch_lift(nc, E.in.cvertex, E.in.frame, E.in.d_n, gap0, q, st);
+    start_gap = 10.0 * opt.eps * opt.eps / std::max(mmax * std::sqrt(std::max(g2, 1e-30)), 1e-300);
+    launch_lift(nc, E.in.cvertex, E.in.frame, E.in.d_n, start_gap, q, fin->q_prev, E.in.d_f, st);
   }
   // residual at a point: R = M (q - qt) + h^2 sum w G^T (G q - p) - h^2 J^T lambda(q); returns ||R||^2 or
   // +inf if the point leaves the local-solve domain (or turns a loaded slip, when asked)
@@ -956,7 +1191,7 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
       ContactArgs ca = E.contact_args(qq, fin->q_prev, nullptr, opt.eps);
       // the loaded mask belongs to the accepted iterate: trial points (check_turn) leave it alone
       launch_local_contact(ca, lam, slip, check_turn ? nullptr : loaded, RR, st);
-      if (check_turn) launch_turn_check(nc, slip_old, slip, loaded, flags, st);
+      if (check_turn) launch_turn_check(nc, slip_old, slip, loaded, flags, E.in.cvertex, RR, st);
     }
     launch_multi_dot(N, 1, RR, N, RR, E.partial, E.scal + 6, st);
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host + 6, E.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -968,7 +1203,61 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     }
     return S.scal_host[6];
   };
-  double phi = evaluate(q, R, slip_old, false);
+  // A batch holds independent scenes: each gets its own line search (a failing or slowly converging
+  // scene must not hold the others back).  The residual kernels poison the rows of a vertex whose
+  // tet inverted, whose contact left the local-solve domain or whose slip turned, so the
+  // per-scene squared norms tell which scenes failed.
+  const int ns = S.n_scenes;
+  const bool batch = ns > 1;
+  std::vector<double> phis(ns, 0.0), phits(ns, 0.0), tsc(ns, 1.0);
+  const int32_t* sov = S.scene_of_vertex.as<int32_t>();
+  if (batch) S.sceneval.ensure(sizeof(double) * 2 * (size_t)ns);
+  auto evaluate_scenes = [&](const double* qq, double* RR, double* slip, bool check_turn,
+                             std::vector<double>& out) -> double {
+    evaluate(qq, RR, slip, check_turn);  // flags are global: the poisoned rows carry the per-scene news
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(flags + FLAG_INVERTED, 0, sizeof(int), st));
+    double* sq = S.sceneval.as<double>();
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(sq, 0, sizeof(double) * ns, st));
+    launch_scene_sq(nv, RR, sov, sq, st);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(out.data(), sq, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (double& v : out) {
+      if (!std::isfinite(v)) v = INFINITY;
+      tot += v;
+    }
+    return tot;
+  };
+  auto set_scene_t = [&](const std::vector<double>& t) {
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.sceneval.as<double>() + ns, t.data(), sizeof(double) * ns,
+                                    cudaMemcpyHostToDevice, st));
+  };
+  double phi = batch ? evaluate_scenes(q, R, slip_old, false, phis) : evaluate(q, R, slip_old, false);
+  {
+    // large forces on light vertices can put the inertial prediction outside the domain (an
+    // inverted tet): back off towards q_prev, q = q_prev + t (qt - q_prev), t = 1/2, 1/4, ...
+    // (per scene in a batch)
+    if (!batch) {
+      double t = 1.0;
+      for (int k = 0; !std::isfinite(phi) && k < 40; ++k) {
+        t *= 0.5;
+        launch_axpby(N, 1.0 - t, fin->q_prev, t, qt, q, st);
+        launch_lift(nc, E.in.cvertex, E.in.frame, E.in.d_n, start_gap, q, fin->q_prev, E.in.d_f, st);
+        phi = evaluate(q, R, slip_old, false);
+      }
+    } else {
+      launch_axpby(N, 1.0, qt, -1.0, fin->q_prev, Rt, st);  // Rt = qt - q_prev (scratch)
+      std::vector<double> t(ns, 1.0);
+      for (int k = 0; !std::isfinite(phi) && k < 40; ++k) {
+        for (int i = 0; i < ns; ++i)
+          if (!std::isfinite(phis[i])) t[i] *= 0.5;
+        set_scene_t(t);
+        launch_step_by_scene(nv, fin->q_prev, Rt, sov, S.sceneval.as<double>() + ns, q, st);
+        launch_lift(nc, E.in.cvertex, E.in.frame, E.in.d_n, start_gap, q, fin->q_prev, E.in.d_f, st);
+        phi = evaluate_scenes(q, R, slip_old, false, phis);
+      }
+    }
+  }
   if (!std::isfinite(phi)) throw Error{NCPADJ_ERR_CONTACT_DOMAIN, "no feasible start point for the Newton solve"};
   int it = 0, kry = 0;
   for (it = 0; it < max_newton; ++it) {
@@ -985,17 +1274,47 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     kry += E.solve(solver, std::min(1e-10, 1e-3), opt.max_iters, &rel, &bn);
     read_flags(S, st);
     raise_flags(S.flags_host);
-    // backtracking line search on ||R||
+    // backtracking line search on ||R|| (per scene in a batch)
     double t = 1.0, phit = INFINITY;
     bool ok = false;
-    for (int ls = 0; ls < 40; ++ls) {
-      launch_axpby(N, 1.0, q, t, E.x, q_out, st);
-      phit = evaluate(q_out, Rt, slip_new, true);
-      if (phit <= (1.0 - 1e-4 * t) * phi) {
-        ok = true;
-        break;
+    if (!batch) {
+      for (int ls = 0; ls < 40; ++ls) {
+        launch_axpby(N, 1.0, q, t, E.x, q_out, st);
+        phit = evaluate(q_out, Rt, slip_new, true);
+        if (phit <= (1.0 - 1e-4 * t) * phi) {
+          ok = true;
+          break;
+        }
+        t *= 0.5;
       }
-      t *= 0.5;
+    } else {
+      std::vector<char> acc(ns, 0);
+      std::fill(tsc.begin(), tsc.end(), 1.0);
+      bool settled = false;
+      for (int ls = 0; ls < 40 && !settled; ++ls) {
+        set_scene_t(tsc);
+        launch_step_by_scene(nv, q, E.x, sov, S.sceneval.as<double>() + ns, q_out, st);
+        phit = evaluate_scenes(q_out, Rt, slip_new, true, phits);
+        settled = true;
+        for (int i = 0; i < ns; ++i) {
+          if (acc[i]) continue;
+          if (phits[i] <= (1.0 - 1e-4 * tsc[i]) * phis[i]) {
+            acc[i] = 1;
+            ok = true;
+          } else {
+            tsc[i] *= 0.5;
+            settled = false;
+          }
+        }
+      }
+      if (ok && !settled) {  // scenes that found no decrease stay where they are
+        for (int i = 0; i < ns; ++i)
+          if (!acc[i]) tsc[i] = 0.0;
+        set_scene_t(tsc);
+        launch_step_by_scene(nv, q, E.x, sov, S.sceneval.as<double>() + ns, q_out, st);
+        phit = evaluate_scenes(q_out, Rt, slip_new, true, phits);
+      }
+      if (ok) phis = phits;
     }
     if (!ok) break;  // no decrease possible: rounding floor
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(q, q_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
@@ -1065,6 +1384,7 @@ void ncpadj_options_default(ncpadj_options* o) {
   o->solver = NCPADJ_SOLVER_AUTO;
   o->memory = NCPADJ_MEM_DEVICE;
   o->cap_precision = NCPADJ_FP64;
+  o->cap_block = 0;
 }
 
 ncpadj_status ncpadj_ctx_create(int device, ncpadj_ctx* out) {
@@ -1144,6 +1464,27 @@ void ncpadj_scene_destroy(ncpadj_scene s) {
   delete s;
 }
 
+ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene && fibre, "NULL argument");
+    Scene& S = scene->s;
+    for (int t = 0; t < S.nt; ++t) {
+      const double* d = fibre + 3 * (size_t)t;
+      const double n2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      NCPADJ_REQUIRE(std::isfinite(n2) && std::fabs(n2 - 1.0) <= 2e-6, "fibre " + std::to_string(t) + " is not a unit vector");
+    }
+    if (scene->ctx) NCPADJ_CUDA_TRY(cudaSetDevice(scene->ctx->c.device));
+    S.fibre.ensure(sizeof(double) * 3 * (size_t)std::max(S.nt, 1));
+    NCPADJ_CUDA_TRY(cudaMemcpy(S.fibre.p, fibre, sizeof(double) * 3 * (size_t)S.nt, cudaMemcpyHostToDevice));
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
 ncpadj_status ncpadj_scene_get_info(ncpadj_scene s, ncpadj_scene_info* out) {
   if (!s || !out) {
     set_error("NULL argument");
@@ -1172,6 +1513,58 @@ ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const dou
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
     launch_ainv(a, x, S.io.as<double>(), y, st);
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, double* Cinv, int32_t precision,
+                                   void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(ctx && C && Cinv && C != Cinv, "NULL or aliased argument");
+    NCPADJ_REQUIRE(n > 0 && n <= gj_cols_max_dim(), "n out of range");
+    NCPADJ_REQUIRE(precision == NCPADJ_FP64 || precision == NCPADJ_MIXED, "bad precision");
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx& X = ctx->c;
+    const bool fp32 = precision == NCPADJ_MIXED;
+    const size_t ne = (size_t)n * n;
+    const size_t mat_bytes = (fp32 ? sizeof(float) : sizeof(double)) * ne + sizeof(int32_t) * (size_t)n +
+                             sizeof(int) * FLAG_COUNT + 256;
+    X.inv_mat.ensure(mat_bytes);
+    const size_t wbytes = gj_cols_scratch_bytes(n, fp32);
+    if (X.inv_work.bytes < wbytes) {
+      X.inv_work.ensure(wbytes);
+      NCPADJ_CUDA_TRY(cudaMemset(X.inv_work.p, 0, wbytes));
+    }
+    char* base = X.inv_mat.as<char>();
+    void* B = base;
+    int32_t* piv = reinterpret_cast<int32_t*>(base + (fp32 ? sizeof(float) : sizeof(double)) * ne);
+    int* flags = reinterpret_cast<int*>(piv + n);
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * FLAG_COUNT, st));
+    bool ok;
+    if (fp32) {
+      launch_convert_f32((long)ne, C, static_cast<float*>(B), st);
+      ok = launch_gj_cols32(n, static_cast<float*>(B), X.inv_work.p, piv, flags, X.sm_count, st);
+    } else {
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(B, C, sizeof(double) * ne, cudaMemcpyDeviceToDevice, st));
+      ok = launch_gj_cols64(n, static_cast<double*>(B), X.inv_work.p, piv, flags, X.sm_count, st);
+    }
+    if (!ok) {
+      cudaGetLastError();
+      throw Error{NCPADJ_ERR_UNSUPPORTED, "the dense inverse could not be launched for n = " + std::to_string(n)};
+    }
+    int fh[FLAG_COUNT];
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(fh, flags, sizeof(fh), cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the dense inverse timed out"};
+    if (fh[FLAG_SINGULAR]) throw Error{NCPADJ_ERR_NONFINITE, "the matrix is singular"};
+    launch_unpermute_inverse(n, B, fp32, piv, Cinv, st);
     NCPADJ_CUDA_TRY(cudaGetLastError());
     return NCPADJ_OK;
   } catch (const Error& e) {

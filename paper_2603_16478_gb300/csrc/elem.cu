@@ -521,18 +521,35 @@ __global__ void k_predict(int nv, const double* q_prev, const double* v_prev, co
   qt[i] = q_prev[i] + h * (v_prev ? v_prev[i] : 0.0) + h * h * acc;
 }
 
-__global__ void k_lift(int nc, const int32_t* vertex, const double* frame, const double* d_n, double gap0, double* q) {
+__global__ void k_lift(int nc, const int32_t* vertex, const double* frame, const double* d_n, double gap0, double* q,
+                       const double* q_prev, const double* d_f) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int v = vertex[c];
   const double* n = frame + 9 * (size_t)c;
   const double dn = n[0] * q[3 * v] + n[1] * q[3 * v + 1] + n[2] * q[3 * v + 2] - d_n[c];
-  if (dn < gap0) {
-    const double d = gap0 - dn;
-    atomicAdd(&q[3 * v], d * n[0]);
-    atomicAdd(&q[3 * v + 1], d * n[1]);
-    atomicAdd(&q[3 * v + 2], d * n[2]);
+  double d[3] = {0.0, 0.0, 0.0};
+  if (dn < gap0)
+    for (int r = 0; r < 3; ++r) d[r] = (gap0 - dn) * n[r];
+  // a frictional contact needs a slip direction: where the prediction has exactly none (at rest
+  // under a normal load), start from a 1e-12 m tangential offset in a direction fixed by c
+  double s1 = 0.0, s2 = 0.0;
+  for (int r = 0; r < 3; ++r) {
+    const double dq = q[3 * v + r] - q_prev[3 * v + r];
+    s1 += n[3 + r] * dq;
+    s2 += n[6 + r] * dq;
   }
+  if (d_f) {
+    s1 -= d_f[2 * c];
+    s2 -= d_f[2 * c + 1];
+  }
+  if (s1 == 0.0 && s2 == 0.0) {
+    const double ang = 6.283185307179586 * (0.6180339887498949 * (double)(c + 1) - floor(0.6180339887498949 * (double)(c + 1)));
+    const double a = 1e-12 * cos(ang), b = 1e-12 * sin(ang);
+    for (int r = 0; r < 3; ++r) d[r] += a * n[3 + r] + b * n[6 + r];
+  }
+  for (int r = 0; r < 3; ++r)
+    if (d[r] != 0.0) atomicAdd(&q[3 * v + r], d[r]);
 }
 
 __global__ void k_inertia(int nv, const double* mass, const double* q, const double* qt, double* R) {
@@ -563,6 +580,9 @@ __global__ void __launch_bounds__(128) k_tet_force(int nt, const int32_t* tets, 
   double U[3][3], V[3][3], sig[3];
   if (!svd3<double>(F, U, sig, V)) {
     atomicExch(&flags[FLAG_INVERTED], 1);
+    // also poison the tet's residual rows, so that a per-scene norm shows which scene it was
+#pragma unroll
+    for (int a = 0; a < 4; ++a) atomicAdd(&R[3 * (size_t)vid[a]], (double)INFINITY);
     return;
   }
   double th[3], Hinv[3][3], logJ;
@@ -609,6 +629,7 @@ __global__ void k_local_contact(ContactArgs A, double* lambda, double* slip, int
   if (!(dn > 0.0) || (mu > 0.0 && !(s > 0.0))) {
     atomicExch(&A.flags[FLAG_INFEASIBLE], 1);
     if (loaded) loaded[c] = 0;
+    if (R) atomicAdd(&R[3 * (size_t)v], (double)INFINITY);  // per-scene norms see it
     return;
   }
   const double lam_n = e2 / dn;
@@ -642,13 +663,24 @@ __global__ void k_scale_by_scene(int nv, double* x, const int32_t* sov, const do
   if (i < 3 * nv) x[i] *= scale[sov[i / 3]];
 }
 
-__global__ void k_turn_check(int nc, const double* so, const double* sn, const int* loaded, int* flags) {
+__global__ void k_turn_check(int nc, const double* so, const double* sn, const int* loaded, int* flags,
+                             const int32_t* cvertex, double* R) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc || !loaded[c]) return;
   const double d = so[2 * c] * sn[2 * c] + so[2 * c + 1] * sn[2 * c + 1];
   const double n0 = sqrt(so[2 * c] * so[2 * c] + so[2 * c + 1] * so[2 * c + 1]);
   const double n1 = sqrt(sn[2 * c] * sn[2 * c] + sn[2 * c + 1] * sn[2 * c + 1]);
-  if (d < 0.5 * n0 * n1) atomicExch(&flags[FLAG_TURN], 1);
+  if (d < 0.5 * n0 * n1) {
+    atomicExch(&flags[FLAG_TURN], 1);
+    if (R) atomicAdd(&R[3 * (size_t)cvertex[c]], (double)INFINITY);
+  }
+}
+
+// q_out[i] = q[i] + t[scene(vertex(i))] dx[i]
+__global__ void k_step_by_scene(int nv, const double* q, const double* dx, const int32_t* sov, const double* t,
+                                double* q_out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * nv) q_out[i] = q[i] + t[sov[i / 3]] * dx[i];
 }
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
@@ -693,15 +725,64 @@ void launch_bsr_init(int nv, int nb, const int32_t* diag_slot, const double* mas
     k_bsr_mass<float><<<nblk(nv, 256), 256, 0, s>>>(nv, diag_slot, mass, bsr32);
   }
 }
+// Actuation as a constant active stress P_i = a_i d_i d_i^T (fibre d_i, activation a_i): the nodal
+// force f_a = -V_i P_i g_a = -V_i a_i (d_i . g_a) d_i is accumulated into f (which holds f_ext).
+__global__ void k_act_force(int nt, const int32_t* __restrict__ tets, const double* __restrict__ gvec,
+                            const double* __restrict__ vol, const float* __restrict__ act,
+                            const double* __restrict__ fibre, double* f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double s = -vol[t] * (double)act[t];
+  if (s == 0.0) return;
+  const double d0 = fibre[3 * (size_t)t], d1 = fibre[3 * (size_t)t + 1], d2 = fibre[3 * (size_t)t + 2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double* g = gvec + 12 * (size_t)t + 3 * a;
+    const double c = s * (d0 * g[0] + d1 * g[1] + d2 * g[2]);
+    double* fv = f + 3 * (size_t)tets[4 * (size_t)t + a];
+    atomicAdd(fv, c * d0);
+    atomicAdd(fv + 1, c * d1);
+    atomicAdd(fv + 2, c * d2);
+  }
+}
+
+// dL/da_i = -h^2 V_i d_i^T Z_i d_i, Z_i = sum_a z_a g_a^T (the adjoint field's gradient on tet i)
+__global__ void k_act_grad(int nt, const int32_t* __restrict__ tets, const double* __restrict__ gvec,
+                           const double* __restrict__ vol, const double* __restrict__ fibre,
+                           const double* __restrict__ z, double h, float* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double d0 = fibre[3 * (size_t)t], d1 = fibre[3 * (size_t)t + 1], d2 = fibre[3 * (size_t)t + 2];
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double* g = gvec + 12 * (size_t)t + 3 * a;
+    const double* za = z + 3 * (size_t)tets[4 * (size_t)t + a];
+    acc += (d0 * za[0] + d1 * za[1] + d2 * za[2]) * (d0 * g[0] + d1 * g[1] + d2 * g[2]);
+  }
+  out[t] = (float)(-h * h * vol[t] * acc);
+}
+
+void launch_act_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const float* act,
+                      const double* fibre, double* f, cudaStream_t s) {
+  g_launches += 1;
+  if (nt) k_act_force<<<nblk(nt, 256), 256, 0, s>>>(nt, tets, gvec, vol, act, fibre, f);
+}
+void launch_act_grad(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* fibre,
+                     const double* z, double h, float* out, cudaStream_t s) {
+  g_launches += 1;
+  if (nt) k_act_grad<<<nblk(nt, 256), 256, 0, s>>>(nt, tets, gvec, vol, fibre, z, h, out);
+}
+
 void launch_predict(int nv, const double* q_prev, const double* v_prev, const double* f_ext, const double* mass,
                     double g0, double g1, double g2, double h, double* qt, cudaStream_t s) {
   g_launches += 1;
   k_predict<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, q_prev, v_prev, f_ext, mass, g0, g1, g2, h, qt);
 }
 void launch_lift(int nc, const int32_t* vertex, const double* frame, const double* d_n, double gap0, double* q,
-                 cudaStream_t s) {
+                 const double* q_prev, const double* d_f, cudaStream_t s) {
   g_launches += 1;
-  if (nc) k_lift<<<nblk(nc, 128), 128, 0, s>>>(nc, vertex, frame, d_n, gap0, q);
+  if (nc) k_lift<<<nblk(nc, 128), 128, 0, s>>>(nc, vertex, frame, d_n, gap0, q, q_prev, d_f);
 }
 void launch_inertia(int nv, const double* mass, const double* q, const double* qt, double* R, cudaStream_t s) {
   g_launches += 1;
@@ -729,10 +810,15 @@ void launch_scale_by_scene(int nv, double* x, const int32_t* sov, const double* 
   g_launches += 1;
   k_scale_by_scene<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, x, sov, scale);
 }
-void launch_turn_check(int nc, const double* slip_old, const double* slip_new, const int* loaded, int* flags,
-                       cudaStream_t s) {
+void launch_step_by_scene(int nv, const double* q, const double* dx, const int32_t* sov, const double* t,
+                          double* q_out, cudaStream_t s) {
   g_launches += 1;
-  if (nc) k_turn_check<<<nblk(nc, 128), 128, 0, s>>>(nc, slip_old, slip_new, loaded, flags);
+  k_step_by_scene<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, q, dx, sov, t, q_out);
+}
+void launch_turn_check(int nc, const double* slip_old, const double* slip_new, const int* loaded, int* flags,
+                       const int32_t* cvertex, double* R, cudaStream_t s) {
+  g_launches += 1;
+  if (nc) k_turn_check<<<nblk(nc, 128), 128, 0, s>>>(nc, slip_old, slip_new, loaded, flags, cvertex, R);
 }
 void launch_contractions(const ContractArgs& a, cudaStream_t s) {
   g_launches += 3;

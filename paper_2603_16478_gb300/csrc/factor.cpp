@@ -12,6 +12,8 @@
 //   4. the columns of S = L^{-1}: column j is nonzero exactly on the elimination-tree path
 //      from j to its root, and is obtained by a forward substitution along that path.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <numeric>
 #include <stdexcept>
@@ -113,13 +115,17 @@ void factor_elastic(const CsrD& As, const double* xyz, ElasticFactor& F) {
       }
     }
   }
-  // 3. up-looking Cholesky: row k of L solves L(0:k,0:k) y = A(0:k, k)
+  // 3. up-looking Cholesky: row k of L solves L(0:k,0:k) y = A(0:k, k).  Row k reads and
+  // appends to columns of k's descendants only, so the rows of disjoint elimination subtrees are
+  // independent: subtrees of about n/(8 threads) nodes are factored in parallel (each in
+  // increasing row order), then the remaining top nodes (separators) in increasing order.  Every
+  // row sees exactly the data it sees in a serial sweep: the result is bit-identical.
   std::vector<std::vector<std::pair<int, double>>> Lcol(n);  // strictly-lower entries (row, val)
   std::vector<double> Ldiag(n);
-  {
-    std::vector<double> x(n, 0.0);
-    std::vector<int32_t> mark(n, -1), reach;
-    for (int k = 0; k < n; ++k) {
+  std::atomic<bool> indefinite{false};
+  auto factor_rows = [&](const std::vector<int32_t>& rows, std::vector<double>& x, std::vector<int32_t>& mark,
+                         std::vector<int32_t>& reach) {
+    for (int k : rows) {
       reach.clear();
       mark[k] = k;
       double akk = 0.0;
@@ -143,37 +149,100 @@ void factor_elastic(const CsrD& As, const double* xyz, ElasticFactor& F) {
         d -= y * y;
         Lcol[j].push_back({k, y});
       }
-      if (!(d > 0.0)) throw Error{NCPADJ_ERR_INVALID_ARG, "elastic matrix is not positive definite"};
+      if (!(d > 0.0)) {
+        indefinite = true;
+        d = 1.0;
+      }
       Ldiag[k] = std::sqrt(d);
     }
-  }
-  F.nnz_L = n;
-  for (int j = 0; j < n; ++j) F.nnz_L += (int64_t)Lcol[j].size();
-  // 4. columns of S = L^{-1} along the elimination-tree paths
+  };
+  const int nthreads = std::max(1, std::min<int>(64, (int)std::thread::hardware_concurrency()));
   {
-    std::vector<double> x(n, 0.0);
-    std::vector<int32_t> path;
-    F.St.n = n;
-    F.St.ptr.assign(n + 1, 0);
-    std::vector<std::vector<std::pair<int, double>>> cols(n);
-    int64_t total = 0;
+    std::vector<std::vector<int32_t>> children(n);
+    std::vector<int32_t> size(n, 1), roots;
     for (int j = 0; j < n; ++j) {
-      path.clear();
-      for (int i = j; i != -1; i = F.parent[i]) path.push_back(i);
-      x[j] = 1.0;
-      for (int i : path) {
-        x[i] /= Ldiag[i];
-        double xi = x[i];
-        for (auto& e : Lcol[i]) x[e.first] -= e.second * xi;
-      }
-      total += (int64_t)path.size();
-      F.St.ptr[j + 1] = total;
-      for (int i : path) {
-        F.St.col.push_back(i);
-        F.St.val.push_back(x[i]);
-        x[i] = 0.0;
+      if (F.parent[j] < 0) roots.push_back(j);
+      else children[F.parent[j]].push_back(j);
+    }
+    for (int j = 0; j < n; ++j)
+      if (F.parent[j] >= 0) size[F.parent[j]] += size[j];  // parent > j: sizes complete in order
+    const int target = std::max(256, n / (8 * nthreads));
+    std::vector<int32_t> top, stack(roots.begin(), roots.end());
+    std::vector<std::vector<int32_t>> tasks;
+    while (!stack.empty()) {
+      const int r = stack.back();
+      stack.pop_back();
+      if (size[r] > target && !children[r].empty()) {
+        top.push_back(r);
+        for (int c : children[r]) stack.push_back(c);
+      } else {
+        std::vector<int32_t> rows, st2{r};
+        while (!st2.empty()) {
+          const int v = st2.back();
+          st2.pop_back();
+          rows.push_back(v);
+          for (int c : children[v]) st2.push_back(c);
+        }
+        std::sort(rows.begin(), rows.end());
+        tasks.push_back(std::move(rows));
       }
     }
+    std::sort(tasks.begin(), tasks.end(), [](const auto& a, const auto& b) { return a.size() > b.size(); });
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      std::vector<double> x(n, 0.0);
+      std::vector<int32_t> mark(n, -1), reach;
+      for (size_t t; (t = next.fetch_add(1)) < tasks.size();) factor_rows(tasks[t], x, mark, reach);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < std::min<int>(nthreads, (int)tasks.size()); ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    std::sort(top.begin(), top.end());
+    std::vector<double> x(n, 0.0);
+    std::vector<int32_t> mark(n, -1), reach;
+    factor_rows(top, x, mark, reach);
+  }
+  if (indefinite) throw Error{NCPADJ_ERR_INVALID_ARG, "elastic matrix is not positive definite"};
+  F.nnz_L = n;
+  for (int j = 0; j < n; ++j) F.nnz_L += (int64_t)Lcol[j].size();
+  // 4. columns of S = L^{-1} along the elimination-tree paths.  Column j has one entry per node of
+  // the path from j to its root, so the layout is known up front; the columns are independent
+  // and are computed by all host threads, each with its own dense work vector.
+  {
+    F.St.n = n;
+    F.St.ptr.assign(n + 1, 0);
+    std::vector<int32_t> depth(n, 0);
+    for (int j = n - 1; j >= 0; --j) depth[j] = F.parent[j] < 0 ? 1 : depth[F.parent[j]] + 1;  // parent > j
+    for (int j = 0; j < n; ++j) F.St.ptr[j + 1] = F.St.ptr[j] + depth[j];
+    const int64_t total = F.St.ptr[n];
+    F.St.col.assign(total, 0);
+    F.St.val.assign(total, 0.0);
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      std::vector<double> x(n, 0.0);
+      for (;;) {
+        const int j0 = next.fetch_add(64);
+        if (j0 >= n) break;
+        for (int j = j0; j < std::min(n, j0 + 64); ++j) {
+          int64_t p = F.St.ptr[j];
+          x[j] = 1.0;
+          for (int i = j; i != -1; i = F.parent[i]) {
+            x[i] /= Ldiag[i];
+            const double xi = x[i];
+            for (auto& e : Lcol[i]) x[e.first] -= e.second * xi;
+            F.St.col[p] = i;
+            F.St.val[p] = xi;
+            x[i] = 0.0;
+            ++p;
+          }
+        }
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
     // S by rows (transpose of St)
     F.S.n = n;
     F.S.ptr.assign(n + 1, 0);

@@ -112,7 +112,12 @@ struct Scene {
   DevBuf scal;                    // double scalars
   DevBuf io;                      // staging for host-memory calls
   DevBuf gmres;                   // GMRES basis + Hessenberg
+  DevBuf fgmres;                  // flexible GMRES: preconditioned basis Z
+  DevBuf capfull;                 // full capacitance of scenes solved iteratively (FP64 D, C; FP32 C)
+  DevBuf inner;                   // inner GMRES on the capacitance: basis and scratch
   DevBuf fwd;                     // forward Newton vectors
+  DevBuf fibre;                   // double [nt][3] actuation fibres (empty: none set)
+  DevBuf actf;                    // forward: f_ext + actuation force [3 nv]; adjoint: dL/da staging
   DevBuf vec32;                   // FP32 scratch of the mixed path
   int* flags_host = nullptr;      // pinned
   double* scal_host = nullptr;    // pinned
@@ -124,6 +129,7 @@ struct Ctx {
   int device = 0;
   int sm_count = 0;
   int coop_ok = 0;
+  DevBuf inv_mat, inv_work;  // workspace of ncpadj_dense_inverse
 };
 
 // kernels launch helpers (kernels.cu)

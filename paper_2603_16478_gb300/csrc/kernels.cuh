@@ -100,11 +100,17 @@ void launch_scale_by_scene(int nv, double* x, const int32_t* scene_of_vertex, co
 
 // ---- forward step (elem.cu) ----------------------------------------------------------------
 // qt = q_prev + h v_prev + h^2 (g + f_ext / m)
+// f += -sum_i V_i G_i^T vec(a_i d_i d_i^T) (actuation force; f holds f_ext on entry)
+void launch_act_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const float* act,
+                      const double* fibre, double* f, cudaStream_t s);
+// out[i] = -h^2 V_i d_i^T Z_i d_i with Z_i = unvec(G_i z) (FP32 output)
+void launch_act_grad(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* fibre,
+                     const double* z, double h, float* out, cudaStream_t s);
 void launch_predict(int nv, const double* q_prev, const double* v_prev, const double* f_ext, const double* mass,
                     double g0, double g1, double g2, double h, double* qt, cudaStream_t s);
 // q[v_c] += max(0, gap0 - delta_n) n_c  (start point inside the local-solve domain)
 void launch_lift(int nc, const int32_t* vertex, const double* frame, const double* d_n, double gap0, double* q,
-                 cudaStream_t s);
+                 const double* q_prev, const double* d_f, cudaStream_t s);
 // R = M (q - qt)
 void launch_inertia(int nv, const double* mass, const double* q, const double* qt, double* R, cudaStream_t s);
 // R[v_a] += h^2 w_i (F - p(F)) g_a  (elastic force of Eq. internal)
@@ -117,12 +123,17 @@ void launch_local_contact(const ContactArgs& a, double* lambda, double* slip, in
                           cudaStream_t s);
 // FLAG_TURN if a loaded contact's slip turned by more than 60 degrees from slip_old
 void launch_turn_check(int nc, const double* slip_old, const double* slip_new, const int* loaded, int* flags,
-                       cudaStream_t s);
+                       const int32_t* cvertex, double* R, cudaStream_t s);
+// q_out = q + t[scene(v)] dx per vertex (per-scene step lengths of a batch)
+void launch_step_by_scene(int nv, const double* q, const double* dx, const int32_t* sov, const double* t,
+                          double* q_out, cudaStream_t s);
 
 // ---- linear algebra (linalg.cu) ---------------------------------------------------------
 // y = B x for the 3x3-block matrix (FP64)
 void launch_bsr_spmv(int nv, const int32_t* row_ptr, const int32_t* col, const double* val,
                      const double* x, double* y, cudaStream_t s);
+// y = C x, C dense row-major FP32 [n][n], x and y double [n]
+void launch_dense_gemv32(int n, const float* Cm, const double* x, double* y, cudaStream_t s);
 void launch_bsr_spmv32(int nv, const int32_t* row_ptr, const int32_t* col, const float* val,
                        const double* x, double* y, cudaStream_t s);
 // inverse of the scalar diagonal of the block matrix
@@ -146,6 +157,19 @@ struct SinvArgs {
   const float *S_val32 = nullptr, *St_val32 = nullptr;  // FP32 copies (mixed precision)
 };
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
+// the two halves of A^{-1} = P^T S^T S P: w = S P x (position space, zeroed first), y = P^T S^T w
+void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s);
+void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s);
+void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s);
+void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s);
+// s_c = K'_c F_c (A^{-1} x)_{v_c} from w = S P x, along the elimination-tree paths of the contact
+// vertices (w: double, or w32 float with the FP32 values when w32 is not null)
+void launch_path_gather(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* w,
+                        const float* w32, const double* frame, const double* cdata, int transpose, double* sc,
+                        cudaStream_t s);
+// w += coef S P J^T t (contact forces t in frame coordinates), along the same paths
+void launch_path_scatter(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* frame,
+                         const double* t, double coef, double* w, float* w32, cudaStream_t s);
 // the same with FP32 values and intermediate (x32, w32 [nv][3] float scratch); y accumulated in FP64
 void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s);
 
@@ -162,6 +186,18 @@ bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flag
 size_t gj_scratch_bytes(int n, int sm_count);
 // FP32 blocked variant (one grid barrier per panel); tmp is an n x n scratch
 bool launch_gj_invert32(int n, float* C, float* tmp, int32_t* piv, int* flags, int sm_count, cudaStream_t s);
+// Column-owned blocked Gauss-Jordan (gj.cu): same result convention as launch_gj_invert.  scratch
+// holds gj_cols_scratch_bytes(n) bytes and must be zero before its first use (the kernel leaves its
+// flags zero).  Returns false without launching when n > gj_cols_max_dim() or the launch is refused.
+size_t gj_cols_scratch_bytes(int n, bool fp32);
+int gj_cols_max_dim();
+// the first gj_cols_reserved_bytes() of that scratch hold its flags: other users of the same
+// buffer must start after them
+size_t gj_cols_reserved_bytes();
+bool launch_gj_cols32(int n, float* C, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s);
+bool launch_gj_cols64(int n, double* C, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s);
+// out[k][piv[k']] = B[piv[k]][k']: the plain inverse from the Gauss-Jordan result B (float or double)
+void launch_unpermute_inverse(int n, const void* B, bool fp32, const int32_t* piv, double* out, cudaStream_t s);
 void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                        cudaStream_t s);
 void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s);
@@ -181,7 +217,11 @@ void launch_rhs(int n, const double* dL_dq, const double* dL_dv, double inv_h, d
 void launch_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y,
                       cudaStream_t s);
 void launch_mul(int n, const double* a, const double* b, double* y, cudaStream_t s);
-// out[k] = sum_i V_k[i] w[i], k < nvec (vectors of length n, stride ld); partials scratch
+// out[k] = sum_i V_k[i] w[i], k < nvec <= kMaxDotVectors (vectors of length n, stride ld); partial is a
+// scratch of dot_scratch_bytes() whose trailing counters must be zero before the first use (the
+// kernel leaves them zero)
+constexpr int kMaxDotVectors = 520;
+inline size_t dot_scratch_bytes() { return sizeof(double) * 64 * kMaxDotVectors + sizeof(unsigned) * kMaxDotVectors; }
 void launch_multi_dot(int n, int nvec, const double* V, long ld, const double* w, double* partial, double* out,
                       cudaStream_t s);
 // w -= sum_k coef[k] V_k (coef on device); if add_to != null also add_to[k] += coef[k]

@@ -57,6 +57,109 @@ __global__ void k_bsr_spmv32(int nv, const int32_t* __restrict__ rp, const int32
   y[i] = acc;
 }
 
+// Half a warp per vertex row: lane l of the half takes blocks rp[v] + l, rp[v] + l + 16, ... and the
+// three row sums are reduced over the half-warp (the row-per-thread form left the GPU nearly empty:
+// one thread per scalar row, each walking its ~15 blocks with dependent loads).
+template <typename V>
+__global__ void __launch_bounds__(256) k_bsr_spmv_hw(int nv, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const V* __restrict__ val,
+                                                     const double* __restrict__ x, double* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = t >> 4, l = t & 15;
+  const bool live = v < nv;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  if (live) {
+    const int pe = rp[v + 1];
+    for (int p = rp[v] + l; p < pe; p += 16) {
+      const int c = col[p];
+      const V* B = val + 9 * (size_t)p;
+      const double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+      a0 += (double)B[0] * x0 + (double)B[1] * x1 + (double)B[2] * x2;
+      a1 += (double)B[3] * x0 + (double)B[4] * x1 + (double)B[5] * x2;
+      a2 += (double)B[6] * x0 + (double)B[7] * x1 + (double)B[8] * x2;
+    }
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (live && l == 0) {
+    y[3 * (size_t)v] = a0;
+    y[3 * (size_t)v + 1] = a1;
+    y[3 * (size_t)v + 2] = a2;
+  }
+}
+
+// x[k] = sum_j B[piv[k]][j] y[piv[j]]: the Gauss-Jordan result B applied to y with both permutations.
+// A block stages y[piv[.]] (as T) in shared memory, then two warps per row split the columns, each
+// lane with four independent accumulators; T = float accumulates in FP32 (preconditioner apply).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cap_apply(int n, const T* __restrict__ B, const int32_t* __restrict__ piv,
+                                                   const double* __restrict__ y, double* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* ys = reinterpret_cast<T*>(smraw);
+  __shared__ T part[4][2];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) ys[j] = (T)y[piv[j]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rloc = warp >> 1, half = warp & 1;
+  const int k = blockIdx.x * 4 + rloc;
+  T acc = 0;
+  if (k < n) {
+    const T* row = B + (size_t)piv[k] * n;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int j = half * 32 + lane;
+    for (; j + 192 < n; j += 256) {
+      a0 += row[j] * ys[j];
+      a1 += row[j + 64] * ys[j + 64];
+      a2 += row[j + 128] * ys[j + 128];
+      a3 += row[j + 192] * ys[j + 192];
+    }
+    for (; j < n; j += 64) a0 += row[j] * ys[j];
+    acc = (a0 + a1) + (a2 + a3);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) part[rloc][half] = acc;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int kk = blockIdx.x * 4 + threadIdx.x;
+    if (kk < n) x[kk] = (double)(part[threadIdx.x][0] + part[threadIdx.x][1]);
+  }
+}
+
+// y = C x for a dense row-major FP32 matrix (the full contact capacitance of the inner solve):
+// two warps per row, four independent accumulators per lane, x read in double from L2.
+__global__ void __launch_bounds__(256) k_dense_gemv32(int n, const float* __restrict__ Cm, const double* __restrict__ x,
+                                                      double* __restrict__ y) {
+  __shared__ float part[4][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rloc = warp >> 1, half = warp & 1;
+  const int k = blockIdx.x * 4 + rloc;
+  float acc = 0.0f;
+  if (k < n) {
+    const float* row = Cm + (size_t)k * n;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int j = half * 32 + lane;
+    for (; j + 192 < n; j += 256) {
+      a0 += row[j] * (float)x[j];
+      a1 += row[j + 64] * (float)x[j + 64];
+      a2 += row[j + 128] * (float)x[j + 128];
+      a3 += row[j + 192] * (float)x[j + 192];
+    }
+    for (; j < n; j += 64) a0 += row[j] * (float)x[j];
+    acc = (a0 + a1) + (a2 + a3);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) part[rloc][half] = acc;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int kk = blockIdx.x * 4 + threadIdx.x;
+    if (kk < n) y[kk] = (double)(part[threadIdx.x][0] + part[threadIdx.x][1]);
+  }
+}
+
 __global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * nv) return;
@@ -105,6 +208,73 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
     atomicAdd(&y[3 * o], (Y)a0);
     atomicAdd(&y[3 * o + 1], (Y)a1);
     atomicAdd(&y[3 * o + 2], (Y)a2);
+  }
+}
+
+// Contact rows of A^{-1} x from w = S P x: (A^{-1} x)_v = sum_i S[i][p(v)] w_i, and column p(v) of S
+// (row p(v) of S^T) lives on the elimination-tree path from p(v) to the root.  One warp per
+// contact walks that path; the result u_c is turned into s_c = K'_c F_c u_c at once (K' = K^T for
+// the adjoint), the input of the capacitance solve.
+template <typename V, typename W>
+__global__ void __launch_bounds__(256) k_path_gather(int nc, const int32_t* __restrict__ cvertex,
+                                                     const int32_t* __restrict__ iperm, const int64_t* __restrict__ ptr,
+                                                     const int32_t* __restrict__ col, const V* __restrict__ val,
+                                                     const W* __restrict__ w, const double* __restrict__ frame,
+                                                     const double* __restrict__ cdata, int transpose,
+                                                     double* __restrict__ sc) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nc) return;
+  const int pv = iperm[cvertex[c]];
+  const int64_t b = ptr[pv], e = ptr[pv + 1];
+  double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+  for (int64_t p = b + lane; p < e; p += 32) {
+    const int i = col[p];
+    const double sv = (double)val[p];
+    u0 += sv * (double)w[3 * (size_t)i];
+    u1 += sv * (double)w[3 * (size_t)i + 1];
+    u2 += sv * (double)w[3 * (size_t)i + 2];
+  }
+  u0 = warp_sum(u0);
+  u1 = warp_sum(u1);
+  u2 = warp_sum(u2);
+  if (lane == 0) {
+    const double* F = frame + 9 * (size_t)c;
+    const double* K = cdata + 12 * (size_t)c;
+    double y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = F[3 * i] * u0 + F[3 * i + 1] * u1 + F[3 * i + 2] * u2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      sc[3 * c + j] = transpose ? K[j] * y[0] + K[3 + j] * y[1] + K[6 + j] * y[2]
+                                : K[3 * j] * y[0] + K[3 * j + 1] * y[1] + K[3 * j + 2] * y[2];
+  }
+}
+
+// w += coef S P J^T t: contact c's force F_c^T t_c at vertex v_c enters S P x through column p(v_c)
+// of S, i.e. along the elimination-tree path of p(v_c) (one warp per contact, atomics).
+template <typename V, typename W>
+__global__ void __launch_bounds__(256) k_path_scatter(int nc, const int32_t* __restrict__ cvertex,
+                                                      const int32_t* __restrict__ iperm, const int64_t* __restrict__ ptr,
+                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
+                                                      const double* __restrict__ frame, const double* __restrict__ t,
+                                                      double coef, W* w) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nc) return;
+  const double* F = frame + 9 * (size_t)c;
+  const double t0 = t[3 * c], t1 = t[3 * c + 1], t2 = t[3 * c + 2];
+  const double f0 = coef * (F[0] * t0 + F[3] * t1 + F[6] * t2);
+  const double f1 = coef * (F[1] * t0 + F[4] * t1 + F[7] * t2);
+  const double f2 = coef * (F[2] * t0 + F[5] * t1 + F[8] * t2);
+  const int pv = iperm[cvertex[c]];
+  const int64_t b = ptr[pv], e = ptr[pv + 1];
+  for (int64_t p = b + lane; p < e; p += 32) {
+    const int i = col[p];
+    const double sv = (double)val[p];
+    atomicAdd(&w[3 * (size_t)i], (W)(sv * f0));
+    atomicAdd(&w[3 * (size_t)i + 1], (W)(sv * f1));
+    atomicAdd(&w[3 * (size_t)i + 2], (W)(sv * f2));
   }
 }
 
@@ -546,6 +716,45 @@ __global__ void k_multi_dot_partial(int n, const double* __restrict__ V, long ld
     if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = v;
   }
 }
+// out[k] = V_k . w in one launch: every block writes its partial for vector k (blockIdx.y), and the
+// last block to finish (counted in cnt[k], which it resets) reduces the partials in a fixed order.
+__global__ void k_multi_dot_fused(int n, const double* __restrict__ V, long ld, const double* __restrict__ w,
+                                  double* partial, unsigned* cnt, double* out) {
+  const int k = blockIdx.y;
+  const double* vk = V + (size_t)k * ld;
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    acc += vk[i] * w[i];
+  acc = warp_sum(acc);
+  __shared__ double sh[32];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      partial[(size_t)k * gridDim.x + blockIdx.x] = v;
+      __threadfence();
+      last = atomicAdd(&cnt[k], 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(&partial[(size_t)k * gridDim.x + i]);
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    out[k] = r;
+    cnt[k] = 0;
+  }
+}
+
 __global__ void k_multi_dot_final(int nparts, const double* partial, double* out) {
   const int k = blockIdx.x;
   double acc = 0.0;
@@ -634,12 +843,16 @@ __global__ void k_nonfinite(int n, const double* x, int* flags) {
 void launch_bsr_spmv(int nv, const int32_t* rp, const int32_t* col, const double* val, const double* x, double* y,
                      cudaStream_t s) {
   g_launches += 1;
-  k_bsr_spmv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+  k_bsr_spmv_hw<double><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
 }
 void launch_bsr_spmv32(int nv, const int32_t* rp, const int32_t* col, const float* val, const double* x, double* y,
                        cudaStream_t s) {
   g_launches += 1;
-  k_bsr_spmv32<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+  k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+}
+void launch_dense_gemv32(int n, const float* Cm, const double* x, double* y, cudaStream_t s) {
+  g_launches += 1;
+  if (n) k_dense_gemv32<<<(n + 3) / 4, 256, 0, s>>>(n, Cm, x, y);
 }
 void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
                      cudaStream_t s) {
@@ -661,6 +874,55 @@ void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, d
   cudaMemsetAsync(y, 0, sizeof(double) * n, s);
   k_spmv_chunks<float, float, double, float><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend,
                                                                              a.St_col, a.St_val32, a.perm, w32, y);
+}
+
+void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s) {
+  g_launches += 1;
+  cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
+  k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend,
+                                                                              a.S_col, a.S_val, nullptr, x, w);
+}
+void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s) {
+  g_launches += 1;
+  cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
+  k_spmv_chunks<double, double, double><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg,
+                                                                               a.St_cend, a.St_col, a.St_val, a.perm,
+                                                                               w, y);
+}
+void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s) {
+  g_launches += 1;
+  cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
+  k_spmv_chunks<float, double, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, x, w32);
+}
+void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s) {
+  g_launches += 1;
+  cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
+  k_spmv_chunks<float, float, double, float><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(
+      a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val32, a.perm, w32, y);
+}
+void launch_path_gather(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* w,
+                        const float* w32, const double* frame, const double* cdata, int transpose, double* sc,
+                        cudaStream_t s) {
+  g_launches += 1;
+  if (!nc) return;
+  if (w32)
+    k_path_gather<float, float><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
+                                                                    a.St_val32, w32, frame, cdata, transpose, sc);
+  else
+    k_path_gather<double, double><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
+                                                                      a.St_val, w, frame, cdata, transpose, sc);
+}
+void launch_path_scatter(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* frame,
+                         const double* t, double coef, double* w, float* w32, cudaStream_t s) {
+  g_launches += 1;
+  if (!nc) return;
+  if (w32)
+    k_path_scatter<float, float><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
+                                                                     a.St_val32, frame, t, coef, w32);
+  else
+    k_path_scatter<double, double><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
+                                                                       a.St_val, frame, t, coef, w);
 }
 
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s) {
@@ -750,15 +1012,15 @@ void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s) {
 }
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                      cudaStream_t s) {
-  g_launches += 2;
-  k_gather_perm<<<nblk(n, 256), 256, 0, s>>>(n, piv, y, ytmp);
-  k_gemv_rows_perm<double><<<nblk(32L * n, 256), 256, 0, s>>>(n, B, piv, ytmp, x);
+  (void)ytmp;
+  g_launches += 1;
+  k_cap_apply<double><<<(n + 3) / 4, 256, sizeof(double) * (size_t)n, s>>>(n, B, piv, y, x);
 }
 void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                        cudaStream_t s) {
-  g_launches += 2;
-  k_gather_perm<<<nblk(n, 256), 256, 0, s>>>(n, piv, y, ytmp);
-  k_gemv_rows_perm<float><<<nblk(32L * n, 256), 256, 0, s>>>(n, B, piv, ytmp, x);
+  (void)ytmp;
+  g_launches += 1;
+  k_cap_apply<float><<<(n + 3) / 4, 256, sizeof(float) * (size_t)n, s>>>(n, B, piv, y, x);
 }
 void launch_contact_gather_kt(int nc, const int32_t* cv, const double* frame, const double* cdata, int transpose,
                               const double* u, double* sc, cudaStream_t s) {
@@ -790,11 +1052,12 @@ void launch_mul(int n, const double* a, const double* b, double* y, cudaStream_t
 }
 void launch_multi_dot(int n, int nvec, const double* V, long ld, const double* w, double* partial, double* out,
                       cudaStream_t s) {
-  g_launches += 2;
+  // partial holds 64 * nvec doubles followed by nvec zero-initialised counters (see dot_scratch_doubles)
+  g_launches += 1;
   int nb = nblk(n, 256);
   if (nb > 64) nb = 64;
-  k_multi_dot_partial<<<dim3(nb, nvec), 256, 0, s>>>(n, V, ld, w, partial);
-  k_multi_dot_final<<<nvec, 64, 0, s>>>(nb, partial, out);
+  unsigned* cnt = reinterpret_cast<unsigned*>(partial + 64 * (size_t)kMaxDotVectors);
+  k_multi_dot_fused<<<dim3(nb, nvec), 256, 0, s>>>(n, V, ld, w, partial, cnt, out);
 }
 void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {
   g_launches += 1;

@@ -62,12 +62,17 @@ def hex_tet_mesh(nx: int, ny: int, nz: int, cell: float, origin=(0.0, 0.0, 0.0))
 
 @dataclass
 class Plane:
-    """Rigid plane {x : n.x = offset} with friction coefficient mu; frame rows n, t1, t2."""
+    """Rigid plane {x : n.x = offset} with friction coefficient mu; frame rows n, t1, t2.
+
+    ``regions`` (optional) splits the plane into a grid of friction regions in its (t1, t2)
+    coordinates: (n1, n2, lo1, hi1, lo2, hi2, mu_values [n1*n2]); a contact then takes the
+    friction coefficient of its cell, and contacts are listed cell by cell."""
     normal: np.ndarray
     offset: float
     mu: float
     t1: np.ndarray = None
     t2: np.ndarray = None
+    regions: tuple = None
 
     def __post_init__(self):
         self.normal = np.asarray(self.normal, float)
@@ -115,22 +120,39 @@ def detect_contacts(x_prev: np.ndarray, planes, margin: float, candidates=None) 
     """Vertices whose gap to a plane at the previous positions is below ``margin``.
 
     ``candidates`` restricts the search to a vertex subset (e.g. a bottom face).
-    Friction regions: one region per plane.
+    Friction regions: one region per plane, or the plane's grid of regions (listed in order,
+    contacts grouped by region and ordered by position inside it).
     """
     verts = np.arange(x_prev.shape[0]) if candidates is None else np.asarray(candidates)
     vs, frames, dn, mus, reg = [], [], [], [], []
-    for pi, pl in enumerate(planes):
+    base = 0
+    for pl in planes:
         gap = x_prev[verts] @ pl.normal - pl.offset
         sel = verts[gap < margin]
-        vs.append(sel)
+        if pl.regions is None:
+            vs.append(sel)
+            mus.append(np.full(len(sel), pl.mu))
+            reg.append(np.full(len(sel), base))
+            base += 1
+        else:
+            n1, n2, lo1, hi1, lo2, hi2, mu_vals = pl.regions
+            u = x_prev[sel] @ pl.t1
+            v = x_prev[sel] @ pl.t2
+            i1 = np.clip(((u - lo1) / (hi1 - lo1) * n1).astype(int), 0, n1 - 1)
+            i2 = np.clip(((v - lo2) / (hi2 - lo2) * n2).astype(int), 0, n2 - 1)
+            cell = i1 + n1 * i2
+            order = np.lexsort((u, v, cell))
+            sel, cell = sel[order], cell[order]
+            vs.append(sel)
+            mus.append(np.asarray(mu_vals, float)[cell])
+            reg.append(base + cell)
+            base += n1 * n2
         frames.append(np.repeat(pl.frame[None], len(sel), 0))
         dn.append(np.full(len(sel), pl.offset))
-        mus.append(np.full(len(sel), pl.mu))
-        reg.append(np.full(len(sel), pi))
     v = np.concatenate(vs).astype(np.int32)
     return Contacts(v, np.concatenate(frames).reshape(-1, 3, 3), np.concatenate(dn),
                     np.zeros((len(v), 2)), np.concatenate(mus), np.concatenate(reg).astype(np.int32),
-                    max(1, len(planes)))
+                    max(1, base))
 
 
 # --------------------------------------------------------------------------------------
@@ -221,6 +243,67 @@ def beam_incline(seed: int = 0, nx: int = 40, ny: int = 10, nz: int = 10, cell: 
                   np.array([0.0, 0.0, -GRAVITY]), [Plane(n, 0.0, mu, t1, [0.0, 1.0, 0.0])], bottom,
                   margin, eps, f"beam{nx}x{ny}x{nz}")
     return Problem(scene, X.copy(), np.zeros_like(X), np.zeros_like(X), X.copy())
+
+
+def jittered_delaunay_ball(r: float = 0.1, cap: float = 0.05, cell: float = 4.5e-3, jitter: float = 0.2,
+                           seed: int = 0, min_quality: float = 1e-2):
+    """Tet mesh of the ball |x| <= r cut flat at |z| <= cap: a cubic lattice of spacing ``cell``
+    jittered by +-jitter*cell (uniform, seeded) inside the body, jittered square lattices on the
+    two cut discs, Delaunay-tetrahedralised (scipy.spatial).  Tets below ``min_quality`` times the
+    lattice tet volume cell^3/6 (slivers) are dropped, and vertices left without a tet removed.
+    Returns (X [n_v, 3], tets int32 [n_t, 4] positively oriented)."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    n = int(np.ceil(r / cell)) + 1
+    g = np.arange(-n, n + 1) * cell
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    P = P + rng.uniform(-jitter, jitter, P.shape) * cell
+    P = P[(np.linalg.norm(P, axis=1) <= r) & (np.abs(P[:, 2]) <= cap - 0.5 * cell)]
+    rc = np.sqrt(r * r - cap * cap)
+    Q = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    discs = []
+    for zc in (-cap, cap):
+        Qj = Q + rng.uniform(-jitter, jitter, Q.shape) * cell
+        Qj = Qj[np.linalg.norm(Qj, axis=1) <= rc]
+        discs.append(np.column_stack([Qj, np.full(len(Qj), zc)]))
+    P = np.vstack([P] + discs)
+    T = Delaunay(P).simplices.astype(np.int64)
+    e = P[T[:, 1:]] - P[T[:, [0]]]
+    vol = np.einsum("ij,ij->i", np.cross(e[:, 0], e[:, 1]), e[:, 2]) / 6.0
+    T[vol < 0] = T[vol < 0][:, [0, 2, 1, 3]]
+    T = T[np.abs(vol) >= min_quality * cell ** 3 / 6.0]
+    used = np.unique(T)
+    remap = -np.ones(len(P), np.int64)
+    remap[used] = np.arange(len(used))
+    return P[used], remap[T].astype(np.int32)
+
+
+def sphere_press(seed: int = 0, r: float = 0.1, cap: float = 0.05, cell: float = 4.5e-3, E: float = 1e5,
+                 nu: float = 0.4, density: float = 1000.0, h: float = 1.0 / 60.0, eps: float = 1e-4,
+                 press: float = 5e-4, gap0: float = 1e-7, margin: float = 2e-3, grid: int = 4,
+                 mu_range=(0.2, 1.0), tgt_sigma: float = 1e-3) -> Problem:
+    """Large contact-heavy scene: a Neo-Hookean ball (r = 0.1 m, flattened at |z| <= cap, the
+    contact patches of a pressed ball) resting on the ground z = -cap, with a kinematic plate on
+    top that moves down by ``press`` during the step.  Each plane carries a grid x grid of friction
+    regions over the cap disc with mu ~ U(mu_range) (seeded).  Default cell 4.5 mm: about 32k
+    vertices, 211k tets, ~2,000 contacts (both discs).  Starts at rest; target X + N(0, tgt_sigma^2).
+    """
+    X, tets = jittered_delaunay_ball(r, cap, cell, 0.2, seed)
+    rng = np.random.default_rng(seed + 1)
+    rc = np.sqrt(r * r - cap * cap)
+    planes = []
+    for k, (nrm, off) in enumerate((([0.0, 0.0, 1.0], -cap - gap0), ([0.0, 0.0, -1.0], -(cap + gap0 - press)))):
+        t1 = np.array([1.0, 0.0, 0.0])
+        t2 = np.cross(nrm, t1)
+        lo1, hi1 = (-rc, rc)
+        lo2, hi2 = (-rc, rc) if t2[1] > 0 else (-rc, rc)
+        mu_vals = rng.uniform(mu_range[0], mu_range[1], grid * grid)
+        planes.append(Plane(nrm, off, float(mu_vals.mean()), t1, t2, (grid, grid, lo1, hi1, lo2, hi2, mu_vals)))
+    on_disc = np.nonzero(np.abs(np.abs(X[:, 2]) - cap) < 1e-12)[0]
+    scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), density, h,
+                  np.array([0.0, 0.0, -GRAVITY]), planes, on_disc, margin, eps, f"sphere{len(X)}")
+    q_tgt = X + rng.normal(0.0, tgt_sigma, X.shape)
+    return Problem(scene, X.copy(), np.zeros_like(X), np.zeros_like(X), q_tgt)
 
 
 def two_tet(seed: int = 0, E: float = 1e5, nu: float = 0.4, h: float = 1.0 / 60.0, mu: float = 0.5,

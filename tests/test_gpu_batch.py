@@ -98,3 +98,42 @@ def test_batch_rejects_ungrouped_contacts(pkg):
     lam = T(np.concatenate([xb.lam_frame(sb, qb), xa.lam_frame(sa, qa)]))
     with pytest.raises(pkg.NcpadjError, match="grouped by scene"):
         pkg.adjoint_step(batch, contacts, q, T(np.concatenate([qa, qb])), lam, torch.ones_like(q), None)
+
+
+def test_batched_forward_reaches_every_scenes_own_state(pkg):
+    """One forward call over a batch (per-scene line searches) converges every scene to the state its
+    own single-scene forward reaches, including scenes that need heavily damped steps."""
+    ctx = pkg.Context(0)
+    from tests._cases import rollout
+    starts = [rollout("cube_drop", 2), rollout("two_tet", 1), rollout("cube_drop", 5), rollout("cube_drop", 0),
+              rollout("cube_drop", 4)]
+    meshes, singles = [], []
+    for pb, q_prev, v_prev in starts:
+        sc = pb.scene
+        meshes.append((sc.X, sc.tets, sc.E, sc.nu, sc.density))
+        scene1 = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+        ct = sc.contacts(q_prev)
+        c1 = None if ct.n == 0 else pkg.Contacts(T(ct.vertex, torch.int32), T(ct.frame), T(ct.d_n), T(ct.mu),
+                                                  None, T(ct.region, torch.int32), ct.n_regions)
+        q1, _, st1 = pkg.forward_step(scene1, c1, T(q_prev), T(v_prev), None, tuple(sc.gravity), eps=sc.eps,
+                                      newton_tol=1e-11)
+        singles.append((q1.cpu().numpy(), ct))
+    batch = pkg.Scene.batch(ctx, meshes, starts[0][0].scene.h)
+    off = batch.vertex_offsets
+    vert, frame, dn, mu, region = [], [], [], [], []
+    for i, (q1, ct) in enumerate(singles):
+        vert.append(ct.vertex + off[i])
+        frame.append(ct.frame)
+        dn.append(ct.d_n)
+        mu.append(ct.mu)
+        region.append(np.full(ct.n, i, np.int32))
+    contacts = pkg.Contacts(T(np.concatenate(vert), torch.int32), T(np.concatenate(frame)), T(np.concatenate(dn)),
+                            T(np.concatenate(mu)), None, T(np.concatenate(region), torch.int32), len(starts))
+    q0 = T(np.concatenate([s[1] for s in starts]))
+    v0 = T(np.concatenate([s[2] for s in starts]))
+    qb, lamb, stb = pkg.forward_step(batch, contacts, q0, v0, None, tuple(starts[0][0].scene.gravity),
+                                     eps=starts[0][0].scene.eps, newton_tol=1e-11, max_newton=120)
+    qb = qb.cpu().numpy()
+    for i, ((q1, _), (pb, q_prev, _)) in enumerate(zip(singles, starts)):
+        seg = qb[off[i]:off[i + 1]]
+        assert rel(seg - q_prev, q1 - q_prev) < 1e-7, (i, rel(seg - q_prev, q1 - q_prev))
