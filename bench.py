@@ -159,7 +159,15 @@ def batched(pkg, torch, dev, steps, warmup):
     nc = sum(len(v) for v in verts)
     contacts = pkg.Contacts(T(np.concatenate(verts), torch.int32), T(np.concatenate(frames)), T(np.concatenate(dn)),
                             T(np.concatenate(mu)), None, T(np.concatenate(reg), torch.int32), len(blocks))
-    q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(blocks[0].scene.gravity), eps=blocks[0].scene.eps)
+    # impacts at up to ~0.15 m/s make some blocks' Newton solves long: the adjoint is timed at the
+    # iterate reached within 150 steps, whose residual is reported
+    try:
+        q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(blocks[0].scene.gravity),
+                                      eps=blocks[0].scene.eps, max_newton=150)
+    except pkg.NcpadjError as e:
+        if not hasattr(e, "state"):
+            raise
+        (q, lam), fs = e.state, e.stats
     tgt = T(np.concatenate([b.q_target for b in blocks]))
     dq = 2 * (q - tgt)
     stream = torch.cuda.Stream(dev)
@@ -196,7 +204,8 @@ def batched(pkg, torch, dev, steps, warmup):
                         f"(log-uniform 2k..50k tets each), {nc} contacts in {sum(1 for v in verts if len(v))} blocks, "
                         "one adjoint step of every block per call",
             "fp64": res["fp64"], "mixed": res["mixed"], "max_rel_err_mixed_vs_fp64": err,
-            "scene_build_s": t_build, "nnz_Linv": info["nnz_Linv"], "forward_newton_iters": fs["newton_iters"]}
+            "scene_build_s": t_build, "nnz_Linv": info["nnz_Linv"], "forward_newton_iters": fs["newton_iters"],
+            "forward_residual": fs["residual"]}
 
 
 def sphere(pkg, torch, dev, steps, warmup):

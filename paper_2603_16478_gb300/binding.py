@@ -340,7 +340,10 @@ def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None
                                  float(newton_tol), int(max_newton), _ptr(q), _ptr(lam), C.byref(stats),
                                  C.c_void_p(stream or 0))
     if st != 0:
-        raise NcpadjError(st, lib.ncpadj_last_error().decode(), stats.to_dict())
+        err = NcpadjError(st, lib.ncpadj_last_error().decode(), stats.to_dict())
+        if status_name(st) == "NOT_CONVERGED":
+            err.state = (q, lam[:nc])  # the last iterate (its residual is in err.stats)
+        raise err
     return q, lam[:nc], stats.to_dict()
 
 

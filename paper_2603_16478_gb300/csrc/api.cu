@@ -288,7 +288,8 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
   S.flags.ensure(FLAG_COUNT * sizeof(int));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
-  NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_host, (2 * 513 + 1) * sizeof(double)));
+  NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_host, 2 * (2 * 513 + 1) * sizeof(double)));  // two slots
+  for (auto& e : S.gs_ev) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (auto& e : S.ev) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
 }
 
@@ -784,7 +785,11 @@ struct Engine {
           std::fill(g.begin(), g.end(), 0.0);
           g[0] = beta;
           int k = 0;
-          for (int j = 0; j < m; ++j) {
+          // Arnoldi step j on the device; its coefficients go to pinned slot j % 2 with an event.
+          // The host enqueues step j + 1 before it reads step j's coefficients, so the GPU never
+          // waits for the host's Givens update (a converged cycle leaves one step unused).
+          const size_t slot = 2 * (size_t)(m + 1) + 1;
+          auto enqueue_step = [&](int j) {
             double* vn = V + (size_t)(j + 1) * N;
             double* zj = flexible ? Z + (size_t)j * N : w;
             apply_precond(V + (size_t)j * N, zj);
@@ -795,11 +800,18 @@ struct Engine {
             launch_multi_axpy(N, j + 1, V, N, gs + (m + 1), vn, st);
             launch_multi_dot(N, 1, vn, N, vn, partial, nrm2, st);
             launch_normalize(N, vn, nrm2, vn, gs + 2 * (m + 1), st);
-            NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_host, gs, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, st));
-            NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+            NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_host + (j & 1) * slot, gs, sizeof(double) * slot,
+                                            cudaMemcpyDeviceToHost, st));
+            NCPADJ_CUDA_TRY(cudaEventRecord(S.gs_ev[j & 1], st));
+          };
+          enqueue_step(0);
+          for (int j = 0; j < m; ++j) {
+            if (j + 1 < m && iters + 1 < max_iters) enqueue_step(j + 1);
+            NCPADJ_CUDA_TRY(cudaEventSynchronize(S.gs_ev[j & 1]));
+            const double* gh = S.gs_host + (j & 1) * slot;
             double* h = &H[(size_t)(m + 1) * j];
-            for (int i = 0; i <= j; ++i) h[i] = S.gs_host[i] + S.gs_host[m + 1 + i];
-            h[j + 1] = S.gs_host[2 * (m + 1)];
+            for (int i = 0; i <= j; ++i) h[i] = gh[i] + gh[m + 1 + i];
+            h[j + 1] = gh[2 * (m + 1)];
             for (int i = 0; i < j; ++i) {  // previous rotations
               const double t = cs[i] * h[i] + sn[i] * h[i + 1];
               h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
@@ -1459,6 +1471,8 @@ void ncpadj_scene_destroy(ncpadj_scene s) {
   if (s->s.flags_host) cudaFreeHost(s->s.flags_host);
   if (s->s.scal_host) cudaFreeHost(s->s.scal_host);
   if (s->s.gs_host) cudaFreeHost(s->s.gs_host);
+  for (auto e : s->s.gs_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& e : s->s.ev)
     if (e) cudaEventDestroy(e);
   delete s;

@@ -123,6 +123,7 @@ struct Scene {
   double* scal_host = nullptr;    // pinned
   double* gs_host = nullptr;      // pinned: Gram-Schmidt coefficients of one GMRES iteration
   cudaEvent_t ev[8] = {};
+  cudaEvent_t gs_ev[2] = {};       // GMRES: coefficients of step j landed in pinned slot j % 2
 };
 
 struct Ctx {

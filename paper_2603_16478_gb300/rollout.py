@@ -46,6 +46,7 @@ class Simulator:
     cap_precision: str = "fp64"
     rtol: float = 1e-8
     newton_tol: float = 1e-10
+    max_newton: int = 100
     _frames: dict = field(default_factory=dict)
 
     def contacts(self, q_prev: torch.Tensor, mu_region: torch.Tensor) -> Optional[Contacts]:
@@ -72,62 +73,73 @@ class Simulator:
                         torch.cat(dn).contiguous(), mu_region.detach()[region.long()].contiguous(), None,
                         region.contiguous(), self.n_regions)
 
-    def step(self, q_prev, v_prev, contacts, f_ext=None):
+    def step(self, q_prev, v_prev, contacts, f_ext=None, act=None):
         return forward_step(self.scene, contacts, q_prev.contiguous(), v_prev.contiguous(), f_ext, self.gravity,
-                            eps=self.eps, newton_tol=self.newton_tol)
+                            eps=self.eps, newton_tol=self.newton_tol, max_newton=self.max_newton,
+                            act=None if act is None else act.detach().contiguous())
 
 
 class StepFn(torch.autograd.Function):
-    """(q_prev, v_prev, E, nu, mu_region, f_ext) -> (q, v) for one implicit step.
+    """(q_prev, v_prev, E, nu, mu_region, f_ext, act) -> (q, v) for one implicit step.
 
     E and nu are scalar tensors equal to the scene's (uniform) material: the scene holds the
     elastic factor built for them, so the forward pass checks the values and the backward pass
     returns dL/dE and dL/dnu summed over tets.  mu_region [n_regions] sets every contact's
-    friction coefficient through its region.
+    friction coefficient through its region.  act (FP32 [n_tets] or None) are the per-tet
+    activations of the scene's fibres (constant active stress a_i d_i d_i^T).
     """
 
     @staticmethod
-    def forward(ctx, q_prev, v_prev, E, nu, mu_region, f_ext, sim: Simulator):
+    def forward(ctx, q_prev, v_prev, E, nu, mu_region, f_ext, act, sim: Simulator):
         contacts = sim.contacts(q_prev, mu_region)
-        q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext)
+        q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext, act)
         v = (q - q_prev) / sim.scene.h
         ctx.sim = sim
         ctx.has_fext = f_ext is not None
+        ctx.has_act = act is not None
         # save the inputs only: the converged state is recomputed in backward
-        ctx.save_for_backward(q_prev, v_prev, mu_region, f_ext if f_ext is not None else torch.empty(0))
+        ctx.save_for_backward(q_prev, v_prev, mu_region, f_ext if f_ext is not None else torch.empty(0),
+                              act if act is not None else torch.empty(0))
         return q, v
 
     @staticmethod
     def backward(ctx, gq, gv):
         sim: Simulator = ctx.sim
-        q_prev, v_prev, mu_region, f_ext = ctx.saved_tensors
+        q_prev, v_prev, mu_region, f_ext, act = ctx.saved_tensors
+        f_ext = f_ext if ctx.has_fext else None
+        act = act if ctx.has_act else None
         contacts = sim.contacts(q_prev, mu_region)
-        q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext if ctx.has_fext else None)
+        q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext, act)
         gq = torch.zeros_like(q) if gq is None else gq.contiguous()
         gv = torch.zeros_like(q) if gv is None else gv.contiguous()
+        want = ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu") + (("dL_dact",) if act is not None
+                                                                                      else ())
         g, _ = adjoint_step(sim.scene, contacts, q, q_prev, lam.contiguous(), gq, gv, eps=sim.eps, rtol=sim.rtol,
-                            precision=sim.precision, cap_precision=sim.cap_precision)
+                            precision=sim.precision, cap_precision=sim.cap_precision, want=want)
         d_mu = g["dL_dmu"] if contacts is not None else torch.zeros_like(mu_region)
         d_f = g["dL_dfext"] if ctx.has_fext else None
-        return (g["dL_dq_prev"], g["dL_dv_prev"], g["dL_dE"].sum(), g["dL_dnu"].sum(), d_mu, d_f, None)
+        d_a = g["dL_dact"] if act is not None else None
+        return (g["dL_dq_prev"], g["dL_dv_prev"], g["dL_dE"].sum(), g["dL_dnu"].sum(), d_mu, d_f, d_a, None)
 
 
-def rollout(sim: Simulator, q0, v0, E, nu, mu_region, n_steps: int, checkpoint_every: int = 0, f_ext=None):
+def rollout(sim: Simulator, q0, v0, E, nu, mu_region, n_steps: int, checkpoint_every: int = 0, f_ext=None,
+            act=None):
     """Run n_steps differentiable steps; returns (q_T, v_T).  With checkpoint_every = k > 0 the steps
-    are grouped in segments of k under torch.utils.checkpoint (forward recomputed in backward)."""
+    are grouped in segments of k under torch.utils.checkpoint (forward recomputed in backward).
+    ``act``: per-tet activations (FP32 [n_tets]) applied at every step (the scene needs fibres)."""
     q, v = q0, v0
 
-    def segment(q_, v_, E_, nu_, mu_, k):
+    def segment(q_, v_, E_, nu_, mu_, k, act_):
         for _ in range(k):
-            q_, v_ = StepFn.apply(q_, v_, E_, nu_, mu_, f_ext, sim)
+            q_, v_ = StepFn.apply(q_, v_, E_, nu_, mu_, f_ext, act_, sim)
         return q_, v_
 
     t = 0
     while t < n_steps:
         k = min(checkpoint_every, n_steps - t) if checkpoint_every > 0 else 1
         if checkpoint_every > 0:
-            q, v = checkpoint(segment, q, v, E, nu, mu_region, k, use_reentrant=False)
+            q, v = checkpoint(segment, q, v, E, nu, mu_region, k, act, use_reentrant=False)
         else:
-            q, v = segment(q, v, E, nu, mu_region, 1)
+            q, v = segment(q, v, E, nu, mu_region, 1, act)
         t += k
     return q, v

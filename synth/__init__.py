@@ -56,6 +56,30 @@ def hex_tet_mesh(nx: int, ny: int, nz: int, cell: float, origin=(0.0, 0.0, 0.0))
     return X, tets.astype(np.int32)
 
 
+def voxel_tet_mesh(occ: np.ndarray, cell: float, origin=(0.0, 0.0, 0.0)):
+    """Tet mesh of the occupied cells of a voxel grid ``occ`` [nx, ny, nz] (bool), each cell split
+    into 5 tets with the parity-alternating pattern of ``hex_tet_mesh`` (so the mesh is conforming
+    for any set of cells).  Unused lattice vertices are dropped.  Returns (X, tets int32)."""
+    occ = np.asarray(occ, bool)
+    nx, ny, nz = occ.shape
+    ci, cj, ck = np.nonzero(occ)
+    vid = lambda i, j, k: i + (nx + 1) * (j + (ny + 1) * k)  # noqa: E731
+    corners = np.stack([vid(ci + (c & 1), cj + ((c >> 1) & 1), ck + ((c >> 2) & 1)) for c in range(8)], 1)
+    even = ((ci + cj + ck) % 2 == 0)
+    tets = np.concatenate([np.where(even[:, None], corners[:, list(te)], corners[:, list(to)])
+                           for te, to in zip(_EVEN_SPLIT, _ODD_SPLIT)], 0).astype(np.int64)
+    used, inv = np.unique(tets, return_inverse=True)
+    tets = inv.reshape(tets.shape)
+    i = used % (nx + 1)
+    j = (used // (nx + 1)) % (ny + 1)
+    k = used // ((nx + 1) * (ny + 1))
+    X = np.stack([i * cell + origin[0], j * cell + origin[1], k * cell + origin[2]], 1).astype(np.float64)
+    e = X[tets[:, 1:]] - X[tets[:, [0]]]
+    neg = np.linalg.det(e) < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    return X, tets.astype(np.int32)
+
+
 # --------------------------------------------------------------------------------------
 # contacts
 # --------------------------------------------------------------------------------------
@@ -247,31 +271,39 @@ def beam_incline(seed: int = 0, nx: int = 40, ny: int = 10, nz: int = 10, cell: 
 
 def jittered_delaunay_ball(r: float = 0.1, cap: float = 0.05, cell: float = 4.5e-3, jitter: float = 0.2,
                            seed: int = 0, min_quality: float = 1e-2):
-    """Tet mesh of the ball |x| <= r cut flat at |z| <= cap: a cubic lattice of spacing ``cell``
-    jittered by +-jitter*cell (uniform, seeded) inside the body, jittered square lattices on the
-    two cut discs, Delaunay-tetrahedralised (scipy.spatial).  Tets below ``min_quality`` times the
-    lattice tet volume cell^3/6 (slivers) are dropped, and vertices left without a tet removed.
-    Returns (X [n_v, 3], tets int32 [n_t, 4] positively oriented)."""
+    """Tet mesh of the ball |x| <= r cut flat at |z| <= cap: points on a lattice of spacing ``cell``
+    in x, y and of nz = round(2 cap / cell) layers exactly spanning [-cap, cap] in z, jittered by
+    +-jitter*spacing (uniform, seeded; the two cut layers are not moved in z, so they stay on the
+    planes and the tets next to them are lattice-shaped), Delaunay-tetrahedralised
+    (scipy.spatial).  Tets below ``min_quality`` times the lattice tet volume (slivers) are dropped
+    and vertices left without a tet removed.  Returns (X [n_v, 3], tets int32 [n_t, 4], positively
+    oriented)."""
     from scipy.spatial import Delaunay
     rng = np.random.default_rng(seed)
     n = int(np.ceil(r / cell)) + 1
-    g = np.arange(-n, n + 1) * cell
-    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
-    P = P + rng.uniform(-jitter, jitter, P.shape) * cell
-    P = P[(np.linalg.norm(P, axis=1) <= r) & (np.abs(P[:, 2]) <= cap - 0.5 * cell)]
-    rc = np.sqrt(r * r - cap * cap)
-    Q = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
-    discs = []
-    for zc in (-cap, cap):
-        Qj = Q + rng.uniform(-jitter, jitter, Q.shape) * cell
-        Qj = Qj[np.linalg.norm(Qj, axis=1) <= rc]
-        discs.append(np.column_stack([Qj, np.full(len(Qj), zc)]))
-    P = np.vstack([P] + discs)
+    nz = max(2, int(round(2 * cap / cell)))
+    dz = 2 * cap / nz
+    gx = np.arange(-n, n + 1) * cell
+    gz = -cap + np.arange(nz + 1) * dz
+    P = np.stack(np.meshgrid(gx, gx, gz, indexing="ij"), -1).reshape(-1, 3)
+    P[:, :2] += rng.uniform(-jitter, jitter, (len(P), 2)) * cell
+    inner = (P[:, 2] > -cap + 0.5 * dz) & (P[:, 2] < cap - 0.5 * dz)
+    P[inner, 2] += rng.uniform(-jitter, jitter, int(inner.sum())) * dz
+    P = P[np.linalg.norm(P, axis=1) <= r]
     T = Delaunay(P).simplices.astype(np.int64)
     e = P[T[:, 1:]] - P[T[:, [0]]]
     vol = np.einsum("ij,ij->i", np.cross(e[:, 0], e[:, 1]), e[:, 2]) / 6.0
     T[vol < 0] = T[vol < 0][:, [0, 2, 1, 3]]
-    T = T[np.abs(vol) >= min_quality * cell ** 3 / 6.0]
+    keep = np.abs(vol) >= min_quality * cell * cell * dz / 6.0
+    # also drop slivers with a tiny altitude (nearly flat tets of large faces)
+    Pt = P[T]
+    alt = np.full(len(T), np.inf)
+    for a in range(4):
+        o = [k for k in range(4) if k != a]
+        area = 0.5 * np.linalg.norm(np.cross(Pt[:, o[1]] - Pt[:, o[0]], Pt[:, o[2]] - Pt[:, o[0]]), axis=1)
+        alt = np.minimum(alt, 3.0 * np.abs(vol) / np.maximum(area, 1e-300))
+    keep &= alt >= 5.0 * min_quality * min(cell, dz)
+    T = T[keep]
     used = np.unique(T)
     remap = -np.ones(len(P), np.int64)
     remap[used] = np.arange(len(used))
@@ -280,30 +312,69 @@ def jittered_delaunay_ball(r: float = 0.1, cap: float = 0.05, cell: float = 4.5e
 
 def sphere_press(seed: int = 0, r: float = 0.1, cap: float = 0.05, cell: float = 4.5e-3, E: float = 1e5,
                  nu: float = 0.4, density: float = 1000.0, h: float = 1.0 / 60.0, eps: float = 1e-4,
-                 press: float = 5e-4, gap0: float = 1e-7, margin: float = 2e-3, grid: int = 4,
+                 press: float = 2e-3, gap0: float = 1e-7, margin: float = 2e-3, grid: int = 4,
                  mu_range=(0.2, 1.0), tgt_sigma: float = 1e-3) -> Problem:
-    """Large contact-heavy scene: a Neo-Hookean ball (r = 0.1 m, flattened at |z| <= cap, the
-    contact patches of a pressed ball) resting on the ground z = -cap, with a kinematic plate on
-    top that moves down by ``press`` during the step.  Each plane carries a grid x grid of friction
-    regions over the cap disc with mu ~ U(mu_range) (seeded).  Default cell 4.5 mm: about 32k
-    vertices, 211k tets, ~2,000 contacts (both discs).  Starts at rest; target X + N(0, tgt_sigma^2).
-    """
+    """Large contact-heavy scene: a Neo-Hookean ball (r = 0.1 m, flattened at |z| <= cap: the contact
+    patches of a pressed ball) between the ground z = -cap and a kinematic plate that has pressed it
+    by ``press``: the start state is the rest shape compressed affinely in z so that its top disc
+    sits at cap - press, touching the plate (both planes ``gap0`` away), at rest.  Each plane carries
+    a grid x grid of friction regions over the cap disc with mu ~ U(mu_range) (seeded).  Default
+    cell 4.5 mm: about 32k vertices, 210k tets, ~2,300 contacts (both discs).  Target X + N(0,
+    tgt_sigma^2)."""
     X, tets = jittered_delaunay_ball(r, cap, cell, 0.2, seed)
     rng = np.random.default_rng(seed + 1)
     rc = np.sqrt(r * r - cap * cap)
     planes = []
-    for k, (nrm, off) in enumerate((([0.0, 0.0, 1.0], -cap - gap0), ([0.0, 0.0, -1.0], -(cap + gap0 - press)))):
+    for nrm, off in (([0.0, 0.0, 1.0], -cap - gap0), ([0.0, 0.0, -1.0], -(cap - press + gap0))):
         t1 = np.array([1.0, 0.0, 0.0])
         t2 = np.cross(nrm, t1)
-        lo1, hi1 = (-rc, rc)
-        lo2, hi2 = (-rc, rc) if t2[1] > 0 else (-rc, rc)
         mu_vals = rng.uniform(mu_range[0], mu_range[1], grid * grid)
-        planes.append(Plane(nrm, off, float(mu_vals.mean()), t1, t2, (grid, grid, lo1, hi1, lo2, hi2, mu_vals)))
+        planes.append(Plane(nrm, off, float(mu_vals.mean()), t1, t2, (grid, grid, -rc, rc, -rc, rc, mu_vals)))
     on_disc = np.nonzero(np.abs(np.abs(X[:, 2]) - cap) < 1e-12)[0]
     scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), density, h,
                   np.array([0.0, 0.0, -GRAVITY]), planes, on_disc, margin, eps, f"sphere{len(X)}")
+    q0 = X.copy()
+    q0[:, 2] = -cap + (X[:, 2] + cap) * (1.0 - press / (2.0 * cap))
     q_tgt = X + rng.normal(0.0, tgt_sigma, X.shape)
-    return Problem(scene, X.copy(), np.zeros_like(X), np.zeros_like(X), q_tgt)
+    return Problem(scene, q0, np.zeros_like(X), np.zeros_like(X), q_tgt)
+
+
+def quadruped(seed: int = 0, torso=(120, 80, 5), leg_r: float = 8.0, leg_h: int = 12, leg_c=(50, 32),
+              pad=(78, 62, 2), cell: float = 5e-3, E: float = 2e5, nu: float = 0.45, density: float = 1000.0,
+              h: float = 1.0 / 200.0, mu: float = 0.8, eps: float = 1e-4, gap0: float = 1e-7,
+              margin: float = 2e-3, act_scale: float = 1e3) -> Problem:
+    """Soft quadruped of voxel cells (``cell`` edge, 5 tets each) standing on the ground z = 0:
+    foot pads (pad[0] x pad[1] x pad[2] cells, centred under the legs), cylindrical legs (radius
+    leg_r cells, leg_h cells high, centred at (+-leg_c[0], +-leg_c[1]) cells from the torso centre)
+    and a torso of torso[0] x torso[1] x torso[2] cells on top.  Defaults: ~96k cells, ~482k tets,
+    ~100k vertices, ~19.9k pad-bottom contacts, E=2e5, nu=0.45, mu=0.8, h=1/200.  The problem also
+    carries seeded per-tet activations a ~ N(0, act_scale^2) Pa and unit fibres (``act``, ``fibre``).
+    """
+    tx, ty, tz = torso
+    px, py, pz = pad
+    half_x = max(tx // 2, leg_c[0] + px // 2 + 1)
+    half_y = max(ty // 2, leg_c[1] + py // 2 + 1)
+    nx, ny, nz = 2 * half_x, 2 * half_y, pz + leg_h + tz
+    occ = np.zeros((nx, ny, nz), bool)
+    ci = np.arange(nx)[:, None] - half_x + 0.5   # cell centres, torso centre at 0
+    cj = np.arange(ny)[None, :] - half_y + 0.5
+    occ[half_x - tx // 2:half_x - tx // 2 + tx, half_y - ty // 2:half_y - ty // 2 + ty, pz + leg_h:] = True
+    for sx in (-1, 1):
+        for sy in (-1, 1):
+            cx, cy = sx * leg_c[0], sy * leg_c[1]
+            disc = (ci - cx) ** 2 + (cj - cy) ** 2 <= leg_r ** 2
+            occ[:, :, pz:pz + leg_h] |= disc[:, :, None]
+            x0 = half_x + cx - px // 2
+            y0 = half_y + cy - py // 2
+            occ[x0:x0 + px, y0:y0 + py, :pz] = True
+    X, tets = voxel_tet_mesh(occ, cell, origin=(-half_x * cell, -half_y * cell, gap0))
+    bottom = np.nonzero(np.isclose(X[:, 2], gap0))[0]
+    scene = Scene(X, tets, np.full(len(tets), E), np.full(len(tets), nu), density, h,
+                  np.array([0.0, 0.0, -GRAVITY]), [Plane([0.0, 0.0, 1.0], 0.0, mu, [1.0, 0, 0], [0, 1.0, 0])],
+                  bottom, margin, eps, f"quadruped{len(tets)}")
+    pb = Problem(scene, X.copy(), np.zeros_like(X), np.zeros_like(X), X.copy())
+    pb.act, pb.fibre = random_actuation(len(tets), seed, act_scale)
+    return pb
 
 
 def two_tet(seed: int = 0, E: float = 1e5, nu: float = 0.4, h: float = 1.0 / 60.0, mu: float = 0.5,

@@ -106,3 +106,45 @@ def test_beam_rollout_30_steps_mixed_vs_fp64(pkg):
         grads[prec] = np.array([E.grad.item(), nu.grad.item(), *mu.grad.cpu().numpy()])
     assert np.all(np.isfinite(grads["fp64"]))
     assert rel(grads["mixed"], grads["fp64"]) < 1e-3, grads
+
+
+def test_quadruped_rollout_activation_gradient_matches_oracle_chain(pkg):
+    """Down-scaled soft quadruped (voxel torso, legs and foot pads; 192 pad contacts, mu = 0.8),
+    2 steps at h = 1/200 with seeded per-tet activations (N(0, 200^2) Pa): dL/da of
+    L = -mean x(q_T) through the autograd rollout against the oracle's chain of one-step adjoints."""
+    from oracle.actuation import actuation_force, actuation_gradient
+    from paper_2603_16478_gb300.rollout import rollout
+    pb = synth.quadruped(torso=(16, 10, 2), leg_r=2.0, leg_h=3, leg_c=(5, 3), pad=(7, 5, 1), cell=0.02,
+                         act_scale=2e2)
+    sc = pb.scene
+    n_steps = 2
+    act, fibre = pb.act.astype(np.float32), pb.fibre
+    # oracle chain
+    q_prev, v_prev = pb.q0.copy(), pb.v0.copy()
+    steps = []
+    for _ in range(n_steps):
+        ct = sc.contacts(q_prev)
+        st = make_step(sc, ct)
+        s = st.forward(q_prev, v_prev, f_ctrl=actuation_force(st.mesh, act.astype(float), fibre))
+        assert s.residual < 1e-8
+        steps.append((st, s, q_prev))
+        v_prev = (s.q - q_prev) / sc.h
+        q_prev = s.q
+    gq = np.zeros_like(q_prev)
+    gq[:, 0] = -1.0 / sc.n_verts
+    gv = np.zeros_like(gq)
+    da = np.zeros(sc.n_tets)
+    for st, s, qp in reversed(steps):
+        g = st.adjoint(s, qp, gq, gv)
+        da += actuation_gradient(st.mesh, g["z"], fibre, sc.h)
+        gq, gv = g["dL_dq_prev"], g["dL_dv_prev"]
+    sim = _sim(pkg, pb)
+    sim.scene.set_fibres(fibre)
+    a = torch.as_tensor(act, device="cuda").requires_grad_(True)
+    E = torch.tensor(float(sc.E[0]), dtype=torch.float64, device="cuda")
+    nu = torch.tensor(float(sc.nu[0]), dtype=torch.float64, device="cuda")
+    mu = torch.tensor([p.mu for p in sc.planes], dtype=torch.float64, device="cuda")
+    qT, _ = rollout(sim, torch.as_tensor(pb.q0, device="cuda"), torch.as_tensor(pb.v0, device="cuda"), E, nu, mu,
+                    n_steps, checkpoint_every=1, act=a)
+    (-qT[:, 0].mean()).backward()
+    assert rel(a.grad.double().cpu().numpy(), da) < 1e-4
