@@ -226,7 +226,12 @@ def sphere(pkg, torch, dev, steps, warmup):
                             T(ct.region, torch.int32), ct.n_regions)
     q0, v0 = T(pb.q0), T(pb.v0)
     t0 = time.perf_counter()
-    q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(sc.gravity), eps=sc.eps, max_newton=100)
+    try:
+        q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(sc.gravity), eps=sc.eps, max_newton=100)
+    except pkg.NcpadjError as e:  # time the adjoint at the last iterate; its residual is reported
+        if not hasattr(e, "state"):
+            raise
+        (q, lam), fs = e.state, e.stats
     t_fwd = time.perf_counter() - t0
     dq = 2 * (q - T(pb.q_target))
     lam = lam.contiguous()
@@ -275,6 +280,81 @@ def sphere(pkg, torch, dev, steps, warmup):
             "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "factor_ms": info["ms_factor"]}
 
 
+def quadruped_measure(pkg, torch, dev, steps, warmup, scale):
+    """The actuated soft quadruped (torso, four legs, foot pads; ``scale`` = 1: ~483k tets, ~129k
+    vertices, ~19.9k pad contacts, mu = 0.8, h = 1/200) with seeded per-tet activations: one GPU
+    forward step gives the state, then the one-step adjoint with dL/da is timed (mixed precision,
+    Woodbury with the inner capacitance solve) and the Krylov iterations of Woodbury and of the
+    elastic-only preconditioner are compared."""
+    import synth
+    s = float(scale)
+    kw = {} if s == 1.0 else dict(torso=(max(2, round(120 * s)), max(2, round(80 * s)), max(1, round(5 * s))),
+                                  leg_r=max(1.5, 8 * s), leg_h=max(2, round(12 * s)),
+                                  leg_c=(max(2, round(50 * s)), max(2, round(32 * s))),
+                                  pad=(max(2, round(78 * s)), max(2, round(62 * s)), max(1, round(2 * s))),
+                                  cell=5e-3 / s)
+    pb = synth.quadruped(**kw)
+    sc = pb.scene
+    ctx = pkg.Context(dev.index or 0)
+    t0 = time.perf_counter()
+    scene = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+    scene.set_fibres(pb.fibre)
+    t_build = time.perf_counter() - t0
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    ct = sc.contacts(pb.q0)
+    contacts = pkg.Contacts(T(ct.vertex, torch.int32), T(ct.frame), T(ct.d_n), T(ct.mu), None,
+                            T(ct.region, torch.int32), ct.n_regions)
+    q0, v0 = T(pb.q0), T(pb.v0)
+    act = T(pb.act, torch.float32)
+    t0 = time.perf_counter()
+    try:
+        q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(sc.gravity), eps=sc.eps, max_newton=60,
+                                      act=act)
+    except pkg.NcpadjError as e:
+        if not hasattr(e, "state"):
+            raise
+        (q, lam), fs = e.state, e.stats
+    t_fwd = time.perf_counter() - t0
+    dq = torch.zeros_like(q)
+    dq[:, 0] = -1.0 / q.shape[0]  # L = -mean x
+    lam = lam.contiguous()
+    stream = torch.cuda.Stream(dev)
+    akw = dict(eps=sc.eps, precision="mixed", cap_precision="mixed", stream=stream.cuda_stream,
+               want=("dL_dact", "dL_dmu", "z"))
+    for _ in range(warmup):
+        pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, **akw)
+    ms, sts = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g, st = pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, **akw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            sts.append(st)
+    iters = {}
+    for pc in ("woodbury", "elastic"):
+        try:
+            _, st = pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, eps=sc.eps, precision="mixed",
+                                     cap_precision="mixed", precond=pc, max_iters=5000, want=("z",))
+            iters[pc] = st["iterations"]
+        except pkg.NcpadjError as e:
+            iters[pc] = "not converged in 5000" if "NOT_CONVERGED" in str(e) else str(e)[:120]
+    info = scene.info()
+    return {"workload": f"soft quadruped, {sc.n_verts} verts / {sc.n_tets} tets, {ct.n} pad contacts (mu=0.8), "
+                        "per-tet activations N(0, 1e3) Pa, h=1/200, one adjoint step with dL/da (mixed)",
+            "gradients_per_s": steps / (sum(ms) / 1e3), "ms_per_call": sum(ms) / steps,
+            "krylov_iterations": statistics.median(x["iterations"] for x in sts),
+            "inner_iterations": statistics.median(x["inner_iterations"] for x in sts),
+            "capacitance_blocks": sts[-1]["capacitance_blocks"],
+            "stage_ms": {k: statistics.mean(x[k] for x in sts) for k in
+                         ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract", "ms_cap_inverse")},
+            "krylov_iterations_by_preconditioner": iters, "scene_build_s": t_build, "forward_s": t_fwd,
+            "forward_newton_iters": fs["newton_iters"], "forward_residual": fs["residual"],
+            "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "factor_ms": info["ms_factor"]}
+
+
 # --------------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------------
@@ -289,6 +369,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-block measurement")
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
+    ap.add_argument("--quadruped", action="store_true", help="add the actuated quadruped measurement")
+    ap.add_argument("--quad-scale", type=float, default=1.0, help="linear scale of the quadruped (1 = full size)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -423,34 +505,41 @@ def main():
     e2e_value = world / (sum(e2e_t) / len(e2e_t)) if e2e_t else None
 
     # ---- roofline of the dominant kernel ----
+    # The Krylov loop dominates the step, and in it the product with A^{-1} = P^T S^T S P (two
+    # launches of k_spmv_chunks, S then S^T, with 3 right-hand sides): it is timed live here through
+    # ncpadj_elastic_solve on its own stream (the same kernels on the same data, FP64 values).
     it = statistics.median(s["iterations"] for s in stats)
-    cap_ms = statistics.mean(s["ms_cap_inverse"] for s in stats)
-    kry_ms = statistics.mean(s["ms_krylov"] for s in stats)
     ncap = stats[0]["capacitance_dim"]
     info = scene.info()
     hbm_peak, hbm_src = peaks()
     launches = int(statistics.median(s["kernel_launches"] for s in stats))
-    if cap_ms >= kry_ms:
-        # capacitance inversion (Gauss-Jordan): n^3 fused multiply-adds, ALU bound
-        flops = 2.0 * ncap ** 3
-        achieved = flops / (cap_ms / 1e3) / 1e12
-        if variants[head][1] == "fp64":
-            peak, src, kname = 1.25, "nominal FP64 1.25 TFLOP/s (no FP64 entry in the measured peaks)", \
-                "k_gj (capacitance inversion, FP64 Gauss-Jordan)"
-        else:
-            peak = 152 * 128 * 2 * 2.07e9 / 1e12
-            src = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)"
-            kname = "k_gj_blocked (capacitance inversion, FP32 blocked Gauss-Jordan)"
-        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": src, "ms_per_launch": cap_ms}
-    else:
-        n3 = 3 * sc.n_verts
-        per_it = (info["n_blocks"] * (72 + 4) + 2 * n3 * 8) + 4 * (info["nnz_Linv"] * 12 + 2 * n3 * 8) + ncap * ncap * 8
-        per_it += (it / 2 + 3) * 2 * n3 * 8
-        achieved = per_it * it / (kry_ms / 1e3) / 1e9
-        roof = {"kernel": "Krylov stage (SpMV + Woodbury apply + CGS2)", "bound": "hbm", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": hbm_src}
+    n3 = 3 * sc.n_verts
+    sx = torch.randn(sc.n_verts, 3, dtype=torch.float64, device=dev)
+    sy = torch.empty_like(sx)
+    sst = torch.cuda.Stream(dev)
+    for _ in range(5):
+        pkg.elastic_solve(scene, sx, sy, stream=sst.cuda_stream)
+    K = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(sst)
+    for _ in range(K):
+        pkg.elastic_solve(scene, sx, sy, stream=sst.cuda_stream)
+    e1.record(sst)
+    torch.cuda.synchronize(dev)
+    ms_apply = e0.elapsed_time(e1) / K
+    # algorithmic bytes of one A^{-1} apply (two triangular solves with the Cholesky factor, each
+    # factor entry read once for the 3 right-hand sides, vectors once per pass): 2 nnz(L) (8 + 4) +
+    # 4 x 3 n_v x 8; the sparse inverse S = L^{-1} the kernels actually read is an implementation
+    # extra (kernel_bytes below)
+    alg = 2 * info["nnz_L"] * 12 + 4 * n3 * 8
+    kb = 2 * info["nnz_Linv"] * 12 + 4 * n3 * 8
+    achieved = alg / (ms_apply / 1e3) / 1e9
+    roof = {"kernel": "k_spmv_chunks x2 (A^-1 = P^T S^T S P, FP64, 3 RHS)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+            "peak_source": hbm_src, "ms_per_launch_pair": ms_apply, "algorithmic_bytes": alg,
+            "kernel_bytes": kb, "kernel_bytes_gbs": kb / (ms_apply / 1e3) / 1e9,
+            "note": "burst figure, inputs L2-resident between launches (53 MB of S and S^T on the beam)"}
 
     # ---- the batched workload ----
     batch_res = None
@@ -466,6 +555,13 @@ def main():
             sphere_res = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)
         except Exception as e:  # noqa: BLE001
             sphere_res = {"error": str(e)[:300]}
+
+    quad_res = None
+    if args.quadruped:
+        try:
+            quad_res = quadruped_measure(pkg, torch, dev, max(2, args.steps // 4), 1, args.quad_scale)
+        except Exception as e:  # noqa: BLE001
+            quad_res = {"error": str(e)[:300]}
 
     # ---- CPU baseline: the oracle, one thread, bounded sample ----
     cpu = None
@@ -496,7 +592,8 @@ def main():
                        "forward_newton_iters": [f["newton_iters"] for f in fwd_stats],
                        "forward_residual": [f["residual"] for f in fwd_stats],
                        "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "batched": batch_res,
-                       **({"sphere": sphere_res} if sphere_res is not None else {})},
+                       **({"sphere": sphere_res} if sphere_res is not None else {}),
+                       **({"quadruped": quad_res} if quad_res is not None else {})},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "gradients/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches * args.steps, "clocks": clk,

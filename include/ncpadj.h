@@ -196,10 +196,11 @@ typedef struct {
  *              keeps the solve's precision and tolerance).
  *   cap_block  most contacts per directly inverted capacitance block (0 = default = 1365, the
  *              most the direct inverse takes; larger values are clamped to it).  A scene with
- *              more contacts has its capacitance solved iteratively (Sec. 4.4): its full dense
- *              capacitance (FP32) is applied by an inner right-preconditioned GMRES to relative
- *              residual 1e-6, preconditioned by the exact inverses of contiguous, nearly equal
- *              groups of its contacts in the given order, and the outer solve becomes flexible
+ *              more contacts has its capacitance solved iteratively (Sec. 4.4): an inner
+ *              right-preconditioned GMRES to relative residual 1e-6 applies the capacitance
+ *              without forming it (a scatter and a gather along the contacts' elimination-tree
+ *              paths per product), preconditioned by the exact inverses of contiguous, nearly
+ *              equal groups of its contacts in the given order; the outer solve becomes flexible
  *              GMRES (the preconditioner varies).  Order the contacts spatially (e.g. by plane,
  *              then by position) so that groups are compact. */
 typedef struct {

@@ -290,6 +290,10 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_host, 2 * (2 * 513 + 1) * sizeof(double)));  // two slots
   for (auto& e : S.gs_ev) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_inner_host, 256 * sizeof(double)));
+  NCPADJ_CUDA_TRY(cudaHostAlloc(&S.gs_map_host, 2 * (2 * 513 + 1) * sizeof(double), cudaHostAllocMapped));
+  NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.gs_map_dev), S.gs_map_host, 0));
+  S.gstep.ensure(64);
   for (auto& e : S.ev) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
 }
 
@@ -339,12 +343,10 @@ struct Engine {
   std::vector<size_t> blk_moff, blk_doff;
   size_t cap_elems = 0, ds_elems = 0;
   // scene blocks above the direct inverse's size are solved iteratively (Sec. 4.4: inner Krylov
-  // solve on the capacitance): the full dense capacitance of such a block (FP32) is applied by an
-  // inner right-preconditioned GMRES whose preconditioner is the exact inverse of each of its
-  // contiguous groups (blk_*).  sup_g0/sup_g1: the groups of super-block k.
+  // solve on the capacitance): an inner right-preconditioned GMRES applies the capacitance of such
+  // a block without forming it (cap_matvec) and is preconditioned by the exact inverse of each of
+  // its contiguous groups (blk_*).  sup_g0/sup_g1: the groups of super-block k.
   std::vector<int> sup_c0, sup_nc, sup_g0, sup_g1;
-  std::vector<size_t> sup_off, sup_doff;
-  size_t sup_elems = 0, sup_delems = 0;
   static constexpr int kInnerRestart = 40;
   double inner_rtol = 1e-6;
   int inner_iters = 0;
@@ -398,15 +400,6 @@ struct Engine {
       }
       blk_c0.swap(c0s);
       blk_nc.swap(ncs);
-    }
-    sup_off.assign(sup_c0.size(), 0);
-    sup_doff.assign(sup_c0.size(), 0);
-    sup_elems = sup_delems = 0;
-    for (size_t k = 0; k < sup_c0.size(); ++k) {
-      sup_off[k] = sup_elems;
-      sup_doff[k] = sup_delems;
-      sup_elems += (size_t)9 * sup_nc[k] * sup_nc[k];
-      sup_delems += (size_t)sup_nc[k] * sup_nc[k];
     }
     blk_moff.assign(blk_c0.size(), 0);
     blk_doff.assign(blk_c0.size(), 0);
@@ -469,8 +462,6 @@ struct Engine {
       if (!sup_c0.empty()) {
         int smax = 0;
         for (int v : sup_nc) smax = std::max(smax, 3 * v);
-        // FP64 Delassus + FP64 capacitance (formed), FP32 capacitance (applied)
-        S.capfull.ensure(sizeof(double) * (sup_delems + sup_elems) + sizeof(float) * sup_elems + 256);
         S.inner.ensure(sizeof(double) * ((size_t)(kInnerRestart + 1) * smax + 3 * (size_t)smax +
                                          2 * (size_t)(kInnerRestart + 2) + 64));
         S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
@@ -552,23 +543,24 @@ struct Engine {
         }
         NCPADJ_CUDA_TRY(cudaGetLastError());
       }
-      for (size_t k = 0; k < sup_c0.size(); ++k) {  // full capacitance of the iteratively solved blocks
-        const int c0 = sup_c0[k], m_ = sup_nc[k];
-        double* Dfull = S.capfull.as<double>() + sup_doff[k];
-        double* Cfull = S.capfull.as<double>() + sup_delems + sup_off[k];
-        float* Cfull32 = reinterpret_cast<float*>(S.capfull.as<double>() + sup_delems + sup_elems) + sup_off[k];
-        launch_delassus(m_, in.cvertex + c0, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
-                        S.St_val.as<double>(), Dfull, st);
-        launch_cap_form(m_, Dfull, in.frame + 9 * (size_t)c0, S.cdata.as<double>() + 12 * (size_t)c0, h, transpose,
-                        Cfull, st);
-        launch_convert_f32((long)9 * m_ * m_, Cfull, Cfull32, st);
-        NCPADJ_CUDA_TRY(cudaGetLastError());
-      }
     }
   }
 
-  float* sup_matrix32(size_t k) {
-    return reinterpret_cast<float*>(S.capfull.as<double>() + sup_delems + sup_elems) + sup_off[k];
+  // out = C y for the contacts of super-block k, without forming C:
+  //   C y = y + h^2 K'_c F_c (A^{-1} J^T y)_{v_c},
+  // where A^{-1} J^T y at the contact vertices is a scatter of y along the contacts'
+  // elimination-tree paths into S P J^T y followed by a gather along the same paths.
+  void cap_matvec(size_t k, const double* yseg, double* out_seg) {
+    const int c0 = sup_c0[k], m_ = sup_nc[k];
+    const int32_t* ip = S.iperm.as<int32_t>();
+    double* w64 = mixed ? nullptr : t2;
+    float* wf = mixed ? x32 : nullptr;
+    if (mixed) NCPADJ_CUDA_TRY(cudaMemsetAsync(wf, 0, sizeof(float) * N, st));
+    else NCPADJ_CUDA_TRY(cudaMemsetAsync(w64, 0, sizeof(double) * N, st));
+    launch_path_scatter(m_, in.cvertex + c0, ip, sinv, in.frame + 9 * (size_t)c0, yseg, 1.0, w64, wf, st);
+    launch_path_gather(m_, in.cvertex + c0, ip, sinv, w64, wf, in.frame + 9 * (size_t)c0,
+                       S.cdata.as<double>() + 12 * (size_t)c0, transpose, out_seg, st);
+    launch_axpby(3 * m_, 1.0, yseg, h * h, out_seg, out_seg, st);
   }
 
   // out = B^{-1} in over the groups g0..g1-1 of a super-block whose first contact is c0 (segment
@@ -587,7 +579,6 @@ struct Engine {
   // Gram-Schmidt twice; Hessenberg on the host), to ||s - C y|| <= inner_rtol ||s||.
   void inner_solve(size_t k, const double* sseg, double* yseg) {
     const int n = 3 * sup_nc[k], c0 = sup_c0[k], mi = kInnerRestart;
-    const float* Cf = sup_matrix32(k);
     double* V = S.inner.as<double>();               // (mi+1) x n
     double* u = V + (size_t)(mi + 1) * n;            // preconditioned vector
     double* rr = u + n;                              // residual
@@ -598,9 +589,10 @@ struct Engine {
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(rr, sseg, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     auto norm_host = [&](const double* a) {
       launch_multi_dot(n, 1, a, n, a, partial, scal + 4, st);
-      NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host + 4, scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_inner_host + 2 * (mi + 1) + 1, scal + 4, sizeof(double),
+                                      cudaMemcpyDeviceToHost, st));
       NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
-      return std::sqrt(S.scal_host[4]);
+      return std::sqrt(S.gs_inner_host[2 * (mi + 1) + 1]);
     };
     const double s0 = norm_host(rr);
     if (!(s0 > 0.0) || !std::isfinite(s0)) return;
@@ -616,18 +608,20 @@ struct Engine {
       for (int j = 0; j < mi; ++j) {
         double* vn = V + (size_t)(j + 1) * n;
         group_precond(sup_g0[k], sup_g1[k], c0, V + (size_t)j * n, u);
-        launch_dense_gemv32(n, Cf, u, vn, st);
+        cap_matvec(k, u, vn);
         launch_multi_dot(n, j + 1, V, n, vn, partial, gs, st);
         launch_multi_axpy(n, j + 1, V, n, gs, vn, st);
         launch_multi_dot(n, j + 1, V, n, vn, partial, gs + (mi + 1), st);
         launch_multi_axpy(n, j + 1, V, n, gs + (mi + 1), vn, st);
         launch_multi_dot(n, 1, vn, n, vn, partial, nrm2, st);
         launch_normalize(n, vn, nrm2, vn, gs + 2 * (mi + 1), st);
-        NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_host, gs, sizeof(double) * (2 * (mi + 1) + 1), cudaMemcpyDeviceToHost, st));
+        // own pinned buffer: the outer GMRES may have a step's coefficients in flight in gs_host
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.gs_inner_host, gs, sizeof(double) * (2 * (mi + 1) + 1),
+                                        cudaMemcpyDeviceToHost, st));
         NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
         double* hcol = &H[(size_t)(mi + 1) * j];
-        for (int i = 0; i <= j; ++i) hcol[i] = S.gs_host[i] + S.gs_host[mi + 1 + i];
-        hcol[j + 1] = S.gs_host[2 * (mi + 1)];
+        for (int i = 0; i <= j; ++i) hcol[i] = S.gs_inner_host[i] + S.gs_inner_host[mi + 1 + i];
+        hcol[j + 1] = S.gs_inner_host[2 * (mi + 1)];
         for (int i = 0; i < j; ++i) {
           const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
           hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
@@ -658,7 +652,7 @@ struct Engine {
       launch_combine(n, kk, V, n, ydev, ww, st);        // ww = V y
       group_precond(sup_g0[k], sup_g1[k], c0, ww, u);  // u = B^{-1} V y
       launch_axpby(n, 1.0, yseg, 1.0, u, yseg, st);
-      launch_dense_gemv32(n, Cf, yseg, ww, st);
+      cap_matvec(k, yseg, ww);
       launch_axpby(n, 1.0, sseg, -1.0, ww, rr, st);
       beta = norm_host(rr);
       if (done || !std::isfinite(beta) || beta <= tol) break;
@@ -725,6 +719,90 @@ struct Engine {
     }
   }
 
+  // ---- captured Arnoldi step (Woodbury, direct capacitance blocks) ----
+  // One CUDA graph holds a whole GMRES step: preconditioner apply on V_j, matvec into V_{j+1},
+  // Gram-Schmidt twice, normalisation, export of the coefficients to host-mapped slot j % 2 and
+  // j <- j + 1, with j read on the device.  Replaying it is one launch per step instead of ~16,
+  // which matters because the step is otherwise bound by the host's launch rate.
+  bool step_graph_possible() const {
+    return precond == NCPADJ_PRECOND_WOODBURY && nc > 0 && sup_c0.empty();
+  }
+  std::vector<uintptr_t> step_key() const {
+    std::vector<uintptr_t> k = {(uintptr_t)nc, (uintptr_t)m, (uintptr_t)N, (uintptr_t)mixed, (uintptr_t)cap_fp32,
+                                (uintptr_t)transpose, (uintptr_t)in.cvertex, (uintptr_t)in.frame,
+                                (uintptr_t)S.gmres.p, (uintptr_t)S.vecs.p, (uintptr_t)S.red.p, (uintptr_t)S.scal.p,
+                                (uintptr_t)S.cap.p, (uintptr_t)S.vec32.p, (uintptr_t)S.cdata.p, (uintptr_t)S.bsr32.p,
+                                (uintptr_t)S.bsr64.p, (uintptr_t)blk_c0.size()};
+    for (size_t b = 0; b < blk_c0.size(); ++b) {
+      k.push_back((uintptr_t)blk_c0[b]);
+      k.push_back((uintptr_t)blk_nc[b]);
+    }
+    return k;
+  }
+  void enqueue_step_indexed(double* V, double* gs, double* nrm2, int* jp) {
+    const int32_t* ip = S.iperm.as<int32_t>();
+    // z = P^{-1} V_j into w (Woodbury, as in apply_precond)
+    launch_sinv_half1_idx(sinv, V, N, jp, mixed ? nullptr : t3, mixed ? w32 : nullptr, st);
+    launch_path_gather(nc, in.cvertex, ip, sinv, t3, mixed ? w32 : nullptr, in.frame, S.cdata.as<double>(), transpose,
+                       sc, st);
+    for (size_t k = 0; k < blk_c0.size(); ++k) {
+      const size_t o = 3 * (size_t)blk_c0[k];
+      const int n_ = 3 * blk_nc[k];
+      if (mixed || cap_fp32) launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+      else launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
+    }
+    launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st);
+    if (mixed) launch_sinv_half2_32(sinv, w32, w, st);
+    else launch_sinv_half2(sinv, t3, w, st);
+    // V_{j+1} = A z
+    launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
+                        mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st);
+    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs, st);
+    launch_multi_axpy_idx(N, V, N, jp, gs, V, st);
+    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs + (m + 1), st);
+    launch_multi_axpy_idx(N, V, N, jp, gs + (m + 1), V, st);
+    launch_multi_dot_idx(N, m, V, N, jp, true, partial, nrm2, st);
+    launch_normalize_idx(N, V, N, jp, nrm2, gs + 2 * (m + 1), st);
+    launch_export_step(gs, 2 * (m + 1) + 1, S.gs_map_dev, jp, st);
+  }
+  // the graph for the current configuration (captured on first use and when it changes); null if
+  // capture is not possible here
+  cudaGraphExec_t step_graph(double* V, double* gs, double* nrm2) {
+    if (!step_graph_possible()) return nullptr;
+    std::vector<uintptr_t> key = step_key();
+    if (S.step_exec && key == S.step_key) return S.step_exec;
+    if (S.step_exec) {
+      cudaGraphExecDestroy(S.step_exec);
+      S.step_exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    const int64_t l0 = g_launches;
+    enqueue_step_indexed(V, gs, nrm2, S.gstep.as<int>());
+    step_launches = (int)(g_launches - l0);
+    g_launches = l0;  // counted when the graph is replayed
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (ce != cudaSuccess || !g) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return nullptr;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    S.step_exec = ex;
+    S.step_key = key;
+    return ex;
+  }
+  int step_launches = 0;
+
   double dot_host(const double* a, const double* bb) {
     launch_multi_dot(N, 1, a, N, bb, partial, scal, st);
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -789,7 +867,15 @@ struct Engine {
           // The host enqueues step j + 1 before it reads step j's coefficients, so the GPU never
           // waits for the host's Givens update (a converged cycle leaves one step unused).
           const size_t slot = 2 * (size_t)(m + 1) + 1;
+          cudaGraphExec_t gx = step_graph(V, gs, nrm2);
+          if (gx) NCPADJ_CUDA_TRY(cudaMemsetAsync(S.gstep.p, 0, sizeof(int), st));
           auto enqueue_step = [&](int j) {
+            if (gx) {
+              NCPADJ_CUDA_TRY(cudaGraphLaunch(gx, st));
+              g_launches += step_launches;
+              NCPADJ_CUDA_TRY(cudaEventRecord(S.gs_ev[j & 1], st));
+              return;
+            }
             double* vn = V + (size_t)(j + 1) * N;
             double* zj = flexible ? Z + (size_t)j * N : w;
             apply_precond(V + (size_t)j * N, zj);
@@ -808,7 +894,7 @@ struct Engine {
           for (int j = 0; j < m; ++j) {
             if (j + 1 < m && iters + 1 < max_iters) enqueue_step(j + 1);
             NCPADJ_CUDA_TRY(cudaEventSynchronize(S.gs_ev[j & 1]));
-            const double* gh = S.gs_host + (j & 1) * slot;
+            const double* gh = (gx ? S.gs_map_host : S.gs_host) + (j & 1) * slot;
             double* h = &H[(size_t)(m + 1) * j];
             for (int i = 0; i <= j; ++i) h[i] = gh[i] + gh[m + 1 + i];
             h[j + 1] = gh[2 * (m + 1)];
@@ -1471,6 +1557,9 @@ void ncpadj_scene_destroy(ncpadj_scene s) {
   if (s->s.flags_host) cudaFreeHost(s->s.flags_host);
   if (s->s.scal_host) cudaFreeHost(s->s.scal_host);
   if (s->s.gs_host) cudaFreeHost(s->s.gs_host);
+  if (s->s.gs_inner_host) cudaFreeHost(s->s.gs_inner_host);
+  if (s->s.gs_map_host) cudaFreeHost(s->s.gs_map_host);
+  if (s->s.step_exec) cudaGraphExecDestroy(s->s.step_exec);
   for (auto e : s->s.gs_ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : s->s.ev)

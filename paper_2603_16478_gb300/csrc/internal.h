@@ -113,7 +113,6 @@ struct Scene {
   DevBuf io;                      // staging for host-memory calls
   DevBuf gmres;                   // GMRES basis + Hessenberg
   DevBuf fgmres;                  // flexible GMRES: preconditioned basis Z
-  DevBuf capfull;                 // full capacitance of scenes solved iteratively (FP64 D, C; FP32 C)
   DevBuf inner;                   // inner GMRES on the capacitance: basis and scratch
   DevBuf fwd;                     // forward Newton vectors
   DevBuf fibre;                   // double [nt][3] actuation fibres (empty: none set)
@@ -122,6 +121,13 @@ struct Scene {
   int* flags_host = nullptr;      // pinned
   double* scal_host = nullptr;    // pinned
   double* gs_host = nullptr;      // pinned: Gram-Schmidt coefficients of one GMRES iteration
+  double* gs_inner_host = nullptr;  // pinned: the same for the inner capacitance solve, and its norms
+  // captured GMRES step (one graph serves every step of a cycle: the kernels read j on the device)
+  double* gs_map_host = nullptr;    // host-mapped pinned slots for the captured step's coefficients
+  double* gs_map_dev = nullptr;     // its device address
+  DevBuf gstep;                     // int j of the captured step
+  cudaGraphExec_t step_exec = nullptr;
+  std::vector<uintptr_t> step_key;  // what the captured graph depends on
   cudaEvent_t ev[8] = {};
   cudaEvent_t gs_ev[2] = {};       // GMRES: coefficients of step j landed in pinned slot j % 2
 };

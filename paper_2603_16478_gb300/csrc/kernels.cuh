@@ -132,8 +132,6 @@ void launch_step_by_scene(int nv, const double* q, const double* dx, const int32
 // y = B x for the 3x3-block matrix (FP64)
 void launch_bsr_spmv(int nv, const int32_t* row_ptr, const int32_t* col, const double* val,
                      const double* x, double* y, cudaStream_t s);
-// y = C x, C dense row-major FP32 [n][n], x and y double [n]
-void launch_dense_gemv32(int n, const float* Cm, const double* x, double* y, cudaStream_t s);
 void launch_bsr_spmv32(int nv, const int32_t* row_ptr, const int32_t* col, const float* val,
                        const double* x, double* y, cudaStream_t s);
 // inverse of the scalar diagonal of the block matrix
@@ -157,6 +155,22 @@ struct SinvArgs {
   const float *S_val32 = nullptr, *St_val32 = nullptr;  // FP32 copies (mixed precision)
 };
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
+// Step-indexed forms for a captured GMRES step (j = *jp on the device; V_{j+1} = V + (j + 1) ld):
+//   w = S P V_j (zeroed first; FP32 values into w32 when given)
+void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, const int* jp, double* w, float* w32,
+                           cudaStream_t s);
+//   V_{j+1} = A x (block matrix, FP64 or FP32 values)
+void launch_bsr_spmv_idx(int nv, const int32_t* rp, const int32_t* col, const double* val, const float* val32,
+                         const double* x, double* ybase, long yld, const int* jp, cudaStream_t s);
+//   out[k] = V_k . V_{j+1}, k <= j (or, with self, out[0] = |V_{j+1}|^2); mmax = largest j + 1
+void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* jp, bool self, double* partial,
+                          double* out, cudaStream_t s);
+//   V_{j+1} -= sum_k coef[k] V_k ;  V_{j+1} /= sqrt(*nrm2) (norm to *h_slot)
+void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const double* coef, double* Vw,
+                           cudaStream_t s);
+void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s);
+//   gs[0..len) to host-mapped slot j % 2, then *jp = j + 1
+void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s);
 // the two halves of A^{-1} = P^T S^T S P: w = S P x (position space, zeroed first), y = P^T S^T w
 void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s);
 void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s);

@@ -60,10 +60,13 @@ __global__ void k_bsr_spmv32(int nv, const int32_t* __restrict__ rp, const int32
 // Half a warp per vertex row: lane l of the half takes blocks rp[v] + l, rp[v] + l + 16, ... and the
 // three row sums are reduced over the half-warp (the row-per-thread form left the GPU nearly empty:
 // one thread per scalar row, each walking its ~15 blocks with dependent loads).
+// jp (nullable): y is written at y + (*jp + 1) * yld (the next Arnoldi vector of a captured step)
 template <typename V>
 __global__ void __launch_bounds__(256) k_bsr_spmv_hw(int nv, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
-                                                     const double* __restrict__ x, double* __restrict__ y) {
+                                                     const double* __restrict__ x, double* __restrict__ y,
+                                                     const int* __restrict__ jp = nullptr, long yld = 0) {
+  if (jp) y += (size_t)(*jp + 1) * yld;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = t >> 4, l = t & 15;
   const bool live = v < nv;
@@ -129,37 +132,6 @@ __global__ void __launch_bounds__(256) k_cap_apply(int n, const T* __restrict__ 
   }
 }
 
-// y = C x for a dense row-major FP32 matrix (the full contact capacitance of the inner solve):
-// two warps per row, four independent accumulators per lane, x read in double from L2.
-__global__ void __launch_bounds__(256) k_dense_gemv32(int n, const float* __restrict__ Cm, const double* __restrict__ x,
-                                                      double* __restrict__ y) {
-  __shared__ float part[4][2];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rloc = warp >> 1, half = warp & 1;
-  const int k = blockIdx.x * 4 + rloc;
-  float acc = 0.0f;
-  if (k < n) {
-    const float* row = Cm + (size_t)k * n;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    int j = half * 32 + lane;
-    for (; j + 192 < n; j += 256) {
-      a0 += row[j] * (float)x[j];
-      a1 += row[j + 64] * (float)x[j + 64];
-      a2 += row[j + 128] * (float)x[j + 128];
-      a3 += row[j + 192] * (float)x[j + 192];
-    }
-    for (; j < n; j += 64) a0 += row[j] * (float)x[j];
-    acc = (a0 + a1) + (a2 + a3);
-  }
-  acc = warp_sum(acc);
-  if (lane == 0) part[rloc][half] = acc;
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    const int kk = blockIdx.x * 4 + threadIdx.x;
-    if (kk < n) y[kk] = (double)(part[threadIdx.x][0] + part[threadIdx.x][1]);
-  }
-}
-
 __global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * nv) return;
@@ -173,12 +145,15 @@ __global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, 
 // lane; partial sums are added atomically into y[3 out(row) + r] (y zeroed by the caller),
 // out(row) = omap ? omap[row] : row.  Splitting the long rows near the elimination-tree root over
 // many warps keeps the product bandwidth- rather than latency-bound.
+// jp (nullable): x is taken at x + (*jp) * xld -- the step index of a captured GMRES step
 template <typename V, typename X, typename Y, typename Acc = Y>
 __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t* __restrict__ crow,
                                                      const int64_t* __restrict__ cbeg, const int64_t* __restrict__ cend,
                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
                                                      const int32_t* __restrict__ omap, const X* __restrict__ x,
-                                                     Y* __restrict__ y) {
+                                                     Y* __restrict__ y, const int* __restrict__ jp = nullptr,
+                                                     long xld = 0) {
+  if (jp) x += (size_t)(*jp) * xld;
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= nchunks) return;
@@ -755,6 +730,82 @@ __global__ void k_multi_dot_fused(int n, const double* __restrict__ V, long ld, 
   }
 }
 
+// Step-indexed Gram-Schmidt kernels of a captured GMRES step: j = *jp, the new vector is
+// V_{j+1} = V + (j + 1) ld and the basis so far is V_0..V_j.
+// out[k] = V_k . V_{j+1} for k <= j (blockIdx.y = k; columns above j return at once); with self,
+// out[0] = V_{j+1} . V_{j+1}.
+__global__ void k_multi_dot_idx(int n, const double* __restrict__ V, long ld, const int* __restrict__ jp, int self,
+                                double* partial, unsigned* cnt, double* out) {
+  const int j = *jp;
+  const int k = blockIdx.y;
+  if (k > (self ? 0 : j)) return;
+  const double* w = V + (size_t)(j + 1) * ld;
+  const double* vk = self ? w : V + (size_t)k * ld;
+  double acc = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    acc += vk[i] * w[i];
+  acc = warp_sum(acc);
+  __shared__ double sh[32];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      partial[(size_t)k * gridDim.x + blockIdx.x] = v;
+      __threadfence();
+      last = atomicAdd(&cnt[k], 1u) == gridDim.x - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(&partial[(size_t)k * gridDim.x + i]);
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    out[k] = r;
+    cnt[k] = 0;
+  }
+}
+// V_{j+1} -= sum_{k <= j} coef[k] V_k
+__global__ void k_multi_axpy_idx(int n, const double* __restrict__ V, long ld, const int* __restrict__ jp,
+                                 const double* __restrict__ coef, double* __restrict__ Vw) {
+  const int j = *jp;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* w = Vw + (size_t)(j + 1) * ld;
+  double acc = w[i];
+  for (int k = 0; k <= j; ++k) acc -= coef[k] * V[(size_t)k * ld + i];
+  w[i] = acc;
+}
+// V_{j+1} /= sqrt(*nrm2); h_slot = the norm
+__global__ void k_normalize_idx(int n, double* V, long ld, const int* __restrict__ jp, const double* nrm2,
+                                double* h_slot) {
+  const int j = *jp;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double nr = sqrt(*nrm2);
+  double* v = V + (size_t)(j + 1) * ld;
+  if (i < n) v[i] = (nr > 0.0) ? v[i] / nr : 0.0;
+  if (i == 0) *h_slot = nr;
+}
+// coefficients of step j to host-mapped slot j % 2, then j <- j + 1 (one block)
+__global__ void k_export_step(const double* __restrict__ gs, int len, double* host_slots, int* jp) {
+  const int j = *jp;
+  double* dst = host_slots + (size_t)(j & 1) * len;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = gs[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    *jp = j + 1;
+  }
+}
+
 __global__ void k_multi_dot_final(int nparts, const double* partial, double* out) {
   const int k = blockIdx.x;
   double acc = 0.0;
@@ -849,10 +900,6 @@ void launch_bsr_spmv32(int nv, const int32_t* rp, const int32_t* col, const floa
                        cudaStream_t s) {
   g_launches += 1;
   k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
-}
-void launch_dense_gemv32(int n, const float* Cm, const double* x, double* y, cudaStream_t s) {
-  g_launches += 1;
-  if (n) k_dense_gemv32<<<(n + 3) / 4, 256, 0, s>>>(n, Cm, x, y);
 }
 void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
                      cudaStream_t s) {
@@ -1058,6 +1105,46 @@ void launch_multi_dot(int n, int nvec, const double* V, long ld, const double* w
   if (nb > 64) nb = 64;
   unsigned* cnt = reinterpret_cast<unsigned*>(partial + 64 * (size_t)kMaxDotVectors);
   k_multi_dot_fused<<<dim3(nb, nvec), 256, 0, s>>>(n, V, ld, w, partial, cnt, out);
+}
+void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* jp, bool self, double* partial,
+                          double* out, cudaStream_t s) {
+  g_launches += 1;
+  int nb = nblk(n, 256);
+  if (nb > 64) nb = 64;
+  unsigned* cnt = reinterpret_cast<unsigned*>(partial + 64 * (size_t)kMaxDotVectors);
+  k_multi_dot_idx<<<dim3(nb, self ? 1 : mmax + 1), 256, 0, s>>>(n, V, ld, jp, self ? 1 : 0, partial, cnt, out);
+}
+void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const double* coef, double* Vw,
+                           cudaStream_t s) {
+  g_launches += 1;
+  k_multi_axpy_idx<<<nblk(n, 256), 256, 0, s>>>(n, V, ld, jp, coef, Vw);
+}
+void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s) {
+  g_launches += 1;
+  k_normalize_idx<<<nblk(n, 256), 256, 0, s>>>(n, V, ld, jp, nrm2, h_slot);
+}
+void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s) {
+  g_launches += 1;
+  k_export_step<<<1, 256, 0, s>>>(gs, len, host_slots, jp);
+}
+void launch_bsr_spmv_idx(int nv, const int32_t* rp, const int32_t* col, const double* val, const float* val32,
+                         const double* x, double* ybase, long yld, const int* jp, cudaStream_t s) {
+  g_launches += 1;
+  if (val32) k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val32, x, ybase, jp, yld);
+  else k_bsr_spmv_hw<double><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, ybase, jp, yld);
+}
+void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, const int* jp, double* w, float* w32,
+                           cudaStream_t s) {
+  g_launches += 1;
+  if (w32) {
+    cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
+    k_spmv_chunks<float, double, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, xbase, w32, jp, xld);
+  } else {
+    cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
+    k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, xbase, w, jp, xld);
+  }
 }
 void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {
   g_launches += 1;

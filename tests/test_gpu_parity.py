@@ -203,3 +203,25 @@ def test_elastic_solve_matches_oracle_matrix(pkg, ctx, name):
     y = pkg.elastic_solve(scene, T(x))
     torch.cuda.synchronize()
     assert rel(y.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_captured_gmres_step_matches_plain_launches(pkg, ctx, precision):
+    """On a non-default stream each GMRES step is one replay of a captured graph (the step index is
+    read on the device); on the legacy default stream the same kernels are launched one by one.
+    Both must give the oracle's gradient, and each other's up to atomic summation order."""
+    case = step_case("cube_drop", 5)
+    g0, ref, s0 = run_both(pkg, ctx, case, rtol=1e-12, precision=precision, cap_precision=precision)
+    side = torch.cuda.Stream()
+    g1, ref, s1 = run_both(pkg, ctx, case, rtol=1e-12, precision=precision, cap_precision=precision,
+                           stream=side.cuda_stream)
+    g2, _, s2 = run_both(pkg, ctx, case, rtol=1e-12, precision=precision, cap_precision=precision,
+                         stream=side.cuda_stream)  # replays the graph captured by the previous call
+    torch.cuda.synchronize()
+    tol = 1e-8 if precision == "fp64" else 1e-3
+    assert_parity(g1, ref, tol, case[1].nc)
+    assert_parity(g2, ref, tol, case[1].nc)
+    assert abs(s1["iterations"] - s0["iterations"]) <= 1
+    for k, _ in KEYS:
+        a, b = g1[k].cpu().numpy().reshape(-1), g0[k].cpu().numpy().reshape(-1)
+        assert rel(a, b) <= (1e-10 if precision == "fp64" else 1e-5), k
