@@ -782,7 +782,7 @@ struct Engine {
     }
     const int64_t l0 = g_launches;
     enqueue_step_indexed(V, gs, nrm2, S.gstep.as<int>());
-    step_launches = (int)(g_launches - l0);
+    S.step_launches = (int)(g_launches - l0);
     g_launches = l0;  // counted when the graph is replayed
     const cudaError_t ce = cudaStreamEndCapture(st, &g);
     if (ce != cudaSuccess || !g) {
@@ -801,8 +801,6 @@ struct Engine {
     S.step_key = key;
     return ex;
   }
-  int step_launches = 0;
-
   double dot_host(const double* a, const double* bb) {
     launch_multi_dot(N, 1, a, N, bb, partial, scal, st);
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -872,7 +870,7 @@ struct Engine {
           auto enqueue_step = [&](int j) {
             if (gx) {
               NCPADJ_CUDA_TRY(cudaGraphLaunch(gx, st));
-              g_launches += step_launches;
+              g_launches += S.step_launches;
               NCPADJ_CUDA_TRY(cudaEventRecord(S.gs_ev[j & 1], st));
               return;
             }

@@ -128,6 +128,7 @@ struct Scene {
   DevBuf gstep;                     // int j of the captured step
   cudaGraphExec_t step_exec = nullptr;
   std::vector<uintptr_t> step_key;  // what the captured graph depends on
+  int step_launches = 0;            // kernels in one replay
   cudaEvent_t ev[8] = {};
   cudaEvent_t gs_ev[2] = {};       // GMRES: coefficients of step j landed in pinned slot j % 2
 };

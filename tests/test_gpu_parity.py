@@ -211,17 +211,18 @@ def test_captured_gmres_step_matches_plain_launches(pkg, ctx, precision):
     read on the device); on the legacy default stream the same kernels are launched one by one.
     Both must give the oracle's gradient, and each other's up to atomic summation order."""
     case = step_case("cube_drop", 5)
-    g0, ref, s0 = run_both(pkg, ctx, case, rtol=1e-12, precision=precision, cap_precision=precision)
+    rtol = 1e-12 if precision == "fp64" else 1e-8  # FP32 matvecs cannot resolve 1e-12
+    g0, ref, s0 = run_both(pkg, ctx, case, rtol=rtol, precision=precision, cap_precision=precision)
     side = torch.cuda.Stream()
-    g1, ref, s1 = run_both(pkg, ctx, case, rtol=1e-12, precision=precision, cap_precision=precision,
+    g1, ref, s1 = run_both(pkg, ctx, case, rtol=rtol, precision=precision, cap_precision=precision,
                            stream=side.cuda_stream)
-    g2, _, s2 = run_both(pkg, ctx, case, rtol=1e-12, precision=precision, cap_precision=precision,
+    g2, _, s2 = run_both(pkg, ctx, case, rtol=rtol, precision=precision, cap_precision=precision,
                          stream=side.cuda_stream)  # replays the graph captured by the previous call
     torch.cuda.synchronize()
     tol = 1e-8 if precision == "fp64" else 1e-3
     assert_parity(g1, ref, tol, case[1].nc)
     assert_parity(g2, ref, tol, case[1].nc)
-    assert abs(s1["iterations"] - s0["iterations"]) <= 1
+    assert abs(s1["iterations"] - s0["iterations"]) <= max(2, s0["iterations"] // 10)
     for k, _ in KEYS:
         a, b = g1[k].cpu().numpy().reshape(-1), g0[k].cpu().numpy().reshape(-1)
         assert rel(a, b) <= (1e-10 if precision == "fp64" else 1e-5), k
