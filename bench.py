@@ -135,6 +135,42 @@ def run_reference(args):
 # --------------------------------------------------------------------------------------------
 # batched uneven scenes: 64 independent blocks (log-uniform 2k..50k tets), one adjoint each
 # --------------------------------------------------------------------------------------------
+def apply_roofline(pkg, torch, dev, scene, K):
+    """GB/s of the product with A^{-1} = P^T S^T S P (two k_spmv_chunks launches, FP64, 3 RHS) on a
+    scene: K applies captured into one CUDA graph and replayed, timed with events on the replay
+    stream.  Returns algorithmic bytes (Cholesky-factor based) and the kernels' own bytes (S, S^T)."""
+    info = scene.info()
+    n3 = 3 * scene.n_verts
+    sx = torch.randn(scene.n_verts, 3, dtype=torch.float64, device=dev)
+    sy = torch.empty_like(sx)
+    sst = torch.cuda.Stream(dev)
+    for _ in range(3):
+        pkg.elastic_solve(scene, sx, sy, stream=sst.cuda_stream)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=sst):
+        for _ in range(K):
+            pkg.elastic_solve(scene, sx, sy, stream=torch.cuda.current_stream().cuda_stream)
+    with torch.cuda.stream(sst):
+        g.replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sst)
+        for _ in range(3):
+            g.replay()
+        e1.record(sst)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / (3 * K)
+    alg = 2 * info["nnz_L"] * 12 + 4 * n3 * 8
+    kb = 2 * info["nnz_Linv"] * 12 + 4 * n3 * 8
+    peak, src = peaks()
+    return {"kernel": "k_spmv_chunks x2 (A^-1 = P^T S^T S P, FP64, 3 RHS)", "bound": "hbm",
+            "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": src, "ms_per_launch_pair": ms,
+            "algorithmic_bytes": alg, "kernel_bytes": kb, "kernel_bytes_gbs": kb / (ms / 1e3) / 1e9,
+            "kernel_bytes_frac": kb / (ms / 1e3) / 1e9 / peak}
+
+
 def batched(pkg, torch, dev, steps, warmup):
     import synth
     blocks = synth.block_batch(64)
@@ -200,12 +236,13 @@ def batched(pkg, torch, dev, steps, warmup):
     for k in ("mixed_grads", "fp64_grads"):
         res.pop(k)
     info = scene.info()
+    roof = apply_roofline(pkg, torch, dev, scene, 10)
     return {"workload": f"64 independent blocks, {scene.n_tets} tets / {scene.n_verts} verts in total "
                         f"(log-uniform 2k..50k tets each), {nc} contacts in {sum(1 for v in verts if len(v))} blocks, "
                         "one adjoint step of every block per call",
             "fp64": res["fp64"], "mixed": res["mixed"], "max_rel_err_mixed_vs_fp64": err,
             "scene_build_s": t_build, "nnz_Linv": info["nnz_Linv"], "forward_newton_iters": fs["newton_iters"],
-            "forward_residual": fs["residual"]}
+            "forward_residual": fs["residual"], "roofline_Ainv": roof}
 
 
 def sphere(pkg, torch, dev, steps, warmup):
@@ -525,42 +562,9 @@ def main():
     hbm_peak, hbm_src = peaks()
     launches = int(statistics.median(s["kernel_launches"] for s in stats))
     n3 = 3 * sc.n_verts
-    sx = torch.randn(sc.n_verts, 3, dtype=torch.float64, device=dev)
-    sy = torch.empty_like(sx)
-    sst = torch.cuda.Stream(dev)
-    for _ in range(5):
-        pkg.elastic_solve(scene, sx, sy, stream=sst.cuda_stream)
-    torch.cuda.synchronize(dev)
-    # the applies are captured into one CUDA graph and replayed, so that the events time the kernels
-    # back to back rather than the host's launch rate
-    K = 50
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=sst):
-        for _ in range(K):
-            pkg.elastic_solve(scene, sx, sy, stream=torch.cuda.current_stream().cuda_stream)
-    with torch.cuda.stream(sst):
-        g.replay()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(sst)
-        for _ in range(3):
-            g.replay()
-        e1.record(sst)
-    torch.cuda.synchronize(dev)
-    ms_apply = e0.elapsed_time(e1) / (3 * K)
-    # algorithmic bytes of one A^{-1} apply (two triangular solves with the Cholesky factor, each
-    # factor entry read once for the 3 right-hand sides, vectors once per pass): 2 nnz(L) (8 + 4) +
-    # 4 x 3 n_v x 8; the sparse inverse S = L^{-1} the kernels actually read is an implementation
-    # extra (kernel_bytes below)
-    alg = 2 * info["nnz_L"] * 12 + 4 * n3 * 8
-    kb = 2 * info["nnz_Linv"] * 12 + 4 * n3 * 8
-    achieved = alg / (ms_apply / 1e3) / 1e9
-    roof = {"kernel": "k_spmv_chunks x2 (A^-1 = P^T S^T S P, FP64, 3 RHS)", "bound": "hbm", "achieved": achieved,
-            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-            "peak_source": hbm_src, "ms_per_launch_pair": ms_apply, "algorithmic_bytes": alg,
-            "kernel_bytes": kb, "kernel_bytes_gbs": kb / (ms_apply / 1e3) / 1e9,
-            "note": "burst figure: 150 applies replayed back to back from a captured graph, S and S^T "
-                    "(53 MB on the beam) L2-resident between launches"}
+    roof = apply_roofline(pkg, torch, dev, scene, 50)
+    roof["note"] = ("burst figure: applies replayed back to back from a captured graph, S and S^T "
+                    "(53 MB on the beam) L2-resident between launches")
 
     # ---- the batched workload ----
     batch_res = None

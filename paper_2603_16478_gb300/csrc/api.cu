@@ -757,11 +757,9 @@ struct Engine {
     // V_{j+1} = A z
     launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
                         mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st);
-    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs, st);
-    launch_multi_axpy_idx(N, V, N, jp, gs, V, st);
-    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs + (m + 1), st);
-    launch_multi_axpy_idx(N, V, N, jp, gs + (m + 1), V, st);
-    launch_multi_dot_idx(N, m, V, N, jp, true, partial, nrm2, st);
+    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs, st);                  // pass 1 products
+    launch_axpy_dot_idx(N, m, V, N, jp, gs, false, partial, gs + (m + 1), st);     // pass 1 update, pass 2 products
+    launch_axpy_dot_idx(N, m, V, N, jp, gs + (m + 1), true, partial, nrm2, st);    // pass 2 update, norm
     launch_normalize_idx(N, V, N, jp, nrm2, gs + 2 * (m + 1), st);
     launch_export_step(gs, 2 * (m + 1) + 1, S.gs_map_dev, jp, st);
   }

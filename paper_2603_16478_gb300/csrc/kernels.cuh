@@ -168,6 +168,9 @@ void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* 
 //   V_{j+1} -= sum_k coef[k] V_k ;  V_{j+1} /= sqrt(*nrm2) (norm to *h_slot)
 void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const double* coef, double* Vw,
                            cudaStream_t s);
+//   V_{j+1} -= sum_k coef[k] V_k, then out[k] = V_k . V_{j+1} (k <= j), or |V_{j+1}|^2 with norm
+void launch_axpy_dot_idx(int n, int mmax, double* V, long ld, const int* jp, const double* coef, bool norm,
+                         double* partial, double* out, cudaStream_t s);
 void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s);
 //   gs[0..len) to host-mapped slot j % 2, then *jp = j + 1
 void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s);
