@@ -194,8 +194,8 @@ typedef struct {
  *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default) or
  *              NCPADJ_MIXED (inverted and applied in FP32; it only preconditions, so the result
  *              keeps the solve's precision and tolerance).
- *   cap_block  most contacts per directly inverted capacitance block (0 = default = 1365, the
- *              most the direct inverse takes; larger values are clamped to it).  A scene with
+ *   cap_block  most contacts per directly inverted capacitance block (0 = default = 2730 with an
+ *              FP32 capacitance, 1365 with FP64; at most 5461 resp. 1365).  A scene with
  *              more contacts has its capacitance solved iteratively (Sec. 4.4): an inner
  *              right-preconditioned GMRES to relative residual 1e-6 applies the capacitance
  *              without forming it (a scatter and a gather along the contacts' elimination-tree
@@ -257,7 +257,8 @@ ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre);
  * preconditioner (Sec. 4.4); exposed so that the inversion can be used and checked on its own.
  * C, Cinv: device arrays [n*n] (not aliased; C is not modified).  precision NCPADJ_FP64 computes
  * in FP64; NCPADJ_MIXED rounds C to FP32 and computes in FP32 (the result is returned as double).
- * 1 <= n <= 4096.  Synchronises the stream (it reads the pivot status).  Uses workspace owned by
+ * 1 <= n <= 16384 (FP64: n <= 4096, else UNSUPPORTED).  Synchronises the stream (it reads the
+ * pivot status).  Uses workspace owned by
  * the context (allocated on first use, grown as needed).
  * Errors: INVALID_ARG, NONFINITE (a zero pivot: C is singular in the working precision),
  * TIMEOUT, UNSUPPORTED (the cooperative launch was refused), OOM, CUDA. */

@@ -377,7 +377,11 @@ struct Engine {
     // blocks above the direct inverse's size (or the caller's limit) are split into contiguous,
     // nearly equal groups; the Delassus coupling between groups is left out of the preconditioner
     {
-      const int lim = cap_block > 0 ? std::min(cap_block, gj_cols_max_dim() / 3) : gj_cols_max_dim() / 3;
+      // direct inverse up to 2,730 contacts (8,190 rows) by default: beyond that the inversion, DRAM
+      // bound at ~2n^3/BP bytes, costs more than the inner iterations; FP64 stops at 4,096 rows
+      const int dmax = (cap_fp32 ? std::min(gj_cols_max_dim(), 8190) : gj_cols_max_dim64()) / 3;
+      const int lim = cap_block > 0 ? std::min(cap_block, (cap_fp32 ? gj_cols_max_dim() : gj_cols_max_dim64()) / 3)
+                                    : dmax;
       std::vector<int> c0s, ncs;
       sup_c0.clear();
       sup_nc.clear();
@@ -520,7 +524,7 @@ struct Engine {
         NCPADJ_CUDA_TRY(cudaGetLastError());
         if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
         bool ok;
-        const bool cols = n_ <= gj_cols_max_dim();
+        const bool cols = n_ <= (cap_fp32 ? gj_cols_max_dim() : gj_cols_max_dim64());
         if (cap_fp32) {
           launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
           ok = cols ? launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st)
@@ -757,9 +761,11 @@ struct Engine {
     // V_{j+1} = A z
     launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
                         mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st);
-    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs, st);                  // pass 1 products
-    launch_axpy_dot_idx(N, m, V, N, jp, gs, false, partial, gs + (m + 1), st);     // pass 1 update, pass 2 products
-    launch_axpy_dot_idx(N, m, V, N, jp, gs + (m + 1), true, partial, nrm2, st);    // pass 2 update, norm
+    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs, st);
+    launch_multi_axpy_idx(N, V, N, jp, gs, V, st);
+    launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs + (m + 1), st);
+    launch_multi_axpy_idx(N, V, N, jp, gs + (m + 1), V, st);
+    launch_multi_dot_idx(N, m, V, N, jp, true, partial, nrm2, st);
     launch_normalize_idx(N, V, N, jp, nrm2, gs + 2 * (m + 1), st);
     launch_export_step(gs, 2 * (m + 1) + 1, S.gs_map_dev, jp, st);
   }

@@ -342,7 +342,8 @@ bool cols_launch(int n, T* A, T* Pbuf, T* colbuf, int32_t* piv, ColsSync sy, int
 // scratch: kSyncBytes of sync words (ready[np], abort, done) at a fixed place -- every launch
 // leaves them zero, whatever its n and type, so one scratch serves inversions of any size --
 // then Pbuf [np][n][BP] and colbuf [np][BP][n] (global-column mode)
-constexpr int kMaxPanels = 8 * kColsThreads / 4;  // n <= 4096 with panels of >= 4 columns
+constexpr int kMaxDim = 32 * kColsThreads;         // n <= 16384
+constexpr int kMaxPanels = kMaxDim / 2;            // panels of >= 2 columns
 constexpr size_t kSyncBytes = ((sizeof(int) * (kMaxPanels + 4) + 255) / 256) * 256;
 template <typename T, int BP>
 struct ColsLayout {
@@ -352,11 +353,30 @@ struct ColsLayout {
   explicit ColsLayout(int n) : np((n + BP - 1) / BP), pbuf_elems((size_t)((n + BP - 1) / BP) * BP * n) {}
 };
 
+// n in (4096, 16384]: the register panel stays at rows x width <= 64 values with panels of 4 (n <= 8192)
+// or 2 columns; columns live in global memory (the matrix exceeds the shared memory of all blocks)
+template <typename T, int BPW, int ROWS>
+bool cols_invert_wide(int n, T* A, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {
+  const ColsLayout<T, BPW> L(n);
+  const int G = L.np < sm_count ? L.np : sm_count;
+  int* words = static_cast<int*>(scratch);
+  T* Pbuf = reinterpret_cast<T*>(static_cast<char*>(scratch) + kSyncBytes);
+  ColsSync sy{words, words + kMaxPanels, words + kMaxPanels + 1};
+  return cols_launch<T, BPW, ROWS, false>(n, A, Pbuf, Pbuf + L.pbuf_elems, piv, sy, flags, G,
+                                            cols_smem<T, BPW>(n, G, false), s);
+}
+
 template <typename T, int BP, int BPL>
 bool cols_invert(int n, T* A, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {
   constexpr size_t kSmemCap = 200 * 1024;
   const int rows = (n + kColsThreads - 1) / kColsThreads;
-  if (rows > 8) return false;
+  if (rows > 32) return false;
+  if constexpr (sizeof(T) == 4) {  // FP64 panels of that height do not fit in registers
+    if (rows > 16) return cols_invert_wide<T, 2, 32>(n, A, scratch, piv, flags, sm_count, s);
+    if (rows > 8) return cols_invert_wide<T, 4, 16>(n, A, scratch, piv, flags, sm_count, s);
+  } else {
+    if (rows > 8) return false;
+  }
   if (rows > 4) {  // n in (2048, 4096]: narrower panels keep the register panel at 8 x BPL
     const ColsLayout<T, BPL> L(n);
     const int G = L.np < sm_count ? L.np : sm_count;
@@ -404,13 +424,12 @@ void launch_unpermute_inverse(int n, const void* B, bool fp32, const int32_t* pi
 }
 
 size_t gj_cols_scratch_bytes(int n, bool fp32) {
-  const bool narrow = n > 4 * kColsThreads;
-  size_t b;
-  if (fp32) b = narrow ? ColsLayout<float, kBP32 / 2>(n).bytes() : ColsLayout<float, kBP32>(n).bytes();
-  else b = narrow ? ColsLayout<double, kBP64 / 2>(n).bytes() : ColsLayout<double, kBP64>(n).bytes();
-  return b + 256;
+  // the published panels and the column store hold about n^2 values whatever the panel width
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  return kSyncBytes + 2 * es * (size_t)n * ((size_t)n + 32) + 256;
 }
-int gj_cols_max_dim() { return 8 * kColsThreads; }
+int gj_cols_max_dim() { return kMaxDim; }
+int gj_cols_max_dim64() { return 8 * kColsThreads; }
 size_t gj_cols_reserved_bytes() { return kSyncBytes; }
 
 bool launch_gj_cols32(int n, float* C, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {

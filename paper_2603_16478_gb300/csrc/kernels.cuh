@@ -168,9 +168,6 @@ void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* 
 //   V_{j+1} -= sum_k coef[k] V_k ;  V_{j+1} /= sqrt(*nrm2) (norm to *h_slot)
 void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const double* coef, double* Vw,
                            cudaStream_t s);
-//   V_{j+1} -= sum_k coef[k] V_k, then out[k] = V_k . V_{j+1} (k <= j), or |V_{j+1}|^2 with norm
-void launch_axpy_dot_idx(int n, int mmax, double* V, long ld, const int* jp, const double* coef, bool norm,
-                         double* partial, double* out, cudaStream_t s);
 void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s);
 //   gs[0..len) to host-mapped slot j % 2, then *jp = j + 1
 void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s);
@@ -207,7 +204,8 @@ bool launch_gj_invert32(int n, float* C, float* tmp, int32_t* piv, int* flags, i
 // holds gj_cols_scratch_bytes(n) bytes and must be zero before its first use (the kernel leaves its
 // flags zero).  Returns false without launching when n > gj_cols_max_dim() or the launch is refused.
 size_t gj_cols_scratch_bytes(int n, bool fp32);
-int gj_cols_max_dim();
+int gj_cols_max_dim();    // FP32
+int gj_cols_max_dim64();  // FP64
 // the first gj_cols_reserved_bytes() of that scratch hold its flags: other users of the same
 // buffer must start after them
 size_t gj_cols_reserved_bytes();

@@ -794,65 +794,6 @@ __global__ void k_multi_dot_idx(int n, const double* __restrict__ V, long ld, co
     cnt[k] = 0;
   }
 }
-// Fused Gram-Schmidt pass: V_{j+1} -= sum_{k <= j} coef[k] V_k, then (norm == 0) out[k] = V_k . V_{j+1}
-// for k <= j, or (norm == 1) out[0] = |V_{j+1}|^2.  A block updates its own slice of V_{j+1} and takes
-// its partial products from that same slice, so one launch does both; the last block to finish
-// (counted in cnt[0], which it resets) sums the partials in block order.
-__global__ void __launch_bounds__(256) k_axpy_dot_idx(int n, double* __restrict__ V, long ld,
-                                                      const int* __restrict__ jp, const double* __restrict__ coef,
-                                                      int norm, double* partial, unsigned* cnt, double* out) {
-  const int j = *jp;
-  const int nb = gridDim.x, b = blockIdx.x;
-  double* w = V + (size_t)(j + 1) * ld;
-  const long per = (n + nb - 1) / nb;
-  const long i0 = (long)b * per, i1 = min((long)n, i0 + per);
-  __shared__ double sh[8][32];
-  __shared__ bool last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    double acc = w[i];
-    for (int k = 0; k <= j; ++k) acc -= coef[k] * V[(size_t)k * ld + i];
-    w[i] = acc;
-  }
-  const int nout = norm ? 1 : j + 1;
-  for (int k0 = 0; k0 < nout; k0 += 32) {  // 32 products at a time per thread
-    double acc[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-    for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int q = 0; q < 32; ++q)
-        if (k0 + q < nout) acc[q] += (norm ? wi : V[(size_t)(k0 + q) * ld + i]) * wi;
-    }
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const double v = warp_sum(acc[q]);
-      if (lane == q) sh[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32 && k0 + threadIdx.x < nout) {
-      double t = 0.0;
-      for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) t += sh[wv][threadIdx.x];
-      partial[(size_t)(k0 + threadIdx.x) * nb + b] = t;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&cnt[0], 1u) == (unsigned)nb - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int k = threadIdx.x; k < nout; k += blockDim.x) {
-    double t = 0.0;
-    for (int q = 0; q < nb; ++q) t += __ldcg(&partial[(size_t)k * nb + q]);
-    out[k] = t;
-  }
-  if (threadIdx.x == 0) cnt[0] = 0;
-}
-
 // V_{j+1} -= sum_{k <= j} coef[k] V_k
 __global__ void k_multi_axpy_idx(int n, const double* __restrict__ V, long ld, const int* __restrict__ jp,
                                  const double* __restrict__ coef, double* __restrict__ Vw) {
@@ -1193,17 +1134,6 @@ void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* 
   if (nb > 64) nb = 64;
   unsigned* cnt = reinterpret_cast<unsigned*>(partial + 64 * (size_t)kMaxDotVectors);
   k_multi_dot_idx<<<dim3(nb, self ? 1 : mmax + 1), 256, 0, s>>>(n, V, ld, jp, self ? 1 : 0, partial, cnt, out);
-}
-void launch_axpy_dot_idx(int n, int mmax, double* V, long ld, const int* jp, const double* coef, bool norm,
-                         double* partial, double* out, cudaStream_t s) {
-  g_launches += 1;
-  int nb = nblk(n, 256);
-  const int cap = (int)((64 * (size_t)kMaxDotVectors) / (size_t)(mmax + 1));
-  if (nb > 304) nb = 304;
-  if (nb > cap) nb = cap;
-  // the counter sits after the per-vector counters of the multi-dot kernels
-  unsigned* cnt = reinterpret_cast<unsigned*>(partial + 64 * (size_t)kMaxDotVectors) + kMaxDotVectors - 1;
-  k_axpy_dot_idx<<<nb, 256, 0, s>>>(n, V, ld, jp, coef, norm ? 1 : 0, partial, cnt, out);
 }
 void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const double* coef, double* Vw,
                            cudaStream_t s) {
