@@ -419,6 +419,8 @@ def main():
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
     ap.add_argument("--quadruped", action="store_true", help="add the actuated quadruped measurement")
     ap.add_argument("--quad-scale", type=float, default=1.0, help="linear scale of the quadruped (1 = full size)")
+    ap.add_argument("--roofline-only", choices=["beam", "batched"], default=None,
+                    help="build the scene and run only the A^-1 roofline measurement (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -438,6 +440,18 @@ def main():
     g.build()
     import paper_2603_16478_gb300 as pkg
     import synth
+
+    if args.roofline_only:
+        ctx = pkg.Context(local)
+        if args.roofline_only == "beam":
+            b = synth.beam_incline().scene
+            scene = pkg.Scene(ctx, b.X, b.tets, b.E, b.nu, b.density, b.h)
+        else:
+            blocks = synth.block_batch(64)
+            scene = pkg.Scene.batch(ctx, [(x.scene.X, x.scene.tets, x.scene.E, x.scene.nu, x.scene.density)
+                                          for x in blocks], blocks[0].scene.h)
+        print(json.dumps({"roofline_only": args.roofline_only, "roofline": apply_roofline(pkg, torch, dev, scene, 10)}))
+        return
 
     pb = synth.beam_incline()
     sc = pb.scene

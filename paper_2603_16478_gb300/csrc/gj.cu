@@ -39,9 +39,34 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <typename T> struct Vec64;  // 64 bytes of a published panel row
-template <> struct Vec64<float> { using V = float4; static constexpr int W = 4; };
-template <> struct Vec64<double> { using V = double2; static constexpr int W = 2; };
+// Vector accesses to panel rows (BP values, rows BP * sizeof(T) bytes apart): the widest of 16, 8 or
+// 4 (8) bytes whose element count W divides BP, so that every access is aligned and inside its row.
+template <typename T, int W> struct VecN;
+template <> struct VecN<float, 4> { using V = float4; };
+template <> struct VecN<float, 2> { using V = float2; };
+template <> struct VecN<float, 1> { using V = float; };
+template <> struct VecN<double, 2> { using V = double2; };
+template <> struct VecN<double, 1> { using V = double; };
+template <typename T, int BP> constexpr int vec_width() {
+  int w = 16 / (int)sizeof(T);
+  while (w > 1 && BP % w != 0) w /= 2;
+  return w;
+}
+template <typename T, int BP> struct RowVec {
+  static constexpr int W = vec_width<T, BP>();
+  using V = typename VecN<T, W>::V;
+};
+__device__ __forceinline__ void unpack(const float4& v, float* d) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+__device__ __forceinline__ void unpack(const float2& v, float* d) { d[0] = v.x; d[1] = v.y; }
+__device__ __forceinline__ void unpack(const float& v, float* d) { d[0] = v; }
+__device__ __forceinline__ void unpack(const double2& v, double* d) { d[0] = v.x; d[1] = v.y; }
+__device__ __forceinline__ void unpack(const double& v, double* d) { d[0] = v; }
+template <typename V, typename T> __device__ __forceinline__ V pack(const T* d);
+template <> __device__ __forceinline__ float4 pack<float4, float>(const float* d) { return make_float4(d[0], d[1], d[2], d[3]); }
+template <> __device__ __forceinline__ float2 pack<float2, float>(const float* d) { return make_float2(d[0], d[1]); }
+template <> __device__ __forceinline__ float pack<float, float>(const float* d) { return d[0]; }
+template <> __device__ __forceinline__ double2 pack<double2, double>(const double* d) { return make_double2(d[0], d[1]); }
+template <> __device__ __forceinline__ double pack<double, double>(const double* d) { return d[0]; }
 
 template <typename T> __device__ __forceinline__ unsigned abs_key(T v);
 template <> __device__ __forceinline__ unsigned abs_key<float>(float v) { return __float_as_uint(fabsf(v)) + 1u; }
@@ -156,8 +181,8 @@ __global__ void __launch_bounds__(kColsThreads) k_gj_cols(int n, T* __restrict__
     }
     if (!ok) return false;
     // keep the panel (it becomes columns of the inverse) and publish it row-major
-    using V = typename Vec64<T>::V;
-    constexpr int W = Vec64<T>::W;
+    using V = typename RowVec<T, BP>::V;
+    constexpr int W = RowVec<T, BP>::W;
 #pragma unroll
     for (int k = 0; k < ROWS; ++k) {
       const int i = tid + k * kColsThreads;
@@ -166,12 +191,7 @@ __global__ void __launch_bounds__(kColsThreads) k_gj_cols(int n, T* __restrict__
         for (int c = 0; c < BP; ++c) pc[(size_t)c * n + i] = Pr[k][c];
         V* dst = reinterpret_cast<V*>(Pbuf + ((size_t)p * n + i) * BP);
 #pragma unroll
-        for (int c = 0; c < BP; c += W) {
-          V v;
-          if constexpr (W == 4) v = make_float4(Pr[k][c], Pr[k][c + 1], Pr[k][c + 2], Pr[k][c + 3]);
-          else v = make_double2(Pr[k][c], Pr[k][c + 1]);
-          __stcg(dst + c / W, v);
-        }
+        for (int c = 0; c < BP; c += W) __stcg(dst + c / W, pack<V, T>(&Pr[k][c]));
       }
     }
     return true;
@@ -194,19 +214,15 @@ __global__ void __launch_bounds__(kColsThreads) k_gj_cols(int n, T* __restrict__
   // apply panel p (staged old pivot rows in MR) to my panel q: one row per thread, BP accumulators
   auto update = [&](int q, int p) {
     const int bb = min(BP, n - p * BP);
-    using V = typename Vec64<T>::V;
-    constexpr int W = Vec64<T>::W;
+    using V = typename RowVec<T, BP>::V;
+    constexpr int W = RowVec<T, BP>::W;
     T* pc = pan(q);
     const T* mr = MR + q * BP;
     for (int i = tid; i < n; i += kColsThreads) {
       T P[BP];
       const V* src = reinterpret_cast<const V*>(Pbuf + ((size_t)p * n + i) * BP);
 #pragma unroll
-      for (int c = 0; c < BP; c += W) {
-        const V v = __ldcg(src + c / W);
-        if constexpr (W == 4) { P[c] = v.x; P[c + 1] = v.y; P[c + 2] = v.z; P[c + 3] = v.w; }
-        else { P[c] = v.x; P[c + 1] = v.y; }
-      }
+      for (int c = 0; c < BP; c += W) unpack(__ldcg(src + c / W), &P[c]);
       const bool is_piv = panel_of[i] == p;
       T acc[BP];
 #pragma unroll
@@ -217,13 +233,10 @@ __global__ void __launch_bounds__(kColsThreads) k_gj_cols(int n, T* __restrict__
           const V* row = reinterpret_cast<const V*>(mr + (size_t)t * ncol);  // broadcast
 #pragma unroll
           for (int c = 0; c < BP; c += W) {
-            const V v = row[c / W];
-            if constexpr (W == 4) {
-              acc[c] = fma(P[t], v.x, acc[c]); acc[c + 1] = fma(P[t], v.y, acc[c + 1]);
-              acc[c + 2] = fma(P[t], v.z, acc[c + 2]); acc[c + 3] = fma(P[t], v.w, acc[c + 3]);
-            } else {
-              acc[c] = fma(P[t], v.x, acc[c]); acc[c + 1] = fma(P[t], v.y, acc[c + 1]);
-            }
+            T m[W];
+            unpack(row[c / W], m);
+#pragma unroll
+            for (int u = 0; u < W; ++u) acc[c + u] = fma(P[t], m[u], acc[c + u]);
           }
         }
       }
