@@ -31,7 +31,11 @@
  *    launch.  ncpadj_last_error() returns a thread-local message for the last failure.
  *  - Streams: the stream is borrowed (cudaStream_t passed as void*; NULL = legacy default
  *    stream).  ncpadj_adjoint_step synchronises that stream before it returns (it reads the
- *    solver status), so it is not capturable in a CUDA graph.
+ *    solver status), so it is not capturable in a CUDA graph.  On a stream other than the legacy
+ *    default stream, the adjoint captures one GMRES step (Woodbury with directly inverted
+ *    capacitance blocks) into a CUDA graph owned by the scene and replays it once per step; the
+ *    graph is rebuilt when the scene's workspace or the contact arrays change.  On the legacy
+ *    default stream the same kernels are launched one by one.
  *  - Threads: a scene's workspace is used by every call on that scene; calls on the same
  *    scene must not overlap.
  */
@@ -114,7 +118,9 @@ void ncpadj_scene_destroy(ncpadj_scene scene);
  * built independently (host threads); the union's matrices are block-diagonal.  In
  * ncpadj_adjoint_step / ncpadj_forward_step on a batch:
  *  - contacts must be grouped by mesh (non-decreasing mesh of their vertex); the contact
- *    capacitance is inverted block by block, one dense block per mesh with contacts;
+ *    capacitance is inverted block by block, one dense block per mesh with contacts (a mesh
+ *    with more contacts than ncpadj_options.cap_block allows is solved iteratively, see there);
+ *  - the forward step gives each mesh its own line search;
  *  - the adjoint scales each mesh's right-hand side to unit norm and tightens the tolerance to
  *    rtol / sqrt(number of meshes with a nonzero seed), so every mesh's own relative residual is
  *    at most rtol (the scaling is undone before the contractions).
@@ -269,8 +275,8 @@ ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, d
  * For callers that cannot have device memory allocated while they run -- programs whose device
  * memory is reserved up front by their own pool, or loops with hard latency limits where a
  * cudaMalloc is not acceptable.  Same arguments and result as ncpadj_elastic_solve; the
- * intermediate vector lives in a static device array sized for at most 262,144 vertices
- * (6 MiB, held by every GPU that loads the library until the process exits).
+ * intermediate vectors live in a static device array sized for at most 262,144 vertices
+ * (12 MiB, held by every GPU that loads the library until the process exits).
  *  - Scenes with more vertices are rejected with NCPADJ_ERR_INVALID_ARG.
  *  - The call makes no cudaMalloc or cudaFree.  Its first call on a device looks up the
  *    array's device address (cudaGetSymbolAddress); make that first call before any stream

@@ -232,7 +232,7 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
       Su.ptr.push_back(so + P.F.S.ptr[r + 1]);
       Stu.ptr.push_back(sto + P.F.St.ptr[r + 1]);
     }
-    for (int32_t c : P.F.S.col) Su.col.push_back(P.F.perm[c] + vo);  // rows of S gather by original id
+    for (int32_t c : P.F.S.col) Su.col.push_back(c + vo);  // position space (x is permuted first)
     Su.val.insert(Su.val.end(), P.F.S.val.begin(), P.F.S.val.end());
     for (int32_t c : P.F.St.col) Stu.col.push_back(c + vo);  // position space
     Stu.val.insert(Stu.val.end(), P.F.St.val.begin(), P.F.St.val.end());
@@ -486,6 +486,9 @@ struct Engine {
                     S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                     S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                     S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};
+    S.xpos.ensure(sizeof(double) * N + sizeof(float) * N + 64);
+    sinv.xpos = S.xpos.as<double>();
+    sinv.xpos32 = reinterpret_cast<float*>(S.xpos.as<double>() + N);
   }
 
   ContactArgs contact_args(const double* q, const double* q_prev, const double* lambda, double eps) const {
@@ -1617,6 +1620,8 @@ ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const dou
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
+    S.xpos.ensure(sizeof(double) * 3 * (size_t)S.nv + 64);
+    a.xpos = S.xpos.as<double>();
     launch_ainv(a, x, S.io.as<double>(), y, st);
     NCPADJ_CUDA_TRY(cudaGetLastError());
     return NCPADJ_OK;

@@ -113,6 +113,7 @@ struct Scene {
   DevBuf io;                      // staging for host-memory calls
   DevBuf gmres;                   // GMRES basis + Hessenberg
   DevBuf fgmres;                  // flexible GMRES: preconditioned basis Z
+  DevBuf xpos;                    // x in elimination order before the product with S (FP64, FP32)
   DevBuf inner;                   // inner GMRES on the capacitance: basis and scratch
   DevBuf fwd;                     // forward Newton vectors
   DevBuf fibre;                   // double [nt][3] actuation fibres (empty: none set)

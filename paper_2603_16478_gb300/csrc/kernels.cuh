@@ -153,6 +153,11 @@ struct SinvArgs {
   const int32_t *S_crow, *St_crow;
   const int64_t *S_cbeg, *S_cend, *St_cbeg, *St_cend;
   const float *S_val32 = nullptr, *St_val32 = nullptr;  // FP32 copies (mixed precision)
+  // scratch [nv][3]: x permuted to elimination (position) order before the product with S, whose
+  // columns are positions -- row p of S covers the descendants of p, a contiguous position range,
+  // so the product gathers x contiguously
+  double* xpos = nullptr;
+  float* xpos32 = nullptr;
 };
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
 // Step-indexed forms for a captured GMRES step (j = *jp on the device; V_{j+1} = V + (j + 1) ld):

@@ -186,6 +186,18 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
   }
 }
 
+// out[3p + r] = x[3 perm[p] + r] (x taken at x + (*jp) * ld when jp is given): the input of the
+// product with S, whose columns are elimination positions
+template <typename O>
+__global__ void k_to_position(int nv, const double* __restrict__ x, const int* __restrict__ jp, long ld,
+                              const int32_t* __restrict__ perm, O* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nv) return;
+  if (jp) x += (size_t)(*jp) * ld;
+  const int p = i / 3, r = i - 3 * p;
+  out[i] = (O)x[3 * (size_t)perm[p] + r];
+}
+
 // Contact rows of A^{-1} x from w = S P x: (A^{-1} x)_v = sum_i S[i][p(v)] w_i, and column p(v) of S
 // (row p(v) of S^T) lives on the elimination-tree path from p(v) to the root.  One warp per
 // contact walks that path; the result u_c is turned into s_c = K'_c F_c u_c at once (K' = K^T for
@@ -932,23 +944,12 @@ __global__ void k_to_float(int n, const double* __restrict__ x, float* __restric
   if (i < n) y[i] = (float)x[i];
 }
 
-void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s) {
-  g_launches += 3;
-  const int n = 3 * a.nv;
-  k_to_float<<<nblk(n, 256), 256, 0, s>>>(n, x, x32);
-  cudaMemsetAsync(w32, 0, sizeof(float) * n, s);
-  k_spmv_chunks<float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend,
-                                                                           a.S_col, a.S_val32, nullptr, x32, w32);
-  cudaMemsetAsync(y, 0, sizeof(double) * n, s);
-  k_spmv_chunks<float, float, double, float><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend,
-                                                                             a.St_col, a.St_val32, a.perm, w32, y);
-}
-
 void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s) {
-  g_launches += 1;
+  g_launches += 2;
+  k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos);
   cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
   k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend,
-                                                                              a.S_col, a.S_val, nullptr, x, w);
+                                                                              a.S_col, a.S_val, nullptr, a.xpos, w);
 }
 void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s) {
   g_launches += 1;
@@ -958,10 +959,11 @@ void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream
                                                                                w, y);
 }
 void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s) {
-  g_launches += 1;
+  g_launches += 2;
+  k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos32);
   cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<float, double, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, x, w32);
+  k_spmv_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32);
 }
 void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s) {
   g_launches += 1;
@@ -994,13 +996,13 @@ void launch_path_scatter(int nc, const int32_t* cvertex, const int32_t* iperm, c
 }
 
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s) {
-  g_launches += 2;
-  cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr,
-                                                      x, w);
-  cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<double, double, double><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val,
-                                                       a.perm, w, y);
+  launch_sinv_half1(a, x, w, s);
+  launch_sinv_half2(a, w, y, s);
+}
+void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s) {
+  (void)x32;
+  launch_sinv_half1_32(a, x, w32, s);
+  launch_sinv_half2_32(a, w32, y, s);
 }
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
                      const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s) {
@@ -1156,15 +1158,17 @@ void launch_bsr_spmv_idx(int nv, const int32_t* rp, const int32_t* col, const do
 }
 void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, const int* jp, double* w, float* w32,
                            cudaStream_t s) {
-  g_launches += 1;
+  g_launches += 2;
   if (w32) {
+    k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos32);
     cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
-    k_spmv_chunks<float, double, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, xbase, w32, jp, xld);
+    k_spmv_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32);
   } else {
+    k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos);
     cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
     k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, xbase, w, jp, xld);
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, a.xpos, w);
   }
 }
 void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {

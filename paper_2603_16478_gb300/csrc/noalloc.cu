@@ -19,7 +19,7 @@ namespace {
 // float64 vector, 6 MiB.  Every GPU that loads this library holds the array until the process
 // exits.
 constexpr int kNoAllocMaxVerts = 262144;
-__device__ __align__(256) double g_noalloc_scratch[3 * (size_t)kNoAllocMaxVerts];
+__device__ __align__(256) double g_noalloc_scratch[2 * 3 * (size_t)kNoAllocMaxVerts];  // w, then x permuted
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
@@ -58,6 +58,7 @@ extern "C" ncpadj_status ncpadj_elastic_solve_noalloc(ncpadj_ctx ctx, ncpadj_sce
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
+    a.xpos = w + 3 * (size_t)kNoAllocMaxVerts;
     // the product zeroes the scratch before accumulating into it, so earlier calls leave nothing behind
     launch_ainv(a, x, w, y, (cudaStream_t)stream);
     NCPADJ_CUDA_TRY(cudaGetLastError());
