@@ -739,7 +739,8 @@ struct Engine {
                                 (uintptr_t)transpose, (uintptr_t)in.cvertex, (uintptr_t)in.frame,
                                 (uintptr_t)S.gmres.p, (uintptr_t)S.vecs.p, (uintptr_t)S.red.p, (uintptr_t)S.scal.p,
                                 (uintptr_t)S.cap.p, (uintptr_t)S.vec32.p, (uintptr_t)S.cdata.p, (uintptr_t)S.bsr32.p,
-                                (uintptr_t)S.bsr64.p, (uintptr_t)blk_c0.size()};
+                                (uintptr_t)S.bsr64.p, (uintptr_t)S.xpos.p, (uintptr_t)S.gstep.p,
+                                (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size()};
     for (size_t b = 0; b < blk_c0.size(); ++b) {
       k.push_back((uintptr_t)blk_c0[b]);
       k.push_back((uintptr_t)blk_nc[b]);
@@ -1240,6 +1241,9 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   E.in.region = nc ? ct->region : nullptr;
   E.in.q_prev = fin->q_prev;
   int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
+  // the Newton solves run in FP64; the capacitance (a preconditioner only) follows cap_precision
+  E.cap_fp32 = opt.cap_precision == NCPADJ_MIXED;
+  E.cap_block = opt.cap_block;
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);  // before any indexing

@@ -27,8 +27,11 @@ def _cases():
     return [step_case("cube_drop", 2), step_case("two_tet", 1), step_case("cube_drop", 5), step_case("cube_drop", 0)]
 
 
+@pytest.mark.parametrize("side_stream", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_equals_single_scene_adjoints(pkg, precision):
+def test_batch_equals_single_scene_adjoints(pkg, precision, side_stream):
+    """On a side stream the GMRES steps are replays of a captured graph (several capacitance
+    blocks in one step); on the default stream the same kernels are launched one by one."""
     ctx = pkg.Context(0)
     cases = _cases()
     rng = np.random.default_rng(0)
@@ -59,10 +62,12 @@ def test_batch_equals_single_scene_adjoints(pkg, precision):
         dvs.append(dv)
     contacts = pkg.Contacts(T(np.concatenate(vert), torch.int32), T(np.concatenate(frame)), T(np.concatenate(dn)),
                             T(np.concatenate(mu)), None, T(np.concatenate(region), torch.int32), nreg)
+    stream = torch.cuda.Stream() if side_stream else None
+    torch.cuda.synchronize()
     g, stats = pkg.adjoint_step(batch, contacts, T(np.concatenate(q)), T(np.concatenate(qp)), T(np.concatenate(lam)),
                                 T(np.concatenate(dqs)), T(np.concatenate(dvs)), eps=cases[0][0].scene.eps,
                                 rtol=1e-12 if precision == "fp64" else 1e-8, precision=precision,
-                                cap_precision=precision)
+                                cap_precision=precision, stream=None if stream is None else stream.cuda_stream)
     torch.cuda.synchronize()
     tol = 1e-8 if precision == "fp64" else 1e-3
     toff = batch.tet_offsets
