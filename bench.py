@@ -199,7 +199,7 @@ def batched(pkg, torch, dev, steps, warmup):
     # iterate reached within 150 steps, whose residual is reported
     try:
         q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(blocks[0].scene.gravity),
-                                      eps=blocks[0].scene.eps, max_newton=150)
+                                      eps=blocks[0].scene.eps, max_newton=150, cap_precision="mixed")
     except pkg.NcpadjError as e:
         if not hasattr(e, "state"):
             raise

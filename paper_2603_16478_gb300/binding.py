@@ -318,7 +318,7 @@ def _contacts_struct(contacts):
 
 def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None, f_ext=None,
                  gravity=(0.0, 0.0, -9.81), *, eps=1e-4, newton_tol=1e-10, max_newton=60, precond="woodbury",
-                 rtol=1e-10, max_iters=2000, restart=64, stream=None, act=None, cap_precision="mixed"):
+                 rtol=1e-10, max_iters=2000, restart=64, stream=None, act=None, cap_precision="fp64"):
     """One forward step on the GPU (device tensors).  ``act``: float32 [n_tets] activations (the
     scene needs fibres, ``Scene.set_fibres``).  Returns (q, lambda [n_c, 3], stats)."""
     lib = scene.lib
@@ -332,7 +332,7 @@ def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
     opt.precond = PRECOND[precond]
-    opt.cap_precision = PRECISION[cap_precision]  # the capacitance only preconditions the Newton solves
+    opt.cap_precision = PRECISION[cap_precision]  # "mixed": FP32 capacitance (it only preconditions)
     stats = _ForwardStats()
     if stream is None and dev.type == "cuda":
         stream = torch.cuda.current_stream(dev).cuda_stream
