@@ -336,7 +336,7 @@ struct Engine {
   bool mixed = false;
   bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
   int cap_block = 0;      // most contacts per capacitance block (0: the largest the direct inverse takes)
-  float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr, *Ctmp32 = nullptr;
+  float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr;
   // the capacitance is block-diagonal by scene (contacts of different meshes share no ancestor
   // in the elimination forest): one dense block per scene that has contacts
   std::vector<int> blk_c0, blk_nc;
@@ -434,11 +434,10 @@ struct Engine {
     if (mixed) S.bsr32.ensure(sizeof(float) * 9 * (size_t)S.nb);
     else S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
     if (mixed || cap_fp32) {
-      S.vec32.ensure(sizeof(float) * (2 * (size_t)N + 2 * cap_elems + 64));
+      S.vec32.ensure(sizeof(float) * (2 * (size_t)N + cap_elems + 64));
       x32 = S.vec32.as<float>();
       w32 = x32 + N;
       Cm32 = w32 + N;
-      Ctmp32 = Cm32 + cap_elems;
     }
     S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
     S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
@@ -454,8 +453,7 @@ struct Engine {
       S.cap.ensure(sizeof(double) * (cap_elems + ds_elems + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
       int nmax = 0;
       for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
-      const size_t wbytes =
-          std::max(gj_cols_reserved_bytes() + gj_scratch_bytes(nmax, C.sm_count), gj_cols_scratch_bytes(nmax, false));
+      const size_t wbytes = gj_cols_scratch_bytes(nmax, false);
       if (S.capw.bytes < wbytes) {  // the column-owned inverse expects its flags zero
         S.capw.ensure(wbytes);
         NCPADJ_CUDA_TRY(cudaMemset(S.capw.p, 0, wbytes));
@@ -527,16 +525,11 @@ struct Engine {
         NCPADJ_CUDA_TRY(cudaGetLastError());
         if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
         bool ok;
-        const bool cols = n_ <= (cap_fp32 ? gj_cols_max_dim() : gj_cols_max_dim64());
         if (cap_fp32) {
           launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
-          ok = cols ? launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st)
-                    : launch_gj_invert32(n_, Cm32 + blk_moff[k], Ctmp32 + blk_moff[k], pb, flags, C.sm_count, st);
+          ok = launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st);
         } else {
-          ok = cols ? launch_gj_cols64(n_, Cb, S.capw.p, pb, flags, C.sm_count, st)
-                    : launch_gj_invert(n_, Cb, pb,
-                                       reinterpret_cast<double*>(S.capw.as<char>() + gj_cols_reserved_bytes()), flags,
-                                       C.sm_count, st);
+          ok = launch_gj_cols64(n_, Cb, S.capw.p, pb, flags, C.sm_count, st);
           if (ok && mixed) launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);  // FP32 apply
         }
         if (!ok) {

@@ -198,14 +198,8 @@ void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const
 // capacitance C = I + h^2 K^T D (3nc x 3nc, row-major)
 void launch_cap_form(int nc, const double* Ds, const double* frame, const double* cdata, double h, int transpose,
                      double* C, cudaStream_t s);
-// in-place Gauss-Jordan inverse with partial pivoting (cooperative); returns false if the
-// launch configuration is impossible (n too large for the shared-memory row blocks)
-bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count,
-                      cudaStream_t s);
-size_t gj_scratch_bytes(int n, int sm_count);
-// FP32 blocked variant (one grid barrier per panel); tmp is an n x n scratch
-bool launch_gj_invert32(int n, float* C, float* tmp, int32_t* piv, int* flags, int sm_count, cudaStream_t s);
-// Column-owned blocked Gauss-Jordan (gj.cu): same result convention as launch_gj_invert.  scratch
+// Column-owned blocked Gauss-Jordan with partial pivoting (gj.cu): C is swept in place into B, the
+// pivot rows go to piv (apply with launch_gj_apply*).  scratch
 // holds gj_cols_scratch_bytes(n) bytes and must be zero before its first use (the kernel leaves its
 // flags zero).  Returns false without launching when n > gj_cols_max_dim() or the launch is refused.
 size_t gj_cols_scratch_bytes(int n, bool fp32);
@@ -225,17 +219,9 @@ void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s);
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
                      cudaStream_t s);
 
-// contact gather/scatter: s_c = K_c^T F_c u_{v_c};  e_{v_c} += F_c^T t_c  (e zeroed first)
-void launch_contact_gather_kt(int nc, const int32_t* cvertex, const double* frame, const double* cdata,
-                              int transpose, const double* u, double* sc, cudaStream_t s);
-void launch_contact_scatter(int nv, int nc, const int32_t* cvertex, const double* frame, const double* t,
-                            double* e, cudaStream_t s);
-
 // vector kernels
 void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
 void launch_rhs(int n, const double* dL_dq, const double* dL_dv, double inv_h, double* b, cudaStream_t s);
-void launch_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y,
-                      cudaStream_t s);
 void launch_mul(int n, const double* a, const double* b, double* y, cudaStream_t s);
 // out[k] = sum_i V_k[i] w[i], k < nvec <= kMaxDotVectors (vectors of length n, stride ld); partial is a
 // scratch of dot_scratch_bytes() whose trailing counters must be zero before the first use (the
@@ -251,9 +237,6 @@ void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* 
 void launch_combine(int n, int nvec, const double* V, long ld, const double* coef, double* y, cudaStream_t s);
 // v_out = w / nrm (nrm on device); writes nrm into H slot too
 void launch_normalize(int n, const double* w, const double* nrm2, double* v_out, double* h_slot, cudaStream_t s);
-// GMRES Givens step for column j (single thread): H [(m+1) x m] column-major, cs, sn, g
-void launch_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res_out, cudaStream_t s);
-void launch_hess_solve(int k, int m, const double* H, const double* g, double* y, cudaStream_t s);
 // CG scalar updates
 void launch_cg_alpha(const double* rz, const double* pAp, double* alpha, cudaStream_t s);
 void launch_cg_update_xr(int n, const double* alpha, const double* p, const double* Ap, double* x, double* r,

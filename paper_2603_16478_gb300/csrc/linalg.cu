@@ -29,34 +29,6 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-__global__ void k_bsr_spmv(int nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 3 * nv) return;
-  const int v = i / 3, r = i - 3 * v;
-  double acc = 0.0;
-  for (int p = rp[v]; p < rp[v + 1]; ++p) {
-    const double* B = val + 9 * (size_t)p + 3 * r;
-    const int c = col[p];
-    acc += B[0] * x[3 * c] + B[1] * x[3 * c + 1] + B[2] * x[3 * c + 2];
-  }
-  y[i] = acc;
-}
-
-__global__ void k_bsr_spmv32(int nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                             const float* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 3 * nv) return;
-  const int v = i / 3, r = i - 3 * v;
-  double acc = 0.0;
-  for (int p = rp[v]; p < rp[v + 1]; ++p) {
-    const float* B = val + 9 * (size_t)p + 3 * r;
-    const int c = col[p];
-    acc += (double)B[0] * x[3 * c] + (double)B[1] * x[3 * c + 1] + (double)B[2] * x[3 * c + 2];
-  }
-  y[i] = acc;
-}
-
 // Half a warp per vertex row: lane l of the half takes blocks rp[v] + l, rp[v] + l + 16, ... and the
 // three row sums are reduced over the half-warp (the row-per-thread form left the GPU nearly empty:
 // one thread per scalar row, each walking its ~15 blocks with dependent loads).
@@ -331,364 +303,6 @@ __global__ void k_cap_form(int nc, const double* __restrict__ Ds, const double* 
 
 // Grid-wide barrier for a cooperative launch, with a bounded wait: after ~1 s of spinning it
 // sets FLAG_TIMEOUT and lets the block go on; every block then stops at its next barrier.
-__device__ bool grid_barrier(int* flags) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile int* vgen = (volatile int*)&flags[FLAG_GEN];
-    const int gen = *vgen;
-    __threadfence();
-    const int arrived = atomicAdd(&flags[FLAG_BARRIER], 1);
-    if (arrived == (int)gridDim.x - 1) {
-      atomicExch(&flags[FLAG_BARRIER], 0);
-      __threadfence();
-      atomicAdd(&flags[FLAG_GEN], 1);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (++spins > (1LL << 24)) {
-          atomicExch(&flags[FLAG_TIMEOUT], 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile int*)&flags[FLAG_TIMEOUT] == 0;
-}
-
-template <typename T>
-struct GJScratch {
-  double* cand_val;  // [2][G]  |pivot candidate| (or -1: no unused row)
-  int* cand_row;     // [2][G]
-  T* cand_data;      // [2][G][n]
-};
-
-// Sweep elimination on pivot pairs (r_k, k): rows are owned round-robin by the blocks and kept
-// in shared memory.  At step k every block agrees on the pivot row r_k (largest |a[i][k]| among
-// rows not used yet; each block published its best candidate row at the end of step k-1), and
-//   a[r][j] <- a[r][j]/p (j != k), a[r][k] <- 1/p,
-//   a[i][j] <- a[i][j] - a[i][k] a[r][j]/p (j != k), a[i][k] <- -a[i][k]/p  (i != r).
-// After n steps the matrix B satisfies  (C^{-1})[k][r_k'] = B[r_k][k'].  One barrier per step.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_gj(int n, int nloc_max, T* C, int32_t* piv, GJScratch<T> sc, int* flags) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int G = gridDim.x, me = blockIdx.x;
-  T* rows = reinterpret_cast<T*>(smraw);          // [nloc_max][n]
-  T* prow = rows + (size_t)nloc_max * n;          // [n]
-  T* fl = prow + n;                               // [nloc_max]
-  int* used = (int*)(fl + nloc_max);              // [nloc_max]
-  __shared__ double red_v[32];
-  __shared__ int red_l[32];
-  __shared__ int s_win, s_row;
-  const int nloc = (me < n) ? (n - me + G - 1) / G : 0;
-  for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
-    const int l = (int)(e / n), j = (int)(e - (long)l * n);
-    rows[e] = C[(size_t)(me + G * l) * n + j];
-  }
-  for (int l = threadIdx.x; l < nloc_max; l += blockDim.x) used[l] = 0;
-  __syncthreads();
-
-  // publish this block's candidate for column col into buffer buf
-  auto publish = [&](int col, int buf) {
-    double best = -1.0;
-    int bl = -1;
-    for (int l = threadIdx.x; l < nloc; l += blockDim.x)
-      if (!used[l]) {
-        const double v = fabs((double)rows[(size_t)l * n + col]);
-        if (v > best) { best = v; bl = l; }
-      }
-    // block argmax (ties -> lower local index)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-      if (ov > best || (ov == best && ol >= 0 && (bl < 0 || ol < bl))) { best = ov; bl = ol; }
-    }
-    if ((threadIdx.x & 31) == 0) { red_v[threadIdx.x >> 5] = best; red_l[threadIdx.x >> 5] = bl; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b = -1.0;
-      int L = -1;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-        if (red_v[w] > b || (red_v[w] == b && red_l[w] >= 0 && (L < 0 || red_l[w] < L))) { b = red_v[w]; L = red_l[w]; }
-      sc.cand_val[buf * G + me] = (L >= 0) ? b : -1.0;
-      sc.cand_row[buf * G + me] = (L >= 0) ? me + G * L : -1;
-      red_l[0] = L;
-    }
-    __syncthreads();
-    const int L = red_l[0];
-    if (L >= 0)
-      for (int j = threadIdx.x; j < n; j += blockDim.x) sc.cand_data[((size_t)buf * G + me) * n + j] = rows[(size_t)L * n + j];
-    __syncthreads();
-  };
-
-  publish(0, 0);
-  if (!grid_barrier(flags)) return;
-
-  for (int k = 0; k < n; ++k) {
-    const int buf = k & 1;
-    {  // winner among the G published candidates: block-wide argmax (ties -> lower row index)
-      double bv = -1.0;
-      int br = -1, bw = -1;
-      for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        const double v = __ldcg(&sc.cand_val[buf * G + g]);
-        const int rr = __ldcg(&sc.cand_row[buf * G + g]);
-        if (rr >= 0 && (v > bv || (v == bv && rr < br))) { bv = v; br = rr; bw = g; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-        const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
-        if (orr >= 0 && (ov > bv || (ov == bv && (br < 0 || orr < br)))) { bv = ov; br = orr; bw = ow; }
-      }
-      __shared__ double wv[32];
-      __shared__ int wr[32], ww[32];
-      if ((threadIdx.x & 31) == 0) { wv[threadIdx.x >> 5] = bv; wr[threadIdx.x >> 5] = br; ww[threadIdx.x >> 5] = bw; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double b = -1.0;
-        int w = -1, rr = -1;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
-          if (wr[i] >= 0 && (wv[i] > b || (wv[i] == b && (rr < 0 || wr[i] < rr)))) { b = wv[i]; rr = wr[i]; w = ww[i]; }
-        s_win = w;
-        s_row = rr;
-        if (w < 0 || !(b > 0.0)) atomicExch(&flags[FLAG_SINGULAR], 1);
-      }
-      __syncthreads();
-    }
-    if (*(volatile int*)&flags[FLAG_SINGULAR]) break;
-    const int w = s_win, r = s_row;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = __ldcg(&sc.cand_data[((size_t)buf * G + w) * n + j]);
-    __syncthreads();
-    const T inv_p = T(1) / prow[k];
-    const int lr = (w == me) ? (r - me) / G : -1;
-    // per-row multipliers a[i][k] / p (one FMA per element below)
-    for (int l = threadIdx.x; l < nloc; l += blockDim.x) fl[l] = rows[(size_t)l * n + k] * inv_p;
-    __syncthreads();
-    for (int l = 0; l < nloc; ++l) {
-      T* row = rows + (size_t)l * n;
-      if (l == lr) {
-        for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = (j == k) ? inv_p : prow[j] * inv_p;
-      } else {
-        const T m = fl[l];
-        for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = (j == k) ? -m : fma(-m, prow[j], row[j]);
-      }
-    }
-    if (lr >= 0 && threadIdx.x == 0) {
-      used[lr] = 1;
-      piv[k] = r;
-    }
-    __syncthreads();
-    if (k + 1 < n) publish(k + 1, buf ^ 1);
-    if (!grid_barrier(flags)) return;
-  }
-  for (long e = threadIdx.x; e < (long)nloc * n; e += blockDim.x) {
-    const int l = (int)(e / n), j = (int)(e - (long)l * n);
-    C[(size_t)(me + G * l) * n + j] = rows[e];
-  }
-}
-
-// Blocked Gauss-Jordan (FP32): the same pivot pairs and result as k_gj, one grid barrier per panel of
-// BP columns instead of one per column.  For panel K (pivot rows R, chosen by partial pivoting on the
-// panel columns alone):
-//   P       = the panel columns after the BP scalar sweeps (computed redundantly by every block, with
-//             each thread holding up to ROWS rows of the panel in registers),
-//   M'[:,K] = P,   M'[R,j] = P[R,:] M[R,j],   M'[i,j] = M[i,j] + P[i,:] M[R,j]  (i not in R, j not in K),
-// with the matrix double-buffered in global memory (A <-> B) so that the old pivot rows stay readable.
-template <int BP, int ROWS>
-__global__ void __launch_bounds__(1024) k_gj_blocked(int n, float* A, float* B, int32_t* piv, int* flags) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* P = reinterpret_cast<float*>(smraw);               // [n][BP] panel (for the update phase)
-  float* MR = P + (size_t)n * BP;                            // [BP][n] old pivot rows
-  int* panel_of = reinterpret_cast<int*>(MR + (size_t)BP * n);  // [n]: panel a row was pivoted in, -1 unused
-  __shared__ float wrow[32][BP];
-  __shared__ float wv[32];
-  __shared__ int wi[32];
-  __shared__ float prow[BP];
-  __shared__ int s_r;
-  __shared__ int R[BP];
-  const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < n; i += nt) panel_of[i] = -1;
-  __syncthreads();
-  float* Mc = A;
-  float* Mn = B;
-  const int npanels = (n + BP - 1) / BP;
-  bool singular = false;
-  float Pr[ROWS][BP];
-  for (int pi = 0; pi < npanels && !singular; ++pi) {
-    const int k0 = pi * BP, bb = min(BP, n - k0);
-#pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
-      const int i = tid + k * nt;
-#pragma unroll
-      for (int c = 0; c < BP; ++c) Pr[k][c] = (i < n && c < bb) ? __ldcg(&Mc[(size_t)i * n + k0 + c]) : 0.0f;
-    }
-    for (int jj = 0; jj < bb; ++jj) {
-      // pivot: largest |P[i][jj]| among rows not used yet (ties -> lower row)
-      float bv = -1.0f;
-      int bi = -1;
-#pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        const int i = tid + k * nt;
-        if (i < n && panel_of[i] < 0) {
-          float v = 0.0f;
-#pragma unroll
-          for (int c = 0; c < BP; ++c)
-            if (c == jj) v = fabsf(Pr[k][c]);
-          if (v > bv) { bv = v; bi = i; }
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (ov > bv || (ov == bv && (bi < 0 || oi < bi)))) { bv = ov; bi = oi; }
-      }
-      // the lane holding the warp's winning row publishes it
-#pragma unroll
-      for (int k = 0; k < ROWS; ++k)
-        if (bi >= 0 && tid + k * nt == bi) {
-#pragma unroll
-          for (int c = 0; c < BP; ++c) wrow[warp][c] = Pr[k][c];
-        }
-      if (lane == 0) { wv[warp] = bv; wi[warp] = bi; }
-      __syncthreads();
-      if (warp == 0) {
-        float v = (lane < (nt >> 5)) ? wv[lane] : -1.0f;
-        int i = (lane < (nt >> 5)) ? wi[lane] : -1;
-        int w = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-          const int ow = __shfl_xor_sync(0xffffffffu, w, o);
-          if (oi >= 0 && (ov > v || (ov == v && (i < 0 || oi < i)))) { v = ov; i = oi; w = ow; }
-        }
-        const bool ok = i >= 0 && v > 0.0f;
-        if (lane < BP) prow[lane] = ok ? wrow[w][lane] : 0.0f;
-        if (lane == 0) {
-          s_r = ok ? i : -1;
-          if (ok) {
-            panel_of[i] = pi;
-            R[jj] = i;
-            if (me == 0) piv[k0 + jj] = i;
-          }
-        }
-      }
-      __syncthreads();
-      const int r = s_r;
-      if (r < 0) {
-        if (tid == 0 && me == 0) atomicExch(&flags[FLAG_SINGULAR], 1);
-        singular = true;
-        break;
-      }
-      const float inv_p = 1.0f / prow[jj];
-#pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        const int i = tid + k * nt;
-        if (i >= n) continue;
-        if (i == r) {
-#pragma unroll
-          for (int c = 0; c < BP; ++c) Pr[k][c] = (c == jj) ? inv_p : prow[c] * inv_p;
-        } else {
-          float m = 0.0f;
-#pragma unroll
-          for (int c = 0; c < BP; ++c)
-            if (c == jj) m = Pr[k][c] * inv_p;
-#pragma unroll
-          for (int c = 0; c < BP; ++c) Pr[k][c] = (c == jj) ? -m : fmaf(-m, prow[c], Pr[k][c]);
-        }
-      }
-    }
-    if (singular) break;
-    // panel to shared memory, old pivot rows of the panel
-#pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
-      const int i = tid + k * nt;
-      if (i < n)
-#pragma unroll
-        for (int c = 0; c < BP; ++c) P[(size_t)i * BP + c] = Pr[k][c];
-    }
-    for (long e = tid; e < (long)bb * n; e += nt) {
-      const int t = (int)(e / n), j = (int)(e - (long)t * n);
-      MR[(size_t)t * n + j] = __ldcg(&Mc[(size_t)R[t] * n + j]);
-    }
-    __syncthreads();
-    // update this block's rows
-    for (int i = me; i < n; i += G) {
-      const float* Pi = P + (size_t)i * BP;
-      const bool is_piv = panel_of[i] == pi;
-      for (int j = tid; j < n; j += nt) {
-        float v;
-        if (j >= k0 && j < k0 + bb) {
-          v = Pi[j - k0];
-        } else {
-          float acc = is_piv ? 0.0f : __ldcg(&Mc[(size_t)i * n + j]);
-          for (int t = 0; t < bb; ++t) acc = fmaf(Pi[t], MR[(size_t)t * n + j], acc);
-          v = acc;
-        }
-        Mn[(size_t)i * n + j] = v;
-      }
-    }
-    if (!grid_barrier(flags)) return;
-    float* tmp = Mc;
-    Mc = Mn;
-    Mn = tmp;
-  }
-  if (Mc != A)  // result must end in A
-    for (int i = me; i < n; i += G)
-      for (int j = tid; j < n; j += nt) A[(size_t)i * n + j] = Mc[(size_t)i * n + j];
-}
-
-__global__ void k_gather_perm(int n, const int32_t* piv, const double* y, double* ytmp) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) ytmp[k] = y[piv[k]];
-}
-
-template <typename T>
-__global__ void k_gemv_rows_perm(int n, const T* __restrict__ B, const int32_t* __restrict__ piv,
-                                 const double* __restrict__ ytmp, double* __restrict__ x) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (k >= n) return;
-  const T* row = B + (size_t)piv[k] * n;
-  T acc = 0;  // FP32 rows accumulate in FP32 (the preconditioner apply of the mixed path)
-  for (int j = lane; j < n; j += 32) acc += row[j] * (T)ytmp[j];
-  acc = warp_sum(acc);
-  if (lane == 0) x[k] = acc;
-}
-
-// s_c = K_c^T F_c u_{v_c} (adjoint) or K_c F_c u_{v_c}
-__global__ void k_contact_gather_kt(int nc, const int32_t* cv, const double* frame, const double* cdata,
-                                    int transpose, const double* u, double* sc) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  const int v = cv[c];
-  const double* F = frame + 9 * (size_t)c;
-  const double* K = cdata + 12 * (size_t)c;
-  double y[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) y[i] = F[3 * i] * u[3 * v] + F[3 * i + 1] * u[3 * v + 1] + F[3 * i + 2] * u[3 * v + 2];
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-    sc[3 * c + j] = transpose ? K[j] * y[0] + K[3 + j] * y[1] + K[6 + j] * y[2]
-                              : K[3 * j] * y[0] + K[3 * j + 1] * y[1] + K[3 * j + 2] * y[2];
-}
-
-__global__ void k_contact_scatter(int nc, const int32_t* cv, const double* frame, const double* t, double* e) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
-  const int v = cv[c];
-  const double* F = frame + 9 * (size_t)c;
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-    atomicAdd(&e[3 * v + r], F[r] * t[3 * c] + F[3 + r] * t[3 * c + 1] + F[6 + r] * t[3 * c + 2]);
-}
-
 __global__ void k_axpby(int n, double a, const double* x, double b, const double* y, double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + b * (y ? y[i] : 0.0);
@@ -697,33 +311,12 @@ __global__ void k_rhs(int n, const double* dq, const double* dv, double inv_h, d
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = dq[i] + (dv ? dv[i] * inv_h : 0.0);
 }
-__global__ void k_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = sign * x[i] * (*num) / (*den);
-}
 __global__ void k_mul(int n, const double* a, const double* b, double* y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = a[i] * b[i];
 }
 
 // partial[k][blk] = sum over this block's slice of V_k . w
-__global__ void k_multi_dot_partial(int n, const double* __restrict__ V, long ld, const double* __restrict__ w,
-                                    double* partial) {
-  const int k = blockIdx.y;
-  const double* vk = V + (size_t)k * ld;
-  double acc = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    acc += vk[i] * w[i];
-  acc = warp_sum(acc);
-  __shared__ double s[32];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = (threadIdx.x < (blockDim.x >> 5)) ? s[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = v;
-  }
-}
 // out[k] = V_k . w in one launch: every block writes its partial for vector k (blockIdx.y), and the
 // last block to finish (counted in cnt[k], which it resets) reduces the partials in a fixed order.
 __global__ void k_multi_dot_fused(int n, const double* __restrict__ V, long ld, const double* __restrict__ w,
@@ -839,20 +432,6 @@ __global__ void k_export_step(const double* __restrict__ gs, int len, double* ho
   }
 }
 
-__global__ void k_multi_dot_final(int nparts, const double* partial, double* out) {
-  const int k = blockIdx.x;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[(size_t)k * nparts + i];
-  acc = warp_sum(acc);
-  __shared__ double s[32];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = (threadIdx.x < (blockDim.x >> 5)) ? s[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) out[k] = v;
-  }
-}
 __global__ void k_multi_axpy(int n, int nvec, const double* __restrict__ V, long ld, const double* __restrict__ coef,
                              double* __restrict__ w) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -874,33 +453,6 @@ __global__ void k_normalize(int n, const double* w, const double* nrm2, double* 
   const double nr = sqrt(*nrm2);
   if (i < n) v[i] = (nr > 0.0) ? w[i] / nr : 0.0;
   if (i == 0 && h_slot) *h_slot = nr;
-}
-__global__ void k_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res) {
-  const int ld = m + 1;
-  double* h = H + (size_t)ld * j;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-    h[i] = t;
-  }
-  const double a = h[j], b = h[j + 1];
-  const double r = hypot(a, b);
-  const double c = (r > 0.0) ? a / r : 1.0, s = (r > 0.0) ? b / r : 0.0;
-  cs[j] = c;
-  sn[j] = s;
-  h[j] = r;
-  h[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  *res = fabs(g[j + 1]);
-}
-__global__ void k_hess_solve(int k, int m, const double* H, const double* g, double* y) {
-  const int ld = m + 1;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int jj = i + 1; jj < k; ++jj) s -= H[(size_t)ld * jj + i] * y[jj];
-    y[i] = s / H[(size_t)ld * i + i];
-  }
 }
 __global__ void k_cg_alpha(const double* rz, const double* pAp, double* alpha) { *alpha = *rz / *pAp; }
 __global__ void k_cg_update_xr(int n, const double* alpha, const double* p, const double* Ap, double* x, double* r) {
@@ -939,11 +491,6 @@ void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const 
   g_launches += 1;
   k_diag_inv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, diag_slot, val, val32, dinv);
 }
-__global__ void k_to_float(int n, const double* __restrict__ x, float* __restrict__ y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (float)x[i];
-}
-
 void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s) {
   g_launches += 2;
   k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos);
@@ -1016,62 +563,6 @@ void launch_cap_form(int nc, const double* Ds, const double* frame, const double
   k_cap_form<<<nblk(n * n, 256), 256, 0, s>>>(nc, Ds, frame, cdata, h * h, transpose, C);
 }
 
-static constexpr int kGJThreads = 1024;
-static int gj_blocks(int n, int sm_count) { return n < sm_count ? n : sm_count; }
-static size_t gj_smem(int n, int G, size_t es) {
-  const int nloc_max = (n + G - 1) / G;
-  return ((size_t)nloc_max * n + n + nloc_max) * es + (size_t)nloc_max * sizeof(int) + 16;
-}
-size_t gj_scratch_bytes(int n, int sm_count) {
-  const int G = gj_blocks(n, sm_count);
-  return (size_t)2 * G * sizeof(double) + (size_t)2 * G * sizeof(int) + (size_t)2 * G * n * sizeof(double) + 256;
-}
-template <typename T>
-static bool gj_invert(int n, T* C, int32_t* piv, double* scratch, int* flags, int sm_count, cudaStream_t s) {
-  g_launches += 1;
-  const int G = gj_blocks(n, sm_count);
-  const int nloc_max = (n + G - 1) / G;
-  const size_t smem = gj_smem(n, G, sizeof(T));
-  if (smem > 220 * 1024) return false;
-  if (cudaFuncSetAttribute(k_gj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj<T>, kGJThreads, smem) != cudaSuccess || per_sm < 1)
-    return false;
-  GJScratch<T> sc;
-  sc.cand_val = scratch;
-  sc.cand_row = reinterpret_cast<int*>(scratch + 2 * G);
-  sc.cand_data = reinterpret_cast<T*>(scratch + 2 * G + G + 1);  // after 2G doubles and 2G ints
-  int nn = n, nl = nloc_max;
-  void* args[] = {&nn, &nl, &C, &piv, &sc, &flags};
-  return cudaLaunchCooperativeKernel((void*)k_gj<T>, dim3(G), dim3(kGJThreads), args, smem, s) == cudaSuccess;
-}
-bool launch_gj_invert(int n, double* C, int32_t* piv, double* scratch, int* flags, int sm_count, cudaStream_t s) {
-  return gj_invert<double>(n, C, piv, scratch, flags, sm_count, s);
-}
-template <int BP, int ROWS>
-static bool gj_blocked(int n, float* C, float* tmp, int32_t* piv, int* flags, int G, cudaStream_t s) {
-  const size_t smem = (size_t)2 * n * BP * sizeof(float) + (size_t)n * sizeof(int) + 64;
-  if (smem > 220 * 1024) return false;
-  if (cudaFuncSetAttribute(k_gj_blocked<BP, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return false;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_blocked<BP, ROWS>, kGJThreads, smem) != cudaSuccess ||
-      per_sm < 1)
-    return false;
-  int nn = n;
-  void* args[] = {&nn, &C, &tmp, &piv, &flags};
-  return cudaLaunchCooperativeKernel((void*)k_gj_blocked<BP, ROWS>, dim3(G), dim3(kGJThreads), args, smem, s) ==
-         cudaSuccess;
-}
-bool launch_gj_invert32(int n, float* C, float* tmp, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {
-  g_launches += 1;
-  const int G = gj_blocks(n, sm_count);
-  if (n <= kGJThreads && n <= 1600) return gj_blocked<16, 1>(n, C, tmp, piv, flags, G, s);
-  if (n <= 1600) return gj_blocked<16, 2>(n, C, tmp, piv, flags, G, s);
-  if (n <= 2 * kGJThreads) return gj_blocked<8, 2>(n, C, tmp, piv, flags, G, s);
-  // larger systems: the one-column-per-barrier form
-  return gj_invert<float>(n, C, piv, reinterpret_cast<double*>(tmp), flags, sm_count, s);
-}
 __global__ void k_to_float_n(long n, const double* __restrict__ x, float* __restrict__ y) {
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i < n) y[i] = (float)x[i];
@@ -1092,17 +583,6 @@ void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* 
   g_launches += 1;
   k_cap_apply<float><<<(n + 3) / 4, 256, sizeof(float) * (size_t)n, s>>>(n, B, piv, y, x);
 }
-void launch_contact_gather_kt(int nc, const int32_t* cv, const double* frame, const double* cdata, int transpose,
-                              const double* u, double* sc, cudaStream_t s) {
-  g_launches += 1;
-  k_contact_gather_kt<<<nblk(nc, 128), 128, 0, s>>>(nc, cv, frame, cdata, transpose, u, sc);
-}
-void launch_contact_scatter(int nv, int nc, const int32_t* cv, const double* frame, const double* t, double* e,
-                            cudaStream_t s) {
-  g_launches += 1;
-  cudaMemsetAsync(e, 0, sizeof(double) * 3 * (size_t)nv, s);
-  k_contact_scatter<<<nblk(nc, 128), 128, 0, s>>>(nc, cv, frame, t, e);
-}
 void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
   g_launches += 1;
   k_axpby<<<nblk(n, 256), 256, 0, s>>>(n, a, x, b, y, out);
@@ -1110,11 +590,6 @@ void launch_axpby(int n, double a, const double* x, double b, const double* y, d
 void launch_rhs(int n, const double* dq, const double* dv, double inv_h, double* b, cudaStream_t s) {
   g_launches += 1;
   k_rhs<<<nblk(n, 256), 256, 0, s>>>(n, dq, dv, inv_h, b);
-}
-void launch_scale_dev(int n, const double* x, const double* num, const double* den, double sign, double* y,
-                      cudaStream_t s) {
-  g_launches += 1;
-  k_scale_dev<<<nblk(n, 256), 256, 0, s>>>(n, x, num, den, sign, y);
 }
 void launch_mul(int n, const double* a, const double* b, double* y, cudaStream_t s) {
   g_launches += 1;
@@ -1182,14 +657,6 @@ void launch_combine(int n, int nvec, const double* V, long ld, const double* coe
 void launch_normalize(int n, const double* w, const double* nrm2, double* v, double* h_slot, cudaStream_t s) {
   g_launches += 1;
   k_normalize<<<nblk(n, 256), 256, 0, s>>>(n, w, nrm2, v, h_slot);
-}
-void launch_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res, cudaStream_t s) {
-  g_launches += 1;
-  k_givens<<<1, 1, 0, s>>>(j, m, H, cs, sn, g, res);
-}
-void launch_hess_solve(int k, int m, const double* H, const double* g, double* y, cudaStream_t s) {
-  g_launches += 1;
-  k_hess_solve<<<1, 1, 0, s>>>(k, m, H, g, y);
 }
 void launch_cg_alpha(const double* rz, const double* pAp, double* alpha, cudaStream_t s) {
   g_launches += 1;
