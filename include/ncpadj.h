@@ -71,6 +71,8 @@ enum {
 };
 enum { NCPADJ_SOLVER_AUTO = 0, NCPADJ_SOLVER_CG = 1, NCPADJ_SOLVER_GMRES = 2 };
 enum { NCPADJ_MEM_DEVICE = 0, NCPADJ_MEM_HOST = 1 };
+/* constitutive model of a tet (App. B.2), see ncpadj_scene_set_model */
+enum { NCPADJ_MODEL_NEO_HOOKEAN = 0, NCPADJ_MODEL_COROTATIONAL = 1, NCPADJ_MODEL_ARAP = 2 };
 
 typedef struct ncpadj_ctx_s* ncpadj_ctx;     /* one per device; owns the CUDA device binding */
 typedef struct ncpadj_scene_s* ncpadj_scene; /* mesh + material + h + elastic factor + workspace */
@@ -257,6 +259,21 @@ ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const dou
  * fibre: HOST array [n_tets*3] of unit vectors (copied; replaces earlier fibres of the scene).
  * Errors: INVALID_ARG (NULL, or a fibre whose length is not 1 within 1e-6), OOM, CUDA. */
 ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre);
+
+/* Constitutive model per tet.  The three isotropic models of App. B.2 share the SVD projection
+ * Jacobian of Sec. 4.3 and differ only in the projection theta(sigma) of the singular values:
+ *   NCPADJ_MODEL_NEO_HOOKEAN (default): zeta = mu/2 (I_1 - log I_3 - 3) + lambda/8 (log I_3)^2;
+ *   NCPADJ_MODEL_COROTATIONAL: zeta = mu ||theta - 1||^2 + lambda/2 (sum_i (theta_i - 1))^2, whose
+ *     projection is linear: theta - 1 = W (sigma - 1) with the constant
+ *     W = I/2 - lambda / (2 (4 mu + 3 lambda)) 1 1^T;
+ *   NCPADJ_MODEL_ARAP: theta = 1 (p(F) is the rotation of F); lambda plays no part and mu only
+ *     sets the weight w = 2 mu (the stretch stiffness).
+ * Every model weights tet i by w_i = 2 mu_i V_i, so the elastic factor does not change.  Every
+ * model rejects det F <= 0 (INVERTED_ELEMENT).  The forward and adjoint steps and the E, nu
+ * gradients follow the model of each tet.
+ * model: HOST array [n_tets] of NCPADJ_MODEL_* (copied), or NULL to make every tet Neo-Hookean.
+ * Errors: INVALID_ARG (NULL scene, a value that is no NCPADJ_MODEL_*), OOM, CUDA. */
+ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model);
 
 /* Cinv = C^{-1} for a dense row-major n x n matrix, by the blocked Gauss-Jordan elimination with
  * partial pivoting that inverts the contact capacitance I + h^2 K D of the Woodbury

@@ -28,7 +28,8 @@ def _free(step: Step) -> Step:
     empty = dataclasses.replace(ct, vertex=ct.vertex[:0], frame=ct.frame[:0], d_n=ct.d_n[:0], d_f=ct.d_f[:0],
                                 mu=ct.mu[:0], region=ct.region[:0])
     X = step.mesh.X
-    return Step(X, step.mesh.tets, step.E, step.nu, step.density, step.h, step.gravity, empty, step.eps)
+    return Step(X, step.mesh.tets, step.E, step.nu, step.density, step.h, step.gravity, empty, step.eps,
+                step.model)
 
 
 def _normals(step: Step) -> np.ndarray:

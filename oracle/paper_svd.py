@@ -1,4 +1,4 @@
-"""The paper's SVD closed form of the Neo-Hookean projection Jacobian, in FP64.
+"""The paper's SVD closed form of the projection Jacobian, in FP64.
 
 Test infrastructure (oracle); see the package docstring.  The adjoint in this oracle uses
 the plain implicit-function form in ``prox``; this module exists so that the readings of
@@ -16,6 +16,11 @@ the closed form (Sec. 4.3 and App. B.0-B.4) are pinned against it on the CPU:
 * theta solves g(theta) = mu(3 theta - 2 sigma - 1/theta) + lambda log(J) / theta = 0 (App. B.2/B.3),
   W = 2 mu (dg/dtheta)^{-1}, dtheta/dmu = -(dg/dtheta)^{-1}(3 theta - 2 sigma - 1/theta),
   dtheta/dlambda = -(dg/dtheta)^{-1} (log J / theta).
+* The co-rotational and ARAP models (App. B.2) change only theta, W and the parameter
+  derivatives (``model_theta``).  For ARAP, App. B.2 states M_ij = N_ij = 1/(sigma_i + sigma_j);
+  App. B.0's definitions give M_ij = 1/(sigma_i + sigma_j) but N_ij = -1/(sigma_i + sigma_j)
+  (A_ij = 0, B_ij = 2/(sigma_i + sigma_j)).  The definitions are taken; the polar-derivative
+  oracle of ``models`` decides between the two.
 """
 from __future__ import annotations
 
@@ -84,11 +89,31 @@ def divided_difference_closed_form(theta, mu, lam, i, j):
     return 2.0 * mu / (3.0 * mu + (mu - lam * lJ) / (theta[i] * theta[j]))
 
 
-def jacobian_svd(F, mu, lam, tau_sigma=1e-6):
+def model_theta(model, sigma, mu, lam):
+    """(theta, W, dtheta/dmu, dtheta/dlambda) of App. B.2/B.3 for 'neo_hookean', 'corotational'
+    (g = 4 mu (theta - 1) + lambda tr(theta - 1) 1 - 2 mu (sigma - 1), H = dg/dtheta =
+    4 mu I + lambda 1 1^T, dg/dmu = 2 (2 theta - sigma - 1), dg/dlambda = tr(theta - 1) 1) or
+    'arap' (theta = 1, W = 0, no parameter dependence)."""
+    sigma = np.asarray(sigma, float)
+    if model == "neo_hookean":
+        th = nh_theta(sigma, mu, lam)
+        return (th,) + nh_theta_derivatives(sigma, th, mu, lam)
+    if model == "corotational":
+        one = np.ones(3)
+        H = 4.0 * mu * np.eye(3) + lam * np.outer(one, one)
+        th = one + np.linalg.solve(H, 2.0 * mu * (sigma - one))
+        Hinv = np.linalg.inv(H)
+        return (th, 2.0 * mu * Hinv, -Hinv @ (2.0 * (2.0 * th - sigma - one)),
+                -Hinv @ (np.sum(th - one) * one))
+    if model == "arap":
+        return np.ones(3), np.zeros((3, 3)), np.zeros(3), np.zeros(3)
+    raise ValueError(model)
+
+
+def jacobian_svd(F, mu, lam, tau_sigma=1e-6, model="neo_hookean"):
     """9x9 dvecP/dvecF by the paper's SVD closed form (single F)."""
     U, s, V = signed_svd(F)
-    th = nh_theta(s, mu, lam)
-    W, _, _ = nh_theta_derivatives(s, th, mu, lam)
+    th, W, _, _ = model_theta(model, s, mu, lam)
     M = np.zeros((3, 3))
     N = np.zeros((3, 3))
     tau = tau_sigma * max(1.0, np.max(np.abs(s)))
@@ -110,8 +135,8 @@ def jacobian_svd(F, mu, lam, tau_sigma=1e-6):
     return K @ inner @ K.T
 
 
-def prox_svd(F, mu, lam):
+def prox_svd(F, mu, lam, model="neo_hookean"):
     """p(F) = U diag(theta) V^T (single F)."""
     U, s, V = signed_svd(F)
-    th = nh_theta(s, mu, lam)
+    th = model_theta(model, s, mu, lam)[0]
     return U @ np.diag(th) @ V.T

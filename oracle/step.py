@@ -32,7 +32,7 @@ import scipy.sparse.linalg as spla
 
 from . import contact as C
 from .model import Mesh, lame, lame_derivatives
-from .prox import prox, prox_derivatives
+from . import models
 
 
 @dataclass
@@ -55,8 +55,10 @@ class State:
 class Step:
     """One time step of a scene with a frozen contact set."""
 
-    def __init__(self, X, tets, E, nu, density, h, gravity, contacts, eps):
+    def __init__(self, X, tets, E, nu, density, h, gravity, contacts, eps, model=models.NEO_HOOKEAN):
         self.mesh = Mesh(X, tets)
+        models.by_model(model, self.mesh.n_tets)  # validates: one name, or one per tet
+        self.model = model if isinstance(model, str) else np.asarray(model).copy()
         self.E = np.broadcast_to(np.asarray(E, float), (self.mesh.n_tets,)).copy()
         self.nu = np.broadcast_to(np.asarray(nu, float), (self.mesh.n_tets,)).copy()
         self.density = float(density)
@@ -95,7 +97,7 @@ class Step:
         mesh = self.mesh
         mu_L, lam_L = self.lame()
         F = mesh.F(q)
-        P = prox(F, mu_L, lam_L)
+        P = models.prox(self.model, F, mu_L, lam_L)
         w = 2.0 * mu_L * mesh.vol
         r_el = np.einsum("tji,tj->ti", mesh.G, (np.swapaxes(F, 1, 2) - np.swapaxes(P, 1, 2)).reshape(-1, 9))
         Rq = (self.mass[:, None] * (q - qt)).reshape(-1) + h2 * mesh.scatter_vectors(w[:, None] * r_el)
@@ -229,8 +231,8 @@ class Step:
         h2 = self.h * self.h
         mu_L, lam_L = self.lame()
         F = mesh.F(state.q)
-        P = prox(F, mu_L, lam_L)
-        Jp, dP_dmu, dP_dlam = prox_derivatives(F, P, mu_L, lam_L)
+        P = models.prox(self.model, F, mu_L, lam_L)
+        Jp, dP_dmu, dP_dlam = models.prox_derivatives(self.model, F, P, mu_L, lam_L)
         w = 2.0 * mu_L * mesh.vol
         blocks = h2 * w[:, None, None] * np.einsum("tki,tkl,tlj->tij", mesh.G, np.eye(9) - Jp, mesh.G)
         A_el = sp.diags(np.repeat(self.mass, 3)) + mesh.scatter_blocks(blocks)

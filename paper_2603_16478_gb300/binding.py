@@ -21,6 +21,7 @@ PRECOND = {"none": 0, "jacobi": 1, "elastic": 2, "woodbury": 3}
 SOLVER = {"auto": 0, "cg": 1, "gmres": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 MEMORY = {"device": 0, "host": 1}
+MODEL = {"neo_hookean": 0, "corotational": 1, "arap": 2}
 
 
 def library_path() -> str:
@@ -102,7 +103,7 @@ EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpad
            "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
            "ncpadj_options_default",
            "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc",
-           "ncpadj_dense_inverse", "ncpadj_scene_set_fibres"]
+           "ncpadj_dense_inverse", "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
 
 
 def load_library(path: Optional[str] = None):
@@ -135,6 +136,7 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_elastic_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_elastic_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_set_fibres.argtypes = [C.c_void_p, C.c_void_p]
+    lib.ncpadj_scene_set_model.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_dense_inverse.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
     if path is None:
         _LIB = lib
@@ -218,6 +220,18 @@ class Scene:
             raise ValueError(f"expected {self.n_tets} fibres, got {f.shape[0]}")
         self._fibre = f
         _check(self.lib, self.lib.ncpadj_scene_set_fibres(self.handle, C.c_void_p(f.data_ptr())))
+
+    def set_model(self, model) -> None:
+        """Constitutive model of every tet (App. B.2): one of "neo_hookean", "corotational", "arap",
+        or a per-tet sequence of those names or of their codes (MODEL)."""
+        if isinstance(model, str):
+            codes = [MODEL[model]] * self.n_tets
+        else:
+            codes = [MODEL[m] if isinstance(m, str) else int(m) for m in model]
+        if len(codes) != self.n_tets:
+            raise ValueError(f"expected {self.n_tets} models, got {len(codes)}")
+        m = torch.tensor(codes, dtype=torch.int32)
+        _check(self.lib, self.lib.ncpadj_scene_set_model(self.handle, C.c_void_p(m.data_ptr())))
 
     def info(self) -> dict:
         inf = _SceneInfo()

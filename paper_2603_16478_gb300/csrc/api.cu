@@ -466,9 +466,9 @@ struct Engine {
         for (int v : sup_nc) smax = std::max(smax, 3 * v);
         S.inner.ensure(sizeof(double) * ((size_t)(kInnerRestart + 1) * smax + 3 * (size_t)smax +
                                          2 * (size_t)(kInnerRestart + 2) + 64));
-        S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
       }
     }
+    if (flexible_gmres()) S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
     double* base = S.vecs.as<double>();
     for (double** v : {&b, &x, &r, &w, &t0, &t1, &t2, &t3, &dinv}) {
       *v = base;
@@ -501,7 +501,7 @@ struct Engine {
     float* b32 = mixed ? S.bsr32.as<float>() : nullptr;
     launch_bsr_init(nv, S.nb, S.diag_slot.as<int32_t>(), S.massd.as<double>(), b64, b32, st);
     TetArgs ta{nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(), S.lam.as<double>(),
-               S.slot.as<int32_t>(), q, h, b64, b32, S.tetdata.as<double>(), flags};
+               S.slot.as<int32_t>(), q, h, b64, b32, S.tetdata.as<double>(), flags, S.model_ptr()};
     if (mixed) launch_tet_assemble32(ta, st);
     else launch_tet_assemble64(ta, st);
     if (nc) launch_contact_blocks(contact_args(q, q_prev, lambda, eps), st);
@@ -724,6 +724,17 @@ struct Engine {
   // Gram-Schmidt twice, normalisation, export of the coefficients to host-mapped slot j % 2 and
   // j <- j + 1, with j read on the device.  Replaying it is one launch per step instead of ~16,
   // which matters because the step is otherwise bound by the host's launch rate.
+  // flexible GMRES (keep z_j = P^{-1} v_j and update x with Z y, Saad's FGMRES) whenever P^{-1} is
+  // not one fixed linear map to FP64 accuracy: an inner iterative capacitance solve makes it vary,
+  // and an FP32 application rounds it, so that P^{-1}(V y) is not the combination of the z_j the
+  // Arnoldi relation holds for (that mismatch, relative ~1e-7 times the cancellation in V y, can
+  // stop a restarted GMRES from converging)
+  bool flexible_gmres() const {
+    const bool inner = !sup_c0.empty() && precond == NCPADJ_PRECOND_WOODBURY && nc > 0;
+    const bool fp32 = (mixed && (precond == NCPADJ_PRECOND_WOODBURY || precond == NCPADJ_PRECOND_ELASTIC)) ||
+                      (cap_fp32 && precond == NCPADJ_PRECOND_WOODBURY && nc > 0);
+    return inner || fp32;
+  }
   bool step_graph_possible() const {
     return precond == NCPADJ_PRECOND_WOODBURY && nc > 0 && sup_c0.empty();
   }
@@ -733,6 +744,7 @@ struct Engine {
                                 (uintptr_t)S.gmres.p, (uintptr_t)S.vecs.p, (uintptr_t)S.red.p, (uintptr_t)S.scal.p,
                                 (uintptr_t)S.cap.p, (uintptr_t)S.vec32.p, (uintptr_t)S.cdata.p, (uintptr_t)S.bsr32.p,
                                 (uintptr_t)S.bsr64.p, (uintptr_t)S.xpos.p, (uintptr_t)S.gstep.p,
+                                (uintptr_t)flexible_gmres(), (uintptr_t)S.fgmres.p,
                                 (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size()};
     for (size_t b = 0; b < blk_c0.size(); ++b) {
       k.push_back((uintptr_t)blk_c0[b]);
@@ -755,6 +767,7 @@ struct Engine {
     launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st);
     if (mixed) launch_sinv_half2_32(sinv, w32, w, st);
     else launch_sinv_half2(sinv, t3, w, st);
+    if (flexible_gmres()) launch_copy_idx(N, w, S.fgmres.as<double>(), N, jp, st);  // Z_j = z
     // V_{j+1} = A z
     launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
                         mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st);
@@ -847,9 +860,7 @@ struct Engine {
         // rotations, triangular solve) on the host, which reads the Gram-Schmidt coefficients of
         // each iteration in one copy together with the convergence check.
         double* V = S.gmres.as<double>();  // (m+1) x N
-        // flexible GMRES when the preconditioner contains an inner iterative solve: keep
-        // z_j = P^{-1} v_j and update x with Z y (Saad's FGMRES)
-        const bool flexible = !sup_c0.empty() && precond == NCPADJ_PRECOND_WOODBURY && nc > 0;
+        const bool flexible = flexible_gmres();
         double* Z = flexible ? S.fgmres.as<double>() : nullptr;
         double* gs = V + (size_t)(m + 1) * N;  // [0..m]: first-pass, [m+1..2m+1]: second-pass, [2m+2]: norm
         double* ydev = gs + 2 * (m + 1) + 1;
@@ -1286,7 +1297,7 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     NCPADJ_CUDA_TRY(cudaMemsetAsync(flags + FLAG_INFEASIBLE, 0, 2 * sizeof(int), st));
     launch_inertia(nv, S.massd.as<double>(), qq, qt, RR, st);
     launch_tet_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
-                     S.lam.as<double>(), qq, S.h, RR, flags, st);
+                     S.lam.as<double>(), S.model_ptr(), qq, S.h, RR, flags, st);
     if (nc) {
       ContactArgs ca = E.contact_args(qq, fin->q_prev, nullptr, opt.eps);
       // the loaded mask belongs to the accepted iterate: trial points (check_turn) leave it alone
@@ -1582,6 +1593,36 @@ ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre) {
     if (scene->ctx) NCPADJ_CUDA_TRY(cudaSetDevice(scene->ctx->c.device));
     S.fibre.ensure(sizeof(double) * 3 * (size_t)std::max(S.nt, 1));
     NCPADJ_CUDA_TRY(cudaMemcpy(S.fibre.p, fibre, sizeof(double) * 3 * (size_t)S.nt, cudaMemcpyHostToDevice));
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene, "NULL scene");
+    Scene& S = scene->s;
+    bool any = false;
+    std::vector<int8_t> m8;
+    if (model) {
+      m8.resize((size_t)std::max(S.nt, 1), 0);
+      for (int t = 0; t < S.nt; ++t) {
+        NCPADJ_REQUIRE(model[t] >= NCPADJ_MODEL_NEO_HOOKEAN && model[t] <= NCPADJ_MODEL_ARAP,
+                       "model " + std::to_string(model[t]) + " of tet " + std::to_string(t) + " is not a NCPADJ_MODEL_*");
+        m8[t] = (int8_t)model[t];
+        any = any || model[t] != NCPADJ_MODEL_NEO_HOOKEAN;
+      }
+    }
+    if (scene->ctx) NCPADJ_CUDA_TRY(cudaSetDevice(scene->ctx->c.device));
+    if (any) {
+      S.model.ensure(m8.size());
+      NCPADJ_CUDA_TRY(cudaMemcpy(S.model.p, m8.data(), m8.size(), cudaMemcpyHostToDevice));
+    }
+    S.model_any = any;
     return NCPADJ_OK;
   } catch (const Error& e) {
     return fail(e);

@@ -183,6 +183,85 @@ __device__ void nh_prox(const T sig[3], T mu, T lam, T th[3], T Hinv[3][3], T& l
     for (int j = 0; j < 3; ++j) Hinv[i][j] = ((i == j) ? T(1) / Dg[i] : T(0)) - c * Dia[i] * Dia[j];
 }
 
+// The local projection on the singular values for the three isotropic models of App. B.2, with
+// what the Jacobian and the contractions need: theta, W = dtheta/dsigma, the total dtheta/dmu and
+// dtheta/dlambda of App. B.3 (w = 2 mu varies with mu), and the divided differences
+// Ad[i][j] = (theta_i - theta_j)/(sigma_i - sigma_j) in a form without cancellation.
+//  - Neo-Hookean: Newton on its stationarity condition (nh_prox); subtracting the conditions of
+//    components i and j gives Ad[i][j] = 2 mu / (3 mu + (mu - lambda log J) / (theta_i theta_j)),
+//    which also covers the degenerate limit of App. B.4.
+//  - co-rotational: the condition 4 mu (theta - 1) + lambda tr(theta - 1) 1 = 2 mu (sigma - 1) is
+//    linear, so theta - 1 = W (sigma - 1) with the constant W = I/2 - c 1 1^T,
+//    c = lambda / (2 (4 mu + 3 lambda)); Ad = 1/2.
+//  - ARAP: theta = 1, W = 0, no parameter dependence (mu acts only through w); Ad = 0.
+template <typename T>
+__device__ void local_prox(int model, const T sig[3], T mu, T lam, T th[3], T W[3][3], T dmu[3], T dlam[3],
+                           T Ad[3][3]) {
+  if (model == MODEL_COROTATIONAL) {
+    const T den = T(4) * mu + T(3) * lam;
+    const T c = lam / (T(2) * den);
+    const T s = (sig[0] - T(1)) + (sig[1] - T(1)) + (sig[2] - T(1));
+    const T gm = T(2) * lam * s / (den * den), gl = -T(2) * mu * s / (den * den);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      th[i] = T(0.5) * (sig[i] + T(1)) - c * s;
+      dmu[i] = gm;
+      dlam[i] = gl;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        W[i][j] = (i == j ? T(0.5) : T(0)) - c;
+        Ad[i][j] = T(0.5);
+      }
+    }
+    return;
+  }
+  if (model == MODEL_ARAP) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      th[i] = T(1);
+      dmu[i] = dlam[i] = T(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) W[i][j] = Ad[i][j] = T(0);
+    }
+    return;
+  }
+  T Hinv[3][3], logJ;
+  nh_prox<T>(sig, mu, lam, th, Hinv, logJ);
+  // W = 2 mu Hinv ; dtheta/dmu = -Hinv (3 theta - 2 sigma - 1/theta) ; dtheta/dlam = -Hinv (log J / theta)
+  T gm[3], gl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gm[i] = T(3) * th[i] - T(2) * sig[i] - T(1) / th[i];
+    gl[i] = logJ / th[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dmu[i] = -(Hinv[i][0] * gm[0] + Hinv[i][1] * gm[1] + Hinv[i][2] * gm[2]);
+    dlam[i] = -(Hinv[i][0] * gl[0] + Hinv[i][1] * gl[1] + Hinv[i][2] * gl[2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      W[i][j] = T(2) * mu * Hinv[i][j];
+      Ad[i][j] = (i == j) ? T(0) : T(2) * mu / (T(3) * mu + (mu - lam * logJ) / (th[i] * th[j]));
+    }
+  }
+}
+
+// theta alone (the forward residual)
+template <typename T>
+__device__ void local_theta(int model, const T sig[3], T mu, T lam, T th[3]) {
+  if (model == MODEL_COROTATIONAL) {
+    const T c = lam / (T(2) * (T(4) * mu + T(3) * lam));
+    const T s = (sig[0] - T(1)) + (sig[1] - T(1)) + (sig[2] - T(1));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) th[i] = T(0.5) * (sig[i] + T(1)) - c * s;
+  } else if (model == MODEL_ARAP) {
+    th[0] = th[1] = th[2] = T(1);
+  } else {
+    T Hinv[3][3], logJ;
+    nh_prox<T>(sig, mu, lam, th, Hinv, logJ);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void atomic_add_out(double* p, T v) { atomicAdd(p, (double)v); }
 template <typename T>
@@ -218,36 +297,17 @@ __global__ void __launch_bounds__(128) k_tet_assemble(TetArgs A, OutT* bsr) {
     return;
   }
   const T mu = (T)A.mu[t], lam = (T)A.lam[t];
-  T th[3], Hinv[3][3], logJ;
-  nh_prox<T>(sig, mu, lam, th, Hinv, logJ);
-  // W = 2 mu Hinv ; dtheta/dmu = -Hinv (3 theta - 2 sigma - 1/theta) ; dtheta/dlam = -Hinv (log J / theta)
-  T W[3][3], dmu[3], dlam[3];
-  {
-    T gm[3], gl[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      gm[i] = T(3) * th[i] - T(2) * sig[i] - T(1) / th[i];
-      gl[i] = logJ / th[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      dmu[i] = -(Hinv[i][0] * gm[0] + Hinv[i][1] * gm[1] + Hinv[i][2] * gm[2]);
-      dlam[i] = -(Hinv[i][0] * gl[0] + Hinv[i][1] * gl[1] + Hinv[i][2] * gl[2]);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) W[i][j] = T(2) * mu * Hinv[i][j];
-    }
-  }
-  // off-diagonal coefficients M_ij = (A_ij + B_ij)/2, N_ij = (A_ij - B_ij)/2 (App. B.0).  The divided
-  // difference A_ij = (theta_i - theta_j)/(sigma_i - sigma_j) is taken from the stationarity condition,
-  // which gives it without cancellation for any gap, including the degenerate limit of App. B.4:
-  //   A_ij = 2 mu / (3 mu + (mu - lambda log J) / (theta_i theta_j)).
+  T th[3], W[3][3], dmu[3], dlam[3], Ad[3][3];
+  local_prox<T>(A.model ? A.model[t] : MODEL_NEO_HOOKEAN, sig, mu, lam, th, W, dmu, dlam, Ad);
+  // off-diagonal coefficients M_ij = (A_ij + B_ij)/2, N_ij = (A_ij - B_ij)/2 (App. B.0), with the
+  // divided difference A_ij from local_prox
   T Mc[3][3], Nc[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       if (i == j) { Mc[i][j] = Nc[i][j] = T(0); continue; }
-      T Aij = T(2) * mu / (T(3) * mu + (mu - lam * logJ) / (th[i] * th[j]));
+      T Aij = Ad[i][j];
       T Bij = (th[i] + th[j]) / (sig[i] + sig[j]);
       Mc[i][j] = T(0.5) * (Aij + Bij);
       Nc[i][j] = T(0.5) * (Aij - Bij);
@@ -559,7 +619,8 @@ __global__ void k_inertia(int nv, const double* mass, const double* q, const dou
 
 __global__ void __launch_bounds__(128) k_tet_force(int nt, const int32_t* tets, const double* gvec,
                                                    const double* vol, const double* mu_, const double* lam_,
-                                                   const double* q, double h, double* R, int* flags) {
+                                                   const int8_t* model, const double* q, double h, double* R,
+                                                   int* flags) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   int vid[4];
@@ -585,8 +646,8 @@ __global__ void __launch_bounds__(128) k_tet_force(int nt, const int32_t* tets, 
     for (int a = 0; a < 4; ++a) atomicAdd(&R[3 * (size_t)vid[a]], (double)INFINITY);
     return;
   }
-  double th[3], Hinv[3][3], logJ;
-  nh_prox<double>(sig, mu_[t], lam_[t], th, Hinv, logJ);
+  double th[3];
+  local_theta<double>(model ? model[t] : MODEL_NEO_HOOKEAN, sig, mu_[t], lam_[t], th);
   // F - P = U diag(sigma - theta) V^T
   double D[3][3];
 #pragma unroll
@@ -789,9 +850,10 @@ void launch_inertia(int nv, const double* mass, const double* q, const double* q
   k_inertia<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, mass, q, qt, R);
 }
 void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
-                      const double* lam, const double* q, double h, double* R, int* flags, cudaStream_t s) {
+                      const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,
+                      cudaStream_t s) {
   g_launches += 1;
-  if (nt) k_tet_force<<<nblk(nt, 128), 128, 0, s>>>(nt, tets, gvec, vol, mu, lam, q, h, R, flags);
+  if (nt) k_tet_force<<<nblk(nt, 128), 128, 0, s>>>(nt, tets, gvec, vol, mu, lam, model, q, h, R, flags);
 }
 void launch_local_contact(const ContactArgs& a, double* lambda, double* slip, int* loaded, double* R,
                           cudaStream_t s) {

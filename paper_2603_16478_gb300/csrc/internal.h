@@ -117,6 +117,9 @@ struct Scene {
   DevBuf inner;                   // inner GMRES on the capacitance: basis and scratch
   DevBuf fwd;                     // forward Newton vectors
   DevBuf fibre;                   // double [nt][3] actuation fibres (empty: none set)
+  DevBuf model;                   // int8 [nt] constitutive model per tet (valid when model_any)
+  bool model_any = false;         // some tet is not Neo-Hookean
+  const int8_t* model_ptr() const { return model_any ? static_cast<const int8_t*>(model.p) : nullptr; }
   DevBuf actf;                    // forward: f_ext + actuation force [3 nv]; adjoint: dL/da staging
   DevBuf vec32;                   // FP32 scratch of the mixed path
   int* flags_host = nullptr;      // pinned

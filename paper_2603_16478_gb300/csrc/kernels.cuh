@@ -25,6 +25,9 @@ enum Flag {
 };
 
 // ---- element / contact / contraction kernels (elem.cu) ---------------------------------
+// constitutive model of a tet (App. B.2); the values are those of NCPADJ_MODEL_*
+enum : int8_t { MODEL_NEO_HOOKEAN = 0, MODEL_COROTATIONAL = 1, MODEL_ARAP = 2 };
+
 struct TetArgs {
   int nt;
   const int32_t* tets;
@@ -39,6 +42,7 @@ struct TetArgs {
   float* bsr32;         // [nb][9] (mixed path) or null
   double* tetdata;      // [nt][18] contraction tensors
   int* flags;
+  const int8_t* model = nullptr;  // [nt] MODEL_* per tet (null: all Neo-Hookean)
 };
 void launch_tet_assemble64(const TetArgs& a, cudaStream_t s);
 void launch_tet_assemble32(const TetArgs& a, cudaStream_t s);
@@ -115,7 +119,8 @@ void launch_lift(int nc, const int32_t* vertex, const double* frame, const doubl
 void launch_inertia(int nv, const double* mass, const double* q, const double* qt, double* R, cudaStream_t s);
 // R[v_a] += h^2 w_i (F - p(F)) g_a  (elastic force of Eq. internal)
 void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
-                      const double* lam, const double* q, double h, double* R, int* flags, cudaStream_t s);
+                      const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,
+                      cudaStream_t s);
 // exact local solution of the contact equations at q: lambda_n = eps^2/delta_n,
 // gamma = mu lambda_n - eps^2/||delta_f||; writes lambda (frame coords), slips, loaded mask, and
 // R[v] -= h^2 F^T lambda
@@ -175,6 +180,8 @@ void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const
                            cudaStream_t s);
 void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s);
 //   gs[0..len) to host-mapped slot j % 2, then *jp = j + 1
+// Y + (*jp) * ld <- x (n values; *jp read on the device)
+void launch_copy_idx(int n, const double* x, double* Y, long ld, const int* jp, cudaStream_t s);
 void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s);
 // the two halves of A^{-1} = P^T S^T S P: w = S P x (position space, zeroed first), y = P^T S^T w
 void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s);

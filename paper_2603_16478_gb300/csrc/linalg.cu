@@ -420,6 +420,12 @@ __global__ void k_normalize_idx(int n, double* V, long ld, const int* __restrict
   if (i < n) v[i] = (nr > 0.0) ? v[i] / nr : 0.0;
   if (i == 0) *h_slot = nr;
 }
+// Y_j = x with j = *jp read on the device (column j of Y, stride ld)
+__global__ void k_copy_idx(int n, const double* __restrict__ x, double* __restrict__ Y, long ld,
+                           const int* __restrict__ jp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Y[(size_t)(*jp) * ld + i] = x[i];
+}
 // coefficients of step j to host-mapped slot j % 2, then j <- j + 1 (one block)
 __global__ void k_export_step(const double* __restrict__ gs, int len, double* host_slots, int* jp) {
   const int j = *jp;
@@ -620,6 +626,10 @@ void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const
 void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s) {
   g_launches += 1;
   k_normalize_idx<<<nblk(n, 256), 256, 0, s>>>(n, V, ld, jp, nrm2, h_slot);
+}
+void launch_copy_idx(int n, const double* x, double* Y, long ld, const int* jp, cudaStream_t s) {
+  g_launches += 1;
+  k_copy_idx<<<nblk(n, 256), 256, 0, s>>>(n, x, Y, ld, jp);
 }
 void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s) {
   g_launches += 1;
