@@ -10,6 +10,8 @@ the paper's fast route:
 
 * the Neo-Hookean prox p(F) is a 9-D Newton minimisation of mu||P-F||^2 + zeta(P) with
   invariant-based derivatives (no SVD),
+* the co-rotational and ARAP projections (App. B.2) come from the polar decomposition F = R S
+  and its differential (``models``),
 * its Jacobian dp/dF is the implicit-function-theorem form (I + grad^2 zeta / w)^{-1}
   of Eq. (pd_expanded), and dp/dmu, dp/dlambda likewise,
 * the contact Jacobian K_c = -d lambda_c / d delta_c comes from implicit differentiation of

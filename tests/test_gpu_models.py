@@ -99,8 +99,11 @@ def test_forward_matches_oracle_state(pkg, ctx, which):
     pb, st, s, q_prev, v_prev = step_case("cube_drop", 5, model)
     sc = pb.scene
     scene = _scene(pkg, ctx, sc, model)
+    # ARAP is not convex under compression: the residual line search damps Newton to t = 1/8 for
+    # about 70 iterations before the quadratic phase (the oracle's own Newton takes 89), so the
+    # forward gets the oracle's iteration budget
     q, lam, stats = pkg.forward_step(scene, gpu_contacts(pkg, st.ct), T(q_prev), T(v_prev), None,
-                                     tuple(sc.gravity), eps=sc.eps, newton_tol=1e-11)
+                                     tuple(sc.gravity), eps=sc.eps, newton_tol=1e-11, max_newton=200)
     assert stats["residual"] < 1e-8
     assert rel(q.cpu().numpy() - q_prev, s.q - q_prev) < 1e-7
     if st.nc:
