@@ -23,13 +23,22 @@ from .step import State, Step
 
 
 def _free(step: Step) -> Step:
-    """The same scene with no contacts."""
+    """The same scene with no contacts and no bindings."""
     ct = step.ct
     empty = dataclasses.replace(ct, vertex=ct.vertex[:0], frame=ct.frame[:0], d_n=ct.d_n[:0], d_f=ct.d_f[:0],
                                 mu=ct.mu[:0], region=ct.region[:0])
     X = step.mesh.X
     return Step(X, step.mesh.tets, step.E, step.nu, step.density, step.h, step.gravity, empty, step.eps,
                 step.model)
+
+
+def vertex_rows(n_verts, vertex):
+    """Rows selecting the coordinates of the given vertices [3 len(vertex), 3 n_verts] (the
+    constraint rows of hard attachments q_v = d)."""
+    Nm = np.zeros((3 * len(vertex), 3 * n_verts))
+    for b, v in enumerate(vertex):
+        Nm[3 * b:3 * b + 3, 3 * v:3 * v + 3] = np.eye(3)
+    return Nm
 
 
 def _normals(step: Step) -> np.ndarray:
@@ -40,16 +49,17 @@ def _normals(step: Step) -> np.ndarray:
     return Nm
 
 
-def constrained_step(step: Step, q_prev, v_prev, q_init, tol=1e-13, max_iter=50):
-    """(q*, lam*) of the step with every contact of ``step`` held at delta_n = 0, by Newton's
-    method on the KKT system with a dense LU, starting from q_init."""
+def constrained_step(step: Step, q_prev, v_prev, q_init, tol=1e-13, max_iter=50, Nm=None, d=None):
+    """(q*, lam*) of the step with every contact of ``step`` held at delta_n = 0 (or, given Nm and
+    d, with N q = d), by Newton's method on the KKT system with a dense LU, starting from q_init."""
     free = _free(step)
-    Nm = _normals(step)
-    d = step.ct.d_n
+    if Nm is None:
+        Nm, d = _normals(step), step.ct.d_n
+    d = np.asarray(d, float).reshape(-1)
     N = step.N
     qt = free.qtilde(q_prev, v_prev, np.zeros_like(q_prev))
     q = np.asarray(q_init, float).copy()
-    lam = np.zeros(step.nc)
+    lam = np.zeros(Nm.shape[0])
     empty = np.zeros(0)
     for _ in range(max_iter):
         Rq = free.residual(q, empty, empty, q_prev, qt)[:N]
@@ -57,22 +67,28 @@ def constrained_step(step: Step, q_prev, v_prev, q_init, tol=1e-13, max_iter=50)
         if np.max(np.abs(F)) <= tol * (1.0 + np.max(np.abs(Rq - Rq.mean()))):
             break
         A_el, _ = free.adjoint_matrix(State(q, empty, empty), q_prev)
-        J = np.block([[A_el.toarray() / step.h ** 2, -Nm.T], [Nm, np.zeros((step.nc, step.nc))]])
+        m = Nm.shape[0]
+        J = np.block([[A_el.toarray() / step.h ** 2, -Nm.T], [Nm, np.zeros((m, m))]])
         dx = np.linalg.solve(J, -F)
         q = q + dx[:N].reshape(-1, 3)
         lam = lam + dx[N:]
     return q, lam
 
 
-def constrained_adjoint(step: Step, q_star, q_prev, dL_dq, dL_dv=None):
-    """z* of the equality-constrained step at its solution q_star (see the module docstring)."""
+def constrained_adjoint(step: Step, q_star, q_prev, dL_dq, dL_dv=None, Nm=None, with_multiplier=False):
+    """z* of the equality-constrained step at its solution q_star (see the module docstring).
+    With ``with_multiplier`` also w_l, which is dL/dd: the constraint targets d enter the KKT
+    residual only as -d in its second block, so dL/dd = [b; 0]^T J^{-1} [0; I] = w_l."""
     free = _free(step)
-    Nm = _normals(step)
+    if Nm is None:
+        Nm = _normals(step)
+    m = Nm.shape[0]
     empty = np.zeros(0)
     A_el, _ = free.adjoint_matrix(State(q_star, empty, empty), q_prev)
-    J = np.block([[A_el.toarray() / step.h ** 2, -Nm.T], [Nm, np.zeros((step.nc, step.nc))]])
+    J = np.block([[A_el.toarray() / step.h ** 2, -Nm.T], [Nm, np.zeros((m, m))]])
     b = np.asarray(dL_dq, float).reshape(-1)
     if dL_dv is not None:
         b = b + np.asarray(dL_dv, float).reshape(-1) / step.h
-    w = np.linalg.solve(J.T, np.concatenate([b, np.zeros(step.nc)]))
-    return w[:step.N].reshape(-1, 3) / step.h ** 2
+    w = np.linalg.solve(J.T, np.concatenate([b, np.zeros(m)]))
+    z = w[:step.N].reshape(-1, 3) / step.h ** 2
+    return (z, w[step.N:]) if with_multiplier else z

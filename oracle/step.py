@@ -55,10 +55,12 @@ class State:
 class Step:
     """One time step of a scene with a frozen contact set."""
 
-    def __init__(self, X, tets, E, nu, density, h, gravity, contacts, eps, model=models.NEO_HOOKEAN):
+    def __init__(self, X, tets, E, nu, density, h, gravity, contacts, eps, model=models.NEO_HOOKEAN,
+                 bindings=None):
         self.mesh = Mesh(X, tets)
         models.by_model(model, self.mesh.n_tets)  # validates: one name, or one per tet
         self.model = model if isinstance(model, str) else np.asarray(model).copy()
+        self.bindings = bindings  # oracle.binding.Bindings or None
         self.E = np.broadcast_to(np.asarray(E, float), (self.mesh.n_tets,)).copy()
         self.nu = np.broadcast_to(np.asarray(nu, float), (self.mesh.n_tets,)).copy()
         self.density = float(density)
@@ -101,6 +103,8 @@ class Step:
         w = 2.0 * mu_L * mesh.vol
         r_el = np.einsum("tji,tj->ti", mesh.G, (np.swapaxes(F, 1, 2) - np.swapaxes(P, 1, 2)).reshape(-1, 9))
         Rq = (self.mass[:, None] * (q - qt)).reshape(-1) + h2 * mesh.scatter_vectors(w[:, None] * r_el)
+        if self.bindings is not None:
+            Rq = Rq + self.bindings.residual_term(q, self.h, mesh.n_verts)
         Rn = np.zeros(self.nc)
         Rf = np.zeros(self.nc)
         for c in range(self.nc):
@@ -236,6 +240,8 @@ class Step:
         w = 2.0 * mu_L * mesh.vol
         blocks = h2 * w[:, None, None] * np.einsum("tki,tkl,tlj->tij", mesh.G, np.eye(9) - Jp, mesh.G)
         A_el = sp.diags(np.repeat(self.mass, 3)) + mesh.scatter_blocks(blocks)
+        if self.bindings is not None:
+            A_el = A_el + self.bindings.matrix_term(self.h, mesh.n_verts)
         K, kmu = self.contact_blocks(state, q_prev, mu_c, eps)
         rows, cols, vals = [], [], []
         for c in range(self.nc):
@@ -288,5 +294,7 @@ class Step:
         out["dL_dlamL"] = dlam
         out["dL_dE"] = dmu * dmu_dE + dlam * dlam_dE
         out["dL_dnu"] = dmu * dmu_dnu + dlam * dlam_dnu
+        if self.bindings is not None:
+            out.update(self.bindings.gradients(state.q, z, h))
         out["A"] = Amat
         return out
