@@ -155,13 +155,33 @@ typedef struct {
   int32_t n_regions;
 } ncpadj_contacts;
 
+/* Bilateral binding constraints on single vertices (Eq. binding), for one call.  Binding b
+ * attaches vertex[b] to the point target[b] through a compliant spring:
+ *   delta_b = q_v - d_b,  phi_b = delta_b + E_b lambda_b = 0,  so lambda_b = -(q_v - d_b) / E_b,
+ * with the compliance E_b = compliance[b] > 0 (small E_b: a stiff attachment; J_b selects the
+ * vertex's three coordinates).  The forward step gains the force h^2 (q_v - d_b) / E_b in its
+ * residual, script_A gains h^2 / E_b I_3 on v's diagonal block (Eq. differential_2), and the
+ * adjoint returns dL/dd_b = h^2 z_v / E_b and dL/dE_b = h^2 z_v . (q_v - d_b) / E_b^2.  The
+ * Woodbury preconditioner does not include them: they perturb the preconditioned operator by a
+ * matrix of rank 3 n_bindings, which Krylov absorbs in at most that many extra iterations.
+ *   vertex [n_bindings] int32 in [0, n_verts), target [n_bindings*3], compliance [n_bindings]:
+ *   device arrays (the call must use NCPADJ_MEM_DEVICE).  Several bindings may share a vertex. */
+typedef struct {
+  int32_t n_bindings;
+  const int32_t* vertex;
+  const double* target;
+  const double* compliance;
+} ncpadj_bindings;
+
 /* Converged forward state: q, q_prev [n_verts*3]; lambda [n_c*3] contact forces in frame
  * coordinates (lambda_n, lambda_f1, lambda_f2).  The tangential multiplier used in the
- * friction blocks is gamma = -lambda_f . delta_f / ||delta_f|| (signed). */
+ * friction blocks is gamma = -lambda_f . delta_f / ||delta_f|| (signed).  bindings: the
+ * call's bilateral bindings, or NULL for none (they must be the ones the forward step used). */
 typedef struct {
   const double* q;
   const double* q_prev;
   const double* lambda;
+  const ncpadj_bindings* bindings;
 } ncpadj_state;
 
 /* Loss seeds dL/dq and dL/dv [n_verts*3] at the end of the step (dL_dv may be NULL = 0). */
@@ -176,7 +196,9 @@ typedef struct {
  *   dL_dmu                               [n_regions] (friction coefficient per region)
  *   dL_dmu_contact                       [n_c]       (per contact)
  *   dL_dact                              [n_tets]    (FP32; per-tet activation, see
- *                                                     ncpadj_scene_set_fibres) */
+ *                                                     ncpadj_scene_set_fibres)
+ *   dL_dbinding_target                   [n_b*3]     (binding targets d_b)
+ *   dL_dcompliance                       [n_b]       (binding compliances E_b) */
 typedef struct {
   double* dL_dq_prev;
   double* dL_dv_prev;
@@ -187,6 +209,8 @@ typedef struct {
   double* dL_dmu_contact;
   double* z;
   float* dL_dact;  /* [n_tets] activation gradient; requires the scene's fibres (see below) */
+  double* dL_dbinding_target;  /* [n_b*3]; requires state.bindings */
+  double* dL_dcompliance;      /* [n_b];   requires state.bindings */
 } ncpadj_grads;
 
 /* Solver options; fill with ncpadj_options_default first.
@@ -323,6 +347,7 @@ typedef struct {
   const double* f_ext;
   double gravity[3];
   const float* act;  /* [n_tets] activations (Pa) or NULL; requires the scene's fibres */
+  const ncpadj_bindings* bindings;  /* bilateral bindings of the step, or NULL */
 } ncpadj_forward_input;
 
 typedef struct {

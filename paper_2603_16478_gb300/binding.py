@@ -55,8 +55,14 @@ class _Contacts(C.Structure):
                 ("d_f", C.c_void_p), ("mu", C.c_void_p), ("region", C.c_void_p), ("n_regions", C.c_int32)]
 
 
+class _Bindings(C.Structure):
+    _fields_ = [("n_bindings", C.c_int32), ("vertex", C.c_void_p), ("target", C.c_void_p),
+                ("compliance", C.c_void_p)]
+
+
 class _State(C.Structure):
-    _fields_ = [("q", C.c_void_p), ("q_prev", C.c_void_p), ("lam", C.c_void_p)]
+    _fields_ = [("q", C.c_void_p), ("q_prev", C.c_void_p), ("lam", C.c_void_p),
+                ("bindings", C.POINTER(_Bindings))]
 
 
 class _Seed(C.Structure):
@@ -66,7 +72,8 @@ class _Seed(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("dL_dq_prev", C.c_void_p), ("dL_dv_prev", C.c_void_p), ("dL_dfext", C.c_void_p),
                 ("dL_dE", C.c_void_p), ("dL_dnu", C.c_void_p), ("dL_dmu", C.c_void_p),
-                ("dL_dmu_contact", C.c_void_p), ("z", C.c_void_p), ("dL_dact", C.c_void_p)]
+                ("dL_dmu_contact", C.c_void_p), ("z", C.c_void_p), ("dL_dact", C.c_void_p),
+                ("dL_dbinding_target", C.c_void_p), ("dL_dcompliance", C.c_void_p)]
 
 
 class _Options(C.Structure):
@@ -88,7 +95,7 @@ class _Stats(C.Structure):
 
 class _ForwardInput(C.Structure):
     _fields_ = [("q_prev", C.c_void_p), ("v_prev", C.c_void_p), ("f_ext", C.c_void_p), ("gravity", C.c_double * 3),
-                ("act", C.c_void_p)]
+                ("act", C.c_void_p), ("bindings", C.POINTER(_Bindings))]
 
 
 class _ForwardStats(C.Structure):
@@ -271,24 +278,50 @@ class Contacts:
                         self.n_regions)
 
 
+@dataclass
+class Bindings:
+    """Bilateral bindings on single vertices (Eq. binding): vertex[b] is held near target[b] by a
+    spring of compliance E_b (tensors on the device the call uses)."""
+    vertex: torch.Tensor      # int32 [n_b]
+    target: torch.Tensor      # float64 [n_b, 3]
+    compliance: torch.Tensor  # float64 [n_b], > 0
+
+    @property
+    def n(self):
+        return int(self.vertex.shape[0])
+
+
+def _bindings_ref(bindings: Optional[Bindings]):
+    """(pointer for the call, the struct it points to: keep it alive for the call)."""
+    if bindings is None or bindings.n == 0:
+        return None, None
+    b = _Bindings(bindings.n, _ptr(bindings.vertex), _ptr(bindings.target), _ptr(bindings.compliance))
+    return C.pointer(b), b
+
+
 def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4,
                  rtol=1e-8, max_iters=2000, restart=64, precision="fp64", cap_precision="fp64", precond="woodbury",
                  solver="auto", cap_block=0,
                  memory="device", outputs: Optional[dict] = None, stream=None, want=("dL_dq_prev", "dL_dv_prev",
-                 "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z")):
+                 "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z"), bindings: Optional[Bindings] = None):
     """One adjoint step through the C-ABI.  Returns (grads dict of tensors, stats dict).
 
     ``outputs`` may hold preallocated output tensors by name; otherwise they are allocated on
-    q's device (pinned CPU memory with memory="host").
+    q's device (pinned CPU memory with memory="host").  With ``bindings`` (the ones the forward
+    step used) the outputs also hold dL_dbinding_target [n_b, 3] and dL_dcompliance [n_b].
     """
     lib = scene.lib
     nc = contacts.n if contacts is not None else 0
+    nb = bindings.n if bindings is not None else 0
     nv, nt = scene.n_verts, scene.n_tets
     nreg = contacts.n_regions if contacts is not None else 1
     dev = q.device
     outputs = dict(outputs or {})
+    if nb:
+        want = tuple(want) + tuple(k for k in ("dL_dbinding_target", "dL_dcompliance") if k not in want)
     shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
-              "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (max(nc, 0),), "dL_dact": (nt,)}
+              "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (max(nc, 0),), "dL_dact": (nt,),
+              "dL_dbinding_target": (nb, 3), "dL_dcompliance": (nb,)}
     for k in want:
         if k not in outputs:
             dt = torch.float32 if k == "dL_dact" else torch.float64
@@ -300,10 +333,12 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     if nc:
         cts = _Contacts(nc, _ptr(contacts.vertex), _ptr(contacts.frame), _ptr(contacts.d_n), _ptr(contacts.d_f),
                         _ptr(contacts.mu), _ptr(contacts.region), int(contacts.n_regions))
-    stt = _State(_ptr(q), _ptr(q_prev), _ptr(lam) if nc else None)
+    bptr, _bkeep = _bindings_ref(bindings)
+    stt = _State(_ptr(q), _ptr(q_prev), _ptr(lam) if nc else None, bptr)
     sd = _Seed(_ptr(dL_dq), _ptr(dL_dv))
     gr = _Grads(*[_ptr(outputs.get(k)) for k in ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu",
-                                                 "dL_dmu", "dL_dmu_contact", "z", "dL_dact")])
+                                                 "dL_dmu", "dL_dmu_contact", "z", "dL_dact", "dL_dbinding_target",
+                                                 "dL_dcompliance")])
     opt = _Options()
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
@@ -332,16 +367,19 @@ def _contacts_struct(contacts):
 
 def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None, f_ext=None,
                  gravity=(0.0, 0.0, -9.81), *, eps=1e-4, newton_tol=1e-10, max_newton=60, precond="woodbury",
-                 rtol=1e-10, max_iters=2000, restart=64, stream=None, act=None, cap_precision="fp64"):
+                 rtol=1e-10, max_iters=2000, restart=64, stream=None, act=None, cap_precision="fp64",
+                 bindings: Optional[Bindings] = None):
     """One forward step on the GPU (device tensors).  ``act``: float32 [n_tets] activations (the
-    scene needs fibres, ``Scene.set_fibres``).  Returns (q, lambda [n_c, 3], stats)."""
+    scene needs fibres, ``Scene.set_fibres``); ``bindings``: bilateral bindings of the step.
+    Returns (q, lambda [n_c, 3], stats)."""
     lib = scene.lib
     nc = contacts.n if contacts is not None else 0
     dev = q_prev.device
     q = torch.empty_like(q_prev)
     lam = torch.empty((max(nc, 1), 3), dtype=torch.float64, device=dev)
+    bptr, _bkeep = _bindings_ref(bindings)
     fin = _ForwardInput(_ptr(q_prev), _ptr(v_prev), _ptr(f_ext), (C.c_double * 3)(*[float(g) for g in gravity]),
-                        _ptr(act))
+                        _ptr(act), bptr)
     opt = _Options()
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)

@@ -314,6 +314,10 @@ struct Inputs {  // device pointers for one call
   const double* lambda = nullptr;
   const double* dL_dq = nullptr;
   const double* dL_dv = nullptr;
+  int nbind = 0;  // bilateral bindings (device arrays)
+  const int32_t* bvertex = nullptr;
+  const double* btarget = nullptr;
+  const double* bcompliance = nullptr;
 };
 
 struct Engine {
@@ -505,6 +509,8 @@ struct Engine {
     if (mixed) launch_tet_assemble32(ta, st);
     else launch_tet_assemble64(ta, st);
     if (nc) launch_contact_blocks(contact_args(q, q_prev, lambda, eps), st);
+    if (in.nbind)
+      launch_binding_blocks(in.nbind, in.bvertex, in.bcompliance, S.diag_slot.as<int32_t>(), h, b64, b32, st);
     NCPADJ_CUDA_TRY(cudaGetLastError());
   }
 
@@ -966,6 +972,23 @@ void check_contacts(Scene& S, int nc, const int32_t* cvertex, const int32_t* reg
   NCPADJ_REQUIRE(S.flags_host[FLAG_BADINDEX] == 0, "a contact vertex or region id is out of range");
 }
 
+// the call's bilateral bindings into the engine's inputs, after checking their vertex ids and
+// compliances on the device (the flags were cleared at the start of the call)
+void take_bindings(Scene& S, const ncpadj_bindings* bd, bool host_mem, Inputs& in, cudaStream_t st) {
+  if (!bd) return;
+  NCPADJ_REQUIRE(bd->n_bindings >= 0, "n_bindings < 0");
+  if (bd->n_bindings == 0) return;
+  NCPADJ_REQUIRE(bd->vertex && bd->target && bd->compliance, "binding arrays vertex, target, compliance are required");
+  NCPADJ_REQUIRE(!host_mem, "bindings need options.memory = NCPADJ_MEM_DEVICE");
+  launch_check_bindings(bd->n_bindings, bd->vertex, bd->compliance, S.nv, S.flags.as<int>(), st);
+  read_flags(S, st);
+  NCPADJ_REQUIRE(S.flags_host[FLAG_BADINDEX] == 0, "a binding vertex is out of range or a compliance is not positive");
+  in.nbind = bd->n_bindings;
+  in.bvertex = bd->vertex;
+  in.btarget = bd->target;
+  in.bcompliance = bd->compliance;
+}
+
 int pick_solver(int requested, int nc, const double* mu, bool host_mem, cudaStream_t st) {
   if (requested != NCPADJ_SOLVER_AUTO) return requested;
   bool frictionless = true;
@@ -1011,6 +1034,9 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   NCPADJ_REQUIRE(state && seed && state->q && state->q_prev && seed->dL_dq, "state.q, state.q_prev and seed.dL_dq are required");
   NCPADJ_REQUIRE(!grads || !grads->dL_dact || sc->s.fibre.p,
                  "dL_dact requested but the scene has no fibres (ncpadj_scene_set_fibres)");
+  NCPADJ_REQUIRE(!grads || (!grads->dL_dbinding_target && !grads->dL_dcompliance) ||
+                     (state->bindings && state->bindings->n_bindings > 0),
+                 "binding gradients requested but state.bindings holds no bindings");
   ncpadj_options opt;
   if (opt_in) opt = *opt_in;
   else ncpadj_options_default(&opt);
@@ -1084,6 +1110,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, in.cvertex, in.region, nreg, st);  // before anything indexes with the ids
+  take_bindings(S, state->bindings, host_mem, in, st);
   E.workspace(nc, opt.gmres_restart, opt.precond);
   // an inner iterative capacitance solve makes the preconditioner vary: flexible GMRES only
   if (!E.sup_c0.empty() && opt.precond == NCPADJ_PRECOND_WOODBURY) solver = NCPADJ_SOLVER_GMRES;
@@ -1163,6 +1190,9 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     launch_act_grad(nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.fibre.as<double>(), E.x, S.h,
                     dact, st);
   }
+  if (in.nbind && grads && (grads->dL_dbinding_target || grads->dL_dcompliance))
+    launch_binding_grad(in.nbind, in.bvertex, in.btarget, in.bcompliance, in.q, E.x, S.h, grads->dL_dbinding_target,
+                        grads->dL_dcompliance, st);
   if (go.z) NCPADJ_CUDA_TRY(cudaMemcpyAsync(go.z, E.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   launch_nonfinite_check(N, E.x, flags, st);
   NCPADJ_CUDA_TRY(cudaGetLastError());
@@ -1251,6 +1281,7 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);  // before any indexing
+  take_bindings(S, fin->bindings, false, E.in, st);
   E.workspace(nc, opt.gmres_restart, opt.precond);
   if (!E.sup_c0.empty() && opt.precond == NCPADJ_PRECOND_WOODBURY) solver = NCPADJ_SOLVER_GMRES;
   E.transpose = 0;
@@ -1298,6 +1329,8 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     launch_inertia(nv, S.massd.as<double>(), qq, qt, RR, st);
     launch_tet_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
                      S.lam.as<double>(), S.model_ptr(), qq, S.h, RR, flags, st);
+    if (E.in.nbind)
+      launch_binding_force(E.in.nbind, E.in.bvertex, E.in.btarget, E.in.bcompliance, qq, S.h, RR, st);
     if (nc) {
       ContactArgs ca = E.contact_args(qq, fin->q_prev, nullptr, opt.eps);
       // the loaded mask belongs to the accepted iterate: trial points (check_turn) leave it alone

@@ -569,6 +569,57 @@ __global__ void k_check_contacts(int nc, const int32_t* vertex, const int32_t* r
   if (bad) atomicExch(&flags[FLAG_BADINDEX], 1);
 }
 
+// ---- bilateral bindings on single vertices (Eq. binding): phi_b = q_v - d_b + E_b lambda_b = 0 ----
+
+// a binding vertex out of range or a compliance that is not a positive finite number
+__global__ void k_check_bindings(int nb, const int32_t* vertex, const double* compliance, int nv, int* flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int v = vertex[b];
+  const double e = compliance[b];
+  if (v < 0 || v >= nv || !(e > 0.0) || !isfinite(e)) atomicExch(&flags[FLAG_BADINDEX], 1);
+}
+// h^2 J_b^T E_b^{-1} J_b = h^2 / E_b I_3 on the bound vertex's diagonal block (Eq. differential_2)
+template <typename OutT>
+__global__ void k_binding_blocks(int nb, const int32_t* __restrict__ vertex, const double* __restrict__ compliance,
+                                 const int32_t* __restrict__ diag_slot, double h, OutT* bsr) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const double k = h * h / compliance[b];
+  OutT* dst = bsr + 9 * (size_t)diag_slot[vertex[b]];
+  atomic_add_out(dst + 0, k);
+  atomic_add_out(dst + 4, k);
+  atomic_add_out(dst + 8, k);
+}
+// the binding force in the momentum residual: -h^2 J_b^T lambda_b = h^2 (q_v - d_b) / E_b at v
+__global__ void k_binding_force(int nb, const int32_t* __restrict__ vertex, const double* __restrict__ target,
+                                const double* __restrict__ compliance, const double* __restrict__ q, double h,
+                                double* R) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int v = vertex[b];
+  const double k = h * h / compliance[b];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) atomicAdd(&R[3 * (size_t)v + r], k * (q[3 * (size_t)v + r] - target[3 * (size_t)b + r]));
+}
+// dL/dd_b = h^2 z_v / E_b ; dL/dE_b = h^2 z_v . (q_v - d_b) / E_b^2 (Eq. compute_gradient)
+__global__ void k_binding_grad(int nb, const int32_t* __restrict__ vertex, const double* __restrict__ target,
+                               const double* __restrict__ compliance, const double* __restrict__ q,
+                               const double* __restrict__ z, double h, double* d_target, double* d_compliance) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int v = vertex[b];
+  const double e = compliance[b], k = h * h / e;
+  double s = 0.0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double zr = z[3 * (size_t)v + r];
+    if (d_target) d_target[3 * (size_t)b + r] = k * zr;
+    s += zr * (q[3 * (size_t)v + r] - target[3 * (size_t)b + r]);
+  }
+  if (d_compliance) d_compliance[b] = k * s / e;
+}
+
 // ---- forward step ---------------------------------------------------------------------------
 
 __global__ void k_predict(int nv, const double* q_prev, const double* v_prev, const double* f_ext, const double* mass,
@@ -848,6 +899,29 @@ void launch_lift(int nc, const int32_t* vertex, const double* frame, const doubl
 void launch_inertia(int nv, const double* mass, const double* q, const double* qt, double* R, cudaStream_t s) {
   g_launches += 1;
   k_inertia<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, mass, q, qt, R);
+}
+void launch_check_bindings(int nb, const int32_t* vertex, const double* compliance, int nv, int* flags,
+                           cudaStream_t s) {
+  g_launches += 1;
+  if (nb) k_check_bindings<<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, compliance, nv, flags);
+}
+void launch_binding_blocks(int nb, const int32_t* vertex, const double* compliance, const int32_t* diag_slot,
+                           double h, double* bsr, float* bsr32, cudaStream_t s) {
+  g_launches += 1;
+  if (!nb) return;
+  if (bsr) k_binding_blocks<double><<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, compliance, diag_slot, h, bsr);
+  else k_binding_blocks<float><<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, compliance, diag_slot, h, bsr32);
+}
+void launch_binding_force(int nb, const int32_t* vertex, const double* target, const double* compliance,
+                          const double* q, double h, double* R, cudaStream_t s) {
+  g_launches += 1;
+  if (nb) k_binding_force<<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, target, compliance, q, h, R);
+}
+void launch_binding_grad(int nb, const int32_t* vertex, const double* target, const double* compliance,
+                         const double* q, const double* z, double h, double* d_target, double* d_compliance,
+                         cudaStream_t s) {
+  g_launches += 1;
+  if (nb) k_binding_grad<<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, target, compliance, q, z, h, d_target, d_compliance);
 }
 void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
                       const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,

@@ -118,6 +118,17 @@ void launch_lift(int nc, const int32_t* vertex, const double* frame, const doubl
 // R = M (q - qt)
 void launch_inertia(int nv, const double* mass, const double* q, const double* qt, double* R, cudaStream_t s);
 // R[v_a] += h^2 w_i (F - p(F)) g_a  (elastic force of Eq. internal)
+// bilateral bindings on single vertices (Eq. binding): index / compliance check (FLAG_BADINDEX),
+// h^2 / E_b I_3 into the diagonal blocks, the residual's binding force, and dL/dd_b, dL/dE_b
+void launch_check_bindings(int nb, const int32_t* vertex, const double* compliance, int nv, int* flags,
+                           cudaStream_t s);
+void launch_binding_blocks(int nb, const int32_t* vertex, const double* compliance, const int32_t* diag_slot,
+                           double h, double* bsr, float* bsr32, cudaStream_t s);
+void launch_binding_force(int nb, const int32_t* vertex, const double* target, const double* compliance,
+                          const double* q, double h, double* R, cudaStream_t s);
+void launch_binding_grad(int nb, const int32_t* vertex, const double* target, const double* compliance,
+                         const double* q, const double* z, double h, double* d_target, double* d_compliance,
+                         cudaStream_t s);
 void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
                       const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,
                       cudaStream_t s);

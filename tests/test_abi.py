@@ -54,3 +54,36 @@ def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2603_16478_gb300 import binding
     with pytest.raises(RuntimeError, match="missing"):
         binding.load_library(str(tmp_path / "nope.so"))
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (compiled by gcc)."""
+    import shutil
+    import subprocess
+    from paper_2603_16478_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"ncpadj_scene_desc": B._SceneDesc, "ncpadj_scene_info": B._SceneInfo, "ncpadj_contacts": B._Contacts,
+             "ncpadj_bindings": B._Bindings, "ncpadj_state": B._State, "ncpadj_seed": B._Seed,
+             "ncpadj_grads": B._Grads, "ncpadj_options": B._Options, "ncpadj_stats": B._Stats,
+             "ncpadj_forward_input": B._ForwardInput, "ncpadj_forward_stats": B._ForwardStats}
+    # the ctypes field names follow the header's, except lambda (a Python keyword)
+    rename = {("ncpadj_state", "lam"): "lambda"}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ncpadj.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            cf = rename.get((cname, f), f)
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                               text=True).stdout.splitlines())
+    for cname, py in pairs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
