@@ -416,6 +416,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-block measurement")
+    ap.add_argument("--no-models", action="store_true",
+                    help="skip the co-rotational / ARAP / bindings timings on the beam")
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
     ap.add_argument("--quadruped", action="store_true", help="add the actuated quadruped measurement")
     ap.add_argument("--quad-scale", type=float, default=1.0, help="linear scale of the quadruped (1 = full size)")
@@ -483,11 +485,11 @@ def main():
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def one(mem="device", ins=None, outs=None, prec="fp64", cap="fp64"):
+    def one(mem="device", ins=None, outs=None, prec="fp64", cap="fp64", bindings=None):
         a = ins or (q_adj, q_prev_adj, lam_adj, dL_dq, dL_dv, contacts)
         return pkg.adjoint_step(scene, a[5], a[0], a[1], a[2], a[3], a[4], eps=sc.eps, rtol=1e-8, memory=mem,
                                 outputs=outs or outputs, stream=stream.cuda_stream, precision=prec,
-                                cap_precision=cap)
+                                cap_precision=cap, bindings=bindings)
 
     variants = {"fp64": ("fp64", "fp64"), "mixed": ("mixed", "mixed"), "mixed_cap64": ("mixed", "fp64")}
     # accuracy of the mixed variants against plain FP64 on the same inputs
@@ -501,10 +503,10 @@ def main():
                          for k in ref)
     torch.cuda.synchronize(dev)
 
-    def timed(pr, cp, steps):
+    def timed(pr, cp, steps, **kw):
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
-                one(prec=pr, cap=cp)
+                one(prec=pr, cap=cp, **kw)
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
@@ -514,7 +516,7 @@ def main():
             for i in range(steps):
                 flush.zero_()  # evict the previous step's working set from L2
                 ev[i][0].record(stream)
-                _, st = one(prec=pr, cap=cp)
+                _, st = one(prec=pr, cap=cp, **kw)
                 ev[i][1].record(stream)
                 sts.append(st)
         torch.cuda.synchronize(dev)
@@ -580,6 +582,35 @@ def main():
     roof["note"] = ("burst figure: applies replayed back to back from a captured graph, S and S^T "
                     "(53 MB on the beam) L2-resident between launches")
 
+    # ---- the other constitutive models (App. B.2) and stiff bindings, same scene and state ----
+    # (one rank only: a failure here must not leave other ranks waiting in a collective)
+    models_res = None
+    if world == 1 and not args.no_models:
+        models_res = {}
+        try:
+            for mname in ("corotational", "arap"):
+                scene.set_model(mname)
+                tm, sm = timed(*variants[head], max(3, args.steps // 4))
+                models_res[mname] = {"gradients_per_s": len(sm) / (tm / 1e3),
+                                     "krylov_iterations": statistics.median(x["iterations"] for x in sm),
+                                     "ms_assemble": statistics.mean(x["ms_assemble"] for x in sm)}
+            scene.set_model("neo_hookean")
+            nbind = 40  # vertices spread over the beam, held where they are by stiff springs
+            bv = torch.arange(0, sc.n_verts, max(1, sc.n_verts // nbind), device=dev,
+                              dtype=torch.int32)[:nbind].contiguous()
+            nbind = int(bv.shape[0])
+            bd = pkg.Bindings(bv, q_adj[bv.long()].contiguous(),
+                              torch.full((nbind,), 1e-6, dtype=torch.float64, device=dev))
+            tm, sm = timed(*variants[head], max(3, args.steps // 4), bindings=bd)
+            models_res["bindings"] = {"n": nbind, "compliance": 1e-6, "gradients_per_s": len(sm) / (tm / 1e3),
+                                      "krylov_iterations": statistics.median(x["iterations"] for x in sm)}
+        except Exception as e:  # noqa: BLE001
+            models_res["error"] = str(e)[:300]
+        try:
+            scene.set_model("neo_hookean")
+        except Exception as e:  # noqa: BLE001
+            models_res["error"] = models_res.get("error", "") + f"; reset: {str(e)[:100]}"
+
     # ---- the batched workload ----
     batch_res = None
     if not args.no_batch:
@@ -631,6 +662,7 @@ def main():
                        "forward_newton_iters": [f["newton_iters"] for f in fwd_stats],
                        "forward_residual": [f["residual"] for f in fwd_stats],
                        "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "batched": batch_res,
+                       **({"models": models_res} if models_res is not None else {}),
                        **({"sphere": sphere_res} if sphere_res is not None else {}),
                        **({"quadruped": quad_res} if quad_res is not None else {})},
             "roofline": roof, "cpu_baseline": cpu,
