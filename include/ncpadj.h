@@ -259,9 +259,10 @@ typedef struct {
 } ncpadj_stats;
 
 /* One adjoint step: assemble script_A^T at the given converged state, solve for z and
- * contract the gradients.  Errors: INVALID_ARG, INVERTED_ELEMENT, CONTACT_DOMAIN,
- * NOT_CONVERGED (outputs hold the last iterate's gradients, stats the residual),
- * NONFINITE, TIMEOUT, OOM, CUDA. */
+ * contract the gradients.  Errors: INVALID_ARG (including a contact or binding vertex out of
+ * range, a compliance that is not positive, bindings with NCPADJ_MEM_HOST, binding gradients
+ * without bindings), INVERTED_ELEMENT, CONTACT_DOMAIN, NOT_CONVERGED (outputs hold the last
+ * iterate's gradients, stats the residual), NONFINITE, TIMEOUT, OOM, CUDA. */
 ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpadj_contacts* contacts,
                                   const ncpadj_state* state, const ncpadj_seed* seed,
                                   const ncpadj_options* opt, ncpadj_grads* grads,
