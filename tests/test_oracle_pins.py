@@ -553,3 +553,30 @@ def test_friction_gradient_is_continuous_through_the_stick_slip_threshold():
     # trapezoid integral of dL/dmu against L(mu_end) - L(mu_start)
     integral = np.sum(0.5 * (gs[1:] + gs[:-1]) * np.diff(mus))
     assert abs(integral - (Ls[-1] - Ls[0])) <= 5e-3 * abs(Ls[-1] - Ls[0])
+
+
+# ---- frame completion: gradients do not depend on the choice of t1, t2 ---------------------
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_gradients_are_invariant_to_the_tangent_frame(k):
+    """Rotating each contact's (t1, t2) about its normal by its own angle leaves the converged
+    state and every gradient unchanged: only the frame coordinates of lambda_f rotate."""
+    import dataclasses
+    pb, st, s, q_prev, v_prev = step_case("cube_drop", k)
+    qt = pb.q_target
+    ct = st.ct
+    ang = np.random.default_rng(31).uniform(0, 2 * np.pi, ct.n)
+    frame = ct.frame.copy()
+    c_, s_ = np.cos(ang)[:, None], np.sin(ang)[:, None]
+    frame[:, 1] = c_ * ct.frame[:, 1] + s_ * ct.frame[:, 2]
+    frame[:, 2] = -s_ * ct.frame[:, 1] + c_ * ct.frame[:, 2]
+    rot = make_step(pb.scene, dataclasses.replace(ct, frame=frame))
+    s2 = rot.forward(q_prev, v_prev, q_init=s.q)
+    assert s2.residual < 1e-8
+    assert np.max(np.abs(s2.q - s.q)) <= 1e-12 * np.max(np.abs(s.q - q_prev))
+    dq = 2 * (s.q - qt)
+    dv = np.random.default_rng(32).normal(size=qt.shape) * 1e-3
+    g1 = st.adjoint(s, q_prev, dq, dv)
+    g2 = rot.adjoint(s2, q_prev, dq, dv)
+    for key in ("z", "dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu_contact"):
+        assert rel(g2[key], g1[key]) < 1e-9, key
