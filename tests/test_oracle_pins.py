@@ -580,3 +580,28 @@ def test_gradients_are_invariant_to_the_tangent_frame(k):
     g2 = rot.adjoint(s2, q_prev, dq, dv)
     for key in ("z", "dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu_contact"):
         assert rel(g2[key], g1[key]) < 1e-9, key
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_paper_epsilon_variant(k):
+    """The paper's own smoothing, 2 eps^2 = 1e-12 (config 1 otherwise unchanged): the forward stops
+    at its rounding floor (residual ~1e-6 of h^2 |M g|, the contacts being ~1e4 times stiffer than at
+    eps = 1e-4), and the adjoint still matches central differences in E."""
+    from tests._cases import rollout
+    eps = np.sqrt(0.5e-12)
+    pb, q_prev, v_prev = rollout("cube_drop", k)
+    sc = pb.scene
+    ct = sc.contacts(q_prev)
+    st = make_step(sc, ct, eps=eps)
+    s = st.forward(q_prev, v_prev)
+    assert s.residual < 1e-5
+    qt = pb.q_target
+    g = st.adjoint(s, q_prev, 2 * (s.q - qt), np.zeros_like(qt))
+
+    def L(E):
+        r = make_step(sc, ct, E=E, eps=eps).forward(q_prev, v_prev, q_init=s.q)
+        return np.sum((r.q - qt) ** 2)
+
+    E0, eta = sc.E[0], 1e-6
+    fd = (L(E0 * (1 + eta)) - L(E0 * (1 - eta))) / (2 * eta * E0)
+    assert rel(g["dL_dE"].sum(), fd) < 1e-7
