@@ -257,13 +257,22 @@ class Step:
         return (A_el + Kc).tocsr(), pieces
 
     def adjoint(self, state: State, q_prev, dL_dq, dL_dv, mu_c=None, eps=None):
-        """All one-step gradients for seeds dL/dq, dL/dv [n_v, 3].  Returns dict."""
+        """All one-step gradients for seeds dL/dq, dL/dv [n_v, 3]: z from a direct sparse LU of
+        script_A^T z = dL/dq + dL/dv / h (Eq. adjoint), then the contractions.  Returns dict."""
+        Amat, pc = self.adjoint_matrix(state, q_prev, mu_c, eps)
+        b = (np.asarray(dL_dq) + np.asarray(dL_dv) / self.h).reshape(-1)
+        z = spla.spsolve(Amat.T.tocsc(), b)
+        out = self.contract(state, z, dL_dv, pc)
+        out["A"] = Amat
+        return out
+
+    def contract(self, state: State, z, dL_dv, pc):
+        """The gradients of Eq. (compute_gradient) for a given adjoint solution z [3 n_v] (pieces
+        ``pc`` from adjoint_matrix at the same state)."""
         mesh = self.mesh
         h = self.h
         h2 = h * h
-        Amat, pc = self.adjoint_matrix(state, q_prev, mu_c, eps)
-        b = (np.asarray(dL_dq) + np.asarray(dL_dv) / h).reshape(-1)
-        z = spla.spsolve(Amat.T.tocsc(), b)
+        z = np.asarray(z, float).reshape(-1)
         out = dict(z=z.reshape(-1, 3))
         # K_qbar = M + h^2 sum_c J_c^T K_c P_f J_c
         Pf = np.diag([0.0, 1.0, 1.0])
@@ -296,5 +305,4 @@ class Step:
         out["dL_dnu"] = dmu * dmu_dnu + dlam * dlam_dnu
         if self.bindings is not None:
             out.update(self.bindings.gradients(state.q, z, h))
-        out["A"] = Amat
         return out
