@@ -117,3 +117,96 @@ def test_soft_bindings_vanish():
     g0 = free.adjoint(s0, q_prev, 2 * (s0.q - qt), np.zeros_like(qt))
     assert rel(g1["dL_dq_prev"], g0["dL_dq_prev"]) < 1e-6
     assert rel(g1["dL_dE"], g0["dL_dE"]) < 1e-6
+
+
+# ---- points inside tets (barycentric weights) -------------------------------------------------
+
+def _bary_case(k, compliance, shift=1e-3):
+    """Cube-drop step k with points inside the four highest tets attached to targets lifted by
+    ``shift`` (seeded barycentric weights)."""
+    pb, q_prev, v_prev = rollout("cube_drop", k)
+    sc = pb.scene
+    cz = sc.X[sc.tets].mean(axis=1)[:, 2]
+    tets = sc.tets[np.argsort(-cz)[:4]]
+    w = np.random.default_rng(7).dirichlet(np.ones(4), size=4)
+    pts = np.einsum("bk,bkj->bj", w, q_prev[tets])
+    bd = Bindings(tets, np.full(4, compliance), pts + np.array([0.0, 0.0, shift]), weight=w)
+    ct = sc.contacts(q_prev)
+    st = Step(sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h, sc.gravity, ct, sc.eps, "neo_hookean", bd)
+    return pb, st, bd, q_prev, v_prev
+
+
+def test_unit_weights_reduce_to_the_single_vertex_binding():
+    pb, st, bd, q_prev, v_prev = _case(2, 1e-4)
+    n = st.mesh.n_verts
+    others = np.stack([bd.vertex, (bd.vertex + 1) % n, (bd.vertex + 2) % n, (bd.vertex + 3) % n], axis=1)
+    w = np.zeros((4, 4))
+    w[:, 0] = 1.0
+    b4 = Bindings(others, bd.compliance, bd.target, weight=w)
+    q = q_prev + 1e-3
+    z = np.random.default_rng(5).normal(size=q.shape)
+    assert np.array_equal(b4.residual_term(q, st.h, n), bd.residual_term(q, st.h, n))
+    assert abs(b4.matrix_term(st.h, n) - bd.matrix_term(st.h, n)).max() == 0.0
+    for key, val in b4.gradients(q, z, st.h).items():
+        assert np.array_equal(val, bd.gradients(q, z, st.h)[key])
+
+
+def test_matrix_term_equals_the_stacked_rows_product():
+    """h^2 J_b^T E_b^{-1} J_b from the coordinate triplets equals the product of the stacked rows."""
+    pb, st, bd, q_prev, v_prev = _bary_case(0, 1e-4)
+    n = st.mesh.n_verts
+    Nm = bd.rows(n)
+    dense = st.h ** 2 * Nm.T @ np.kron(np.diag(1.0 / bd.compliance), np.eye(3)) @ Nm
+    assert np.allclose(bd.matrix_term(st.h, n).toarray(), dense, rtol=0, atol=1e-14 * np.abs(dense).max())
+    q = q_prev + 1e-3
+    assert np.allclose(bd.point(q), (Nm @ q.reshape(-1)).reshape(-1, 3))
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_barycentric_gradients_match_central_differences(k):
+    pb, st, bd, q_prev, v_prev = _bary_case(k, 1e-4)
+    qt = pb.q_target
+    base = st.forward(q_prev, v_prev)
+    assert base.residual < 1e-9
+    g = st.adjoint(base, q_prev, 2 * (base.q - qt), np.zeros_like(qt))
+
+    def L(target=bd.target, compliance=bd.compliance):
+        b2 = Bindings(bd.vertex, compliance, target, weight=bd.weight)
+        s2 = Step(st.mesh.X, st.mesh.tets, st.E, st.nu, st.density, st.h, st.gravity, st.ct, st.eps, st.model, b2)
+        r = s2.forward(q_prev, v_prev, q_init=base.q)
+        assert r.residual < 1e-9
+        return np.sum((r.q - qt) ** 2)
+
+    d = np.random.default_rng(13).standard_normal(bd.target.shape)
+    d /= np.linalg.norm(d)
+    fd = (L(target=bd.target + 1e-7 * d) - L(target=bd.target - 1e-7 * d)) / 2e-7
+    assert rel(np.sum(g["dL_dbinding_target"] * d), fd) < 1e-5
+    e = 1e-4 * bd.compliance[0]
+    de = np.zeros(bd.n)
+    de[0] = 1.0
+    fd = (L(compliance=bd.compliance + e * de) - L(compliance=bd.compliance - e * de)) / (2 * e)
+    assert rel(g["dL_dcompliance"][0], fd) < 1e-5
+
+
+def test_stiff_barycentric_bindings_converge_to_the_hard_attachment():
+    """As for single vertices; a point inside a tet spreads the spring over four vertices (weights
+    ~1/4), so the O(E_b) regime starts a decade stiffer."""
+    errs_q, errs_g = [], []
+    hard = None
+    for E in (1e-5, 1e-6, 1e-7, 1e-8):
+        pb, st, bd, q_prev, v_prev = _bary_case(0, E)
+        assert st.nc == 0
+        qt = pb.q_target
+        s = st.forward(q_prev, v_prev, tol=1e-12)
+        g = st.adjoint(s, q_prev, 2 * (s.q - qt), np.zeros_like(qt))
+        if hard is None:
+            Nm = bd.rows(st.mesh.n_verts)
+            q_h, _ = constrained_step(st, q_prev, v_prev, s.q, Nm=Nm, d=bd.target)
+            assert np.allclose(bd.point(q_h), bd.target, atol=1e-14)
+            _, w_l = constrained_adjoint(st, q_h, q_prev, 2 * (q_h - qt), Nm=Nm, with_multiplier=True)
+            hard = (q_h, w_l.reshape(-1, 3))
+        errs_q.append(rel(s.q - q_prev, hard[0] - q_prev))
+        errs_g.append(rel(g["dL_dbinding_target"], hard[1]))
+    for e in (errs_q, errs_g):
+        assert all(e[i + 1] < e[i] / 8 for i in range(len(e) - 1)), e
+    assert errs_q[-1] < 1e-4 and errs_g[-1] < 1e-4, (errs_q, errs_g)
