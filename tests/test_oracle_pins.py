@@ -605,3 +605,18 @@ def test_paper_epsilon_variant(k):
     E0, eta = sc.E[0], 1e-6
     fd = (L(E0 * (1 + eta)) - L(E0 * (1 - eta))) / (2 * eta * E0)
     assert rel(g["dL_dE"].sum(), fd) < 1e-7
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_frictionless_adjoint_is_symmetric_positive_definite(k):
+    """Sec. 4.4: without friction the contact blocks are R^T diag(lambda_n/delta_n, 0, 0) R, so
+    script_A stays symmetric and (here) positive definite."""
+    import dataclasses
+    pb, st, s, q_prev, v_prev = step_case("cube_drop", k)
+    ct0 = dataclasses.replace(st.ct, mu=np.zeros(st.nc))
+    st0 = make_step(pb.scene, ct0)
+    s0 = st0.forward(q_prev, v_prev)
+    assert s0.residual < 1e-8 and st0.nc > 0
+    A, _ = st0.adjoint_matrix(s0, q_prev)
+    assert abs(A - A.T).max() <= 1e-13 * abs(A).max()
+    np.linalg.cholesky(A.toarray())  # raises if not positive definite
