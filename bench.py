@@ -102,11 +102,13 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------------
 # reference arm and CPU baseline: the FP64 oracle, single-threaded, in a child process
 # --------------------------------------------------------------------------------------------
-def oracle_times(steps, warmup):
+def oracle_times(steps, warmup, state=None):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-m", "oracle.timing", "--steps", str(steps), "--warmup", str(warmup)],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    cmd = [sys.executable, "-m", "oracle.timing", "--steps", str(steps), "--warmup", str(warmup)]
+    if state:
+        cmd += ["--state", state]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -495,10 +497,12 @@ def main():
     # accuracy of the mixed variants against plain FP64 on the same inputs
     ref = {k: v.clone() for k, v in one(prec="fp64")[0].items()}
     errs = {}
+    grads_by = {"fp64": ref}  # kept for the oracle comparison of the CPU-baseline leg
     for name, (pr, cp) in variants.items():
         if name == "fp64":
             continue
         g_ = one(prec=pr, cap=cp)[0]
+        grads_by[name] = {k: v.clone() for k, v in g_.items()}
         errs[name] = max(float((torch.linalg.norm(g_[k] - ref[k]) / torch.linalg.norm(ref[k]).clamp_min(1e-300)).item())
                          for k in ref)
     torch.cuda.synchronize(dev)
@@ -634,15 +638,35 @@ def main():
             quad_res = {"error": str(e)[:300]}
 
     # ---- CPU baseline: the oracle, one thread, bounded sample ----
+    # The oracle runs at the bench's own state (the GPU forward's), on the same seeds, so the same
+    # runs also give each GPU variant's gradient error against the oracle.
     cpu = None
+    err_oracle = None
     if rank == 0 and not args.no_cpu_baseline:
+        import tempfile
+        d = None
+        where = "the bench's GPU state (3 forward steps from rest, same seeds)"
         try:
-            d = oracle_times(3, 1)
+            with tempfile.TemporaryDirectory() as tdir:
+                path = os.path.join(tdir, "state.npz")
+                arrays = {"q": q_adj.cpu().numpy(), "q_prev": q_prev_adj.cpu().numpy(), "dL_dq": dL_dq.cpu().numpy(),
+                          "dL_dv": dL_dv.cpu().numpy()}
+                for vname, gv in grads_by.items():
+                    for k, v in gv.items():
+                        arrays[f"{vname}/{k}"] = v.cpu().numpy()
+                np.savez(path, **arrays)
+                d = oracle_times(3, 1, state=path)
+            err_oracle = d.get("rel_err_vs_oracle")
+        except Exception:  # noqa: BLE001 -- fall back to the oracle's own start point
+            where = "the oracle's start point of step 1"
+            try:
+                d = oracle_times(3, 1)
+            except Exception as e:  # noqa: BLE001
+                cpu = {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+        if d is not None:
             cpu = {"value": len(d["seconds"]) / sum(d["seconds"]), "unit": "gradients/s", "cores": d["threads"],
                    "kind": "oracle", "sample": f"{len(d['seconds'])} oracle adjoints of the beam (assembly + direct "
-                   "sparse LU + contractions) at the oracle's start point of step 1, after 1 warm-up"}
-        except Exception as e:  # noqa: BLE001
-            cpu = {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+                   f"sparse LU + contractions) at {where}, after 1 warm-up"}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
@@ -653,7 +677,8 @@ def main():
                        "precision": {"fp64": "plain FP64", "mixed": "FP32 matrix/preconditioner/capacitance factor, FP64 "
                                      "Krylov reductions", "mixed_cap64": "FP32 matrix/preconditioner, FP64 capacitance "
                                      "factor and Krylov reductions"}[head],
-                       "gradients_per_s": rate, "max_rel_err_vs_fp64": errs, "preconditioner": "Woodbury",
+                       "gradients_per_s": rate, "max_rel_err_vs_fp64": errs, "max_rel_err_vs_oracle": err_oracle,
+                       "preconditioner": "Woodbury",
                        "solver": "GMRES(64)", "rtol": 1e-8, "krylov_iterations": it, "capacitance_dim": ncap,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
                        "wall_s": t_wall, "stage_ms": {k: statistics.mean(s[k] for s in stats) for k in
