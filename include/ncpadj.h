@@ -9,7 +9,10 @@
  * with the per-tet SVD projection Jacobians of Sec. 4.3 / App. B, the per-contact smoothed
  * FB blocks of Sec. 4.2 / Eq. final_diff_contact, a Woodbury-preconditioned Krylov solve
  * (Sec. 4.4, Eq. woodbury_formula) and the gradient contractions dL/dx = z^T K_x
- * (Eq. compute_gradient, App. B.3).
+ * (Eq. compute_gradient, App. B.3).  Each tet may instead use the co-rotational or ARAP
+ * projection of App. B.2 (ncpadj_scene_set_model); per-tet actuation (ncpadj_scene_set_fibres)
+ * and bilateral bindings of vertices (ncpadj_bindings, Eq. binding) add their terms and their
+ * gradients.  ncpadj_forward_step produces the converged states the adjoint needs.
  *
  * Conventions
  *  - Positions are [n_verts][3] row-major float64 (DOF 3v+r is coordinate r of vertex v).
