@@ -210,3 +210,35 @@ def test_stiff_barycentric_bindings_converge_to_the_hard_attachment():
     for e in (errs_q, errs_g):
         assert all(e[i + 1] < e[i] / 8 for i in range(len(e) - 1)), e
     assert errs_q[-1] < 1e-4 and errs_g[-1] < 1e-4, (errs_q, errs_g)
+
+
+def test_models_bindings_and_friction_compose():
+    """Co-rotational tets, stiff bindings and frictional contacts in one step: every gradient
+    against central differences of the whole step."""
+    pb, st0, bd, q_prev, v_prev = _case(2, 1e-5)
+    sc = pb.scene
+    mk = lambda E=sc.E, target=bd.target, compliance=bd.compliance: Step(  # noqa: E731
+        sc.X, sc.tets, E, sc.nu, sc.density, sc.h, sc.gravity, st0.ct, sc.eps, "corotational",
+        Bindings(bd.vertex, compliance, target))
+    st = mk()
+    qt = pb.q_target
+    base = st.forward(q_prev, v_prev)
+    assert base.residual < 1e-9 and st.nc > 0
+    g = st.adjoint(base, q_prev, 2 * (base.q - qt), np.zeros_like(qt))
+
+    def L(**kw):
+        r = mk(**kw).forward(q_prev, v_prev, q_init=base.q)
+        assert r.residual < 1e-9
+        return np.sum((r.q - qt) ** 2)
+
+    E0 = sc.E[0]
+    fd = (L(E=E0 * (1 + 1e-6)) - L(E=E0 * (1 - 1e-6))) / (2e-6 * E0)
+    assert rel(g["dL_dE"].sum(), fd) < 1e-5
+    d = np.random.default_rng(17).standard_normal(bd.target.shape)
+    d /= np.linalg.norm(d)
+    fd = (L(target=bd.target + 1e-7 * d) - L(target=bd.target - 1e-7 * d)) / 2e-7
+    assert rel(np.sum(g["dL_dbinding_target"] * d), fd) < 1e-5
+    e = np.zeros(bd.n)
+    e[1] = 1e-4 * bd.compliance[1]
+    fd = (L(compliance=bd.compliance + e) - L(compliance=bd.compliance - e)) / (2 * e[1])
+    assert rel(g["dL_dcompliance"][1], fd) < 1e-5

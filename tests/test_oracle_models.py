@@ -210,3 +210,12 @@ def test_per_tet_models_dispatch_by_group():
         assert np.array_equal(dmu[i], mi[0]) and np.array_equal(dlam[i], li[0])
     with pytest.raises(ValueError):
         Mo.prox(np.array(["stvk"] * 6), F, MU, LAM)
+
+
+def test_arap_gradients_in_E_and_nu_are_tied_through_mu():
+    """ARAP ignores lambda, so per tet dL/dnu = -E / (1 + nu) dL/dE (both act through mu alone)."""
+    pb, st, s, q_prev, v_prev = step_case("cube_drop", 2, Mo.ARAP)
+    g = st.adjoint(s, q_prev, 2 * (s.q - pb.q_target), np.zeros_like(pb.q_target))
+    expect = -g["dL_dE"] * st.E / (1.0 + st.nu)
+    assert np.allclose(g["dL_dnu"], expect, rtol=1e-12, atol=1e-14 * np.abs(expect).max())
+    assert np.abs(g["dL_dlamL"]).max() == 0.0
