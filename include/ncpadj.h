@@ -72,7 +72,7 @@ enum {
   NCPADJ_PRECOND_ELASTIC = 2,  /* A^{-1} by the elastic factor (sparse-inverse preconditioner) */
   NCPADJ_PRECOND_WOODBURY = 3  /* (A + K_c)^{-1} by Eq. woodbury_formula (default) */
 };
-enum { NCPADJ_SOLVER_AUTO = 0, NCPADJ_SOLVER_CG = 1, NCPADJ_SOLVER_GMRES = 2 };
+enum { NCPADJ_SOLVER_AUTO = 0, NCPADJ_SOLVER_CG = 1, NCPADJ_SOLVER_GMRES = 2, NCPADJ_SOLVER_BICGSTAB = 3 };
 enum { NCPADJ_MEM_DEVICE = 0, NCPADJ_MEM_HOST = 1 };
 /* constitutive model of a tet (App. B.2), see ncpadj_scene_set_model */
 enum { NCPADJ_MODEL_NEO_HOOKEAN = 0, NCPADJ_MODEL_COROTATIONAL = 1, NCPADJ_MODEL_ARAP = 2 };
@@ -225,7 +225,10 @@ typedef struct {
  *              FP32), FP32 matvec and preconditioner apply, FP64 vectors, dot products,
  *              Gram-Schmidt and Hessenberg; contact blocks always from FP64 state.
  *   precond    NCPADJ_PRECOND_* (default WOODBURY); solver NCPADJ_SOLVER_* (default AUTO:
- *              CG when every mu is 0, else GMRES, Sec. 4.4); memory NCPADJ_MEM_*.
+ *              CG when every mu is 0, else GMRES, Sec. 4.4; NCPADJ_SOLVER_BICGSTAB on request:
+ *              right-preconditioned BiCGSTAB, no restart, at least 7 vectors of workspace; an
+ *              inner iterative capacitance solve makes the preconditioner vary, and then GMRES
+ *              (flexible) is used whatever is asked); memory NCPADJ_MEM_*.
  *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default) or
  *              NCPADJ_MIXED (inverted and applied in FP32; it only preconditions, so the result
  *              keeps the solve's precision and tolerance).
@@ -250,7 +253,7 @@ void ncpadj_options_default(ncpadj_options* opt);
 /* Per-call statistics (nullable).  Times are CUDA-event times of the stages on the stream. */
 typedef struct {
   int32_t iterations;       /* Krylov iterations */
-  int32_t solver_used;      /* NCPADJ_SOLVER_CG or NCPADJ_SOLVER_GMRES */
+  int32_t solver_used;      /* NCPADJ_SOLVER_CG, _GMRES or _BICGSTAB */
   int32_t n_contacts;
   int32_t capacitance_dim;  /* dimension of the dense contact-space system (0 if none) */
   double rel_residual;      /* final ||b - script_A^T z|| / ||b|| (recomputed explicitly) */

@@ -447,7 +447,8 @@ struct Engine {
     S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
     const size_t nvec = 9, ncv = 3 * (size_t)std::max(ncap, 1);
     S.vecs.ensure(sizeof(double) * (nvec * N + ncv + 64));
-    S.gmres.ensure(sizeof(double) * ((size_t)(m + 1) * N + 3 * (size_t)(m + 1) + 16));
+    // (m + 1) basis vectors and the coefficient slots; at least 7 vectors (BiCGSTAB's)
+    S.gmres.ensure(sizeof(double) * ((size_t)std::max(m + 1, 7) * N + 3 * (size_t)(m + 1) + 16));
     if (S.red.bytes < dot_scratch_bytes()) {  // counters of the fused dot product start at zero
       S.red.ensure(dot_scratch_bytes());
       NCPADJ_CUDA_TRY(cudaMemset(S.red.p, 0, dot_scratch_bytes()));
@@ -861,6 +862,54 @@ struct Engine {
           launch_copy_scalar(s2 + 1, s2 + 0, st);
         }
         iters = std::min(iters, max_iters);
+      } else if (solver == NCPADJ_SOLVER_BICGSTAB) {
+        // right-preconditioned BiCGSTAB (van der Vorst 1992): iterates on A P^{-1} u = b and
+        // accumulates x = P^{-1} u directly.  Scalars on the host (one synchronisation per inner
+        // product); the seven vectors in columns of the GMRES buffer, t and s adjacent so that one
+        // call gives t.t and s.t.  A breakdown ends the loop; the true residual below decides.
+        double* G = S.gmres.as<double>();
+        double *rh = G, *p = G + N, *v = G + 2 * (size_t)N, *ph = G + 3 * (size_t)N, *t = G + 4 * (size_t)N,
+               *s = G + 5 * (size_t)N, *sh = G + 6 * (size_t)N;
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(rh, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        for (iters = 1; iters <= max_iters; ++iters) {
+          const double rho = dot_host(rh, r);
+          if (!std::isfinite(rho) || rho == 0.0) break;
+          if (iters == 1) {
+            NCPADJ_CUDA_TRY(cudaMemcpyAsync(p, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+          } else {
+            const double beta = (rho / rho_old) * (alpha / omega);
+            launch_axpby(N, 1.0, p, -omega, v, p, st);  // p - omega v
+            launch_axpby(N, 1.0, r, beta, p, p, st);    // r + beta (p - omega v)
+          }
+          apply_precond(p, ph);
+          matvec(ph, v);
+          const double rv = dot_host(rh, v);
+          if (!std::isfinite(rv) || rv == 0.0) break;
+          alpha = rho / rv;
+          launch_axpby(N, 1.0, r, -alpha, v, s, st);  // s = r - alpha v
+          const double sn = std::sqrt(dot_host(s, s));
+          if (!std::isfinite(sn)) break;
+          if (sn <= tol) {
+            launch_axpby(N, 1.0, x, alpha, ph, x, st);
+            break;
+          }
+          apply_precond(s, sh);
+          matvec(sh, t);
+          launch_multi_dot(N, 2, t, N, t, partial, scal + 12, st);  // t.t, s.t
+          NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host + 12, scal + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+          const double tt = S.scal_host[12], ts = S.scal_host[13];
+          omega = (tt > 0.0 && std::isfinite(tt)) ? ts / tt : 0.0;
+          launch_axpby(N, 1.0, x, alpha, ph, x, st);
+          launch_axpby(N, 1.0, x, omega, sh, x, st);
+          launch_axpby(N, 1.0, s, -omega, t, r, st);  // r = s - omega t
+          rho_old = rho;
+          const double rn = std::sqrt(dot_host(r, r));
+          if (!std::isfinite(rn) || rn <= tol || omega == 0.0) break;
+        }
+        iters = std::min(iters, max_iters);
       } else {
         // Arnoldi vectors on the device; the small Hessenberg least-squares problem (Givens
         // rotations, triangular solve) on the host, which reads the Gram-Schmidt coefficients of
@@ -1007,7 +1056,7 @@ int pick_solver(int requested, int nc, const double* mu, bool host_mem, cudaStre
 void validate_options(const ncpadj_options& opt) {
   NCPADJ_REQUIRE(opt.eps > 0 && opt.rtol > 0 && opt.max_iters > 0 && opt.gmres_restart > 0 && opt.gmres_restart <= 512,
                  "bad options (eps, rtol, max_iters, gmres_restart)");
-  NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 2, "bad precond/solver");
+  NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 3, "bad precond/solver");
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
   NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
   NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED, "bad cap_precision");
