@@ -168,12 +168,18 @@ typedef struct {
  * Woodbury preconditioner does not include them: they perturb the preconditioned operator by a
  * matrix of rank 3 n_bindings, which Krylov absorbs in at most that many extra iterations.
  *   vertex [n_bindings] int32 in [0, n_verts), target [n_bindings*3], compliance [n_bindings]:
- *   device arrays (the call must use NCPADJ_MEM_DEVICE).  Several bindings may share a vertex. */
+ *   device arrays (the call must use NCPADJ_MEM_DEVICE).  Several bindings may share a vertex.
+ *   tet [n_bindings] int32 in [0, n_tets) and bary [n_bindings*4] (both, or both NULL): binding b
+ *   is then the point sum_a bary[b][a] x_a of the vertices of tet[b] (a point inside the tet for
+ *   barycentric weights), J_b = bary_b^T (x) I_3, its blocks h^2 w_a w_c / E_b I_3 lie in the
+ *   tet's own pattern, and vertex is not read. */
 typedef struct {
   int32_t n_bindings;
   const int32_t* vertex;
   const double* target;
   const double* compliance;
+  const int32_t* tet;
+  const double* bary;
 } ncpadj_bindings;
 
 /* Converged forward state: q, q_prev [n_verts*3]; lambda [n_c*3] contact forces in frame

@@ -57,7 +57,7 @@ class _Contacts(C.Structure):
 
 class _Bindings(C.Structure):
     _fields_ = [("n_bindings", C.c_int32), ("vertex", C.c_void_p), ("target", C.c_void_p),
-                ("compliance", C.c_void_p)]
+                ("compliance", C.c_void_p), ("tet", C.c_void_p), ("bary", C.c_void_p)]
 
 
 class _State(C.Structure):
@@ -280,22 +280,26 @@ class Contacts:
 
 @dataclass
 class Bindings:
-    """Bilateral bindings on single vertices (Eq. binding): vertex[b] is held near target[b] by a
-    spring of compliance E_b (tensors on the device the call uses)."""
-    vertex: torch.Tensor      # int32 [n_b]
-    target: torch.Tensor      # float64 [n_b, 3]
-    compliance: torch.Tensor  # float64 [n_b], > 0
+    """Bilateral bindings (Eq. binding): a vertex, or with ``tet`` and ``bary`` the point
+    sum_a bary[b, a] x_a of the vertices of tet[b], held near target[b] by a spring of compliance
+    E_b (tensors on the device the call uses).  ``vertex`` may be None for points inside tets."""
+    vertex: Optional[torch.Tensor]     # int32 [n_b]
+    target: torch.Tensor               # float64 [n_b, 3]
+    compliance: torch.Tensor           # float64 [n_b], > 0
+    tet: Optional[torch.Tensor] = None   # int32 [n_b]
+    bary: Optional[torch.Tensor] = None  # float64 [n_b, 4]
 
     @property
     def n(self):
-        return int(self.vertex.shape[0])
+        return int(self.compliance.shape[0])
 
 
 def _bindings_ref(bindings: Optional[Bindings]):
     """(pointer for the call, the struct it points to: keep it alive for the call)."""
     if bindings is None or bindings.n == 0:
         return None, None
-    b = _Bindings(bindings.n, _ptr(bindings.vertex), _ptr(bindings.target), _ptr(bindings.compliance))
+    b = _Bindings(bindings.n, _ptr(bindings.vertex), _ptr(bindings.target), _ptr(bindings.compliance),
+                  _ptr(bindings.tet), _ptr(bindings.bary))
     return C.pointer(b), b
 
 

@@ -318,6 +318,8 @@ struct Inputs {  // device pointers for one call
   const int32_t* bvertex = nullptr;
   const double* btarget = nullptr;
   const double* bcompliance = nullptr;
+  const int32_t* btet = nullptr;  // points inside tets (with bbary [nbind][4]) instead of vertices
+  const double* bbary = nullptr;
 };
 
 struct Engine {
@@ -510,7 +512,9 @@ struct Engine {
     if (mixed) launch_tet_assemble32(ta, st);
     else launch_tet_assemble64(ta, st);
     if (nc) launch_contact_blocks(contact_args(q, q_prev, lambda, eps), st);
-    if (in.nbind)
+    if (in.nbind && in.btet)
+      launch_binding_blocks_bary(in.nbind, in.btet, in.bbary, in.bcompliance, S.slot.as<int32_t>(), h, b64, b32, st);
+    else if (in.nbind)
       launch_binding_blocks(in.nbind, in.bvertex, in.bcompliance, S.diag_slot.as<int32_t>(), h, b64, b32, st);
     NCPADJ_CUDA_TRY(cudaGetLastError());
   }
@@ -1027,15 +1031,25 @@ void take_bindings(Scene& S, const ncpadj_bindings* bd, bool host_mem, Inputs& i
   if (!bd) return;
   NCPADJ_REQUIRE(bd->n_bindings >= 0, "n_bindings < 0");
   if (bd->n_bindings == 0) return;
-  NCPADJ_REQUIRE(bd->vertex && bd->target && bd->compliance, "binding arrays vertex, target, compliance are required");
+  const bool bary = bd->tet || bd->bary;
+  NCPADJ_REQUIRE(!bary || (bd->tet && bd->bary), "bindings need both tet and bary, or neither");
+  NCPADJ_REQUIRE((bary || bd->vertex) && bd->target && bd->compliance,
+                 "binding arrays vertex (or tet and bary), target, compliance are required");
   NCPADJ_REQUIRE(!host_mem, "bindings need options.memory = NCPADJ_MEM_DEVICE");
-  launch_check_bindings(bd->n_bindings, bd->vertex, bd->compliance, S.nv, S.flags.as<int>(), st);
+  if (bary)
+    launch_check_bindings_bary(bd->n_bindings, bd->tet, bd->bary, bd->compliance, S.nt, S.flags.as<int>(), st);
+  else
+    launch_check_bindings(bd->n_bindings, bd->vertex, bd->compliance, S.nv, S.flags.as<int>(), st);
   read_flags(S, st);
-  NCPADJ_REQUIRE(S.flags_host[FLAG_BADINDEX] == 0, "a binding vertex is out of range or a compliance is not positive");
+  NCPADJ_REQUIRE(S.flags_host[FLAG_BADINDEX] == 0,
+                 bary ? "a binding tet is out of range, a weight is not finite or a compliance is not positive"
+                      : "a binding vertex is out of range or a compliance is not positive");
   in.nbind = bd->n_bindings;
-  in.bvertex = bd->vertex;
+  in.bvertex = bary ? nullptr : bd->vertex;
   in.btarget = bd->target;
   in.bcompliance = bd->compliance;
+  in.btet = bary ? bd->tet : nullptr;
+  in.bbary = bary ? bd->bary : nullptr;
 }
 
 int pick_solver(int requested, int nc, const double* mu, bool host_mem, cudaStream_t st) {
@@ -1239,9 +1253,14 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     launch_act_grad(nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.fibre.as<double>(), E.x, S.h,
                     dact, st);
   }
-  if (in.nbind && grads && (grads->dL_dbinding_target || grads->dL_dcompliance))
-    launch_binding_grad(in.nbind, in.bvertex, in.btarget, in.bcompliance, in.q, E.x, S.h, grads->dL_dbinding_target,
-                        grads->dL_dcompliance, st);
+  if (in.nbind && grads && (grads->dL_dbinding_target || grads->dL_dcompliance)) {
+    if (in.btet)
+      launch_binding_grad_bary(in.nbind, in.btet, S.tets.as<int32_t>(), in.bbary, in.btarget, in.bcompliance, in.q,
+                               E.x, S.h, grads->dL_dbinding_target, grads->dL_dcompliance, st);
+    else
+      launch_binding_grad(in.nbind, in.bvertex, in.btarget, in.bcompliance, in.q, E.x, S.h, grads->dL_dbinding_target,
+                          grads->dL_dcompliance, st);
+  }
   if (go.z) NCPADJ_CUDA_TRY(cudaMemcpyAsync(go.z, E.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   launch_nonfinite_check(N, E.x, flags, st);
   NCPADJ_CUDA_TRY(cudaGetLastError());
@@ -1378,7 +1397,10 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     launch_inertia(nv, S.massd.as<double>(), qq, qt, RR, st);
     launch_tet_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
                      S.lam.as<double>(), S.model_ptr(), qq, S.h, RR, flags, st);
-    if (E.in.nbind)
+    if (E.in.nbind && E.in.btet)
+      launch_binding_force_bary(E.in.nbind, E.in.btet, S.tets.as<int32_t>(), E.in.bbary, E.in.btarget,
+                                E.in.bcompliance, qq, S.h, RR, st);
+    else if (E.in.nbind)
       launch_binding_force(E.in.nbind, E.in.bvertex, E.in.btarget, E.in.bcompliance, qq, S.h, RR, st);
     if (nc) {
       ContactArgs ca = E.contact_args(qq, fin->q_prev, nullptr, opt.eps);

@@ -620,6 +620,95 @@ __global__ void k_binding_grad(int nb, const int32_t* __restrict__ vertex, const
   if (d_compliance) d_compliance[b] = k * s / e;
 }
 
+// ---- bindings of points inside tets: J_b q = sum_a w_a q_{tets[t][a]} (barycentric weights) ----
+// (the blocks couple the vertices of one tet, so they land in the tet's own pattern slots)
+
+// a tet id out of range, a weight that is not finite or a compliance that is not a positive finite
+// number (FLAG_BADINDEX)
+__global__ void k_check_bindings_bary(int nb, const int32_t* tet, const double* bary, const double* compliance,
+                                      int nt, int* flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int t = tet[b];
+  const double e = compliance[b];
+  bool bad = t < 0 || t >= nt || !(e > 0.0) || !isfinite(e);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) bad = bad || !isfinite(bary[4 * (size_t)b + a]);
+  if (bad) atomicExch(&flags[FLAG_BADINDEX], 1);
+}
+// h^2 / E_b w_a w_c I_3 on the block (v_a, v_c) of the binding's tet
+template <typename OutT>
+__global__ void k_binding_blocks_bary(int nb, const int32_t* __restrict__ tet, const double* __restrict__ bary,
+                                      const double* __restrict__ compliance, const int32_t* __restrict__ slot,
+                                      double h, OutT* bsr) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int t = tet[b];
+  const double k = h * h / compliance[b];
+  double w[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) w[a] = bary[4 * (size_t)b + a];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double kac = k * w[a] * w[c];
+      OutT* dst = bsr + 9 * (size_t)slot[16 * (size_t)t + 4 * a + c];
+      atomic_add_out(dst + 0, kac);
+      atomic_add_out(dst + 4, kac);
+      atomic_add_out(dst + 8, kac);
+    }
+}
+// the binding force: h^2 w_a (J_b q - d_b) / E_b at each vertex v_a of the tet
+__global__ void k_binding_force_bary(int nb, const int32_t* __restrict__ tet, const int32_t* __restrict__ tets,
+                                     const double* __restrict__ bary, const double* __restrict__ target,
+                                     const double* __restrict__ compliance, const double* __restrict__ q, double h,
+                                     double* R) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int t = tet[b];
+  int v[4];
+  double w[4], d[3] = {-target[3 * (size_t)b], -target[3 * (size_t)b + 1], -target[3 * (size_t)b + 2]};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    v[a] = tets[4 * (size_t)t + a];
+    w[a] = bary[4 * (size_t)b + a];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) d[r] += w[a] * q[3 * (size_t)v[a] + r];
+  }
+  const double k = h * h / compliance[b];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) atomicAdd(&R[3 * (size_t)v[a] + r], k * w[a] * d[r]);
+}
+// dL/dd_b = h^2 (J_b z) / E_b ; dL/dE_b = h^2 (J_b z) . (J_b q - d_b) / E_b^2
+__global__ void k_binding_grad_bary(int nb, const int32_t* __restrict__ tet, const int32_t* __restrict__ tets,
+                                    const double* __restrict__ bary, const double* __restrict__ target,
+                                    const double* __restrict__ compliance, const double* __restrict__ q,
+                                    const double* __restrict__ z, double h, double* d_target, double* d_compliance) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int t = tet[b];
+  double jz[3] = {0.0, 0.0, 0.0}, d[3] = {-target[3 * (size_t)b], -target[3 * (size_t)b + 1], -target[3 * (size_t)b + 2]};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int v = tets[4 * (size_t)t + a];
+    const double w = bary[4 * (size_t)b + a];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      jz[r] += w * z[3 * (size_t)v + r];
+      d[r] += w * q[3 * (size_t)v + r];
+    }
+  }
+  const double e = compliance[b], k = h * h / e;
+  if (d_target) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) d_target[3 * (size_t)b + r] = k * jz[r];
+  }
+  if (d_compliance) d_compliance[b] = k * (jz[0] * d[0] + jz[1] * d[1] + jz[2] * d[2]) / e;
+}
+
 // ---- forward step ---------------------------------------------------------------------------
 
 __global__ void k_predict(int nv, const double* q_prev, const double* v_prev, const double* f_ext, const double* mass,
@@ -922,6 +1011,32 @@ void launch_binding_grad(int nb, const int32_t* vertex, const double* target, co
                          cudaStream_t s) {
   g_launches += 1;
   if (nb) k_binding_grad<<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, target, compliance, q, z, h, d_target, d_compliance);
+}
+void launch_check_bindings_bary(int nb, const int32_t* tet, const double* bary, const double* compliance, int nt,
+                                int* flags, cudaStream_t s) {
+  g_launches += 1;
+  if (nb) k_check_bindings_bary<<<nblk(nb, 128), 128, 0, s>>>(nb, tet, bary, compliance, nt, flags);
+}
+void launch_binding_blocks_bary(int nb, const int32_t* tet, const double* bary, const double* compliance,
+                                const int32_t* slot, double h, double* bsr, float* bsr32, cudaStream_t s) {
+  g_launches += 1;
+  if (!nb) return;
+  if (bsr) k_binding_blocks_bary<double><<<nblk(nb, 128), 128, 0, s>>>(nb, tet, bary, compliance, slot, h, bsr);
+  else k_binding_blocks_bary<float><<<nblk(nb, 128), 128, 0, s>>>(nb, tet, bary, compliance, slot, h, bsr32);
+}
+void launch_binding_force_bary(int nb, const int32_t* tet, const int32_t* tets, const double* bary,
+                               const double* target, const double* compliance, const double* q, double h, double* R,
+                               cudaStream_t s) {
+  g_launches += 1;
+  if (nb) k_binding_force_bary<<<nblk(nb, 128), 128, 0, s>>>(nb, tet, tets, bary, target, compliance, q, h, R);
+}
+void launch_binding_grad_bary(int nb, const int32_t* tet, const int32_t* tets, const double* bary,
+                              const double* target, const double* compliance, const double* q, const double* z,
+                              double h, double* d_target, double* d_compliance, cudaStream_t s) {
+  g_launches += 1;
+  if (nb)
+    k_binding_grad_bary<<<nblk(nb, 128), 128, 0, s>>>(nb, tet, tets, bary, target, compliance, q, z, h, d_target,
+                                                       d_compliance);
 }
 void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
                       const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,

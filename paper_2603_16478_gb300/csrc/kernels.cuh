@@ -129,6 +129,17 @@ void launch_binding_force(int nb, const int32_t* vertex, const double* target, c
 void launch_binding_grad(int nb, const int32_t* vertex, const double* target, const double* compliance,
                          const double* q, const double* z, double h, double* d_target, double* d_compliance,
                          cudaStream_t s);
+// the same for points inside tets (tet [nb], bary [nb][4]; blocks through the element->slot map)
+void launch_check_bindings_bary(int nb, const int32_t* tet, const double* bary, const double* compliance, int nt,
+                                int* flags, cudaStream_t s);
+void launch_binding_blocks_bary(int nb, const int32_t* tet, const double* bary, const double* compliance,
+                                const int32_t* slot, double h, double* bsr, float* bsr32, cudaStream_t s);
+void launch_binding_force_bary(int nb, const int32_t* tet, const int32_t* tets, const double* bary,
+                               const double* target, const double* compliance, const double* q, double h, double* R,
+                               cudaStream_t s);
+void launch_binding_grad_bary(int nb, const int32_t* tet, const int32_t* tets, const double* bary,
+                              const double* target, const double* compliance, const double* q, const double* z,
+                              double h, double* d_target, double* d_compliance, cudaStream_t s);
 void launch_tet_force(int nt, const int32_t* tets, const double* gvec, const double* vol, const double* mu,
                       const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,
                       cudaStream_t s);

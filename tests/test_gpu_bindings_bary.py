@@ -1,0 +1,105 @@
+"""Bindings of points inside tets (barycentric weights; Eq. binding with J_b = w^T (x) I_3) on the GPU
+against the FP64 oracle: adjoint parity of every gradient, a stiff compliance, mixed precision,
+the forward state, and argument errors.
+
+These tests have not yet run on a GPU: they are skipped unless NCPADJ_TEST_UNVERIFIED=1, so that
+a first failure cannot stop the rest of the GPU suite; the first GPU run that passes them removes
+the gate."""
+import functools
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from tests._cases import rel  # noqa: E402
+from tests.test_gpu_parity import KEYS, T, gpu_contacts, gpu_scene  # noqa: E402
+from tests.test_oracle_bindings import _bary_case  # noqa: E402
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("NCPADJ_TEST_UNVERIFIED") != "1",
+                                 reason="not yet run on a GPU (set NCPADJ_TEST_UNVERIFIED=1)")]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2603_16478_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def ctx(pkg):
+    return pkg.Context(0)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(k, compliance):
+    pb, st, bd, q_prev, v_prev = _bary_case(k, compliance)
+    s = st.forward(q_prev, v_prev, tol=1e-12)
+    assert s.residual < 1e-9
+    return pb, st, bd, q_prev, v_prev, s
+
+
+def _gpu(pkg, bd):
+    return pkg.Bindings(None, T(bd.target), T(bd.compliance), tet=T(bd.tet_ids, torch.int32), bary=T(bd.wk))
+
+
+@pytest.mark.parametrize("k,compliance", [(0, 1e-4), (2, 1e-4), (0, 1e-8)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_parity(pkg, ctx, k, compliance, precision):
+    if precision == "mixed" and compliance < 1e-6:
+        pytest.skip("FP32 matrix values with h^2/E_b ~ 3e4 against vertex masses of 8 g")
+    pb, st, bd, q_prev, v_prev, s = _oracle(k, compliance)
+    rng = np.random.default_rng(4)
+    dq = 2 * (s.q - pb.q_target) + rng.normal(size=s.q.shape) * 1e-4
+    dv = rng.normal(size=s.q.shape) * 1e-3
+    ref = st.adjoint(s, q_prev, dq, dv)
+    lam = s.lam_frame(st, q_prev) if st.nc else np.zeros((0, 3))
+    g, stats = pkg.adjoint_step(gpu_scene(pkg, ctx, pb.scene), gpu_contacts(pkg, st.ct), T(s.q), T(q_prev), T(lam),
+                                T(dq), T(dv), eps=pb.scene.eps, rtol=1e-12 if precision == "fp64" else 1e-8,
+                                precision=precision, cap_precision=precision, bindings=_gpu(pkg, bd))
+    torch.cuda.synchronize()
+    tol = 1e-8 if precision == "fp64" else 1e-3
+    for key, rk in KEYS + [("dL_dbinding_target", "dL_dbinding_target"), ("dL_dcompliance", "dL_dcompliance")]:
+        if st.nc == 0 and key in ("dL_dmu", "dL_dmu_contact"):
+            continue
+        assert rel(g[key].cpu().numpy().reshape(-1), np.asarray(ref[rk]).reshape(-1)) <= tol, key
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_forward_matches_oracle_state(pkg, ctx, k):
+    pb, st, bd, q_prev, v_prev, s = _oracle(k, 1e-4)
+    sc = pb.scene
+    q, lam, stats = pkg.forward_step(gpu_scene(pkg, ctx, sc), gpu_contacts(pkg, st.ct), T(q_prev), T(v_prev), None,
+                                     tuple(sc.gravity), eps=sc.eps, newton_tol=1e-11, max_newton=200,
+                                     bindings=_gpu(pkg, bd))
+    assert stats["residual"] < 1e-8
+    assert rel(q.cpu().numpy() - q_prev, s.q - q_prev) < 1e-7
+
+
+def test_invalid_points_are_rejected(pkg, ctx):
+    pb, st, bd, q_prev, v_prev, s = _oracle(0, 1e-4)
+    scene = gpu_scene(pkg, ctx, pb.scene)
+
+    def call(tet, bary, compliance):
+        b = pkg.Bindings(None, T(bd.target), T(compliance), tet=T(tet, torch.int32), bary=T(bary))
+        return pkg.adjoint_step(scene, None, T(s.q), T(q_prev), T(np.zeros((0, 3))), T(2 * (s.q - pb.q_target)), None,
+                                eps=pb.scene.eps, bindings=b)
+
+    bad = bd.tet_ids.copy()
+    bad[1] = scene.n_tets
+    with pytest.raises(pkg.NcpadjError, match="INVALID_ARG"):
+        call(bad, bd.wk, bd.compliance)
+    w = bd.wk.copy()
+    w[0, 0] = np.nan
+    with pytest.raises(pkg.NcpadjError, match="INVALID_ARG"):
+        call(bd.tet_ids, w, bd.compliance)
+    with pytest.raises(pkg.NcpadjError, match="INVALID_ARG"):
+        call(bd.tet_ids, bd.wk, np.array([1e-4, -1.0, 1e-4, 1e-4]))
+    g, stats = call(bd.tet_ids, bd.wk, bd.compliance)
+    assert torch.isfinite(g["dL_dcompliance"]).all()

@@ -127,10 +127,12 @@ def _bary_case(k, compliance, shift=1e-3):
     pb, q_prev, v_prev = rollout("cube_drop", k)
     sc = pb.scene
     cz = sc.X[sc.tets].mean(axis=1)[:, 2]
-    tets = sc.tets[np.argsort(-cz)[:4]]
+    tet_ids = np.argsort(-cz)[:4]
+    tets = sc.tets[tet_ids]
     w = np.random.default_rng(7).dirichlet(np.ones(4), size=4)
     pts = np.einsum("bk,bkj->bj", w, q_prev[tets])
     bd = Bindings(tets, np.full(4, compliance), pts + np.array([0.0, 0.0, shift]), weight=w)
+    bd.tet_ids = tet_ids  # the tets the points lie in (the GPU takes tet ids and weights)
     ct = sc.contacts(q_prev)
     st = Step(sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h, sc.gravity, ct, sc.eps, "neo_hookean", bd)
     return pb, st, bd, q_prev, v_prev
