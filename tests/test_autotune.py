@@ -59,3 +59,56 @@ def test_cache_round_trip(tmp_path):
     c.put("k", at.Choice({"precision": "mixed", "restart": 64}, 6.2, 5.9e-5))
     again = at.Cache(path)
     assert again.get("k") == {"precision": "mixed", "restart": 64}
+
+
+def test_tune_adjoint_glue_with_fake_device(monkeypatch, tmp_path):
+    """tune_adjoint end to end with a fake adjoint call and fake CUDA events: the FP64 reference,
+    per-candidate timing (median of the repeats), the accuracy gate, the choice and the cache."""
+    import contextlib
+    import types
+
+    import torch
+
+    from paper_2603_16478_gb300 import binding
+
+    clock = {"t": 0.0, "calls": 0}
+    base = {("fp64", "fp64"): 10.0, ("mixed", "fp64"): 8.0, ("mixed", "mixed"): 5.0}
+    err = {("fp64", "fp64"): 0.0, ("mixed", "fp64"): 5e-5, ("mixed", "mixed"): 2e-3}
+
+    def fake_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv, *, precision, cap_precision, restart,
+                     cap_block, **kw):
+        clock["calls"] += 1
+        clock["t"] += base[(precision, cap_precision)] - (0.5 if restart == 128 else 0.0)
+        e = err[(precision, cap_precision)]
+        g = {"dL_dq_prev": torch.ones(4, 3, dtype=torch.float64) * (1 + e), "dL_dE": torch.ones(6, dtype=torch.float64)}
+        return g, {"iterations": 30}
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = clock["t"]
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(binding, "adjoint_step", fake_adjoint)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda dev=None: types.SimpleNamespace(cuda_stream=0))
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda dev=None: None)
+    scene = types.SimpleNamespace(n_verts=4961, n_tets=20000, info=lambda: {"n_scenes": 1})
+    contacts = types.SimpleNamespace(n=451)
+    q = torch.zeros(4, 3, dtype=torch.float64)
+    cache = at.Cache(str(tmp_path / "tune.json"))
+    ch = at.tune_adjoint(scene, contacts, q, q, q, q, None, repeats=3, cache=cache)
+    assert ch.options == {"precision": "mixed", "cap_precision": "fp64", "restart": 128, "cap_block": 0}
+    assert ch.ms == 7.5 and abs(ch.rel_err - 5e-5) < 1e-12
+    assert len(ch.trials) == 9 and clock["calls"] == 1 + 9 * (1 + 3)  # reference, then warm-up + repeats each
+    calls = clock["calls"]
+    again = at.tune_adjoint(scene, contacts, q, q, q, q, None, cache=at.Cache(str(tmp_path / "tune.json")))
+    assert again.options == ch.options and clock["calls"] == calls  # from the cache, nothing run
