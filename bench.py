@@ -114,6 +114,58 @@ def oracle_times(steps, warmup, state=None):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def models_leg(pkg, torch, dev, scene, n_verts, q_adj, timed):
+    """The co-rotational and ARAP adjoints, then 40 stiff bindings on Neo-Hookean tets, on the
+    bench's scene at its state.  ``timed(**kw) -> (total ms, stats list)`` times the headline
+    variant.  Failures are reported in the result, and the scene is left Neo-Hookean."""
+    res = {}
+    try:
+        for mname in ("corotational", "arap"):
+            scene.set_model(mname)
+            tm, sm = timed()
+            res[mname] = {"gradients_per_s": len(sm) / (tm / 1e3),
+                          "krylov_iterations": statistics.median(x["iterations"] for x in sm),
+                          "ms_assemble": statistics.mean(x["ms_assemble"] for x in sm)}
+        scene.set_model("neo_hookean")
+        nbind = 40  # vertices spread over the mesh, held where they are by stiff springs
+        bv = torch.arange(0, n_verts, max(1, n_verts // nbind), device=dev, dtype=torch.int32)[:nbind].contiguous()
+        nbind = int(bv.shape[0])
+        bd = pkg.Bindings(bv, q_adj[bv.long()].contiguous(), torch.full((nbind,), 1e-6, dtype=torch.float64, device=dev))
+        tm, sm = timed(bindings=bd)
+        res["bindings"] = {"n": nbind, "compliance": 1e-6, "gradients_per_s": len(sm) / (tm / 1e3),
+                           "krylov_iterations": statistics.median(x["iterations"] for x in sm)}
+    except Exception as e:  # noqa: BLE001
+        res["error"] = str(e)[:300]
+    try:
+        scene.set_model("neo_hookean")
+    except Exception as e:  # noqa: BLE001
+        res["error"] = res.get("error", "") + f"; reset: {str(e)[:100]}"
+    return res
+
+
+def cpu_baseline_leg(arrays):
+    """The oracle at the bench's state: ``arrays`` holds q, q_prev, dL_dq, dL_dv and the GPU
+    gradients as '<variant>/<key>'.  Falls back to the oracle's own start point if that state
+    cannot be used.  Returns (the cpu_baseline object, the relative errors vs the oracle or None)."""
+    import tempfile
+    d, err, where = None, None, "the bench's GPU state (3 forward steps from rest, same seeds)"
+    try:
+        with tempfile.TemporaryDirectory() as tdir:
+            path = os.path.join(tdir, "state.npz")
+            np.savez(path, **arrays)
+            d = oracle_times(3, 1, state=path)
+        err = d.get("rel_err_vs_oracle")
+    except Exception:  # noqa: BLE001 -- fall back to the oracle's own start point
+        where = "the oracle's start point of step 1"
+        try:
+            d = oracle_times(3, 1)
+        except Exception as e:  # noqa: BLE001
+            return {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}, None
+    return ({"value": len(d["seconds"]) / sum(d["seconds"]), "unit": "gradients/s", "cores": d["threads"],
+             "kind": "oracle", "sample": f"{len(d['seconds'])} oracle adjoints of the beam (assembly + direct sparse "
+             f"LU + contractions) at {where}, after 1 warm-up"}, err)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -590,30 +642,8 @@ def main():
     # (one rank only: a failure here must not leave other ranks waiting in a collective)
     models_res = None
     if world == 1 and not args.no_models:
-        models_res = {}
-        try:
-            for mname in ("corotational", "arap"):
-                scene.set_model(mname)
-                tm, sm = timed(*variants[head], max(3, args.steps // 4))
-                models_res[mname] = {"gradients_per_s": len(sm) / (tm / 1e3),
-                                     "krylov_iterations": statistics.median(x["iterations"] for x in sm),
-                                     "ms_assemble": statistics.mean(x["ms_assemble"] for x in sm)}
-            scene.set_model("neo_hookean")
-            nbind = 40  # vertices spread over the beam, held where they are by stiff springs
-            bv = torch.arange(0, sc.n_verts, max(1, sc.n_verts // nbind), device=dev,
-                              dtype=torch.int32)[:nbind].contiguous()
-            nbind = int(bv.shape[0])
-            bd = pkg.Bindings(bv, q_adj[bv.long()].contiguous(),
-                              torch.full((nbind,), 1e-6, dtype=torch.float64, device=dev))
-            tm, sm = timed(*variants[head], max(3, args.steps // 4), bindings=bd)
-            models_res["bindings"] = {"n": nbind, "compliance": 1e-6, "gradients_per_s": len(sm) / (tm / 1e3),
-                                      "krylov_iterations": statistics.median(x["iterations"] for x in sm)}
-        except Exception as e:  # noqa: BLE001
-            models_res["error"] = str(e)[:300]
-        try:
-            scene.set_model("neo_hookean")
-        except Exception as e:  # noqa: BLE001
-            models_res["error"] = models_res.get("error", "") + f"; reset: {str(e)[:100]}"
+        models_res = models_leg(pkg, torch, dev, scene, sc.n_verts, q_adj,
+                                lambda **kw: timed(*variants[head], max(3, args.steps // 4), **kw))
 
     # ---- the batched workload ----
     batch_res = None
@@ -640,33 +670,14 @@ def main():
     # ---- CPU baseline: the oracle, one thread, bounded sample ----
     # The oracle runs at the bench's own state (the GPU forward's), on the same seeds, so the same
     # runs also give each GPU variant's gradient error against the oracle.
-    cpu = None
-    err_oracle = None
+    cpu, err_oracle = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        import tempfile
-        d = None
-        where = "the bench's GPU state (3 forward steps from rest, same seeds)"
-        try:
-            with tempfile.TemporaryDirectory() as tdir:
-                path = os.path.join(tdir, "state.npz")
-                arrays = {"q": q_adj.cpu().numpy(), "q_prev": q_prev_adj.cpu().numpy(), "dL_dq": dL_dq.cpu().numpy(),
-                          "dL_dv": dL_dv.cpu().numpy()}
-                for vname, gv in grads_by.items():
-                    for k, v in gv.items():
-                        arrays[f"{vname}/{k}"] = v.cpu().numpy()
-                np.savez(path, **arrays)
-                d = oracle_times(3, 1, state=path)
-            err_oracle = d.get("rel_err_vs_oracle")
-        except Exception:  # noqa: BLE001 -- fall back to the oracle's own start point
-            where = "the oracle's start point of step 1"
-            try:
-                d = oracle_times(3, 1)
-            except Exception as e:  # noqa: BLE001
-                cpu = {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
-        if d is not None:
-            cpu = {"value": len(d["seconds"]) / sum(d["seconds"]), "unit": "gradients/s", "cores": d["threads"],
-                   "kind": "oracle", "sample": f"{len(d['seconds'])} oracle adjoints of the beam (assembly + direct "
-                   f"sparse LU + contractions) at {where}, after 1 warm-up"}
+        arrays = {"q": q_adj.cpu().numpy(), "q_prev": q_prev_adj.cpu().numpy(), "dL_dq": dL_dq.cpu().numpy(),
+                  "dL_dv": dL_dv.cpu().numpy()}
+        for vname, gv in grads_by.items():
+            for k, v in gv.items():
+                arrays[f"{vname}/{k}"] = v.cpu().numpy()
+        cpu, err_oracle = cpu_baseline_leg(arrays)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
