@@ -93,3 +93,17 @@ def test_cpu_baseline_reports_a_double_failure(monkeypatch):
     monkeypatch.setattr(bench, "oracle_times", fake)
     cpu, err = bench.cpu_baseline_leg(_arrays())
     assert cpu["value"] is None and "failed" in cpu["sample"] and err is None
+
+
+def test_clock_sampler_parses_nvidia_smi_lines():
+    """Median SM clock, maximum clock and the throttle reasons seen active in any sample."""
+    cs = bench.ClockSampler(0)
+    cs.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0, kill=lambda: None)
+    cs.lines = ["0, 2070, 2070, 700.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "0, 1980, 2070, 1399.0, 0x4, Not Active, Not Active, Not Active, Active",
+                "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbage line", "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    out = cs.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    none = bench.ClockSampler(0)
+    assert none.stop()["reasons"] == ["nvidia-smi unavailable"]
