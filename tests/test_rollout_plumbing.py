@@ -114,3 +114,27 @@ def test_per_step_targets_need_one_slice_per_step(sim):
         R.rollout(sim, torch.zeros(NV, 3, dtype=torch.float64), torch.zeros(NV, 3, dtype=torch.float64), E, nu, mu, 3,
                   binding_targets=torch.zeros(2, len(BV), 3, dtype=torch.float64),
                   binding_compliance=torch.ones(len(BV), dtype=torch.float64))
+
+
+def test_simulator_contact_detection_matches_the_input_generator():
+    """Simulator.contacts (torch, used by rollouts) selects the same vertices with the same frames,
+    offsets and per-region friction as synth.detect_contacts for planes without region grids."""
+    import numpy as np
+
+    import synth
+    pb = synth.beam_incline(nx=8, ny=3, nz=3)
+    sc = pb.scene
+    q = torch.as_tensor(pb.q0)
+    planes = [R.PlaneCollider(p.normal.tolist(), p.offset, p.t1.tolist(), p.t2.tolist(), region=i)
+              for i, p in enumerate(sc.planes)]
+    ref_planes = [synth.Plane(p.normal, p.offset, mu) for p, mu in zip(sc.planes, (0.3, 0.7))]
+    for rp, p in zip(ref_planes, sc.planes):
+        rp.t1, rp.t2 = p.t1, p.t2
+    sim = R.Simulator(types.SimpleNamespace(h=sc.h), planes, margin=2e-3, n_regions=len(planes))
+    mu_region = torch.tensor([0.3, 0.7][:len(planes)], dtype=torch.float64)
+    got = sim.contacts(q, mu_region)
+    ref = synth.detect_contacts(pb.q0, ref_planes, 2e-3)
+    assert got.n == ref.n > 0
+    assert np.array_equal(got.vertex.numpy(), ref.vertex)
+    assert np.allclose(got.frame.numpy(), ref.frame) and np.allclose(got.d_n.numpy(), ref.d_n)
+    assert np.array_equal(got.region.numpy(), ref.region) and np.allclose(got.mu.numpy(), ref.mu)
