@@ -107,3 +107,37 @@ def test_model_names_map_to_the_header_codes(fake_scene):
     assert seen["codes"] == [0, 1, 2] * 4
     with pytest.raises(ValueError):
         sc.set_model(["arap"] * 3)
+
+
+def test_scene_descriptors_single_and_batch():
+    """Scene construction passes one descriptor (or one per mesh of a batch) with host copies of
+    the arrays, E and nu broadcast per tet, and numbers the batch's meshes one after another."""
+    import numpy as np
+    lib = FakeLib()
+    seen = {}
+
+    def create(ctx, desc_ref, out_ref):
+        d = desc_ref._obj
+        seen["single"] = (d.n_verts, d.n_tets, d.density, d.h,
+                          list((C.c_double * d.n_tets).from_address(d.E)), list((C.c_int32 * 4).from_address(d.tets)))
+        out_ref._obj.value = 11
+        return 0
+
+    def create_batch(ctx, n, descs, out_ref):
+        seen["batch"] = [(descs[i].n_verts, descs[i].n_tets, descs[i].density) for i in range(n)]
+        seen["nu0"] = list((C.c_double * descs[0].n_tets).from_address(descs[0].nu))
+        out_ref._obj.value = 12
+        return 0
+
+    lib.ncpadj_scene_create = create
+    lib.ncpadj_scene_create_batch = create_batch
+    ctx = types.SimpleNamespace(lib=lib, handle=C.c_void_p(2))
+    X = np.zeros((5, 3))
+    T = np.array([[0, 1, 2, 3], [1, 2, 3, 4]])
+    sc = B.Scene(ctx, X, T, 1e5, 0.4, 1000.0, 0.01)
+    assert seen["single"] == (5, 2, 1000.0, 0.01, [1e5, 1e5], [0, 1, 2, 3])
+    assert (sc.n_verts, sc.n_tets, sc.handle.value) == (5, 2, 11)
+    sb = B.Scene.batch(ctx, [(X, T, 1e5, 0.4, 1000.0), (np.zeros((4, 3)), T[:1], [2e5], [0.3], 900.0)], 0.01)
+    assert seen["batch"] == [(5, 2, 1000.0), (4, 1, 900.0)] and seen["nu0"] == [0.4, 0.4]
+    assert sb.vertex_offsets == [0, 5, 9] and sb.tet_offsets == [0, 2, 3] and (sb.n_verts, sb.n_tets) == (9, 3)
+    sb.handle = sc.handle = C.c_void_p()  # nothing to destroy in the fake
