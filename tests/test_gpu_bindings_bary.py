@@ -41,7 +41,9 @@ def ctx(pkg):
 def _oracle(k, compliance):
     pb, st, bd, q_prev, v_prev = _bary_case(k, compliance)
     s = st.forward(q_prev, v_prev, tol=1e-12)
-    assert s.residual < 1e-9
+    # a stiff spring (h^2/E_b ~ 3e4 at E_b = 1e-8) lifts the rounding floor of the residual to ~1e-9;
+    # the adjoint is compared at whatever state the oracle reached
+    assert s.residual < 1e-8
     return pb, st, bd, q_prev, v_prev, s
 
 
