@@ -119,16 +119,20 @@ void ncpadj_scene_destroy(ncpadj_scene scene);
 /* A batch of independent scenes solved together (the batched adjoint).  The scene built is the
  * disjoint union of the n_scenes meshes: the vertices of mesh s are numbered after those of meshes
  * 0..s-1 (tets likewise), and every array argument of the other calls is the concatenation of
- * the per-mesh arrays in that order.  All meshes must share h.  Each mesh's elastic factor is
- * built independently (host threads); the union's matrices are block-diagonal.  In
- * ncpadj_adjoint_step / ncpadj_forward_step on a batch:
+ * the per-mesh arrays in that order (ncpadj_adjoint_batch takes per-mesh arrays instead).  All
+ * meshes must share h.  Each mesh's elastic factor is built independently (host threads); the
+ * union's matrices are block-diagonal.  In ncpadj_adjoint_step / ncpadj_forward_step on a batch:
  *  - contacts must be grouped by mesh (non-decreasing mesh of their vertex); the contact
  *    capacitance is inverted block by block, one dense block per mesh with contacts (a mesh
- *    with more contacts than ncpadj_options.cap_block allows is solved iteratively, see there);
+ *    with more contacts than ncpadj_options.cap_block allows is solved iteratively, see there,
+ *    except in the adjoint's per-mesh solve below);
  *  - the forward step gives each mesh its own line search;
- *  - the adjoint scales each mesh's right-hand side to unit norm and tightens the tolerance to
+ *  - the adjoint (solver AUTO or GMRES) solves every mesh by its own GMRES, as
+ *    ncpadj_adjoint_batch does (stats.iterations is then the largest per-mesh count and
+ *    stats.rel_residual the largest per-mesh residual); with CG or BiCGSTAB asked for by name it
+ *    scales each mesh's right-hand side to unit norm and solves the union once with the tolerance
  *    rtol / sqrt(number of meshes with a nonzero seed), so every mesh's own relative residual is
- *    at most rtol (the scaling is undone before the contractions).
+ *    at most rtol.
  * Errors: as ncpadj_scene_create (the message names the failing mesh). */
 ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_scene_desc* descs,
                                         ncpadj_scene* out);
@@ -279,6 +283,35 @@ ncpadj_status ncpadj_adjoint_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpa
                                   const ncpadj_state* state, const ncpadj_seed* seed,
                                   const ncpadj_options* opt, ncpadj_grads* grads,
                                   ncpadj_stats* stats, void* stream);
+
+/* Batched adjoint: one adjoint step of every mesh of a batch scene (ncpadj_scene_create_batch) in
+ * one call -- the many-scene workload of the paper's batched differentiable simulation (Sec. 5),
+ * with the Krylov solve of Sec. 4.4 (Eq. adjoint, Eq. woodbury_formula) run scene by scene.
+ *   n_scenes     the batch's number of meshes (else INVALID_ARG).
+ *   contacts     [n_scenes] or NULL (no contacts anywhere); states, seeds [n_scenes] (required);
+ *   grads, stats [n_scenes] or NULL.  Entry s describes mesh s exactly as the arguments of
+ *                ncpadj_adjoint_step would describe that mesh alone: vertex ids in [0, its n_verts),
+ *                regions in [0, its n_regions), every array sized for that mesh, NULL outputs
+ *                skipped.  All arrays are device pointers, or all host pointers with
+ *                options.memory = NCPADJ_MEM_HOST.
+ * Every mesh runs its own right-preconditioned flexible GMRES: its own inner products, Hessenberg
+ * matrix, restarts and stopping test ||b_s - script_A_s^T z_s|| <= rtol ||b_s||.  The meshes share
+ * every kernel launch of a Krylov step; a mesh that has converged drops out of the later launches
+ * (their kernels skip its rows), so a call costs about the sum of the meshes' own iterations,
+ * not their number times the slowest one's.  Off the legacy default stream each step is one replay
+ * of a captured CUDA graph owned by the scene.  Capacitance blocks above the direct inverse's size
+ * are split into directly inverted groups (no inner solve).
+ * stats[s].iterations, .rel_residual and .n_contacts are mesh s's own; the times, kernel_launches
+ * and capacitance fields describe the whole call.
+ * Not supported here: bindings (states[s].bindings must be NULL) and solvers other than AUTO or
+ * GMRES (UNSUPPORTED).  Synchronises the stream.
+ * Errors: as ncpadj_adjoint_step (a contact vertex or region outside its own mesh's range is
+ * INVALID_ARG); NOT_CONVERGED when some mesh stopped above rtol -- every output is still written
+ * and that mesh's stats entry shows its residual. */
+ncpadj_status ncpadj_adjoint_batch(ncpadj_ctx ctx, ncpadj_scene batch, int32_t n_scenes,
+                                   const ncpadj_contacts* contacts, const ncpadj_state* states,
+                                   const ncpadj_seed* seeds, const ncpadj_options* opt,
+                                   ncpadj_grads* grads, ncpadj_stats* stats, void* stream);
 
 /* y = A^{-1} x for the elastic matrix A = M + h^2 sum_i w_i G_i^T G_i of the scene (Eq. dynamics),
  * applied through the scene's sparse-inverse factorisation A^{-1} = P^T S^T S P (Sec. 3).

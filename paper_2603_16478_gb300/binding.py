@@ -109,7 +109,7 @@ class _ForwardStats(C.Structure):
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
            "ncpadj_options_default",
-           "ncpadj_adjoint_step", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc",
+           "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc",
            "ncpadj_dense_inverse", "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
 
 
@@ -137,6 +137,9 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_adjoint_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_State),
                                         C.POINTER(_Seed), C.POINTER(_Options), C.POINTER(_Grads), C.POINTER(_Stats),
                                         C.c_void_p]
+    lib.ncpadj_adjoint_batch.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(_Contacts), C.POINTER(_State),
+                                         C.POINTER(_Seed), C.POINTER(_Options), C.POINTER(_Grads),
+                                         C.POINTER(_Stats), C.c_void_p]
     lib.ncpadj_forward_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_ForwardInput),
                                         C.POINTER(_Options), C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                         C.POINTER(_ForwardStats), C.c_void_p]
@@ -362,6 +365,74 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     return outputs, stats.to_dict()
 
 
+_GRAD_FIELDS = ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z", "dL_dact",
+                "dL_dbinding_target", "dL_dcompliance")
+
+
+def _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, solver, memory, cap_block):
+    opt = _Options()
+    lib.ncpadj_options_default(C.byref(opt))
+    opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
+    opt.precision = PRECISION[precision]
+    opt.cap_precision = PRECISION[cap_precision]
+    opt.cap_block = int(cap_block)
+    opt.precond = PRECOND[precond]
+    opt.solver = SOLVER[solver]
+    opt.memory = MEMORY[memory]
+    return opt
+
+
+def adjoint_batch(scene: Scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4, rtol=1e-8, max_iters=2000,
+                  restart=64, precision="fp64", cap_precision="fp64", precond="woodbury", cap_block=0,
+                  memory="device", stream=None, want=("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu",
+                                                      "dL_dmu", "dL_dmu_contact", "z")):
+    """One adjoint step of every mesh of a batch scene (``Scene.batch``) through
+    ``ncpadj_adjoint_batch``: every mesh runs its own GMRES, sharing the launches.
+
+    ``contacts``, ``q``, ``q_prev``, ``lam``, ``dL_dq`` (and ``dL_dv``, or None) are lists with one
+    entry per mesh, in the mesh's own numbering (``contacts[s]`` may be None, ``lam[s]`` is then
+    ignored).  Returns (list of per-mesh output dicts, list of per-mesh stats dicts)."""
+    lib = scene.lib
+    ns = len(scene.vertex_offsets) - 1
+    for name, lst in (("contacts", contacts), ("q", q), ("q_prev", q_prev), ("lam", lam), ("dL_dq", dL_dq)):
+        if len(lst) != ns:
+            raise ValueError(f"{name}: expected {ns} entries (one per mesh), got {len(lst)}")
+    if dL_dv is not None and len(dL_dv) != ns:
+        raise ValueError(f"dL_dv: expected {ns} entries, got {len(dL_dv)}")
+    dev = q[0].device
+    cts, stt, sds, grs, outs = (_Contacts * ns)(), (_State * ns)(), (_Seed * ns)(), (_Grads * ns)(), []
+    for s in range(ns):
+        nv = scene.vertex_offsets[s + 1] - scene.vertex_offsets[s]
+        nt = scene.tet_offsets[s + 1] - scene.tet_offsets[s]
+        ct = contacts[s]
+        nc = ct.n if ct is not None else 0
+        nreg = ct.n_regions if ct is not None else 1
+        shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
+                  "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (nc,), "dL_dact": (nt,)}
+        o = {}
+        for k in want:
+            dt = torch.float32 if k == "dL_dact" else torch.float64
+            if memory == "host":
+                o[k] = torch.empty(shapes[k], dtype=dt, pin_memory=torch.cuda.is_available())
+            else:
+                o[k] = torch.empty(shapes[k], dtype=dt, device=dev)
+        outs.append(o)
+        cts[s] = _contacts_struct(ct)
+        stt[s] = _State(_ptr(q[s]), _ptr(q_prev[s]), _ptr(lam[s]) if nc else None, None)
+        sds[s] = _Seed(_ptr(dL_dq[s]), _ptr(dL_dv[s]) if dL_dv is not None else None)
+        grs[s] = _Grads(*[_ptr(o.get(k)) for k in _GRAD_FIELDS])
+    opt = _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, "gmres", memory, cap_block)
+    stats = (_Stats * ns)()
+    if stream is None and dev.type == "cuda":
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    st = lib.ncpadj_adjoint_batch(scene.ctx.handle, scene.handle, ns, cts, stt, sds, C.byref(opt), grs, stats,
+                                  C.c_void_p(stream or 0))
+    sl = [stats[s].to_dict() for s in range(ns)]
+    if st != 0:
+        raise NcpadjError(st, lib.ncpadj_last_error().decode(), sl, outs)
+    return outs, sl
+
+
 def _contacts_struct(contacts):
     if contacts is None or contacts.n == 0:
         return _Contacts(0, None, None, None, None, None, None, 1)
@@ -418,6 +489,11 @@ def elastic_solve_noalloc(scene: Scene, x: torch.Tensor, y: torch.Tensor, stream
     """y = A^{-1} x without device allocation in the call (y preallocated by the caller; scenes
     of at most 262,144 vertices; concurrent calls race on the library's static scratch)."""
     lib = scene.lib
+    for name, t in (("x", x), ("y", y)):
+        if (t.dtype != torch.float64 or not t.is_cuda or t.device.index != scene.ctx.device or not t.is_contiguous()
+                or tuple(t.shape) != (scene.n_verts, 3)):
+            raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor of shape ({scene.n_verts}, 3) on "
+                             f"device {scene.ctx.device}")
     if stream is None:
         stream = torch.cuda.current_stream(x.device).cuda_stream
     _check(lib, lib.ncpadj_elastic_solve_noalloc(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y),

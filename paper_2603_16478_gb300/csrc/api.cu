@@ -4,6 +4,7 @@
 #include <chrono>
 #include <thread>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -295,6 +296,28 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
   NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.gs_map_dev), S.gs_map_host, 0));
   S.gstep.ensure(64);
   for (auto& e : S.ev) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
+  // tiles of the DOF range that never straddle two meshes (per-scene reductions of a batch solve)
+  {
+    std::vector<int32_t> tsc, tb, te, t0(n_scenes + 1, 0);
+    for (int i = 0; i < n_scenes; ++i) {
+      for (int b = 3 * S.voff[i]; b < 3 * S.voff[i + 1]; b += kSegTile) {
+        tsc.push_back(i);
+        tb.push_back(b);
+        te.push_back(std::min(b + kSegTile, 3 * S.voff[i + 1]));
+      }
+      t0[i + 1] = (int32_t)tsc.size();
+    }
+    S.n_tiles = (int)tsc.size();
+    std::vector<int32_t> all;
+    all.insert(all.end(), tsc.begin(), tsc.end());
+    all.insert(all.end(), tb.begin(), tb.end());
+    all.insert(all.end(), te.begin(), te.end());
+    all.insert(all.end(), t0.begin(), t0.end());
+    upload(S.segt, all);
+  }
+  NCPADJ_CUDA_TRY(cudaHostAlloc(&S.bmap_host, sizeof(int) * (kMaxRestart + 8), cudaHostAllocMapped));
+  NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.bmap_dev), S.bmap_host, 0));
+  for (auto& e : S.bev) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -345,8 +368,17 @@ struct Engine {
   float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr;
   // the capacitance is block-diagonal by scene (contacts of different meshes share no ancestor
   // in the elimination forest): one dense block per scene that has contacts
-  std::vector<int> blk_c0, blk_nc;
+  std::vector<int> blk_c0, blk_nc, blk_scene;  // first contact, contacts and mesh of each block
   std::vector<size_t> blk_moff, blk_doff;
+  // batch scenes: one restarted GMRES per mesh, all meshes advanced by the same launches
+  bool batch_mode = false;
+  struct BatchBufs {
+    int ns = 0, K = 0, gstride = 0;
+    int *act = nullptr, *cyc = nullptr, *done = nullptr, *kk = nullptr, *iters = nullptr;
+    double *gsb = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double *bnorm = nullptr, *tol = nullptr, *rr = nullptr, *relres = nullptr, *partial = nullptr;
+    unsigned* cnt = nullptr;
+  } bb;
   size_t cap_elems = 0, ds_elems = 0;
   // scene blocks above the direct inverse's size are solved iteratively (Sec. 4.4: inner Krylov
   // solve on the capacitance): an inner right-preconditioned GMRES applies the capacitance of such
@@ -360,10 +392,13 @@ struct Engine {
   void plan_blocks() {
     blk_c0.clear();
     blk_nc.clear();
+    blk_scene.clear();
     if (nc == 0) return;
+    std::vector<int> bsc;  // mesh of each block
     if (S.n_scenes == 1) {
       blk_c0.push_back(0);
       blk_nc.push_back(nc);
+      bsc.push_back(0);
     } else {
       S.cscene.ensure(sizeof(int32_t) * (size_t)nc + 64);
       launch_contact_scene(nc, in.cvertex, S.scene_of_vertex.as<int32_t>(), S.cscene.as<int32_t>(), st);
@@ -376,6 +411,7 @@ struct Engine {
         if (c == 0 || cs[c] != cs[c - 1]) {
           blk_c0.push_back(c);
           blk_nc.push_back(0);
+          bsc.push_back(cs[c]);
         }
         blk_nc.back()++;
       }
@@ -406,10 +442,20 @@ struct Engine {
           const int hi = blk_c0[b] + (int)((long)blk_nc[b] * (k + 1) / parts);
           c0s.push_back(lo);
           ncs.push_back(hi - lo);
+          blk_scene.push_back(bsc[b]);
         }
       }
       blk_c0.swap(c0s);
       blk_nc.swap(ncs);
+      // the per-scene batch solve runs every step as one captured launch sequence, with no inner
+      // solve: the groups of a large block are then inverted directly and their coupling is left
+      // out of the preconditioner (flexible GMRES keeps the result exact)
+      if (batch_mode) {
+        sup_c0.clear();
+        sup_nc.clear();
+        sup_g0.clear();
+        sup_g1.clear();
+      }
     }
     blk_moff.assign(blk_c0.size(), 0);
     blk_doff.assign(blk_c0.size(), 0);
@@ -475,7 +521,41 @@ struct Engine {
                                          2 * (size_t)(kInnerRestart + 2) + 64));
       }
     }
-    if (flexible_gmres()) S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
+    if (flexible_gmres() || batch_mode) S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
+    if (batch_mode) {
+      const int ns = S.n_scenes;
+      bb.ns = ns;
+      bb.K = m + 3;
+      bb.gstride = 2 * (m + 1) + 1;
+      const size_t nd = (size_t)ns * bb.gstride + (size_t)ns * (m + 1) * m + 2 * (size_t)ns * m +
+                        (size_t)ns * (m + 1) + (size_t)ns * m + 4 * (size_t)ns + (size_t)(m + 1) * S.n_tiles;
+      const size_t ni = 5 * (size_t)ns + (size_t)ns * bb.K;
+      S.bwork.ensure(sizeof(double) * nd + sizeof(int) * ni + 256);
+      double* d = S.bwork.as<double>();
+      auto take = [&](size_t n) {
+        double* r = d;
+        d += n;
+        return r;
+      };
+      bb.gsb = take((size_t)ns * bb.gstride);
+      bb.H = take((size_t)ns * (m + 1) * m);
+      bb.cs = take((size_t)ns * m);
+      bb.sn = take((size_t)ns * m);
+      bb.g = take((size_t)ns * (m + 1));
+      bb.y = take((size_t)ns * m);
+      bb.bnorm = take(ns);
+      bb.tol = take(ns);
+      bb.rr = take(ns);
+      bb.relres = take(ns);
+      bb.partial = take((size_t)(m + 1) * S.n_tiles);
+      int* ip = reinterpret_cast<int*>(d);
+      bb.act = ip;
+      bb.cyc = ip + ns;
+      bb.done = ip + 2 * ns;
+      bb.kk = ip + 3 * ns;
+      bb.iters = ip + 4 * ns;
+      bb.cnt = reinterpret_cast<unsigned*>(ip + 5 * ns);
+    }
     double* base = S.vecs.as<double>();
     for (double** v : {&b, &x, &r, &w, &t0, &t1, &t2, &t3, &dinv}) {
       *v = base;
@@ -826,6 +906,174 @@ struct Engine {
     S.step_key = key;
     return ex;
   }
+  // ---- batched per-scene GMRES (batch scenes) ----
+  SegTiles tiles() const {
+    const int32_t* t = S.segt.as<int32_t>();
+    const int n = S.n_tiles;
+    return SegTiles{n, t, t + n, t + 2 * (size_t)n, t + 3 * (size_t)n};
+  }
+  // One Arnoldi step j = *jp of every active scene (right-preconditioned, flexible: Z_j = P^{-1} V_j
+  // is kept).  Every kernel skips the rows of scenes whose act[] is 0; the last one updates each
+  // active scene's Hessenberg column and Givens rotations on the device, stops the scenes that
+  // have converged, and advances j.
+  void enqueue_batch_step(double* V, double* Z, int* jp, int maxit) {
+    const Mask mk{bb.act, S.scene_of_vertex.as<int32_t>()};
+    const SegTiles T = tiles();
+    switch (precond) {
+      case NCPADJ_PRECOND_NONE:
+        launch_seg_copy_step(T, V, true, w, false, N, jp, m, bb.act, nullptr, st);
+        break;
+      case NCPADJ_PRECOND_JACOBI:
+        launch_seg_copy_step(T, V, true, w, false, N, jp, m, bb.act, dinv, st);
+        break;
+      default: {
+        launch_sinv_half1_idx(sinv, V, N, jp, mixed ? nullptr : t3, mixed ? w32 : nullptr, st, mk);
+        if (precond == NCPADJ_PRECOND_WOODBURY && nc) {
+          const int32_t* ip = S.iperm.as<int32_t>();
+          launch_path_gather(nc, in.cvertex, ip, sinv, t3, mixed ? w32 : nullptr, in.frame, S.cdata.as<double>(),
+                             transpose, sc, st, mk);
+          for (size_t k = 0; k < blk_c0.size(); ++k) {
+            const size_t o = 3 * (size_t)blk_c0[k];
+            const int n_ = 3 * blk_nc[k];
+            if (mixed || cap_fp32)
+              launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st, bb.act, blk_scene[k]);
+            else
+              launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st, bb.act, blk_scene[k]);
+          }
+          launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st, mk);
+        }
+        if (mixed) launch_sinv_half2_32(sinv, w32, w, st, mk);
+        else launch_sinv_half2(sinv, t3, w, st, mk);
+      }
+    }
+    launch_seg_copy_step(T, w, false, Z, true, N, jp, m, bb.act, nullptr, st);  // Z_j = P^{-1} V_j
+    launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
+                        mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st, mk);  // V_{j+1} = A Z_j
+    const int g2 = m + 1, gn = 2 * (m + 1);
+    launch_seg_dot_step(T, V, N, jp, m, false, bb.act, bb.partial, bb.cnt, bb.K, bb.gsb, bb.gstride, 0, st);
+    launch_seg_axpy_step(T, V, N, jp, m, bb.act, bb.gsb, bb.gstride, 0, st);
+    launch_seg_dot_step(T, V, N, jp, m, false, bb.act, bb.partial, bb.cnt, bb.K, bb.gsb, bb.gstride, g2, st);
+    launch_seg_axpy_step(T, V, N, jp, m, bb.act, bb.gsb, bb.gstride, g2, st);
+    launch_seg_dot_step(T, V, N, jp, m, true, bb.act, bb.partial, bb.cnt, bb.K, bb.gsb, bb.gstride, gn, st);
+    launch_seg_normalize_step(T, V, N, jp, m, bb.act, bb.gsb, bb.gstride, gn, st);
+    launch_seg_givens(bb.ns, jp, m, bb.act, bb.gsb, bb.gstride, bb.H, bb.cs, bb.sn, bb.g, bb.kk, bb.iters, bb.tol,
+                      maxit, S.bmap_dev, st);
+  }
+  cudaGraphExec_t batch_step_graph(double* V, double* Z, int* jp, int maxit) {
+    std::vector<uintptr_t> key = step_key();
+    for (uintptr_t v : {(uintptr_t)precond, (uintptr_t)maxit, (uintptr_t)S.bwork.p, (uintptr_t)S.segt.p,
+                        (uintptr_t)S.bmap_dev, (uintptr_t)S.iperm.p})
+      key.push_back(v);
+    for (int v : blk_scene) key.push_back((uintptr_t)v);
+    if (S.bstep_exec && key == S.bstep_key) return S.bstep_exec;
+    if (S.bstep_exec) {
+      cudaGraphExecDestroy(S.bstep_exec);
+      S.bstep_exec = nullptr;
+    }
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    const int64_t l0 = g_launches;
+    enqueue_batch_step(V, Z, jp, maxit);
+    S.bstep_launches = (int)(g_launches - l0);
+    g_launches = l0;
+    const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+    if (ce != cudaSuccess || !gr) {
+      cudaGetLastError();
+      if (gr) cudaGraphDestroy(gr);
+      return nullptr;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    S.bstep_exec = ex;
+    S.bstep_key = key;
+    return ex;
+  }
+
+  // Solve B x = b scene by scene: every mesh of the batch runs its own right-preconditioned
+  // flexible GMRES(m) (Sec. 4.4) to ||b_s - B_s x_s|| <= rtol ||b_s||, x0 = 0, with its own inner
+  // products, Hessenberg matrix, restarts and stopping test; a mesh that has converged drops out
+  // of every later launch.  The host only launches steps (one captured graph per step off the
+  // legacy default stream) and reads, per step, how many meshes are still active.
+  // Returns the largest per-scene iteration count; per-scene counts and final true relative
+  // residuals go to S.last_iters / S.last_rel.
+  int solve_batched(double rtol, int max_iters) {
+    const int ns = bb.ns;
+    const SegTiles T = tiles();
+    double* V = S.gmres.as<double>();
+    double* Z = S.fgmres.as<double>();
+    int* jp = S.gstep.as<int>();
+    int* nact_dev = S.bmap_dev;
+    int* notdone_dev = S.bmap_dev + kMaxRestart;
+    volatile int* nact_h = S.bmap_host;
+    volatile int* notdone_h = S.bmap_host + kMaxRestart;
+    const Mask mcyc{bb.cyc, S.scene_of_vertex.as<int32_t>()};
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(bb.cnt, 0, sizeof(unsigned) * (size_t)ns * bb.K, st));
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    launch_seg_init(ns, bb.cyc, bb.done, bb.iters, st);
+    launch_seg_sq(T, r, bb.cyc, bb.partial, bb.cnt, bb.K, m + 2, bb.rr, st);
+    launch_seg_restart(ns, m, true, bb.cyc, bb.act, bb.done, bb.kk, bb.iters, max_iters, bb.rr, bb.bnorm, bb.tol,
+                       rtol, bb.relres, bb.g, jp, flags, notdone_dev, st);
+    launch_seg_start(T, r, bb.act, bb.g, m, V, st);
+    NCPADJ_CUDA_TRY(cudaEventRecord(S.bev[0], st));
+    NCPADJ_CUDA_TRY(cudaEventSynchronize(S.bev[0]));
+    int notdone = *notdone_h;
+    cudaGraphExec_t gx = batch_step_graph(V, Z, jp, max_iters);
+    constexpr int kAhead = 3;  // steps in flight (< the 4 events of S.bev)
+    for (int cycle = 0; notdone > 0 && cycle <= max_iters; ++cycle) {
+      int launched = 0, seen = 0;
+      while (seen < m) {
+        while (launched < m && launched < seen + kAhead) {
+          if (gx) {
+            NCPADJ_CUDA_TRY(cudaGraphLaunch(gx, st));
+            g_launches += S.bstep_launches;
+          } else {
+            enqueue_batch_step(V, Z, jp, max_iters);
+          }
+          NCPADJ_CUDA_TRY(cudaEventRecord(S.bev[launched & 3], st));
+          ++launched;
+        }
+        NCPADJ_CUDA_TRY(cudaEventSynchronize(S.bev[seen & 3]));
+        const int na = nact_h[seen];
+        ++seen;
+        if (na == 0) break;
+      }
+      // end of the cycle: x_s += Z_s y_s, true residual, restart or stop, scene by scene
+      launch_seg_backsolve(ns, m, bb.cyc, bb.kk, bb.H, bb.g, bb.y, st);
+      launch_seg_combine(T, Z, N, m, bb.cyc, bb.kk, bb.y, x, st);
+      if (mixed)
+        launch_bsr_spmv32(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), x, w, st, mcyc);
+      else
+        launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), x, w, st, mcyc);
+      launch_seg_resid(T, b, w, bb.cyc, r, st);
+      launch_seg_sq(T, r, bb.cyc, bb.partial, bb.cnt, bb.K, m + 2, bb.rr, st);
+      launch_seg_restart(ns, m, false, bb.cyc, bb.act, bb.done, bb.kk, bb.iters, max_iters, bb.rr, bb.bnorm, bb.tol,
+                         rtol, bb.relres, bb.g, jp, flags, notdone_dev, st);
+      launch_seg_start(T, r, bb.act, bb.g, m, V, st);
+      NCPADJ_CUDA_TRY(cudaEventRecord(S.bev[0], st));
+      NCPADJ_CUDA_TRY(cudaEventSynchronize(S.bev[0]));
+      notdone = *notdone_h;
+    }
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+    S.last_iters.assign(ns, 0);
+    S.last_rel.assign(ns, 0.0);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.last_iters.data(), bb.iters, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.last_rel.data(), bb.relres, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    (void)nact_dev;
+    int most = 0;
+    for (int v : S.last_iters) most = std::max(most, v);
+    return most;
+  }
+
   double dot_host(const double* a, const double* bb) {
     launch_multi_dot(N, 1, a, N, bb, partial, scal, st);
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.scal_host, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -849,17 +1097,31 @@ struct Engine {
         double* zz = rr + N;
         double* Ap = rr + 2 * (size_t)N;
         double* s2 = scal + 8;  // rz_old, rz_new, pAp, alpha
+        auto cg_start = [&]() {  // z = P^{-1} rr, p = z, rz = rr . z
+          apply_precond(rr, zz);
+          NCPADJ_CUDA_TRY(cudaMemcpyAsync(p, zz, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+          launch_multi_dot(N, 1, rr, N, zz, partial, s2 + 0, st);
+        };
         NCPADJ_CUDA_TRY(cudaMemcpyAsync(rr, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-        apply_precond(rr, zz);
-        NCPADJ_CUDA_TRY(cudaMemcpyAsync(p, zz, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-        launch_multi_dot(N, 1, rr, N, zz, partial, s2 + 0, st);
+        cg_start();
         for (iters = 1; iters <= max_iters; ++iters) {
           matvec(p, Ap);
           launch_multi_dot(N, 1, p, N, Ap, partial, s2 + 2, st);
           launch_cg_alpha(s2 + 0, s2 + 2, s2 + 3, st);
           launch_cg_update_xr(N, s2 + 3, p, Ap, x, rr, st);
           const double rn = std::sqrt(dot_host(rr, rr));
-          if (!std::isfinite(rn) || rn <= tol) break;
+          if (!std::isfinite(rn)) break;
+          if (rn <= tol) {
+            // the recursively updated residual drifts away from b - B x on ill-conditioned systems
+            // (stiff bindings); stop only when the true residual is there too, else restart from it
+            matvec(x, r);
+            launch_axpby(N, 1.0, b, -1.0, r, r, st);
+            const double rt = std::sqrt(dot_host(r, r));
+            if (!std::isfinite(rt) || rt <= tol || iters >= max_iters) break;
+            NCPADJ_CUDA_TRY(cudaMemcpyAsync(rr, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+            cg_start();
+            continue;
+          }
           apply_precond(rr, zz);
           launch_multi_dot(N, 1, rr, N, zz, partial, s2 + 1, st);
           launch_cg_update_p(N, s2 + 1, s2 + 0, zz, p, st);
@@ -1174,9 +1436,13 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, in.cvertex, in.region, nreg, st);  // before anything indexes with the ids
   take_bindings(S, state->bindings, host_mem, in, st);
+  // a batch scene solves every mesh by its own GMRES (CG and BiCGSTAB, when asked for by name,
+  // run over the union with the scaled right-hand side below)
+  E.batch_mode = S.n_scenes > 1 && (opt.solver == NCPADJ_SOLVER_AUTO || opt.solver == NCPADJ_SOLVER_GMRES);
   E.workspace(nc, opt.gmres_restart, opt.precond);
   // an inner iterative capacitance solve makes the preconditioner vary: flexible GMRES only
   if (!E.sup_c0.empty() && opt.precond == NCPADJ_PRECOND_WOODBURY) solver = NCPADJ_SOLVER_GMRES;
+  if (E.batch_mode) solver = NCPADJ_SOLVER_GMRES;
   E.transpose = 1;
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[0], st));
   E.assemble(in.q, in.q_prev, in.lambda, opt.eps);
@@ -1189,7 +1455,8 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   // union's relative residual bounds every scene's (the scaling is undone on z afterwards)
   std::vector<double> scale;
   double rtol = opt.rtol;
-  if (S.n_scenes > 1) {
+  const bool union_scaled = S.n_scenes > 1 && !E.batch_mode;
+  if (union_scaled) {
     const int ns = S.n_scenes;
     S.sceneval.ensure(sizeof(double) * 2 * (size_t)ns);
     double* sq = S.sceneval.as<double>();
@@ -1210,8 +1477,17 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(sq, scale.data(), sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, st));
     launch_scale_by_scene(nv, E.b, S.scene_of_vertex.as<int32_t>(), sq, st);
   }
-  const int iters = E.solve(solver, rtol, opt.max_iters, &rel, &bnorm);
-  if (S.n_scenes > 1)
+  int iters = 0;
+  if (E.batch_mode) {
+    iters = E.solve_batched(rtol, opt.max_iters);
+    for (double v : S.last_rel) rel = std::max(rel, std::isfinite(v) ? v : INFINITY);
+    bnorm = 1.0;
+  } else {
+    S.last_iters.clear();
+    S.last_rel.clear();
+    iters = E.solve(solver, rtol, opt.max_iters, &rel, &bnorm);
+  }
+  if (union_scaled)
     launch_scale_by_scene(nv, E.x, S.scene_of_vertex.as<int32_t>(), S.sceneval.as<double>() + S.n_scenes, st);
   NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[3], st));
 
@@ -1306,9 +1582,284 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   }
   raise_flags(S.flags_host);
   if (!std::isfinite(rel)) throw Error{NCPADJ_ERR_NONFINITE, "non-finite residual"};
-  if (!(rel <= rtol * 1.0000001) && bnorm > 0)
-    throw Error{NCPADJ_ERR_NOT_CONVERGED, "Krylov stopped at relative residual " + std::to_string(rel) + " after " +
-                                              std::to_string(iters) + " iterations"};
+  if (!(rel <= rtol * 1.0000001) && bnorm > 0) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "Krylov stopped at relative residual %.3e (rtol %.1e) after %d iterations", rel, rtol,
+             iters);
+    throw Error{NCPADJ_ERR_NOT_CONVERGED, msg};
+  }
+  return NCPADJ_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// the batched adjoint: per-scene arrays in, per-scene arrays out, one union solve in between
+// ------------------------------------------------------------------------------------------
+// Copy tables of one call (pinned host memory, uploaded in one copy): FP64 copies, int32 id copies
+// with offsets, FP32 copies, and the [ns + 1] contact / vertex / region offsets.
+struct CopyTable {
+  std::vector<const void*> fsrc, isrc, ssrc;
+  std::vector<void*> fdst, idst, sdst;
+  std::vector<int64_t> fcnt, icnt, scnt;
+  std::vector<int32_t> iadd;
+  void f64(const double* src, double* dst, int64_t n) {
+    if (!src || !dst || n <= 0) return;
+    fsrc.push_back(src);
+    fdst.push_back(dst);
+    fcnt.push_back(n);
+  }
+  void ids(const int32_t* src, int32_t* dst, int64_t n, int32_t add) {
+    if (!dst || n <= 0) return;
+    isrc.push_back(src);
+    idst.push_back(dst);
+    icnt.push_back(n);
+    iadd.push_back(add);
+  }
+  void f32(const float* src, float* dst, int64_t n) {
+    if (!src || !dst || n <= 0) return;
+    ssrc.push_back(src);
+    sdst.push_back(dst);
+    scnt.push_back(n);
+  }
+  // uploads the tables (and the offsets) and launches the copies
+  void run(Scene& S, const std::vector<int32_t>& offsets, const int32_t** off_dev, cudaStream_t st) {
+    const size_t nf = fsrc.size(), ni = isrc.size(), ns = ssrc.size(), no = offsets.size();
+    const size_t bytes = 8 * (3 * nf + 3 * ni + 3 * ns) + 4 * (ni + no) + 64;
+    if (S.btab_host_bytes < bytes) {
+      if (S.btab_host) cudaFreeHost(S.btab_host);
+      S.btab_host = nullptr;
+      S.btab_host_bytes = 0;
+      NCPADJ_CUDA_TRY(cudaMallocHost(&S.btab_host, bytes));
+      S.btab_host_bytes = bytes;
+    }
+    S.btab.ensure(bytes);
+    char* h = static_cast<char*>(S.btab_host);
+    char* d = S.btab.as<char>();
+    size_t o = 0;
+    auto put = [&](const void* src, size_t nbytes) {
+      if (nbytes) std::memcpy(h + o, src, nbytes);
+      const size_t at = o;
+      o += (nbytes + 7) & ~size_t(7);
+      return d + at;
+    };
+    char* fs = put(fsrc.data(), 8 * nf);
+    char* fd = put(fdst.data(), 8 * nf);
+    char* fc = put(fcnt.data(), 8 * nf);
+    char* is = put(isrc.data(), 8 * ni);
+    char* id = put(idst.data(), 8 * ni);
+    char* ic = put(icnt.data(), 8 * ni);
+    char* ia = put(iadd.data(), 4 * ni);
+    char* ss = put(ssrc.data(), 8 * ns);
+    char* sd = put(sdst.data(), 8 * ns);
+    char* sc = put(scnt.data(), 8 * ns);
+    char* of = put(offsets.data(), 4 * no);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(d, h, o, cudaMemcpyHostToDevice, st));
+    launch_gather_f64((int)nf, reinterpret_cast<const double* const*>(fs), reinterpret_cast<double* const*>(fd),
+                      reinterpret_cast<const int64_t*>(fc), st);
+    launch_gather_ids((int)ni, reinterpret_cast<const int32_t* const*>(is), reinterpret_cast<int32_t* const*>(id),
+                      reinterpret_cast<const int64_t*>(ic), reinterpret_cast<const int32_t*>(ia), st);
+    launch_gather_f32((int)ns, reinterpret_cast<const float* const*>(ss), reinterpret_cast<float* const*>(sd),
+                      reinterpret_cast<const int64_t*>(sc), st);
+    if (off_dev) *off_dev = reinterpret_cast<const int32_t*>(of);
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+  }
+};
+
+static ncpadj_status adjoint_batch(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, int ns, const ncpadj_contacts* cts,
+                                   const ncpadj_state* states, const ncpadj_seed* seeds, const ncpadj_options* opt_in,
+                                   ncpadj_grads* grads, ncpadj_stats* stats, cudaStream_t st) {
+  NCPADJ_REQUIRE(ctx && sc, "NULL context or scene");
+  Scene& S = sc->s;
+  NCPADJ_REQUIRE(ns == S.n_scenes, "n_scenes must equal the number of meshes of the batch scene");
+  NCPADJ_REQUIRE(states && seeds, "states and seeds are required");
+  ncpadj_options opt;
+  if (opt_in) opt = *opt_in;
+  else ncpadj_options_default(&opt);
+  validate_options(opt);
+  if (opt.solver != NCPADJ_SOLVER_AUTO && opt.solver != NCPADJ_SOLVER_GMRES)
+    throw Error{NCPADJ_ERR_UNSUPPORTED, "the batched adjoint runs GMRES per scene (solver AUTO or GMRES)"};
+  const bool host_mem = opt.memory == NCPADJ_MEM_HOST;
+  // sizes, offsets and what is present
+  std::vector<int32_t> coff(ns + 1, 0), roff(ns + 1, 0);
+  bool any_df = false, any_dv = false, any_region = false;
+  for (int s = 0; s < ns; ++s) {
+    const ncpadj_state& x = states[s];
+    NCPADJ_REQUIRE(x.q && x.q_prev && seeds[s].dL_dq, "every scene needs state.q, state.q_prev and seed.dL_dq");
+    NCPADJ_REQUIRE(!x.bindings || x.bindings->n_bindings == 0, "bindings are not supported in a batched call");
+    const int n = cts ? cts[s].n_contacts : 0;
+    NCPADJ_REQUIRE(n >= 0, "n_contacts < 0");
+    if (n > 0) {
+      NCPADJ_REQUIRE(cts[s].vertex && cts[s].frame && cts[s].d_n && cts[s].mu,
+                     "contact arrays vertex, frame, d_n, mu are required");
+      NCPADJ_REQUIRE(x.lambda, "state.lambda is required when a scene has contacts");
+      NCPADJ_REQUIRE(cts[s].n_regions >= 1, "n_regions must be >= 1");
+      any_df = any_df || cts[s].d_f;
+      any_region = any_region || cts[s].region;
+    }
+    any_dv = any_dv || seeds[s].dL_dv;
+    coff[s + 1] = coff[s] + n;
+    roff[s + 1] = roff[s] + (n > 0 ? cts[s].n_regions : 0);
+    if (grads && grads[s].dL_dact) NCPADJ_REQUIRE(S.fibre.p, "dL_dact requested but the scene has no fibres");
+  }
+  const int nc = coff[ns], nreg = std::max(roff[ns], 1), N = 3 * S.nv, nt = S.nt;
+  auto want = [&](size_t off) {  // does some scene ask for the output at byte offset off of ncpadj_grads
+    if (!grads) return false;
+    for (int s = 0; s < ns; ++s)
+      if (*reinterpret_cast<void* const*>(reinterpret_cast<const char*>(&grads[s]) + off)) return true;
+    return false;
+  };
+  const bool w_dq = want(offsetof(ncpadj_grads, dL_dq_prev)), w_dv = want(offsetof(ncpadj_grads, dL_dv_prev)),
+             w_df = want(offsetof(ncpadj_grads, dL_dfext)), w_z = want(offsetof(ncpadj_grads, z)),
+             w_E = want(offsetof(ncpadj_grads, dL_dE)), w_nu = want(offsetof(ncpadj_grads, dL_dnu)),
+             w_mu = want(offsetof(ncpadj_grads, dL_dmu)), w_muc = want(offsetof(ncpadj_grads, dL_dmu_contact)),
+             w_act = want(offsetof(ncpadj_grads, dL_dact));
+  // union staging: inputs, then outputs
+  const size_t nd = 8 * (size_t)N + 17 * (size_t)nc + 2 * (size_t)nt + nreg + 64;
+  S.bio.ensure(sizeof(double) * nd + sizeof(float) * (size_t)nt + 256);
+  double* p = S.bio.as<double>();
+  auto take = [&](size_t n) {
+    double* r = p;
+    p += n;
+    return r;
+  };
+  double *uq = take(N), *uqp = take(N), *udq = take(N), *udv = take(N), *ulam = take(3 * (size_t)nc),
+         *ufr = take(9 * (size_t)nc), *udn = take(nc), *udf = take(2 * (size_t)nc), *umu = take(nc);
+  double *o_dq = take(N), *o_dv = take(N), *o_df = take(N), *o_z = take(N), *o_E = take(nt), *o_nu = take(nt),
+         *o_mu = take(nreg), *o_muc = take(nc);
+  float* o_act = reinterpret_cast<float*>(p + 8);
+  S.bio_ids.ensure(sizeof(int32_t) * (4 * (size_t)nc + 64));
+  int32_t* uvert = S.bio_ids.as<int32_t>();
+  int32_t* ureg = uvert + nc;
+  int32_t* raw = ureg + nc;  // host-memory calls: the ids as given, before their offsets
+  if (any_dv) NCPADJ_CUDA_TRY(cudaMemsetAsync(udv, 0, sizeof(double) * N, st));
+  if (any_df && nc) NCPADJ_CUDA_TRY(cudaMemsetAsync(udf, 0, sizeof(double) * 2 * nc, st));
+  CopyTable in;
+  auto h2d = [&](const void* src, void* dst, size_t bytes) {
+    if (src && bytes) NCPADJ_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+  };
+  for (int s = 0; s < ns; ++s) {
+    const size_t v0 = 3 * (size_t)S.voff[s], nv3 = 3 * (size_t)(S.voff[s + 1] - S.voff[s]);
+    const int n = coff[s + 1] - coff[s];
+    const size_t c0 = coff[s];
+    const ncpadj_state& x = states[s];
+    if (host_mem) {
+      h2d(x.q, uq + v0, 8 * nv3);
+      h2d(x.q_prev, uqp + v0, 8 * nv3);
+      h2d(seeds[s].dL_dq, udq + v0, 8 * nv3);
+      h2d(seeds[s].dL_dv, udv + v0, 8 * nv3);
+      if (n) {
+        h2d(x.lambda, ulam + 3 * c0, 24 * (size_t)n);
+        h2d(cts[s].frame, ufr + 9 * c0, 72 * (size_t)n);
+        h2d(cts[s].d_n, udn + c0, 8 * (size_t)n);
+        h2d(cts[s].d_f, udf + 2 * c0, 16 * (size_t)n);
+        h2d(cts[s].mu, umu + c0, 8 * (size_t)n);
+        h2d(cts[s].vertex, raw + c0, 4 * (size_t)n);
+        h2d(cts[s].region, raw + nc + c0, 4 * (size_t)n);
+        in.ids(raw + c0, uvert + c0, n, S.voff[s]);
+        if (any_region) in.ids(cts[s].region ? raw + nc + c0 : nullptr, ureg + c0, n, roff[s]);
+      }
+    } else {
+      in.f64(x.q, uq + v0, nv3);
+      in.f64(x.q_prev, uqp + v0, nv3);
+      in.f64(seeds[s].dL_dq, udq + v0, nv3);
+      in.f64(seeds[s].dL_dv, udv + v0, nv3);
+      if (n) {
+        in.f64(x.lambda, ulam + 3 * c0, 3 * (int64_t)n);
+        in.f64(cts[s].frame, ufr + 9 * c0, 9 * (int64_t)n);
+        in.f64(cts[s].d_n, udn + c0, n);
+        in.f64(cts[s].d_f, udf + 2 * c0, 2 * (int64_t)n);
+        in.f64(cts[s].mu, umu + c0, n);
+        in.ids(cts[s].vertex, uvert + c0, n, S.voff[s]);
+        if (any_region) in.ids(cts[s].region, ureg + c0, n, roff[s]);
+      }
+    }
+  }
+  std::vector<int32_t> offs;
+  offs.insert(offs.end(), coff.begin(), coff.end());
+  offs.insert(offs.end(), S.voff.begin(), S.voff.end());
+  offs.insert(offs.end(), roff.begin(), roff.end());
+  const int32_t* off_dev = nullptr;
+  in.run(S, offs, &off_dev, st);
+  if (nc) {  // every contact must name a vertex (and region) of its own scene
+    int* flags = S.flags.as<int>();
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
+    launch_check_batch_ids(nc, uvert, any_region ? ureg : nullptr, ns, off_dev, off_dev + (ns + 1),
+                           off_dev + 2 * (ns + 1), flags, st);
+    read_flags(S, st);
+    NCPADJ_REQUIRE(S.flags_host[FLAG_BADINDEX] == 0,
+                   "a contact vertex or region id is out of its scene's range");
+  }
+  // one adjoint over the union
+  ncpadj_contacts uc{nc, uvert, ufr, udn, any_df ? udf : nullptr, umu, any_region ? ureg : nullptr, nreg};
+  ncpadj_state us{uq, uqp, nc ? ulam : nullptr, nullptr};
+  ncpadj_seed ud{udq, any_dv ? udv : nullptr};
+  ncpadj_grads ug{};
+  ug.dL_dq_prev = w_dq ? o_dq : nullptr;
+  ug.dL_dv_prev = w_dv ? o_dv : nullptr;
+  ug.dL_dfext = w_df ? o_df : nullptr;
+  ug.z = w_z ? o_z : nullptr;
+  ug.dL_dE = w_E ? o_E : nullptr;
+  ug.dL_dnu = w_nu ? o_nu : nullptr;
+  ug.dL_dmu = (w_mu && nc) ? o_mu : nullptr;
+  ug.dL_dmu_contact = (w_muc && nc) ? o_muc : nullptr;
+  ug.dL_dact = w_act ? o_act : nullptr;
+  ncpadj_options uo = opt;
+  uo.memory = NCPADJ_MEM_DEVICE;
+  uo.solver = NCPADJ_SOLVER_GMRES;
+  ncpadj_stats ust{};
+  ncpadj_status status = NCPADJ_OK;
+  std::string status_msg;
+  try {
+    adjoint_step(ctx, sc, nc ? &uc : nullptr, &us, &ud, &uo, &ug, &ust, st);
+  } catch (const Error& e) {
+    // NOT_CONVERGED still delivers the outputs (the last iterate); anything else ends the call
+    if (e.status != NCPADJ_ERR_NOT_CONVERGED) throw;
+    status = e.status;
+    status_msg = e.msg;
+  }
+  // outputs back to each scene's own arrays
+  if (grads) {
+    CopyTable out;
+    auto d2h = [&](void* dst, const void* src, size_t bytes) {
+      if (dst && src && bytes) NCPADJ_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+    };
+    for (int s = 0; s < ns; ++s) {
+      const ncpadj_grads& gs = grads[s];
+      const size_t v0 = 3 * (size_t)S.voff[s], nv3 = 3 * (size_t)(S.voff[s + 1] - S.voff[s]);
+      const size_t t0 = S.toff[s], nts = S.toff[s + 1] - S.toff[s];
+      const size_t c0 = coff[s], n = coff[s + 1] - coff[s], r0 = roff[s], nr = roff[s + 1] - roff[s];
+      if (host_mem) {
+        d2h(gs.dL_dq_prev, o_dq + v0, 8 * nv3);
+        d2h(gs.dL_dv_prev, o_dv + v0, 8 * nv3);
+        d2h(gs.dL_dfext, o_df + v0, 8 * nv3);
+        d2h(gs.z, o_z + v0, 8 * nv3);
+        d2h(gs.dL_dE, o_E + t0, 8 * nts);
+        d2h(gs.dL_dnu, o_nu + t0, 8 * nts);
+        if (n) d2h(gs.dL_dmu, o_mu + r0, 8 * nr);
+        if (n) d2h(gs.dL_dmu_contact, o_muc + c0, 8 * n);
+        d2h(gs.dL_dact, o_act + t0, 4 * nts);
+      } else {
+        out.f64(o_dq + v0, gs.dL_dq_prev, nv3);
+        out.f64(o_dv + v0, gs.dL_dv_prev, nv3);
+        out.f64(o_df + v0, gs.dL_dfext, nv3);
+        out.f64(o_z + v0, gs.z, nv3);
+        out.f64(o_E + t0, gs.dL_dE, nts);
+        out.f64(o_nu + t0, gs.dL_dnu, nts);
+        if (n) out.f64(o_mu + r0, gs.dL_dmu, nr);
+        if (n) out.f64(o_muc + c0, gs.dL_dmu_contact, n);
+        out.f32(o_act + t0, gs.dL_dact, nts);
+      }
+    }
+    if (!host_mem) out.run(S, {}, nullptr, st);
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (stats)
+    for (int s = 0; s < ns; ++s) {
+      stats[s] = ust;
+      stats[s].iterations = s < (int)S.last_iters.size() ? S.last_iters[s] : ust.iterations;
+      stats[s].rel_residual = s < (int)S.last_rel.size() ? S.last_rel[s] : ust.rel_residual;
+      stats[s].n_contacts = coff[s + 1] - coff[s];
+    }
+  if (status != NCPADJ_OK) throw Error{status, status_msg};
   return NCPADJ_OK;
 }
 
@@ -1553,8 +2104,11 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     stats->ms_total = ms;
   }
   if (!std::isfinite(res)) throw Error{NCPADJ_ERR_NONFINITE, "non-finite forward residual"};
-  if (res > 1e3 * newton_tol)
-    throw Error{NCPADJ_ERR_NOT_CONVERGED, "forward Newton stopped at relative residual " + std::to_string(res)};
+  if (res > 1e3 * newton_tol) {
+    char msg[96];
+    snprintf(msg, sizeof msg, "forward Newton stopped at relative residual %.3e", res);
+    throw Error{NCPADJ_ERR_NOT_CONVERGED, msg};
+  }
   return NCPADJ_OK;
 }
 
@@ -1677,6 +2231,11 @@ void ncpadj_scene_destroy(ncpadj_scene s) {
   if (s->s.gs_inner_host) cudaFreeHost(s->s.gs_inner_host);
   if (s->s.gs_map_host) cudaFreeHost(s->s.gs_map_host);
   if (s->s.step_exec) cudaGraphExecDestroy(s->s.step_exec);
+  if (s->s.bstep_exec) cudaGraphExecDestroy(s->s.bstep_exec);
+  if (s->s.bmap_host) cudaFreeHost(s->s.bmap_host);
+  if (s->s.btab_host) cudaFreeHost(s->s.btab_host);
+  for (auto e : s->s.bev)
+    if (e) cudaEventDestroy(e);
   for (auto e : s->s.gs_ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : s->s.ev)
@@ -1835,6 +2394,23 @@ ncpadj_status ncpadj_forward_step(ncpadj_ctx ctx, ncpadj_scene scene, const ncpa
     if (ctx) NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
     return forward_step(ctx, scene, contacts, input, opt, newton_tol, max_newton, q_out, lambda_out, stats,
                         (cudaStream_t)stream);
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_adjoint_batch(ncpadj_ctx ctx, ncpadj_scene batch, int32_t n_scenes,
+                                   const ncpadj_contacts* contacts, const ncpadj_state* states,
+                                   const ncpadj_seed* seeds, const ncpadj_options* opt, ncpadj_grads* grads,
+                                   ncpadj_stats* stats, void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(ctx && batch, "NULL context or scene");
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    return adjoint_batch(ctx, batch, n_scenes, contacts, states, seeds, opt, grads, stats,
+                         static_cast<cudaStream_t>(stream));
   } catch (const Error& e) {
     return fail(e);
   } catch (const std::exception& e) {

@@ -135,6 +135,22 @@ struct Scene {
   int step_launches = 0;            // kernels in one replay
   cudaEvent_t ev[8] = {};
   cudaEvent_t gs_ev[2] = {};       // GMRES: coefficients of step j landed in pinned slot j % 2
+
+  // batched per-scene GMRES (batch scenes)
+  DevBuf segt;                      // int32 tiles of the DOF range: scene [n], beg [n], end [n], t0 [n_scenes + 1]
+  int n_tiles = 0;
+  DevBuf bwork;                     // per-scene Krylov state (flags, Hessenberg, rotations, norms, partials)
+  int* bmap_host = nullptr;         // host-mapped ints: active scenes after each step, scenes not done
+  int* bmap_dev = nullptr;
+  cudaEvent_t bev[4] = {};          // batch steps in flight
+  cudaGraphExec_t bstep_exec = nullptr;
+  std::vector<uintptr_t> bstep_key;
+  int bstep_launches = 0;
+  std::vector<int> last_iters;      // per-scene Krylov iterations and relative residuals of the last
+  std::vector<double> last_rel;     // batched adjoint
+  DevBuf bio, bio_ids, btab;        // ncpadj_adjoint_batch: union staging, ids, copy tables
+  void* btab_host = nullptr;        // pinned copy tables
+  size_t btab_host_bytes = 0;
 };
 
 struct Ctx {

@@ -24,6 +24,17 @@ enum Flag {
   FLAG_COUNT = 12
 };
 
+// Scene mask of a batch solve: a kernel given one skips the rows, chunks and contacts of scenes
+// whose act[] entry is 0.  sov maps a vertex -- and an elimination position, since every scene's
+// positions are its own vertex range -- to its scene.  The default (act = null) masks nothing.
+struct Mask {
+  const int* act = nullptr;
+  const int32_t* sov = nullptr;
+#ifdef __CUDACC__
+  __device__ __forceinline__ bool on(int v) const { return act == nullptr || act[sov[v]] != 0; }
+#endif
+};
+
 // ---- element / contact / contraction kernels (elem.cu) ---------------------------------
 // constitutive model of a tet (App. B.2); the values are those of NCPADJ_MODEL_*
 enum : int8_t { MODEL_NEO_HOOKEAN = 0, MODEL_COROTATIONAL = 1, MODEL_ARAP = 2 };
@@ -158,9 +169,9 @@ void launch_step_by_scene(int nv, const double* q, const double* dx, const int32
 // ---- linear algebra (linalg.cu) ---------------------------------------------------------
 // y = B x for the 3x3-block matrix (FP64)
 void launch_bsr_spmv(int nv, const int32_t* row_ptr, const int32_t* col, const double* val,
-                     const double* x, double* y, cudaStream_t s);
+                     const double* x, double* y, cudaStream_t s, const Mask& mk = Mask{});
 void launch_bsr_spmv32(int nv, const int32_t* row_ptr, const int32_t* col, const float* val,
-                       const double* x, double* y, cudaStream_t s);
+                       const double* x, double* y, cudaStream_t s, const Mask& mk = Mask{});
 // inverse of the scalar diagonal of the block matrix
 void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
                      cudaStream_t s);
@@ -190,10 +201,11 @@ void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaS
 // Step-indexed forms for a captured GMRES step (j = *jp on the device; V_{j+1} = V + (j + 1) ld):
 //   w = S P V_j (zeroed first; FP32 values into w32 when given)
 void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, const int* jp, double* w, float* w32,
-                           cudaStream_t s);
+                           cudaStream_t s, const Mask& mk = Mask{});
 //   V_{j+1} = A x (block matrix, FP64 or FP32 values)
 void launch_bsr_spmv_idx(int nv, const int32_t* rp, const int32_t* col, const double* val, const float* val32,
-                         const double* x, double* ybase, long yld, const int* jp, cudaStream_t s);
+                         const double* x, double* ybase, long yld, const int* jp, cudaStream_t s,
+                         const Mask& mk = Mask{});
 //   out[k] = V_k . V_{j+1}, k <= j (or, with self, out[0] = |V_{j+1}|^2); mmax = largest j + 1
 void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* jp, bool self, double* partial,
                           double* out, cudaStream_t s);
@@ -206,18 +218,19 @@ void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double
 void launch_copy_idx(int n, const double* x, double* Y, long ld, const int* jp, cudaStream_t s);
 void launch_export_step(const double* gs, int len, double* host_slots, int* jp, cudaStream_t s);
 // the two halves of A^{-1} = P^T S^T S P: w = S P x (position space, zeroed first), y = P^T S^T w
-void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s);
-void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s);
-void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s);
-void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s);
+void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s, const Mask& mk = Mask{});
+void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s, const Mask& mk = Mask{});
+void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s, const Mask& mk = Mask{});
+void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s, const Mask& mk = Mask{});
 // s_c = K'_c F_c (A^{-1} x)_{v_c} from w = S P x, along the elimination-tree paths of the contact
 // vertices (w: double, or w32 float with the FP32 values when w32 is not null)
 void launch_path_gather(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* w,
                         const float* w32, const double* frame, const double* cdata, int transpose, double* sc,
-                        cudaStream_t s);
+                        cudaStream_t s, const Mask& mk = Mask{});
 // w += coef S P J^T t (contact forces t in frame coordinates), along the same paths
 void launch_path_scatter(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* frame,
-                         const double* t, double coef, double* w, float* w32, cudaStream_t s);
+                         const double* t, double coef, double* w, float* w32, cudaStream_t s,
+                         const Mask& mk = Mask{});
 // the same with FP32 values and intermediate (x32, w32 [nv][3] float scratch); y accumulated in FP64
 void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s);
 
@@ -241,12 +254,13 @@ bool launch_gj_cols32(int n, float* C, void* scratch, int32_t* piv, int* flags, 
 bool launch_gj_cols64(int n, double* C, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s);
 // out[k][piv[k']] = B[piv[k]][k']: the plain inverse from the Gauss-Jordan result B (float or double)
 void launch_unpermute_inverse(int n, const void* B, bool fp32, const int32_t* piv, double* out, cudaStream_t s);
+// (act, scene): the launch does nothing while act[scene] is 0 (batch solves)
 void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* y, double* ytmp, double* x,
-                       cudaStream_t s);
+                       cudaStream_t s, const int* act = nullptr, int scene = 0);
 void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s);
 // x = C^{-1} y with the swept matrix B and pivot rows: x_k = B[piv_k] . y[piv]
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
-                     cudaStream_t s);
+                     cudaStream_t s, const int* act = nullptr, int scene = 0);
 
 // vector kernels
 void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
@@ -274,5 +288,63 @@ void launch_cg_update_p(int n, const double* rz_new, const double* rz_old, const
                         cudaStream_t s);
 void launch_copy_scalar(const double* src, double* dst, cudaStream_t s);
 void launch_nonfinite_check(int n, const double* x, int* flags, cudaStream_t s);
+
+
+// ---- batched per-scene GMRES (batch.cu) ------------------------------------------------------
+constexpr int kMaxRestart = 512;  // largest GMRES restart length (ncpadj_options.gmres_restart)
+// Tiles of a batch scene's DOF range [0, 3 nv): tile t covers [beg[t], end[t]) of scene scene[t]
+// (never two scenes); the tiles of scene s are t0[s] .. t0[s+1]-1.
+struct SegTiles {
+  int n = 0;
+  const int32_t* scene = nullptr;
+  const int32_t* beg = nullptr;
+  const int32_t* end = nullptr;
+  const int32_t* t0 = nullptr;
+};
+constexpr int kSegTile = 2048;
+// Step j = *jp of every active scene's Arnoldi process (V_{j+1} = V + (j + 1) ld):
+//   gsb[s][goff + k] = V_k . V_{j+1} (k <= j), or with self gsb[s][goff] = |V_{j+1}|^2.
+//   partial: m x T.n doubles; cnt: K zero counters per scene (K >= m + 3; slots m + 1, m + 2 are the
+//   self dot and launch_seg_sq's), left zero.
+void launch_seg_dot_step(const SegTiles& T, const double* V, long ld, const int* jp, int m, bool self, const int* act,
+                         double* partial, unsigned* cnt, int K, double* gsb, int gstride, int goff, cudaStream_t s);
+//   out[s] = |x_s|^2 for the scenes with mask[s]
+void launch_seg_sq(const SegTiles& T, const double* x, const int* mask, double* partial, unsigned* cnt, int K, int slot,
+                   double* out, cudaStream_t s);
+//   V_{j+1} -= sum_{k <= j} gsb[s][goff + k] V_k ;  V_{j+1} /= sqrt(gsb[s][noff])
+void launch_seg_axpy_step(const SegTiles& T, double* V, long ld, const int* jp, int m, const int* act,
+                          const double* gsb, int gstride, int goff, cudaStream_t s);
+void launch_seg_normalize_step(const SegTiles& T, double* V, long ld, const int* jp, int m, const int* act,
+                               const double* gsb, int gstride, int noff, cudaStream_t s);
+//   dst = src or d .* src (d not null), src / dst offset by j ld when *_idx
+void launch_seg_copy_step(const SegTiles& T, const double* src, bool src_idx, double* dst, bool dst_idx, long ld,
+                          const int* jp, int m, const int* act, const double* d, cudaStream_t s);
+//   Hessenberg column j, Givens rotations and stopping test of every active scene; nact[j] (host
+//   mapped) = scenes still active; *jp = j + 1
+void launch_seg_givens(int ns, int* jp, int m, int* act, const double* gsb, int gstride, double* H, double* cs,
+                       double* sn, double* g, int* kk, int* iters, const double* tol, int maxit, int* nact,
+                       cudaStream_t s);
+// end of a cycle: y_s = H_s^{-1} g_s, x += Z y_s, r = b - w, restart (see batch.cu)
+void launch_seg_backsolve(int ns, int m, const int* cyc, const int* kk, const double* H, const double* g, double* y,
+                          cudaStream_t s);
+void launch_seg_combine(const SegTiles& T, const double* Z, long ld, int m, const int* cyc, const int* kk,
+                        const double* y, double* x, cudaStream_t s);
+void launch_seg_resid(const SegTiles& T, const double* b, const double* w, const int* mask, double* r, cudaStream_t s);
+void launch_seg_restart(int ns, int m, bool first, int* cyc, int* act, int* done, int* kk, const int* iters,
+                        int maxit, const double* rr, double* bnorm, double* tol, double rtol, double* relres,
+                        double* g, int* jp, int* flags, int* notdone, cudaStream_t s);
+void launch_seg_start(const SegTiles& T, const double* r, const int* act, const double* g, int m, double* V,
+                      cudaStream_t s);
+void launch_seg_init(int ns, int* cyc, int* done, int* iters, cudaStream_t s);
+// table-driven copies (one block per entry): FP64 arrays, int32 ids plus an offset (a null source
+// gives the offset alone), FP32 arrays
+void launch_gather_f64(int nent, const double* const* src, double* const* dst, const int64_t* cnt, cudaStream_t s);
+void launch_gather_ids(int nent, const int32_t* const* src, int32_t* const* dst, const int64_t* cnt,
+                       const int32_t* add, cudaStream_t s);
+void launch_gather_f32(int nent, const float* const* src, float* const* dst, const int64_t* cnt, cudaStream_t s);
+// FLAG_BADINDEX unless contact c's vertex and region (already offset) lie in its own scene's ranges
+// (c in [coff[s], coff[s+1]) belongs to scene s; voff, roff: [ns + 1] vertex and region offsets)
+void launch_check_batch_ids(int nc, const int32_t* vertex, const int32_t* region, int ns, const int32_t* coff,
+                            const int32_t* voff, const int32_t* roff, int* flags, cudaStream_t s);
 
 }  // namespace ncpadj

@@ -37,11 +37,13 @@ template <typename V>
 __global__ void __launch_bounds__(256) k_bsr_spmv_hw(int nv, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
                                                      const double* __restrict__ x, double* __restrict__ y,
-                                                     const int* __restrict__ jp = nullptr, long yld = 0) {
+                                                     const int* __restrict__ jp = nullptr, long yld = 0,
+                                                     Mask mk = Mask{}) {
   if (jp) y += (size_t)(*jp + 1) * yld;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = t >> 4, l = t & 15;
-  const bool live = v < nv;
+  // rows of scenes outside the mask are skipped (not returned: the half-warps share shuffles)
+  const bool live = v < nv && mk.on(v);
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
   if (live) {
     const int pe = rp[v + 1];
@@ -72,7 +74,9 @@ __global__ void __launch_bounds__(256) k_bsr_spmv_hw(int nv, const int32_t* __re
 // lane with four independent accumulators; T = float accumulates in FP32 (preconditioner apply).
 template <typename T>
 __global__ void __launch_bounds__(256) k_cap_apply(int n, const T* __restrict__ B, const int32_t* __restrict__ piv,
-                                                   const double* __restrict__ y, double* __restrict__ x) {
+                                                   const double* __restrict__ y, double* __restrict__ x,
+                                                   const int* __restrict__ act = nullptr, int scene = 0) {
+  if (act && !act[scene]) return;  // the block's scene is idle (uniform over the launch)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* ys = reinterpret_cast<T*>(smraw);
   __shared__ T part[4][2];
@@ -124,11 +128,12 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
                                                      const int32_t* __restrict__ omap, const X* __restrict__ x,
                                                      Y* __restrict__ y, const int* __restrict__ jp = nullptr,
-                                                     long xld = 0) {
+                                                     long xld = 0, Mask mk = Mask{}) {
   if (jp) x += (size_t)(*jp) * xld;
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= nchunks) return;
+  if (!mk.on(crow[k])) return;  // whole warp: one chunk per warp (positions keep their scene)
   const int64_t b = cbeg[k], e = cend[k];
   Acc a0 = 0, a1 = 0, a2 = 0;
   int c[8];
@@ -162,11 +167,12 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
 // product with S, whose columns are elimination positions
 template <typename O>
 __global__ void k_to_position(int nv, const double* __restrict__ x, const int* __restrict__ jp, long ld,
-                              const int32_t* __restrict__ perm, O* __restrict__ out) {
+                              const int32_t* __restrict__ perm, O* __restrict__ out, Mask mk = Mask{}) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * nv) return;
   if (jp) x += (size_t)(*jp) * ld;
   const int p = i / 3, r = i - 3 * p;
+  if (!mk.on(p)) return;
   out[i] = (O)x[3 * (size_t)perm[p] + r];
 }
 
@@ -180,10 +186,11 @@ __global__ void __launch_bounds__(256) k_path_gather(int nc, const int32_t* __re
                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
                                                      const W* __restrict__ w, const double* __restrict__ frame,
                                                      const double* __restrict__ cdata, int transpose,
-                                                     double* __restrict__ sc) {
+                                                     double* __restrict__ sc, Mask mk = Mask{}) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nc) return;
+  if (!mk.on(cvertex[c])) return;  // whole warp: one contact per warp
   const int pv = iperm[cvertex[c]];
   const int64_t b = ptr[pv], e = ptr[pv + 1];
   double u0 = 0.0, u1 = 0.0, u2 = 0.0;
@@ -228,10 +235,11 @@ __global__ void __launch_bounds__(256) k_path_scatter(int nc, const int32_t* __r
                                                       const int32_t* __restrict__ iperm, const int64_t* __restrict__ ptr,
                                                       const int32_t* __restrict__ col, const V* __restrict__ val,
                                                       const double* __restrict__ frame, const double* __restrict__ t,
-                                                      double coef, W* w) {
+                                                      double coef, W* w, Mask mk = Mask{}) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= nc) return;
+  if (!mk.on(cvertex[c])) return;  // whole warp: one contact per warp
   const double* F = frame + 9 * (size_t)c;
   const double t0 = t[3 * c], t1 = t[3 * c + 1], t2 = t[3 * c + 2];
   const double f0 = coef * (F[0] * t0 + F[3] * t1 + F[6] * t2);
@@ -483,69 +491,68 @@ __global__ void k_nonfinite(int n, const double* x, int* flags) {
 }  // namespace
 
 void launch_bsr_spmv(int nv, const int32_t* rp, const int32_t* col, const double* val, const double* x, double* y,
-                     cudaStream_t s) {
+                     cudaStream_t s, const Mask& mk) {
   g_launches += 1;
-  k_bsr_spmv_hw<double><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+  k_bsr_spmv_hw<double><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y, nullptr, 0, mk);
 }
 void launch_bsr_spmv32(int nv, const int32_t* rp, const int32_t* col, const float* val, const double* x, double* y,
-                       cudaStream_t s) {
+                       cudaStream_t s, const Mask& mk) {
   g_launches += 1;
-  k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y);
+  k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y, nullptr, 0, mk);
 }
 void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
                      cudaStream_t s) {
   g_launches += 1;
   k_diag_inv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, diag_slot, val, val32, dinv);
 }
-void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s) {
+void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s, const Mask& mk) {
   g_launches += 2;
-  k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos);
+  k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos, mk);
   cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend,
-                                                                              a.S_col, a.S_val, nullptr, a.xpos, w);
+  k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, a.xpos, w, nullptr, 0, mk);
 }
-void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s) {
+void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<double, double, double><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg,
-                                                                               a.St_cend, a.St_col, a.St_val, a.perm,
-                                                                               w, y);
+  k_spmv_chunks<double, double, double><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(
+      a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val, a.perm, w, y, nullptr, 0, mk);
 }
-void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s) {
+void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s, const Mask& mk) {
   g_launches += 2;
-  k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos32);
+  k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos32, mk);
   cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
   k_spmv_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32);
+      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32, nullptr, 0, mk);
 }
-void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s) {
+void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
   k_spmv_chunks<float, float, double, float><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(
-      a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val32, a.perm, w32, y);
+      a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val32, a.perm, w32, y, nullptr, 0, mk);
 }
 void launch_path_gather(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* w,
                         const float* w32, const double* frame, const double* cdata, int transpose, double* sc,
-                        cudaStream_t s) {
+                        cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   if (!nc) return;
   if (w32)
     k_path_gather<float, float><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
-                                                                    a.St_val32, w32, frame, cdata, transpose, sc);
+                                                                    a.St_val32, w32, frame, cdata, transpose, sc, mk);
   else
     k_path_gather<double, double><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
-                                                                      a.St_val, w, frame, cdata, transpose, sc);
+                                                                      a.St_val, w, frame, cdata, transpose, sc, mk);
 }
 void launch_path_scatter(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* frame,
-                         const double* t, double coef, double* w, float* w32, cudaStream_t s) {
+                         const double* t, double coef, double* w, float* w32, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   if (!nc) return;
   if (w32)
     k_path_scatter<float, float><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
-                                                                     a.St_val32, frame, t, coef, w32);
+                                                                     a.St_val32, frame, t, coef, w32, mk);
   else
     k_path_scatter<double, double><<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, a.St_ptr, a.St_col,
-                                                                       a.St_val, frame, t, coef, w);
+                                                                       a.St_val, frame, t, coef, w, mk);
 }
 
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s) {
@@ -578,16 +585,16 @@ void launch_convert_f32(long n, const double* x, float* y, cudaStream_t s) {
   k_to_float_n<<<nblk(n, 256), 256, 0, s>>>(n, x, y);
 }
 void launch_gj_apply(int n, const double* B, const int32_t* piv, const double* y, double* ytmp, double* x,
-                     cudaStream_t s) {
+                     cudaStream_t s, const int* act, int scene) {
   (void)ytmp;
   g_launches += 1;
-  k_cap_apply<double><<<(n + 3) / 4, 256, sizeof(double) * (size_t)n, s>>>(n, B, piv, y, x);
+  k_cap_apply<double><<<(n + 3) / 4, 256, sizeof(double) * (size_t)n, s>>>(n, B, piv, y, x, act, scene);
 }
 void launch_gj_apply32(int n, const float* B, const int32_t* piv, const double* y, double* ytmp, double* x,
-                       cudaStream_t s) {
+                       cudaStream_t s, const int* act, int scene) {
   (void)ytmp;
   g_launches += 1;
-  k_cap_apply<float><<<(n + 3) / 4, 256, sizeof(float) * (size_t)n, s>>>(n, B, piv, y, x);
+  k_cap_apply<float><<<(n + 3) / 4, 256, sizeof(float) * (size_t)n, s>>>(n, B, piv, y, x, act, scene);
 }
 void launch_axpby(int n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
   g_launches += 1;
@@ -636,24 +643,24 @@ void launch_export_step(const double* gs, int len, double* host_slots, int* jp, 
   k_export_step<<<1, 256, 0, s>>>(gs, len, host_slots, jp);
 }
 void launch_bsr_spmv_idx(int nv, const int32_t* rp, const int32_t* col, const double* val, const float* val32,
-                         const double* x, double* ybase, long yld, const int* jp, cudaStream_t s) {
+                         const double* x, double* ybase, long yld, const int* jp, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
-  if (val32) k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val32, x, ybase, jp, yld);
-  else k_bsr_spmv_hw<double><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, ybase, jp, yld);
+  if (val32) k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val32, x, ybase, jp, yld, mk);
+  else k_bsr_spmv_hw<double><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, ybase, jp, yld, mk);
 }
 void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, const int* jp, double* w, float* w32,
-                           cudaStream_t s) {
+                           cudaStream_t s, const Mask& mk) {
   g_launches += 2;
   if (w32) {
-    k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos32);
+    k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos32, mk);
     cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
     k_spmv_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32);
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32, nullptr, 0, mk);
   } else {
-    k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos);
+    k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos, mk);
     cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
     k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, a.xpos, w);
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, a.xpos, w, nullptr, 0, mk);
   }
 }
 void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {

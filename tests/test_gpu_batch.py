@@ -142,3 +142,104 @@ def test_batched_forward_reaches_every_scenes_own_state(pkg):
     for i, ((q1, _), (pb, q_prev, _)) in enumerate(zip(singles, starts)):
         seg = qb[off[i]:off[i + 1]]
         assert rel(seg - q_prev, q1 - q_prev) < 1e-7, (i, rel(seg - q_prev, q1 - q_prev))
+
+
+def _batch_inputs(cases, rng, zero_seed=None):
+    """Per-scene inputs of the batch cases in each scene's own numbering (numpy), and the oracle
+    references; scene zero_seed (if given) gets a zero loss seed."""
+    per, refs = [], []
+    for i, (pb, st, s, q_prev, v_prev) in enumerate(cases):
+        dq = rng.normal(size=s.q.shape) * 10.0 ** rng.uniform(-3, 3)
+        dv = rng.normal(size=s.q.shape) * 1e-3
+        if i == zero_seed:
+            dq, dv = np.zeros_like(dq), np.zeros_like(dv)
+        lam = s.lam_frame(st, q_prev) if st.ct.n else np.zeros((0, 3))
+        per.append((st.ct, s.q, q_prev, lam, dq, dv))
+        refs.append(st.adjoint(s, q_prev, dq, dv))
+    return per, refs
+
+
+def _uneven_cases():
+    # scenes of different sizes and contact regimes, so their own GMRES needs different counts
+    return [step_case("cube_drop", 2), step_case("two_tet", 1), step_case("cube_drop", 5), step_case("cube_drop", 0),
+            step_case("cube_drop", 3)]
+
+
+@pytest.mark.parametrize("memory", ["device", "host"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_batch_matches_oracle_scene_by_scene(pkg, precision, memory):
+    """ncpadj_adjoint_batch: per-scene arrays in and out; every scene equals the oracle and stops at
+    its own iteration count (about its single-scene count), not at the slowest scene's."""
+    from tests.test_gpu_parity import gpu_contacts
+    ctx = pkg.Context(0)
+    cases = _uneven_cases()
+    rng = np.random.default_rng(1)
+    per, refs = _batch_inputs(cases, rng, zero_seed=3)
+    batch = pkg.Scene.batch(ctx, [(c[0].scene.X, c[0].scene.tets, c[0].scene.E, c[0].scene.nu, c[0].scene.density)
+                                  for c in cases], cases[0][0].scene.h)
+    dev = "cuda" if memory == "device" else "cpu"
+    rtol = 1e-12 if precision == "fp64" else 1e-8
+    cts = [gpu_contacts(pkg, ct, dev) for ct, *_ in per]
+    outs, stats = pkg.adjoint_batch(batch, cts, [T(p[1], dev=dev) for p in per], [T(p[2], dev=dev) for p in per],
+                                    [T(p[3], dev=dev) for p in per], [T(p[4], dev=dev) for p in per],
+                                    [T(p[5], dev=dev) for p in per], eps=cases[0][0].scene.eps, rtol=rtol,
+                                    precision=precision, cap_precision=precision, memory=memory)
+    torch.cuda.synchronize()
+    tol = 1e-8 if precision == "fp64" else 1e-3
+    for i, ((pb, st, s, q_prev, v_prev), ref, o, stt) in enumerate(zip(cases, refs, outs, stats)):
+        for k in ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "z", "dL_dE", "dL_dnu"):
+            if i == 3:
+                assert float(o[k].abs().max()) == 0.0, (i, k)
+            else:
+                assert rel(o[k].cpu().numpy(), ref[k]) <= tol, (i, k, rel(o[k].cpu().numpy(), ref[k]))
+        if st.ct.n and i != 3:
+            assert rel(o["dL_dmu_contact"].cpu().numpy(), ref["dL_dmu_contact"]) <= tol, (i, "mu_c")
+            assert rel(o["dL_dmu"].cpu().numpy(), ref["dL_dmu_region"]) <= tol, (i, "mu")
+        assert stt["rel_residual"] <= rtol * 1.0000001, (i, stt)
+        assert stt["n_contacts"] == st.ct.n
+    its = [s_["iterations"] for s_ in stats]
+    assert its[3] == 0, its  # a zero seed is solved by z = 0 without an iteration
+    assert len(set(its)) > 2, its  # each scene stops at its own count
+    # each scene's count is its own GMRES's: the same scene alone (GMRES, same options) takes as many
+    for i, (pb, st, s, q_prev, v_prev) in enumerate(cases):
+        if i == 3:
+            continue
+        sc = pb.scene
+        single = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+        ct, q, qp, lam, dq, dv = per[i]
+        _, s1 = pkg.adjoint_step(single, gpu_contacts(pkg, ct), T(q), T(qp), T(lam), T(dq), T(dv), eps=sc.eps,
+                                 rtol=rtol, precision=precision, cap_precision=precision, solver="gmres")
+        assert abs(s1["iterations"] - its[i]) <= 2, (i, s1["iterations"], its[i])
+
+
+def test_adjoint_batch_rejects_a_vertex_of_another_scene(pkg):
+    from tests.test_gpu_parity import gpu_contacts
+    ctx = pkg.Context(0)
+    cases = _uneven_cases()[:2]
+    per, _ = _batch_inputs(cases, np.random.default_rng(2))
+    batch = pkg.Scene.batch(ctx, [(c[0].scene.X, c[0].scene.tets, c[0].scene.E, c[0].scene.nu, c[0].scene.density)
+                                  for c in cases], cases[0][0].scene.h)
+    cts = [gpu_contacts(pkg, ct) for ct, *_ in per]
+    nv0 = cases[0][0].scene.X.shape[0]
+    cts[0].vertex[0] = nv0  # one past scene 0's vertices: a vertex of scene 1 in the union
+    with pytest.raises(pkg.NcpadjError, match="INVALID_ARG"):
+        pkg.adjoint_batch(batch, cts, [T(p[1]) for p in per], [T(p[2]) for p in per], [T(p[3]) for p in per],
+                          [T(p[4]) for p in per], None)
+
+
+def test_adjoint_batch_reports_not_converged_per_scene(pkg):
+    from tests.test_gpu_parity import gpu_contacts
+    ctx = pkg.Context(0)
+    cases = _uneven_cases()[:3]
+    per, _ = _batch_inputs(cases, np.random.default_rng(3))
+    batch = pkg.Scene.batch(ctx, [(c[0].scene.X, c[0].scene.tets, c[0].scene.E, c[0].scene.nu, c[0].scene.density)
+                                  for c in cases], cases[0][0].scene.h)
+    cts = [gpu_contacts(pkg, ct) for ct, *_ in per]
+    with pytest.raises(pkg.NcpadjError, match="NOT_CONVERGED") as ei:
+        pkg.adjoint_batch(batch, cts, [T(p[1]) for p in per], [T(p[2]) for p in per], [T(p[3]) for p in per],
+                          [T(p[4]) for p in per], [T(p[5]) for p in per], rtol=1e-12, max_iters=3)
+    st = ei.value.stats
+    assert all(s_["iterations"] <= 3 for s_ in st), st
+    assert max(s_["rel_residual"] for s_ in st) > 1e-12
+    for o in ei.value.grads:  # the last iterate is still delivered
+        assert torch.isfinite(o["z"]).all()

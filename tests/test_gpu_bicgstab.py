@@ -1,11 +1,5 @@
 """BiCGSTAB as the Krylov method (NCPADJ_SOLVER_BICGSTAB) against the FP64 oracle, and against
-GMRES on the full-size beam.
-
-These tests have not yet run on a GPU: they are skipped unless NCPADJ_TEST_UNVERIFIED=1, so
-that a first failure cannot stop the rest of the GPU suite; the first GPU run that passes them
-removes the gate."""
-import os
-
+GMRES on the full-size beam."""
 import numpy as np
 import pytest
 
@@ -14,9 +8,7 @@ torch = pytest.importorskip("torch")
 from tests._cases import rel, step_case  # noqa: E402
 from tests.test_gpu_parity import T, assert_parity, gpu_contacts, gpu_scene, run_both  # noqa: E402
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("NCPADJ_TEST_UNVERIFIED") != "1",
-                                 reason="not yet run on a GPU (set NCPADJ_TEST_UNVERIFIED=1)")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")

@@ -2,11 +2,10 @@
 against the FP64 oracle: adjoint parity of every gradient, a stiff compliance, mixed precision,
 the forward state, and argument errors.
 
-These tests have not yet run on a GPU: they are skipped unless NCPADJ_TEST_UNVERIFIED=1, so that
-a first failure cannot stop the rest of the GPU suite; the first GPU run that passes them removes
-the gate."""
+With no contacts the adjoint is solved by CG; at the stiff compliance (h^2/E_b ~ 3e4 against
+vertex masses of 8 g) its recursively updated residual drifts from the true one, and CG restarts
+from the true residual until that one meets rtol."""
 import functools
-import os
 
 import numpy as np
 import pytest
@@ -17,9 +16,7 @@ from tests._cases import rel  # noqa: E402
 from tests.test_gpu_parity import KEYS, T, gpu_contacts, gpu_scene  # noqa: E402
 from tests.test_oracle_bindings import _bary_case  # noqa: E402
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("NCPADJ_TEST_UNVERIFIED") != "1",
-                                 reason="not yet run on a GPU (set NCPADJ_TEST_UNVERIFIED=1)")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
