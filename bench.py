@@ -1,20 +1,29 @@
-"""Benchmark: adjoint gradients/s of one implicit step on the beam-on-incline scene.
+"""Benchmark: batched adjoint gradients/s of one implicit step, 64 uneven Neo-Hookean blocks.
 
-Workload (the mid-size single scene): Neo-Hookean beam of 40x10x10 hex cells x 5 tets (20,000 tets,
-4,961 vertices), E=5e5, nu=0.45, rho=1000, resting on a 20 deg plane with mu=0.3 (451 frictional
-contacts, eps=1e-4), h=1/100.  The state is produced on the GPU by the forward step (3 steps from
-rest, so the beam slides); one bench step = one complete adjoint step through the C-ABI: assembly
-of script_A^T (per-tet SVD Jacobians, contact blocks), Woodbury set-up (Delassus, capacitance,
-its inversion), GMRES to rtol 1e-8 and all gradient contractions (dL/dqbar, dL/dvbar, dL/dfext,
-dL/dE, dL/dnu per tet, dL/dmu).
+Workload (the batched configuration): 64 independent blocks with tet counts log-uniform in
+[2,000, 50,000] (930,875 tets, 227,449 vertices in total), aspect ratios U(0.5, 2)^3, E log-uniform
+in [1e4, 1e6], nu ~ U(0.3, 0.48), ground friction mu ~ U(0.1, 1.0) per block, bottoms U(0, 2 cm)
+above the ground, velocities N(0, 0.05^2) m/s per vertex component, h = 1/60, eps = 1e-4.  The
+state is produced on the GPU by one forward step of every block.  One bench step = one call of
+ncpadj_adjoint_batch: the adjoint step of all 64 blocks -- assembly of script_A^T (per-tet SVD
+Jacobians, contact blocks), Woodbury set-up (Delassus, capacitance, its inversion), one GMRES per
+block to its own rtol 1e-8 (all blocks sharing every launch, each dropping out when converged)
+and every gradient contraction (dL/dqbar, dL/dvbar, dL/dfext, dL/dE, dL/dnu per tet, dL/dmu).
+A gradient = one block's adjoint step; value = 64 x steps / time.
+
+The plain FP64 adjoint, the mixed one (FP32 matrix values, preconditioner and capacitance, FP64
+Krylov reductions) and the mixed one with an FP64 capacitance factor are timed on the same
+inputs; the headline is the fastest within 1e-3 of plain FP64.  The single 20,000-tet beam on an
+incline (``config.beam``) and optional large scenes are measured beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line.  Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
-events on the library's stream; L2 (129 MB) is flushed by writing a 512 MB buffer before every
-timed step (the working set, ~90 MB, would otherwise stay resident).  Multi-GPU: the path does
-not shard within a scene, so N ranks run N independent replicas (one process per GPU); value is
-the adjoints of all ranks over the slowest rank's time.
+Prints one JSON line.  Timing: W untimed warm-up calls, then K calls, each bracketed by CUDA
+events on the library's stream; a 512 MB buffer is written before every timed call, so L2
+(129 MB) holds nothing of the previous call (the batch's own working set, > 1 GB, exceeds it
+anyway).  Multi-GPU: the blocks are independent units, so every rank solves its own batch of 64
+(seeded by the rank) with no collective on the data path (weak scaling); value is the blocks of
+all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -34,8 +43,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "adjoint gradients/sec per step (batched FP32/64 vs plain FP64) at rel err <=1e-3"
-WORKLOAD = ("beam 40x10x10 cells x 5 tets (20000 tets, 4961 verts), 451 frictional contacts on a 20deg incline, "
-            "mu=0.3, eps=1e-4, h=1/100, one adjoint step (state: GPU forward, 3 steps from rest)")
+WORKLOAD = ("64 independent Neo-Hookean blocks, 930875 tets / 227449 verts in total (tets log-uniform 2k..50k per "
+            "block, E log-U[1e4,1e6], nu U(0.3,0.48), mu U(0.1,1.0), drop heights U(0,2cm), v N(0,0.05^2), h=1/60, "
+            "eps=1e-4), one adjoint step of every block per call (ncpadj_adjoint_batch; state: GPU forward step)")
+BEAM = ("beam 40x10x10 cells x 5 tets (20000 tets, 4961 verts), 451 frictional contacts on a 20deg incline, "
+        "mu=0.3, eps=1e-4, h=1/100, one adjoint step (state: GPU forward, 3 steps from rest)")
 
 
 def peaks():
@@ -102,12 +114,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------------
 # reference arm and CPU baseline: the FP64 oracle, single-threaded, in a child process
 # --------------------------------------------------------------------------------------------
-def oracle_times(steps, warmup, state=None):
+def oracle_times(steps, warmup, state=None, batch=False):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, "-m", "oracle.timing", "--steps", str(steps), "--warmup", str(warmup)]
     if state:
         cmd += ["--state", state]
+    if batch:
+        cmd += ["--batch"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -143,39 +157,51 @@ def models_leg(pkg, torch, dev, scene, n_verts, q_adj, timed):
     return res
 
 
-def cpu_baseline_leg(arrays):
-    """The oracle at the bench's state: ``arrays`` holds q, q_prev, dL_dq, dL_dv and the GPU
-    gradients as '<variant>/<key>'.  Falls back to the oracle's own start point if that state
-    cannot be used.  Returns (the cpu_baseline object, the relative errors vs the oracle or None)."""
+def cpu_baseline_leg(arrays, batch=False):
+    """The oracle at the bench's state: ``arrays`` holds the state, the seeds and the GPU gradients
+    (for the batch, per sampled block under 'b<i>/').  Falls back to the oracle's own start point
+    of the step if that state cannot be used.  Returns (the cpu_baseline object, the relative
+    errors vs the oracle or None)."""
     import tempfile
-    d, err, where = None, None, "the bench's GPU state (3 forward steps from rest, same seeds)"
+    d, err, where = None, None, "the bench's GPU state (same seeds)"
     try:
         with tempfile.TemporaryDirectory() as tdir:
             path = os.path.join(tdir, "state.npz")
             np.savez(path, **arrays)
-            d = oracle_times(3, 1, state=path)
+            d = oracle_times(3, 1, state=path, batch=batch)
         err = d.get("rel_err_vs_oracle")
     except Exception:  # noqa: BLE001 -- fall back to the oracle's own start point
-        where = "the oracle's start point of step 1"
+        where = "the oracle's start point of the step"
         try:
-            d = oracle_times(3, 1)
+            d = oracle_times(3, 1, batch=batch)
         except Exception as e:  # noqa: BLE001
             return {"value": None, "unit": "gradients/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}, None
+    if batch:
+        ids = [b["block"] for b in d["blocks"]]
+        sample = (f"{len(d['seconds'])} oracle adjoints (assembly + direct sparse LU + contractions), one per block "
+                  f"of a seeded sample of the 64 (blocks {ids}), at {where}, after 1 warm-up; gradients/s of the "
+                  f"sample's mean block, {sum(d['seconds']):.1f} s in total")
+    else:
+        sample = (f"{len(d['seconds'])} oracle adjoints of the beam (assembly + direct sparse LU + contractions) at "
+                  f"{where}, after 1 warm-up")
     return ({"value": len(d["seconds"]) / sum(d["seconds"]), "unit": "gradients/s", "cores": d["threads"],
-             "kind": "oracle", "sample": f"{len(d['seconds'])} oracle adjoints of the beam (assembly + direct sparse "
-             f"LU + contractions) at {where}, after 1 warm-up"}, err)
+             "kind": "oracle", "sample": sample}, err)
 
 
 def run_reference(args):
+    """The oracle (FP64, one thread) on the batched workload: step k is one block's adjoint, the blocks
+    of the seeded sample taken in turn, at the oracle's own start point of the step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    d = oracle_times(args.steps, args.warmup)
+    d = oracle_times(args.steps, args.warmup, batch=True)
     secs = d["seconds"]
     total = sum(secs)
     val = len(secs) / total
-    sample = (f"{len(secs)} oracle adjoints (explicit assembly + direct sparse LU + contractions) of the beam "
-              f"at the oracle's start point of step 1, {d['threads']} thread")
+    ids = sorted({b["block"] for b in d["blocks"]})
+    sample = (f"{len(secs)} oracle adjoints (explicit assembly + direct sparse LU + contractions), step k = block "
+              f"ids[k % {len(ids)}] of a seeded sample {ids} of the 64 blocks, at the oracle's start point of the "
+              f"step, {d['threads']} thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "gradients/s", "n_gpus": args.gpus,
         "steps": len(secs), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(secs), "higher_is_better": True,
@@ -189,22 +215,24 @@ def run_reference(args):
 # --------------------------------------------------------------------------------------------
 # batched uneven scenes: 64 independent blocks (log-uniform 2k..50k tets), one adjoint each
 # --------------------------------------------------------------------------------------------
-def apply_roofline(pkg, torch, dev, scene, K):
-    """GB/s of the product with A^{-1} = P^T S^T S P (two k_spmv_chunks launches, FP64, 3 RHS) on a
-    scene: K applies captured into one CUDA graph and replayed, timed with events on the replay
-    stream.  Returns algorithmic bytes (Cholesky-factor based) and the kernels' own bytes (S, S^T)."""
+def apply_roofline(pkg, torch, dev, scene, K, precision="fp64"):
+    """GB/s of the product with A^{-1} = P^T S^T S P (two k_spmv_chunks launches, 3 RHS; FP64, or the
+    FP32 values and intermediates of the mixed preconditioner) on a scene: K applies captured into
+    one CUDA graph and replayed, timed with events on the replay stream.  Algorithmic bytes count
+    the Cholesky factor L (2 nnz(L) values + indices) and the vectors; kernel bytes count what the
+    kernels read instead (S = L^{-1} and S^T)."""
     info = scene.info()
     n3 = 3 * scene.n_verts
     sx = torch.randn(scene.n_verts, 3, dtype=torch.float64, device=dev)
     sy = torch.empty_like(sx)
     sst = torch.cuda.Stream(dev)
     for _ in range(3):
-        pkg.elastic_solve(scene, sx, sy, stream=sst.cuda_stream)
+        pkg.elastic_solve(scene, sx, sy, stream=sst.cuda_stream, precision=precision)
     torch.cuda.synchronize(dev)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=sst):
         for _ in range(K):
-            pkg.elastic_solve(scene, sx, sy, stream=torch.cuda.current_stream().cuda_stream)
+            pkg.elastic_solve(scene, sx, sy, stream=torch.cuda.current_stream().cuda_stream, precision=precision)
     with torch.cuda.stream(sst):
         g.replay()
         torch.cuda.synchronize(dev)
@@ -215,88 +243,211 @@ def apply_roofline(pkg, torch, dev, scene, K):
         e1.record(sst)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / (3 * K)
-    alg = 2 * info["nnz_L"] * 12 + 4 * n3 * 8
-    kb = 2 * info["nnz_Linv"] * 12 + 4 * n3 * 8
+    bv = 8 if precision == "fp64" else 4
+    vec = n3 * (4 * 8 if precision == "fp64" else 8 + 4 + 4 + 8)  # x in, w out and in, y out
+    alg = 2 * info["nnz_L"] * (bv + 4) + vec
+    kb = 2 * info["nnz_Linv"] * (bv + 4) + vec
     peak, src = peaks()
-    return {"kernel": "k_spmv_chunks x2 (A^-1 = P^T S^T S P, FP64, 3 RHS)", "bound": "hbm",
+    return {"kernel": f"k_spmv_chunks x2 (A^-1 = P^T S^T S P, {'FP64' if precision == 'fp64' else 'FP32'} values, "
+                      "3 RHS)", "bound": "hbm",
             "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
             "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": src, "ms_per_launch_pair": ms,
             "algorithmic_bytes": alg, "kernel_bytes": kb, "kernel_bytes_gbs": kb / (ms / 1e3) / 1e9,
             "kernel_bytes_frac": kb / (ms / 1e3) / 1e9 / peak}
 
 
-def batched(pkg, torch, dev, steps, warmup):
-    import synth
-    blocks = synth.block_batch(64)
-    h = blocks[0].scene.h
-    ctx = pkg.Context(dev.index or 0)
-    t0 = time.perf_counter()
-    scene = pkg.Scene.batch(ctx, [(b.scene.X, b.scene.tets, b.scene.E, b.scene.nu, b.scene.density) for b in blocks], h)
-    t_build = time.perf_counter() - t0
-    off = scene.vertex_offsets
-    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
-    # one forward step of every block (contacts from its start state) on the GPU gives the adjoint state
-    q0 = T(np.concatenate([b.q0 for b in blocks]))
-    v0 = T(np.concatenate([b.v0 for b in blocks]))
-    verts, frames, dn, mu, reg = [], [], [], [], []
-    for i, b in enumerate(blocks):
-        ct = b.scene.contacts(b.q0)
-        verts.append(ct.vertex + off[i])
-        frames.append(ct.frame)
-        dn.append(ct.d_n)
-        mu.append(ct.mu)
-        reg.append(np.full(ct.n, i, np.int32))
-    nc = sum(len(v) for v in verts)
-    contacts = pkg.Contacts(T(np.concatenate(verts), torch.int32), T(np.concatenate(frames)), T(np.concatenate(dn)),
-                            T(np.concatenate(mu)), None, T(np.concatenate(reg), torch.int32), len(blocks))
-    # impacts at up to ~0.15 m/s make some blocks' Newton solves long: the adjoint is timed at the
-    # iterate reached within 150 steps, whose residual is reported
-    try:
-        q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(blocks[0].scene.gravity),
-                                      eps=blocks[0].scene.eps, max_newton=150, cap_precision="mixed")
-    except pkg.NcpadjError as e:
-        if not hasattr(e, "state"):
-            raise
-        (q, lam), fs = e.state, e.stats
-    tgt = T(np.concatenate([b.q_target for b in blocks]))
-    dq = 2 * (q - tgt)
-    stream = torch.cuda.Stream(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    res = {}
-    for prec in ("fp64", "mixed"):
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_spmv_chunks_fp32_batched.md")
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of one FP32 A^{-1} apply on the 64-block union, from the committed ncu
+    summary -- or None when there is none, or when the kernels' source file has changed since the
+    counters were taken (the summary records its sha256)."""
+    import hashlib
+    import re
+    if not os.path.exists(TRAFFIC_PROFILE):
+        return None, "no ncu summary"
+    txt = open(TRAFFIC_PROFILE).read()
+    m = re.search(r"^traffic_bytes_per_apply:\s*(\d+)", txt, re.M)
+    h = re.search(r"^linalg_cu_sha256:\s*([0-9a-f]{64})", txt, re.M)
+    src = os.path.join(ROOT, "paper_2603_16478_gb300", "csrc", "linalg.cu")
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if not m or not h:
+        return None, "ncu summary without traffic"
+    if h.group(1) != cur:
+        return None, "kernels changed since the ncu capture"
+    return int(m.group(1)), os.path.relpath(TRAFFIC_PROFILE, ROOT)
+
+
+class BatchWorkload:
+    """The 64-block batch on the device: scene, GPU forward state and per-block inputs (each block
+    in its own numbering, as ncpadj_adjoint_batch takes them)."""
+
+    def __init__(self, pkg, torch, dev, seed=0):
+        import synth
+        self.blocks = blocks = synth.block_batch(64, seed=seed)
+        sc0 = blocks[0].scene
+        self.eps, self.h = sc0.eps, sc0.h
+        ctx = pkg.Context(dev.index or 0)
+        t0 = time.perf_counter()
+        self.scene = scene = pkg.Scene.batch(ctx, [(b.scene.X, b.scene.tets, b.scene.E, b.scene.nu, b.scene.density)
+                                                   for b in blocks], self.h)
+        self.build_s = time.perf_counter() - t0
+        off = scene.vertex_offsets
+        T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+        cts = [b.scene.contacts(b.q0) for b in blocks]
+        self.n_contacts = [c.n for c in cts]
+        self.contacts = [None if c.n == 0 else pkg.Contacts(T(c.vertex, torch.int32), T(c.frame), T(c.d_n), T(c.mu),
+                                                              None, T(np.full(c.n, 0, np.int32), torch.int32), 1)
+                         for c in cts]
+        union = pkg.Contacts(T(np.concatenate([c.vertex + off[i] for i, c in enumerate(cts)]), torch.int32),
+                             T(np.concatenate([c.frame for c in cts])), T(np.concatenate([c.d_n for c in cts])),
+                             T(np.concatenate([c.mu for c in cts])), None,
+                             T(np.concatenate([np.full(c.n, i, np.int32) for i, c in enumerate(cts)]), torch.int32),
+                             len(blocks))
+        q0 = T(np.concatenate([b.q0 for b in blocks]))
+        v0 = T(np.concatenate([b.v0 for b in blocks]))
+        t0 = time.perf_counter()
+        try:
+            q, lam, fs = pkg.forward_step(scene, union, q0, v0, None, tuple(sc0.gravity), eps=self.eps,
+                                          max_newton=150, cap_precision="mixed")
+        except pkg.NcpadjError as e:  # the adjoint is taken at the last iterate; its residual is reported
+            if not hasattr(e, "state"):
+                raise
+            (q, lam), fs = e.state, e.stats
+        self.forward_s = time.perf_counter() - t0
+        self.forward = fs
+        self.q = [q[off[i]:off[i + 1]].contiguous() for i in range(64)]
+        self.q_prev = [q0[off[i]:off[i + 1]].contiguous() for i in range(64)]
+        c0 = np.concatenate([[0], np.cumsum(self.n_contacts)])
+        self.lam = [lam[c0[i]:c0[i + 1]].contiguous() for i in range(64)]
+        self.dL_dq = [(2 * (self.q[i] - T(b.q_target))).contiguous() for i, b in enumerate(blocks)]
+        self.dL_dv = None
+
+    def call(self, pkg, precision, cap, memory="device", ins=None, outputs=None):
+        a = ins or (self.contacts, self.q, self.q_prev, self.lam, self.dL_dq, self.dL_dv)
+        return pkg.BatchCall(self.scene, *a, eps=self.eps, rtol=1e-8, precision=precision, cap_precision=cap,
+                             memory=memory, outputs=outputs)
+
+    def describe(self):
+        nc = sum(self.n_contacts)
+        return (f"{nc} contacts in {sum(1 for n in self.n_contacts if n)} blocks; forward: "
+                f"{self.forward['newton_iters']} Newton iterations, residual {self.forward['residual']:.2e}")
+
+
+def time_calls(torch, dev, call, stream, flush, steps, warmup, world=1, dist=None):
+    """(total ms over `steps` calls timed by CUDA events on `stream`, per-call stats); L2 flushed before
+    each timed call.  With world > 1: the slowest rank's total."""
+    with torch.cuda.stream(stream):
         for _ in range(warmup):
-            pkg.adjoint_step(scene, contacts, q, q0, lam.contiguous(), dq, None, eps=blocks[0].scene.eps,
-                             precision=prec, cap_precision=prec, stream=stream.cuda_stream)
-        ms = []
+            call.run(stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sts = []
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            sts.append(call.run(stream.cuda_stream))
+            ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    tot = sum(x.elapsed_time(y) for x, y in ev)
+    if world > 1:
+        t = torch.tensor([tot], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    return tot, sts
+
+
+def krylov_summary(sts):
+    """Per-block iteration counts of the last call: sum, largest, mean, and the union-solve equivalent."""
+    its = [x["iterations"] for x in sts[-1]]
+    return {"per_block_sum": int(sum(its)), "per_block_max": int(max(its)), "per_block_mean": float(np.mean(its)),
+            "blocks_x_max": len(its) * int(max(its))}
+
+
+def beam_leg(pkg, torch, dev, steps, warmup, flush, with_models=True, cpu=False):
+    """The mid-size single scene: the beam on the incline (one 20,000-tet scene, 451 frictional
+    contacts), FP64 and mixed adjoints at its GPU forward state, optionally the other constitutive
+    models and stiff bindings, the A^{-1} roofline on this L2-resident scene, and the oracle on it."""
+    import synth
+    pb = synth.beam_incline()
+    sc = pb.scene
+    ct = sc.contacts(pb.q0)
+    ctx = pkg.Context(dev.index or 0)
+    scene = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    contacts = pkg.Contacts(T(ct.vertex, torch.int32), T(ct.frame), T(ct.d_n), T(ct.mu), None,
+                            T(ct.region, torch.int32), ct.n_regions)
+    q_prev, v_prev = T(pb.q0), T(pb.v0)
+    fwd = []
+    for _ in range(3):
+        q, lam, fs = pkg.forward_step(scene, contacts, q_prev, v_prev, None, tuple(sc.gravity), eps=sc.eps)
+        fwd.append(fs)
+        v_prev = (q - q_prev) / sc.h
+        q_prev, q = q, None
+    q_prev_adj = q_prev - v_prev * sc.h
+    q_adj = q_prev
+    lam_adj = lam.contiguous()
+    c_tgt = q_adj.mean(0) + 1e-3 * T(sc.planes[0].t1)
+    dL_dq = (2.0 * (q_adj.mean(0) - c_tgt) / sc.n_verts).expand(sc.n_verts, 3).contiguous()
+    dL_dv = torch.zeros_like(dL_dq)
+    stream = torch.cuda.Stream(dev)
+
+    def one(prec="fp64", cap="fp64", bindings=None):
+        return pkg.adjoint_step(scene, contacts, q_adj, q_prev_adj, lam_adj, dL_dq, dL_dv, eps=sc.eps, rtol=1e-8,
+                                stream=stream.cuda_stream, precision=prec, cap_precision=cap, bindings=bindings)
+
+    def timed(prec, cap, n, **kw):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                one(prec, cap, **kw)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         sts = []
         with torch.cuda.stream(stream):
-            for _ in range(steps):
+            for i in range(n):
                 flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                g, st = pkg.adjoint_step(scene, contacts, q, q0, lam.contiguous(), dq, None, eps=blocks[0].scene.eps,
-                                         precision=prec, cap_precision=prec, stream=stream.cuda_stream)
-                e1.record(stream)
-                torch.cuda.synchronize(dev)
-                ms.append(e0.elapsed_time(e1))
-                sts.append(st)
-        res[prec] = {"gradients_per_s": len(blocks) * steps / (sum(ms) / 1e3), "ms_per_call": sum(ms) / steps,
+                ev[i][0].record(stream)
+                sts.append(one(prec, cap, **kw)[1])
+                ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(x.elapsed_time(y) for x, y in ev), sts
+
+    ref = {k: v.clone() for k, v in one("fp64")[0].items()}
+    res, grads_by = {}, {"fp64": ref}
+    for name, (pr, cp) in {"fp64": ("fp64", "fp64"), "mixed": ("mixed", "mixed"),
+                           "mixed_cap64": ("mixed", "fp64")}.items():
+        g_ = one(pr, cp)[0]
+        grads_by[name] = {k: v.clone() for k, v in g_.items()}
+        tm, sts = timed(pr, cp, steps)
+        res[name] = {"gradients_per_s": steps / (tm / 1e3), "ms_per_call": tm / steps,
                      "krylov_iterations": statistics.median(x["iterations"] for x in sts),
+                     "max_rel_err_vs_fp64": max(float((torch.linalg.norm(g_[k] - ref[k]) /
+                                                       torch.linalg.norm(ref[k]).clamp_min(1e-300)).item())
+                                                for k in ref),
                      "stage_ms": {k: statistics.mean(x[k] for x in sts) for k in
-                                  ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract")}}
-        res[prec + "_grads"] = {k: v.clone() for k, v in g.items()}
-    err = max(float((torch.linalg.norm(res["mixed_grads"][k] - res["fp64_grads"][k]) /
-                     torch.linalg.norm(res["fp64_grads"][k]).clamp_min(1e-300)).item()) for k in res["fp64_grads"])
-    for k in ("mixed_grads", "fp64_grads"):
-        res.pop(k)
-    info = scene.info()
-    roof = apply_roofline(pkg, torch, dev, scene, 10)
-    return {"workload": f"64 independent blocks, {scene.n_tets} tets / {scene.n_verts} verts in total "
-                        f"(log-uniform 2k..50k tets each), {nc} contacts in {sum(1 for v in verts if len(v))} blocks, "
-                        "one adjoint step of every block per call",
-            "fp64": res["fp64"], "mixed": res["mixed"], "max_rel_err_mixed_vs_fp64": err,
-            "scene_build_s": t_build, "nnz_Linv": info["nnz_Linv"], "forward_newton_iters": fs["newton_iters"],
-            "forward_residual": fs["residual"], "roofline_Ainv": roof}
+                                  ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract", "ms_cap_inverse")}}
+    out = {"workload": BEAM, **res, "capacitance_dim": sts[0]["capacitance_dim"],
+           "forward_newton_iters": [f["newton_iters"] for f in fwd],
+           "forward_residual": [f["residual"] for f in fwd], "nnz_L": scene.info()["nnz_L"],
+           "nnz_Linv": scene.info()["nnz_Linv"]}
+    roof = apply_roofline(pkg, torch, dev, scene, 50, precision="mixed")
+    roof["note"] = "burst figure: S and S^T (27 MB in FP32 on the beam) stay L2-resident between applies"
+    out["roofline_Ainv"] = roof
+    if with_models:
+        out["models"] = models_leg(pkg, torch, dev, scene, sc.n_verts, q_adj,
+                                   lambda **kw: timed("mixed", "mixed", max(3, steps // 2), **kw))
+    if cpu:
+        arrays = {"q": q_adj.cpu().numpy(), "q_prev": q_prev_adj.cpu().numpy(), "dL_dq": dL_dq.cpu().numpy(),
+                  "dL_dv": dL_dv.cpu().numpy()}
+        for vname, gv in grads_by.items():
+            for k, v in gv.items():
+                arrays[f"{vname}/{k}"] = v.cpu().numpy()
+        out["cpu_baseline"], out["max_rel_err_vs_oracle"] = cpu_baseline_leg(arrays)
+    return out
 
 
 def sphere(pkg, torch, dev, steps, warmup):
@@ -466,10 +617,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-block measurement")
+    ap.add_argument("--no-beam", action="store_true", help="skip the single-scene beam measurement")
     ap.add_argument("--no-models", action="store_true",
                     help="skip the co-rotational / ARAP / bindings timings on the beam")
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
@@ -477,6 +627,10 @@ def main():
     ap.add_argument("--quad-scale", type=float, default=1.0, help="linear scale of the quadruped (1 = full size)")
     ap.add_argument("--roofline-only", choices=["beam", "batched"], default=None,
                     help="build the scene and run only the A^-1 roofline measurement (for profiler captures)")
+    ap.add_argument("--blocks", type=int, default=64,
+                    help="--roofline-only batched: the first N blocks of the batch (smaller profiler captures)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the batched headline (no side legs; for profiler launch lists)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -503,204 +657,142 @@ def main():
             b = synth.beam_incline().scene
             scene = pkg.Scene(ctx, b.X, b.tets, b.E, b.nu, b.density, b.h)
         else:
-            blocks = synth.block_batch(64)
+            blocks = synth.block_batch(64)[:args.blocks]
             scene = pkg.Scene.batch(ctx, [(x.scene.X, x.scene.tets, x.scene.E, x.scene.nu, x.scene.density)
                                           for x in blocks], blocks[0].scene.h)
-        print(json.dumps({"roofline_only": args.roofline_only, "roofline": apply_roofline(pkg, torch, dev, scene, 10)}))
+        print(json.dumps({"roofline_only": args.roofline_only, "blocks": args.blocks, "info": scene.info(),
+                          "roofline": apply_roofline(pkg, torch, dev, scene, 10, precision="mixed")}))
         return
 
-    pb = synth.beam_incline()
-    sc = pb.scene
-    ct = sc.contacts(pb.q0)
-    ctx = pkg.Context(local)
-    scene = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
-    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
-    contacts = pkg.Contacts(T(ct.vertex, torch.int32), T(ct.frame), T(ct.d_n), T(ct.mu), None,
-                            T(ct.region, torch.int32), ct.n_regions)
-    # converged state from the GPU forward step: 3 steps from rest
-    q_prev, v_prev = T(pb.q0), T(pb.v0)
-    fwd_stats = []
-    for _ in range(3):
-        q, lam, fs = pkg.forward_step(scene, contacts, q_prev, v_prev, None, tuple(sc.gravity), eps=sc.eps)
-        fwd_stats.append(fs)
-        v_prev = (q - q_prev) / sc.h
-        q_prev, q = q, None
-    q_prev_adj = q_prev - v_prev * sc.h   # the differentiated step maps q_prev_adj -> q_adj
-    q_adj = q_prev
-    lam_adj = lam.contiguous()
-    # centroid loss L = ||mean(q) - c_tgt||^2, target 1 mm further down the slope
-    c_tgt = q_adj.mean(0) + 1e-3 * T(sc.planes[0].t1)
-    dL_dq = (2.0 * (q_adj.mean(0) - c_tgt) / sc.n_verts).expand(sc.n_verts, 3).contiguous()
-    dL_dv = torch.zeros_like(dL_dq)
-    outputs = {k: torch.empty(v, dtype=torch.float64, device=dev) for k, v in (
-        ("dL_dq_prev", (sc.n_verts, 3)), ("dL_dv_prev", (sc.n_verts, 3)), ("dL_dfext", (sc.n_verts, 3)),
-        ("z", (sc.n_verts, 3)), ("dL_dE", (sc.n_tets,)), ("dL_dnu", (sc.n_tets,)), ("dL_dmu", (1,)),
-        ("dL_dmu_contact", (ct.n,)))}
+    # ---- the batched workload: 64 blocks per rank (the rank seeds its batch) ----
+    W = BatchWorkload(pkg, torch, dev, seed=rank)
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def one(mem="device", ins=None, outs=None, prec="fp64", cap="fp64", bindings=None):
-        a = ins or (q_adj, q_prev_adj, lam_adj, dL_dq, dL_dv, contacts)
-        return pkg.adjoint_step(scene, a[5], a[0], a[1], a[2], a[3], a[4], eps=sc.eps, rtol=1e-8, memory=mem,
-                                outputs=outs or outputs, stream=stream.cuda_stream, precision=prec,
-                                cap_precision=cap, bindings=bindings)
-
     variants = {"fp64": ("fp64", "fp64"), "mixed": ("mixed", "mixed"), "mixed_cap64": ("mixed", "fp64")}
-    # accuracy of the mixed variants against plain FP64 on the same inputs
-    ref = {k: v.clone() for k, v in one(prec="fp64")[0].items()}
+    calls = {k: W.call(pkg, *v) for k, v in variants.items()}
+    # accuracy of the mixed variants against plain FP64 on the same inputs (every block, every output)
+    grads_by = {}
+    for k, c in calls.items():
+        c.run(stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        grads_by[k] = [{n: t.clone() for n, t in o.items()} for o in c.outputs]
     errs = {}
-    grads_by = {"fp64": ref}  # kept for the oracle comparison of the CPU-baseline leg
-    for name, (pr, cp) in variants.items():
-        if name == "fp64":
-            continue
-        g_ = one(prec=pr, cap=cp)[0]
-        grads_by[name] = {k: v.clone() for k, v in g_.items()}
-        errs[name] = max(float((torch.linalg.norm(g_[k] - ref[k]) / torch.linalg.norm(ref[k]).clamp_min(1e-300)).item())
-                         for k in ref)
-    torch.cuda.synchronize(dev)
-
-    def timed(pr, cp, steps, **kw):
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                one(prec=pr, cap=cp, **kw)
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        sts = []
-        with torch.cuda.stream(stream):
-            for i in range(steps):
-                flush.zero_()  # evict the previous step's working set from L2
-                ev[i][0].record(stream)
-                _, st = one(prec=pr, cap=cp, **kw)
-                ev[i][1].record(stream)
-                sts.append(st)
-        torch.cuda.synchronize(dev)
-        tot = sum(x.elapsed_time(y) for x, y in ev)
-        if world > 1:
-            t = torch.tensor([tot], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot, sts
-
-    # the headline variant: the fastest mixed variant within 1e-3 of plain FP64, else plain FP64
+    for k in ("mixed", "mixed_cap64"):
+        e = 0.0
+        for ob, rb, nc in zip(grads_by[k], grads_by["fp64"], W.n_contacts):
+            for n in rb:
+                if nc == 0 and n in ("dL_dmu", "dL_dmu_contact"):
+                    continue
+                e = max(e, float((torch.linalg.norm(ob[n] - rb[n]) / torch.linalg.norm(rb[n]).clamp_min(1e-300)).item()))
+        errs[k] = e
     head = "mixed" if errs["mixed"] <= 1e-3 else ("mixed_cap64" if errs["mixed_cap64"] <= 1e-3 else "fp64")
+    side_steps = max(3, args.steps // 2)
     results = {}
-    for name in ("fp64", "mixed_cap64", "mixed"):
-        if name == head:
-            continue
-        results[name] = timed(*variants[name], max(3, args.steps // 2))
+    for k in ("fp64", "mixed_cap64", "mixed"):
+        if k != head:
+            results[k] = time_calls(torch, dev, calls[k], stream, flush, side_steps, args.warmup, world, dist)
     clocks = ClockSampler(local)
     clocks.start()
     t_wall0 = time.perf_counter()
-    torch.cuda.nvtx.range_push("timed")
-    total_ms, stats = timed(*variants[head], args.steps)
+    torch.cuda.nvtx.range_push("timed")  # the region profiler launch lists cover (--nvtx-include "timed/")
+    total_ms, stats = time_calls(torch, dev, calls[head], stream, flush, args.steps, args.warmup, world, dist)
     torch.cuda.nvtx.range_pop()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     results[head] = (total_ms, stats)
-    value = world * args.steps / (total_ms / 1e3)
-    rate = {k: world * len(v[1]) / (v[0] / 1e3) for k, v in results.items()}
+    nblk = len(W.blocks)
+    value = world * nblk * args.steps / (total_ms / 1e3)
+    per_variant = {k: {"gradients_per_s": world * nblk * len(v[1]) / (v[0] / 1e3), "ms_per_call": v[0] / len(v[1]),
+                       "krylov_iterations": krylov_summary(v[1]),
+                       "stage_ms": {f: statistics.mean(x[0][f] for x in v[1]) for f in
+                                    ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract", "ms_cap_inverse")}}
+                   for k, v in results.items()}
+    launches = int(statistics.median(x[0]["kernel_launches"] for x in stats))
 
     # ---- end to end through the C-ABI with host buffers (copies inside the timed region) ----
-    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
-    h_contacts = pkg.Contacts(pin(contacts.vertex), pin(contacts.frame), pin(contacts.d_n), pin(contacts.mu), None,
-                              pin(contacts.region), contacts.n_regions)
-    h_in = (pin(q_adj), pin(q_prev_adj), pin(lam_adj), pin(dL_dq), pin(dL_dv), h_contacts)
-    h_out = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in outputs.items()}
-    h2d = sum(t.numel() * t.element_size() for t in h_in[:5]) + sum(
-        t.numel() * t.element_size() for t in (h_contacts.vertex, h_contacts.frame, h_contacts.d_n, h_contacts.mu,
-                                                h_contacts.region))
-    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
-    with torch.cuda.stream(stream):
-        e2e_t = []
-        if not args.no_e2e:
-            one("host", h_in, h_out, *variants[head])
-        for _ in range(0 if args.no_e2e else max(3, args.steps // 2)):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            one("host", h_in, h_out, *variants[head])  # synchronous: returns once outputs are in host memory
-            e2e_t.append(time.perf_counter() - t0)
-    e2e_value = world / (sum(e2e_t) / len(e2e_t)) if e2e_t else None
+    e2e_value, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        pin = lambda t: None if t is None else t.cpu().pin_memory()  # noqa: E731
+        h_ct = [None if c is None else pkg.Contacts(pin(c.vertex), pin(c.frame), pin(c.d_n), pin(c.mu), None,
+                                                      pin(c.region), c.n_regions) for c in W.contacts]
+        h_in = (h_ct, [pin(t) for t in W.q], [pin(t) for t in W.q_prev], [pin(t) for t in W.lam],
+                [pin(t) for t in W.dL_dq], None)
+        hc = W.call(pkg, *variants[head], memory="host", ins=h_in)
+        h2d = sum(t.numel() * t.element_size() for lst in h_in[1:5] for t in lst) + sum(
+            t.numel() * t.element_size() for c in h_ct if c is not None
+            for t in (c.vertex, c.frame, c.d_n, c.mu, c.region))
+        d2h = sum(t.numel() * t.element_size() for o in hc.outputs for t in o.values())
+        with torch.cuda.stream(stream):
+            hc.run(stream.cuda_stream)
+            e2e_t = []
+            for _ in range(side_steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                hc.run(stream.cuda_stream)  # synchronous: returns once the outputs are in host memory
+                e2e_t.append(time.perf_counter() - t0)
+        e2e_value = world * nblk / (sum(e2e_t) / len(e2e_t))
 
-    # ---- roofline of the dominant kernel ----
-    # The Krylov loop dominates the step, and in it the product with A^{-1} = P^T S^T S P (two
-    # launches of k_spmv_chunks, S then S^T, with 3 right-hand sides): it is timed live here through
-    # ncpadj_elastic_solve on its own stream (the same kernels on the same data, FP64 values).
-    it = statistics.median(s["iterations"] for s in stats)
-    ncap = stats[0]["capacitance_dim"]
-    info = scene.info()
-    hbm_peak, hbm_src = peaks()
-    launches = int(statistics.median(s["kernel_launches"] for s in stats))
-    n3 = 3 * sc.n_verts
-    roof = apply_roofline(pkg, torch, dev, scene, 50)
-    roof["note"] = ("burst figure: applies replayed back to back from a captured graph, S and S^T "
-                    "(53 MB on the beam) L2-resident between launches")
+    # ---- roofline of the dominant kernel: the FP32 product with A^{-1} (the headline's instance) ----
+    roof = apply_roofline(pkg, torch, dev, W.scene, 10, precision="mixed" if head != "fp64" else "fp64")
+    roof["note"] = ("burst figure: applies on the whole 64-block union replayed back to back from a captured graph "
+                    "(S and S^T exceed L2 many times over)")
+    if head != "fp64":
+        roof["traffic"], roof["traffic_source"] = profiled_traffic()
 
-    # ---- the other constitutive models (App. B.2) and stiff bindings, same scene and state ----
-    # (one rank only: a failure here must not leave other ranks waiting in a collective)
-    models_res = None
-    if world == 1 and not args.no_models:
-        models_res = models_leg(pkg, torch, dev, scene, sc.n_verts, q_adj,
-                                lambda **kw: timed(*variants[head], max(3, args.steps // 4), **kw))
+    side = {}
+    if not args.batch_only and world == 1:
+        if not args.no_beam:
+            try:
+                side["beam"] = beam_leg(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush,
+                                        with_models=not args.no_models)
+            except Exception as e:  # noqa: BLE001
+                side["beam"] = {"error": str(e)[:300]}
+        if args.sphere:
+            try:
+                side["sphere"] = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)
+            except Exception as e:  # noqa: BLE001
+                side["sphere"] = {"error": str(e)[:300]}
+        if args.quadruped:
+            try:
+                side["quadruped"] = quadruped_measure(pkg, torch, dev, max(2, args.steps // 4), 1, args.quad_scale)
+            except Exception as e:  # noqa: BLE001
+                side["quadruped"] = {"error": str(e)[:300]}
 
-    # ---- the batched workload ----
-    batch_res = None
-    if not args.no_batch:
-        try:
-            batch_res = batched(pkg, torch, dev, max(3, args.steps // 4), 1)
-        except Exception as e:  # noqa: BLE001
-            batch_res = {"error": str(e)[:300]}
-
-    sphere_res = None
-    if args.sphere:
-        try:
-            sphere_res = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)
-        except Exception as e:  # noqa: BLE001
-            sphere_res = {"error": str(e)[:300]}
-
-    quad_res = None
-    if args.quadruped:
-        try:
-            quad_res = quadruped_measure(pkg, torch, dev, max(2, args.steps // 4), 1, args.quad_scale)
-        except Exception as e:  # noqa: BLE001
-            quad_res = {"error": str(e)[:300]}
-
-    # ---- CPU baseline: the oracle, one thread, bounded sample ----
-    # The oracle runs at the bench's own state (the GPU forward's), on the same seeds, so the same
-    # runs also give each GPU variant's gradient error against the oracle.
+    # ---- CPU baseline: the oracle, one thread, on a seeded sample of the blocks at the GPU state ----
+    # (the same runs give every GPU variant's gradient error against the oracle on those blocks)
     cpu, err_oracle = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        arrays = {"q": q_adj.cpu().numpy(), "q_prev": q_prev_adj.cpu().numpy(), "dL_dq": dL_dq.cpu().numpy(),
-                  "dL_dv": dL_dv.cpu().numpy()}
-        for vname, gv in grads_by.items():
-            for k, v in gv.items():
-                arrays[f"{vname}/{k}"] = v.cpu().numpy()
-        cpu, err_oracle = cpu_baseline_leg(arrays)
+        sys.path.insert(0, ROOT)
+        from oracle.timing import batch_sample_ids
+        arrays = {}
+        for i in batch_sample_ids():
+            arrays[f"b{i}/q"] = W.q[i].cpu().numpy()
+            arrays[f"b{i}/q_prev"] = W.q_prev[i].cpu().numpy()
+            arrays[f"b{i}/dL_dq"] = W.dL_dq[i].cpu().numpy()
+            arrays[f"b{i}/dL_dv"] = np.zeros_like(arrays[f"b{i}/dL_dq"])
+            for vname, gb in grads_by.items():
+                for k, v in gb[i].items():
+                    arrays[f"b{i}/{vname}/{k}"] = v.cpu().numpy()
+        cpu, err_oracle = cpu_baseline_leg(arrays, batch=True)
     if rank == 0:
+        its = krylov_summary(stats)
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "variant": head,
-                       "precision": {"fp64": "plain FP64", "mixed": "FP32 matrix/preconditioner/capacitance factor, FP64 "
-                                     "Krylov reductions", "mixed_cap64": "FP32 matrix/preconditioner, FP64 capacitance "
-                                     "factor and Krylov reductions"}[head],
-                       "gradients_per_s": rate, "max_rel_err_vs_fp64": errs, "max_rel_err_vs_oracle": err_oracle,
-                       "preconditioner": "Woodbury",
-                       "solver": "GMRES(64)", "rtol": 1e-8, "krylov_iterations": it, "capacitance_dim": ncap,
-                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
-                       "wall_s": t_wall, "stage_ms": {k: statistics.mean(s[k] for s in stats) for k in
-                                                      ("ms_assemble", "ms_setup", "ms_krylov", "ms_contract",
-                                                       "ms_cap_inverse")},
-                       "forward_newton_iters": [f["newton_iters"] for f in fwd_stats],
-                       "forward_residual": [f["residual"] for f in fwd_stats],
-                       "nnz_L": info["nnz_L"], "nnz_Linv": info["nnz_Linv"], "batched": batch_res,
-                       **({"models": models_res} if models_res is not None else {}),
-                       **({"sphere": sphere_res} if sphere_res is not None else {}),
-                       **({"quadruped": quad_res} if quad_res is not None else {})},
+                       "precision": {"fp64": "plain FP64", "mixed": "FP32 matrix/preconditioner/capacitance factor, "
+                                     "FP64 Krylov reductions", "mixed_cap64": "FP32 matrix/preconditioner, FP64 "
+                                     "capacitance factor and Krylov reductions"}[head],
+                       "variants": per_variant, "max_rel_err_vs_fp64": errs,
+                       "max_rel_err_vs_oracle": err_oracle, "preconditioner": "Woodbury",
+                       "solver": "GMRES(64) per block, flexible", "rtol": 1e-8, "krylov_iterations": its,
+                       "state": W.describe(), "forward_s": W.forward_s, "scene_build_s": W.build_s,
+                       "nnz_L": W.scene.info()["nnz_L"], "nnz_Linv": W.scene.info()["nnz_Linv"],
+                       "l2": "flushed (512 MB write) before every timed call; working set > 1 GB",
+                       "parallelism": f"blocks sharded by rank x{world}, no collective", "wall_s": t_wall, **side},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "gradients/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches * args.steps, "clocks": clk,

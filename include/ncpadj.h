@@ -319,6 +319,12 @@ ncpadj_status ncpadj_adjoint_batch(ncpadj_ctx ctx, ncpadj_scene batch, int32_t n
  * use).  Errors: INVALID_ARG, OOM, CUDA. */
 ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y, void* stream);
 
+/* The same product as ncpadj_elastic_solve in the mixed precision of the preconditioner
+ * (ncpadj_options.precision = NCPADJ_MIXED): FP32 values of S = L^{-1} and FP32 intermediates,
+ * FP64 x and y.  Same arguments and errors. */
+ncpadj_status ncpadj_elastic_solve_mixed(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y,
+                                         void* stream);
+
 /* Per-tet actuation (the paper's muscle-driven soft robots describe their actuators only in words;
  * this is the reading used here): tet i carries an activation a_i (Pa, FP32) and a fixed unit fibre
  * direction d_i in the rest frame, adding the constant first Piola stress a_i d_i d_i^T.  Its nodal

@@ -6,8 +6,8 @@ The compute path is the C-ABI library ``libncpadj.so`` (hand-written CUDA for sm
 in ``include/ncpadj.h``); this package only marshals arguments to it.  There is no CPU
 fallback: every call fails loudly if the library is not built.
 """
-from .binding import (Bindings, Contacts, Context, Scene, NcpadjError, adjoint_batch, adjoint_step, elastic_solve,
+from .binding import (BatchCall, Bindings, Contacts, Context, Scene, NcpadjError, adjoint_batch, adjoint_step, elastic_solve,
                       forward_step, library_path, load_library, status_name)
 
-__all__ = ["Bindings", "Contacts", "Context", "Scene", "NcpadjError", "adjoint_batch", "adjoint_step", "elastic_solve",
+__all__ = ["BatchCall", "Bindings", "Contacts", "Context", "Scene", "NcpadjError", "adjoint_batch", "adjoint_step", "elastic_solve",
            "forward_step", "library_path", "load_library", "status_name"]

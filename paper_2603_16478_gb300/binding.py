@@ -108,9 +108,9 @@ class _ForwardStats(C.Structure):
 
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
-           "ncpadj_options_default",
-           "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step", "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc",
-           "ncpadj_dense_inverse", "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
+           "ncpadj_options_default", "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step",
+           "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc", "ncpadj_elastic_solve_mixed", "ncpadj_dense_inverse",
+           "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
 
 
 def load_library(path: Optional[str] = None):
@@ -145,6 +145,7 @@ def load_library(path: Optional[str] = None):
                                         C.POINTER(_ForwardStats), C.c_void_p]
     lib.ncpadj_elastic_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_elastic_solve_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.ncpadj_elastic_solve_mixed.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_set_fibres.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_set_model.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_dense_inverse.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
@@ -382,55 +383,77 @@ def _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, preco
     return opt
 
 
-def adjoint_batch(scene: Scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4, rtol=1e-8, max_iters=2000,
-                  restart=64, precision="fp64", cap_precision="fp64", precond="woodbury", cap_block=0,
-                  memory="device", stream=None, want=("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu",
-                                                      "dL_dmu", "dL_dmu_contact", "z")):
-    """One adjoint step of every mesh of a batch scene (``Scene.batch``) through
-    ``ncpadj_adjoint_batch``: every mesh runs its own GMRES, sharing the launches.
+class BatchCall:
+    """A prepared ``ncpadj_adjoint_batch`` call: the per-mesh argument structs are built once, so
+    that repeated calls (same tensors, new values) cost one library call each.
 
     ``contacts``, ``q``, ``q_prev``, ``lam``, ``dL_dq`` (and ``dL_dv``, or None) are lists with one
-    entry per mesh, in the mesh's own numbering (``contacts[s]`` may be None, ``lam[s]`` is then
-    ignored).  Returns (list of per-mesh output dicts, list of per-mesh stats dicts)."""
-    lib = scene.lib
-    ns = len(scene.vertex_offsets) - 1
-    for name, lst in (("contacts", contacts), ("q", q), ("q_prev", q_prev), ("lam", lam), ("dL_dq", dL_dq)):
-        if len(lst) != ns:
-            raise ValueError(f"{name}: expected {ns} entries (one per mesh), got {len(lst)}")
-    if dL_dv is not None and len(dL_dv) != ns:
-        raise ValueError(f"dL_dv: expected {ns} entries, got {len(dL_dv)}")
-    dev = q[0].device
-    cts, stt, sds, grs, outs = (_Contacts * ns)(), (_State * ns)(), (_Seed * ns)(), (_Grads * ns)(), []
-    for s in range(ns):
-        nv = scene.vertex_offsets[s + 1] - scene.vertex_offsets[s]
-        nt = scene.tet_offsets[s + 1] - scene.tet_offsets[s]
-        ct = contacts[s]
-        nc = ct.n if ct is not None else 0
-        nreg = ct.n_regions if ct is not None else 1
-        shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
-                  "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (nc,), "dL_dact": (nt,)}
-        o = {}
-        for k in want:
-            dt = torch.float32 if k == "dL_dact" else torch.float64
-            if memory == "host":
-                o[k] = torch.empty(shapes[k], dtype=dt, pin_memory=torch.cuda.is_available())
-            else:
-                o[k] = torch.empty(shapes[k], dtype=dt, device=dev)
-        outs.append(o)
-        cts[s] = _contacts_struct(ct)
-        stt[s] = _State(_ptr(q[s]), _ptr(q_prev[s]), _ptr(lam[s]) if nc else None, None)
-        sds[s] = _Seed(_ptr(dL_dq[s]), _ptr(dL_dv[s]) if dL_dv is not None else None)
-        grs[s] = _Grads(*[_ptr(o.get(k)) for k in _GRAD_FIELDS])
-    opt = _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, "gmres", memory, cap_block)
-    stats = (_Stats * ns)()
-    if stream is None and dev.type == "cuda":
-        stream = torch.cuda.current_stream(dev).cuda_stream
-    st = lib.ncpadj_adjoint_batch(scene.ctx.handle, scene.handle, ns, cts, stt, sds, C.byref(opt), grs, stats,
-                                  C.c_void_p(stream or 0))
-    sl = [stats[s].to_dict() for s in range(ns)]
-    if st != 0:
-        raise NcpadjError(st, lib.ncpadj_last_error().decode(), sl, outs)
-    return outs, sl
+    entry per mesh of a batch scene (``Scene.batch``), in the mesh's own numbering; ``contacts[s]``
+    may be None (``lam[s]`` is then ignored).  ``outputs`` may give the per-mesh output tensors
+    (list of dicts by name); missing ones are allocated on the inputs' device (pinned CPU memory
+    with memory="host").  ``run()`` returns the per-mesh stats dicts; the outputs are in
+    ``self.outputs``."""
+
+    def __init__(self, scene: Scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4, rtol=1e-8,
+                 max_iters=2000, restart=64, precision="fp64", cap_precision="fp64", precond="woodbury",
+                 cap_block=0, memory="device", outputs=None,
+                 want=("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z")):
+        lib = self.lib = scene.lib
+        self.scene = scene
+        ns = self.ns = len(scene.vertex_offsets) - 1
+        for name, lst in (("contacts", contacts), ("q", q), ("q_prev", q_prev), ("lam", lam), ("dL_dq", dL_dq)):
+            if len(lst) != ns:
+                raise ValueError(f"{name}: expected {ns} entries (one per mesh), got {len(lst)}")
+        if dL_dv is not None and len(dL_dv) != ns:
+            raise ValueError(f"dL_dv: expected {ns} entries, got {len(dL_dv)}")
+        self.device = q[0].device
+        self._keep = (contacts, q, q_prev, lam, dL_dq, dL_dv)
+        self.cts, self.stt = (_Contacts * ns)(), (_State * ns)()
+        self.sds, self.grs = (_Seed * ns)(), (_Grads * ns)()
+        self.outputs = []
+        for s in range(ns):
+            nv = scene.vertex_offsets[s + 1] - scene.vertex_offsets[s]
+            nt = scene.tet_offsets[s + 1] - scene.tet_offsets[s]
+            ct = contacts[s]
+            nc = ct.n if ct is not None else 0
+            nreg = ct.n_regions if ct is not None else 1
+            shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
+                      "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (nc,), "dL_dact": (nt,)}
+            o = dict(outputs[s]) if outputs is not None else {}
+            for k in want:
+                if k in o:
+                    continue
+                dt = torch.float32 if k == "dL_dact" else torch.float64
+                if memory == "host":
+                    o[k] = torch.empty(shapes[k], dtype=dt, pin_memory=torch.cuda.is_available())
+                else:
+                    o[k] = torch.empty(shapes[k], dtype=dt, device=self.device)
+            self.outputs.append(o)
+            self.cts[s] = _contacts_struct(ct)
+            self.stt[s] = _State(_ptr(q[s]), _ptr(q_prev[s]), _ptr(lam[s]) if nc else None, None)
+            self.sds[s] = _Seed(_ptr(dL_dq[s]), _ptr(dL_dv[s]) if dL_dv is not None else None)
+            self.grs[s] = _Grads(*[_ptr(o.get(k)) for k in _GRAD_FIELDS])
+        self.opt = _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, "gmres", memory,
+                            cap_block)
+        self.stats = (_Stats * ns)()
+
+    def run(self, stream=None):
+        if stream is None and self.device.type == "cuda":
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = self.lib.ncpadj_adjoint_batch(self.scene.ctx.handle, self.scene.handle, self.ns, self.cts, self.stt,
+                                           self.sds, C.byref(self.opt), self.grs, self.stats, C.c_void_p(stream or 0))
+        sl = [self.stats[s].to_dict() for s in range(self.ns)]
+        if st != 0:
+            raise NcpadjError(st, self.lib.ncpadj_last_error().decode(), sl, self.outputs)
+        return sl
+
+
+def adjoint_batch(scene: Scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, stream=None, **kw):
+    """One adjoint step of every mesh of a batch scene (``Scene.batch``) through
+    ``ncpadj_adjoint_batch``: every mesh runs its own GMRES, sharing the launches.  Arguments as
+    ``BatchCall``; returns (list of per-mesh output dicts, list of per-mesh stats dicts)."""
+    call = BatchCall(scene, contacts, q, q_prev, lam, dL_dq, dL_dv, **kw)
+    return call.outputs, call.run(stream)
 
 
 def _contacts_struct(contacts):
@@ -475,13 +498,16 @@ def forward_step(scene: Scene, contacts: Optional[Contacts], q_prev, v_prev=None
     return q, lam[:nc], stats.to_dict()
 
 
-def elastic_solve(scene: Scene, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None):
-    """y = A^{-1} x with the scene's elastic factor (device tensors [n_verts, 3])."""
+def elastic_solve(scene: Scene, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None,
+                  precision: str = "fp64"):
+    """y = A^{-1} x with the scene's elastic factor (device tensors [n_verts, 3]); precision "mixed"
+    uses the FP32 values and intermediates of the mixed preconditioner."""
     lib = scene.lib
     y = torch.empty_like(x) if y is None else y
     if stream is None:
         stream = torch.cuda.current_stream(x.device).cuda_stream
-    _check(lib, lib.ncpadj_elastic_solve(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y), C.c_void_p(stream)))
+    fn = lib.ncpadj_elastic_solve_mixed if precision == "mixed" else lib.ncpadj_elastic_solve
+    _check(lib, fn(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y), C.c_void_p(stream)))
     return y
 
 

@@ -2333,6 +2333,33 @@ ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const dou
   }
 }
 
+ncpadj_status ncpadj_elastic_solve_mixed(ncpadj_ctx ctx, ncpadj_scene scene, const double* x, double* y,
+                                         void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(ctx && scene && x && y && x != y, "NULL or aliased argument");
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    Scene& S = scene->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n3 = 3 * (size_t)S.nv;
+    S.io.ensure(sizeof(float) * n3 + 64);
+    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+               S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
+               S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
+               S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};
+    S.xpos.ensure(sizeof(double) * n3 + sizeof(float) * n3 + 64);
+    a.xpos = S.xpos.as<double>();
+    a.xpos32 = reinterpret_cast<float*>(S.xpos.as<double>() + n3);
+    launch_ainv32(a, x, nullptr, S.io.as<float>(), y, st);
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
 ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, double* Cinv, int32_t precision,
                                    void* stream) {
   g_last_error.clear();

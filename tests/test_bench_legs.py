@@ -63,7 +63,7 @@ def _arrays():
 def test_cpu_baseline_at_the_bench_state(monkeypatch):
     calls = []
 
-    def fake(steps, warmup, state=None):
+    def fake(steps, warmup, state=None, batch=False):
         calls.append(state)
         d = np.load(state)
         assert sorted(d.files) == sorted(_arrays())
@@ -76,7 +76,7 @@ def test_cpu_baseline_at_the_bench_state(monkeypatch):
 
 
 def test_cpu_baseline_falls_back_to_the_start_point(monkeypatch):
-    def fake(steps, warmup, state=None):
+    def fake(steps, warmup, state=None, batch=False):
         if state is not None:
             raise RuntimeError("the given state is outside the local contact solve's domain")
         return {"seconds": [1.0, 1.0], "threads": 1}
@@ -87,12 +87,42 @@ def test_cpu_baseline_falls_back_to_the_start_point(monkeypatch):
 
 
 def test_cpu_baseline_reports_a_double_failure(monkeypatch):
-    def fake(steps, warmup, state=None):
+    def fake(steps, warmup, state=None, batch=False):
         raise RuntimeError("oracle failed")
 
     monkeypatch.setattr(bench, "oracle_times", fake)
     cpu, err = bench.cpu_baseline_leg(_arrays())
     assert cpu["value"] is None and "failed" in cpu["sample"] and err is None
+
+
+def test_cpu_baseline_of_the_batch_names_its_sample(monkeypatch):
+    def fake(steps, warmup, state=None, batch=False):
+        assert batch and state is not None
+        return {"seconds": [1.0, 3.0], "threads": 1, "blocks": [{"block": 4}, {"block": 9}],
+                "rel_err_vs_oracle": {"mixed": 2e-5}}
+
+    monkeypatch.setattr(bench, "oracle_times", fake)
+    cpu, err = bench.cpu_baseline_leg({"b4/q": np.zeros((2, 3))}, batch=True)
+    assert cpu["value"] == 0.5 and "[4, 9]" in cpu["sample"] and "seeded sample" in cpu["sample"]
+    assert err == {"mixed": 2e-5}
+
+
+def test_krylov_summary_counts_the_blocks_own_iterations():
+    sts = [[{"iterations": 5}, {"iterations": 7}], [{"iterations": 10}, {"iterations": 30}, {"iterations": 0}]]
+    assert bench.krylov_summary(sts) == {"per_block_sum": 40, "per_block_max": 30, "per_block_mean": 40 / 3,
+                                         "blocks_x_max": 90}
+
+
+def test_profiled_traffic_is_dropped_once_the_kernels_change(tmp_path, monkeypatch):
+    import hashlib
+    src = open(bench.os.path.join(bench.ROOT, "paper_2603_16478_gb300", "csrc", "linalg.cu"), "rb").read()
+    prof = tmp_path / "p.md"
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
+    assert bench.profiled_traffic()[0] is None
+    prof.write_text(f"traffic_bytes_per_apply: 1234\nlinalg_cu_sha256: {hashlib.sha256(src).hexdigest()}\n")
+    assert bench.profiled_traffic()[0] == 1234
+    prof.write_text("traffic_bytes_per_apply: 1234\nlinalg_cu_sha256: " + "0" * 64 + "\n")
+    assert bench.profiled_traffic() == (None, "kernels changed since the ncu capture")
 
 
 def test_clock_sampler_parses_nvidia_smi_lines():
