@@ -369,11 +369,11 @@ ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, d
  * memory is reserved up front by their own pool, or loops with hard latency limits where a
  * cudaMalloc is not acceptable.  Same arguments and result as ncpadj_elastic_solve; the
  * intermediate vectors live in a static device array sized for at most 262,144 vertices
- * (12 MiB, held by every GPU that loads the library until the process exits).
+ * (12 MiB, held by every GPU on which a context is created, until the process exits).
  *  - Scenes with more vertices are rejected with NCPADJ_ERR_INVALID_ARG.
- *  - The call makes no cudaMalloc or cudaFree.  Its first call on a device looks up the
- *    array's device address (cudaGetSymbolAddress); make that first call before any stream
- *    capture.
+ *  - The call makes no cudaMalloc or cudaFree.  ncpadj_ctx_create looks up the array's device
+ *    address (cudaGetSymbolAddress), which makes CUDA load it: the array is allocated when the
+ *    context is created, never during this call.
  *  - Every call shares the one array: calls that overlap on the GPU (other streams, other
  *    threads) race with each other.  Each call clears the array before use.
  * Errors: INVALID_ARG, CUDA. */

@@ -2169,6 +2169,12 @@ ncpadj_status ncpadj_ctx_create(int device, ncpadj_ctx* out) {
     c->c.device = device;
     cudaDeviceGetAttribute(&c->c.sm_count, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&c->c.coop_ok, cudaDevAttrCooperativeLaunch, device);
+    try {
+      noalloc_prepare(device);  // the allocation-free solve's static scratch is loaded now, not in that call
+    } catch (...) {
+      delete c;
+      throw;
+    }
     *out = c;
     return NCPADJ_OK;
   } catch (const Error& e) {

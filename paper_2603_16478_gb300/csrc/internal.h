@@ -160,6 +160,10 @@ struct Ctx {
   DevBuf inv_mat, inv_work;  // workspace of ncpadj_dense_inverse
 };
 
+// looks up (and so loads) the static scratch of ncpadj_elastic_solve_noalloc on `device`, which
+// must be current; called by ncpadj_ctx_create (noalloc.cu)
+void noalloc_prepare(int device);
+
 // kernels launch helpers (kernels.cu)
 struct AdjointArgs;  // defined in kernels.cuh
 }  // namespace ncpadj

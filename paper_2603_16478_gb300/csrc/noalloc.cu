@@ -3,10 +3,14 @@
 // Some callers cannot let a library allocate device memory once they are running: programs
 // whose device memory is reserved up front by their own pool or allocator, and loops with hard
 // latency limits where a cudaMalloc (which may synchronise the device and take milliseconds) is
-// not acceptable.  For them this entry point keeps its one intermediate vector -- S P x of the
-// sparse-inverse product A^{-1} = P^T S^T S P -- in a static device array instead of the scene's
-// grow-on-demand workspace.  The caller still provides x and y; the scene's arrays were
-// allocated when the scene was created.
+// not acceptable.  For them this entry point keeps its two intermediate vectors -- x permuted to
+// elimination order, and S P x of the sparse-inverse product A^{-1} = P^T S^T S P -- in a static
+// device array instead of the scene's grow-on-demand workspace.  The caller still provides x and
+// y; the scene's arrays were allocated when the scene was created.
+//
+// The array lives in this file's own module.  CUDA loads a module's device memory lazily, when one
+// of its symbols is first used, so ncpadj_ctx_create looks the array up (noalloc_prepare): the
+// array is then allocated while the context is created, and the solve itself allocates nothing.
 #include <mutex>
 
 #include "internal.h"
@@ -15,9 +19,9 @@
 namespace ncpadj {
 namespace {
 
-// Largest scene (in vertices) this entry point accepts: the scratch holds one [n_verts][3]
-// float64 vector, 6 MiB.  Every GPU that loads this library holds the array until the process
-// exits.
+// Largest scene (in vertices) this entry point accepts: the scratch holds two [n_verts][3]
+// float64 vectors, 12 MiB.  Every GPU on which a context is created holds the array until the
+// process exits.
 constexpr int kNoAllocMaxVerts = 262144;
 __device__ __align__(256) double g_noalloc_scratch[2 * 3 * (size_t)kNoAllocMaxVerts];  // w, then x permuted
 
@@ -38,6 +42,12 @@ double* scratch_address(int device) {
 }
 
 }  // namespace
+
+void noalloc_prepare(int device) {
+  NCPADJ_REQUIRE(device >= 0 && device < kMaxDevices, "device ordinal out of range");
+  scratch_address(device);
+}
+
 }  // namespace ncpadj
 
 using namespace ncpadj;
@@ -53,7 +63,7 @@ extern "C" ncpadj_status ncpadj_elastic_solve_noalloc(ncpadj_ctx ctx, ncpadj_sce
                    "scene has " + std::to_string(S.nv) + " vertices; ncpadj_elastic_solve_noalloc supports at most " +
                        std::to_string(kNoAllocMaxVerts));
     NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
-    double* w = scratch_address(ctx->c.device);
+    double* w = scratch_address(ctx->c.device);  // looked up by ncpadj_ctx_create: no allocation here
     SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
