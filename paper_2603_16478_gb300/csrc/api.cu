@@ -366,6 +366,7 @@ struct Engine {
   bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
   int cap_block = 0;      // most contacts per capacitance block (0: the largest the direct inverse takes)
   float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr;
+  float2* zsplit = nullptr;  // double-float pairs of the Arnoldi matvec's input (mixed)
   // the capacitance is block-diagonal by scene (contacts of different meshes share no ancestor
   // in the elimination forest): one dense block per scene that has contacts
   std::vector<int> blk_c0, blk_nc, blk_scene;  // first contact, contacts and mesh of each block
@@ -490,6 +491,10 @@ struct Engine {
       x32 = S.vec32.as<float>();
       w32 = x32 + N;
       Cm32 = w32 + N;
+    }
+    if (mixed) {
+      S.xsplit.ensure(sizeof(float2) * (size_t)N + 64);
+      zsplit = S.xsplit.as<float2>();
     }
     S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
     S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
@@ -750,9 +755,16 @@ struct Engine {
     }
   }
 
-  void matvec(const double* xin, double* yout) {
-    if (mixed) launch_bsr_spmv32(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), xin, yout, st);
-    else launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), xin, yout, st);
+  // yout = B xin for the assembled matrix (rows of scenes outside mk skipped); mixed: FP32 values
+  // with double-float products and sums (xin split into zsplit first)
+  void matvec(const double* xin, double* yout, const Mask& mk = Mask{}) {
+    if (mixed) {
+      launch_split(N, xin, zsplit, st);
+      launch_bsr_spmv_ff(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), zsplit, yout, 0,
+                         nullptr, st, mk);
+    } else {
+      launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), xin, yout, st, mk);
+    }
   }
   void ainv(const double* xin, double* yout) {
     if (mixed) launch_ainv32(sinv, xin, x32, w32, yout, st);
@@ -836,7 +848,7 @@ struct Engine {
                                 (uintptr_t)S.cap.p, (uintptr_t)S.vec32.p, (uintptr_t)S.cdata.p, (uintptr_t)S.bsr32.p,
                                 (uintptr_t)S.bsr64.p, (uintptr_t)S.xpos.p, (uintptr_t)S.gstep.p,
                                 (uintptr_t)flexible_gmres(), (uintptr_t)S.fgmres.p,
-                                (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size()};
+                                (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size(), (uintptr_t)S.xsplit.p};
     for (size_t b = 0; b < blk_c0.size(); ++b) {
       k.push_back((uintptr_t)blk_c0[b]);
       k.push_back((uintptr_t)blk_nc[b]);
@@ -859,9 +871,14 @@ struct Engine {
     if (mixed) launch_sinv_half2_32(sinv, w32, w, st);
     else launch_sinv_half2(sinv, t3, w, st);
     if (flexible_gmres()) launch_copy_idx(N, w, S.fgmres.as<double>(), N, jp, st);  // Z_j = z
-    // V_{j+1} = A z
-    launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
-                        mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st);
+    // V_{j+1} = A z (mixed: FP32 values, double-float products and sums)
+    if (mixed) {
+      launch_split(N, w, zsplit, st);
+      launch_bsr_spmv_ff(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), zsplit, V, N, jp, st);
+    } else {
+      launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), nullptr, w, V, N,
+                          jp, st);
+    }
     launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs, st);
     launch_multi_axpy_idx(N, V, N, jp, gs, V, st);
     launch_multi_dot_idx(N, m, V, N, jp, false, partial, gs + (m + 1), st);
@@ -946,9 +963,14 @@ struct Engine {
         else launch_sinv_half2(sinv, t3, w, st, mk);
       }
     }
-    launch_seg_copy_step(T, w, false, Z, true, N, jp, m, bb.act, nullptr, st);  // Z_j = P^{-1} V_j
-    launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
-                        mixed ? S.bsr32.as<float>() : nullptr, w, V, N, jp, st, mk);  // V_{j+1} = A Z_j
+    // Z_j = P^{-1} V_j (and its double-float pairs for the mixed product); V_{j+1} = A Z_j
+    launch_seg_copy_step(T, w, false, Z, true, N, jp, m, bb.act, nullptr, st, mixed ? zsplit : nullptr);
+    if (mixed)
+      launch_bsr_spmv_ff(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), zsplit, V, N, jp, st,
+                         mk);
+    else
+      launch_bsr_spmv_idx(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), nullptr, w, V, N,
+                          jp, st, mk);
     const int g2 = m + 1, gn = 2 * (m + 1);
     launch_seg_dot_step(T, V, N, jp, m, false, bb.act, bb.partial, bb.cnt, bb.K, bb.gsb, bb.gstride, 0, st);
     launch_seg_axpy_step(T, V, N, jp, m, bb.act, bb.gsb, bb.gstride, 0, st);
@@ -1049,10 +1071,7 @@ struct Engine {
       // end of the cycle: x_s += Z_s y_s, true residual, restart or stop, scene by scene
       launch_seg_backsolve(ns, m, bb.cyc, bb.kk, bb.H, bb.g, bb.y, st);
       launch_seg_combine(T, Z, N, m, bb.cyc, bb.kk, bb.y, x, st);
-      if (mixed)
-        launch_bsr_spmv32(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr32.as<float>(), x, w, st, mcyc);
-      else
-        launch_bsr_spmv(nv, S.row_ptr.as<int32_t>(), S.col.as<int32_t>(), S.bsr64.as<double>(), x, w, st, mcyc);
+      matvec(x, w, mcyc);
       launch_seg_resid(T, b, w, bb.cyc, r, st);
       launch_seg_sq(T, r, bb.cyc, bb.partial, bb.cnt, bb.K, m + 2, bb.rr, st);
       launch_seg_restart(ns, m, false, bb.cyc, bb.act, bb.done, bb.kk, bb.iters, max_iters, bb.rr, bb.bnorm, bb.tol,

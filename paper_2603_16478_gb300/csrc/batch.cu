@@ -11,6 +11,7 @@
 // a step, the preconditioner and the matrix product included, skips its rows.
 #include <math.h>
 
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace ncpadj {
@@ -126,18 +127,23 @@ __global__ void __launch_bounds__(256) k_seg_normalize_step(SegTiles T, double* 
 }
 
 // dst = src, or dst = d .* src when d is given, on the tiles of active scenes; src is taken at
-// src + j ld when src_idx, dst at dst + j ld when dst_idx (j = *jp)
+// src + j ld when src_idx, dst at dst + j ld when dst_idx (j = *jp); with split, also the
+// double-float pairs of dst (the input of the double-float block product)
 __global__ void __launch_bounds__(256) k_seg_copy_step(SegTiles T, const double* __restrict__ src, int src_idx,
                                                        double* __restrict__ dst, int dst_idx, long ld,
                                                        const int* __restrict__ jp, int m, const int* __restrict__ act,
-                                                       const double* __restrict__ d) {
+                                                       const double* __restrict__ d, float2* __restrict__ split) {
   const int j = *jp;
   if (j >= m) return;
   const int t = blockIdx.x, s = T.scene[t];
   if (!act[s]) return;
   if (src_idx) src += (size_t)j * ld;
   if (dst_idx) dst += (size_t)j * ld;
-  for (int i = T.beg[t] + (int)threadIdx.x; i < T.end[t]; i += blockDim.x) dst[i] = d ? d[i] * src[i] : src[i];
+  for (int i = T.beg[t] + (int)threadIdx.x; i < T.end[t]; i += blockDim.x) {
+    const double v = d ? d[i] * src[i] : src[i];
+    dst[i] = v;
+    if (split) split[i] = df_split(v);
+  }
 }
 
 // The Hessenberg column of step j of every active scene (first- plus second-pass Gram-Schmidt
@@ -368,9 +374,9 @@ void launch_seg_normalize_step(const SegTiles& T, double* V, long ld, const int*
   k_seg_normalize_step<<<T.n, 256, 0, s>>>(T, V, ld, jp, m, act, gsb, gstride, noff);
 }
 void launch_seg_copy_step(const SegTiles& T, const double* src, bool src_idx, double* dst, bool dst_idx, long ld,
-                          const int* jp, int m, const int* act, const double* d, cudaStream_t s) {
+                          const int* jp, int m, const int* act, const double* d, cudaStream_t s, float2* split) {
   g_launches += 1;
-  k_seg_copy_step<<<T.n, 256, 0, s>>>(T, src, src_idx ? 1 : 0, dst, dst_idx ? 1 : 0, ld, jp, m, act, d);
+  k_seg_copy_step<<<T.n, 256, 0, s>>>(T, src, src_idx ? 1 : 0, dst, dst_idx ? 1 : 0, ld, jp, m, act, d, split);
 }
 void launch_seg_givens(int ns, int* jp, int m, int* act, const double* gsb, int gstride, double* H, double* cs,
                        double* sn, double* g, int* kk, int* iters, const double* tol, int maxit, int* nact,

@@ -122,6 +122,7 @@ struct Scene {
   const int8_t* model_ptr() const { return model_any ? static_cast<const int8_t*>(model.p) : nullptr; }
   DevBuf actf;                    // forward: f_ext + actuation force [3 nv]; adjoint: dL/da staging
   DevBuf vec32;                   // FP32 scratch of the mixed path
+  DevBuf xsplit;                  // float2 [3 nv]: double-float pairs of the Arnoldi matvec's input (mixed)
   int* flags_host = nullptr;      // pinned
   double* scal_host = nullptr;    // pinned
   double* gs_host = nullptr;      // pinned: Gram-Schmidt coefficients of one GMRES iteration

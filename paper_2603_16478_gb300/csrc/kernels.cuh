@@ -172,6 +172,12 @@ void launch_bsr_spmv(int nv, const int32_t* row_ptr, const int32_t* col, const d
                      const double* x, double* y, cudaStream_t s, const Mask& mk = Mask{});
 void launch_bsr_spmv32(int nv, const int32_t* row_ptr, const int32_t* col, const float* val,
                        const double* x, double* y, cudaStream_t s, const Mask& mk = Mask{});
+// y = B x for FP32 block values with x as double-float pairs (hi, lo) [3 nv], double-float
+// arithmetic (FP64-class accuracy) on the FP32 pipes; with jp, y is V_{j+1} = ybase + (*jp + 1) yld
+void launch_bsr_spmv_ff(int nv, const int32_t* rp, const int32_t* col, const float* val, const float2* x2,
+                        double* ybase, long yld, const int* jp, cudaStream_t s, const Mask& mk = Mask{});
+// x2 = double-float pairs of x (n values)
+void launch_split(int n, const double* x, float2* x2, cudaStream_t s);
 // inverse of the scalar diagonal of the block matrix
 void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
                      cudaStream_t s);
@@ -316,9 +322,11 @@ void launch_seg_axpy_step(const SegTiles& T, double* V, long ld, const int* jp, 
                           const double* gsb, int gstride, int goff, cudaStream_t s);
 void launch_seg_normalize_step(const SegTiles& T, double* V, long ld, const int* jp, int m, const int* act,
                                const double* gsb, int gstride, int noff, cudaStream_t s);
-//   dst = src or d .* src (d not null), src / dst offset by j ld when *_idx
+//   dst = src or d .* src (d not null), src / dst offset by j ld when *_idx; with split (not null)
+//   also split[i] = the double-float pair of dst[i]
 void launch_seg_copy_step(const SegTiles& T, const double* src, bool src_idx, double* dst, bool dst_idx, long ld,
-                          const int* jp, int m, const int* act, const double* d, cudaStream_t s);
+                          const int* jp, int m, const int* act, const double* d, cudaStream_t s,
+                          float2* split = nullptr);
 //   Hessenberg column j, Givens rotations and stopping test of every active scene; nact[j] (host
 //   mapped) = scenes still active; *jp = j + 1
 void launch_seg_givens(int ns, int* jp, int m, int* act, const double* gsb, int gstride, double* H, double* cs,

@@ -12,6 +12,7 @@
 
 #include <cooperative_groups.h>
 
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace ncpadj {
@@ -67,6 +68,58 @@ __global__ void __launch_bounds__(256) k_bsr_spmv_hw(int nv, const int32_t* __re
     y[3 * (size_t)v + 1] = a1;
     y[3 * (size_t)v + 2] = a2;
   }
+}
+
+// The same product for FP32 block values with x given as double-float pairs x2 = (hi, lo): every
+// product and sum in double-float on the FP32 pipes (about 48 significant bits, FP64-class
+// accuracy), y in FP64.  The FP64 accumulation above spends 9 FMAs and 9 conversions per block
+// on this part's slow FP64 pipe, which bounds that kernel far below the memory rate.
+__global__ void __launch_bounds__(256) k_bsr_spmv_ff(int nv, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                     const float2* __restrict__ x2, double* __restrict__ y,
+                                                     const int* __restrict__ jp, long yld, Mask mk) {
+  if (jp) y += (size_t)(*jp + 1) * yld;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = t >> 4, l = t & 15;
+  const bool live = v < nv && mk.on(v);  // skipped, not returned: the half-warps share shuffles
+  float h0 = 0.f, h1 = 0.f, h2 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f;
+  if (live) {
+    const int pe = rp[v + 1];
+    for (int p = rp[v] + l; p < pe; p += 16) {
+      const int c = col[p];
+      const float* B = val + 9 * (size_t)p;
+      const float2 a = x2[3 * (size_t)c], b = x2[3 * (size_t)c + 1], d = x2[3 * (size_t)c + 2];
+      df_fma(B[0], a.x, a.y, h0, l0);
+      df_fma(B[1], b.x, b.y, h0, l0);
+      df_fma(B[2], d.x, d.y, h0, l0);
+      df_fma(B[3], a.x, a.y, h1, l1);
+      df_fma(B[4], b.x, b.y, h1, l1);
+      df_fma(B[5], d.x, d.y, h1, l1);
+      df_fma(B[6], a.x, a.y, h2, l2);
+      df_fma(B[7], b.x, b.y, h2, l2);
+      df_fma(B[8], d.x, d.y, h2, l2);
+    }
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const float a0 = __shfl_xor_sync(0xffffffffu, h0, o), b0 = __shfl_xor_sync(0xffffffffu, l0, o);
+    const float a1 = __shfl_xor_sync(0xffffffffu, h1, o), b1 = __shfl_xor_sync(0xffffffffu, l1, o);
+    const float a2 = __shfl_xor_sync(0xffffffffu, h2, o), b2 = __shfl_xor_sync(0xffffffffu, l2, o);
+    df_add(h0, l0, a0, b0);
+    df_add(h1, l1, a1, b1);
+    df_add(h2, l2, a2, b2);
+  }
+  if (live && l == 0) {
+    y[3 * (size_t)v] = df_to_double(h0, l0);
+    y[3 * (size_t)v + 1] = df_to_double(h1, l1);
+    y[3 * (size_t)v + 2] = df_to_double(h2, l2);
+  }
+}
+
+// x2[i] = (hi, lo) of x[i]: the double-float input of k_bsr_spmv_ff
+__global__ void k_split(int n, const double* __restrict__ x, float2* __restrict__ x2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x2[i] = df_split(x[i]);
 }
 
 // x[k] = sum_j B[piv[k]][j] y[piv[j]]: the Gauss-Jordan result B applied to y with both permutations.
@@ -499,6 +552,15 @@ void launch_bsr_spmv32(int nv, const int32_t* rp, const int32_t* col, const floa
                        cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   k_bsr_spmv_hw<float><<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x, y, nullptr, 0, mk);
+}
+void launch_bsr_spmv_ff(int nv, const int32_t* rp, const int32_t* col, const float* val, const float2* x2,
+                        double* ybase, long yld, const int* jp, cudaStream_t s, const Mask& mk) {
+  g_launches += 1;
+  k_bsr_spmv_ff<<<nblk(16L * nv, 256), 256, 0, s>>>(nv, rp, col, val, x2, ybase, jp, yld, mk);
+}
+void launch_split(int n, const double* x, float2* x2, cudaStream_t s) {
+  g_launches += 1;
+  k_split<<<nblk(n, 256), 256, 0, s>>>(n, x, x2);
 }
 void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const float* val32, double* dinv,
                      cudaStream_t s) {
