@@ -250,13 +250,21 @@ typedef struct {
  *              paths per product), preconditioned by the exact inverses of contiguous, nearly
  *              equal groups of its contacts in the given order; the outer solve becomes flexible
  *              GMRES (the preconditioner varies).  Order the contacts spatially (e.g. by plane,
- *              then by position) so that groups are compact. */
+ *              then by position) so that groups are compact.
+ *   cap_drop   contacts whose rows of the capacitance stand within this of the identity are left
+ *              out of it: contact c is dropped when h^2 |K_c|_F (A^{-1})_{v_c v_c} <= cap_drop
+ *              (default 1e-2; 0 keeps every contact).  A separating contact, whose blocks are
+ *              ~eps^2/delta_n^2, scores far below that, an active one far above.  The Woodbury
+ *              preconditioner is then exact for the kept contacts; the dropped ones stay in the
+ *              matrix, so the result keeps its tolerance.  stats.capacitance_dim counts the kept
+ *              rows. */
 typedef struct {
   double eps, rtol;
   int32_t max_iters, gmres_restart;
   int32_t precision, precond, solver, memory;
   int32_t cap_precision;
   int32_t cap_block;
+  double cap_drop;
 } ncpadj_options;
 void ncpadj_options_default(ncpadj_options* opt);
 

@@ -79,7 +79,7 @@ class _Grads(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("eps", C.c_double), ("rtol", C.c_double), ("max_iters", C.c_int32), ("gmres_restart", C.c_int32),
                 ("precision", C.c_int32), ("precond", C.c_int32), ("solver", C.c_int32), ("memory", C.c_int32),
-                ("cap_precision", C.c_int32), ("cap_block", C.c_int32)]
+                ("cap_precision", C.c_int32), ("cap_block", C.c_int32), ("cap_drop", C.c_double)]
 
 
 class _Stats(C.Structure):
@@ -309,7 +309,7 @@ def _bindings_ref(bindings: Optional[Bindings]):
 
 def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4,
                  rtol=1e-8, max_iters=2000, restart=64, precision="fp64", cap_precision="fp64", precond="woodbury",
-                 solver="auto", cap_block=0,
+                 solver="auto", cap_block=0, cap_drop=1e-2,
                  memory="device", outputs: Optional[dict] = None, stream=None, want=("dL_dq_prev", "dL_dv_prev",
                  "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z"), bindings: Optional[Bindings] = None):
     """One adjoint step through the C-ABI.  Returns (grads dict of tensors, stats dict).
@@ -353,6 +353,7 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     opt.precision = PRECISION[precision]
     opt.cap_precision = PRECISION[cap_precision]
     opt.cap_block = int(cap_block)
+    opt.cap_drop = float(cap_drop)
     opt.precond = PRECOND[precond]
     opt.solver = SOLVER[solver]
     opt.memory = MEMORY[memory]
@@ -370,13 +371,15 @@ _GRAD_FIELDS = ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_d
                 "dL_dbinding_target", "dL_dcompliance")
 
 
-def _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, solver, memory, cap_block):
+def _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, solver, memory, cap_block,
+             cap_drop=1e-2):
     opt = _Options()
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
     opt.precision = PRECISION[precision]
     opt.cap_precision = PRECISION[cap_precision]
     opt.cap_block = int(cap_block)
+    opt.cap_drop = float(cap_drop)
     opt.precond = PRECOND[precond]
     opt.solver = SOLVER[solver]
     opt.memory = MEMORY[memory]
@@ -396,7 +399,7 @@ class BatchCall:
 
     def __init__(self, scene: Scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4, rtol=1e-8,
                  max_iters=2000, restart=64, precision="fp64", cap_precision="fp64", precond="woodbury",
-                 cap_block=0, memory="device", outputs=None,
+                 cap_block=0, cap_drop=1e-2, memory="device", outputs=None,
                  want=("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z")):
         lib = self.lib = scene.lib
         self.scene = scene
@@ -434,7 +437,7 @@ class BatchCall:
             self.sds[s] = _Seed(_ptr(dL_dq[s]), _ptr(dL_dv[s]) if dL_dv is not None else None)
             self.grs[s] = _Grads(*[_ptr(o.get(k)) for k in _GRAD_FIELDS])
         self.opt = _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, "gmres", memory,
-                            cap_block)
+                            cap_block, cap_drop)
         self.stats = (_Stats * ns)()
 
     def run(self, stream=None):

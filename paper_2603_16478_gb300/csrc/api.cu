@@ -369,6 +369,14 @@ struct Engine {
   float2* zsplit = nullptr;  // double-float pairs of the Arnoldi matvec's input (mixed)
   // the capacitance is block-diagonal by scene (contacts of different meshes share no ancestor
   // in the elimination forest): one dense block per scene that has contacts
+  // The contacts of the Woodbury capacitance (select_capacitance): every contact except those whose
+  // capacitance rows are within cap_drop of the identity; the assembled matrix and the contractions
+  // always take every contact.
+  int cnc = 0;
+  const int32_t* cvx = nullptr;  // [cnc] vertex ids
+  const double* cfr = nullptr;   // [cnc][9] frames
+  const double* ccd = nullptr;   // [cnc][12] K, k_mu
+  double cap_drop = 0.0;
   std::vector<int> blk_c0, blk_nc, blk_scene;  // first contact, contacts and mesh of each block
   std::vector<size_t> blk_moff, blk_doff;
   // batch scenes: one restarted GMRES per mesh, all meshes advanced by the same launches
@@ -390,24 +398,25 @@ struct Engine {
   double inner_rtol = 1e-6;
   int inner_iters = 0;
 
+  // the capacitance blocks over the contacts of the capacitance set (cnc of them)
   void plan_blocks() {
     blk_c0.clear();
     blk_nc.clear();
     blk_scene.clear();
-    if (nc == 0) return;
+    if (cnc == 0) return;
     std::vector<int> bsc;  // mesh of each block
     if (S.n_scenes == 1) {
       blk_c0.push_back(0);
-      blk_nc.push_back(nc);
+      blk_nc.push_back(cnc);
       bsc.push_back(0);
     } else {
-      S.cscene.ensure(sizeof(int32_t) * (size_t)nc + 64);
-      launch_contact_scene(nc, in.cvertex, S.scene_of_vertex.as<int32_t>(), S.cscene.as<int32_t>(), st);
-      std::vector<int32_t> cs(nc);
-      NCPADJ_CUDA_TRY(cudaMemcpyAsync(cs.data(), S.cscene.as<int32_t>(), sizeof(int32_t) * nc, cudaMemcpyDeviceToHost,
-                                      st));
+      S.cscene.ensure(sizeof(int32_t) * (size_t)cnc + 64);
+      launch_contact_scene(cnc, cvx, S.scene_of_vertex.as<int32_t>(), S.cscene.as<int32_t>(), st);
+      std::vector<int32_t> cs(cnc);
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(cs.data(), S.cscene.as<int32_t>(), sizeof(int32_t) * cnc,
+                                      cudaMemcpyDeviceToHost, st));
       NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
-      for (int c = 0; c < nc; ++c) {
+      for (int c = 0; c < cnc; ++c) {
         NCPADJ_REQUIRE(c == 0 || cs[c] >= cs[c - 1], "contacts of a batch scene must be grouped by scene");
         if (c == 0 || cs[c] != cs[c - 1]) {
           blk_c0.push_back(c);
@@ -478,35 +487,14 @@ struct Engine {
     flags = S.flags.as<int>();
   }
 
-  void workspace(int nc_, int m_, int precond_) {
-    nc = nc_;
-    m = m_;
-    precond = precond_;
-    ncap = 3 * nc;
-    plan_blocks();
-    if (mixed) S.bsr32.ensure(sizeof(float) * 9 * (size_t)S.nb);
-    else S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
+  // capacitance matrices, the inverse's scratch and the inner solve's basis for the current plan
+  void alloc_capacitance() {
     if (mixed || cap_fp32) {
       S.vec32.ensure(sizeof(float) * (2 * (size_t)N + cap_elems + 64));
       x32 = S.vec32.as<float>();
       w32 = x32 + N;
       Cm32 = w32 + N;
     }
-    if (mixed) {
-      S.xsplit.ensure(sizeof(float2) * (size_t)N + 64);
-      zsplit = S.xsplit.as<float2>();
-    }
-    S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
-    S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
-    const size_t nvec = 9, ncv = 3 * (size_t)std::max(ncap, 1);
-    S.vecs.ensure(sizeof(double) * (nvec * N + ncv + 64));
-    // (m + 1) basis vectors and the coefficient slots; at least 7 vectors (BiCGSTAB's)
-    S.gmres.ensure(sizeof(double) * ((size_t)std::max(m + 1, 7) * N + 3 * (size_t)(m + 1) + 16));
-    if (S.red.bytes < dot_scratch_bytes()) {  // counters of the fused dot product start at zero
-      S.red.ensure(dot_scratch_bytes());
-      NCPADJ_CUDA_TRY(cudaMemset(S.red.p, 0, dot_scratch_bytes()));
-    }
-    S.scal.ensure(sizeof(double) * (64 + (size_t)m + 8));
     if (nc && precond == NCPADJ_PRECOND_WOODBURY) {
       S.cap.ensure(sizeof(double) * (cap_elems + ds_elems + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
       int nmax = 0;
@@ -526,6 +514,36 @@ struct Engine {
                                          2 * (size_t)(kInnerRestart + 2) + 64));
       }
     }
+  }
+
+  void workspace(int nc_, int m_, int precond_) {
+    nc = nc_;
+    m = m_;
+    precond = precond_;
+    ncap = 3 * nc;
+    S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
+    cnc = nc;  // until select_capacitance: every contact (the largest plan)
+    cvx = in.cvertex;
+    cfr = in.frame;
+    ccd = S.cdata.as<double>();
+    plan_blocks();
+    if (mixed) S.bsr32.ensure(sizeof(float) * 9 * (size_t)S.nb);
+    else S.bsr64.ensure(sizeof(double) * 9 * (size_t)S.nb);
+    if (mixed) {
+      S.xsplit.ensure(sizeof(float2) * (size_t)N + 64);
+      zsplit = S.xsplit.as<float2>();
+    }
+    S.tetdata.ensure(sizeof(double) * 18 * (size_t)nt);
+    const size_t nvec = 9, ncv = 3 * (size_t)std::max(ncap, 1);
+    S.vecs.ensure(sizeof(double) * (nvec * N + ncv + 64));
+    // (m + 1) basis vectors and the coefficient slots; at least 7 vectors (BiCGSTAB's)
+    S.gmres.ensure(sizeof(double) * ((size_t)std::max(m + 1, 7) * N + 3 * (size_t)(m + 1) + 16));
+    if (S.red.bytes < dot_scratch_bytes()) {  // counters of the fused dot product start at zero
+      S.red.ensure(dot_scratch_bytes());
+      NCPADJ_CUDA_TRY(cudaMemset(S.red.p, 0, dot_scratch_bytes()));
+    }
+    S.scal.ensure(sizeof(double) * (64 + (size_t)m + 8));
+    alloc_capacitance();
     if (flexible_gmres() || batch_mode) S.fgmres.ensure(sizeof(double) * (size_t)(m + 1) * N);
     if (batch_mode) {
       const int ns = S.n_scenes;
@@ -604,20 +622,59 @@ struct Engine {
     NCPADJ_CUDA_TRY(cudaGetLastError());
   }
 
+  // The capacitance set: contact c stays out when h^2 |K_c|_F (A_s^{-1})_{v_c v_c} <= cap_drop, i.e.
+  // when its rows of I + h^2 K^T D stand within about cap_drop of the identity (a separating
+  // contact: K_c ~ eps^2 / delta_n^2).  The preconditioner is then the exact Woodbury inverse of
+  // A + h^2 J_k^T K_k J_k over the kept contacts; the left-out ones stay in the matrix, and the
+  // Krylov solve absorbs them (flexible GMRES: the result keeps its tolerance).
+  void select_capacitance() {
+    cnc = nc;
+    cvx = in.cvertex;
+    cfr = in.frame;
+    ccd = S.cdata.as<double>();
+    if (!(cap_drop > 0.0) || nc == 0) return;
+    S.capsel.ensure(sizeof(double) * (size_t)nc * 22 + sizeof(int32_t) * 2 * (size_t)nc + 256);
+    double* score = S.capsel.as<double>();
+    double* fr = score + nc;
+    double* cd = fr + 9 * (size_t)nc;
+    int32_t* idx = reinterpret_cast<int32_t*>(cd + 12 * (size_t)nc);
+    int32_t* vx = idx + nc;
+    launch_contact_score(nc, in.cvertex, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_val.as<double>(),
+                         S.cdata.as<double>(), h, score, st);
+    std::vector<double> sh(nc);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(sh.data(), score, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int32_t> keep;
+    keep.reserve(nc);
+    for (int c = 0; c < nc; ++c)
+      if (!(sh[c] <= cap_drop)) keep.push_back(c);  // NaN scores stay in
+    if ((int)keep.size() == nc) return;
+    cnc = (int)keep.size();
+    if (cnc) {
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(idx, keep.data(), sizeof(int32_t) * cnc, cudaMemcpyHostToDevice, st));
+      launch_gather_contacts(cnc, idx, in.cvertex, in.frame, S.cdata.as<double>(), vx, fr, cd, st);
+    }
+    cvx = vx;
+    cfr = fr;
+    ccd = cd;
+  }
+
   void setup_precond() {
     if (precond == NCPADJ_PRECOND_JACOBI)
       launch_diag_inv(nv, S.diag_slot.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
                       mixed ? S.bsr32.as<float>() : nullptr, dinv, st);
     if (precond == NCPADJ_PRECOND_WOODBURY && nc) {
+      select_capacitance();
+      plan_blocks();
+      alloc_capacitance();
       for (size_t k = 0; k < blk_c0.size(); ++k) {
         const int c0 = blk_c0[k], m_ = blk_nc[k], n_ = 3 * m_;
         double* Cb = Cm + blk_moff[k];
         double* Db = Ds + blk_doff[k];
         int32_t* pb = piv + 3 * c0;
-        launch_delassus(m_, in.cvertex + c0, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
+        launch_delassus(m_, cvx + c0, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
                         S.St_val.as<double>(), Db, st);
-        launch_cap_form(m_, Db, in.frame + 9 * (size_t)c0, S.cdata.as<double>() + 12 * (size_t)c0, h, transpose, Cb,
-                        st);
+        launch_cap_form(m_, Db, cfr + 9 * (size_t)c0, ccd + 12 * (size_t)c0, h, transpose, Cb, st);
         NCPADJ_CUDA_TRY(cudaGetLastError());
         if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
         bool ok;
@@ -653,9 +710,9 @@ struct Engine {
     float* wf = mixed ? x32 : nullptr;
     if (mixed) NCPADJ_CUDA_TRY(cudaMemsetAsync(wf, 0, sizeof(float) * N, st));
     else NCPADJ_CUDA_TRY(cudaMemsetAsync(w64, 0, sizeof(double) * N, st));
-    launch_path_scatter(m_, in.cvertex + c0, ip, sinv, in.frame + 9 * (size_t)c0, yseg, 1.0, w64, wf, st);
-    launch_path_gather(m_, in.cvertex + c0, ip, sinv, w64, wf, in.frame + 9 * (size_t)c0,
-                       S.cdata.as<double>() + 12 * (size_t)c0, transpose, out_seg, st);
+    launch_path_scatter(m_, cvx + c0, ip, sinv, cfr + 9 * (size_t)c0, yseg, 1.0, w64, wf, st);
+    launch_path_gather(m_, cvx + c0, ip, sinv, w64, wf, cfr + 9 * (size_t)c0, ccd + 12 * (size_t)c0, transpose,
+                       out_seg, st);
     launch_axpby(3 * m_, 1.0, yseg, h * h, out_seg, out_seg, st);
   }
 
@@ -789,15 +846,14 @@ struct Engine {
         // w = S P x once; J A^{-1} x needs A^{-1} x at the contact vertices only, i.e. rows of S^T
         // (elimination-tree paths) against w; the correction enters w along the same paths; then
         // y = P^T S^T w.  One full product with S and one with S^T per apply instead of two each.
-        if (nc == 0) {
+        if (cnc == 0) {
           ainv(xin, yout);
           break;
         }
         const int32_t* ip = S.iperm.as<int32_t>();
         if (mixed) launch_sinv_half1_32(sinv, xin, w32, st);
         else launch_sinv_half1(sinv, xin, t3, st);
-        launch_path_gather(nc, in.cvertex, ip, sinv, t3, mixed ? w32 : nullptr, in.frame, S.cdata.as<double>(),
-                           transpose, sc, st);
+        launch_path_gather(cnc, cvx, ip, sinv, t3, mixed ? w32 : nullptr, cfr, ccd, transpose, sc, st);
         {
           size_t ks = 0;  // super-blocks in contact order
           for (size_t k = 0; k < blk_c0.size();) {
@@ -815,7 +871,7 @@ struct Engine {
             ++k;
           }
         }
-        launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st);
+        launch_path_scatter(cnc, cvx, ip, sinv, cfr, tc, -h * h, t3, mixed ? w32 : nullptr, st);
         if (mixed) launch_sinv_half2_32(sinv, w32, yout, st);
         else launch_sinv_half2(sinv, t3, yout, st);
       }
@@ -836,14 +892,18 @@ struct Engine {
     const bool inner = !sup_c0.empty() && precond == NCPADJ_PRECOND_WOODBURY && nc > 0;
     const bool fp32 = (mixed && (precond == NCPADJ_PRECOND_WOODBURY || precond == NCPADJ_PRECOND_ELASTIC)) ||
                       (cap_fp32 && precond == NCPADJ_PRECOND_WOODBURY && nc > 0);
+    // contacts left out of the capacitance: the preconditioner is not the matrix's inverse even in
+    // exact arithmetic, but it is one fixed map, so plain right-preconditioned GMRES stays exact;
+    // flexible GMRES is kept for the rounding cases above only
     return inner || fp32;
   }
   bool step_graph_possible() const {
-    return precond == NCPADJ_PRECOND_WOODBURY && nc > 0 && sup_c0.empty();
+    return precond == NCPADJ_PRECOND_WOODBURY && cnc > 0 && sup_c0.empty();
   }
   std::vector<uintptr_t> step_key() const {
     std::vector<uintptr_t> k = {(uintptr_t)nc, (uintptr_t)m, (uintptr_t)N, (uintptr_t)mixed, (uintptr_t)cap_fp32,
-                                (uintptr_t)transpose, (uintptr_t)in.cvertex, (uintptr_t)in.frame,
+                                (uintptr_t)transpose, (uintptr_t)cvx, (uintptr_t)cfr, (uintptr_t)ccd,
+                                (uintptr_t)cnc,
                                 (uintptr_t)S.gmres.p, (uintptr_t)S.vecs.p, (uintptr_t)S.red.p, (uintptr_t)S.scal.p,
                                 (uintptr_t)S.cap.p, (uintptr_t)S.vec32.p, (uintptr_t)S.cdata.p, (uintptr_t)S.bsr32.p,
                                 (uintptr_t)S.bsr64.p, (uintptr_t)S.xpos.p, (uintptr_t)S.gstep.p,
@@ -859,15 +919,14 @@ struct Engine {
     const int32_t* ip = S.iperm.as<int32_t>();
     // z = P^{-1} V_j into w (Woodbury, as in apply_precond)
     launch_sinv_half1_idx(sinv, V, N, jp, mixed ? nullptr : t3, mixed ? w32 : nullptr, st);
-    launch_path_gather(nc, in.cvertex, ip, sinv, t3, mixed ? w32 : nullptr, in.frame, S.cdata.as<double>(), transpose,
-                       sc, st);
+    launch_path_gather(cnc, cvx, ip, sinv, t3, mixed ? w32 : nullptr, cfr, ccd, transpose, sc, st);
     for (size_t k = 0; k < blk_c0.size(); ++k) {
       const size_t o = 3 * (size_t)blk_c0[k];
       const int n_ = 3 * blk_nc[k];
       if (mixed || cap_fp32) launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
       else launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
     }
-    launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st);
+    launch_path_scatter(cnc, cvx, ip, sinv, cfr, tc, -h * h, t3, mixed ? w32 : nullptr, st);
     if (mixed) launch_sinv_half2_32(sinv, w32, w, st);
     else launch_sinv_half2(sinv, t3, w, st);
     if (flexible_gmres()) launch_copy_idx(N, w, S.fgmres.as<double>(), N, jp, st);  // Z_j = z
@@ -945,10 +1004,9 @@ struct Engine {
         break;
       default: {
         launch_sinv_half1_idx(sinv, V, N, jp, mixed ? nullptr : t3, mixed ? w32 : nullptr, st, mk);
-        if (precond == NCPADJ_PRECOND_WOODBURY && nc) {
+        if (precond == NCPADJ_PRECOND_WOODBURY && cnc) {
           const int32_t* ip = S.iperm.as<int32_t>();
-          launch_path_gather(nc, in.cvertex, ip, sinv, t3, mixed ? w32 : nullptr, in.frame, S.cdata.as<double>(),
-                             transpose, sc, st, mk);
+          launch_path_gather(cnc, cvx, ip, sinv, t3, mixed ? w32 : nullptr, cfr, ccd, transpose, sc, st, mk);
           for (size_t k = 0; k < blk_c0.size(); ++k) {
             const size_t o = 3 * (size_t)blk_c0[k];
             const int n_ = 3 * blk_nc[k];
@@ -957,7 +1015,7 @@ struct Engine {
             else
               launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st, bb.act, blk_scene[k]);
           }
-          launch_path_scatter(nc, in.cvertex, ip, sinv, in.frame, tc, -h * h, t3, mixed ? w32 : nullptr, st, mk);
+          launch_path_scatter(cnc, cvx, ip, sinv, cfr, tc, -h * h, t3, mixed ? w32 : nullptr, st, mk);
         }
         if (mixed) launch_sinv_half2_32(sinv, w32, w, st, mk);
         else launch_sinv_half2(sinv, t3, w, st, mk);
@@ -1351,6 +1409,7 @@ int pick_solver(int requested, int nc, const double* mu, bool host_mem, cudaStre
 void validate_options(const ncpadj_options& opt) {
   NCPADJ_REQUIRE(opt.eps > 0 && opt.rtol > 0 && opt.max_iters > 0 && opt.gmres_restart > 0 && opt.gmres_restart <= 512,
                  "bad options (eps, rtol, max_iters, gmres_restart)");
+  NCPADJ_REQUIRE(opt.cap_drop >= 0 && std::isfinite(opt.cap_drop), "bad option cap_drop (must be finite, >= 0)");
   NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 3, "bad precond/solver");
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
   NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
@@ -1451,6 +1510,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   E.mixed = opt.precision == NCPADJ_MIXED;
   E.cap_fp32 = opt.cap_precision == NCPADJ_MIXED;
   E.cap_block = opt.cap_block;
+  E.cap_drop = opt.cap_drop;
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, in.cvertex, in.region, nreg, st);  // before anything indexes with the ids
@@ -1579,7 +1639,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     stats->iterations = iters;
     stats->solver_used = solver;
     stats->n_contacts = nc;
-    stats->capacitance_dim = (opt.precond == NCPADJ_PRECOND_WOODBURY) ? 3 * nc : 0;
+    stats->capacitance_dim = (opt.precond == NCPADJ_PRECOND_WOODBURY) ? 3 * E.cnc : 0;
     stats->capacitance_blocks = (opt.precond == NCPADJ_PRECOND_WOODBURY && nc) ? (int32_t)E.blk_c0.size() : 0;
     stats->inner_iterations = E.inner_iters;
     stats->rel_residual = rel;
@@ -1916,6 +1976,7 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   // the Newton solves run in FP64; the capacitance (a preconditioner only) follows cap_precision
   E.cap_fp32 = opt.cap_precision == NCPADJ_MIXED;
   E.cap_block = opt.cap_block;
+  E.cap_drop = opt.cap_drop;
   int* flags = E.flags;
   NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, FLAG_COUNT * sizeof(int), st));
   check_contacts(S, nc, E.in.cvertex, E.in.region, nc ? ct->n_regions : 1, st);  // before any indexing
@@ -2167,6 +2228,7 @@ void ncpadj_options_default(ncpadj_options* o) {
   o->rtol = 1e-8;
   o->max_iters = 2000;
   o->gmres_restart = 64;
+  o->cap_drop = 1e-2;
   o->precision = NCPADJ_FP64;
   o->precond = NCPADJ_PRECOND_WOODBURY;
   o->solver = NCPADJ_SOLVER_AUTO;

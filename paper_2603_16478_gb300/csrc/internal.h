@@ -107,6 +107,7 @@ struct Scene {
   DevBuf c_in;                    // staging of contact inputs for host-memory calls
   DevBuf vecs;                    // Krylov vectors
   DevBuf cap, capw;               // capacitance matrix / inverse and scratch
+  DevBuf capsel;                  // the capacitance set: scores, kept indices, vertices, frames, K
   DevBuf red;                     // reduction scratch
   DevBuf flags;                   // int32 status flags
   DevBuf scal;                    // double scalars

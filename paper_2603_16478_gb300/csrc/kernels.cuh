@@ -240,6 +240,13 @@ void launch_path_scatter(int nc, const int32_t* cvertex, const int32_t* iperm, c
 // the same with FP32 values and intermediate (x32, w32 [nv][3] float scratch); y accumulated in FP64
 void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, double* y, cudaStream_t s);
 
+// score[c] = h^2 |K_c|_F (A_s^{-1})_{v_c v_c}: the distance of contact c's capacitance rows from the
+// identity (contacts far below 1 are left out of the capacitance set)
+void launch_contact_score(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
+                          const double* St_val, const double* cdata, double h, double* score, cudaStream_t s);
+// vertex, frame and K / k_mu of the contacts idx[0..nk) into compact arrays
+void launch_gather_contacts(int nk, const int32_t* idx, const int32_t* vertex, const double* frame,
+                            const double* cdata, int32_t* ov, double* of, double* oc, cudaStream_t s);
 // Delassus of the contact vertices: Ds[a][b] = (A_s^{-1})_{v_a v_b}
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
                      const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s);

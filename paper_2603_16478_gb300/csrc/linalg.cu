@@ -340,6 +340,42 @@ __global__ void k_delassus(int nc, const int32_t* __restrict__ cvertex, const in
   Ds[idx] = acc;
 }
 
+// score_c = h^2 |K_c|_F (A_s^{-1})_{v_c v_c}: how far contact c's rows of the capacitance
+// I + h^2 K^T D stand from the identity.  (A_s^{-1})_{vv} = |S[:, p(v)]|^2 is the squared norm of row
+// p(v) of S^T (the elimination-tree path of v's position); one warp per contact.
+__global__ void k_contact_score(int nc, const int32_t* __restrict__ cvertex, const int32_t* __restrict__ iperm,
+                                const int64_t* __restrict__ ptr, const double* __restrict__ val,
+                                const double* __restrict__ cdata, double h2, double* __restrict__ score) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= nc) return;
+  const int pv = iperm[cvertex[c]];
+  double acc = 0.0;
+  for (int64_t p = ptr[pv] + lane; p < ptr[pv + 1]; p += 32) acc += val[p] * val[p];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double* K = cdata + 12 * (size_t)c;
+    double kk = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) kk += K[i] * K[i];
+    score[c] = h2 * sqrt(kk) * acc;
+  }
+}
+
+// the contacts idx[0..nk) of the capacitance set, copied together: vertex, frame (9), K and k_mu (12)
+__global__ void k_gather_contacts(int nk, const int32_t* __restrict__ idx, const int32_t* __restrict__ vertex,
+                                  const double* __restrict__ frame, const double* __restrict__ cdata,
+                                  int32_t* __restrict__ ov, double* __restrict__ of, double* __restrict__ oc) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int c = idx[k];
+  ov[k] = vertex[c];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) of[9 * (size_t)k + i] = frame[9 * (size_t)c + i];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) oc[12 * (size_t)k + i] = cdata[12 * (size_t)c + i];
+}
+
 // C[3a+r][3b+s] = delta + h^2 Ds[a][b] sum_l K'_a[r][l] (F_a F_b^T)[l][s],  K' = K^T (adjoint) or K
 __global__ void k_cap_form(int nc, const double* __restrict__ Ds, const double* __restrict__ frame,
                            const double* __restrict__ cdata, double h2, int transpose, double* C) {
@@ -625,6 +661,16 @@ void launch_ainv32(const SinvArgs& a, const double* x, float* x32, float* w32, d
   (void)x32;
   launch_sinv_half1_32(a, x, w32, s);
   launch_sinv_half2_32(a, w32, y, s);
+}
+void launch_contact_score(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
+                          const double* St_val, const double* cdata, double h, double* score, cudaStream_t s) {
+  g_launches += 1;
+  if (nc) k_contact_score<<<nblk(32L * nc, 256), 256, 0, s>>>(nc, cvertex, iperm, St_ptr, St_val, cdata, h * h, score);
+}
+void launch_gather_contacts(int nk, const int32_t* idx, const int32_t* vertex, const double* frame,
+                            const double* cdata, int32_t* ov, double* of, double* oc, cudaStream_t s) {
+  g_launches += 1;
+  if (nk) k_gather_contacts<<<nblk(nk, 128), 128, 0, s>>>(nk, idx, vertex, frame, cdata, ov, of, oc);
 }
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
                      const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s) {

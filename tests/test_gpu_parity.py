@@ -277,3 +277,60 @@ def test_paper_smoothing_parity(pkg, ctx, k, precision):
         raise
     torch.cuda.synchronize()
     assert_parity(g, ref, 1e-6 if precision == "fp64" else 1e-3, st.nc)
+
+
+@functools.lru_cache(maxsize=None)
+def _separating_case():
+    """The cube 1 cm above the ground with a 2 cm detection margin: 25 contacts, all separating."""
+    import synth
+    pb = synth.cube_drop(margin=0.02)
+    sc = pb.scene
+    st = make_step(sc, sc.contacts(pb.q0))
+    s = st.forward(pb.q0, pb.v0)
+    assert s.residual < 1e-8 and st.nc == 25
+    return pb, st, s, pb.q0, pb.v0
+
+
+def _oracle_capacitance_scores(st, s, q_prev):
+    """h^2 |K_c|_F (A^{-1})_{v_c v_c} per contact from the oracle's own K_c (implicit differentiation of
+    the contact equations) and its elastic matrix A (a sparse LU solve per contact vertex)."""
+    import scipy.sparse.linalg as spla
+    from oracle.model import elastic_matrix
+    mu_L, _ = st.lame()
+    lu = spla.splu(elastic_matrix(st.mesh, st.mass, mu_L, st.h).tocsc())
+    K, _ = st.contact_blocks(s, q_prev)
+    out = []
+    for c in range(st.nc):
+        e = np.zeros(3 * st.mesh.n_verts)
+        e[3 * st.ct.vertex[c]] = 1.0
+        out.append(st.h ** 2 * np.linalg.norm(K[c]) * lu.solve(e)[3 * st.ct.vertex[c]])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_negligible_contacts_are_left_out_of_the_capacitance(pkg, ctx, precision):
+    """The capacitance set (cap_drop, reading C-12): a contact stays out when its capacitance rows are
+    within 1e-2 of the identity.  On the cube hovering 1 cm above the ground every contact
+    separates, but those with small slips keep friction rows of order eps^2 / |delta_f|^2: the kept
+    set is exactly the oracle's contacts scoring above 1e-2 (none within a factor 1.5 of it).  Every
+    contact of the resting cube is kept, and cap_drop = 0 keeps all.  Gradients match the oracle in
+    every case."""
+    tol, rtol = (1e-8, 1e-12) if precision == "fp64" else (1e-3, 1e-8)
+    kw = dict(rtol=rtol, precision=precision, cap_precision=precision)
+    case = _separating_case()
+    pb, st, s, q_prev, _ = case
+    score = _oracle_capacitance_scores(st, s, q_prev)
+    assert not np.any((score > 1e-2 / 1.5) & (score < 1.5e-2))
+    kept = int(np.sum(score > 1e-2))
+    assert 0 < kept < st.nc
+    g, ref, st0 = run_both(pkg, ctx, case, **kw)
+    assert st0["capacitance_dim"] == 3 * kept
+    assert_parity(g, ref, tol, st.nc)
+    g, ref, st1 = run_both(pkg, ctx, case, cap_drop=0.0, **kw)
+    assert st1["capacitance_dim"] == 3 * st.nc
+    assert_parity(g, ref, tol, st.nc)
+    active = step_case("cube_drop", 5)
+    assert np.all(_oracle_capacitance_scores(active[1], active[2], active[3]) > 1.0)
+    g, ref, st5 = run_both(pkg, ctx, active, **kw)
+    assert st5["capacitance_dim"] == 3 * active[1].nc
+    assert_parity(g, ref, tol, active[1].nc)
