@@ -220,7 +220,8 @@ def apply_roofline(pkg, torch, dev, scene, K, precision="fp64"):
     FP32 values and intermediates of the mixed preconditioner) on a scene: K applies captured into
     one CUDA graph and replayed, timed with events on the replay stream.  Algorithmic bytes count
     the Cholesky factor L (2 nnz(L) values + indices) and the vectors; kernel bytes count what the
-    kernels read instead (S = L^{-1} and S^T)."""
+    kernels read instead (the values of S = L^{-1}, whose rows are column ranges, and the values and
+    indices of S^T)."""
     info = scene.info()
     n3 = 3 * scene.n_verts
     sx = torch.randn(scene.n_verts, 3, dtype=torch.float64, device=dev)
@@ -246,7 +247,7 @@ def apply_roofline(pkg, torch, dev, scene, K, precision="fp64"):
     bv = 8 if precision == "fp64" else 4
     vec = n3 * (4 * 8 if precision == "fp64" else 8 + 4 + 4 + 8)  # x in, w out and in, y out
     alg = 2 * info["nnz_L"] * (bv + 4) + vec
-    kb = 2 * info["nnz_Linv"] * (bv + 4) + vec
+    kb = info["nnz_Linv"] * (2 * bv + 4) + vec  # S: values only (rows are column ranges); S^T: values + indices
     peak, src = peaks()
     return {"kernel": f"k_spmv_chunks x2 (A^-1 = P^T S^T S P, {'FP64' if precision == 'fp64' else 'FP32'} values, "
                       "3 RHS)", "bound": "hbm",

@@ -259,7 +259,6 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
   upload(S.iperm, iperm);
   upload(S.scene_of_vertex, scene_of_vertex);
   upload(S.S_ptr, Su.ptr);
-  upload(S.S_col, Su.col);
   upload(S.S_val, Su.val);
   upload(S.St_ptr, Stu.ptr);
   upload(S.St_col, Stu.col);
@@ -285,6 +284,18 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
     return (int)r.size();
   };
   S.nS_chunks = chunk(Su, S.S_crow, S.S_cbeg, S.S_cend);
+  {  // rows of S are contiguous column ranges (postordered factor): each chunk keeps its first column
+    std::vector<int32_t> c0;
+    c0.reserve(S.nS_chunks);
+    for (int i = 0; i < Su.n; ++i)
+      for (int64_t p = Su.ptr[i]; p < Su.ptr[i + 1]; p += 256) {
+        c0.push_back(Su.col[p]);
+        for (int64_t q = p; q < std::min<int64_t>(p + 256, Su.ptr[i + 1]); ++q)
+          if (Su.col[q] != Su.col[p] + (int32_t)(q - p))
+            throw Error{NCPADJ_ERR_NOT_FACTORED, "internal: a row of the sparse inverse is not a column range"};
+      }
+    upload(S.S_c0, c0);
+  }
   S.nSt_chunks = chunk(Stu, S.St_crow, S.St_cbeg, S.St_cend);
   S.flags.ensure(FLAG_COUNT * sizeof(int));
   NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
@@ -590,7 +601,7 @@ struct Engine {
     ytmp = base; base += nv3;
     partial = S.red.as<double>();
     scal = S.scal.as<double>();
-    sinv = SinvArgs{nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+    sinv = SinvArgs{nv, S.S_ptr.as<int64_t>(), S.S_c0.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
                     S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                     S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                     S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};
@@ -2404,7 +2415,7 @@ ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const dou
     Scene& S = scene->s;
     cudaStream_t st = (cudaStream_t)stream;
     S.io.ensure(sizeof(double) * 3 * (size_t)S.nv);
-    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_c0.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
@@ -2430,7 +2441,7 @@ ncpadj_status ncpadj_elastic_solve_mixed(ncpadj_ctx ctx, ncpadj_scene scene, con
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n3 = 3 * (size_t)S.nv;
     S.io.ensure(sizeof(float) * n3 + 64);
-    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_c0.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};

@@ -6,11 +6,15 @@
 // per scene:
 //   1. a nested-dissection ordering from the vertex coordinates (recursive median
 //      bisection along the longest axis with one-sided vertex separators, separators last),
-//   2. the elimination tree of the permuted matrix,
+//   2. the elimination tree of the permuted matrix, and the ordering refined to a postorder of
+//      that tree (an equivalent ordering: the same fill and the same tree, relabelled so that
+//      every subtree is a contiguous range of positions ending at its root),
 //   3. the Cholesky factor by the up-looking row-by-row algorithm (each row of L is a
 //      sparse triangular solve whose pattern is the row's reach in the elimination tree),
 //   4. the columns of S = L^{-1}: column j is nonzero exactly on the elimination-tree path
-//      from j to its root, and is obtained by a forward substitution along that path.
+//      from j to its root, and is obtained by a forward substitution along that path.  So row i
+//      of S holds exactly the descendants of i: in the postorder, the contiguous range
+//      [i - size(i) + 1, i].
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -89,16 +93,19 @@ void factor_elastic(const CsrD& As, const double* xyz, ElasticFactor& F) {
   }
   // permuted matrix, upper part by columns: for column k, rows i <= k with A(i,k) != 0
   std::vector<std::vector<std::pair<int, double>>> upper(n);
-  for (int v = 0; v < n; ++v) {
-    int k = F.iperm[v];
-    for (int64_t p = As.ptr[v]; p < As.ptr[v + 1]; ++p) {
-      int i = F.iperm[As.col[p]];
-      if (i <= k) upper[k].push_back({i, As.val[p]});
+  auto permute = [&]() {
+    for (auto& u : upper) u.clear();
+    for (int v = 0; v < n; ++v) {
+      int k = F.iperm[v];
+      for (int64_t p = As.ptr[v]; p < As.ptr[v + 1]; ++p) {
+        int i = F.iperm[As.col[p]];
+        if (i <= k) upper[k].push_back({i, As.val[p]});
+      }
     }
-  }
+  };
   // 2. elimination tree (with path compression through `anc`)
-  F.parent.assign(n, -1);
-  {
+  auto etree = [&]() {
+    F.parent.assign(n, -1);
     std::vector<int32_t> anc(n, -1);
     for (int k = 0; k < n; ++k) {
       for (auto& e : upper[k]) {
@@ -114,6 +121,42 @@ void factor_elastic(const CsrD& As, const double* xyz, ElasticFactor& F) {
         }
       }
     }
+  };
+  permute();
+  etree();
+  // postorder of the forest (roots and children in increasing position), then the same tree in
+  // that numbering: position k of the new ordering is node post[k] of the old one
+  {
+    std::vector<int32_t> first(n, -1), next(n, -1), post;
+    post.reserve(n);
+    for (int j = n - 1; j >= 0; --j)  // child lists in increasing order
+      if (F.parent[j] >= 0) {
+        next[j] = first[F.parent[j]];
+        first[F.parent[j]] = j;
+      }
+    std::vector<int32_t> stack;
+    for (int r = 0; r < n; ++r) {
+      if (F.parent[r] >= 0) continue;
+      stack.push_back(r);
+      while (!stack.empty()) {
+        const int v = stack.back();
+        if (first[v] >= 0) {  // descend into the next unvisited child
+          const int c = first[v];
+          first[v] = next[c];
+          stack.push_back(c);
+        } else {
+          post.push_back(v);
+          stack.pop_back();
+        }
+      }
+    }
+    if ((int)post.size() != n) throw Error{NCPADJ_ERR_INVALID_ARG, "postorder lost nodes"};
+    std::vector<int32_t> perm(n);
+    for (int k = 0; k < n; ++k) perm[k] = F.perm[post[k]];
+    F.perm = perm;
+    for (int i = 0; i < n; ++i) F.iperm[F.perm[i]] = i;
+    permute();
+    etree();
   }
   // 3. up-looking Cholesky: row k of L solves L(0:k,0:k) y = A(0:k, k).  Row k reads and
   // appends to columns of k's descendants only, so the rows of disjoint elimination subtrees are

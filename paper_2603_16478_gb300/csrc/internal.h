@@ -90,7 +90,8 @@ struct Scene {
   DevBuf diag_slot; // int32 [nv]
   // elastic factor (position space), device copies
   DevBuf perm, iperm;          // int32 [nv]
-  DevBuf S_ptr, S_col, S_val;  // rows of S; S_col holds ORIGINAL vertex ids (gather from x)
+  DevBuf S_ptr, S_c0, S_val;   // rows of S (position space; each a contiguous column range),
+                               // S_c0: the first column of each chunk
   DevBuf St_ptr, St_col, St_val;  // rows of S^T; St_col in position space
   DevBuf S_val32, St_val32;       // FP32 copies of the values (mixed precision)
   DevBuf S_crow, S_cbeg, S_cend, St_crow, St_cbeg, St_cend;  // row chunks (<= 256 entries)

@@ -186,7 +186,8 @@ void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const 
 struct SinvArgs {
   int nv;
   const int64_t* S_ptr;
-  const int32_t* S_col;   // original vertex ids
+  const int32_t* S_c0;    // [nS] first column (position) of each chunk of S: rows of S are
+                          // contiguous column ranges, so no per-entry index is kept
   const double* S_val;
   const int64_t* St_ptr;
   const int32_t* St_col;  // positions

@@ -2,7 +2,9 @@
 //
 //  * block sparse matrix-vector product with the assembled script_A^T (3x3 blocks),
 //  * A^{-1} x = P^T S^T S P x through the explicit sparse inverse S = L^{-1} of the scalar
-//    elastic factor, applied to the 3 coordinates at once (Sec. 3, sparse-inverse factorisation),
+//    elastic factor, applied to the 3 coordinates at once (Sec. 3, sparse-inverse factorisation);
+//    the rows of S are contiguous column ranges (postordered elimination tree), those of S^T the
+//    elimination-tree paths,
 //  * the contact-space pieces of the Woodbury preconditioner (Eq. woodbury_formula, used in the
 //    form without K^{-1}): Delassus entries (A_s^{-1})_{v_a v_b}, the capacitance
 //    C = I + h^2 K^T D, its inverse by in-place Gauss-Jordan elimination with partial pivoting in
@@ -213,6 +215,52 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
     atomicAdd(&y[3 * o], (Y)a0);
     atomicAdd(&y[3 * o + 1], (Y)a1);
     atomicAdd(&y[3 * o + 2], (Y)a2);
+  }
+}
+
+// The product with S = L^{-1} in a postordered elimination tree: row i of S holds exactly the
+// descendants of i, the contiguous column range [i - size(i) + 1, i], so no column index is stored.
+// Chunk k covers entries [cbeg[k], cend[k]) of row crow[k], whose columns run from c0[k] upwards;
+// one warp per chunk, 8 values per lane in flight, x read contiguously; partial sums added
+// atomically into y[3 row + r] (y zeroed by the caller).
+template <typename V, typename X, typename Y, typename Acc = Y>
+__global__ void __launch_bounds__(256) k_spmv_range_chunks(int nchunks, const int32_t* __restrict__ crow,
+                                                           const int64_t* __restrict__ cbeg,
+                                                           const int64_t* __restrict__ cend,
+                                                           const int32_t* __restrict__ c0, const V* __restrict__ val,
+                                                           const X* __restrict__ x, Y* __restrict__ y,
+                                                           Mask mk = Mask{}) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= nchunks) return;
+  const int row = crow[k];
+  if (!mk.on(row)) return;  // whole warp: one chunk per warp (positions keep their scene)
+  const int64_t b = cbeg[k], e = cend[k];
+  const int col0 = c0[k];
+  Acc a0 = 0, a1 = 0, a2 = 0;
+  V s[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int64_t p = b + lane + 32 * u;
+    s[u] = (p < e) ? val[p] : V(0);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int off = lane + 32 * u;
+    if (b + off < e) {
+      const size_t c = 3 * (size_t)(col0 + off);
+      a0 += (Acc)s[u] * (Acc)x[c];
+      a1 += (Acc)s[u] * (Acc)x[c + 1];
+      a2 += (Acc)s[u] * (Acc)x[c + 2];
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane == 0) {
+    atomicAdd(&y[3 * row], (Y)a0);
+    atomicAdd(&y[3 * row + 1], (Y)a1);
+    atomicAdd(&y[3 * row + 2], (Y)a2);
   }
 }
 
@@ -607,8 +655,8 @@ void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream
   g_launches += 2;
   k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos, mk);
   cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, a.xpos, w, nullptr, 0, mk);
+  k_spmv_range_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val, a.xpos, w, mk);
 }
 void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
@@ -620,8 +668,8 @@ void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaSt
   g_launches += 2;
   k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos32, mk);
   cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32, nullptr, 0, mk);
+  k_spmv_range_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val32, a.xpos32, w32, mk);
 }
 void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
@@ -762,13 +810,13 @@ void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, con
   if (w32) {
     k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos32, mk);
     cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
-    k_spmv_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val32, nullptr, a.xpos32, w32, nullptr, 0, mk);
+    k_spmv_range_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val32, a.xpos32, w32, mk);
   } else {
     k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos, mk);
     cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-    k_spmv_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_col, a.S_val, nullptr, a.xpos, w, nullptr, 0, mk);
+    k_spmv_range_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
+        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val, a.xpos, w, mk);
   }
 }
 void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {

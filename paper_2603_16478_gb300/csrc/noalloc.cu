@@ -64,7 +64,7 @@ extern "C" ncpadj_status ncpadj_elastic_solve_noalloc(ncpadj_ctx ctx, ncpadj_sce
                        std::to_string(kNoAllocMaxVerts));
     NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
     double* w = scratch_address(ctx->c.device);  // looked up by ncpadj_ctx_create: no allocation here
-    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_col.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
+    SinvArgs a{S.nv, S.S_ptr.as<int64_t>(), S.S_c0.as<int32_t>(), S.S_val.as<double>(), S.St_ptr.as<int64_t>(),
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};

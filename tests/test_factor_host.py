@@ -1,7 +1,8 @@
 """The library's host factorisation of the scalar elastic matrix (factor.cpp), compiled on its own
 with g++ and checked on the CPU against its definition: with the nested-dissection permutation P,
 S = L^{-1} must satisfy S (P A P^T) S^T = I; S is lower triangular; column j of S is stored on
-exactly the elimination-tree path from j to its root; S^T is stored consistently; an indefinite
+exactly the elimination-tree path from j to its root; the ordering is a postorder of that tree, so
+row i of S is the contiguous range of i's subtree; S^T is stored consistently; an indefinite
 matrix is rejected.  Matrices: the oracle's elastic matrices of the cube and of a small beam,
 and a random SPD matrix on a graph with two components."""
 import os
@@ -91,6 +92,14 @@ def _check(F, A):
             path.append(i)
             i = parent[i]
         assert St.indices[St.indptr[j]:St.indptr[j + 1]].tolist() == path
+    # the ordering is a postorder of the tree: every subtree is the contiguous range ending at its
+    # root, so row i of S (the descendants of i) is exactly [i - size(i) + 1, i]
+    size = np.ones(n, int)
+    for j in range(n):
+        if parent[j] >= 0:
+            size[parent[j]] += size[j]
+    for i in range(n):
+        assert S.indices[S.indptr[i]:S.indptr[i + 1]].tolist() == list(range(i - size[i] + 1, i + 1))
     # nnz(L) counts the factor's nonzero pattern: L = S^{-1} has no entry outside it
     L = np.linalg.inv(S.toarray())
     assert np.count_nonzero(np.abs(np.tril(L)) > 1e-13 * np.abs(L).max()) <= F["nnz_L"]
