@@ -137,6 +137,19 @@ void ncpadj_scene_destroy(ncpadj_scene scene);
 ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_scene_desc* descs,
                                         ncpadj_scene* out);
 
+/* New material for an existing scene (per-tet Young's modulus E > 0 and Poisson ratio nu in
+ * (-1, 0.5), HOST arrays [n_tets] over the whole scene, batch meshes concatenated).  Everything that
+ * depends on the material is rebuilt from the scene's kept geometry: the Lame parameters and their
+ * derivatives, A_s = M_s + h^2 sum_i w_i B_i^T B_i (w_i = 2 mu_i V_i), its Cholesky factor and the
+ * sparse inverse S = L^{-1} (Sec. 3, sparse-inverse factorisation; Eq. dynamics).  The mesh, the
+ * step size, the fibres and the constitutive models are kept.  Work queued on `stream` is waited
+ * for first (it may read the arrays being rebuilt); the call is synchronous.  Calls on the scene
+ * must not overlap it.  Errors: INVALID_ARG (NULL, a value out of range: nothing is changed),
+ * OOM, CUDA. */
+ncpadj_status ncpadj_scene_refactor(ncpadj_scene scene, const double* E, const double* nu, void* stream);
+/* The scene's current per-tet E and nu (HOST arrays [n_tets] to fill). */
+ncpadj_status ncpadj_scene_get_material(ncpadj_scene scene, double* E, double* nu);
+
 typedef struct {
   int32_t n_verts, n_tets;
   int32_t n_blocks;        /* 3x3 blocks in the pattern of script_A */

@@ -108,6 +108,7 @@ class _ForwardStats(C.Structure):
 
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
+           "ncpadj_scene_refactor", "ncpadj_scene_get_material",
            "ncpadj_options_default", "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step",
            "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc", "ncpadj_elastic_solve_mixed", "ncpadj_dense_inverse",
            "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
@@ -133,6 +134,8 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_scene_destroy.argtypes = [C.c_void_p]
     lib.ncpadj_scene_create_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_SceneDesc), C.POINTER(C.c_void_p)]
     lib.ncpadj_scene_get_info.argtypes = [C.c_void_p, C.POINTER(_SceneInfo)]
+    lib.ncpadj_scene_refactor.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.ncpadj_scene_get_material.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_options_default.argtypes = [C.POINTER(_Options)]
     lib.ncpadj_adjoint_step.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Contacts), C.POINTER(_State),
                                         C.POINTER(_Seed), C.POINTER(_Options), C.POINTER(_Grads), C.POINTER(_Stats),
@@ -243,6 +246,24 @@ class Scene:
             raise ValueError(f"expected {self.n_tets} models, got {len(codes)}")
         m = torch.tensor(codes, dtype=torch.int32)
         _check(self.lib, self.lib.ncpadj_scene_set_model(self.handle, C.c_void_p(m.data_ptr())))
+
+    def refactor(self, E, nu, stream=None) -> None:
+        """New per-tet (or scalar) Young's modulus and Poisson ratio: the material-dependent arrays and
+        the elastic factor are rebuilt (host-side factorisation; synchronous)."""
+        Et = torch.as_tensor(E, dtype=torch.float64).expand(self.n_tets).contiguous().cpu()
+        nut = torch.as_tensor(nu, dtype=torch.float64).expand(self.n_tets).contiguous().cpu()
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream(self.ctx.device).cuda_stream
+        _check(self.lib, self.lib.ncpadj_scene_refactor(self.handle, C.c_void_p(Et.data_ptr()),
+                                                        C.c_void_p(nut.data_ptr()), C.c_void_p(stream or 0)))
+
+    def material(self):
+        """(E, nu): the scene's current per-tet material (CPU float64 tensors [n_tets])."""
+        E = torch.empty(self.n_tets, dtype=torch.float64)
+        nu = torch.empty(self.n_tets, dtype=torch.float64)
+        _check(self.lib, self.lib.ncpadj_scene_get_material(self.handle, C.c_void_p(E.data_ptr()),
+                                                            C.c_void_p(nu.data_ptr())))
+        return E, nu
 
     def info(self) -> dict:
         inf = _SceneInfo()

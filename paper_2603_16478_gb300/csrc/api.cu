@@ -297,16 +297,21 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
     upload(S.S_c0, c0);
   }
   S.nSt_chunks = chunk(Stu, S.St_crow, S.St_cbeg, S.St_cend);
+  // host-side resources, made once per scene (a refactor rebuilds only the arrays above)
   S.flags.ensure(FLAG_COUNT * sizeof(int));
-  NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
-  NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
-  NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_host, 2 * (2 * 513 + 1) * sizeof(double)));  // two slots
-  for (auto& e : S.gs_ev) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_inner_host, 256 * sizeof(double)));
-  NCPADJ_CUDA_TRY(cudaHostAlloc(&S.gs_map_host, 2 * (2 * 513 + 1) * sizeof(double), cudaHostAllocMapped));
-  NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.gs_map_dev), S.gs_map_host, 0));
+  if (!S.flags_host) NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
+  if (!S.scal_host) NCPADJ_CUDA_TRY(cudaMallocHost(&S.scal_host, 16 * sizeof(double)));
+  if (!S.gs_host) NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_host, 2 * (2 * 513 + 1) * sizeof(double)));  // two slots
+  for (auto& e : S.gs_ev)
+    if (!e) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  if (!S.gs_inner_host) NCPADJ_CUDA_TRY(cudaMallocHost(&S.gs_inner_host, 256 * sizeof(double)));
+  if (!S.gs_map_host) {
+    NCPADJ_CUDA_TRY(cudaHostAlloc(&S.gs_map_host, 2 * (2 * 513 + 1) * sizeof(double), cudaHostAllocMapped));
+    NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.gs_map_dev), S.gs_map_host, 0));
+  }
   S.gstep.ensure(64);
-  for (auto& e : S.ev) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
+  for (auto& e : S.ev)
+    if (!e) NCPADJ_CUDA_TRY(cudaEventCreate(&e));
   // tiles of the DOF range that never straddle two meshes (per-scene reductions of a batch solve)
   {
     std::vector<int32_t> tsc, tb, te, t0(n_scenes + 1, 0);
@@ -326,9 +331,50 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
     all.insert(all.end(), t0.begin(), t0.end());
     upload(S.segt, all);
   }
-  NCPADJ_CUDA_TRY(cudaHostAlloc(&S.bmap_host, sizeof(int) * (kMaxRestart + 8), cudaHostAllocMapped));
-  NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.bmap_dev), S.bmap_host, 0));
-  for (auto& e : S.bev) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  if (!S.bmap_host) {
+    NCPADJ_CUDA_TRY(cudaHostAlloc(&S.bmap_host, sizeof(int) * (kMaxRestart + 8), cudaHostAllocMapped));
+    NCPADJ_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&S.bmap_dev), S.bmap_host, 0));
+  }
+  for (auto& e : S.bev)
+    if (!e) NCPADJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // captured steps read the arrays above: they are captured again on their next use
+  if (S.step_exec) cudaGraphExecDestroy(S.step_exec);
+  if (S.bstep_exec) cudaGraphExecDestroy(S.bstep_exec);
+  S.step_exec = S.bstep_exec = nullptr;
+  S.step_key.clear();
+  S.bstep_key.clear();
+}
+
+// host copies of the meshes a scene was built from, so that it can be refactored with new materials
+static void keep_geometry(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) {
+  S.geo_pos.assign(n_scenes, {});
+  S.geo_tets.assign(n_scenes, {});
+  S.geo_density.assign(n_scenes, 0.0);
+  S.mat_E.clear();
+  S.mat_nu.clear();
+  for (int i = 0; i < n_scenes; ++i) {
+    const ncpadj_scene_desc& d = descs[i];
+    S.geo_pos[i].assign(d.rest_pos, d.rest_pos + 3 * (size_t)d.n_verts);
+    S.geo_tets[i].assign(d.tets, d.tets + 4 * (size_t)d.n_tets);
+    S.geo_density[i] = d.density;
+    S.mat_E.insert(S.mat_E.end(), d.E, d.E + d.n_tets);
+    S.mat_nu.insert(S.mat_nu.end(), d.nu, d.nu + d.n_tets);
+  }
+}
+
+// New Young's moduli and Poisson ratios (host arrays [n_tets] over the whole scene): every
+// material-dependent array and the elastic factor are rebuilt from the kept geometry.
+static void refactor_scene(Scene& S, const double* E, const double* nu) {
+  const int ns = S.n_scenes;
+  std::vector<ncpadj_scene_desc> descs(ns);
+  for (int i = 0; i < ns; ++i) {
+    const int t0 = S.toff[i];
+    descs[i] = ncpadj_scene_desc{S.voff[i + 1] - S.voff[i], S.toff[i + 1] - S.toff[i], S.geo_pos[i].data(),
+                                 S.geo_tets[i].data(), E + t0, nu + t0, S.geo_density[i], S.h};
+  }
+  build_scene(S, descs.data(), ns);
+  S.mat_E.assign(E, E + S.nt);
+  S.mat_nu.assign(nu, nu + S.nt);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -384,6 +430,7 @@ struct Engine {
   // capacitance rows are within cap_drop of the identity; the assembled matrix and the contractions
   // always take every contact.
   int cnc = 0;
+  int nbc = 0;                   // single-vertex bindings among the candidates (after the contacts)
   const int32_t* cvx = nullptr;  // [cnc] vertex ids
   const double* cfr = nullptr;   // [cnc][9] frames
   const double* ccd = nullptr;   // [cnc][12] K, k_mu
@@ -506,7 +553,7 @@ struct Engine {
       w32 = x32 + N;
       Cm32 = w32 + N;
     }
-    if (nc && precond == NCPADJ_PRECOND_WOODBURY) {
+    if ((nc + nbc) && precond == NCPADJ_PRECOND_WOODBURY) {
       S.cap.ensure(sizeof(double) * (cap_elems + ds_elems + 16) + sizeof(int32_t) * ((size_t)ncap + 16));
       int nmax = 0;
       for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
@@ -531,9 +578,11 @@ struct Engine {
     nc = nc_;
     m = m_;
     precond = precond_;
-    ncap = 3 * nc;
+    // single-vertex bindings join the capacitance (one scene: a batch groups it by mesh)
+    nbc = (S.n_scenes == 1 && in.nbind > 0 && in.bvertex && precond_ == NCPADJ_PRECOND_WOODBURY) ? in.nbind : 0;
+    ncap = 3 * (nc + nbc);
     S.cdata.ensure(sizeof(double) * 12 * (size_t)std::max(nc, 1));
-    cnc = nc;  // until select_capacitance: every contact (the largest plan)
+    cnc = nc + nbc;  // until select_capacitance: every candidate (the largest plan)
     cvx = in.cvertex;
     cfr = in.frame;
     ccd = S.cdata.as<double>();
@@ -638,32 +687,58 @@ struct Engine {
   // contact: K_c ~ eps^2 / delta_n^2).  The preconditioner is then the exact Woodbury inverse of
   // A + h^2 J_k^T K_k J_k over the kept contacts; the left-out ones stay in the matrix, and the
   // Krylov solve absorbs them (flexible GMRES: the result keeps its tolerance).
+  // Candidates are the contacts followed by the single-vertex bindings (J_b = e_v^T (x) I_3, K = I / E_b,
+  // Sec. 3.2.1 puts J_b in the same low-rank term), so that stiff bindings are preconditioned exactly.
   void select_capacitance() {
-    cnc = nc;
+    const int ncand = nc + nbc;
+    cnc = ncand;
     cvx = in.cvertex;
     cfr = in.frame;
     ccd = S.cdata.as<double>();
-    if (!(cap_drop > 0.0) || nc == 0) return;
-    S.capsel.ensure(sizeof(double) * (size_t)nc * 22 + sizeof(int32_t) * 2 * (size_t)nc + 256);
-    double* score = S.capsel.as<double>();
-    double* fr = score + nc;
-    double* cd = fr + 9 * (size_t)nc;
-    int32_t* idx = reinterpret_cast<int32_t*>(cd + 12 * (size_t)nc);
-    int32_t* vx = idx + nc;
-    launch_contact_score(nc, in.cvertex, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_val.as<double>(),
-                         S.cdata.as<double>(), h, score, st);
-    std::vector<double> sh(nc);
-    NCPADJ_CUDA_TRY(cudaMemcpyAsync(sh.data(), score, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+    if (ncand == 0 || (!(cap_drop > 0.0) && nbc == 0)) return;
+    // layout: candidates (vertex, frame, K) when bindings join, then the kept set, scores, indices
+    S.capsel.ensure(sizeof(double) * (size_t)ncand * (21 + 21 + 1) + sizeof(int32_t) * 3 * (size_t)ncand + 256);
+    double* cand_f = S.capsel.as<double>();
+    double* cand_c = cand_f + 9 * (size_t)ncand;
+    double* fr = cand_c + 12 * (size_t)ncand;
+    double* cd = fr + 9 * (size_t)ncand;
+    double* score = cd + 12 * (size_t)ncand;
+    int32_t* cand_v = reinterpret_cast<int32_t*>(score + ncand);
+    int32_t* idx = cand_v + ncand;
+    int32_t* vx = idx + ncand;
+    const int32_t* sv = in.cvertex;
+    const double* sf = in.frame;
+    const double* sd = S.cdata.as<double>();
+    if (nbc) {
+      if (nc) {
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(cand_v, in.cvertex, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(cand_f, in.frame, sizeof(double) * 9 * nc, cudaMemcpyDeviceToDevice, st));
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(cand_c, S.cdata.as<double>(), sizeof(double) * 12 * nc,
+                                        cudaMemcpyDeviceToDevice, st));
+      }
+      launch_binding_capdata(nbc, in.bvertex, in.bcompliance, nc, cand_v, cand_f, cand_c, st);
+      sv = cand_v;
+      sf = cand_f;
+      sd = cand_c;
+      cvx = sv;
+      cfr = sf;
+      ccd = sd;
+    }
+    if (!(cap_drop > 0.0)) return;
+    launch_contact_score(ncand, sv, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_val.as<double>(), sd, h,
+                         score, st);
+    std::vector<double> sh(ncand);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(sh.data(), score, sizeof(double) * ncand, cudaMemcpyDeviceToHost, st));
     NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<int32_t> keep;
-    keep.reserve(nc);
-    for (int c = 0; c < nc; ++c)
+    keep.reserve(ncand);
+    for (int c = 0; c < ncand; ++c)
       if (!(sh[c] <= cap_drop)) keep.push_back(c);  // NaN scores stay in
-    if ((int)keep.size() == nc) return;
+    if ((int)keep.size() == ncand) return;
     cnc = (int)keep.size();
     if (cnc) {
       NCPADJ_CUDA_TRY(cudaMemcpyAsync(idx, keep.data(), sizeof(int32_t) * cnc, cudaMemcpyHostToDevice, st));
-      launch_gather_contacts(cnc, idx, in.cvertex, in.frame, S.cdata.as<double>(), vx, fr, cd, st);
+      launch_gather_contacts(cnc, idx, sv, sf, sd, vx, fr, cd, st);
     }
     cvx = vx;
     cfr = fr;
@@ -674,7 +749,7 @@ struct Engine {
     if (precond == NCPADJ_PRECOND_JACOBI)
       launch_diag_inv(nv, S.diag_slot.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
                       mixed ? S.bsr32.as<float>() : nullptr, dinv, st);
-    if (precond == NCPADJ_PRECOND_WOODBURY && nc) {
+    if (precond == NCPADJ_PRECOND_WOODBURY && (nc + nbc)) {
       select_capacitance();
       plan_blocks();
       alloc_capacitance();
@@ -900,9 +975,9 @@ struct Engine {
   // Arnoldi relation holds for (that mismatch, relative ~1e-7 times the cancellation in V y, can
   // stop a restarted GMRES from converging)
   bool flexible_gmres() const {
-    const bool inner = !sup_c0.empty() && precond == NCPADJ_PRECOND_WOODBURY && nc > 0;
+    const bool inner = !sup_c0.empty() && precond == NCPADJ_PRECOND_WOODBURY && nc + nbc > 0;
     const bool fp32 = (mixed && (precond == NCPADJ_PRECOND_WOODBURY || precond == NCPADJ_PRECOND_ELASTIC)) ||
-                      (cap_fp32 && precond == NCPADJ_PRECOND_WOODBURY && nc > 0);
+                      (cap_fp32 && precond == NCPADJ_PRECOND_WOODBURY && nc + nbc > 0);
     // contacts left out of the capacitance: the preconditioner is not the matrix's inverse even in
     // exact arithmetic, but it is one fixed map, so plain right-preconditioned GMRES stays exact;
     // flexible GMRES is kept for the rounding cases above only
@@ -2288,6 +2363,7 @@ ncpadj_status ncpadj_scene_create(ncpadj_ctx ctx, const ncpadj_scene_desc* desc,
     s = new ncpadj_scene_s();
     s->ctx = ctx;
     build_scene(s->s, desc, 1);
+    keep_geometry(s->s, desc, 1);
     *out = s;
     return NCPADJ_OK;
   } catch (const Error& e) {
@@ -2310,6 +2386,7 @@ ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const 
     s = new ncpadj_scene_s();
     s->ctx = ctx;
     build_scene(s->s, descs, n_scenes);
+    keep_geometry(s->s, descs, n_scenes);
     *out = s;
     return NCPADJ_OK;
   } catch (const Error& e) {
@@ -2318,6 +2395,40 @@ ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const 
   } catch (const std::exception& e) {
     ncpadj_scene_destroy(s);
     return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_refactor(ncpadj_scene scene, const double* E, const double* nu, void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene && E && nu, "NULL argument");
+    NCPADJ_REQUIRE(scene->ctx, "scene without a context");
+    NCPADJ_CUDA_TRY(cudaSetDevice(scene->ctx->c.device));
+    Scene& S = scene->s;
+    for (int t = 0; t < S.nt; ++t)
+      NCPADJ_REQUIRE(E[t] > 0 && std::isfinite(E[t]) && nu[t] > -1.0 && nu[t] < 0.5,
+                     "tet " + std::to_string(t) + ": need E > 0 and -1 < nu < 0.5");
+    // work already queued on the stream may still read the arrays that are rebuilt
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    refactor_scene(S, E, nu);
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_get_material(ncpadj_scene scene, double* E, double* nu) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene && E && nu, "NULL argument");
+    const Scene& S = scene->s;
+    std::copy(S.mat_E.begin(), S.mat_E.end(), E);
+    std::copy(S.mat_nu.begin(), S.mat_nu.end(), nu);
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
   }
 }
 

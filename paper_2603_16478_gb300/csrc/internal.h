@@ -99,6 +99,11 @@ struct Scene {
   int64_t nnz_S = 0;
   int64_t nnz_L = 0;
   double ms_factor = 0;
+  // host copies of the meshes (for a refactor with new materials) and the current material
+  std::vector<std::vector<double>> geo_pos;
+  std::vector<std::vector<int32_t>> geo_tets;
+  std::vector<double> geo_density;
+  std::vector<double> mat_E, mat_nu;  // [nt]
   std::vector<int64_t> St_ptr_h;  // host copy (Delassus pair scheduling)
 
   // per-call workspace

@@ -248,6 +248,10 @@ void launch_contact_score(int nc, const int32_t* cvertex, const int32_t* iperm, 
 // vertex, frame and K / k_mu of the contacts idx[0..nk) into compact arrays
 void launch_gather_contacts(int nk, const int32_t* idx, const int32_t* vertex, const double* frame,
                             const double* cdata, int32_t* ov, double* of, double* oc, cudaStream_t s);
+// single-vertex bindings as capacitance members after the first `off`: vertex, identity frame,
+// K = I / E_b
+void launch_binding_capdata(int nb, const int32_t* vertex, const double* compliance, int off, int32_t* ov,
+                            double* of, double* oc, cudaStream_t s);
 // Delassus of the contact vertices: Ds[a][b] = (A_s^{-1})_{v_a v_b}
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
                      const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s);

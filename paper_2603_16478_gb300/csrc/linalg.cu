@@ -424,6 +424,26 @@ __global__ void k_gather_contacts(int nk, const int32_t* __restrict__ idx, const
   for (int i = 0; i < 12; ++i) oc[12 * (size_t)k + i] = cdata[12 * (size_t)c + i];
 }
 
+// Single-vertex bilateral bindings as members of the capacitance set: binding b acts on vertex[b]
+// through J_b = e_v^T (x) I_3 with the stiffness I / E_b, i.e. a vertex "contact" with the identity
+// frame and K = I / E_b (no friction coefficient).  Written after the first `off` candidates.
+__global__ void k_binding_capdata(int nb, const int32_t* __restrict__ vertex, const double* __restrict__ compliance,
+                                  int off, int32_t* __restrict__ ov, double* __restrict__ of,
+                                  double* __restrict__ oc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const size_t k = (size_t)off + b;
+  ov[k] = vertex[b];
+  const double kb = 1.0 / compliance[b];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    of[9 * k + i] = (i % 4 == 0) ? 1.0 : 0.0;
+    oc[12 * k + i] = (i % 4 == 0) ? kb : 0.0;
+  }
+#pragma unroll
+  for (int i = 9; i < 12; ++i) oc[12 * k + i] = 0.0;
+}
+
 // C[3a+r][3b+s] = delta + h^2 Ds[a][b] sum_l K'_a[r][l] (F_a F_b^T)[l][s],  K' = K^T (adjoint) or K
 __global__ void k_cap_form(int nc, const double* __restrict__ Ds, const double* __restrict__ frame,
                            const double* __restrict__ cdata, double h2, int transpose, double* C) {
@@ -719,6 +739,11 @@ void launch_gather_contacts(int nk, const int32_t* idx, const int32_t* vertex, c
                             const double* cdata, int32_t* ov, double* of, double* oc, cudaStream_t s) {
   g_launches += 1;
   if (nk) k_gather_contacts<<<nblk(nk, 128), 128, 0, s>>>(nk, idx, vertex, frame, cdata, ov, of, oc);
+}
+void launch_binding_capdata(int nb, const int32_t* vertex, const double* compliance, int off, int32_t* ov,
+                            double* of, double* oc, cudaStream_t s) {
+  g_launches += 1;
+  if (nb) k_binding_capdata<<<nblk(nb, 128), 128, 0, s>>>(nb, vertex, compliance, off, ov, of, oc);
 }
 void launch_delassus(int nc, const int32_t* cvertex, const int32_t* iperm, const int64_t* St_ptr,
                      const int32_t* St_col, const double* St_val, double* Ds, cudaStream_t s) {

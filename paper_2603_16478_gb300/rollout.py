@@ -52,6 +52,7 @@ class Simulator:
     newton_tol: float = 1e-10
     max_newton: int = 100
     _frames: dict = field(default_factory=dict)
+    _material: Optional[tuple] = None  # (E, nu) the scene's factor is built for, when uniform
     # bilateral bindings: vertices [n_b] (int32), or points inside tets (tet ids [n_b] and
     # barycentric weights [n_b, 4]); their targets and compliances are rollout inputs
     binding_vertex: Optional[torch.Tensor] = None
@@ -90,6 +91,18 @@ class Simulator:
                         torch.cat(dn).contiguous(), mu_region.detach()[region.long()].contiguous(), None,
                         region.contiguous(), self.n_regions)
 
+    def use_material(self, E, nu) -> None:
+        """Make the scene's elastic factor the one of the uniform material (E, nu): the scene is
+        refactored (ncpadj_scene_refactor) when its current material differs."""
+        want = (float(E), float(nu))
+        if self._material is None:
+            e, n = self.scene.material()
+            if bool((e == e[0]).all()) and bool((n == n[0]).all()):
+                self._material = (float(e[0]), float(n[0]))
+        if self._material != want:
+            self.scene.refactor(want[0], want[1])
+            self._material = want
+
     def step(self, q_prev, v_prev, contacts, f_ext=None, act=None, bindings=None):
         return forward_step(self.scene, contacts, q_prev.contiguous(), v_prev.contiguous(), f_ext, self.gravity,
                             eps=self.eps, newton_tol=self.newton_tol, max_newton=self.max_newton,
@@ -100,9 +113,10 @@ class StepFn(torch.autograd.Function):
     """(q_prev, v_prev, E, nu, mu_region, f_ext, act, b_target, b_compliance) -> (q, v) for one
     implicit step.
 
-    E and nu are scalar tensors equal to the scene's (uniform) material: the scene holds the
-    elastic factor built for them, so the forward pass checks the values and the backward pass
-    returns dL/dE and dL/dnu summed over tets.  mu_region [n_regions] sets every contact's
+    E and nu are scalar tensors: the uniform material of the step.  The scene's elastic factor is
+    built for one material, so the forward pass (and the backward pass, which recomputes the step)
+    first refactors the scene when its material differs; the backward pass returns dL/dE and
+    dL/dnu summed over tets.  mu_region [n_regions] sets every contact's
     friction coefficient through its region.  act (FP32 [n_tets] or None) are the per-tet
     activations of the scene's fibres (constant active stress a_i d_i d_i^T).  b_target [n_b, 3]
     and b_compliance [n_b] (or None) are the step's bilateral bindings on the simulator's
@@ -111,6 +125,8 @@ class StepFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, q_prev, v_prev, E, nu, mu_region, f_ext, act, b_target, b_compliance, sim: Simulator):
+        sim.use_material(E, nu)
+        ctx.material = (float(E), float(nu))
         contacts = sim.contacts(q_prev, mu_region)
         q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext, act, sim.bindings(b_target, b_compliance))
         v = (q - q_prev) / sim.scene.h
@@ -132,6 +148,7 @@ class StepFn(torch.autograd.Function):
         f_ext = f_ext if ctx.has_fext else None
         act = act if ctx.has_act else None
         bd = sim.bindings(b_target, b_compliance) if ctx.has_bind else None
+        sim.use_material(*ctx.material)
         contacts = sim.contacts(q_prev, mu_region)
         q, lam, _ = sim.step(q_prev, v_prev, contacts, f_ext, act, bd)
         gq = torch.zeros_like(q) if gq is None else gq.contiguous()

@@ -107,3 +107,20 @@ def test_invalid_bindings_are_rejected(pkg, ctx):
     g, stats = call(bd.vertex, bd.compliance, rtol=1e-10)
     assert stats["rel_residual"] <= 1e-10
     assert torch.isfinite(g["dL_dcompliance"]).all()
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_stiff_bindings_are_preconditioned_exactly(pkg, ctx, k):
+    """The bindings sit in the Woodbury low-rank term beside the contacts (Sec. 3.2.1, Sec. 4.4): the
+    capacitance counts their rows, and stiff springs (E_b = 1e-7) cost no more Krylov iterations
+    than soft ones (E_b = 1e-4) -- left out of the preconditioner they cost up to 3 n_b more."""
+    st_soft, errs = _adjoint(pkg, ctx, k, 1e-4, rtol=1e-10)
+    assert max(errs.values()) <= 1e-6, errs
+    st_stiff, errs = _adjoint(pkg, ctx, k, 1e-7, rtol=1e-10)
+    assert max(errs.values()) <= 1e-6, errs
+    nb = len(_case(k, 1e-7)[2].vertex)
+    nc = _oracle(k, 1e-7)[1].nc
+    assert st_stiff["capacitance_dim"] == 3 * (nc + nb)
+    assert st_stiff["iterations"] <= st_soft["iterations"] + 3, (st_stiff["iterations"], st_soft["iterations"])
+    _, errs = _adjoint(pkg, ctx, k, 1e-7, rtol=1e-10, cap_drop=0.0)  # every member kept: same gradients
+    assert max(errs.values()) <= 1e-6, errs

@@ -47,12 +47,47 @@ def _fake_adjoint(scene, contacts, q, q_prev, lam, gq, gv, *, want=(), bindings=
     return g, {"iterations": 0}
 
 
+class _FakeScene:
+    """The scene's side of the material handling: its current per-tet material and the refactors asked for."""
+    h, n_verts, n_tets = H, NV, 5
+
+    def __init__(self):
+        self.E = torch.full((5,), 1e5, dtype=torch.float64)
+        self.nu = torch.full((5,), 0.4, dtype=torch.float64)
+        self.refactors = []
+
+    def material(self):
+        return self.E.clone(), self.nu.clone()
+
+    def refactor(self, E, nu):
+        self.refactors.append((E, nu))
+        self.E[:], self.nu[:] = E, nu
+
+
 @pytest.fixture
 def sim(monkeypatch):
     monkeypatch.setattr(R, "forward_step", _fake_forward)
     monkeypatch.setattr(R, "adjoint_step", _fake_adjoint)
-    scene = types.SimpleNamespace(h=H, n_verts=NV, n_tets=5)
-    return R.Simulator(scene, planes=[], binding_vertex=BV)
+    return R.Simulator(_FakeScene(), planes=[], binding_vertex=BV)
+
+
+@pytest.mark.parametrize("ckpt", [0, 2])
+def test_a_new_material_refactors_the_scene_once(sim, ckpt):
+    """The factor is built for one material: E or nu different from the scene's refactor it before the
+    first step, and only then (the steps and the backward recomputation share the material)."""
+    n = 4
+    q0 = torch.randn(NV, 3, dtype=torch.float64, requires_grad=True)
+    v0 = torch.zeros(NV, 3, dtype=torch.float64)
+    mu = torch.zeros(1, dtype=torch.float64)
+    qT, _ = R.rollout(sim, q0, v0, torch.tensor(1e5, dtype=torch.float64), torch.tensor(0.4, dtype=torch.float64), mu,
+                      n, checkpoint_every=ckpt)
+    qT.sum().backward()
+    assert sim.scene.refactors == []  # the scene's own material: nothing to rebuild
+    qT, _ = R.rollout(sim, q0, v0, torch.tensor(2e5, dtype=torch.float64), torch.tensor(0.45, dtype=torch.float64),
+                      mu, n, checkpoint_every=ckpt)
+    qT.sum().backward()
+    assert sim.scene.refactors == [(2e5, 0.45)]
+    assert float(sim.scene.E[0]) == 2e5 and float(sim.scene.nu[3]) == 0.45
 
 
 @pytest.mark.parametrize("ckpt", [0, 2])
