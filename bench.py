@@ -311,7 +311,7 @@ class BatchWorkload:
         t0 = time.perf_counter()
         try:
             q, lam, fs = pkg.forward_step(scene, union, q0, v0, None, tuple(sc0.gravity), eps=self.eps,
-                                          max_newton=150, cap_precision="mixed")
+                                          max_newton=400, cap_precision="mixed")
         except pkg.NcpadjError as e:  # the adjoint is taken at the last iterate; its residual is reported
             if not hasattr(e, "state"):
                 raise
@@ -435,6 +435,22 @@ def beam_leg(pkg, torch, dev, steps, warmup, flush, with_models=True, cpu=False)
            "forward_newton_iters": [f["newton_iters"] for f in fwd],
            "forward_residual": [f["residual"] for f in fwd], "nnz_L": scene.info()["nnz_L"],
            "nnz_Linv": scene.info()["nnz_Linv"]}
+    # solver study (Sec. 5): Krylov iterations to rtol 1e-8 by solver and preconditioner, FP64,
+    # against the semi-implicit fixed-point baseline (Richardson with A^{-1}), capped at 2000
+    study = {}
+    for name, kw in (("gmres_woodbury", dict(precond="woodbury", solver="gmres")),
+                     ("gmres_jacobi", dict(precond="jacobi", solver="gmres")),
+                     ("gmres_elastic", dict(precond="elastic", solver="gmres")),
+                     ("bicgstab_woodbury", dict(precond="woodbury", solver="bicgstab")),
+                     ("semi_implicit_elastic", dict(precond="elastic", solver="semi_implicit"))):
+        try:
+            _, st_ = pkg.adjoint_step(scene, contacts, q_adj, q_prev_adj, lam_adj, dL_dq, dL_dv, eps=sc.eps, rtol=1e-8,
+                                      stream=stream.cuda_stream, max_iters=2000, **kw)
+            study[name] = st_["iterations"]
+        except pkg.NcpadjError as e:
+            study[name] = (f"not converged: {e.stats['iterations']} iterations, relative residual "
+                           f"{e.stats['rel_residual']:.1e}")
+    out["solver_study_iterations"] = study
     roof = apply_roofline(pkg, torch, dev, scene, 50, precision="mixed")
     roof["note"] = "burst figure: S and S^T (27 MB in FP32 on the beam) stay L2-resident between applies"
     out["roofline_Ainv"] = roof

@@ -72,7 +72,18 @@ enum {
   NCPADJ_PRECOND_ELASTIC = 2,  /* A^{-1} by the elastic factor (sparse-inverse preconditioner) */
   NCPADJ_PRECOND_WOODBURY = 3  /* (A + K_c)^{-1} by Eq. woodbury_formula (default) */
 };
-enum { NCPADJ_SOLVER_AUTO = 0, NCPADJ_SOLVER_CG = 1, NCPADJ_SOLVER_GMRES = 2, NCPADJ_SOLVER_BICGSTAB = 3 };
+/* NCPADJ_SOLVER_SEMI_IMPLICIT: the stationary splitting that reuses the forward solver's structure
+ * (Sec. 4.4, Eq. semi-implicit), preconditioned Richardson x^{k+1} = x^k + P^{-1}(b - B x^k); with
+ * NCPADJ_PRECOND_ELASTIC (P = A) it is the paper's semi-implicit fixed-point baseline.  It
+ * converges only when the spectral radius of I - P^{-1} B is below 1; a residual growing past
+ * 1e6 ||b|| ends it (NOT_CONVERGED).  Offered for solver studies, never chosen by AUTO. */
+enum {
+  NCPADJ_SOLVER_AUTO = 0,
+  NCPADJ_SOLVER_CG = 1,
+  NCPADJ_SOLVER_GMRES = 2,
+  NCPADJ_SOLVER_BICGSTAB = 3,
+  NCPADJ_SOLVER_SEMI_IMPLICIT = 4
+};
 enum { NCPADJ_MEM_DEVICE = 0, NCPADJ_MEM_HOST = 1 };
 /* constitutive model of a tet (App. B.2), see ncpadj_scene_set_model */
 enum { NCPADJ_MODEL_NEO_HOOKEAN = 0, NCPADJ_MODEL_COROTATIONAL = 1, NCPADJ_MODEL_ARAP = 2 };
@@ -284,7 +295,7 @@ void ncpadj_options_default(ncpadj_options* opt);
 /* Per-call statistics (nullable).  Times are CUDA-event times of the stages on the stream. */
 typedef struct {
   int32_t iterations;       /* Krylov iterations */
-  int32_t solver_used;      /* NCPADJ_SOLVER_CG, _GMRES or _BICGSTAB */
+  int32_t solver_used;      /* NCPADJ_SOLVER_CG, _GMRES, _BICGSTAB or _SEMI_IMPLICIT */
   int32_t n_contacts;
   int32_t capacitance_dim;  /* dimension of the dense contact-space system (0 if none) */
   double rel_residual;      /* final ||b - script_A^T z|| / ||b|| (recomputed explicitly) */

@@ -1291,6 +1291,23 @@ struct Engine {
           launch_copy_scalar(s2 + 1, s2 + 0, st);
         }
         iters = std::min(iters, max_iters);
+      } else if (solver == NCPADJ_SOLVER_SEMI_IMPLICIT) {
+        // The stationary splitting of the forward solver's local-global structure (Sec. 4.4, Eq.
+        // semi-implicit): P x^{k+1} = (P - B) x^k + b, i.e. preconditioned Richardson
+        // x^{k+1} = x^k + P^{-1} (b - B x^k).  With the elastic preconditioner (P = A) this is the
+        // baseline the paper compares against; it converges only when the spectral radius of
+        // I - P^{-1} B is below 1 and is stopped when the residual grows past 1e6 ||b||.
+        double* zz = S.gmres.as<double>();
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        for (iters = 1; iters <= max_iters; ++iters) {
+          apply_precond(r, zz);
+          launch_axpby(N, 1.0, x, 1.0, zz, x, st);
+          matvec(x, w);
+          launch_axpby(N, 1.0, b, -1.0, w, r, st);
+          const double rn = std::sqrt(dot_host(r, r));
+          if (!std::isfinite(rn) || rn <= tol || rn > 1e6 * bnorm) break;
+        }
+        iters = std::min(iters, max_iters);
       } else if (solver == NCPADJ_SOLVER_BICGSTAB) {
         // right-preconditioned BiCGSTAB (van der Vorst 1992): iterates on A P^{-1} u = b and
         // accumulates x = P^{-1} u directly.  Scalars on the host (one synchronisation per inner
@@ -1496,7 +1513,7 @@ void validate_options(const ncpadj_options& opt) {
   NCPADJ_REQUIRE(opt.eps > 0 && opt.rtol > 0 && opt.max_iters > 0 && opt.gmres_restart > 0 && opt.gmres_restart <= 512,
                  "bad options (eps, rtol, max_iters, gmres_restart)");
   NCPADJ_REQUIRE(opt.cap_drop >= 0 && std::isfinite(opt.cap_drop), "bad option cap_drop (must be finite, >= 0)");
-  NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 3, "bad precond/solver");
+  NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 4, "bad precond/solver");
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
   NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
   NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED, "bad cap_precision");
