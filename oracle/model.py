@@ -48,6 +48,8 @@ def lame_derivatives(E, nu):
 class Mesh:
     """Per-tet rest operators of a tet mesh (float64)."""
 
+    nF = 9  # entries of vec(F)
+
     def __init__(self, X, tets):
         self.X = np.asarray(X, float)
         self.tets = np.asarray(tets, np.int64)
@@ -71,6 +73,13 @@ class Mesh:
         self.G = G
         # global DOF ids of each tet's 12 local DOFs
         self.dofs = (3 * self.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(self.n_tets, 12)
+
+    vec = staticmethod(vec)
+    unvec = staticmethod(unvec)
+
+    def min_jacobian(self, F):
+        """The smallest det F (<= 0: some tet inverted)."""
+        return float(np.linalg.det(F).min())
 
     def F(self, q):
         """Deformation gradients [n_t, 3, 3] of positions q [n_v, 3]."""

@@ -101,8 +101,12 @@ def by_model(model, n):
 
 
 def prox(model, F, mu, lam):
-    """p(F) for a batch F [n, 3, 3] with per-item mu, lam [n]; model is one name or one per item."""
+    """p(F) for a batch F [n, 3, 3] with per-item mu, lam [n]; model is one name or one per item.
+    Triangles' F [n, 3, 2] go to the shell projections (``shell``)."""
     F = np.asarray(F, float)
+    if F.shape[-1] == 2:
+        from . import shell
+        return shell.prox(model, F, mu, lam)
     n = F.shape[0]
     mu = np.broadcast_to(np.asarray(mu, float), (n,))
     lam = np.broadcast_to(np.asarray(lam, float), (n,))
@@ -123,8 +127,12 @@ def prox(model, F, mu, lam):
 
 
 def prox_derivatives(model, F, P, mu, lam):
-    """dP/dF [n,9,9] (vec basis), dP/dmu [n,3,3], dP/dlam [n,3,3] at P = prox(model, F)."""
+    """dP/dF [n,9,9] (vec basis), dP/dmu [n,3,3], dP/dlam [n,3,3] at P = prox(model, F) (triangles:
+    [n,6,6], [n,3,2], [n,3,2] from ``shell``)."""
     F = np.asarray(F, float)
+    if F.shape[-1] == 2:
+        from . import shell
+        return shell.prox_derivatives(model, F, P, mu, lam)
     n = F.shape[0]
     mu = np.broadcast_to(np.asarray(mu, float), (n,))
     lam = np.broadcast_to(np.asarray(lam, float), (n,))

@@ -20,9 +20,13 @@ from .model import elastic_matrix
 
 
 def elastic_part(step):
-    """A = M + h^2 sum_i w_i G_i^T G_i of a Step (Eq. dynamics), sparse [3 n_v, 3 n_v]."""
+    """A = M + h^2 sum_i w_i G_i^T G_i of a Step (Eq. dynamics), sparse [3 n_v, 3 n_v]; a shell's
+    constant bending Hessian h^2 k_b Q belongs to it too."""
     mu_L, _ = step.lame()
-    return elastic_matrix(step.mesh, step.mass, mu_L, step.h).tocsc()
+    A = elastic_matrix(step.mesh, step.mass, mu_L, step.h)
+    if getattr(step, "Qb", None) is not None:
+        A = A + step.h * step.h * step.bend * step.Qb
+    return A.tocsc()
 
 
 def semi_implicit(A, B, b, rtol=1e-10, max_iters=1000, blowup=1e6):

@@ -56,8 +56,18 @@ class Step:
     """One time step of a scene with a frozen contact set."""
 
     def __init__(self, X, tets, E, nu, density, h, gravity, contacts, eps, model=models.NEO_HOOKEAN,
-                 bindings=None):
-        self.mesh = Mesh(X, tets)
+                 bindings=None, thickness=None, bend=0.0):
+        # triangles (3 vertices per element) are shells of the given thickness (App. B.1, 2D formulation),
+        # with isometric bending of stiffness `bend`
+        tets = np.asarray(tets)
+        if tets.shape[1] == 3:
+            from .shell import TriMesh
+            self.mesh = TriMesh(X, tets, 1e-3 if thickness is None else thickness)
+            self.bend = float(bend)
+            self.Qb = self.mesh.bending_matrix() if self.bend != 0.0 else None
+        else:
+            self.mesh = Mesh(X, tets)
+            self.bend, self.Qb = 0.0, None
         models.by_model(model, self.mesh.n_tets)  # validates: one name, or one per tet
         self.model = model if isinstance(model, str) else np.asarray(model).copy()
         self.bindings = bindings  # oracle.binding.Bindings or None
@@ -101,8 +111,10 @@ class Step:
         F = mesh.F(q)
         P = models.prox(self.model, F, mu_L, lam_L)
         w = 2.0 * mu_L * mesh.vol
-        r_el = np.einsum("tji,tj->ti", mesh.G, (np.swapaxes(F, 1, 2) - np.swapaxes(P, 1, 2)).reshape(-1, 9))
+        r_el = np.einsum("tji,tj->ti", mesh.G, mesh.vec(F - P))
         Rq = (self.mass[:, None] * (q - qt)).reshape(-1) + h2 * mesh.scatter_vectors(w[:, None] * r_el)
+        if self.Qb is not None:
+            Rq = Rq + h2 * self.bend * (self.Qb @ q.reshape(-1))
         if self.bindings is not None:
             Rq = Rq + self.bindings.residual_term(q, self.h, mesh.n_verts)
         Rn = np.zeros(self.nc)
@@ -137,7 +149,7 @@ class Step:
         rng = np.random.default_rng(seed)
         q = qt.copy()
         t = 1.0
-        while np.linalg.det(self.mesh.F(q)).min() <= 0 and t > 1e-12:
+        while self.mesh.min_jacobian(self.mesh.F(q)) <= 0 and t > 1e-12:
             t *= 0.5
             q = q_prev + t * (qt - q_prev)
         gap0 = 10.0 * self.eps * self.eps / (np.max(self.mass) * np.linalg.norm(self.gravity) + 1e-300)
@@ -238,8 +250,10 @@ class Step:
         P = models.prox(self.model, F, mu_L, lam_L)
         Jp, dP_dmu, dP_dlam = models.prox_derivatives(self.model, F, P, mu_L, lam_L)
         w = 2.0 * mu_L * mesh.vol
-        blocks = h2 * w[:, None, None] * np.einsum("tki,tkl,tlj->tij", mesh.G, np.eye(9) - Jp, mesh.G)
+        blocks = h2 * w[:, None, None] * np.einsum("tki,tkl,tlj->tij", mesh.G, np.eye(mesh.nF) - Jp, mesh.G)
         A_el = sp.diags(np.repeat(self.mass, 3)) + mesh.scatter_blocks(blocks)
+        if self.Qb is not None:
+            A_el = A_el + h2 * self.bend * self.Qb
         if self.bindings is not None:
             A_el = A_el + self.bindings.matrix_term(self.h, mesh.n_verts)
         K, kmu = self.contact_blocks(state, q_prev, mu_c, eps)
@@ -292,8 +306,8 @@ class Step:
         nreg = self.ct.n_regions
         out["dL_dmu_region"] = np.bincount(self.ct.region, weights=dmu_c, minlength=nreg) if self.nc else np.zeros(nreg)
         # elastic parameters
-        from .model import vec
-        Gz = mesh.Gx(z)                       # vec(G_i z)  [n_t, 9]
+        vec = mesh.vec
+        Gz = mesh.Gx(z)                       # vec(G_i z)  [n_t, 9] ([n_t, 6] for triangles)
         mu_L, lam_L = pc["mu_L"], pc["lam_L"]
         pmF = vec(pc["P"] - pc["F"])
         dmu = 2.0 * h2 * mesh.vol * np.sum(Gz * (mu_L[:, None] * vec(pc["dP_dmu"]) + pmF), axis=1)
@@ -303,6 +317,8 @@ class Step:
         out["dL_dlamL"] = dlam
         out["dL_dE"] = dmu * dmu_dE + dlam * dlam_dE
         out["dL_dnu"] = dmu * dmu_dnu + dlam * dlam_dnu
+        if self.Qb is not None:  # the bending force h^2 k_b Q q of the residual
+            out["dL_dbend"] = -h2 * float(z @ (self.Qb @ state.q.reshape(-1)))
         if self.bindings is not None:
             out.update(self.bindings.gradients(state.q, z, h))
         return out

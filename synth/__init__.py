@@ -140,7 +140,33 @@ class Contacts:
                         np.zeros(0), np.zeros(0, np.int32), 1)
 
 
-def detect_contacts(x_prev: np.ndarray, planes, margin: float, candidates=None) -> Contacts:
+@dataclass
+class Sphere:
+    """Rigid sphere collider (center, radius) with friction coefficient mu.  A contact's frame is
+    frozen at the previous positions: n = (x_prev - c)/|x_prev - c| with an orthonormal completion
+    t1, t2, and d_n = n . c + radius, so delta_n = n . x - d_n is the gap along that normal."""
+    center: np.ndarray
+    radius: float
+    mu: float = 0.0
+
+    def contacts(self, x_prev: np.ndarray, margin: float, verts, region: int):
+        c = np.asarray(self.center, float)
+        d = x_prev[verts] - c
+        dist = np.linalg.norm(d, axis=1)
+        sel = verts[dist - self.radius < margin]
+        frames, dn = [], []
+        for v in sel:
+            n = (x_prev[v] - c) / np.linalg.norm(x_prev[v] - c)
+            a = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+            t1 = a - n * (a @ n)
+            t1 /= np.linalg.norm(t1)
+            frames.append(np.stack([n, t1, np.cross(n, t1)]))
+            dn.append(n @ c + self.radius)
+        return sel, np.asarray(frames).reshape(-1, 3, 3), np.asarray(dn, float), np.full(len(sel), self.mu), \
+            np.full(len(sel), region)
+
+
+def detect_contacts(x_prev: np.ndarray, planes, margin: float, candidates=None, spheres=()) -> Contacts:
     """Vertices whose gap to a plane at the previous positions is below ``margin``.
 
     ``candidates`` restricts the search to a vertex subset (e.g. a bottom face).
@@ -173,6 +199,16 @@ def detect_contacts(x_prev: np.ndarray, planes, margin: float, candidates=None) 
             base += n1 * n2
         frames.append(np.repeat(pl.frame[None], len(sel), 0))
         dn.append(np.full(len(sel), pl.offset))
+    for sph in spheres:
+        sel, fr, d, m, r = sph.contacts(x_prev, margin, verts, base)
+        vs.append(sel)
+        frames.append(fr)
+        dn.append(d)
+        mus.append(m)
+        reg.append(r)
+        base += 1
+    if not vs:
+        return Contacts.empty()
     v = np.concatenate(vs).astype(np.int32)
     return Contacts(v, np.concatenate(frames).reshape(-1, 3, 3), np.concatenate(dn),
                     np.zeros((len(v), 2)), np.concatenate(mus), np.concatenate(reg).astype(np.int32),
@@ -198,6 +234,9 @@ class Scene:
     margin: float = 2e-3
     eps: float = 1e-4
     name: str = ""
+    spheres: list = field(default_factory=list)
+    thickness: float = None  # triangle meshes (shells): thickness tau (m); None for tet meshes
+    bend: float = 0.0        # shells: isometric bending stiffness k_b
 
     @property
     def n_verts(self):
@@ -208,9 +247,9 @@ class Scene:
         return int(self.tets.shape[0])
 
     def contacts(self, x_prev):
-        if not self.planes:
+        if not self.planes and not self.spheres:
             return Contacts.empty()
-        return detect_contacts(x_prev, self.planes, self.margin, self.contact_candidates)
+        return detect_contacts(x_prev, self.planes, self.margin, self.contact_candidates, self.spheres)
 
 
 @dataclass
@@ -222,6 +261,45 @@ class Problem:
     v0: np.ndarray
     f_ctrl: np.ndarray
     q_target: np.ndarray
+
+
+def tri_grid(nx: int, ny: int, size_x: float, size_y: float, origin=(0.0, 0.0, 0.0)):
+    """Flat (nx+1) x (ny+1) vertex grid in the z = origin[2] plane, two triangles per cell with
+    alternating diagonals, counter-clockwise seen from +z.  Returns (X [n_v, 3], tris [n_t, 3])."""
+    xs = origin[0] + np.linspace(0.0, size_x, nx + 1)
+    ys = origin[1] + np.linspace(0.0, size_y, ny + 1)
+    X = np.array([[x, y, origin[2]] for y in ys for x in xs])
+    vid = lambda i, j: i + (nx + 1) * j  # noqa: E731
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    return X, np.asarray(tris, np.int32)
+
+
+def cloth_drape(seed: int = 0, n: int = 31, size: float = 0.3, height: float = 0.005, radius: float = 0.08,
+                E: float = 1e5, nu: float = 0.3, density: float = 1000.0, thickness: float = 1e-3,
+                bend: float = 1e-4, h: float = 0.01, mu: float = 0.0, eps: float = 1e-4,
+                margin: float = 2e-3, sag: float = 0.0) -> Problem:
+    """A square cloth patch of n x n cells (2 triangles each) centred above a sphere collider of the
+    given radius at the origin, its lowest point ``height`` above the sphere's top (sag > 0 bends it
+    over the sphere first: z -= sag r^2 / R^2 at distance r from the axis, R the patch half-width),
+    falling under gravity: the draping cloth of the paper's batched experiment (Sec. 5), with
+    isometric bending.  Default 32 x 32 vertices (1,024), 1,922 triangles, frictionless sphere."""
+    rng = np.random.default_rng(seed)
+    X, tris = tri_grid(n, n, size, size, origin=(-size / 2, -size / 2, radius + height))
+    r2 = X[:, 0] ** 2 + X[:, 1] ** 2
+    X[:, 2] -= sag * r2 / (size / 2) ** 2
+    ntri = len(tris)
+    scene = Scene(X, tris, np.full(ntri, E), np.full(ntri, nu), density, h, np.array([0.0, 0.0, -GRAVITY]), [],
+                  None, margin, eps, f"cloth{n}", spheres=[Sphere(np.zeros(3), radius, mu)], thickness=thickness,
+                  bend=bend)
+    v0 = rng.normal(0.0, 1e-3, X.shape)
+    return Problem(scene, X.copy(), v0, np.zeros_like(X), X + rng.normal(0.0, 1e-3, X.shape))
 
 
 def cube_drop(seed: int = 0, cells: int = 4, edge: float = 0.1, drop: float = 0.01,

@@ -9,9 +9,11 @@ import synth
 from oracle.step import Step
 
 
-def make_step(scene, contacts, E=None, nu=None, eps=None, model="neo_hookean"):
+def make_step(scene, contacts, E=None, nu=None, eps=None, model="neo_hookean", bend=None):
     return Step(scene.X, scene.tets, scene.E if E is None else E, scene.nu if nu is None else nu,
-                scene.density, scene.h, scene.gravity, contacts, scene.eps if eps is None else eps, model)
+                scene.density, scene.h, scene.gravity, contacts, scene.eps if eps is None else eps, model,
+                thickness=getattr(scene, "thickness", None),
+                bend=getattr(scene, "bend", 0.0) if bend is None else bend)
 
 
 @functools.lru_cache(maxsize=None)

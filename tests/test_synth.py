@@ -68,3 +68,32 @@ def test_actuation_draws():
     assert np.allclose(np.linalg.norm(d1, axis=1), 1.0, atol=1e-12)
     a3, _ = synth.random_actuation(100, seed=6)
     assert not np.array_equal(a1, a3)
+
+
+def test_cloth_grid_and_sphere_contacts():
+    """The cloth recipe: an (n+1)^2 grid of 2 n^2 counter-clockwise triangles (alternating
+    diagonals), above a sphere; each sphere contact's frame rows are orthonormal with the normal
+    radial at the previous position, and n . x - d_n is the distance to the sphere there."""
+    X, T = synth.tri_grid(4, 3, 0.4, 0.3)
+    assert X.shape == (20, 3) and T.shape == (24, 3)
+    e1, e2 = X[T[:, 1]] - X[T[:, 0]], X[T[:, 2]] - X[T[:, 0]]
+    assert np.all(np.cross(e1, e2)[:, 2] > 0) and np.allclose(0.5 * np.cross(e1, e2)[:, 2].sum(), 0.12)
+    pb = synth.cloth_drape()
+    sc = pb.scene
+    assert sc.X.shape[0] == 1024 and sc.tets.shape[0] == 1922 and sc.thickness > 0 and sc.bend > 0
+    a, b = _arrays(pb), _arrays(synth.cloth_drape())
+    for x, y in zip(a, b):
+        assert np.asarray(x).tobytes() == np.asarray(y).tobytes()
+    sph = synth.Sphere(np.array([0.1, -0.2, 0.0]), 0.3, mu=0.4)
+    rng = np.random.default_rng(0)
+    d = rng.normal(size=(50, 3))
+    xp = sph.center + d / np.linalg.norm(d, axis=1)[:, None] * rng.uniform(0.29, 0.31, (50, 1))
+    verts, frames, dn, mu, reg = sph.contacts(xp, 2e-3, np.arange(50), 0)
+    assert len(verts) > 0 and np.all(mu == 0.4) and np.all(reg == 0)
+    assert np.allclose(np.einsum("cij,ckj->cik", frames, frames), np.eye(3), atol=1e-12)
+    assert np.all(np.linalg.det(frames) > 0)
+    dist = np.linalg.norm(xp[verts] - sph.center, axis=1) - sph.radius
+    assert np.all(dist < 2e-3)
+    assert np.allclose(np.einsum("ci,ci->c", frames[:, 0], xp[verts]) - dn, dist, atol=1e-14)
+    ct = synth.detect_contacts(xp, [], 2e-3, None, [sph])
+    assert np.array_equal(ct.vertex, verts) and ct.n_regions == 1
