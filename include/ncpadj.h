@@ -148,6 +148,43 @@ void ncpadj_scene_destroy(ncpadj_scene scene);
 ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_scene_desc* descs,
                                         ncpadj_scene* out);
 
+/* Shells: a mesh of triangles with thickness tau and isometric bending, the 2D formulation of
+ * App. B.1.  A triangle's F = D_s D_m^{-1} is 3 x 2 (D_m: the rest edges in the triangle's own
+ * plane); its projection p(F) uses the thin SVD F = U diag(sigma) V^T of the same three models
+ * (ncpadj_scene_set_model), with the out-of-plane rows of dP/dF equal to theta_j / sigma_j; the
+ * element weight is w_i = 2 mu_i A_i tau and the lumped mass m_v = density tau sum A_i / 3.
+ * Bending (Bergou et al. 2006, a quadratic model for inextensible surfaces): per interior edge e
+ * with the cotangent stencil K_e of its four vertices, the energy 1/2 bend (3/(A_1+A_2))
+ * |sum_a K_a x_a|^2, whose constant Hessian bend Q joins A_s (so the Woodbury preconditioner and
+ * the sparse inverse include it) and script_A; the adjoint returns dL/d(bend) per mesh.
+ *   rest_pos [n_verts*3] float64, tris [n_tris*3] int32 (any orientation; an edge shared by more
+ *   than two triangles is an error), E and nu [n_tris], density > 0 (kg/m^3), h > 0 (s),
+ *   thickness > 0 (m), bend >= 0 (N m). */
+typedef struct {
+  int32_t n_verts, n_tris;
+  const double* rest_pos;
+  const int32_t* tris;
+  const double* E;
+  const double* nu;
+  double density, h;
+  double thickness;
+  double bend;
+} ncpadj_shell_desc;
+
+/* Build a scene of n_scenes >= 1 shells (a batch as in ncpadj_scene_create_batch: meshes in order,
+ * shared h).  Every other call takes it like a tet scene with n_tets = the triangles; actuation
+ * fibres and bindings inside elements (ncpadj_bindings.tet) are not supported on shells.  Errors:
+ * INVALID_ARG (sizes, indices out of range, a degenerate rest triangle, a non-manifold edge, bad
+ * material, thickness or bend), OOM, CUDA. */
+ncpadj_status ncpadj_scene_create_shells(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_shell_desc* descs,
+                                         ncpadj_scene* out);
+/* New bending stiffness of each mesh of a shell scene (HOST array [n_scenes], each >= 0): A_s,
+ * its factor and the sparse inverse are rebuilt as by ncpadj_scene_refactor (same rules).  Errors:
+ * INVALID_ARG (NULL, a tet scene, a value out of range: nothing is changed), OOM, CUDA. */
+ncpadj_status ncpadj_scene_set_bending(ncpadj_scene scene, const double* bend, void* stream);
+/* The current bending stiffness of each mesh (HOST array [n_scenes]; 0 for tet scenes). */
+ncpadj_status ncpadj_scene_get_bending(ncpadj_scene scene, double* bend);
+
 /* New material for an existing scene (per-tet Young's modulus E > 0 and Poisson ratio nu in
  * (-1, 0.5), HOST arrays [n_tets] over the whole scene, batch meshes concatenated).  Everything that
  * depends on the material is rebuilt from the scene's kept geometry: the Lame parameters and their
@@ -168,6 +205,8 @@ typedef struct {
   int64_t nnz_Linv;        /* nonzeros of its explicit inverse S */
   double ms_factor;        /* host time of ordering + factorisation + inversion (summed over meshes) */
   int32_t n_scenes;        /* meshes in the scene (1 unless built by ncpadj_scene_create_batch) */
+  int32_t element_verts;   /* 4: tets, 3: triangles (ncpadj_scene_create_shells) */
+  int32_t n_hinges;        /* interior edges carrying bending (shells) */
 } ncpadj_scene_info;
 ncpadj_status ncpadj_scene_get_info(ncpadj_scene scene, ncpadj_scene_info* out);
 
@@ -235,7 +274,9 @@ typedef struct {
  *   dL_dact                              [n_tets]    (FP32; per-tet activation, see
  *                                                     ncpadj_scene_set_fibres)
  *   dL_dbinding_target                   [n_b*3]     (binding targets d_b)
- *   dL_dcompliance                       [n_b]       (binding compliances E_b) */
+ *   dL_dcompliance                       [n_b]       (binding compliances E_b)
+ *   dL_dbend                             [n_scenes]  (bending stiffness of each shell mesh;
+ *                                                     -h^2 z^T Q q, 0 for tet scenes) */
 typedef struct {
   double* dL_dq_prev;
   double* dL_dv_prev;
@@ -248,6 +289,7 @@ typedef struct {
   float* dL_dact;  /* [n_tets] activation gradient; requires the scene's fibres (see below) */
   double* dL_dbinding_target;  /* [n_b*3]; requires state.bindings */
   double* dL_dcompliance;      /* [n_b];   requires state.bindings */
+  double* dL_dbend;            /* [n_scenes] */
 } ncpadj_grads;
 
 /* Solver options; fill with ncpadj_options_default first.

@@ -45,9 +45,16 @@ class _SceneDesc(C.Structure):
                 ("E", C.c_void_p), ("nu", C.c_void_p), ("density", C.c_double), ("h", C.c_double)]
 
 
+class _ShellDesc(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("rest_pos", C.c_void_p), ("tris", C.c_void_p),
+                ("E", C.c_void_p), ("nu", C.c_void_p), ("density", C.c_double), ("h", C.c_double),
+                ("thickness", C.c_double), ("bend", C.c_double)]
+
+
 class _SceneInfo(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("n_blocks", C.c_int32), ("nnz_L", C.c_int64),
-                ("nnz_Linv", C.c_int64), ("ms_factor", C.c_double), ("n_scenes", C.c_int32)]
+                ("nnz_Linv", C.c_int64), ("ms_factor", C.c_double), ("n_scenes", C.c_int32),
+                ("element_verts", C.c_int32), ("n_hinges", C.c_int32)]
 
 
 class _Contacts(C.Structure):
@@ -73,7 +80,7 @@ class _Grads(C.Structure):
     _fields_ = [("dL_dq_prev", C.c_void_p), ("dL_dv_prev", C.c_void_p), ("dL_dfext", C.c_void_p),
                 ("dL_dE", C.c_void_p), ("dL_dnu", C.c_void_p), ("dL_dmu", C.c_void_p),
                 ("dL_dmu_contact", C.c_void_p), ("z", C.c_void_p), ("dL_dact", C.c_void_p),
-                ("dL_dbinding_target", C.c_void_p), ("dL_dcompliance", C.c_void_p)]
+                ("dL_dbinding_target", C.c_void_p), ("dL_dcompliance", C.c_void_p), ("dL_dbend", C.c_void_p)]
 
 
 class _Options(C.Structure):
@@ -108,7 +115,8 @@ class _ForwardStats(C.Structure):
 
 EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpadj_ctx_create", "ncpadj_ctx_destroy",
            "ncpadj_scene_create", "ncpadj_scene_create_batch", "ncpadj_scene_destroy", "ncpadj_scene_get_info",
-           "ncpadj_scene_refactor", "ncpadj_scene_get_material",
+           "ncpadj_scene_refactor", "ncpadj_scene_get_material", "ncpadj_scene_create_shells",
+           "ncpadj_scene_set_bending", "ncpadj_scene_get_bending",
            "ncpadj_options_default", "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step",
            "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc", "ncpadj_elastic_solve_mixed", "ncpadj_dense_inverse",
            "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
@@ -134,6 +142,9 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_scene_destroy.argtypes = [C.c_void_p]
     lib.ncpadj_scene_create_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_SceneDesc), C.POINTER(C.c_void_p)]
     lib.ncpadj_scene_get_info.argtypes = [C.c_void_p, C.POINTER(_SceneInfo)]
+    lib.ncpadj_scene_create_shells.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_ShellDesc), C.POINTER(C.c_void_p)]
+    lib.ncpadj_scene_set_bending.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.ncpadj_scene_get_bending.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_refactor.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_get_material.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ncpadj_options_default.argtypes = [C.POINTER(_Options)]
@@ -190,29 +201,38 @@ class Scene:
     """Mesh + material + step size; builds the elastic factor on construction (host arrays).
 
     ``Scene.batch(ctx, meshes, h)`` builds a batch: the disjoint union of several meshes, each
-    ``(X, tets, E, nu, density)``, numbered one after the other (``vertex_offsets``)."""
+    ``(X, tets, E, nu, density)``, numbered one after the other (``vertex_offsets``).
+    ``Scene.shells(ctx, meshes, h)`` builds one or more triangle meshes (shells), each
+    ``(X, tris, E, nu, density, thickness, bend)``; their elements take the place of the tets
+    (``n_tets`` counts triangles)."""
 
-    def __init__(self, ctx: Context, X, tets, E, nu, density: float, h: float, _batch=None):
+    def __init__(self, ctx: Context, X, tets, E, nu, density: float, h: float, _batch=None, _shells=None):
         self.ctx = ctx
         self.lib = ctx.lib
-        meshes = _batch if _batch is not None else [(X, tets, E, nu, density)]
+        if _shells is not None:
+            meshes = _shells
+        else:
+            meshes = [m + (0.0, 0.0) for m in (_batch if _batch is not None else [(X, tets, E, nu, density)])]
         self._keep = []
-        descs = (_SceneDesc * len(meshes))()
+        descs = (_ShellDesc if _shells is not None else _SceneDesc) * len(meshes)
+        descs = descs()
         offs = [0]
         toffs = [0]
-        for i, (Xi, Ti, Ei, nui, rho) in enumerate(meshes):
+        for i, (Xi, Ti, Ei, nui, rho, tau, kb) in enumerate(meshes):
             Xt = torch.as_tensor(Xi, dtype=torch.float64).contiguous().cpu()
             Tt = torch.as_tensor(Ti, dtype=torch.int32).contiguous().cpu()
             nt = Tt.shape[0]
             Et = torch.as_tensor(Ei, dtype=torch.float64).expand(nt).contiguous().cpu()
             nut = torch.as_tensor(nui, dtype=torch.float64).expand(nt).contiguous().cpu()
             self._keep += [Xt, Tt, Et, nut]
-            descs[i] = _SceneDesc(Xt.shape[0], nt, Xt.data_ptr(), Tt.data_ptr(), Et.data_ptr(), nut.data_ptr(),
-                                  float(rho), float(h))
+            args = (Xt.shape[0], nt, Xt.data_ptr(), Tt.data_ptr(), Et.data_ptr(), nut.data_ptr(), float(rho), float(h))
+            descs[i] = _ShellDesc(*args, float(tau), float(kb)) if _shells is not None else _SceneDesc(*args)
             offs.append(offs[-1] + Xt.shape[0])
             toffs.append(toffs[-1] + nt)
         hnd = C.c_void_p()
-        if _batch is None:
+        if _shells is not None:
+            _check(self.lib, self.lib.ncpadj_scene_create_shells(ctx.handle, len(meshes), descs, C.byref(hnd)))
+        elif _batch is None:
             _check(self.lib, self.lib.ncpadj_scene_create(ctx.handle, C.byref(descs[0]), C.byref(hnd)))
         else:
             _check(self.lib, self.lib.ncpadj_scene_create_batch(ctx.handle, len(meshes), descs, C.byref(hnd)))
@@ -226,6 +246,28 @@ class Scene:
     @classmethod
     def batch(cls, ctx: Context, meshes, h: float) -> "Scene":
         return cls(ctx, None, None, None, None, None, h, _batch=list(meshes))
+
+    @classmethod
+    def shells(cls, ctx: Context, meshes, h: float) -> "Scene":
+        return cls(ctx, None, None, None, None, None, h, _shells=list(meshes))
+
+    @property
+    def n_scenes(self) -> int:
+        return len(self.vertex_offsets) - 1
+
+    def set_bending(self, bend, stream=None) -> None:
+        """New bending stiffness of each shell mesh (scalar or [n_scenes]); rebuilds the elastic factor."""
+        b = torch.as_tensor(bend, dtype=torch.float64).expand(self.n_scenes).contiguous().cpu()
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream(self.ctx.device).cuda_stream
+        _check(self.lib, self.lib.ncpadj_scene_set_bending(self.handle, C.c_void_p(b.data_ptr()),
+                                                           C.c_void_p(stream or 0)))
+
+    def bending(self):
+        """The bending stiffness of each mesh (CPU float64 [n_scenes]; zeros for tet scenes)."""
+        b = torch.empty(self.n_scenes, dtype=torch.float64)
+        _check(self.lib, self.lib.ncpadj_scene_get_bending(self.handle, C.c_void_p(b.data_ptr())))
+        return b
 
     def set_fibres(self, fibre) -> None:
         """Unit fibre directions [n_tets, 3] of the per-tet actuation (host array)."""
@@ -351,6 +393,8 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
               "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (max(nc, 0),), "dL_dact": (nt,),
               "dL_dbinding_target": (nb, 3), "dL_dcompliance": (nb,)}
+    if "dL_dbend" in want:
+        shapes["dL_dbend"] = (scene.n_scenes,)
     for k in want:
         if k not in outputs:
             dt = torch.float32 if k == "dL_dact" else torch.float64
@@ -365,9 +409,7 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
     bptr, _bkeep = _bindings_ref(bindings)
     stt = _State(_ptr(q), _ptr(q_prev), _ptr(lam) if nc else None, bptr)
     sd = _Seed(_ptr(dL_dq), _ptr(dL_dv))
-    gr = _Grads(*[_ptr(outputs.get(k)) for k in ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu",
-                                                 "dL_dmu", "dL_dmu_contact", "z", "dL_dact", "dL_dbinding_target",
-                                                 "dL_dcompliance")])
+    gr = _Grads(*[_ptr(outputs.get(k)) for k in _GRAD_FIELDS])
     opt = _Options()
     lib.ncpadj_options_default(C.byref(opt))
     opt.eps, opt.rtol, opt.max_iters, opt.gmres_restart = float(eps), float(rtol), int(max_iters), int(restart)
@@ -389,7 +431,7 @@ def adjoint_step(scene: Scene, contacts: Optional[Contacts], q, q_prev, lam, dL_
 
 
 _GRAD_FIELDS = ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact", "z", "dL_dact",
-                "dL_dbinding_target", "dL_dcompliance")
+                "dL_dbinding_target", "dL_dcompliance", "dL_dbend")
 
 
 def _options(lib, eps, rtol, max_iters, restart, precision, cap_precision, precond, solver, memory, cap_block,
@@ -442,7 +484,8 @@ class BatchCall:
             nc = ct.n if ct is not None else 0
             nreg = ct.n_regions if ct is not None else 1
             shapes = {"dL_dq_prev": (nv, 3), "dL_dv_prev": (nv, 3), "dL_dfext": (nv, 3), "z": (nv, 3), "dL_dE": (nt,),
-                      "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (nc,), "dL_dact": (nt,)}
+                      "dL_dnu": (nt,), "dL_dmu": (nreg,), "dL_dmu_contact": (nc,), "dL_dact": (nt,),
+                      "dL_dbend": (1,)}
             o = dict(outputs[s]) if outputs is not None else {}
             for k in want:
                 if k in o:

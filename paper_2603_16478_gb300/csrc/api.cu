@@ -50,22 +50,181 @@ static ncpadj_status fail(const Error& e) {
 // ------------------------------------------------------------------------------------------
 // scene set-up
 // ------------------------------------------------------------------------------------------
+// One mesh of a scene: tets (nvpe = 4), or the triangles of a shell (nvpe = 3) with its thickness
+// and bending stiffness.
+struct MeshSpec {
+  int nv = 0, ne = 0, nvpe = 4;
+  const double* rest_pos = nullptr;
+  const int32_t* elems = nullptr;
+  const double* E = nullptr;
+  const double* nu = nullptr;
+  double density = 0, h = 0, thickness = 0, bend = 0;
+};
+static MeshSpec spec_of(const ncpadj_scene_desc& d) {
+  MeshSpec m;
+  m.nv = d.n_verts;
+  m.ne = d.n_tets;
+  m.rest_pos = d.rest_pos;
+  m.elems = d.tets;
+  m.E = d.E;
+  m.nu = d.nu;
+  m.density = d.density;
+  m.h = d.h;
+  return m;
+}
+static MeshSpec spec_of(const ncpadj_shell_desc& d) {
+  MeshSpec m;
+  m.nv = d.n_verts;
+  m.ne = d.n_tris;
+  m.nvpe = 3;
+  m.rest_pos = d.rest_pos;
+  m.elems = d.tris;
+  m.E = d.E;
+  m.nu = d.nu;
+  m.density = d.density;
+  m.h = d.h;
+  m.thickness = d.thickness;
+  m.bend = d.bend;
+  return m;
+}
+
 // One mesh's share of a (batch) scene, computed independently of the others.
 struct MeshPart {
   std::vector<double> gvec, vol, mu, lam, lame_d, mass;
   std::vector<int32_t> row_ptr, col, slot, diag_slot;  // local vertex numbering
+  std::vector<int32_t> bidx, bslot;                    // bending hinges: vertices [4], slots [16]
+  std::vector<double> bcoef;                           // K_0..K_3, 3/(A_1+A_2)
   ElasticFactor F;
   double ms_factor = 0;
 };
 
-static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
-  const int nv = d.n_verts, nt = d.n_tets;
-  NCPADJ_REQUIRE(nv > 0 && nt > 0, "n_verts and n_tets must be positive");
-  NCPADJ_REQUIRE(d.rest_pos && d.tets && d.E && d.nu, "scene arrays must not be NULL");
+// Rest operator of tet t: g_a = row (a-1) of D_m^{-1} for a = 1..3, g_0 = -(g_1 + g_2 + g_3), so that
+// F = sum_a x_a g_a^T; returns the volume.
+static double tet_rest(const double* X, const int v[4], int t, double* g) {
+  double Dm[3][3];  // columns X_a - X_0
+  for (int a = 1; a < 4; ++a)
+    for (int r = 0; r < 3; ++r) Dm[r][a - 1] = X[3 * v[a] + r] - X[3 * v[0] + r];
+  double det = Dm[0][0] * (Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1]) -
+               Dm[0][1] * (Dm[1][0] * Dm[2][2] - Dm[1][2] * Dm[2][0]) +
+               Dm[0][2] * (Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0]);
+  NCPADJ_REQUIRE(det > 0 && std::isfinite(det), "tet " + std::to_string(t) + " is inverted or degenerate at rest");
+  double B[3][3];  // inverse by cofactors
+  B[0][0] = (Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1]) / det;
+  B[0][1] = (Dm[0][2] * Dm[2][1] - Dm[0][1] * Dm[2][2]) / det;
+  B[0][2] = (Dm[0][1] * Dm[1][2] - Dm[0][2] * Dm[1][1]) / det;
+  B[1][0] = (Dm[1][2] * Dm[2][0] - Dm[1][0] * Dm[2][2]) / det;
+  B[1][1] = (Dm[0][0] * Dm[2][2] - Dm[0][2] * Dm[2][0]) / det;
+  B[1][2] = (Dm[0][2] * Dm[1][0] - Dm[0][0] * Dm[1][2]) / det;
+  B[2][0] = (Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0]) / det;
+  B[2][1] = (Dm[0][1] * Dm[2][0] - Dm[0][0] * Dm[2][1]) / det;
+  B[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) / det;
+  for (int k = 0; k < 3; ++k) {
+    g[k] = -(B[0][k] + B[1][k] + B[2][k]);
+    for (int a = 1; a < 4; ++a) g[3 * a + k] = B[a - 1][k];
+  }
+  return det / 6.0;
+}
+
+static inline void sub3(const double* X, int i, int j, double* out) {
+  for (int r = 0; r < 3; ++r) out[r] = X[3 * i + r] - X[3 * j + r];
+}
+static inline void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Rest operator of triangle t in its own plane: orthonormal axes a_1 = e_1/|e_1|, a_2 = n x a_1,
+// D_m = [a_i . e_j] (2 x 2), g_a = row (a-1) of D_m^{-1} for a = 1, 2, g_0 = -(g_1 + g_2); returns
+// the area.
+static double tri_rest(const double* X, const int v[3], int t, double* g) {
+  double e1[3], e2[3], n[3];
+  sub3(X, v[1], v[0], e1);
+  sub3(X, v[2], v[0], e2);
+  cross3(e1, e2, n);
+  const double area2 = std::sqrt(dot3(n, n)), l1 = std::sqrt(dot3(e1, e1));
+  NCPADJ_REQUIRE(area2 > 0 && std::isfinite(area2) && l1 > 0,
+                 "triangle " + std::to_string(t) + " is degenerate at rest");
+  double a1[3], a2[3], nn[3];
+  for (int r = 0; r < 3; ++r) {
+    a1[r] = e1[r] / l1;
+    nn[r] = n[r] / area2;
+  }
+  cross3(nn, a1, a2);
+  const double D00 = dot3(a1, e1), D01 = dot3(a1, e2), D10 = dot3(a2, e1), D11 = dot3(a2, e2);
+  const double det = D00 * D11 - D01 * D10;
+  const double B[2][2] = {{D11 / det, -D01 / det}, {-D10 / det, D00 / det}};
+  for (int k = 0; k < 2; ++k) {
+    g[k] = -(B[0][k] + B[1][k]);
+    g[2 + k] = B[0][k];
+    g[4 + k] = B[1][k];
+  }
+  return 0.5 * area2;
+}
+
+// Isometric bending hinges of a triangle mesh: for every edge (i0, i1) shared by two triangles with
+// opposite vertices i2, i3, the cotangent stencil (Bergou et al. 2006)
+//   K = (c03 + c04, c01 + c02, -c01 - c03, -c02 - c04),
+// c0j the cotangent of the angle at vertex i0 between the edge and (x_ij - x_i0) (j = 2, 3 as c01, c02),
+// c1j the same at i1 (as c03, c04), and 3/(A_1 + A_2) with A_1, A_2 the triangles' areas.
+static void bending_hinges(const MeshSpec& d, MeshPart& P) {
+  const double* X = d.rest_pos;
+  std::vector<std::pair<int64_t, int32_t>> he;  // (edge key, opposite vertex)
+  he.reserve(3 * (size_t)d.ne);
+  for (int t = 0; t < d.ne; ++t) {
+    const int32_t* v = d.elems + 3 * (size_t)t;
+    for (int k = 0; k < 3; ++k) {
+      const int32_t u = v[k], w = v[(k + 1) % 3], o = v[(k + 2) % 3];
+      he.push_back({(int64_t)std::min(u, w) * d.nv + std::max(u, w), o});
+    }
+  }
+  std::sort(he.begin(), he.end());
+  auto cot = [](const double* p, const double* q) {
+    double c[3];
+    cross3(p, q, c);
+    return dot3(p, q) / std::sqrt(dot3(c, c));
+  };
+  for (size_t i = 0; i < he.size();) {
+    size_t j = i;
+    while (j < he.size() && he[j].first == he[i].first) ++j;
+    NCPADJ_REQUIRE(j - i <= 2, "an edge is shared by more than two triangles");
+    if (j - i == 2) {
+      const int i0 = (int)(he[i].first / d.nv), i1 = (int)(he[i].first % d.nv);
+      const int i2 = he[i].second, i3 = he[i + 1].second;
+      double e0[3], e1[3], e2[3], e3[3], e4[3], m0[3], n1[3], n2[3];
+      sub3(X, i1, i0, e0);
+      sub3(X, i2, i0, e1);
+      sub3(X, i3, i0, e2);
+      sub3(X, i2, i1, e3);
+      sub3(X, i3, i1, e4);
+      for (int r = 0; r < 3; ++r) m0[r] = -e0[r];
+      const double c01 = cot(e0, e1), c02 = cot(e0, e2), c03 = cot(m0, e3), c04 = cot(m0, e4);
+      cross3(e0, e1, n1);
+      cross3(e0, e2, n2);
+      const double A = 0.5 * (std::sqrt(dot3(n1, n1)) + std::sqrt(dot3(n2, n2)));
+      const double K[5] = {c03 + c04, c01 + c02, -c01 - c03, -c02 - c04, 3.0 / A};
+      NCPADJ_REQUIRE(std::isfinite(K[0] + K[1] + K[2] + K[3] + K[4]), "a degenerate triangle at a bending hinge");
+      const int32_t ids[4] = {i0, i1, i2, i3};
+      P.bidx.insert(P.bidx.end(), ids, ids + 4);
+      P.bcoef.insert(P.bcoef.end(), K, K + 5);
+    }
+    i = j;
+  }
+}
+
+static void build_part(const MeshSpec& d, double h, MeshPart& P) {
+  const int nv = d.nv, nt = d.ne, k = d.nvpe, gd = k - 1;  // g_a has k - 1 components
+  const std::string en = k == 4 ? "tet " : "triangle ";
+  NCPADJ_REQUIRE(nv > 0 && nt > 0, "n_verts and the element count must be positive");
+  NCPADJ_REQUIRE(d.rest_pos && d.elems && d.E && d.nu, "scene arrays must not be NULL");
   NCPADJ_REQUIRE(d.density > 0 && d.h > 0 && std::isfinite(d.density) && std::isfinite(d.h),
                  "density and h must be positive");
   NCPADJ_REQUIRE(d.h == h, "every scene of a batch must use the same step size h");
-  P.gvec.assign(12 * (size_t)nt, 0.0);
+  if (k == 3)
+    NCPADJ_REQUIRE(d.thickness > 0 && std::isfinite(d.thickness) && d.bend >= 0 && std::isfinite(d.bend),
+                   "a shell needs thickness > 0 and bend >= 0");
+  P.gvec.assign((size_t)k * gd * nt, 0.0);
   P.vol.assign(nt, 0.0);
   P.mu.assign(nt, 0.0);
   P.lam.assign(nt, 0.0);
@@ -73,36 +232,15 @@ static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
   P.mass.assign(nv, 0.0);
   for (int t = 0; t < nt; ++t) {
     int v[4];
-    for (int a = 0; a < 4; ++a) {
-      v[a] = d.tets[4 * t + a];
-      NCPADJ_REQUIRE(v[a] >= 0 && v[a] < nv, "tet " + std::to_string(t) + " has a vertex index out of range");
+    for (int a = 0; a < k; ++a) {
+      v[a] = d.elems[(size_t)k * t + a];
+      NCPADJ_REQUIRE(v[a] >= 0 && v[a] < nv, en + std::to_string(t) + " has a vertex index out of range");
     }
-    double Dm[3][3];  // columns X_a - X_0
-    for (int a = 1; a < 4; ++a)
-      for (int r = 0; r < 3; ++r) Dm[r][a - 1] = d.rest_pos[3 * v[a] + r] - d.rest_pos[3 * v[0] + r];
-    double det = Dm[0][0] * (Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1]) -
-                 Dm[0][1] * (Dm[1][0] * Dm[2][2] - Dm[1][2] * Dm[2][0]) +
-                 Dm[0][2] * (Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0]);
-    NCPADJ_REQUIRE(det > 0 && std::isfinite(det), "tet " + std::to_string(t) + " is inverted or degenerate at rest");
-    double B[3][3];  // inverse by cofactors
-    B[0][0] = (Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1]) / det;
-    B[0][1] = (Dm[0][2] * Dm[2][1] - Dm[0][1] * Dm[2][2]) / det;
-    B[0][2] = (Dm[0][1] * Dm[1][2] - Dm[0][2] * Dm[1][1]) / det;
-    B[1][0] = (Dm[1][2] * Dm[2][0] - Dm[1][0] * Dm[2][2]) / det;
-    B[1][1] = (Dm[0][0] * Dm[2][2] - Dm[0][2] * Dm[2][0]) / det;
-    B[1][2] = (Dm[0][2] * Dm[1][0] - Dm[0][0] * Dm[1][2]) / det;
-    B[2][0] = (Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0]) / det;
-    B[2][1] = (Dm[0][1] * Dm[2][0] - Dm[0][0] * Dm[2][1]) / det;
-    B[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) / det;
-    // g_a = row (a-1) of B for a = 1..3, g_0 = -(g_1 + g_2 + g_3): F = sum_a x_a g_a^T
-    for (int k = 0; k < 3; ++k) {
-      P.gvec[12 * t + k] = -(B[0][k] + B[1][k] + B[2][k]);
-      for (int a = 1; a < 4; ++a) P.gvec[12 * t + 3 * a + k] = B[a - 1][k];
-    }
-    P.vol[t] = det / 6.0;
+    double* g = P.gvec.data() + (size_t)k * gd * t;
+    P.vol[t] = k == 4 ? tet_rest(d.rest_pos, v, t, g) : d.thickness * tri_rest(d.rest_pos, v, t, g);
     const double E = d.E[t], nu = d.nu[t];
     NCPADJ_REQUIRE(E > 0 && nu > -1.0 && nu < 0.5 && std::isfinite(E),
-                   "tet " + std::to_string(t) + ": need E > 0 and -1 < nu < 0.5");
+                   en + std::to_string(t) + ": need E > 0 and -1 < nu < 0.5");
     P.mu[t] = E / (2.0 * (1.0 + nu));
     P.lam[t] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     P.lame_d[4 * t + 0] = 1.0 / (2.0 * (1.0 + nu));
@@ -110,14 +248,21 @@ static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
     P.lame_d[4 * t + 2] = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
     const double q = (1.0 + nu) * (1.0 - 2.0 * nu);
     P.lame_d[4 * t + 3] = E * (1.0 + 2.0 * nu * nu) / (q * q);
-    for (int a = 0; a < 4; ++a) P.mass[v[a]] += d.density * P.vol[t] / 4.0;
+    for (int a = 0; a < k; ++a) P.mass[v[a]] += d.density * P.vol[t] / k;
   }
-  // block pattern: vertices sharing a tet (sorted neighbour lists, self included)
+  P.bidx.clear();
+  P.bcoef.clear();
+  if (k == 3) bending_hinges(d, P);
+  const int nh = (int)P.bidx.size() / 4;
+  // block pattern: vertices sharing an element or a hinge (sorted neighbour lists, self included)
   std::vector<std::vector<int32_t>> nbr(nv);
   for (int v = 0; v < nv; ++v) nbr[v].push_back(v);
   for (int t = 0; t < nt; ++t)
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) nbr[d.elems[(size_t)k * t + a]].push_back(d.elems[(size_t)k * t + b]);
+  for (int e = 0; e < nh; ++e)
     for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) nbr[d.tets[4 * t + a]].push_back(d.tets[4 * t + b]);
+      for (int b = 0; b < 4; ++b) nbr[P.bidx[4 * e + a]].push_back(P.bidx[4 * e + b]);
   P.row_ptr.assign(nv + 1, 0);
   P.col.clear();
   for (int v = 0; v < nv; ++v) {
@@ -131,13 +276,18 @@ static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
     auto b = P.col.begin() + P.row_ptr[u], e = P.col.begin() + P.row_ptr[u + 1];
     return (int32_t)(std::lower_bound(b, e, w) - P.col.begin());
   };
-  P.slot.assign(16 * (size_t)nt, 0);
+  P.slot.assign((size_t)k * k * nt, 0);
   P.diag_slot.assign(nv, 0);
   for (int t = 0; t < nt; ++t)
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) P.slot[16 * t + 4 * a + b] = find_slot(d.tets[4 * t + a], d.tets[4 * t + b]);
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b)
+        P.slot[(size_t)k * k * t + k * a + b] = find_slot(d.elems[(size_t)k * t + a], d.elems[(size_t)k * t + b]);
   for (int v = 0; v < nv; ++v) P.diag_slot[v] = find_slot(v, v);
-  // scalar elastic matrix A_s = M_s + h^2 sum_i w_i (g_a . g_b), w_i = 2 mu_i V_i
+  P.bslot.assign(16 * (size_t)nh, 0);
+  for (int e = 0; e < nh; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) P.bslot[16 * e + 4 * a + b] = find_slot(P.bidx[4 * e + a], P.bidx[4 * e + b]);
+  // scalar elastic matrix A_s = M_s + h^2 sum_i w_i (g_a . g_b) + h^2 bend Q_s, w_i = 2 mu_i V_i
   CsrD As;
   As.n = nv;
   As.ptr.assign(P.row_ptr.begin(), P.row_ptr.end());
@@ -147,12 +297,18 @@ static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
   const double h2 = d.h * d.h;
   for (int t = 0; t < nt; ++t) {
     const double w = 2.0 * P.mu[t] * P.vol[t];
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) {
+    const double* g = P.gvec.data() + (size_t)k * gd * t;
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
         double gg = 0;
-        for (int k = 0; k < 3; ++k) gg += P.gvec[12 * t + 3 * a + k] * P.gvec[12 * t + 3 * b + k];
-        As.val[P.slot[16 * t + 4 * a + b]] += h2 * w * gg;
+        for (int c = 0; c < gd; ++c) gg += g[gd * a + c] * g[gd * b + c];
+        As.val[P.slot[(size_t)k * k * t + k * a + b]] += h2 * w * gg;
       }
+  }
+  for (int e = 0; e < nh; ++e) {
+    const double* K = P.bcoef.data() + 5 * (size_t)e;
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) As.val[P.bslot[16 * e + 4 * a + b]] += h2 * d.bend * K[4] * K[a] * K[b];
   }
   auto t0 = std::chrono::steady_clock::now();
   factor_elastic(As, d.rest_pos, P.F);
@@ -162,9 +318,12 @@ static void build_part(const ncpadj_scene_desc& d, double h, MeshPart& P) {
 // A scene is the disjoint union of one or more meshes (a batch): vertex and tet ids of mesh s are
 // offset by the counts of meshes 0..s-1.  Each mesh's factor is computed independently (in
 // parallel) and the union's matrices are block-diagonal.
-static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) {
+static void build_scene(Scene& S, const MeshSpec* descs, int n_scenes) {
   NCPADJ_REQUIRE(n_scenes >= 1 && descs, "need at least one scene description");
   const double h = descs[0].h;
+  const int nvpe = descs[0].nvpe;
+  for (int i = 0; i < n_scenes; ++i)
+    NCPADJ_REQUIRE(descs[i].nvpe == nvpe, "a batch mixes tet meshes and shells");
   std::vector<MeshPart> parts(n_scenes);
   std::vector<Error> errs(n_scenes, Error{NCPADJ_OK, ""});
   {
@@ -193,16 +352,18 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
   S.voff.assign(n_scenes + 1, 0);
   S.toff.assign(n_scenes + 1, 0);
   for (int i = 0; i < n_scenes; ++i) {
-    S.voff[i + 1] = S.voff[i] + descs[i].n_verts;
-    S.toff[i + 1] = S.toff[i] + descs[i].n_tets;
+    S.voff[i + 1] = S.voff[i] + descs[i].nv;
+    S.toff[i + 1] = S.toff[i] + descs[i].ne;
   }
   const int nv = S.voff[n_scenes], nt = S.toff[n_scenes];
   S.nv = nv;
   S.nt = nt;
   S.h = h;
   S.density = descs[0].density;
-  std::vector<double> gvec, vol, mu, lam, lame_d;
-  std::vector<int32_t> tets, row_ptr(1, 0), col, slot, diag_slot, perm, iperm, scene_of_vertex;
+  S.nvpe = nvpe;
+  std::vector<double> gvec, vol, mu, lam, lame_d, bcoef, bkb;
+  std::vector<int32_t> tets, row_ptr(1, 0), col, slot, diag_slot, perm, iperm, scene_of_vertex, bidx, bslot,
+      beoff(1, 0);
   S.mass.clear();
   CsrD Su, Stu;  // union sparse inverse (position space of the union = concatenated positions)
   Su.n = Stu.n = nv;
@@ -220,14 +381,19 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
     lam.insert(lam.end(), P.lam.begin(), P.lam.end());
     lame_d.insert(lame_d.end(), P.lame_d.begin(), P.lame_d.end());
     S.mass.insert(S.mass.end(), P.mass.begin(), P.mass.end());
-    for (int t = 0; t < descs[i].n_tets * 4; ++t) tets.push_back(descs[i].tets[t] + vo);
-    for (int v = 0; v < descs[i].n_verts; ++v) row_ptr.push_back(bo + P.row_ptr[v + 1]);
+    for (size_t t = 0; t < (size_t)descs[i].ne * nvpe; ++t) tets.push_back(descs[i].elems[t] + vo);
+    for (int v = 0; v < descs[i].nv; ++v) row_ptr.push_back(bo + P.row_ptr[v + 1]);
+    for (int32_t x : P.bidx) bidx.push_back(x + vo);
+    for (int32_t x : P.bslot) bslot.push_back(x + bo);
+    bcoef.insert(bcoef.end(), P.bcoef.begin(), P.bcoef.end());
+    bkb.insert(bkb.end(), P.bidx.size() / 4, descs[i].bend);
+    beoff.push_back(beoff.back() + (int32_t)(P.bidx.size() / 4));
     for (int32_t c : P.col) col.push_back(c + vo);
     for (int32_t x : P.slot) slot.push_back(x + bo);
     for (int32_t x : P.diag_slot) diag_slot.push_back(x + bo);
     for (int32_t x : P.F.perm) perm.push_back(x + vo);
     for (int32_t x : P.F.iperm) iperm.push_back(x + vo);
-    scene_of_vertex.insert(scene_of_vertex.end(), descs[i].n_verts, i);
+    scene_of_vertex.insert(scene_of_vertex.end(), descs[i].nv, i);
     const int64_t so = (int64_t)Su.col.size(), sto = (int64_t)Stu.col.size();
     for (int r = 0; r < P.F.n; ++r) {
       Su.ptr.push_back(so + P.F.S.ptr[r + 1]);
@@ -258,6 +424,12 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
   upload(S.perm, perm);
   upload(S.iperm, iperm);
   upload(S.scene_of_vertex, scene_of_vertex);
+  S.n_bend = beoff.back();
+  upload(S.bend_idx, bidx);
+  upload(S.bend_coef, bcoef);
+  upload(S.bend_kb, bkb);
+  upload(S.bend_slot, bslot);
+  upload(S.bend_eoff, beoff);
   upload(S.S_ptr, Su.ptr);
   upload(S.S_val, Su.val);
   upload(S.St_ptr, Stu.ptr);
@@ -346,35 +518,52 @@ static void build_scene(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) 
 }
 
 // host copies of the meshes a scene was built from, so that it can be refactored with new materials
-static void keep_geometry(Scene& S, const ncpadj_scene_desc* descs, int n_scenes) {
+static void keep_geometry(Scene& S, const MeshSpec* descs, int n_scenes) {
   S.geo_pos.assign(n_scenes, {});
   S.geo_tets.assign(n_scenes, {});
   S.geo_density.assign(n_scenes, 0.0);
+  S.geo_thickness.assign(n_scenes, 0.0);
+  S.mat_bend.assign(n_scenes, 0.0);
   S.mat_E.clear();
   S.mat_nu.clear();
   for (int i = 0; i < n_scenes; ++i) {
-    const ncpadj_scene_desc& d = descs[i];
-    S.geo_pos[i].assign(d.rest_pos, d.rest_pos + 3 * (size_t)d.n_verts);
-    S.geo_tets[i].assign(d.tets, d.tets + 4 * (size_t)d.n_tets);
+    const MeshSpec& d = descs[i];
+    S.geo_pos[i].assign(d.rest_pos, d.rest_pos + 3 * (size_t)d.nv);
+    S.geo_tets[i].assign(d.elems, d.elems + (size_t)d.nvpe * d.ne);
     S.geo_density[i] = d.density;
-    S.mat_E.insert(S.mat_E.end(), d.E, d.E + d.n_tets);
-    S.mat_nu.insert(S.mat_nu.end(), d.nu, d.nu + d.n_tets);
+    S.geo_thickness[i] = d.thickness;
+    S.mat_bend[i] = d.bend;
+    S.mat_E.insert(S.mat_E.end(), d.E, d.E + d.ne);
+    S.mat_nu.insert(S.mat_nu.end(), d.nu, d.nu + d.ne);
   }
 }
 
-// New Young's moduli and Poisson ratios (host arrays [n_tets] over the whole scene): every
-// material-dependent array and the elastic factor are rebuilt from the kept geometry.
-static void refactor_scene(Scene& S, const double* E, const double* nu) {
+// New Young's moduli and Poisson ratios (host arrays [n_tets] over the whole scene) and bending
+// stiffnesses ([n_scenes], shells): every material-dependent array and the elastic factor are
+// rebuilt from the kept geometry.
+static void refactor_scene(Scene& S, const double* E, const double* nu, const double* bend) {
   const int ns = S.n_scenes;
-  std::vector<ncpadj_scene_desc> descs(ns);
+  const std::vector<double> e(E, E + S.nt), n(nu, nu + S.nt), b(bend, bend + ns);  // may alias S.mat_*
+  std::vector<MeshSpec> descs(ns);
   for (int i = 0; i < ns; ++i) {
+    MeshSpec& m = descs[i];
     const int t0 = S.toff[i];
-    descs[i] = ncpadj_scene_desc{S.voff[i + 1] - S.voff[i], S.toff[i + 1] - S.toff[i], S.geo_pos[i].data(),
-                                 S.geo_tets[i].data(), E + t0, nu + t0, S.geo_density[i], S.h};
+    m.nv = S.voff[i + 1] - S.voff[i];
+    m.ne = S.toff[i + 1] - S.toff[i];
+    m.nvpe = S.nvpe;
+    m.rest_pos = S.geo_pos[i].data();
+    m.elems = S.geo_tets[i].data();
+    m.E = e.data() + t0;
+    m.nu = n.data() + t0;
+    m.density = S.geo_density[i];
+    m.h = S.h;
+    m.thickness = S.geo_thickness[i];
+    m.bend = b[i];
   }
   build_scene(S, descs.data(), ns);
-  S.mat_E.assign(E, E + S.nt);
-  S.mat_nu.assign(nu, nu + S.nt);
+  S.mat_E = e;
+  S.mat_nu = n;
+  S.mat_bend = b;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -672,8 +861,16 @@ struct Engine {
     launch_bsr_init(nv, S.nb, S.diag_slot.as<int32_t>(), S.massd.as<double>(), b64, b32, st);
     TetArgs ta{nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(), S.lam.as<double>(),
                S.slot.as<int32_t>(), q, h, b64, b32, S.tetdata.as<double>(), flags, S.model_ptr()};
-    if (mixed) launch_tet_assemble32(ta, st);
-    else launch_tet_assemble64(ta, st);
+    if (S.nvpe == 3) {
+      if (mixed) launch_tri_assemble32(ta, st);
+      else launch_tri_assemble64(ta, st);
+      launch_bend_blocks(S.n_bend, S.bend_idx.as<int32_t>(), S.bend_coef.as<double>(), S.bend_kb.as<double>(),
+                         S.bend_slot.as<int32_t>(), h, b64, b32, st);
+    } else if (mixed) {
+      launch_tet_assemble32(ta, st);
+    } else {
+      launch_tet_assemble64(ta, st);
+    }
     if (nc) launch_contact_blocks(contact_args(q, q_prev, lambda, eps), st);
     if (in.nbind && in.btet)
       launch_binding_blocks_bary(in.nbind, in.btet, in.bbary, in.bcompliance, S.slot.as<int32_t>(), h, b64, b32, st);
@@ -1475,6 +1672,7 @@ void take_bindings(Scene& S, const ncpadj_bindings* bd, bool host_mem, Inputs& i
   if (bd->n_bindings == 0) return;
   const bool bary = bd->tet || bd->bary;
   NCPADJ_REQUIRE(!bary || (bd->tet && bd->bary), "bindings need both tet and bary, or neither");
+  NCPADJ_REQUIRE(!bary || S.nvpe == 4, "bindings inside elements (tet, bary) need a tet scene");
   NCPADJ_REQUIRE((bary || bd->vertex) && bd->target && bd->compliance,
                  "binding arrays vertex (or tet and bary), target, compliance are required");
   NCPADJ_REQUIRE(!host_mem, "bindings need options.memory = NCPADJ_MEM_DEVICE");
@@ -1677,7 +1875,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   ncpadj_grads go{};
   if (grads) go = *grads;
   if (host_mem) {  // device staging for outputs
-    size_t need = (size_t)4 * N + 2 * (size_t)nt + nreg + nc + 16;
+    size_t need = (size_t)4 * N + 2 * (size_t)nt + nreg + nc + S.n_scenes + 16;
     S.c_in.ensure(need * sizeof(double));
     double* p = S.c_in.as<double>();
     auto slot = [&](double* user, size_t n) -> double* {
@@ -1686,6 +1884,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
       p += n;
       return r;
     };
+    go.dL_dbend = slot(grads ? grads->dL_dbend : nullptr, S.n_scenes);
     go.dL_dq_prev = slot(grads ? grads->dL_dq_prev : nullptr, N);
     go.dL_dv_prev = slot(grads ? grads->dL_dv_prev : nullptr, N);
     go.dL_dfext = slot(grads ? grads->dL_dfext : nullptr, N);
@@ -1696,10 +1895,22 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     go.dL_dmu_contact = slot(grads ? grads->dL_dmu_contact : nullptr, nc);
   }
   if (go.dL_dmu) NCPADJ_CUDA_TRY(cudaMemsetAsync(go.dL_dmu, 0, sizeof(double) * nreg, st));
-  ContractArgs ka{nv, nt, nc, S.h, E.x, S.massd.as<double>(), in.dL_dv, S.tets.as<int32_t>(), S.gvec.as<double>(),
-                  S.tetdata.as<double>(), S.lame_d.as<double>(), in.cvertex, in.frame, S.cdata.as<double>(), in.region,
-                  go.dL_dq_prev, go.dL_dv_prev, go.dL_dfext, go.dL_dE, go.dL_dnu, go.dL_dmu, go.dL_dmu_contact};
+  ContractArgs ka{nv, S.nvpe == 4 ? nt : 0, nc, S.h, E.x, S.massd.as<double>(), in.dL_dv, S.tets.as<int32_t>(),
+                  S.gvec.as<double>(), S.tetdata.as<double>(), S.lame_d.as<double>(), in.cvertex, in.frame,
+                  S.cdata.as<double>(), in.region, go.dL_dq_prev, go.dL_dv_prev, go.dL_dfext, go.dL_dE, go.dL_dnu,
+                  go.dL_dmu, go.dL_dmu_contact};
   launch_contractions(ka, st);
+  if (S.nvpe == 3) {
+    ka.nt = nt;
+    launch_contract_tri(ka, st);
+  }
+  if (go.dL_dbend) {
+    if (S.n_bend)
+      launch_bend_grad(S.n_scenes, S.bend_eoff.as<int32_t>(), S.bend_idx.as<int32_t>(), S.bend_coef.as<double>(), in.q,
+                       E.x, S.h, go.dL_dbend, st);
+    else
+      NCPADJ_CUDA_TRY(cudaMemsetAsync(go.dL_dbend, 0, sizeof(double) * S.n_scenes, st));
+  }
   float* dact = nullptr;
   if (grads && grads->dL_dact) {
     if (host_mem) {
@@ -1735,6 +1946,7 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
     back(grads->dL_dnu, go.dL_dnu, nt);
     back(grads->dL_dmu, go.dL_dmu, nreg);
     back(grads->dL_dmu_contact, go.dL_dmu_contact, nc);
+    back(grads->dL_dbend, go.dL_dbend, S.n_scenes);
     if (dact) NCPADJ_CUDA_TRY(cudaMemcpyAsync(grads->dL_dact, dact, sizeof(float) * nt, cudaMemcpyDeviceToHost, st));
   }
   read_flags(S, st);
@@ -1893,9 +2105,9 @@ static ncpadj_status adjoint_batch(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, int ns
              w_df = want(offsetof(ncpadj_grads, dL_dfext)), w_z = want(offsetof(ncpadj_grads, z)),
              w_E = want(offsetof(ncpadj_grads, dL_dE)), w_nu = want(offsetof(ncpadj_grads, dL_dnu)),
              w_mu = want(offsetof(ncpadj_grads, dL_dmu)), w_muc = want(offsetof(ncpadj_grads, dL_dmu_contact)),
-             w_act = want(offsetof(ncpadj_grads, dL_dact));
+             w_act = want(offsetof(ncpadj_grads, dL_dact)), w_bend = want(offsetof(ncpadj_grads, dL_dbend));
   // union staging: inputs, then outputs
-  const size_t nd = 8 * (size_t)N + 17 * (size_t)nc + 2 * (size_t)nt + nreg + 64;
+  const size_t nd = 8 * (size_t)N + 17 * (size_t)nc + 2 * (size_t)nt + nreg + ns + 64;
   S.bio.ensure(sizeof(double) * nd + sizeof(float) * (size_t)nt + 256);
   double* p = S.bio.as<double>();
   auto take = [&](size_t n) {
@@ -1906,7 +2118,7 @@ static ncpadj_status adjoint_batch(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, int ns
   double *uq = take(N), *uqp = take(N), *udq = take(N), *udv = take(N), *ulam = take(3 * (size_t)nc),
          *ufr = take(9 * (size_t)nc), *udn = take(nc), *udf = take(2 * (size_t)nc), *umu = take(nc);
   double *o_dq = take(N), *o_dv = take(N), *o_df = take(N), *o_z = take(N), *o_E = take(nt), *o_nu = take(nt),
-         *o_mu = take(nreg), *o_muc = take(nc);
+         *o_mu = take(nreg), *o_muc = take(nc), *o_bend = take(ns);
   float* o_act = reinterpret_cast<float*>(p + 8);
   S.bio_ids.ensure(sizeof(int32_t) * (4 * (size_t)nc + 64));
   int32_t* uvert = S.bio_ids.as<int32_t>();
@@ -1984,6 +2196,7 @@ static ncpadj_status adjoint_batch(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, int ns
   ug.dL_dmu = (w_mu && nc) ? o_mu : nullptr;
   ug.dL_dmu_contact = (w_muc && nc) ? o_muc : nullptr;
   ug.dL_dact = w_act ? o_act : nullptr;
+  ug.dL_dbend = w_bend ? o_bend : nullptr;
   ncpadj_options uo = opt;
   uo.memory = NCPADJ_MEM_DEVICE;
   uo.solver = NCPADJ_SOLVER_GMRES;
@@ -2019,6 +2232,7 @@ static ncpadj_status adjoint_batch(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, int ns
         if (n) d2h(gs.dL_dmu, o_mu + r0, 8 * nr);
         if (n) d2h(gs.dL_dmu_contact, o_muc + c0, 8 * n);
         d2h(gs.dL_dact, o_act + t0, 4 * nts);
+        d2h(gs.dL_dbend, o_bend + s, 8);
       } else {
         out.f64(o_dq + v0, gs.dL_dq_prev, nv3);
         out.f64(o_dv + v0, gs.dL_dv_prev, nv3);
@@ -2029,6 +2243,7 @@ static ncpadj_status adjoint_batch(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, int ns
         if (n) out.f64(o_mu + r0, gs.dL_dmu, nr);
         if (n) out.f64(o_muc + c0, gs.dL_dmu_contact, n);
         out.f32(o_act + t0, gs.dL_dact, nts);
+        out.f64(o_bend + s, gs.dL_dbend, 1);
       }
     }
     if (!host_mem) out.run(S, {}, nullptr, st);
@@ -2129,8 +2344,15 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   auto evaluate = [&](const double* qq, double* RR, double* slip, bool check_turn) -> double {
     NCPADJ_CUDA_TRY(cudaMemsetAsync(flags + FLAG_INFEASIBLE, 0, 2 * sizeof(int), st));
     launch_inertia(nv, S.massd.as<double>(), qq, qt, RR, st);
-    launch_tet_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
-                     S.lam.as<double>(), S.model_ptr(), qq, S.h, RR, flags, st);
+    if (S.nvpe == 3) {
+      launch_tri_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
+                       S.lam.as<double>(), S.model_ptr(), qq, S.h, RR, flags, st);
+      launch_bend_force(S.n_bend, S.bend_idx.as<int32_t>(), S.bend_coef.as<double>(), S.bend_kb.as<double>(), qq,
+                        S.h, RR, st);
+    } else {
+      launch_tet_force(S.nt, S.tets.as<int32_t>(), S.gvec.as<double>(), S.vol.as<double>(), S.mu.as<double>(),
+                       S.lam.as<double>(), S.model_ptr(), qq, S.h, RR, flags, st);
+    }
     if (E.in.nbind && E.in.btet)
       launch_binding_force_bary(E.in.nbind, E.in.btet, S.tets.as<int32_t>(), E.in.bbary, E.in.btarget,
                                 E.in.bcompliance, qq, S.h, RR, st);
@@ -2379,8 +2601,9 @@ ncpadj_status ncpadj_scene_create(ncpadj_ctx ctx, const ncpadj_scene_desc* desc,
     NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
     s = new ncpadj_scene_s();
     s->ctx = ctx;
-    build_scene(s->s, desc, 1);
-    keep_geometry(s->s, desc, 1);
+    const MeshSpec m = spec_of(*desc);
+    build_scene(s->s, &m, 1);
+    keep_geometry(s->s, &m, 1);
     *out = s;
     return NCPADJ_OK;
   } catch (const Error& e) {
@@ -2402,8 +2625,10 @@ ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const 
     NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
     s = new ncpadj_scene_s();
     s->ctx = ctx;
-    build_scene(s->s, descs, n_scenes);
-    keep_geometry(s->s, descs, n_scenes);
+    std::vector<MeshSpec> m(n_scenes);
+    for (int i = 0; i < n_scenes; ++i) m[i] = spec_of(descs[i]);
+    build_scene(s->s, m.data(), n_scenes);
+    keep_geometry(s->s, m.data(), n_scenes);
     *out = s;
     return NCPADJ_OK;
   } catch (const Error& e) {
@@ -2412,6 +2637,63 @@ ncpadj_status ncpadj_scene_create_batch(ncpadj_ctx ctx, int32_t n_scenes, const 
   } catch (const std::exception& e) {
     ncpadj_scene_destroy(s);
     return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_create_shells(ncpadj_ctx ctx, int32_t n_scenes, const ncpadj_shell_desc* descs,
+                                         ncpadj_scene* out) {
+  g_last_error.clear();
+  ncpadj_scene_s* s = nullptr;
+  try {
+    NCPADJ_REQUIRE(ctx && descs && out && n_scenes >= 1, "NULL argument or n_scenes < 1");
+    *out = nullptr;
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    s = new ncpadj_scene_s();
+    s->ctx = ctx;
+    std::vector<MeshSpec> m(n_scenes);
+    for (int i = 0; i < n_scenes; ++i) m[i] = spec_of(descs[i]);
+    build_scene(s->s, m.data(), n_scenes);
+    keep_geometry(s->s, m.data(), n_scenes);
+    *out = s;
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    ncpadj_scene_destroy(s);
+    return fail(e);
+  } catch (const std::exception& e) {
+    ncpadj_scene_destroy(s);
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_set_bending(ncpadj_scene scene, const double* bend, void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene && bend, "NULL argument");
+    NCPADJ_REQUIRE(scene->ctx, "scene without a context");
+    Scene& S = scene->s;
+    NCPADJ_REQUIRE(S.nvpe == 3, "bending stiffness belongs to shell scenes (ncpadj_scene_create_shells)");
+    for (int i = 0; i < S.n_scenes; ++i)
+      NCPADJ_REQUIRE(bend[i] >= 0 && std::isfinite(bend[i]), "mesh " + std::to_string(i) + ": need bend >= 0");
+    NCPADJ_CUDA_TRY(cudaSetDevice(scene->ctx->c.device));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    refactor_scene(S, S.mat_E.data(), S.mat_nu.data(), bend);
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_scene_get_bending(ncpadj_scene scene, double* bend) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene && bend, "NULL argument");
+    const Scene& S = scene->s;
+    for (int i = 0; i < S.n_scenes; ++i) bend[i] = i < (int)S.mat_bend.size() ? S.mat_bend[i] : 0.0;
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
   }
 }
 
@@ -2427,7 +2709,7 @@ ncpadj_status ncpadj_scene_refactor(ncpadj_scene scene, const double* E, const d
                      "tet " + std::to_string(t) + ": need E > 0 and -1 < nu < 0.5");
     // work already queued on the stream may still read the arrays that are rebuilt
     NCPADJ_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
-    refactor_scene(S, E, nu);
+    refactor_scene(S, E, nu, S.mat_bend.data());
     return NCPADJ_OK;
   } catch (const Error& e) {
     return fail(e);
@@ -2474,6 +2756,7 @@ ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre) {
   try {
     NCPADJ_REQUIRE(scene && fibre, "NULL argument");
     Scene& S = scene->s;
+    NCPADJ_REQUIRE(S.nvpe == 4, "actuation fibres belong to tet scenes");
     for (int t = 0; t < S.nt; ++t) {
       const double* d = fibre + 3 * (size_t)t;
       const double n2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -2532,6 +2815,8 @@ ncpadj_status ncpadj_scene_get_info(ncpadj_scene s, ncpadj_scene_info* out) {
   out->nnz_Linv = s->s.nnz_S;
   out->ms_factor = s->s.ms_factor;
   out->n_scenes = s->s.n_scenes;
+  out->element_verts = s->s.nvpe;
+  out->n_hinges = s->s.n_bend;
   return NCPADJ_OK;
 }
 

@@ -99,11 +99,21 @@ struct Scene {
   int64_t nnz_S = 0;
   int64_t nnz_L = 0;
   double ms_factor = 0;
+  // shells (nvpe = 3): the triangles take the tet arrays above with their own layout (tets [nt][3],
+  // gvec [nt][6], slot [nt][9], tetdata [nt][12], vol = area * thickness); bending hinges:
+  int nvpe = 4;                     // vertices per element
+  int n_bend = 0;                   // hinges (interior edges) over the whole scene
+  DevBuf bend_idx;                  // int32 [n_bend][4] vertices (edge, then the two opposite)
+  DevBuf bend_coef;                 // double [n_bend][5] cotangent stencil K_0..K_3, 3/(A_1+A_2)
+  DevBuf bend_kb;                   // double [n_bend] bending stiffness of the hinge's mesh
+  DevBuf bend_slot;                 // int32 [n_bend][16] block slots of the vertex pairs
+  DevBuf bend_eoff;                 // int32 [n_scenes + 1] hinge offsets of each mesh
   // host copies of the meshes (for a refactor with new materials) and the current material
   std::vector<std::vector<double>> geo_pos;
   std::vector<std::vector<int32_t>> geo_tets;
-  std::vector<double> geo_density;
+  std::vector<double> geo_density, geo_thickness;
   std::vector<double> mat_E, mat_nu;  // [nt]
+  std::vector<double> mat_bend;       // [n_scenes] (shells)
   std::vector<int64_t> St_ptr_h;  // host copy (Delassus pair scheduling)
 
   // per-call workspace

@@ -58,6 +58,24 @@ struct TetArgs {
 void launch_tet_assemble64(const TetArgs& a, cudaStream_t s);
 void launch_tet_assemble32(const TetArgs& a, cudaStream_t s);
 
+// ---- triangle (shell) elements and isometric bending (shell.cu) ---------------------------
+// TetArgs with the triangle layout: tets [nt][3], gvec [nt][6] (2-vectors g_0..g_2), slot [nt][9],
+// tetdata [nt][12] (P_mu, P_lam as 3 x 2 row-major), vol = area * thickness
+void launch_tri_assemble64(const TetArgs& a, cudaStream_t s);
+void launch_tri_assemble32(const TetArgs& a, cudaStream_t s);
+void launch_tri_force(int nt, const int32_t* tris, const double* gvec, const double* vol, const double* mu,
+                      const double* lam, const int8_t* model, const double* q, double h, double* R, int* flags,
+                      cudaStream_t s);
+// hinges: idx [ne][4] vertices, coef [ne][5] = (K_0..K_3, 3/(A_1+A_2)), kb [ne] stiffness of the
+// hinge's mesh, slot [ne][16] block slots of the vertex pairs
+void launch_bend_blocks(int ne, const int32_t* idx, const double* coef, const double* kb, const int32_t* slot,
+                        double h, double* bsr, float* bsr32, cudaStream_t s);
+void launch_bend_force(int ne, const int32_t* idx, const double* coef, const double* kb, const double* q, double h,
+                       double* R, cudaStream_t s);
+// out[s] = dL/dk_b of mesh s = -h^2 z^T Q_s q over its hinges [eoff[s], eoff[s+1])
+void launch_bend_grad(int n_scenes, const int32_t* eoff, const int32_t* idx, const double* coef, const double* q,
+                      const double* z, double h, double* out, cudaStream_t s);
+
 struct ContactArgs {
   int nc;
   const int32_t* vertex;
@@ -106,7 +124,8 @@ struct ContractArgs {
   double* dL_dmu;         // [n_regions] (zeroed by the caller)
   double* dL_dmu_contact; // [nc]
 };
-void launch_contractions(const ContractArgs& a, cudaStream_t s);
+void launch_contractions(const ContractArgs& a, cudaStream_t s);  // the tet part runs when nt > 0
+void launch_contract_tri(const ContractArgs& a, cudaStream_t s);  // dL/dE, dL/dnu of triangles
 // batch scenes: scene id of every contact; per-scene sums of squares of a DOF vector (sq zeroed by
 // the caller); x[i] *= scale[scene_of_vertex[i / 3]]
 void launch_contact_scene(int nc, const int32_t* cvertex, const int32_t* scene_of_vertex, int32_t* out, cudaStream_t s);

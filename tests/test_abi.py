@@ -64,7 +64,8 @@ def test_ctypes_structs_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    pairs = {"ncpadj_scene_desc": B._SceneDesc, "ncpadj_scene_info": B._SceneInfo, "ncpadj_contacts": B._Contacts,
+    pairs = {"ncpadj_scene_desc": B._SceneDesc, "ncpadj_shell_desc": B._ShellDesc,
+             "ncpadj_scene_info": B._SceneInfo, "ncpadj_contacts": B._Contacts,
              "ncpadj_bindings": B._Bindings, "ncpadj_state": B._State, "ncpadj_seed": B._Seed,
              "ncpadj_grads": B._Grads, "ncpadj_options": B._Options, "ncpadj_stats": B._Stats,
              "ncpadj_forward_input": B._ForwardInput, "ncpadj_forward_stats": B._ForwardStats}
