@@ -467,6 +467,91 @@ def beam_leg(pkg, torch, dev, steps, warmup, flush, with_models=True, cpu=False)
     return out
 
 
+# paper's backward time per step of the batched cloth (Sec. 5.5.3, Table tab:parallel_env_scaling; RTX 5090)
+PAPER_CLOTH_BWD_MS = {4: 11.9, 8: 29.9, 16: 33.3, 32: 34.3, 64: 61.0, 128: 94.1, 256: 158.6, 512: 294.3}
+
+
+def union_contacts(pkg, torch, T, cts, off):
+    """The per-mesh contact sets as one contact set of the union scene (grouped by mesh)."""
+    if sum(c.n for c in cts) == 0:
+        return None
+    return pkg.Contacts(T(np.concatenate([c.vertex + off[i] for i, c in enumerate(cts)]), torch.int32),
+                        T(np.concatenate([c.frame for c in cts])), T(np.concatenate([c.d_n for c in cts])),
+                        T(np.concatenate([c.mu for c in cts])), None,
+                        T(np.concatenate([np.zeros(c.n, np.int32) for c in cts]), torch.int32), 1)
+
+
+def cloth_leg(pkg, torch, dev, steps, warmup, flush, sizes=(64, 512), n_fwd=12):
+    """The paper's batched cloth (Sec. 5.5.3): N cloth patches (1,024 vertices, 1,922 triangles each)
+    with ARAP elasticity and isometric bending draping onto a frictionless sphere, E log-uniform in
+    [1e4, 1e6] per cloth.  The GPU forward runs n_fwd steps (contacts re-detected on the host every
+    step); then one batched adjoint (one GMRES per cloth, ncpadj_adjoint_batch) of the last step is
+    timed in FP64 and mixed precision, beside the paper's backward time per step at the same N."""
+    import synth
+    out = {}
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    stream = torch.cuda.Stream(dev)
+    for N in sizes:
+        rng = np.random.default_rng(1000 + N)
+        Es = np.exp(rng.uniform(np.log(1e4), np.log(1e6), N))
+        pbs = [synth.cloth_drape(seed=i, E=float(Es[i])) for i in range(N)]
+        sc0 = pbs[0].scene
+        ctx = pkg.Context(dev.index or 0)
+        t0 = time.perf_counter()
+        scene = pkg.Scene.shells(ctx, [(p.scene.X, p.scene.tets, p.scene.E, p.scene.nu, p.scene.density,
+                                        p.scene.thickness, p.scene.bend) for p in pbs], sc0.h)
+        scene.set_model("arap")
+        build_s = time.perf_counter() - t0
+        off = scene.vertex_offsets
+        q_prev = T(np.concatenate([p.q0 for p in pbs]))
+        v_prev = T(np.concatenate([p.v0 for p in pbs]))
+        fwd, t0 = [], time.perf_counter()
+        for k in range(n_fwd):
+            qp = q_prev.cpu().numpy()
+            cts = [p.scene.contacts(qp[off[i]:off[i + 1]]) for i, p in enumerate(pbs)]
+            try:
+                q, lam, fs = pkg.forward_step(scene, union_contacts(pkg, torch, T, cts, off), q_prev, v_prev, None,
+                                              tuple(sc0.gravity), eps=sc0.eps, max_newton=200, cap_precision="mixed")
+            except pkg.NcpadjError as e:  # the step goes on from the last iterate; its residual is reported
+                if not hasattr(e, "state"):
+                    raise
+                (q, lam), fs = e.state, e.stats
+            fwd.append(fs)
+            if k < n_fwd - 1:
+                v_prev, q_prev = (q - q_prev) / sc0.h, q
+        forward_s = time.perf_counter() - t0
+        ncs = [c.n for c in cts]
+        c0 = np.concatenate([[0], np.cumsum(ncs)])
+        contacts = [None if c.n == 0 else pkg.Contacts(T(c.vertex, torch.int32), T(c.frame), T(c.d_n), T(c.mu), None,
+                                                         T(np.zeros(c.n, np.int32), torch.int32), 1) for c in cts]
+        qs = [q[off[i]:off[i + 1]].contiguous() for i in range(N)]
+        qps = [q_prev[off[i]:off[i + 1]].contiguous() for i in range(N)]
+        lams = [lam[c0[i]:c0[i + 1]].contiguous() for i in range(N)]
+        dq = [(2 * (qs[i] - T(p.q_target))).contiguous() for i, p in enumerate(pbs)]
+        res, grads = {}, {}
+        for name, prec in (("fp64", "fp64"), ("mixed", "mixed")):
+            call = pkg.BatchCall(scene, contacts, qs, qps, lams, dq, None, eps=sc0.eps, rtol=1e-8, precision=prec,
+                                 cap_precision=prec, want=("dL_dE", "dL_dq_prev", "z"))
+            tot, sts = time_calls(torch, dev, call, stream, flush, steps, warmup)
+            grads[name] = [{k: v.clone() for k, v in o.items()} for o in call.outputs]
+            res[name] = {"ms_per_call": tot / steps, "gradients_per_s": N * steps / (tot / 1e3),
+                         "krylov_iterations": krylov_summary(sts),
+                         "kernel_launches": int(statistics.median(x[0]["kernel_launches"] for x in sts))}
+        err = 0.0
+        for a, b in zip(grads["mixed"], grads["fp64"]):
+            for k in b:
+                err = max(err, float((torch.linalg.norm(a[k] - b[k]) / torch.linalg.norm(b[k]).clamp_min(1e-300))))
+        pm = PAPER_CLOTH_BWD_MS.get(N)
+        out[str(N)] = {"cloths": N, "verts": off[-1], "dof": 3 * off[-1], "triangles": scene.n_tets,
+                       "contacts": int(sum(ncs)), "scene_build_s": build_s, "forward_steps": n_fwd,
+                       "forward_s": forward_s, "forward_last": fwd[-1], **res, "max_rel_err_mixed_vs_fp64": err,
+                       "paper_bwd_ms_per_step_rtx5090": pm,
+                       "paper_gradients_per_s_rtx5090": None if pm is None else N * 1e3 / pm}
+        del scene, call
+        torch.cuda.synchronize(dev)
+    return out
+
+
 def sphere(pkg, torch, dev, steps, warmup):
     """The large contact-heavy scene at full size: ball (r = 0.1 m, ~32k vertices, ~211k tets) pressed
     between the ground and a kinematic plate, ~2,300 frictional contacts in 32 friction regions.
@@ -639,6 +724,8 @@ def main():
     ap.add_argument("--no-beam", action="store_true", help="skip the single-scene beam measurement")
     ap.add_argument("--no-models", action="store_true",
                     help="skip the co-rotational / ARAP / bindings timings on the beam")
+    ap.add_argument("--no-cloth", action="store_true", help="skip the batched cloth measurement (shells)")
+    ap.add_argument("--cloth-only", action="store_true", help="run only the batched cloth measurement")
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
     ap.add_argument("--quadruped", action="store_true", help="add the actuated quadruped measurement")
     ap.add_argument("--quad-scale", type=float, default=1.0, help="linear scale of the quadruped (1 = full size)")
@@ -679,6 +766,11 @@ def main():
                                           for x in blocks], blocks[0].scene.h)
         print(json.dumps({"roofline_only": args.roofline_only, "blocks": args.blocks, "info": scene.info(),
                           "roofline": apply_roofline(pkg, torch, dev, scene, 10, precision="mixed")}))
+        return
+
+    if args.cloth_only:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"cloth": cloth_leg(pkg, torch, dev, max(3, args.steps // 4), 1, flush)}))
         return
 
     # ---- the batched workload: 64 blocks per rank (the rank seeds its batch) ----
@@ -765,6 +857,11 @@ def main():
                                         with_models=not args.no_models)
             except Exception as e:  # noqa: BLE001
                 side["beam"] = {"error": str(e)[:300]}
+        if not args.no_cloth:
+            try:
+                side["cloth"] = cloth_leg(pkg, torch, dev, max(3, args.steps // 4), 1, flush)
+            except Exception as e:  # noqa: BLE001
+                side["cloth"] = {"error": str(e)[:300]}
         if args.sphere:
             try:
                 side["sphere"] = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)

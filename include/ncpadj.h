@@ -65,7 +65,7 @@ typedef enum {
   NCPADJ_ERR_CONTACT_DOMAIN = 10   /* a frictional contact has zero slip (no direction) */
 } ncpadj_status;
 
-enum { NCPADJ_FP64 = 0, NCPADJ_MIXED = 1 };
+enum { NCPADJ_FP64 = 0, NCPADJ_MIXED = 1, NCPADJ_TF32X3 = 2 };
 enum {
   NCPADJ_PRECOND_NONE = 0,
   NCPADJ_PRECOND_JACOBI = 1,   /* diag(script_A)^{-1} (Sec. 4.4, Jacobi preconditioner) */
@@ -305,9 +305,11 @@ typedef struct {
  *              right-preconditioned BiCGSTAB, no restart, at least 7 vectors of workspace; an
  *              inner iterative capacitance solve makes the preconditioner vary, and then GMRES
  *              (flexible) is used whatever is asked); memory NCPADJ_MEM_*.
- *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default) or
- *              NCPADJ_MIXED (inverted and applied in FP32; it only preconditions, so the result
- *              keeps the solve's precision and tolerance).
+ *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default),
+ *              NCPADJ_MIXED (inverted by Gauss-Jordan and applied in FP32; it only preconditions,
+ *              so the result keeps the solve's precision and tolerance) or NCPADJ_TF32X3 (FP32,
+ *              inverted by the Schur-complement recursion with tensor-core products of
+ *              ncpadj_dense_inverse; no pivoting across its 64-row leaves).
  *   cap_block  most contacts per directly inverted capacitance block (0 = default = 2730 with an
  *              FP32 capacitance, 1365 with FP64; at most 5461 resp. 1365).  A scene with
  *              more contacts has its capacitance solved iteratively (Sec. 4.4): an inner
@@ -429,7 +431,11 @@ ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model);
  * partial pivoting that inverts the contact capacitance I + h^2 K D of the Woodbury
  * preconditioner (Sec. 4.4); exposed so that the inversion can be used and checked on its own.
  * C, Cinv: device arrays [n*n] (not aliased; C is not modified).  precision NCPADJ_FP64 computes
- * in FP64; NCPADJ_MIXED rounds C to FP32 and computes in FP32 (the result is returned as double).
+ * in FP64; NCPADJ_MIXED rounds C to FP32 and computes in FP32 (the result is returned as double);
+ * NCPADJ_TF32X3 rounds C to FP32 and inverts it by Schur-complement recursion whose products run
+ * on the tensor cores (ncpadj_dense_gemm with split = 1), with 64-row leaves inverted by pivoted
+ * Gauss-Jordan elimination (pivoting only inside a leaf: every leading block the recursion meets
+ * must be invertible).
  * 1 <= n <= 16384 (FP64: n <= 4096, else UNSUPPORTED).  Synchronises the stream (it reads the
  * pivot status).  Uses workspace owned by
  * the context (allocated on first use, grown as needed).
@@ -437,6 +443,19 @@ ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model);
  * TIMEOUT, UNSUPPORTED (the cooperative launch was refused), OOM, CUDA. */
 ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, double* Cinv, int32_t precision,
                                    void* stream);
+
+/* C = alpha A B + beta C on the fifth-generation tensor cores (tcgen05.mma, kind::tf32, FP32
+ * accumulation in tensor memory): the GEMM of the capacitance inverse's Schur-complement recursion
+ * (Sec. 4.4, Woodbury preconditioner), exposed so that it can be used and checked on its own.
+ * A [M][K], B [K][N], C [M][N]: row-major FP32 DEVICE arrays with leading dimensions lda >= K,
+ * ldb >= N, ldc >= N (elements); C must not overlap A or B.  split = 1 splits every operand into a
+ * TF32 head and tail and adds the three leading products (about FP32 accuracy: relative error of a
+ * product ~1e-6 of sum |a_ik b_kj|); split = 0 rounds the operands to TF32 (~1e-3).  beta = 0 does
+ * not read C.  Synchronises the stream (it reads the kernel's status).
+ * Errors: INVALID_ARG, TIMEOUT (a wait of the kernel gave up), OOM, CUDA. */
+ncpadj_status ncpadj_dense_gemm(ncpadj_ctx ctx, int32_t M, int32_t N, int32_t K, float alpha, const float* A,
+                                int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                                int32_t split, void* stream);
 
 /* Variant of ncpadj_elastic_solve that allocates nothing (the paper has no counterpart).
  * For callers that cannot have device memory allocated while they run -- programs whose device

@@ -19,7 +19,7 @@ STATUS = ["OK", "INVALID_ARG", "CUDA", "OOM", "INVERTED_ELEMENT", "NOT_CONVERGED
           "NOT_FACTORED", "UNSUPPORTED", "CONTACT_DOMAIN"]
 PRECOND = {"none": 0, "jacobi": 1, "elastic": 2, "woodbury": 3}
 SOLVER = {"auto": 0, "cg": 1, "gmres": 2, "bicgstab": 3, "semi_implicit": 4}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "tf32x3": 2}
 MEMORY = {"device": 0, "host": 1}
 MODEL = {"neo_hookean": 0, "corotational": 1, "arap": 2}
 
@@ -119,6 +119,7 @@ EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpad
            "ncpadj_scene_set_bending", "ncpadj_scene_get_bending",
            "ncpadj_options_default", "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step",
            "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc", "ncpadj_elastic_solve_mixed", "ncpadj_dense_inverse",
+           "ncpadj_dense_gemm",
            "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
 
 
@@ -163,6 +164,8 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_scene_set_fibres.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_set_model.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_dense_inverse.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    lib.ncpadj_dense_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_int64,
+                                      C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]
     if path is None:
         _LIB = lib
     return lib
@@ -592,6 +595,30 @@ def elastic_solve_noalloc(scene: Scene, x: torch.Tensor, y: torch.Tensor, stream
     _check(lib, lib.ncpadj_elastic_solve_noalloc(scene.ctx.handle, scene.handle, _ptr(x), _ptr(y),
                                                  C.c_void_p(stream)))
     return y
+
+
+def dense_gemm(ctx: Context, A: torch.Tensor, B: torch.Tensor, Cout: Optional[torch.Tensor] = None,
+               alpha: float = 1.0, beta: float = 0.0, split: bool = True, stream=None) -> torch.Tensor:
+    """C = alpha A B + beta C on the tensor cores (ncpadj_dense_gemm): FP32 CUDA matrices with unit
+    column stride (row strides are the leading dimensions); split=True is 3xTF32 (about FP32
+    accuracy), False plain TF32."""
+    lib = ctx.lib
+    for name, t in (("A", A), ("B", B)) + ((("C", Cout),) if Cout is not None else ()):
+        if t.dim() != 2 or t.dtype != torch.float32 or not t.is_cuda or t.stride(1) != 1:
+            raise ValueError(f"{name}: expected a 2-D float32 CUDA matrix with unit column stride")
+    M, K = A.shape
+    if B.shape[0] != K:
+        raise ValueError(f"inner dimensions differ: {K} and {B.shape[0]}")
+    N = B.shape[1]
+    if Cout is None:
+        Cout = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    elif tuple(Cout.shape) != (M, N):
+        raise ValueError(f"C: expected shape {(M, N)}, got {tuple(Cout.shape)}")
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+    _check(lib, lib.ncpadj_dense_gemm(ctx.handle, M, N, K, float(alpha), _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                      float(beta), _ptr(Cout), Cout.stride(0), int(bool(split)), C.c_void_p(stream)))
+    return Cout
 
 
 def dense_inverse(ctx: Context, Cm: torch.Tensor, precision: str = "fp64", stream=None) -> torch.Tensor:

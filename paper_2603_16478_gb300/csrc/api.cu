@@ -610,6 +610,7 @@ struct Engine {
   // mixed precision: FP32 matrix values, FP32 A^{-1} products and capacitance apply
   bool mixed = false;
   bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
+  bool cap_tc = false;    // ... by the Schur-complement recursion on the tensor cores (else Gauss-Jordan)
   int cap_block = 0;      // most contacts per capacitance block (0: the largest the direct inverse takes)
   float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr;
   float2* zsplit = nullptr;  // double-float pairs of the Arnoldi matvec's input (mixed)
@@ -950,6 +951,11 @@ struct Engine {
       select_capacitance();
       plan_blocks();
       alloc_capacitance();
+      if (cap_tc) {  // its own scratch, sized once for the largest block (capw's sync words must stay zero)
+        int nmax = 0;
+        for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
+        S.recw.ensure(sizeof(float) * rec_inverse_scratch(nmax));
+      }
       for (size_t k = 0; k < blk_c0.size(); ++k) {
         const int c0 = blk_c0[k], m_ = blk_nc[k], n_ = 3 * m_;
         double* Cb = Cm + blk_moff[k];
@@ -961,7 +967,11 @@ struct Engine {
         NCPADJ_CUDA_TRY(cudaGetLastError());
         if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
         bool ok;
-        if (cap_fp32) {
+        if (cap_tc) {
+          launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
+          launch_rec_inverse(n_, Cm32 + blk_moff[k], n_, S.recw.as<float>(), pb, flags, st);
+          ok = true;
+        } else if (cap_fp32) {
           launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
           ok = launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st);
         } else {
@@ -1714,7 +1724,9 @@ void validate_options(const ncpadj_options& opt) {
   NCPADJ_REQUIRE(opt.precond >= 0 && opt.precond <= 3 && opt.solver >= 0 && opt.solver <= 4, "bad precond/solver");
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
   NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
-  NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED, "bad cap_precision");
+  NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED ||
+                     opt.cap_precision == NCPADJ_TF32X3,
+                 "bad cap_precision");
   NCPADJ_REQUIRE(opt.cap_block >= 0, "bad cap_block");
 }
 
@@ -1809,7 +1821,8 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   }
   int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
   E.mixed = opt.precision == NCPADJ_MIXED;
-  E.cap_fp32 = opt.cap_precision == NCPADJ_MIXED;
+  E.cap_fp32 = opt.cap_precision != NCPADJ_FP64;
+  E.cap_tc = opt.cap_precision == NCPADJ_TF32X3;
   E.cap_block = opt.cap_block;
   E.cap_drop = opt.cap_drop;
   int* flags = E.flags;
@@ -2292,7 +2305,8 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   E.in.q_prev = fin->q_prev;
   int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
   // the Newton solves run in FP64; the capacitance (a preconditioner only) follows cap_precision
-  E.cap_fp32 = opt.cap_precision == NCPADJ_MIXED;
+  E.cap_fp32 = opt.cap_precision != NCPADJ_FP64;
+  E.cap_tc = opt.cap_precision == NCPADJ_TF32X3;
   E.cap_block = opt.cap_block;
   E.cap_drop = opt.cap_drop;
   int* flags = E.flags;
@@ -2877,10 +2891,32 @@ ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, d
   try {
     NCPADJ_REQUIRE(ctx && C && Cinv && C != Cinv, "NULL or aliased argument");
     NCPADJ_REQUIRE(n > 0 && n <= gj_cols_max_dim(), "n out of range");
-    NCPADJ_REQUIRE(precision == NCPADJ_FP64 || precision == NCPADJ_MIXED, "bad precision");
+    NCPADJ_REQUIRE(precision == NCPADJ_FP64 || precision == NCPADJ_MIXED || precision == NCPADJ_TF32X3,
+                   "bad precision");
     NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
     cudaStream_t st = (cudaStream_t)stream;
     Ctx& X = ctx->c;
+    if (precision == NCPADJ_TF32X3) {
+      const size_t ne = (size_t)n * n;
+      X.inv_mat.ensure(sizeof(float) * ne + sizeof(int32_t) * (size_t)n + sizeof(int) * FLAG_COUNT + 256);
+      // its own scratch: the Gauss-Jordan inverse keeps sync words at the start of inv_work that must stay zero
+      X.rec_work.ensure(sizeof(float) * rec_inverse_scratch(n));
+      float* B = X.inv_mat.as<float>();
+      int32_t* piv = reinterpret_cast<int32_t*>(B + ne);
+      int* flags = reinterpret_cast<int*>(piv + n);
+      NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * FLAG_COUNT, st));
+      launch_convert_f32((long)ne, C, B, st);
+      launch_rec_inverse(n, B, n, X.rec_work.as<float>(), piv, flags, st);
+      NCPADJ_CUDA_TRY(cudaGetLastError());
+      int fh[FLAG_COUNT];
+      NCPADJ_CUDA_TRY(cudaMemcpyAsync(fh, flags, sizeof(fh), cudaMemcpyDeviceToHost, st));
+      NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+      if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the tensor-core GEMM timed out"};
+      if (fh[FLAG_SINGULAR]) throw Error{NCPADJ_ERR_NONFINITE, "a leading block is singular"};
+      launch_unpermute_inverse(n, B, true, piv, Cinv, st);
+      NCPADJ_CUDA_TRY(cudaGetLastError());
+      return NCPADJ_OK;
+    }
     const bool fp32 = precision == NCPADJ_MIXED;
     const size_t ne = (size_t)n * n;
     const size_t mat_bytes = (fp32 ? sizeof(float) : sizeof(double)) * ne + sizeof(int32_t) * (size_t)n +
@@ -2915,6 +2951,35 @@ ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, d
     if (fh[FLAG_SINGULAR]) throw Error{NCPADJ_ERR_NONFINITE, "the matrix is singular"};
     launch_unpermute_inverse(n, B, fp32, piv, Cinv, st);
     NCPADJ_CUDA_TRY(cudaGetLastError());
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
+ncpadj_status ncpadj_dense_gemm(ncpadj_ctx ctx, int32_t M, int32_t N, int32_t K, float alpha, const float* A,
+                                int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                                int32_t split, void* stream) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(ctx && A && B && C, "NULL argument");
+    NCPADJ_REQUIRE(M >= 1 && N >= 1 && K >= 1, "M, N and K must be positive");
+    NCPADJ_REQUIRE(lda >= K && ldb >= N && ldc >= N, "a leading dimension is below its row length");
+    NCPADJ_REQUIRE(split == 0 || split == 1, "split must be 0 or 1");
+    NCPADJ_CUDA_TRY(cudaSetDevice(ctx->c.device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx& X = ctx->c;
+    X.gemm_flags.ensure(sizeof(int) * FLAG_COUNT);
+    int* flags = X.gemm_flags.as<int>();
+    NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * FLAG_COUNT, st));
+    launch_tc_gemm(GemmArgs{M, N, K, alpha, beta, A, (long)lda, B, (long)ldb, C, (long)ldc, split, flags}, st);
+    NCPADJ_CUDA_TRY(cudaGetLastError());
+    int fh[FLAG_COUNT];
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(fh, flags, sizeof(fh), cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the tensor-core GEMM timed out"};
     return NCPADJ_OK;
   } catch (const Error& e) {
     return fail(e);

@@ -445,12 +445,17 @@ int gj_cols_max_dim() { return kMaxDim; }
 int gj_cols_max_dim64() { return 8 * kColsThreads; }
 size_t gj_cols_reserved_bytes() { return kSyncBytes; }
 
+// The sync words are cleared before every launch as well: a launch leaves them zero, but a scratch that
+// something else wrote (or a fresh allocation) would otherwise let blocks read panels that are not
+// published yet, with their stale pivot rows as indices.
 bool launch_gj_cols32(int n, float* C, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {
   g_launches += 1;
+  if (cudaMemsetAsync(scratch, 0, kSyncBytes, s) != cudaSuccess) return false;
   return cols_invert<float, kBP32, kBP32 / 2>(n, C, scratch, piv, flags, sm_count, s);
 }
 bool launch_gj_cols64(int n, double* C, void* scratch, int32_t* piv, int* flags, int sm_count, cudaStream_t s) {
   g_launches += 1;
+  if (cudaMemsetAsync(scratch, 0, kSyncBytes, s) != cudaSuccess) return false;
   return cols_invert<double, kBP64, kBP64 / 2>(n, C, scratch, piv, flags, sm_count, s);
 }
 

@@ -122,7 +122,8 @@ struct Scene {
   DevBuf cdata;                   // double [nc][16]  per-contact K (9), kmu (3), M_a pieces
   DevBuf c_in;                    // staging of contact inputs for host-memory calls
   DevBuf vecs;                    // Krylov vectors
-  DevBuf cap, capw;               // capacitance matrix / inverse and scratch
+  DevBuf cap, capw;               // capacitance matrix / inverse and the Gauss-Jordan scratch (sync words zero)
+  DevBuf recw;                    // scratch of the tensor-core capacitance inverse (separate from capw)
   DevBuf capsel;                  // the capacitance set: scores, kept indices, vertices, frames, K
   DevBuf red;                     // reduction scratch
   DevBuf flags;                   // int32 status flags
@@ -176,6 +177,8 @@ struct Ctx {
   int sm_count = 0;
   int coop_ok = 0;
   DevBuf inv_mat, inv_work;  // workspace of ncpadj_dense_inverse
+  DevBuf gemm_flags;         // status flags of ncpadj_dense_gemm
+  DevBuf rec_work;           // scratch of ncpadj_dense_inverse's Schur-complement recursion
 };
 
 // looks up (and so loads) the static scratch of ncpadj_elastic_solve_noalloc on `device`, which

@@ -58,6 +58,31 @@ struct TetArgs {
 void launch_tet_assemble64(const TetArgs& a, cudaStream_t s);
 void launch_tet_assemble32(const TetArgs& a, cudaStream_t s);
 
+// ---- dense FP32 GEMM on the tensor cores (tc.cu) -------------------------------------------
+// C = alpha A B + beta C, row-major with leading dimensions (elements); K >= 1.  split: 3xTF32
+// (about FP32 accuracy) instead of plain TF32.  A wait that gives up raises FLAG_TIMEOUT in flags.
+struct GemmArgs {
+  int M, N, K;
+  float alpha, beta;
+  const float* A;
+  long lda;
+  const float* B;
+  long ldb;
+  float* C;
+  long ldc;
+  int split;
+  int* flags;
+};
+void launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
+size_t tc_gemm_smem(int split);
+
+// M (n x n FP32, row stride ld) <- M^{-1} by Schur-complement recursion with tensor-core GEMMs and
+// pivoted Gauss-Jordan leaves (capinv.cu); scratch: rec_inverse_scratch(n) floats; piv (or null)
+// receives the identity permutation, so the Gauss-Jordan apply kernels take the result as it is.
+// A zero leaf pivot raises FLAG_SINGULAR, a GEMM wait that gives up FLAG_TIMEOUT.
+size_t rec_inverse_scratch(int n);
+void launch_rec_inverse(int n, float* M, long ld, float* scratch, int32_t* piv, int* flags, cudaStream_t s);
+
 // ---- triangle (shell) elements and isometric bending (shell.cu) ---------------------------
 // TetArgs with the triangle layout: tets [nt][3], gvec [nt][6] (2-vectors g_0..g_2), slot [nt][9],
 // tetdata [nt][12] (P_mu, P_lam as 3 x 2 row-major), vol = area * thickness

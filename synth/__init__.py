@@ -2,7 +2,7 @@
 
 This module builds the inputs that both the CUDA path and the FP64 oracle consume:
 tetrahedral meshes of hex lattices (5-tet split with alternating parity), material
-draws, initial velocities, targets, and vertex-plane contact sets with their frames.
+draws, initial velocities, targets, and vertex-plane and vertex-sphere contact sets with their frames.
 It holds geometry and random draws only -- none of the adjoint method's arithmetic --
 so that the oracle and the GPU library can share inputs without sharing any code.
 
@@ -154,22 +154,19 @@ class Sphere:
         d = x_prev[verts] - c
         dist = np.linalg.norm(d, axis=1)
         sel = verts[dist - self.radius < margin]
-        frames, dn = [], []
-        for v in sel:
-            n = (x_prev[v] - c) / np.linalg.norm(x_prev[v] - c)
-            a = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
-            t1 = a - n * (a @ n)
-            t1 /= np.linalg.norm(t1)
-            frames.append(np.stack([n, t1, np.cross(n, t1)]))
-            dn.append(n @ c + self.radius)
-        return sel, np.asarray(frames).reshape(-1, 3, 3), np.asarray(dn, float), np.full(len(sel), self.mu), \
-            np.full(len(sel), region)
+        n = (x_prev[sel] - c) / np.linalg.norm(x_prev[sel] - c, axis=1)[:, None]
+        a = np.where((np.abs(n[:, 0]) < 0.9)[:, None], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0])
+        t1 = a - n * np.sum(a * n, axis=1)[:, None]
+        t1 /= np.linalg.norm(t1, axis=1)[:, None]
+        frames = np.stack([n, t1, np.cross(n, t1)], axis=1).reshape(-1, 3, 3)
+        return sel, frames, n @ c + self.radius, np.full(len(sel), self.mu), np.full(len(sel), region)
 
 
 def detect_contacts(x_prev: np.ndarray, planes, margin: float, candidates=None, spheres=()) -> Contacts:
-    """Vertices whose gap to a plane at the previous positions is below ``margin``.
+    """Vertices whose gap to a plane or a sphere at the previous positions is below ``margin``.
 
-    ``candidates`` restricts the search to a vertex subset (e.g. a bottom face).
+    ``candidates`` restricts the search to a vertex subset (e.g. a bottom face).  Each sphere is one
+    more friction region, after the planes'.
     Friction regions: one region per plane, or the plane's grid of regions (listed in order,
     contacts grouped by region and ordered by position inside it).
     """

@@ -111,3 +111,43 @@ def test_alternating_sizes_and_precisions_share_one_workspace(ctx):
         rng = np.random.default_rng(n)
         M = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
         _check(ctx, M, prec, (1e-12 if prec == "fp64" else 1e-5) * np.linalg.cond(M) * np.sqrt(n))
+
+
+# ---- the Schur-complement recursion on the tensor cores (NCPADJ_TF32X3) ----------------------
+
+@pytest.mark.parametrize("n", [1, 5, 63, 64, 65, 128, 200, 1353, 2088, 3001])
+def test_recursive_tensor_core_inverse(ctx, n):
+    """FP32 storage, 3xTF32 products: the recursion's result is within FP32 rounding of the inverse
+    (well-conditioned matrices whose leading blocks are invertible)."""
+    rng = np.random.default_rng(n + 11)
+    M = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
+    cond = np.linalg.cond(M) if n <= 2048 else 6.0
+    _check(ctx, M, "tf32x3", 2e-6 * cond * np.sqrt(n))
+
+
+@pytest.mark.parametrize("n", [300, 1353])
+def test_recursive_inverse_of_capacitance_like_matrices(ctx, n):
+    """The capacitance structure I + K D (3 x 3 contact blocks of widely spread magnitude): as a
+    preconditioner the result must leave ||I - M B|| small, like the pivoted Gauss-Jordan's."""
+    from paper_2603_16478_gb300.binding import dense_inverse
+    M = _capacitance_like(n, n + 1)
+    Cm = torch.tensor(M, dtype=torch.float64, device="cuda")
+    res = {}
+    for prec in ("mixed", "tf32x3"):
+        B = dense_inverse(ctx, Cm, prec).cpu().numpy()
+        res[prec] = np.linalg.norm(np.eye(n) - M @ B) / np.sqrt(n)
+    assert res["tf32x3"] < max(1e-3, 20 * res["mixed"]), res
+
+
+def test_recursive_inverse_needs_invertible_leading_blocks(ctx):
+    """The recursion pivots only inside its 64-row leaves: a matrix whose leading leaf is singular
+    is reported (NONFINITE), not returned as garbage."""
+    from paper_2603_16478_gb300 import NcpadjError
+    from paper_2603_16478_gb300.binding import dense_inverse
+    n = 100
+    rng = np.random.default_rng(1)
+    M = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
+    M[:64, :64] = 0.0  # the leading 64 x 64 block is zero
+    M[:64, 64:] = rng.standard_normal((64, 36))
+    with pytest.raises(NcpadjError, match="NONFINITE"):
+        dense_inverse(ctx, torch.tensor(M, device="cuda"), "tf32x3")

@@ -36,7 +36,7 @@ def _errors(g, ref, nc):
     return out
 
 
-@pytest.mark.parametrize("cap", ["fp64", "mixed"])
+@pytest.mark.parametrize("cap", ["fp64", "mixed", "tf32x3"])
 @pytest.mark.parametrize("name,k", [("cube_drop", 0), ("cube_drop", 2), ("cube_drop", 5), ("two_tet", 1)])
 def test_mixed_against_oracle(pkg, ctx, name, k, cap):
     case = step_case(name, k)
@@ -45,7 +45,7 @@ def test_mixed_against_oracle(pkg, ctx, name, k, cap):
     assert max(errs.values()) <= 1e-3, errs
 
 
-@pytest.mark.parametrize("cap", ["fp64", "mixed"])
+@pytest.mark.parametrize("cap", ["fp64", "mixed", "tf32x3"])
 def test_mixed_against_fp64_on_the_beam(pkg, ctx, cap):
     """Full-size beam (20k tets, 451 contacts): GPU mixed vs GPU FP64 on a GPU-forward state."""
     import synth
@@ -68,3 +68,16 @@ def test_mixed_against_fp64_on_the_beam(pkg, ctx, cap):
     for k, _ in KEYS:
         e = rel(g32[k].cpu().numpy(), g64[k].cpu().numpy())
         assert e <= 1e-3, (k, e)
+
+
+def test_tensor_core_capacitance_keeps_fp64_results_and_iterations(pkg, ctx):
+    """The tensor-core capacitance inverse only preconditions: with FP64 matrices the gradients match
+    the oracle to 1e-8 at rtol 1e-12, in about as many iterations as the FP32 Gauss-Jordan inverse."""
+    from tests.test_gpu_parity import assert_parity
+    case = step_case("cube_drop", 5)
+    its = {}
+    for cap in ("mixed", "tf32x3"):
+        g, ref, stats = run_both(pkg, ctx, case, rtol=1e-12, cap_precision=cap)
+        assert_parity(g, ref, 1e-8, case[1].nc)
+        its[cap] = stats["iterations"]
+    assert its["tf32x3"] <= its["mixed"] + 2, its
