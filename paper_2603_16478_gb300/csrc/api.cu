@@ -611,6 +611,13 @@ struct Engine {
   bool mixed = false;
   bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
   bool cap_tc = false;    // ... by the Schur-complement recursion on the tensor cores (else Gauss-Jordan)
+  int cap_nmax = 0;       // largest capacitance block (rows); S.capmeta holds the block table
+
+  // x = C^{-1} y over every directly inverted capacitance block, in one launch
+  void cap_apply_all(const double* y, double* x, const int* act = nullptr) {
+    launch_cap_apply_all((int)blk_c0.size(), cap_nmax, S.capmeta.as<int64_t>(), (mixed || cap_fp32) ? Cm32 : nullptr,
+                         (mixed || cap_fp32) ? nullptr : Cm, piv, y, x, act, st);
+  }
   int cap_block = 0;      // most contacts per capacitance block (0: the largest the direct inverse takes)
   float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr;
   float2* zsplit = nullptr;  // double-float pairs of the Arnoldi matvec's input (mixed)
@@ -951,44 +958,75 @@ struct Engine {
       select_capacitance();
       plan_blocks();
       alloc_capacitance();
+      {  // block table of the one-launch capacitance apply: element offset, row offset, dimension, scene
+        const size_t nbk = blk_c0.size();
+        std::vector<int64_t> meta(5 * nbk);
+        cap_nmax = 0;
+        for (size_t k = 0; k < nbk; ++k) {
+          meta[k] = (int64_t)blk_moff[k];
+          meta[nbk + k] = 3 * (int64_t)blk_c0[k];
+          meta[2 * nbk + k] = 3 * (int64_t)blk_nc[k];
+          meta[3 * nbk + k] = k < blk_scene.size() ? blk_scene[k] : 0;
+          meta[4 * nbk + k] = (int64_t)blk_doff[k];
+          cap_nmax = std::max(cap_nmax, 3 * blk_nc[k]);
+        }
+        S.capmeta.ensure(sizeof(int64_t) * std::max<size_t>(meta.size(), 4));
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.capmeta.p, meta.data(), sizeof(int64_t) * meta.size(),
+                                        cudaMemcpyHostToDevice, st));
+        NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));  // meta is a local
+      }
       if (cap_tc) {  // its own scratch, sized once for the largest block (capw's sync words must stay zero)
         int nmax = 0;
         for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
         S.recw.ensure(sizeof(float) * rec_inverse_scratch(nmax));
       }
+      // the capacitance of every block (Delassus, then C = I + h^2 K'^T D), FP32 copies where it is
+      // inverted in FP32
+      launch_cap_form_all((int)blk_c0.size(), cap_nmax / 3, S.capmeta.as<int64_t>(), cvx, S.iperm.as<int32_t>(),
+                          S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(), S.St_val.as<double>(), Ds, cfr, ccd, h,
+                          transpose, Cm, cap_fp32 ? Cm32 : nullptr, st);
+      NCPADJ_CUDA_TRY(cudaGetLastError());
+      NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
+      // the inverses: every small block in one launch, one CTA each; the others one by one
+      const int smax = small_inverse_max(cap_fp32);
+      std::vector<int32_t> small;
+      for (size_t k = 0; k < blk_c0.size(); ++k)
+        if (3 * blk_nc[k] <= smax) small.push_back((int32_t)k);
+      if (!small.empty()) {
+        int nmax_small = 0;
+        for (int32_t k : small) nmax_small = std::max(nmax_small, 3 * blk_nc[k]);
+        S.capids.ensure(sizeof(int32_t) * small.size());
+        NCPADJ_CUDA_TRY(cudaMemcpyAsync(S.capids.p, small.data(), sizeof(int32_t) * small.size(),
+                                        cudaMemcpyHostToDevice, st));
+        launch_small_inverse((int)small.size(), S.capids.as<int32_t>(), (int)blk_c0.size(), S.capmeta.as<int64_t>(),
+                             nmax_small, cap_fp32 ? Cm32 : nullptr, cap_fp32 ? nullptr : Cm, piv, flags, st);
+        NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));  // small is a local
+      }
       for (size_t k = 0; k < blk_c0.size(); ++k) {
-        const int c0 = blk_c0[k], m_ = blk_nc[k], n_ = 3 * m_;
+        const int c0 = blk_c0[k], n_ = 3 * blk_nc[k];
+        if (n_ <= smax) continue;
         double* Cb = Cm + blk_moff[k];
-        double* Db = Ds + blk_doff[k];
         int32_t* pb = piv + 3 * c0;
-        launch_delassus(m_, cvx + c0, S.iperm.as<int32_t>(), S.St_ptr.as<int64_t>(), S.St_col.as<int32_t>(),
-                        S.St_val.as<double>(), Db, st);
-        launch_cap_form(m_, Db, cfr + 9 * (size_t)c0, ccd + 12 * (size_t)c0, h, transpose, Cb, st);
-        NCPADJ_CUDA_TRY(cudaGetLastError());
-        if (k == 0) NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[6], st));
         bool ok;
         if (cap_tc) {
-          launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
           launch_rec_inverse(n_, Cm32 + blk_moff[k], n_, S.recw.as<float>(), pb, flags, st);
           ok = true;
         } else if (cap_fp32) {
-          launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);
           ok = launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st);
         } else {
           ok = launch_gj_cols64(n_, Cb, S.capw.p, pb, flags, C.sm_count, st);
-          if (ok && mixed) launch_convert_f32((long)n_ * n_, Cb, Cm32 + blk_moff[k], st);  // FP32 apply
         }
         if (!ok) {
           cudaGetLastError();
           throw Error{NCPADJ_ERR_UNSUPPORTED,
                       "capacitance block of dimension " + std::to_string(n_) + " does not fit the direct inverse"};
         }
-        if (k + 1 == blk_c0.size()) {
-          NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[7], st));
-          cap_timed = true;
-        }
         NCPADJ_CUDA_TRY(cudaGetLastError());
       }
+      NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[7], st));
+      cap_timed = true;
+      if (!cap_fp32 && mixed) launch_convert_f32((long)cap_elems, Cm, Cm32, st);  // FP64 inverses, FP32 apply
+      NCPADJ_CUDA_TRY(cudaGetLastError());
     }
   }
 
@@ -1147,7 +1185,9 @@ struct Engine {
         if (mixed) launch_sinv_half1_32(sinv, xin, w32, st);
         else launch_sinv_half1(sinv, xin, t3, st);
         launch_path_gather(cnc, cvx, ip, sinv, t3, mixed ? w32 : nullptr, cfr, ccd, transpose, sc, st);
-        {
+        if (sup_c0.empty()) {
+          cap_apply_all(sc, tc);
+        } else {
           size_t ks = 0;  // super-blocks in contact order
           for (size_t k = 0; k < blk_c0.size();) {
             if (ks < sup_c0.size() && (int)k == sup_g0[ks]) {
@@ -1201,7 +1241,8 @@ struct Engine {
                                 (uintptr_t)S.cap.p, (uintptr_t)S.vec32.p, (uintptr_t)S.cdata.p, (uintptr_t)S.bsr32.p,
                                 (uintptr_t)S.bsr64.p, (uintptr_t)S.xpos.p, (uintptr_t)S.gstep.p,
                                 (uintptr_t)flexible_gmres(), (uintptr_t)S.fgmres.p,
-                                (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size(), (uintptr_t)S.xsplit.p};
+                                (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size(), (uintptr_t)S.xsplit.p,
+                                (uintptr_t)S.capmeta.p, (uintptr_t)cap_nmax};
     for (size_t b = 0; b < blk_c0.size(); ++b) {
       k.push_back((uintptr_t)blk_c0[b]);
       k.push_back((uintptr_t)blk_nc[b]);
@@ -1213,12 +1254,7 @@ struct Engine {
     // z = P^{-1} V_j into w (Woodbury, as in apply_precond)
     launch_sinv_half1_idx(sinv, V, N, jp, mixed ? nullptr : t3, mixed ? w32 : nullptr, st);
     launch_path_gather(cnc, cvx, ip, sinv, t3, mixed ? w32 : nullptr, cfr, ccd, transpose, sc, st);
-    for (size_t k = 0; k < blk_c0.size(); ++k) {
-      const size_t o = 3 * (size_t)blk_c0[k];
-      const int n_ = 3 * blk_nc[k];
-      if (mixed || cap_fp32) launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
-      else launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st);
-    }
+    cap_apply_all(sc, tc);
     launch_path_scatter(cnc, cvx, ip, sinv, cfr, tc, -h * h, t3, mixed ? w32 : nullptr, st);
     if (mixed) launch_sinv_half2_32(sinv, w32, w, st);
     else launch_sinv_half2(sinv, t3, w, st);
@@ -1300,14 +1336,7 @@ struct Engine {
         if (precond == NCPADJ_PRECOND_WOODBURY && cnc) {
           const int32_t* ip = S.iperm.as<int32_t>();
           launch_path_gather(cnc, cvx, ip, sinv, t3, mixed ? w32 : nullptr, cfr, ccd, transpose, sc, st, mk);
-          for (size_t k = 0; k < blk_c0.size(); ++k) {
-            const size_t o = 3 * (size_t)blk_c0[k];
-            const int n_ = 3 * blk_nc[k];
-            if (mixed || cap_fp32)
-              launch_gj_apply32(n_, Cm32 + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st, bb.act, blk_scene[k]);
-            else
-              launch_gj_apply(n_, Cm + blk_moff[k], piv + o, sc + o, ytmp + o, tc + o, st, bb.act, blk_scene[k]);
-          }
+          cap_apply_all(sc, tc, bb.act);
           launch_path_scatter(cnc, cvx, ip, sinv, cfr, tc, -h * h, t3, mixed ? w32 : nullptr, st, mk);
         }
         if (mixed) launch_sinv_half2_32(sinv, w32, w, st, mk);

@@ -124,6 +124,8 @@ struct Scene {
   DevBuf vecs;                    // Krylov vectors
   DevBuf cap, capw;               // capacitance matrix / inverse and the Gauss-Jordan scratch (sync words zero)
   DevBuf recw;                    // scratch of the tensor-core capacitance inverse (separate from capw)
+  DevBuf capmeta;                 // int64 [4][blocks]: the capacitance block table of the one-launch apply
+  DevBuf capids;                  // int32: the blocks small enough for the one-launch inverse
   DevBuf capsel;                  // the capacitance set: scores, kept indices, vertices, frames, K
   DevBuf red;                     // reduction scratch
   DevBuf flags;                   // int32 status flags

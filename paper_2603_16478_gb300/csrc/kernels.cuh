@@ -81,6 +81,24 @@ size_t tc_gemm_smem(int split);
 // receives the identity permutation, so the Gauss-Jordan apply kernels take the result as it is.
 // A zero leaf pivot raises FLAG_SINGULAR, a GEMM wait that gives up FLAG_TIMEOUT.
 size_t rec_inverse_scratch(int n);
+// In-place inverses (FP32 B32 or FP64 B64) of the nsmall blocks ids[] of the capacitance block table
+// meta (as launch_cap_apply_all's), one CTA each in one launch, with identity pivots written to piv;
+// every listed block must have at most small_inverse_max(fp32) rows and nmax its largest dimension.
+int small_inverse_max(bool fp32);
+// Delassus blocks D_k (rows [Ds + meta[4 nb + k]], m_k x m_k) and capacitances C_k (FP64 at
+// C + meta[k], and FP32 at C32 + meta[k] when C32 is given) of every block in two launches; the
+// table has a fifth row, the offsets of the D_k; mmax = the largest m_k
+void launch_cap_form_all(int nb, int mmax, const int64_t* meta, const int32_t* cvertex, const int32_t* iperm,
+                         const int64_t* St_ptr, const int32_t* St_col, const double* St_val, double* Ds,
+                         const double* frame, const double* cdata, double h, int transpose, double* C, float* C32,
+                         cudaStream_t s);
+void launch_small_inverse(int nsmall, const int32_t* ids, int nb, const int64_t* meta, int nmax, float* B32,
+                          double* B64, int32_t* piv, int* flags, cudaStream_t s);
+// x_k = B_k y_k (both pivot permutations, as launch_gj_apply*) for all nb capacitance blocks in one
+// launch; meta: int64 [4][nb] = element offset of B_k, offset 3 c0_k of its rows in y/x (and piv),
+// dimension n_k <= nmax, scene; B32 (FP32 inverses) or B64; act (nullable): skip blocks of idle scenes
+void launch_cap_apply_all(int nb, int nmax, const int64_t* meta, const float* B32, const double* B64,
+                          const int32_t* piv, const double* y, double* x, const int* act, cudaStream_t s);
 void launch_rec_inverse(int n, float* M, long ld, float* scratch, int32_t* piv, int* flags, cudaStream_t s);
 
 // ---- triangle (shell) elements and isometric bending (shell.cu) ---------------------------
