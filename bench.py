@@ -913,7 +913,7 @@ def main():
             "config": {"workload": WORKLOAD, "variant": head,
                        "precision": {"fp64": "plain FP64", "mixed": "FP32 matrix/preconditioner/capacitance factor, "
                                      "FP64 Krylov reductions", "mixed_tc": "FP32 matrix/preconditioner, capacitance "
-                                     "inverted in FP32 by the tensor-core Schur-complement recursion (3xTF32), FP64 "
+                                     "inverted in FP32 by the tensor-core blocked Gauss-Jordan (3xTF32), FP64 "
                                      "Krylov reductions", "mixed_cap64": "FP32 matrix/preconditioner, FP64 "
                                      "capacitance factor and Krylov reductions"}[head],
                        "variants": per_variant, "max_rel_err_vs_fp64": errs,

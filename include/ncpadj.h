@@ -308,8 +308,9 @@ typedef struct {
  *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default),
  *              NCPADJ_MIXED (inverted by Gauss-Jordan and applied in FP32; it only preconditions,
  *              so the result keeps the solve's precision and tolerance) or NCPADJ_TF32X3 (FP32,
- *              inverted by the Schur-complement recursion with tensor-core products of
- *              ncpadj_dense_inverse; no pivoting across its 64-row leaves).
+ *              inverted by the blocked Gauss-Jordan elimination of ncpadj_dense_inverse whose
+ *              rank-64 updates run on the tensor cores; pivoting only inside its 64 x 64
+ *              diagonal blocks).
  *   cap_block  most contacts per directly inverted capacitance block (0 = default = 2730 with an
  *              FP32 capacitance, 1365 with FP64; at most 5461 resp. 1365).  A scene with
  *              more contacts has its capacitance solved iteratively (Sec. 4.4): an inner
@@ -432,10 +433,11 @@ ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model);
  * preconditioner (Sec. 4.4); exposed so that the inversion can be used and checked on its own.
  * C, Cinv: device arrays [n*n] (not aliased; C is not modified).  precision NCPADJ_FP64 computes
  * in FP64; NCPADJ_MIXED rounds C to FP32 and computes in FP32 (the result is returned as double);
- * NCPADJ_TF32X3 rounds C to FP32 and inverts it by Schur-complement recursion whose products run
- * on the tensor cores (ncpadj_dense_gemm with split = 1), with 64-row leaves inverted by pivoted
- * Gauss-Jordan elimination (pivoting only inside a leaf: every leading block the recursion meets
- * must be invertible).
+ * NCPADJ_TF32X3 rounds C to FP32 and inverts it by blocked Gauss-Jordan elimination, 64 columns
+ * per step, in one persistent cooperative launch: each step's 64 x 64 diagonal block is inverted
+ * with pivoting among its own rows, and the rank-64 update of the whole matrix runs on the tensor
+ * cores (tcgen05.mma kind::tf32 with the 3xTF32 split, about FP32 accuracy).  There is no pivoting
+ * across blocks: every diagonal block met along the way must be invertible (else NONFINITE).
  * 1 <= n <= 16384 (FP64: n <= 4096, else UNSUPPORTED).  Synchronises the stream (it reads the
  * pivot status).  Uses workspace owned by
  * the context (allocated on first use, grown as needed).
@@ -445,8 +447,8 @@ ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, d
                                    void* stream);
 
 /* C = alpha A B + beta C on the fifth-generation tensor cores (tcgen05.mma, kind::tf32, FP32
- * accumulation in tensor memory): the GEMM of the capacitance inverse's Schur-complement recursion
- * (Sec. 4.4, Woodbury preconditioner), exposed so that it can be used and checked on its own.
+ * accumulation in tensor memory), the dense product the capacitance inverse of the Woodbury
+ * preconditioner (Sec. 4.4) is built from, exposed so that it can be used and checked on its own.
  * A [M][K], B [K][N], C [M][N]: row-major FP32 DEVICE arrays with leading dimensions lda >= K,
  * ldb >= N, ldc >= N (elements); C must not overlap A or B.  split = 1 splits every operand into a
  * TF32 head and tail and adds the three leading products (about FP32 accuracy: relative error of a

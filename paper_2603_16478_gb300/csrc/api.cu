@@ -610,7 +610,7 @@ struct Engine {
   // mixed precision: FP32 matrix values, FP32 A^{-1} products and capacitance apply
   bool mixed = false;
   bool cap_fp32 = false;  // factorise the capacitance in FP32 as well
-  bool cap_tc = false;    // ... by the Schur-complement recursion on the tensor cores (else Gauss-Jordan)
+  bool cap_tc = false;    // ... by the blocked Gauss-Jordan on the tensor cores (else pivoted Gauss-Jordan)
   int cap_nmax = 0;       // largest capacitance block (rows); S.capmeta holds the block table
 
   // x = C^{-1} y over every directly inverted capacitance block, in one launch
@@ -978,7 +978,7 @@ struct Engine {
       if (cap_tc) {  // its own scratch, sized once for the largest block (capw's sync words must stay zero)
         int nmax = 0;
         for (int v : blk_nc) nmax = std::max(nmax, 3 * v);
-        S.recw.ensure(sizeof(float) * rec_inverse_scratch(nmax));
+        S.recw.ensure(bgj_scratch_bytes(nmax));
       }
       // the capacitance of every block (Delassus, then C = I + h^2 K'^T D), FP32 copies where it is
       // inverted in FP32
@@ -1009,8 +1009,7 @@ struct Engine {
         int32_t* pb = piv + 3 * c0;
         bool ok;
         if (cap_tc) {
-          launch_rec_inverse(n_, Cm32 + blk_moff[k], n_, S.recw.as<float>(), pb, flags, st);
-          ok = true;
+          ok = launch_bgj_inverse(n_, Cm32 + blk_moff[k], n_, S.recw.p, pb, flags, C.sm_count, st);
         } else if (cap_fp32) {
           ok = launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, pb, flags, C.sm_count, st);
         } else {
@@ -2929,19 +2928,22 @@ ncpadj_status ncpadj_dense_inverse(ncpadj_ctx ctx, int32_t n, const double* C, d
       const size_t ne = (size_t)n * n;
       X.inv_mat.ensure(sizeof(float) * ne + sizeof(int32_t) * (size_t)n + sizeof(int) * FLAG_COUNT + 256);
       // its own scratch: the Gauss-Jordan inverse keeps sync words at the start of inv_work that must stay zero
-      X.rec_work.ensure(sizeof(float) * rec_inverse_scratch(n));
+      X.rec_work.ensure(bgj_scratch_bytes(n));
       float* B = X.inv_mat.as<float>();
       int32_t* piv = reinterpret_cast<int32_t*>(B + ne);
       int* flags = reinterpret_cast<int*>(piv + n);
       NCPADJ_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * FLAG_COUNT, st));
       launch_convert_f32((long)ne, C, B, st);
-      launch_rec_inverse(n, B, n, X.rec_work.as<float>(), piv, flags, st);
+      if (!launch_bgj_inverse(n, B, n, X.rec_work.p, piv, flags, X.sm_count, st)) {
+        cudaGetLastError();
+        throw Error{NCPADJ_ERR_UNSUPPORTED, "the cooperative grid of the tensor-core inverse does not fit"};
+      }
       NCPADJ_CUDA_TRY(cudaGetLastError());
       int fh[FLAG_COUNT];
       NCPADJ_CUDA_TRY(cudaMemcpyAsync(fh, flags, sizeof(fh), cudaMemcpyDeviceToHost, st));
       NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
-      if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the tensor-core GEMM timed out"};
-      if (fh[FLAG_SINGULAR]) throw Error{NCPADJ_ERR_NONFINITE, "a leading block is singular"};
+      if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the tensor-core inverse timed out"};
+      if (fh[FLAG_SINGULAR]) throw Error{NCPADJ_ERR_NONFINITE, "a diagonal block is singular"};
       launch_unpermute_inverse(n, B, true, piv, Cinv, st);
       NCPADJ_CUDA_TRY(cudaGetLastError());
       return NCPADJ_OK;
@@ -3008,7 +3010,7 @@ ncpadj_status ncpadj_dense_gemm(ncpadj_ctx ctx, int32_t M, int32_t N, int32_t K,
     int fh[FLAG_COUNT];
     NCPADJ_CUDA_TRY(cudaMemcpyAsync(fh, flags, sizeof(fh), cudaMemcpyDeviceToHost, st));
     NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
-    if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the tensor-core GEMM timed out"};
+    if (fh[FLAG_TIMEOUT]) throw Error{NCPADJ_ERR_TIMEOUT, "a wait of the tensor-core inverse timed out"};
     return NCPADJ_OK;
   } catch (const Error& e) {
     return fail(e);

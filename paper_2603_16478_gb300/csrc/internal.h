@@ -180,7 +180,7 @@ struct Ctx {
   int coop_ok = 0;
   DevBuf inv_mat, inv_work;  // workspace of ncpadj_dense_inverse
   DevBuf gemm_flags;         // status flags of ncpadj_dense_gemm
-  DevBuf rec_work;           // scratch of ncpadj_dense_inverse's Schur-complement recursion
+  DevBuf rec_work;           // scratch of ncpadj_dense_inverse's tensor-core blocked Gauss-Jordan
 };
 
 // looks up (and so loads) the static scratch of ncpadj_elastic_solve_noalloc on `device`, which

@@ -76,11 +76,15 @@ struct GemmArgs {
 void launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
 size_t tc_gemm_smem(int split);
 
-// M (n x n FP32, row stride ld) <- M^{-1} by Schur-complement recursion with tensor-core GEMMs and
-// pivoted Gauss-Jordan leaves (capinv.cu); scratch: rec_inverse_scratch(n) floats; piv (or null)
-// receives the identity permutation, so the Gauss-Jordan apply kernels take the result as it is.
-// A zero leaf pivot raises FLAG_SINGULAR, a GEMM wait that gives up FLAG_TIMEOUT.
-size_t rec_inverse_scratch(int n);
+// M (n x n FP32, row stride ld) <- M^{-1} by blocked Gauss-Jordan elimination in one persistent
+// cooperative launch, 64 columns per step, rank-64 updates on the tensor cores (bgj.cu); pivoting
+// inside the 64 x 64 diagonal blocks only.  scratch: bgj_scratch_bytes(n) bytes, 16-byte aligned;
+// piv (or null) receives the identity permutation, so the Gauss-Jordan apply kernels take the result
+// as it is.  A zero pivot raises FLAG_SINGULAR, a wait that gives up FLAG_TIMEOUT.  False if the
+// device cannot hold the cooperative grid (nothing launched).
+size_t bgj_scratch_bytes(int n);
+bool launch_bgj_inverse(int n, float* M, long ld, void* scratch, int32_t* piv, int* flags, int sm_count,
+                        cudaStream_t s);
 // In-place inverses (FP32 B32 or FP64 B64) of the nsmall blocks ids[] of the capacitance block table
 // meta (as launch_cap_apply_all's), one CTA each in one launch, with identity pivots written to piv;
 // every listed block must have at most small_inverse_max(fp32) rows and nmax its largest dimension.
@@ -99,7 +103,6 @@ void launch_small_inverse(int nsmall, const int32_t* ids, int nb, const int64_t*
 // dimension n_k <= nmax, scene; B32 (FP32 inverses) or B64; act (nullable): skip blocks of idle scenes
 void launch_cap_apply_all(int nb, int nmax, const int64_t* meta, const float* B32, const double* B64,
                           const int32_t* piv, const double* y, double* x, const int* act, cudaStream_t s);
-void launch_rec_inverse(int n, float* M, long ld, float* scratch, int32_t* piv, int* flags, cudaStream_t s);
 
 // ---- triangle (shell) elements and isometric bending (shell.cu) ---------------------------
 // TetArgs with the triangle layout: tets [nt][3], gvec [nt][6] (2-vectors g_0..g_2), slot [nt][9],

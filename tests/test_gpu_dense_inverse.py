@@ -113,20 +113,20 @@ def test_alternating_sizes_and_precisions_share_one_workspace(ctx):
         _check(ctx, M, prec, (1e-12 if prec == "fp64" else 1e-5) * np.linalg.cond(M) * np.sqrt(n))
 
 
-# ---- the Schur-complement recursion on the tensor cores (NCPADJ_TF32X3) ----------------------
+# ---- the blocked Gauss-Jordan on the tensor cores (NCPADJ_TF32X3) ---------------------------
 
-@pytest.mark.parametrize("n", [1, 5, 63, 64, 65, 128, 200, 1353, 2088, 3001])
-def test_recursive_tensor_core_inverse(ctx, n):
-    """FP32 storage, 3xTF32 products: the recursion's result is within FP32 rounding of the inverse
-    (well-conditioned matrices whose leading blocks are invertible)."""
+@pytest.mark.parametrize("n", [1, 5, 63, 64, 65, 127, 128, 129, 200, 1353, 2088, 3001])
+def test_tensor_core_blocked_inverse(ctx, n):
+    """FP32 storage, 3xTF32 rank-64 updates: the result is within FP32 rounding of the inverse
+    (well-conditioned matrices whose diagonal blocks stay invertible); ragged last blocks and tiles."""
     rng = np.random.default_rng(n + 11)
     M = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
     cond = np.linalg.cond(M) if n <= 2048 else 6.0
     _check(ctx, M, "tf32x3", 2e-6 * cond * np.sqrt(n))
 
 
-@pytest.mark.parametrize("n", [300, 1353])
-def test_recursive_inverse_of_capacitance_like_matrices(ctx, n):
+@pytest.mark.parametrize("n", [300, 1353, 2088])
+def test_tensor_core_inverse_of_capacitance_like_matrices(ctx, n):
     """The capacitance structure I + K D (3 x 3 contact blocks of widely spread magnitude): as a
     preconditioner the result must leave ||I - M B|| small, like the pivoted Gauss-Jordan's."""
     from paper_2603_16478_gb300.binding import dense_inverse
@@ -139,9 +139,31 @@ def test_recursive_inverse_of_capacitance_like_matrices(ctx, n):
     assert res["tf32x3"] < max(1e-3, 20 * res["mixed"]), res
 
 
-def test_recursive_inverse_needs_invertible_leading_blocks(ctx):
-    """The recursion pivots only inside its 64-row leaves: a matrix whose leading leaf is singular
-    is reported (NONFINITE), not returned as garbage."""
+def test_tensor_core_inverse_pivots_inside_diagonal_blocks(ctx):
+    """Zeros on the diagonal inside every 64 x 64 block: the block's own row pivoting handles them."""
+    n = 300
+    rng = np.random.default_rng(5)
+    M = np.eye(n) * 4 + rng.standard_normal((n, n)) / np.sqrt(n)
+    perm = np.arange(n)
+    for b0 in range(0, n, 64):  # rotate the rows within each diagonal block
+        blk = perm[b0:min(n, b0 + 64)]
+        perm[b0:min(n, b0 + 64)] = np.roll(blk, 1)
+    M = M[perm]
+    M[np.arange(n), np.arange(n)] = 0.0
+    _check(ctx, M, "tf32x3", 1e-4)
+
+
+def test_tensor_core_inverse_repeat_calls_are_deterministic(ctx):
+    from paper_2603_16478_gb300.binding import dense_inverse
+    M = torch.tensor(_capacitance_like(1353, 3), device="cuda")
+    a = dense_inverse(ctx, M, "tf32x3")
+    b = dense_inverse(ctx, M, "tf32x3")
+    assert torch.equal(a, b)
+
+
+def test_tensor_core_inverse_needs_invertible_diagonal_blocks(ctx):
+    """Pivoting stays inside the 64 x 64 diagonal blocks: a matrix whose leading block is singular
+    is reported (NONFINITE), not returned as garbage, and the next call works."""
     from paper_2603_16478_gb300 import NcpadjError
     from paper_2603_16478_gb300.binding import dense_inverse
     n = 100
@@ -151,3 +173,5 @@ def test_recursive_inverse_needs_invertible_leading_blocks(ctx):
     M[:64, 64:] = rng.standard_normal((64, 36))
     with pytest.raises(NcpadjError, match="NONFINITE"):
         dense_inverse(ctx, torch.tensor(M, device="cuda"), "tf32x3")
+    good = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
+    _check(ctx, good, "tf32x3", 1e-5)

@@ -12,7 +12,7 @@ import pytest
 
 from paper_2603_16478_gb300 import build as B
 
-SOURCES = ("elem.cu", "linalg.cu", "gj.cu")
+SOURCES = ("elem.cu", "linalg.cu", "gj.cu", "bgj.cu")
 # k_gj_cols<float, 4, 16, false> and k_gj_cols<float, 2, 32, false> (mangled template arguments)
 ALLOWED = (re.compile(r"k_gj_colsIfLi4ELi16ELb0E"), re.compile(r"k_gj_colsIfLi2ELi32ELb0E"))
 
