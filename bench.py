@@ -260,19 +260,34 @@ def apply_roofline(pkg, torch, dev, scene, K, precision="fp64"):
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_spmv_chunks_fp32_batched.md")
 
 
+def spmv_kernels_digest(src_text):
+    """sha256 of the source text of the two kernels of the A^{-1} product (k_spmv_range_chunks and
+    k_spmv_chunks, each from its template line to its closing brace): the profiled traffic stays valid
+    while that text is unchanged, whatever else changes in the file."""
+    import hashlib
+    import re
+    parts = []
+    for name in ("k_spmv_range_chunks", "k_spmv_chunks"):
+        m = re.search(r"^template <[^\n]*>\n__global__ void __launch_bounds__\(256\) " + name + r"\(.*?^}\n",
+                      src_text, re.M | re.S)
+        if not m:
+            return None
+        parts.append(m.group(0))
+    return hashlib.sha256("".join(parts).encode()).hexdigest()
+
+
 def profiled_traffic():
     """DRAM bytes (read + write) of one FP32 A^{-1} apply on the 64-block union, from the committed ncu
-    summary -- or None when there is none, or when the kernels' source file has changed since the
-    counters were taken (the summary records its sha256)."""
-    import hashlib
+    summary -- or None when there is none, or when the kernels have changed since the counters were
+    taken (the summary records the digest of their source text)."""
     import re
     if not os.path.exists(TRAFFIC_PROFILE):
         return None, "no ncu summary"
     txt = open(TRAFFIC_PROFILE).read()
     m = re.search(r"^traffic_bytes_per_apply:\s*(\d+)", txt, re.M)
-    h = re.search(r"^linalg_cu_sha256:\s*([0-9a-f]{64})", txt, re.M)
+    h = re.search(r"^spmv_kernels_sha256:\s*([0-9a-f]{64})", txt, re.M)
     src = os.path.join(ROOT, "paper_2603_16478_gb300", "csrc", "linalg.cu")
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    cur = spmv_kernels_digest(open(src).read())
     if not m or not h:
         return None, "ncu summary without traffic"
     if h.group(1) != cur:

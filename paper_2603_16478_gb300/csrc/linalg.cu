@@ -565,15 +565,27 @@ __global__ void k_multi_dot_idx(int n, const double* __restrict__ V, long ld, co
   }
 }
 // V_{j+1} -= sum_{k <= j} coef[k] V_k
-__global__ void k_multi_axpy_idx(int n, const double* __restrict__ V, long ld, const int* __restrict__ jp,
-                                 const double* __restrict__ coef, double* __restrict__ Vw) {
+// 256 threads per block = 32 elements x 8 groups of the basis: thread (e, g) sums coef[k] V_k[i] over
+// k = g, g + 8, ..., and the eight partial sums of an element are added in group order.
+__global__ void __launch_bounds__(256) k_multi_axpy_idx(int n, const double* __restrict__ V, long ld,
+                                                        const int* __restrict__ jp, const double* __restrict__ coef,
+                                                        double* __restrict__ Vw) {
   const int j = *jp;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double* w = Vw + (size_t)(j + 1) * ld;
-  double acc = w[i];
-  for (int k = 0; k <= j; ++k) acc -= coef[k] * V[(size_t)k * ld + i];
-  w[i] = acc;
+  const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + e;
+  __shared__ double part[8][32];
+  double acc = 0.0;
+  if (i < n)
+    for (int k = g; k <= j; k += 8) acc += coef[k] * V[(size_t)k * ld + i];
+  part[g][e] = acc;
+  __syncthreads();
+  if (g == 0 && i < n) {
+    double t = part[0][e];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += part[q][e];
+    double* w = Vw + (size_t)(j + 1) * ld;
+    w[i] -= t;
+  }
 }
 // V_{j+1} /= sqrt(*nrm2); h_slot = the norm
 __global__ void k_normalize_idx(int n, double* V, long ld, const int* __restrict__ jp, const double* nrm2,
@@ -809,7 +821,7 @@ void launch_multi_dot_idx(int n, int mmax, const double* V, long ld, const int* 
 void launch_multi_axpy_idx(int n, const double* V, long ld, const int* jp, const double* coef, double* Vw,
                            cudaStream_t s) {
   g_launches += 1;
-  k_multi_axpy_idx<<<nblk(n, 256), 256, 0, s>>>(n, V, ld, jp, coef, Vw);
+  k_multi_axpy_idx<<<nblk(n, 32), 256, 0, s>>>(n, V, ld, jp, coef, Vw);
 }
 void launch_normalize_idx(int n, double* V, long ld, const int* jp, const double* nrm2, double* h_slot, cudaStream_t s) {
   g_launches += 1;

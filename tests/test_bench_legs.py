@@ -114,14 +114,20 @@ def test_krylov_summary_counts_the_blocks_own_iterations():
 
 
 def test_profiled_traffic_is_dropped_once_the_kernels_change(tmp_path, monkeypatch):
-    import hashlib
-    src = open(bench.os.path.join(bench.ROOT, "paper_2603_16478_gb300", "csrc", "linalg.cu"), "rb").read()
+    """The traffic of the committed capture stands while the two kernels' source text is unchanged,
+    whatever else changes in their file."""
+    src = open(bench.os.path.join(bench.ROOT, "paper_2603_16478_gb300", "csrc", "linalg.cu")).read()
+    digest = bench.spmv_kernels_digest(src)
+    assert digest is not None
+    assert bench.spmv_kernels_digest(src + "\n// another kernel\n") == digest
+    edited = src.replace("a0 = warp_sum(a0);", "a0 = warp_sum(a0) * 1;", 1)
+    assert bench.spmv_kernels_digest(edited) != digest
     prof = tmp_path / "p.md"
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
     assert bench.profiled_traffic()[0] is None
-    prof.write_text(f"traffic_bytes_per_apply: 1234\nlinalg_cu_sha256: {hashlib.sha256(src).hexdigest()}\n")
+    prof.write_text(f"traffic_bytes_per_apply: 1234\nspmv_kernels_sha256: {digest}\n")
     assert bench.profiled_traffic()[0] == 1234
-    prof.write_text("traffic_bytes_per_apply: 1234\nlinalg_cu_sha256: " + "0" * 64 + "\n")
+    prof.write_text("traffic_bytes_per_apply: 1234\nspmv_kernels_sha256: " + "0" * 64 + "\n")
     assert bench.profiled_traffic() == (None, "kernels changed since the ncu capture")
 
 
