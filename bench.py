@@ -435,7 +435,7 @@ def beam_leg(pkg, torch, dev, steps, warmup, flush, with_models=True, cpu=False)
     ref = {k: v.clone() for k, v in one("fp64")[0].items()}
     res, grads_by = {}, {"fp64": ref}
     for name, (pr, cp) in {"fp64": ("fp64", "fp64"), "mixed": ("mixed", "mixed"), "mixed_tc": ("mixed", "tf32x3"),
-                           "mixed_cap64": ("mixed", "fp64")}.items():
+                           "mixed_cap64": ("mixed", "fp64"), "mixed_refined": ("mixed", "refined")}.items():
         g_ = one(pr, cp)[0]
         grads_by[name] = {k: v.clone() for k, v in g_.items()}
         tm, sts = timed(pr, cp, steps)
@@ -799,7 +799,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     variants = {"fp64": ("fp64", "fp64"), "mixed": ("mixed", "mixed"), "mixed_tc": ("mixed", "tf32x3"),
-                "mixed_cap64": ("mixed", "fp64")}
+                "mixed_cap64": ("mixed", "fp64"), "mixed_refined": ("mixed", "refined")}
     calls = {k: W.call(pkg, *v) for k, v in variants.items()}
     # accuracy of the mixed variants against plain FP64 on the same inputs (every block, every output)
     grads_by = {}
@@ -808,7 +808,7 @@ def main():
         torch.cuda.synchronize(dev)
         grads_by[k] = [{n: t.clone() for n, t in o.items()} for o in c.outputs]
     errs = {}
-    for k in ("mixed", "mixed_tc", "mixed_cap64"):
+    for k in ("mixed", "mixed_tc", "mixed_cap64", "mixed_refined"):
         e = 0.0
         for ob, rb, nc in zip(grads_by[k], grads_by["fp64"], W.n_contacts):
             for n in rb:
@@ -825,7 +825,7 @@ def main():
     head = fast[0] if fast else ("mixed_cap64" if errs["mixed_cap64"] <= 1e-3 else "fp64")
     side_steps = max(3, args.steps // 2)
     results = {}
-    for k in ("fp64", "mixed_cap64", "mixed", "mixed_tc"):
+    for k in ("fp64", "mixed_cap64", "mixed_refined", "mixed", "mixed_tc"):
         if k != head:
             results[k] = time_calls(torch, dev, calls[k], stream, flush, side_steps, args.warmup, world, dist)
     clocks = ClockSampler(local)
@@ -930,7 +930,10 @@ def main():
                                      "FP64 Krylov reductions", "mixed_tc": "FP32 matrix/preconditioner, capacitance "
                                      "inverted in FP32 by the tensor-core blocked Gauss-Jordan (3xTF32), FP64 "
                                      "Krylov reductions", "mixed_cap64": "FP32 matrix/preconditioner, FP64 "
-                                     "capacitance factor and Krylov reductions"}[head],
+                                     "capacitance factor and Krylov reductions", "mixed_refined": "FP32 "
+                                     "matrix/preconditioner, FP64-accurate capacitance solve (tensor-core FP32 "
+                                     "inverse refined once against the FP64 capacitance), FP64 Krylov "
+                                     "reductions"}[head],
                        "variants": per_variant, "max_rel_err_vs_fp64": errs,
                        "max_rel_err_vs_oracle": err_oracle, "preconditioner": "Woodbury",
                        "solver": "GMRES(64) per block, flexible", "rtol": 1e-8, "krylov_iterations": its,

@@ -65,7 +65,7 @@ typedef enum {
   NCPADJ_ERR_CONTACT_DOMAIN = 10   /* a frictional contact has zero slip (no direction) */
 } ncpadj_status;
 
-enum { NCPADJ_FP64 = 0, NCPADJ_MIXED = 1, NCPADJ_TF32X3 = 2 };
+enum { NCPADJ_FP64 = 0, NCPADJ_MIXED = 1, NCPADJ_TF32X3 = 2, NCPADJ_REFINED = 3 };
 enum {
   NCPADJ_PRECOND_NONE = 0,
   NCPADJ_PRECOND_JACOBI = 1,   /* diag(script_A)^{-1} (Sec. 4.4, Jacobi preconditioner) */
@@ -307,10 +307,12 @@ typedef struct {
  *              (flexible) is used whatever is asked); memory NCPADJ_MEM_*.
  *   cap_precision  inversion of the contact capacitance I + h^2 K^T D: NCPADJ_FP64 (default),
  *              NCPADJ_MIXED (inverted by Gauss-Jordan and applied in FP32; it only preconditions,
- *              so the result keeps the solve's precision and tolerance) or NCPADJ_TF32X3 (FP32,
+ *              so the result keeps the solve's precision and tolerance), NCPADJ_TF32X3 (FP32,
  *              inverted by the blocked Gauss-Jordan elimination of ncpadj_dense_inverse whose
  *              rank-64 updates run on the tensor cores; pivoting only inside its 64 x 64
- *              diagonal blocks).
+ *              diagonal blocks) or NCPADJ_REFINED (the TF32X3 inverse X, and every capacitance
+ *              solve refined once against the FP64 capacitance C: x = X y, x += X (y - C x), an
+ *              FP64-accurate solve while ||I - C X|| is small; directly inverted blocks only).
  *   cap_block  most contacts per directly inverted capacitance block (0 = default = 2730 with an
  *              FP32 capacitance, 1365 with FP64; at most 5461 resp. 1365).  A scene with
  *              more contacts has its capacitance solved iteratively (Sec. 4.4): an inner

@@ -19,7 +19,7 @@ STATUS = ["OK", "INVALID_ARG", "CUDA", "OOM", "INVERTED_ELEMENT", "NOT_CONVERGED
           "NOT_FACTORED", "UNSUPPORTED", "CONTACT_DOMAIN"]
 PRECOND = {"none": 0, "jacobi": 1, "elastic": 2, "woodbury": 3}
 SOLVER = {"auto": 0, "cg": 1, "gmres": 2, "bicgstab": 3, "semi_implicit": 4}
-PRECISION = {"fp64": 0, "mixed": 1, "tf32x3": 2}
+PRECISION = {"fp64": 0, "mixed": 1, "tf32x3": 2, "refined": 3}  # "refined": capacitance precision only
 MEMORY = {"device": 0, "host": 1}
 MODEL = {"neo_hookean": 0, "corotational": 1, "arap": 2}
 

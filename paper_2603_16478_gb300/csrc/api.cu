@@ -615,9 +615,16 @@ struct Engine {
 
   // x = C^{-1} y over every directly inverted capacitance block, in one launch
   void cap_apply_all(const double* y, double* x, const int* act = nullptr) {
-    launch_cap_apply_all((int)blk_c0.size(), cap_nmax, S.capmeta.as<int64_t>(), (mixed || cap_fp32) ? Cm32 : nullptr,
+    const int nbk = (int)blk_c0.size();
+    launch_cap_apply_all(nbk, cap_nmax, S.capmeta.as<int64_t>(), (mixed || cap_fp32) ? Cm32 : nullptr,
                          (mixed || cap_fp32) ? nullptr : Cm, piv, y, x, act, st);
+    if (cap_refine) {  // one step of iterative refinement against the FP64 capacitance: x += X (y - C x)
+      double* r = S.capres.as<double>();
+      launch_cap_resid_all(nbk, cap_nmax, S.capmeta.as<int64_t>(), Cm, y, x, r, act, st);
+      launch_cap_apply_all(nbk, cap_nmax, S.capmeta.as<int64_t>(), Cm32, nullptr, piv, r, x, act, st, true);
+    }
   }
+  bool cap_refine = false;  // NCPADJ_REFINED: FP32 inverse, each solve refined against the FP64 capacitance
   int cap_block = 0;      // most contacts per capacitance block (0: the largest the direct inverse takes)
   float *x32 = nullptr, *w32 = nullptr, *Cm32 = nullptr;
   float2* zsplit = nullptr;  // double-float pairs of the Arnoldi matvec's input (mixed)
@@ -761,6 +768,7 @@ struct Engine {
       }
       Cm = S.cap.as<double>();
       Ds = Cm + cap_elems;
+      if (cap_refine) S.capres.ensure(sizeof(double) * ((size_t)ncap + 16));
       piv = reinterpret_cast<int32_t*>(Ds + ds_elems + 16);
       if (!sup_c0.empty()) {
         int smax = 0;
@@ -1241,7 +1249,8 @@ struct Engine {
                                 (uintptr_t)S.bsr64.p, (uintptr_t)S.xpos.p, (uintptr_t)S.gstep.p,
                                 (uintptr_t)flexible_gmres(), (uintptr_t)S.fgmres.p,
                                 (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size(), (uintptr_t)S.xsplit.p,
-                                (uintptr_t)S.capmeta.p, (uintptr_t)cap_nmax};
+                                (uintptr_t)S.capmeta.p, (uintptr_t)cap_nmax, (uintptr_t)cap_refine,
+                                (uintptr_t)S.capres.p};
     for (size_t b = 0; b < blk_c0.size(); ++b) {
       k.push_back((uintptr_t)blk_c0[b]);
       k.push_back((uintptr_t)blk_nc[b]);
@@ -1753,7 +1762,7 @@ void validate_options(const ncpadj_options& opt) {
   NCPADJ_REQUIRE(opt.memory == NCPADJ_MEM_DEVICE || opt.memory == NCPADJ_MEM_HOST, "bad memory kind");
   NCPADJ_REQUIRE(opt.precision == NCPADJ_FP64 || opt.precision == NCPADJ_MIXED, "bad precision");
   NCPADJ_REQUIRE(opt.cap_precision == NCPADJ_FP64 || opt.cap_precision == NCPADJ_MIXED ||
-                     opt.cap_precision == NCPADJ_TF32X3,
+                     opt.cap_precision == NCPADJ_TF32X3 || opt.cap_precision == NCPADJ_REFINED,
                  "bad cap_precision");
   NCPADJ_REQUIRE(opt.cap_block >= 0, "bad cap_block");
 }
@@ -1850,7 +1859,8 @@ static ncpadj_status adjoint_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   int solver = pick_solver(opt.solver, nc, nc ? ct->mu : nullptr, host_mem, st);
   E.mixed = opt.precision == NCPADJ_MIXED;
   E.cap_fp32 = opt.cap_precision != NCPADJ_FP64;
-  E.cap_tc = opt.cap_precision == NCPADJ_TF32X3;
+  E.cap_tc = opt.cap_precision == NCPADJ_TF32X3 || opt.cap_precision == NCPADJ_REFINED;
+  E.cap_refine = opt.cap_precision == NCPADJ_REFINED;
   E.cap_block = opt.cap_block;
   E.cap_drop = opt.cap_drop;
   int* flags = E.flags;
@@ -2334,7 +2344,8 @@ static ncpadj_status forward_step(ncpadj_ctx_s* ctx, ncpadj_scene_s* sc, const n
   int solver = pick_solver(opt.solver, nc, E.in.mu, false, st);
   // the Newton solves run in FP64; the capacitance (a preconditioner only) follows cap_precision
   E.cap_fp32 = opt.cap_precision != NCPADJ_FP64;
-  E.cap_tc = opt.cap_precision == NCPADJ_TF32X3;
+  E.cap_tc = opt.cap_precision == NCPADJ_TF32X3 || opt.cap_precision == NCPADJ_REFINED;
+  E.cap_refine = opt.cap_precision == NCPADJ_REFINED;
   E.cap_block = opt.cap_block;
   E.cap_drop = opt.cap_drop;
   int* flags = E.flags;

@@ -115,7 +115,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cap_apply_all(int nb, const int64_t* __restrict__ meta,
                                                        const T* __restrict__ Bs, const int32_t* __restrict__ piv,
                                                        const double* __restrict__ y, double* __restrict__ x,
-                                                       const int* __restrict__ act) {
+                                                       const int* __restrict__ act, int accumulate) {
   const int k = blockIdx.y;
   const int64_t moff = meta[k], o = meta[nb + k];
   const int n = (int)meta[2 * nb + k], scene = (int)meta[3 * nb + k];
@@ -149,7 +149,54 @@ __global__ void __launch_bounds__(256) k_cap_apply_all(int nb, const int64_t* __
   __syncthreads();
   if (threadIdx.x < 4) {
     const int rr = blockIdx.x * 4 + threadIdx.x;
-    if (rr < n) x[o + rr] = (double)(part[threadIdx.x][0] + part[threadIdx.x][1]);
+    if (rr < n) {
+      const double v = (double)(part[threadIdx.x][0] + part[threadIdx.x][1]);
+      x[o + rr] = accumulate ? x[o + rr] + v : v;
+    }
+  }
+}
+
+// r_k = y_k - C_k x_k in FP64 for every capacitance block k (C_k the capacitance itself, row-major at
+// C + meta[k], unpermuted; x_k in natural order): the residual of one step of iterative refinement.
+// Layout as k_cap_apply_all: block (bx, k) takes rows 4 bx .. 4 bx + 3, two warps per row, x_k staged
+// in shared memory.
+__global__ void __launch_bounds__(256) k_cap_resid_all(int nb, const int64_t* __restrict__ meta,
+                                                       const double* __restrict__ C, const double* __restrict__ y,
+                                                       const double* __restrict__ x, double* __restrict__ r,
+                                                       const int* __restrict__ act) {
+  const int k = blockIdx.y;
+  const int64_t moff = meta[k], o = meta[nb + k];
+  const int n = (int)meta[2 * nb + k], scene = (int)meta[3 * nb + k];
+  if (act && !act[scene]) return;
+  if ((int)blockIdx.x * 4 >= n) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* xs = reinterpret_cast<double*>(smraw);
+  __shared__ double part[4][2];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = x[o + j];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rloc = warp >> 1, half = warp & 1;
+  const int row_i = blockIdx.x * 4 + rloc;
+  double acc = 0;
+  if (row_i < n) {
+    const double* row = C + moff + (size_t)row_i * n;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int j = half * 32 + lane;
+    for (; j + 192 < n; j += 256) {
+      a0 += row[j] * xs[j];
+      a1 += row[j + 64] * xs[j + 64];
+      a2 += row[j + 128] * xs[j + 128];
+      a3 += row[j + 192] * xs[j + 192];
+    }
+    for (; j < n; j += 64) a0 += row[j] * xs[j];
+    acc = (a0 + a1) + (a2 + a3);
+  }
+  acc = lane_sum(acc);
+  if (lane == 0) part[rloc][half] = acc;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int rr = blockIdx.x * 4 + threadIdx.x;
+    if (rr < n) r[o + rr] = y[o + rr] - (part[threadIdx.x][0] + part[threadIdx.x][1]);
   }
 }
 
@@ -219,12 +266,28 @@ void launch_cap_form_all(int nb, int mmax, const int64_t* meta, const int32_t* c
 }
 
 void launch_cap_apply_all(int nb, int nmax, const int64_t* meta, const float* B32, const double* B64,
-                          const int32_t* piv, const double* y, double* x, const int* act, cudaStream_t s) {
+                          const int32_t* piv, const double* y, double* x, const int* act, cudaStream_t s,
+                          bool accumulate) {
   if (nb <= 0 || nmax <= 0) return;
   g_launches += 1;
   const dim3 grid((nmax + 3) / 4, nb);
-  if (B32) k_cap_apply_all<float><<<grid, 256, sizeof(float) * (size_t)nmax, s>>>(nb, meta, B32, piv, y, x, act);
-  else k_cap_apply_all<double><<<grid, 256, sizeof(double) * (size_t)nmax, s>>>(nb, meta, B64, piv, y, x, act);
+  if (B32)
+    k_cap_apply_all<float><<<grid, 256, sizeof(float) * (size_t)nmax, s>>>(nb, meta, B32, piv, y, x, act, accumulate);
+  else
+    k_cap_apply_all<double><<<grid, 256, sizeof(double) * (size_t)nmax, s>>>(nb, meta, B64, piv, y, x, act, accumulate);
+}
+
+void launch_cap_resid_all(int nb, int nmax, const int64_t* meta, const double* C, const double* y, const double* x,
+                          double* r, const int* act, cudaStream_t s) {
+  if (nb <= 0 || nmax <= 0) return;
+  g_launches += 1;
+  const size_t sm = sizeof(double) * (size_t)nmax;
+  static thread_local size_t sm_set = 0;
+  if (sm > 48 * 1024 && sm > sm_set) {
+    cudaFuncSetAttribute(k_cap_resid_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    sm_set = sm;
+  }
+  k_cap_resid_all<<<dim3((nmax + 3) / 4, nb), 256, sm, s>>>(nb, meta, C, y, x, r, act);
 }
 
 int small_inverse_max(bool fp32) { return fp32 ? 192 : 128; }

@@ -100,9 +100,15 @@ void launch_small_inverse(int nsmall, const int32_t* ids, int nb, const int64_t*
                           double* B64, int32_t* piv, int* flags, cudaStream_t s);
 // x_k = B_k y_k (both pivot permutations, as launch_gj_apply*) for all nb capacitance blocks in one
 // launch; meta: int64 [4][nb] = element offset of B_k, offset 3 c0_k of its rows in y/x (and piv),
-// dimension n_k <= nmax, scene; B32 (FP32 inverses) or B64; act (nullable): skip blocks of idle scenes
+// dimension n_k <= nmax, scene; B32 (FP32 inverses) or B64; act (nullable): skip blocks of idle scenes;
+// accumulate: x_k += B_k y_k
 void launch_cap_apply_all(int nb, int nmax, const int64_t* meta, const float* B32, const double* B64,
-                          const int32_t* piv, const double* y, double* x, const int* act, cudaStream_t s);
+                          const int32_t* piv, const double* y, double* x, const int* act, cudaStream_t s,
+                          bool accumulate = false);
+// r_k = y_k - C_k x_k in FP64 for every block of the same table, C_k the capacitance itself (unpermuted,
+// at C + meta[k]), x_k in natural order: the residual of a refinement step of the capacitance solve
+void launch_cap_resid_all(int nb, int nmax, const int64_t* meta, const double* C, const double* y, const double* x,
+                          double* r, const int* act, cudaStream_t s);
 
 // ---- triangle (shell) elements and isometric bending (shell.cu) ---------------------------
 // TetArgs with the triangle layout: tets [nt][3], gvec [nt][6] (2-vectors g_0..g_2), slot [nt][9],
