@@ -216,7 +216,8 @@ def run_reference(args):
 # batched uneven scenes: 64 independent blocks (log-uniform 2k..50k tets), one adjoint each
 # --------------------------------------------------------------------------------------------
 def apply_roofline(pkg, torch, dev, scene, K, precision="fp64"):
-    """GB/s of the product with A^{-1} = P^T S^T S P (two k_spmv_chunks launches, 3 RHS; FP64, or the
+    """GB/s of the product with A^{-1} = P^T S^T S P (k_spmv_range_chunks for S, k_spmv_chunks for S^T,
+    3 RHS, at the scene's chunk length; FP64, or the
     FP32 values and intermediates of the mixed preconditioner) on a scene: K applies captured into
     one CUDA graph and replayed, timed with events on the replay stream.  Algorithmic bytes count
     the Cholesky factor L (2 nnz(L) values + indices) and the vectors; kernel bytes count what the
@@ -249,8 +250,9 @@ def apply_roofline(pkg, torch, dev, scene, K, precision="fp64"):
     alg = 2 * info["nnz_L"] * (bv + 4) + vec
     kb = info["nnz_Linv"] * (2 * bv + 4) + vec  # S: values only (rows are column ranges); S^T: values + indices
     peak, src = peaks()
-    return {"kernel": f"k_spmv_chunks x2 (A^-1 = P^T S^T S P, {'FP64' if precision == 'fp64' else 'FP32'} values, "
-                      "3 RHS)", "bound": "hbm",
+    return {"kernel": f"k_spmv_range_chunks + k_spmv_chunks (A^-1 = P^T S^T S P, "
+                      f"{'FP64' if precision == 'fp64' else 'FP32'} values, 3 RHS, chunks of {scene.chunk})",
+            "bound": "hbm",
             "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
             "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": src, "ms_per_launch_pair": ms,
             "algorithmic_bytes": alg, "kernel_bytes": kb, "kernel_bytes_gbs": kb / (ms / 1e3) / 1e9,
@@ -753,6 +755,8 @@ def main():
                     help="build the scene and run only the A^-1 roofline measurement (for profiler captures)")
     ap.add_argument("--blocks", type=int, default=64,
                     help="--roofline-only batched: the first N blocks of the batch (smaller profiler captures)")
+    ap.add_argument("--chunk", type=int, default=0, choices=[0, 128, 256, 512],
+                    help="chunk length of the A^-1 product (0: tuned by timing; with --roofline-only: 256)")
     ap.add_argument("--batch-only", action="store_true",
                     help="time only the batched headline (no side legs; for profiler launch lists)")
     args = ap.parse_args()
@@ -784,7 +788,10 @@ def main():
             blocks = synth.block_batch(64)[:args.blocks]
             scene = pkg.Scene.batch(ctx, [(x.scene.X, x.scene.tets, x.scene.E, x.scene.nu, x.scene.density)
                                           for x in blocks], blocks[0].scene.h)
-        print(json.dumps({"roofline_only": args.roofline_only, "blocks": args.blocks, "info": scene.info(),
+        if args.chunk:
+            scene.set_chunk(args.chunk)
+        print(json.dumps({"roofline_only": args.roofline_only, "blocks": args.blocks, "chunk": scene.chunk,
+                          "info": scene.info(),
                           "roofline": apply_roofline(pkg, torch, dev, scene, 10, precision="mixed")}))
         return
 
@@ -823,6 +830,15 @@ def main():
         pre = {k: time_calls(torch, dev, calls[k], stream, flush, 2, 1, world, dist)[0] for k in fast}
         fast.sort(key=lambda k: pre[k])
     head = fast[0] if fast else ("mixed_cap64" if errs["mixed_cap64"] <= 1e-3 else "fp64")
+    # launch shape of the A^{-1} product (chunk length per warp), picked by timing the headline call
+    from paper_2603_16478_gb300.autotune import CHUNKS, tune_shape
+    if args.chunk:
+        W.scene.set_chunk(args.chunk)
+        chunk, chunk_ms = args.chunk, {}
+    else:
+        chunk, chunk_ms = tune_shape(
+            W.scene.set_chunk,
+            lambda: time_calls(torch, dev, calls[head], stream, flush, 2, 1, world, dist)[0] / 2, list(CHUNKS))
     side_steps = max(3, args.steps // 2)
     results = {}
     for k in ("fp64", "mixed_cap64", "mixed_refined", "mixed", "mixed_tc"):
@@ -934,6 +950,8 @@ def main():
                                      "matrix/preconditioner, FP64-accurate capacitance solve (tensor-core FP32 "
                                      "inverse refined once against the FP64 capacitance), FP64 Krylov "
                                      "reductions"}[head],
+                       "launch_shape": {"chunk": chunk, "ms_per_call_by_chunk": chunk_ms,
+                                        "tuner": "autotune.tune_shape over the headline call"},
                        "variants": per_variant, "max_rel_err_vs_fp64": errs,
                        "max_rel_err_vs_oracle": err_oracle, "preconditioner": "Woodbury",
                        "solver": "GMRES(64) per block, flexible", "rtol": 1e-8, "krylov_iterations": its,

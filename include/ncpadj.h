@@ -430,6 +430,16 @@ ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre);
  * Errors: INVALID_ARG (NULL scene, a value that is no NCPADJ_MODEL_*), OOM, CUDA. */
 ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model);
 
+/* Launch shape of the product with A^{-1} = P^T S^T S P (the sparse-inverse preconditioner of
+ * Sec. 3, GPU acceleration via sparse-inverse factorization; the paper fixes no launch shape): the
+ * rows of S and S^T are cut into chunks of at most `entries` nonzeros, one warp per chunk with
+ * entries / 32 values in flight per lane.  128, 256 (the default) or 512; the best depends on the
+ * scene's factor and is found by timing (paper_2603_16478_gb300.autotune).  Results agree to
+ * rounding (the chunks' partial sums are added in a different grouping).  Takes effect from the
+ * next call on the scene; a refactor keeps it.
+ * Errors: INVALID_ARG (NULL scene, another size), OOM, CUDA. */
+ncpadj_status ncpadj_scene_set_chunk(ncpadj_scene scene, int32_t entries);
+
 /* Cinv = C^{-1} for a dense row-major n x n matrix, by the blocked Gauss-Jordan elimination with
  * partial pivoting that inverts the contact capacitance I + h^2 K D of the Woodbury
  * preconditioner (Sec. 4.4); exposed so that the inversion can be used and checked on its own.

@@ -1,15 +1,20 @@
-"""Autotuner for the adjoint's runtime choices on a given scene.
+"""Autotuner for the adjoint's launch shapes and runtime choices on a given scene.
 
-The adjoint exposes its choices as options: the precision variant (plain FP64; FP32 matrix and
-preconditioner with the FP64 capacitance inverse; everything FP32 but the Krylov reductions),
-the GMRES restart length and the largest capacitance block inverted directly (beyond it the
-contact-space system is solved iteratively, Sec. 4.4).  Which combination is fastest depends on
-the scene: the number of contacts, how stiff they are, the mesh size.  The tuner times every
-candidate with the real call on the real inputs, keeps those whose gradients stay within a
-relative error bound of the plain FP64 result on the same inputs, and returns the fastest.
-Choices are cached per scene signature (sizes, rounded to powers of two), so a rollout or a
-batch tunes once.  Only host-side selection lives here; every timed step runs in the library's
-kernels.
+Two stages, both timed with the real call on the real inputs:
+
+1. The launch shape of the dominant kernels, the product with A^{-1} = P^T S^T S P: the chunk length
+   (128, 256 or 512 nonzeros per warp, ``Scene.set_chunk``).  Which is fastest depends on the
+   factor's row lengths and on whether S and S^T stay in L2.  ``tune_shape`` times each candidate
+   and keeps the fastest.
+2. The options: the precision variant (plain FP64; FP32 matrix and preconditioner with the
+   capacitance inverted in FP64, by pivoted Gauss-Jordan in FP32, by the tensor-core blocked
+   Gauss-Jordan, or by the tensor-core inverse refined against the FP64 capacitance), the GMRES
+   restart length and the largest capacitance block inverted directly (beyond it the contact-space
+   system is solved iteratively, Sec. 4.4).  Candidates whose gradients leave a relative error bound
+   of the plain FP64 result on the same inputs are dropped; the fastest of the rest wins.
+
+Choices are cached per scene signature (sizes, rounded to powers of two), so a rollout or a batch
+tunes once.  Only host-side selection lives here; every timed step runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -19,7 +24,9 @@ import os
 from dataclasses import dataclass, field
 from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 
-PRECISION_VARIANTS = (("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "mixed"))
+PRECISION_VARIANTS = (("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "mixed"), ("mixed", "tf32x3"),
+                      ("mixed", "refined"))
+CHUNKS = (128, 256, 512)
 GRAD_KEYS = ("dL_dq_prev", "dL_dv_prev", "dL_dfext", "dL_dE", "dL_dnu", "dL_dmu", "dL_dmu_contact")
 
 
@@ -39,6 +46,8 @@ class Choice:
     ms: float
     rel_err: float
     trials: List[Trial] = field(default_factory=list)
+    chunk: Optional[int] = None                        # launch shape of the A^{-1} product
+    chunk_ms: Dict[int, float] = field(default_factory=dict)
 
 
 def default_candidates(n_contacts: int, restarts: Sequence[int] = (32, 64, 128)) -> List[Dict[str, object]]:
@@ -51,6 +60,27 @@ def default_candidates(n_contacts: int, restarts: Sequence[int] = (32, 64, 128))
             for cb in blocks:
                 out.append({"precision": prec, "cap_precision": cap, "restart": int(m), "cap_block": int(cb)})
     return out
+
+
+def tune_shape(apply: Callable[[object], None], measure: Callable[[], float], shapes: Sequence[object]):
+    """Launch-shape stage: for each shape, ``apply(shape)`` then ``measure() -> ms``; the fastest shape is
+    applied again and returned with every timing ({shape: ms}; a failing shape gets inf)."""
+    times = {}
+    for sh in shapes:
+        try:
+            apply(sh)
+            times[sh] = float(measure())
+        except Exception:  # noqa: BLE001 -- a shape that fails is skipped
+            times[sh] = math.inf
+    ok = [sh for sh in shapes if math.isfinite(times[sh])]
+    if not ok:
+        raise ValueError("no launch shape could be timed")
+    best = ok[0]
+    for sh in ok[1:]:
+        if times[sh] < times[best]:
+            best = sh
+    apply(best)
+    return best, times
 
 
 def select(trials: Iterable[Trial], max_rel_err: float) -> Trial:
@@ -132,7 +162,10 @@ class Cache:
         return None if e is None else dict(e["options"])
 
     def put(self, key: str, choice: Choice) -> None:
-        self.entries[key] = {"options": dict(choice.options), "ms": choice.ms, "rel_err": choice.rel_err}
+        opts = dict(choice.options)
+        if choice.chunk is not None:
+            opts["chunk"] = int(choice.chunk)
+        self.entries[key] = {"options": opts, "ms": choice.ms, "rel_err": choice.rel_err}
         if self.path:
             tmp = self.path + ".tmp"
             with open(tmp, "w") as f:
@@ -142,12 +175,15 @@ class Cache:
 
 def tune_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4, rtol=1e-8,
                  candidates: Optional[Sequence[Dict[str, object]]] = None, max_rel_err: float = 1e-3,
-                 repeats: int = 3, cache: Optional[Cache] = None, stream=None) -> Choice:
-    """Tune ``adjoint_step`` options on these inputs (device tensors, as for adjoint_step).
+                 repeats: int = 3, cache: Optional[Cache] = None, stream=None,
+                 chunks: Optional[Sequence[int]] = CHUNKS) -> Choice:
+    """Tune the launch shape and then the ``adjoint_step`` options on these inputs (device tensors, as
+    for adjoint_step).
 
-    Each candidate runs once untimed, then ``repeats`` times between CUDA events on the call's
-    stream; its time is the median.  The returned options go straight into adjoint_step
-    (``restart``, ``precision``, ``cap_precision``, ``cap_block``)."""
+    Each timing runs the call once untimed, then ``repeats`` times between CUDA events on the call's
+    stream, and takes the median.  The chunk length is timed with the FP32 tensor-core variant and left
+    set on the scene (``chunks=None`` skips that stage); the returned options go straight into
+    adjoint_step (``restart``, ``precision``, ``cap_precision``, ``cap_block``)."""
     import torch
 
     from .binding import adjoint_step
@@ -156,7 +192,10 @@ def tune_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4
     if cache is not None:
         hit = cache.get(key)
         if hit is not None:
-            return Choice(hit, float("nan"), float("nan"))
+            ch = hit.pop("chunk", None)
+            if ch is not None:
+                scene.set_chunk(int(ch))
+            return Choice(hit, float("nan"), float("nan"), chunk=ch)
     dev = q.device
     st = torch.cuda.Stream(dev) if stream is None else stream
 
@@ -185,12 +224,17 @@ def tune_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4
         times.sort()
         return times[len(times) // 2], grads, stats["iterations"]
 
+    chunk, chunk_ms = None, {}
+    if chunks:
+        fast = {"precision": "mixed", "cap_precision": "tf32x3", "restart": 64, "cap_block": 0}
+        chunk, chunk_ms = tune_shape(scene.set_chunk, lambda: measure(fast)[0], list(chunks))
     choice = tune(measure, candidates or default_candidates(nc), reference, max_rel_err,
                   norm=lambda x: float(torch.linalg.norm(x.double() if hasattr(x, "double") else torch.tensor(x))))
+    choice.chunk, choice.chunk_ms = chunk, chunk_ms
     if cache is not None:
         cache.put(key, choice)
     return choice
 
 
-__all__ = ["Trial", "Choice", "Cache", "default_candidates", "select", "tune", "tune_adjoint", "signature",
-           "PRECISION_VARIANTS"]
+__all__ = ["Trial", "Choice", "Cache", "default_candidates", "select", "tune", "tune_adjoint", "tune_shape",
+           "signature", "PRECISION_VARIANTS", "CHUNKS"]

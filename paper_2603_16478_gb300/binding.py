@@ -120,7 +120,7 @@ EXPORTS = ["ncpadj_version", "ncpadj_status_string", "ncpadj_last_error", "ncpad
            "ncpadj_options_default", "ncpadj_adjoint_step", "ncpadj_adjoint_batch", "ncpadj_forward_step",
            "ncpadj_elastic_solve", "ncpadj_elastic_solve_noalloc", "ncpadj_elastic_solve_mixed", "ncpadj_dense_inverse",
            "ncpadj_dense_gemm",
-           "ncpadj_scene_set_fibres", "ncpadj_scene_set_model"]
+           "ncpadj_scene_set_fibres", "ncpadj_scene_set_model", "ncpadj_scene_set_chunk"]
 
 
 def load_library(path: Optional[str] = None):
@@ -164,6 +164,7 @@ def load_library(path: Optional[str] = None):
     lib.ncpadj_scene_set_fibres.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_scene_set_model.argtypes = [C.c_void_p, C.c_void_p]
     lib.ncpadj_dense_inverse.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    lib.ncpadj_scene_set_chunk.argtypes = [C.c_void_p, C.c_int32]
     lib.ncpadj_dense_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_int64,
                                       C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]
     if path is None:
@@ -208,6 +209,8 @@ class Scene:
     ``Scene.shells(ctx, meshes, h)`` builds one or more triangle meshes (shells), each
     ``(X, tris, E, nu, density, thickness, bend)``; their elements take the place of the tets
     (``n_tets`` counts triangles)."""
+
+    chunk = 256  # chunk length of the A^{-1} product (set_chunk)
 
     def __init__(self, ctx: Context, X, tets, E, nu, density: float, h: float, _batch=None, _shells=None):
         self.ctx = ctx
@@ -279,6 +282,12 @@ class Scene:
             raise ValueError(f"expected {self.n_tets} fibres, got {f.shape[0]}")
         self._fibre = f
         _check(self.lib, self.lib.ncpadj_scene_set_fibres(self.handle, C.c_void_p(f.data_ptr())))
+
+    def set_chunk(self, entries: int) -> None:
+        """Chunk length (128, 256 or 512 nonzeros per warp) of the A^{-1} product's kernels; a launch
+        shape the autotuner picks by timing."""
+        _check(self.lib, self.lib.ncpadj_scene_set_chunk(self.handle, int(entries)))
+        self.chunk = int(entries)
 
     def set_model(self, model) -> None:
         """Constitutive model of every tet (App. B.2): one of "neo_hookean", "corotational", "arap",

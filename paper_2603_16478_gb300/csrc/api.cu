@@ -42,6 +42,35 @@ static void upload(DevBuf& b, const std::vector<T>& v) {
   if (!v.empty()) NCPADJ_CUDA_TRY(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
 
+// Chunks of the rows of S and S^T for the A^{-1} product: at most len entries each (one warp per
+// chunk, len / 32 values per lane), with S's first column per chunk (its rows are column ranges)
+static void rechunk(Scene& S, int len) {
+  auto chunk = [len](const std::vector<int64_t>& ptr, int n, DevBuf& crow, DevBuf& cb, DevBuf& ce) {
+    std::vector<int32_t> r;
+    std::vector<int64_t> b, e;
+    for (int i = 0; i < n; ++i)
+      for (int64_t p = ptr[i]; p < ptr[i + 1]; p += len) {
+        r.push_back(i);
+        b.push_back(p);
+        e.push_back(std::min<int64_t>(p + len, ptr[i + 1]));
+      }
+    upload(crow, r);
+    upload(cb, b);
+    upload(ce, e);
+    return (int)r.size();
+  };
+  const int n = (int)S.S_first_h.size();
+  S.nS_chunks = chunk(S.S_ptr_h, n, S.S_crow, S.S_cbeg, S.S_cend);
+  std::vector<int32_t> c0;
+  c0.reserve(S.nS_chunks);
+  for (int i = 0; i < n; ++i)
+    for (int64_t p = S.S_ptr_h[i]; p < S.S_ptr_h[i + 1]; p += len)
+      c0.push_back(S.S_first_h[i] + (int32_t)(p - S.S_ptr_h[i]));
+  upload(S.S_c0, c0);
+  S.nSt_chunks = chunk(S.St_ptr_h, n, S.St_crow, S.St_cbeg, S.St_cend);
+  S.chunk = len;
+}
+
 static ncpadj_status fail(const Error& e) {
   set_error(e.msg);
   return e.status;
@@ -441,34 +470,18 @@ static void build_scene(Scene& S, const MeshSpec* descs, int n_scenes) {
     upload(S.St_val32, f2);
   }
   S.St_ptr_h = Stu.ptr;
-  auto chunk = [](const CsrD& M, DevBuf& crow, DevBuf& cb, DevBuf& ce) {
-    std::vector<int32_t> r;
-    std::vector<int64_t> b, e;
-    for (int i = 0; i < M.n; ++i)
-      for (int64_t p = M.ptr[i]; p < M.ptr[i + 1]; p += 256) {
-        r.push_back(i);
-        b.push_back(p);
-        e.push_back(std::min<int64_t>(p + 256, M.ptr[i + 1]));
-      }
-    upload(crow, r);
-    upload(cb, b);
-    upload(ce, e);
-    return (int)r.size();
-  };
-  S.nS_chunks = chunk(Su, S.S_crow, S.S_cbeg, S.S_cend);
-  {  // rows of S are contiguous column ranges (postordered factor): each chunk keeps its first column
-    std::vector<int32_t> c0;
-    c0.reserve(S.nS_chunks);
-    for (int i = 0; i < Su.n; ++i)
-      for (int64_t p = Su.ptr[i]; p < Su.ptr[i + 1]; p += 256) {
-        c0.push_back(Su.col[p]);
-        for (int64_t q = p; q < std::min<int64_t>(p + 256, Su.ptr[i + 1]); ++q)
-          if (Su.col[q] != Su.col[p] + (int32_t)(q - p))
-            throw Error{NCPADJ_ERR_NOT_FACTORED, "internal: a row of the sparse inverse is not a column range"};
-      }
-    upload(S.S_c0, c0);
+  {  // rows of S are contiguous column ranges (postordered factor): a chunk needs only its first column
+    S.S_ptr_h = Su.ptr;
+    S.S_first_h.assign(Su.n, 0);
+    for (int i = 0; i < Su.n; ++i) {
+      const int64_t p0 = Su.ptr[i], p1 = Su.ptr[i + 1];
+      if (p1 > p0) S.S_first_h[i] = Su.col[p0];
+      for (int64_t q = p0; q < p1; ++q)
+        if (Su.col[q] != Su.col[p0] + (int32_t)(q - p0))
+          throw Error{NCPADJ_ERR_NOT_FACTORED, "internal: a row of the sparse inverse is not a column range"};
+    }
   }
-  S.nSt_chunks = chunk(Stu, S.St_crow, S.St_cbeg, S.St_cend);
+  rechunk(S, S.chunk);
   // host-side resources, made once per scene (a refactor rebuilds only the arrays above)
   S.flags.ensure(FLAG_COUNT * sizeof(int));
   if (!S.flags_host) NCPADJ_CUDA_TRY(cudaMallocHost(&S.flags_host, FLAG_COUNT * sizeof(int)));
@@ -859,6 +872,7 @@ struct Engine {
                     S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                     S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                     S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};
+    sinv.chunk = S.chunk;
     S.xpos.ensure(sizeof(double) * N + sizeof(float) * N + 64);
     sinv.xpos = S.xpos.as<double>();
     sinv.xpos32 = reinterpret_cast<float*>(S.xpos.as<double>() + N);
@@ -1250,7 +1264,10 @@ struct Engine {
                                 (uintptr_t)flexible_gmres(), (uintptr_t)S.fgmres.p,
                                 (uintptr_t)S.gs_map_dev, (uintptr_t)blk_c0.size(), (uintptr_t)S.xsplit.p,
                                 (uintptr_t)S.capmeta.p, (uintptr_t)cap_nmax, (uintptr_t)cap_refine,
-                                (uintptr_t)S.capres.p};
+                                (uintptr_t)S.capres.p, (uintptr_t)S.chunk, (uintptr_t)S.nS_chunks,
+                                (uintptr_t)S.nSt_chunks, (uintptr_t)S.S_crow.p, (uintptr_t)S.S_cbeg.p,
+                                (uintptr_t)S.S_cend.p, (uintptr_t)S.S_c0.p, (uintptr_t)S.St_crow.p,
+                                (uintptr_t)S.St_cbeg.p, (uintptr_t)S.St_cend.p};
     for (size_t b = 0; b < blk_c0.size(); ++b) {
       k.push_back((uintptr_t)blk_c0[b]);
       k.push_back((uintptr_t)blk_nc[b]);
@@ -2826,6 +2843,22 @@ ncpadj_status ncpadj_scene_set_fibres(ncpadj_scene scene, const double* fibre) {
   }
 }
 
+ncpadj_status ncpadj_scene_set_chunk(ncpadj_scene scene, int32_t entries) {
+  g_last_error.clear();
+  try {
+    NCPADJ_REQUIRE(scene, "NULL scene");
+    NCPADJ_REQUIRE(entries == 128 || entries == 256 || entries == 512, "entries must be 128, 256 or 512");
+    Scene& S = scene->s;
+    if (scene->ctx) NCPADJ_CUDA_TRY(cudaSetDevice(scene->ctx->c.device));
+    if (entries != S.chunk) rechunk(S, entries);
+    return NCPADJ_OK;
+  } catch (const Error& e) {
+    return fail(e);
+  } catch (const std::exception& e) {
+    return fail(Error{NCPADJ_ERR_OOM, e.what()});
+  }
+}
+
 ncpadj_status ncpadj_scene_set_model(ncpadj_scene scene, const int32_t* model) {
   g_last_error.clear();
   try {
@@ -2885,6 +2918,7 @@ ncpadj_status ncpadj_elastic_solve(ncpadj_ctx ctx, ncpadj_scene scene, const dou
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
+    a.chunk = S.chunk;
     S.xpos.ensure(sizeof(double) * 3 * (size_t)S.nv + 64);
     a.xpos = S.xpos.as<double>();
     launch_ainv(a, x, S.io.as<double>(), y, st);
@@ -2911,6 +2945,7 @@ ncpadj_status ncpadj_elastic_solve_mixed(ncpadj_ctx ctx, ncpadj_scene scene, con
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>(), S.S_val32.as<float>(), S.St_val32.as<float>()};
+    a.chunk = S.chunk;
     S.xpos.ensure(sizeof(double) * n3 + sizeof(float) * n3 + 64);
     a.xpos = S.xpos.as<double>();
     a.xpos32 = reinterpret_cast<float*>(S.xpos.as<double>() + n3);

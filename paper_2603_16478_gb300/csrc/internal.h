@@ -96,6 +96,7 @@ struct Scene {
   DevBuf S_val32, St_val32;       // FP32 copies of the values (mixed precision)
   DevBuf S_crow, S_cbeg, S_cend, St_crow, St_cbeg, St_cend;  // row chunks (<= 256 entries)
   int nS_chunks = 0, nSt_chunks = 0;
+  int chunk = 256;  // entries per chunk of the A^{-1} product (128, 256 or 512; ncpadj_scene_set_chunk)
   int64_t nnz_S = 0;
   int64_t nnz_L = 0;
   double ms_factor = 0;
@@ -115,6 +116,8 @@ struct Scene {
   std::vector<double> mat_E, mat_nu;  // [nt]
   std::vector<double> mat_bend;       // [n_scenes] (shells)
   std::vector<int64_t> St_ptr_h;  // host copy (Delassus pair scheduling)
+  std::vector<int64_t> S_ptr_h;   // host copies of S's row pointers and each row's first column (chunking)
+  std::vector<int32_t> S_first_h;
 
   // per-call workspace
   DevBuf bsr64, bsr32;            // block values

@@ -264,7 +264,7 @@ struct SinvArgs {
   const int32_t* St_col;  // positions
   const double* St_val;
   const int32_t* perm;
-  // chunks of at most 256 entries of the rows of S and S^T
+  // chunks of at most `chunk` entries (128, 256 or 512) of the rows of S and S^T
   int nS, nSt;
   const int32_t *S_crow, *St_crow;
   const int64_t *S_cbeg, *S_cend, *St_cbeg, *St_cend;
@@ -274,6 +274,7 @@ struct SinvArgs {
   // so the product gathers x contiguously
   double* xpos = nullptr;
   float* xpos32 = nullptr;
+  int chunk = 256;
 };
 void launch_ainv(const SinvArgs& a, const double* x, double* w, double* y, cudaStream_t s);
 // Step-indexed forms for a captured GMRES step (j = *jp on the device; V_{j+1} = V + (j + 1) ld):

@@ -172,12 +172,12 @@ __global__ void k_diag_inv(int nv, const int32_t* diag_slot, const double* val, 
 }
 
 // Chunked product of a CSR matrix with 3 right-hand sides: chunk k covers entries
-// [cbeg[k], cend[k]) of row crow[k] (at most 256), one warp per chunk with 8 loads in flight per
+// [cbeg[k], cend[k]) of row crow[k] (at most 32 PL), one warp per chunk with PL loads in flight per
 // lane; partial sums are added atomically into y[3 out(row) + r] (y zeroed by the caller),
 // out(row) = omap ? omap[row] : row.  Splitting the long rows near the elimination-tree root over
 // many warps keeps the product bandwidth- rather than latency-bound.
 // jp (nullable): x is taken at x + (*jp) * xld -- the step index of a captured GMRES step
-template <typename V, typename X, typename Y, typename Acc = Y>
+template <typename V, typename X, typename Y, typename Acc = Y, int PL = 8>
 __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t* __restrict__ crow,
                                                      const int64_t* __restrict__ cbeg, const int64_t* __restrict__ cend,
                                                      const int32_t* __restrict__ col, const V* __restrict__ val,
@@ -191,16 +191,16 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
   if (!mk.on(crow[k])) return;  // whole warp: one chunk per warp (positions keep their scene)
   const int64_t b = cbeg[k], e = cend[k];
   Acc a0 = 0, a1 = 0, a2 = 0;
-  int c[8];
-  V s[8];
+  int c[PL];
+  V s[PL];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < PL; ++u) {
     const int64_t p = b + lane + 32 * u;
     c[u] = (p < e) ? col[p] : -1;
     s[u] = (p < e) ? val[p] : V(0);
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u)
+  for (int u = 0; u < PL; ++u)
     if (c[u] >= 0) {
       a0 += (Acc)s[u] * (Acc)x[3 * c[u]];
       a1 += (Acc)s[u] * (Acc)x[3 * c[u] + 1];
@@ -220,10 +220,10 @@ __global__ void __launch_bounds__(256) k_spmv_chunks(int nchunks, const int32_t*
 
 // The product with S = L^{-1} in a postordered elimination tree: row i of S holds exactly the
 // descendants of i, the contiguous column range [i - size(i) + 1, i], so no column index is stored.
-// Chunk k covers entries [cbeg[k], cend[k]) of row crow[k], whose columns run from c0[k] upwards;
-// one warp per chunk, 8 values per lane in flight, x read contiguously; partial sums added
+// Chunk k covers entries [cbeg[k], cend[k]) of row crow[k] (at most 32 PL), whose columns run from
+// c0[k] upwards; one warp per chunk, PL values per lane in flight, x read contiguously; partial sums added
 // atomically into y[3 row + r] (y zeroed by the caller).
-template <typename V, typename X, typename Y, typename Acc = Y>
+template <typename V, typename X, typename Y, typename Acc = Y, int PL = 8>
 __global__ void __launch_bounds__(256) k_spmv_range_chunks(int nchunks, const int32_t* __restrict__ crow,
                                                            const int64_t* __restrict__ cbeg,
                                                            const int64_t* __restrict__ cend,
@@ -238,14 +238,14 @@ __global__ void __launch_bounds__(256) k_spmv_range_chunks(int nchunks, const in
   const int64_t b = cbeg[k], e = cend[k];
   const int col0 = c0[k];
   Acc a0 = 0, a1 = 0, a2 = 0;
-  V s[8];
+  V s[PL];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < PL; ++u) {
     const int64_t p = b + lane + 32 * u;
     s[u] = (p < e) ? val[p] : V(0);
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < PL; ++u) {
     const int off = lane + 32 * u;
     if (b + off < e) {
       const size_t c = 3 * (size_t)(col0 + off);
@@ -683,31 +683,52 @@ void launch_diag_inv(int nv, const int32_t* diag_slot, const double* val, const 
   g_launches += 1;
   k_diag_inv<<<nblk(3L * nv, 256), 256, 0, s>>>(nv, diag_slot, val, val32, dinv);
 }
+// the product kernels at the scene's chunk length (entries per warp: 32 x 4, 8 or 16 per lane)
+template <typename V, typename X, typename Y, typename Acc>
+static void range_product(const SinvArgs& a, const V* val, const X* x, Y* y, cudaStream_t s, const Mask& mk) {
+  const dim3 g(nblk(32L * a.nS, 256));
+  if (a.chunk == 128)
+    k_spmv_range_chunks<V, X, Y, Acc, 4><<<g, 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, val, x, y, mk);
+  else if (a.chunk == 512)
+    k_spmv_range_chunks<V, X, Y, Acc, 16><<<g, 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, val, x, y, mk);
+  else
+    k_spmv_range_chunks<V, X, Y, Acc, 8><<<g, 256, 0, s>>>(a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, val, x, y, mk);
+}
+template <typename V, typename X, typename Y, typename Acc>
+static void transpose_product(const SinvArgs& a, const V* val, const X* w, Y* y, cudaStream_t s, const Mask& mk) {
+  const dim3 g(nblk(32L * a.nSt, 256));
+  if (a.chunk == 128)
+    k_spmv_chunks<V, X, Y, Acc, 4><<<g, 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, val, a.perm, w,
+                                                     y, nullptr, 0, mk);
+  else if (a.chunk == 512)
+    k_spmv_chunks<V, X, Y, Acc, 16><<<g, 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, val, a.perm, w,
+                                                      y, nullptr, 0, mk);
+  else
+    k_spmv_chunks<V, X, Y, Acc, 8><<<g, 256, 0, s>>>(a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, val, a.perm, w,
+                                                     y, nullptr, 0, mk);
+}
+
 void launch_sinv_half1(const SinvArgs& a, const double* x, double* w, cudaStream_t s, const Mask& mk) {
   g_launches += 2;
   k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos, mk);
   cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_range_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val, a.xpos, w, mk);
+  range_product<double, double, double, double>(a, a.S_val, a.xpos, w, s, mk);
 }
 void launch_sinv_half2(const SinvArgs& a, const double* w, double* y, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<double, double, double><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(
-      a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val, a.perm, w, y, nullptr, 0, mk);
+  transpose_product<double, double, double, double>(a, a.St_val, w, y, s, mk);
 }
 void launch_sinv_half1_32(const SinvArgs& a, const double* x, float* w32, cudaStream_t s, const Mask& mk) {
   g_launches += 2;
   k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, x, nullptr, 0, a.perm, a.xpos32, mk);
   cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
-  k_spmv_range_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-      a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val32, a.xpos32, w32, mk);
+  range_product<float, float, float, float>(a, a.S_val32, a.xpos32, w32, s, mk);
 }
 void launch_sinv_half2_32(const SinvArgs& a, const float* w32, double* y, cudaStream_t s, const Mask& mk) {
   g_launches += 1;
   cudaMemsetAsync(y, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-  k_spmv_chunks<float, float, double, float><<<nblk(32L * a.nSt, 256), 256, 0, s>>>(
-      a.nSt, a.St_crow, a.St_cbeg, a.St_cend, a.St_col, a.St_val32, a.perm, w32, y, nullptr, 0, mk);
+  transpose_product<float, float, double, float>(a, a.St_val32, w32, y, s, mk);
 }
 void launch_path_gather(int nc, const int32_t* cvertex, const int32_t* iperm, const SinvArgs& a, const double* w,
                         const float* w32, const double* frame, const double* cdata, int transpose, double* sc,
@@ -847,13 +868,11 @@ void launch_sinv_half1_idx(const SinvArgs& a, const double* xbase, long xld, con
   if (w32) {
     k_to_position<float><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos32, mk);
     cudaMemsetAsync(w32, 0, sizeof(float) * 3 * (size_t)a.nv, s);
-    k_spmv_range_chunks<float, float, float, float><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val32, a.xpos32, w32, mk);
+    range_product<float, float, float, float>(a, a.S_val32, a.xpos32, w32, s, mk);
   } else {
     k_to_position<double><<<nblk(3L * a.nv, 256), 256, 0, s>>>(a.nv, xbase, jp, xld, a.perm, a.xpos, mk);
     cudaMemsetAsync(w, 0, sizeof(double) * 3 * (size_t)a.nv, s);
-    k_spmv_range_chunks<double, double, double><<<nblk(32L * a.nS, 256), 256, 0, s>>>(
-        a.nS, a.S_crow, a.S_cbeg, a.S_cend, a.S_c0, a.S_val, a.xpos, w, mk);
+    range_product<double, double, double, double>(a, a.S_val, a.xpos, w, s, mk);
   }
 }
 void launch_multi_axpy(int n, int nvec, const double* V, long ld, const double* coef, double* w, cudaStream_t s) {

@@ -68,6 +68,7 @@ extern "C" ncpadj_status ncpadj_elastic_solve_noalloc(ncpadj_ctx ctx, ncpadj_sce
                S.St_col.as<int32_t>(), S.St_val.as<double>(), S.perm.as<int32_t>(), S.nS_chunks, S.nSt_chunks,
                S.S_crow.as<int32_t>(), S.St_crow.as<int32_t>(), S.S_cbeg.as<int64_t>(), S.S_cend.as<int64_t>(),
                S.St_cbeg.as<int64_t>(), S.St_cend.as<int64_t>()};
+    a.chunk = S.chunk;
     a.xpos = w + 3 * (size_t)kNoAllocMaxVerts;
     // the product zeroes the scratch before accumulating into it, so earlier calls leave nothing behind
     launch_ainv(a, x, w, y, (cudaStream_t)stream);

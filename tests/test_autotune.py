@@ -9,11 +9,30 @@ from paper_2603_16478_gb300 import autotune as at
 
 def test_default_candidates_cover_every_variant_and_restart():
     c = at.default_candidates(451)
-    assert len(c) == 3 * 3
+    assert len(c) == 5 * 3
     assert {(x["precision"], x["cap_precision"]) for x in c} == set(at.PRECISION_VARIANTS)
     assert {x["restart"] for x in c} == {32, 64, 128} and {x["cap_block"] for x in c} == {0}
     big = at.default_candidates(2329)
-    assert len(big) == 3 * 3 * 2 and {x["cap_block"] for x in big} == {0, 1024}
+    assert len(big) == 5 * 3 * 2 and {x["cap_block"] for x in big} == {0, 1024}
+
+
+def test_tune_shape_times_every_shape_and_applies_the_fastest():
+    applied, cost = [], {128: 3.0, 256: 2.0, 512: 2.5, 1024: None}
+
+    def apply(sh):
+        applied.append(sh)
+
+    def measure():
+        c = cost[applied[-1]]
+        if c is None:
+            raise RuntimeError("INVALID_ARG")
+        return c
+
+    best, times = at.tune_shape(apply, measure, [128, 256, 512, 1024])
+    assert best == 256 and applied[-1] == 256
+    assert times[128] == 3.0 and times[512] == 2.5 and math.isinf(times[1024])
+    with pytest.raises(ValueError):
+        at.tune_shape(apply, lambda: (_ for _ in ()).throw(RuntimeError("x")), [128])
 
 
 def test_select_takes_the_fastest_accurate_success():
@@ -72,13 +91,16 @@ def test_tune_adjoint_glue_with_fake_device(monkeypatch, tmp_path):
     from paper_2603_16478_gb300 import binding
 
     clock = {"t": 0.0, "calls": 0}
-    base = {("fp64", "fp64"): 10.0, ("mixed", "fp64"): 8.0, ("mixed", "mixed"): 5.0}
-    err = {("fp64", "fp64"): 0.0, ("mixed", "fp64"): 5e-5, ("mixed", "mixed"): 2e-3}
+    base = {("fp64", "fp64"): 10.0, ("mixed", "fp64"): 8.0, ("mixed", "mixed"): 5.0, ("mixed", "tf32x3"): 4.0,
+            ("mixed", "refined"): 4.5}
+    err = {("fp64", "fp64"): 0.0, ("mixed", "fp64"): 5e-5, ("mixed", "mixed"): 2e-3, ("mixed", "tf32x3"): 5e-4,
+           ("mixed", "refined"): 5e-5}
+    chunk_cost = {128: 1.0, 256: 0.0, 512: -0.25}
 
     def fake_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv, *, precision, cap_precision, restart,
                      cap_block, **kw):
         clock["calls"] += 1
-        clock["t"] += base[(precision, cap_precision)] - (0.5 if restart == 128 else 0.0)
+        clock["t"] += base[(precision, cap_precision)] + chunk_cost[scene.chunk] - (0.5 if restart == 128 else 0.0)
         e = err[(precision, cap_precision)]
         g = {"dL_dq_prev": torch.ones(4, 3, dtype=torch.float64) * (1 + e), "dL_dE": torch.ones(6, dtype=torch.float64)}
         return g, {"iterations": 30}
@@ -101,14 +123,19 @@ def test_tune_adjoint_glue_with_fake_device(monkeypatch, tmp_path):
     monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
     monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
     monkeypatch.setattr(torch.cuda, "synchronize", lambda dev=None: None)
-    scene = types.SimpleNamespace(n_verts=4961, n_tets=20000, info=lambda: {"n_scenes": 1})
+    scene = types.SimpleNamespace(n_verts=4961, n_tets=20000, info=lambda: {"n_scenes": 1}, chunk=256)
+    scene.set_chunk = lambda n: setattr(scene, "chunk", int(n))
     contacts = types.SimpleNamespace(n=451)
     q = torch.zeros(4, 3, dtype=torch.float64)
     cache = at.Cache(str(tmp_path / "tune.json"))
     ch = at.tune_adjoint(scene, contacts, q, q, q, q, None, repeats=3, cache=cache)
-    assert ch.options == {"precision": "mixed", "cap_precision": "fp64", "restart": 128, "cap_block": 0}
-    assert ch.ms == 7.5 and abs(ch.rel_err - 5e-5) < 1e-12
-    assert len(ch.trials) == 9 and clock["calls"] == 1 + 9 * (1 + 3)  # reference, then warm-up + repeats each
+    # launch shape first (timed with the tensor-core variant), then the options at that shape
+    assert ch.chunk == 512 and scene.chunk == 512 and ch.chunk_ms == {128: 5.0, 256: 4.0, 512: 3.75}
+    assert ch.options == {"precision": "mixed", "cap_precision": "tf32x3", "restart": 128, "cap_block": 0}
+    assert ch.ms == 3.25 and abs(ch.rel_err - 5e-4) < 1e-12
+    assert len(ch.trials) == 15 and clock["calls"] == 1 + 3 * (1 + 3) + 15 * (1 + 3)
     calls = clock["calls"]
+    scene.chunk = 256
     again = at.tune_adjoint(scene, contacts, q, q, q, q, None, cache=at.Cache(str(tmp_path / "tune.json")))
     assert again.options == ch.options and clock["calls"] == calls  # from the cache, nothing run
+    assert again.chunk == 512 and scene.chunk == 512                # the cached shape is applied
