@@ -755,6 +755,9 @@ def main():
                     help="build the scene and run only the A^-1 roofline measurement (for profiler captures)")
     ap.add_argument("--blocks", type=int, default=64,
                     help="--roofline-only batched: the first N blocks of the batch (smaller profiler captures)")
+    ap.add_argument("--inverse-only", type=int, default=0, metavar="N",
+                    help="time only the tensor-core capacitance inverse (ncpadj_dense_inverse, TF32X3) of a seeded "
+                         "N x N matrix, 3 I + G / sqrt(N) (for profiler captures)")
     ap.add_argument("--chunk", type=int, default=0, choices=[0, 128, 256, 512],
                     help="chunk length of the A^-1 product (0: tuned by timing; with --roofline-only: 256)")
     ap.add_argument("--batch-only", action="store_true",
@@ -793,6 +796,24 @@ def main():
         print(json.dumps({"roofline_only": args.roofline_only, "blocks": args.blocks, "chunk": scene.chunk,
                           "info": scene.info(),
                           "roofline": apply_roofline(pkg, torch, dev, scene, 10, precision="mixed")}))
+        return
+
+    if args.inverse_only:
+        from paper_2603_16478_gb300.binding import dense_inverse
+        ctx = pkg.Context(local)
+        n = args.inverse_only
+        rng = np.random.default_rng(n)
+        M = torch.tensor(np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n), device=dev)
+        ts = []
+        for _ in range(max(2, args.warmup + 1)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B = dense_inverse(ctx, M, "tf32x3")
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        res = float(torch.linalg.norm(B @ M - torch.eye(n, dtype=M.dtype, device=dev)).item()) / np.sqrt(n)
+        print(json.dumps({"inverse_only": n, "ms_per_call": statistics.median(ts[1:]), "residual_rms": res}))
         return
 
     if args.cloth_only:
