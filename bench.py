@@ -498,6 +498,51 @@ def union_contacts(pkg, torch, T, cts, off):
                         T(np.concatenate([np.zeros(c.n, np.int32) for c in cts]), torch.int32), 1)
 
 
+def rollout_leg(pkg, torch, dev, n_steps=30):
+    """Config 2's differentiable rollout: the 20,000-tet beam on the 20-degree incline, n_steps steps at
+    h = 1/100 through StepFn (forward: ncpadj_forward_step; backward: ncpadj_adjoint_step), checkpointed
+    every step, loss = |COM(q_T) - COM_tgt|^2, gradients w.r.t. E, nu and mu.  Times one rollout
+    (forward pass, then backward with the forward recomputed per checkpoint) for the FP64 and the mixed
+    step, after one untimed rollout of each; reports steps per second of the whole forward + backward and
+    the mixed gradients' error against FP64."""
+    import synth
+    from paper_2603_16478_gb300.rollout import PlaneCollider, Simulator, rollout
+    pb = synth.beam_incline()
+    sc = pb.scene
+    ctx = pkg.Context(dev.index or 0)
+    scene = pkg.Scene(ctx, sc.X, sc.tets, sc.E, sc.nu, sc.density, sc.h)
+    planes = [PlaneCollider(tuple(p.normal), p.offset, tuple(p.t1), tuple(p.t2), i) for i, p in enumerate(sc.planes)]
+    tgt = torch.as_tensor(pb.q0.mean(0) + 5e-3 * np.asarray(sc.planes[0].t1), device=dev)
+    out, grads = {}, {}
+    for prec, cap in (("fp64", "fp64"), ("mixed", "tf32x3")):
+        sim = Simulator(scene, planes, torch.as_tensor(sc.contact_candidates, device=dev), sc.margin, sc.eps,
+                        tuple(sc.gravity), n_regions=len(sc.planes), precision=prec, cap_precision=cap)
+        for rep in range(2):
+            E = torch.tensor(float(sc.E[0]), dtype=torch.float64, device=dev, requires_grad=True)
+            nu = torch.tensor(float(sc.nu[0]), dtype=torch.float64, device=dev, requires_grad=True)
+            mu = torch.tensor([p.mu for p in sc.planes], dtype=torch.float64, device=dev, requires_grad=True)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            qT, _ = rollout(sim, torch.as_tensor(pb.q0, device=dev), torch.as_tensor(pb.v0, device=dev), E, nu, mu,
+                            n_steps, checkpoint_every=1)
+            loss = ((qT.mean(0) - tgt) ** 2).sum()
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            loss.backward()
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+        grads[prec] = np.array([E.grad.item(), nu.grad.item(), *mu.grad.cpu().numpy()])
+        out[prec] = {"forward_s": t1 - t0, "backward_s": t2 - t1,
+                     "steps_per_s": n_steps / (t2 - t0), "backward_steps_per_s": n_steps / (t2 - t1),
+                     "capacitance": cap}
+    out["mixed"]["max_rel_err_vs_fp64"] = float(np.linalg.norm(grads["mixed"] - grads["fp64"]) /
+                                               np.linalg.norm(grads["fp64"]))
+    out["workload"] = (f"beam 20,000 tets on a 20-degree incline, {n_steps}-step autograd rollout (h = 1/100, "
+                       "checkpoint every step), gradients of the final COM error w.r.t. E, nu, mu; the backward "
+                       "recomputes each step's forward before its adjoint")
+    return out
+
+
 def cloth_leg(pkg, torch, dev, steps, warmup, flush, sizes=(64, 512), n_fwd=5, max_newton=40):
     """The paper's batched cloth (Sec. 5.5.3): N cloth patches (1,024 vertices, 1,922 triangles each)
     with ARAP elasticity and isometric bending draping onto a frictionless sphere, E log-uniform in
@@ -746,6 +791,7 @@ def main():
     ap.add_argument("--no-models", action="store_true",
                     help="skip the co-rotational / ARAP / bindings timings on the beam")
     ap.add_argument("--no-cloth", action="store_true", help="skip the batched cloth measurement (shells)")
+    ap.add_argument("--no-rollout", action="store_true", help="skip the 30-step beam rollout measurement")
     ap.add_argument("--cloth-only", action="store_true", help="run only the batched cloth measurement")
     ap.add_argument("--cloth-sizes", default="64,512", help="numbers of cloths of the batched cloth measurement")
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
@@ -922,6 +968,11 @@ def main():
                                         with_models=not args.no_models)
             except Exception as e:  # noqa: BLE001
                 side["beam"] = {"error": str(e)[:300]}
+        if not args.no_rollout:
+            try:
+                side["rollout"] = rollout_leg(pkg, torch, dev)
+            except Exception as e:  # noqa: BLE001
+                side["rollout"] = {"error": str(e)[:300]}
         if not args.no_cloth:
             try:
                 side["cloth"] = cloth_leg(pkg, torch, dev, max(3, args.steps // 4), 1, flush,
