@@ -727,7 +727,7 @@ def quadruped_measure(pkg, torch, dev, steps, warmup, scale):
     t0 = time.perf_counter()
     try:
         q, lam, fs = pkg.forward_step(scene, contacts, q0, v0, None, tuple(sc.gravity), eps=sc.eps, max_newton=30,
-                                      act=act)
+                                      act=act, cap_precision="tf32x3")
     except pkg.NcpadjError as e:
         if not hasattr(e, "state"):
             raise
@@ -738,7 +738,7 @@ def quadruped_measure(pkg, torch, dev, steps, warmup, scale):
     dq[:, 0] = -1.0 / q.shape[0]  # L = -mean x
     lam = lam.contiguous()
     stream = torch.cuda.Stream(dev)
-    akw = dict(eps=sc.eps, precision="mixed", cap_precision="mixed", stream=stream.cuda_stream,
+    akw = dict(eps=sc.eps, precision="mixed", cap_precision="tf32x3", stream=stream.cuda_stream,
                want=("dL_dact", "dL_dmu", "z"))
     for _ in range(warmup):
         pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, **akw)
@@ -757,7 +757,7 @@ def quadruped_measure(pkg, torch, dev, steps, warmup, scale):
     for pc in ("woodbury", "elastic"):
         try:
             _, st = pkg.adjoint_step(scene, contacts, q, q0, lam, dq, None, eps=sc.eps, precision="mixed",
-                                     cap_precision="mixed", precond=pc, max_iters=2000, want=("z",))
+                                     cap_precision="tf32x3", precond=pc, max_iters=2000, want=("z",))
             iters[pc] = st["iterations"]
         except pkg.NcpadjError as e:
             iters[pc] = "not converged in 2000" if "NOT_CONVERGED" in str(e) else str(e)[:120]
@@ -779,6 +779,40 @@ def quadruped_measure(pkg, torch, dev, steps, warmup, scale):
 # --------------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------------
+def side_legs(args, pkg, torch, dev, flush):
+    """The single-scene and other side measurements the flags enable (each caught: an error is reported
+    in its place)."""
+    side = {}
+    if not args.no_beam:
+        try:
+            side["beam"] = beam_leg(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush,
+                                    with_models=not args.no_models)
+        except Exception as e:  # noqa: BLE001
+            side["beam"] = {"error": str(e)[:300]}
+    if not args.no_rollout:
+        try:
+            side["rollout"] = rollout_leg(pkg, torch, dev)
+        except Exception as e:  # noqa: BLE001
+            side["rollout"] = {"error": str(e)[:300]}
+    if not args.no_cloth:
+        try:
+            side["cloth"] = cloth_leg(pkg, torch, dev, max(3, args.steps // 4), 1, flush,
+                                      sizes=tuple(int(x) for x in args.cloth_sizes.split(",")))
+        except Exception as e:  # noqa: BLE001
+            side["cloth"] = {"error": str(e)[:300]}
+    if args.sphere:
+        try:
+            side["sphere"] = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)
+        except Exception as e:  # noqa: BLE001
+            side["sphere"] = {"error": str(e)[:300]}
+    if args.quadruped:
+        try:
+            side["quadruped"] = quadruped_measure(pkg, torch, dev, max(2, args.steps // 4), 1, args.quad_scale)
+        except Exception as e:  # noqa: BLE001
+            side["quadruped"] = {"error": str(e)[:300]}
+    return side
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -792,6 +826,8 @@ def main():
                     help="skip the co-rotational / ARAP / bindings timings on the beam")
     ap.add_argument("--no-cloth", action="store_true", help="skip the batched cloth measurement (shells)")
     ap.add_argument("--no-rollout", action="store_true", help="skip the 30-step beam rollout measurement")
+    ap.add_argument("--side-only", action="store_true",
+                    help="run only the side measurements the other flags enable (no batched headline)")
     ap.add_argument("--cloth-only", action="store_true", help="run only the batched cloth measurement")
     ap.add_argument("--cloth-sizes", default="64,512", help="numbers of cloths of the batched cloth measurement")
     ap.add_argument("--sphere", action="store_true", help="add the large contact-heavy sphere measurement")
@@ -860,6 +896,11 @@ def main():
             ts.append(e0.elapsed_time(e1))
         res = float(torch.linalg.norm(B @ M - torch.eye(n, dtype=M.dtype, device=dev)).item()) / np.sqrt(n)
         print(json.dumps({"inverse_only": n, "ms_per_call": statistics.median(ts[1:]), "residual_rms": res}))
+        return
+
+    if args.side_only:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"side": side_legs(args, pkg, torch, dev, flush)}))
         return
 
     if args.cloth_only:
@@ -962,33 +1003,7 @@ def main():
 
     side = {}
     if not args.batch_only and world == 1:
-        if not args.no_beam:
-            try:
-                side["beam"] = beam_leg(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush,
-                                        with_models=not args.no_models)
-            except Exception as e:  # noqa: BLE001
-                side["beam"] = {"error": str(e)[:300]}
-        if not args.no_rollout:
-            try:
-                side["rollout"] = rollout_leg(pkg, torch, dev)
-            except Exception as e:  # noqa: BLE001
-                side["rollout"] = {"error": str(e)[:300]}
-        if not args.no_cloth:
-            try:
-                side["cloth"] = cloth_leg(pkg, torch, dev, max(3, args.steps // 4), 1, flush,
-                                          sizes=tuple(int(x) for x in args.cloth_sizes.split(",")))
-            except Exception as e:  # noqa: BLE001
-                side["cloth"] = {"error": str(e)[:300]}
-        if args.sphere:
-            try:
-                side["sphere"] = sphere(pkg, torch, dev, max(3, args.steps // 4), 1)
-            except Exception as e:  # noqa: BLE001
-                side["sphere"] = {"error": str(e)[:300]}
-        if args.quadruped:
-            try:
-                side["quadruped"] = quadruped_measure(pkg, torch, dev, max(2, args.steps // 4), 1, args.quad_scale)
-            except Exception as e:  # noqa: BLE001
-                side["quadruped"] = {"error": str(e)[:300]}
+        side = side_legs(args, pkg, torch, dev, flush)
 
     # ---- CPU baseline: the oracle, one thread, on a seeded sample of the blocks at the GPU state ----
     # (the same runs give every GPU variant's gradient error against the oracle on those blocks)

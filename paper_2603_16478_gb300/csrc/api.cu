@@ -972,6 +972,41 @@ struct Engine {
     ccd = cd;
   }
 
+  // The tensor-core inverse pivots only inside its 64 x 64 diagonal blocks; where that meets a nearly
+  // singular block its result is no preconditioner.  One probe per capacitance block, y = 1:
+  // x = X y, r = y - C x (FP64 C); a block with ||r|| > 0.5 ||y|| is inverted again by the pivoted
+  // Gauss-Jordan of gj.cu (blocks of at most smax rows were inverted with full pivoting already).
+  void check_tc_inverses(int smax) {
+    const int nbk = (int)blk_c0.size();
+    S.capchk.ensure(sizeof(double) * 3 * ((size_t)ncap + 16));
+    double* yv = S.capchk.as<double>();
+    double* xv = yv + ncap + 16;
+    double* rv = xv + ncap + 16;
+    launch_fill(ncap, 1.0, yv, st);
+    launch_cap_apply_all(nbk, cap_nmax, S.capmeta.as<int64_t>(), Cm32, nullptr, piv, yv, xv, nullptr, st);
+    launch_cap_resid_all(nbk, cap_nmax, S.capmeta.as<int64_t>(), Cm, yv, xv, rv, nullptr, st);
+    std::vector<double> rh((size_t)ncap);
+    NCPADJ_CUDA_TRY(cudaMemcpyAsync(rh.data(), rv, sizeof(double) * ncap, cudaMemcpyDeviceToHost, st));
+    NCPADJ_CUDA_TRY(cudaStreamSynchronize(st));
+    cap_fallbacks = 0;
+    for (int k = 0; k < nbk; ++k) {
+      const int n_ = 3 * blk_nc[k];
+      if (n_ <= smax) continue;
+      double r2 = 0.0;
+      for (int i = 0; i < n_; ++i) r2 += rh[3 * (size_t)blk_c0[k] + i] * rh[3 * (size_t)blk_c0[k] + i];
+      if (std::isfinite(r2) && r2 <= 0.25 * n_) continue;
+      launch_convert_f32((long)n_ * n_, Cm + blk_moff[k], Cm32 + blk_moff[k], st);
+      if (!launch_gj_cols32(n_, Cm32 + blk_moff[k], S.capw.p, piv + 3 * (size_t)blk_c0[k], flags, C.sm_count, st)) {
+        cudaGetLastError();
+        throw Error{NCPADJ_ERR_UNSUPPORTED,
+                    "capacitance block of dimension " + std::to_string(n_) + " does not fit the direct inverse"};
+      }
+      NCPADJ_CUDA_TRY(cudaGetLastError());
+      ++cap_fallbacks;
+    }
+  }
+  int cap_fallbacks = 0;  // blocks the check sent back to the pivoted Gauss-Jordan (last set-up)
+
   void setup_precond() {
     if (precond == NCPADJ_PRECOND_JACOBI)
       launch_diag_inv(nv, S.diag_slot.as<int32_t>(), mixed ? nullptr : S.bsr64.as<double>(),
@@ -1044,6 +1079,7 @@ struct Engine {
         }
         NCPADJ_CUDA_TRY(cudaGetLastError());
       }
+      if (cap_tc) check_tc_inverses(smax);
       NCPADJ_CUDA_TRY(cudaEventRecord(S.ev[7], st));
       cap_timed = true;
       if (!cap_fp32 && mixed) launch_convert_f32((long)cap_elems, Cm, Cm32, st);  // FP64 inverses, FP32 apply

@@ -250,7 +250,18 @@ __global__ void k_cap_form_all(int nb, const int64_t* __restrict__ meta, const d
   if (C32) C32[meta[k] + idx] = (float)v;
 }
 
+__global__ void k_fill(long n, double v, double* x) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
 }  // namespace
+
+void launch_fill(long n, double v, double* x, cudaStream_t s) {
+  if (n <= 0) return;
+  g_launches += 1;
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, v, x);
+}
 
 void launch_cap_form_all(int nb, int mmax, const int64_t* meta, const int32_t* cvertex, const int32_t* iperm,
                          const int64_t* St_ptr, const int32_t* St_col, const double* St_val, double* Ds,

@@ -129,6 +129,7 @@ struct Scene {
   DevBuf recw;                    // scratch of the tensor-core capacitance inverse (separate from capw)
   DevBuf capmeta;                 // int64 [4][blocks]: the capacitance block table of the one-launch apply
   DevBuf capres;                  // residual of the refined capacitance solve (NCPADJ_REFINED) [3 contacts]
+  DevBuf capchk;                  // probe, product and residual of the tensor-core inverse check [3][3 contacts]
   DevBuf capids;                  // int32: the blocks small enough for the one-launch inverse
   DevBuf capsel;                  // the capacitance set: scores, kept indices, vertices, frames, K
   DevBuf red;                     // reduction scratch

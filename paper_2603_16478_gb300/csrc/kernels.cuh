@@ -109,6 +109,8 @@ void launch_cap_apply_all(int nb, int nmax, const int64_t* meta, const float* B3
 // at C + meta[k]), x_k in natural order: the residual of a refinement step of the capacitance solve
 void launch_cap_resid_all(int nb, int nmax, const int64_t* meta, const double* C, const double* y, const double* x,
                           double* r, const int* act, cudaStream_t s);
+// x[0..n) = v
+void launch_fill(long n, double v, double* x, cudaStream_t s);
 
 // ---- triangle (shell) elements and isometric bending (shell.cu) ---------------------------
 // TetArgs with the triangle layout: tets [nt][3], gvec [nt][6] (2-vectors g_0..g_2), slot [nt][9],
