@@ -226,8 +226,18 @@ def tune_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv=None, *, eps=1e-4
 
     chunk, chunk_ms = None, {}
     if chunks:
-        fast = {"precision": "mixed", "cap_precision": "tf32x3", "restart": 64, "cap_block": 0}
-        chunk, chunk_ms = tune_shape(scene.set_chunk, lambda: measure(fast)[0], list(chunks))
+        # timed with the tensor-core variant, or plain FP64 where that one fails on the scene; a scene on
+        # which neither runs keeps its chunk length
+        before = getattr(scene, "chunk", None)
+        for base in ({"precision": "mixed", "cap_precision": "tf32x3", "restart": 64, "cap_block": 0},
+                     {"precision": "fp64", "cap_precision": "fp64", "restart": 64, "cap_block": 0}):
+            try:
+                chunk, chunk_ms = tune_shape(scene.set_chunk, lambda b=base: measure(b)[0], list(chunks))
+                break
+            except ValueError:
+                chunk, chunk_ms = None, {}
+        if chunk is None and before is not None:
+            scene.set_chunk(before)
     choice = tune(measure, candidates or default_candidates(nc), reference, max_rel_err,
                   norm=lambda x: float(torch.linalg.norm(x.double() if hasattr(x, "double") else torch.tensor(x))))
     choice.chunk, choice.chunk_ms = chunk, chunk_ms

@@ -293,11 +293,8 @@ void launch_cap_resid_all(int nb, int nmax, const int64_t* meta, const double* C
   if (nb <= 0 || nmax <= 0) return;
   g_launches += 1;
   const size_t sm = sizeof(double) * (size_t)nmax;
-  static thread_local size_t sm_set = 0;
-  if (sm > 48 * 1024 && sm > sm_set) {
+  if (sm > 48 * 1024)  // per device: set on every call that needs it
     cudaFuncSetAttribute(k_cap_resid_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    sm_set = sm;
-  }
   k_cap_resid_all<<<dim3((nmax + 3) / 4, nb), 256, sm, s>>>(nb, meta, C, y, x, r, act);
 }
 

@@ -139,3 +139,55 @@ def test_tune_adjoint_glue_with_fake_device(monkeypatch, tmp_path):
     again = at.tune_adjoint(scene, contacts, q, q, q, q, None, cache=at.Cache(str(tmp_path / "tune.json")))
     assert again.options == ch.options and clock["calls"] == calls  # from the cache, nothing run
     assert again.chunk == 512 and scene.chunk == 512                # the cached shape is applied
+
+
+def test_tune_adjoint_shape_stage_falls_back_to_fp64_and_keeps_the_chunk(monkeypatch):
+    """Where the tensor-core variant fails on a scene the launch shape is timed with plain FP64; where
+    nothing runs the scene keeps its chunk length and the option stage still reports the failures."""
+    import contextlib
+    import types
+
+    import torch
+
+    from paper_2603_16478_gb300 import binding
+
+    clock = {"t": 0.0}
+    broken = {("mixed", "tf32x3")}
+    cost = {128: 3.0, 256: 2.0, 512: 2.5}
+
+    def fake_adjoint(scene, contacts, q, q_prev, lam, dL_dq, dL_dv, *, precision, cap_precision, restart,
+                     cap_block, **kw):
+        if (precision, cap_precision) in broken or scene.dead:
+            raise RuntimeError("ncpadj NOT_CONVERGED")
+        clock["t"] += cost[scene.chunk]
+        return {"dL_dE": torch.ones(3, dtype=torch.float64)}, {"iterations": 10}
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            self.t = clock["t"]
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(binding, "adjoint_step", fake_adjoint)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda dev=None: types.SimpleNamespace(cuda_stream=0))
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda dev=None: None)
+    scene = types.SimpleNamespace(n_verts=10, n_tets=20, info=lambda: {"n_scenes": 1}, chunk=512, dead=False)
+    scene.set_chunk = lambda n: setattr(scene, "chunk", int(n))
+    q = torch.zeros(2, 3, dtype=torch.float64)
+    cands = [{"precision": "fp64", "cap_precision": "fp64", "restart": 64, "cap_block": 0}]
+    ch = at.tune_adjoint(scene, types.SimpleNamespace(n=0), q, q, q, q, None, candidates=cands, repeats=1)
+    assert ch.chunk == 256 and scene.chunk == 256 and ch.chunk_ms == {128: 3.0, 256: 2.0, 512: 2.5}
+    # nothing runs at all: the reference call itself fails before any stage
+    scene.dead, scene.chunk = True, 512
+    with pytest.raises(RuntimeError):
+        at.tune_adjoint(scene, types.SimpleNamespace(n=0), q, q, q, q, None, candidates=cands, repeats=1)
+    assert scene.chunk == 512
