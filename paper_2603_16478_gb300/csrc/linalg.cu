@@ -464,10 +464,8 @@ __global__ void k_cap_form(int nc, const double* __restrict__ Ds, const double* 
   C[idx] = (R == Cc ? 1.0 : 0.0) + h2 * Ds[(size_t)a * nc + b] * acc;
 }
 
-// ---- cooperative Gauss-Jordan inversion -------------------------------------------------
+// ---- vector kernels of the Krylov solves -----------------------------------------------
 
-// Grid-wide barrier for a cooperative launch, with a bounded wait: after ~1 s of spinning it
-// sets FLAG_TIMEOUT and lets the block go on; every block then stops at its next barrier.
 __global__ void k_axpby(int n, double a, const double* x, double b, const double* y, double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + b * (y ? y[i] : 0.0);
